@@ -1,0 +1,347 @@
+"""FP64 CPU oracle of the DSMC collision step (arXiv 2602.21244).
+
+TEST INFRASTRUCTURE ONLY: only tests/, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  The CUDA library never calls it, and it shares no code with it.
+
+The heavy parts are plain C in ``dsmc_oracle.c`` (built here with gcc,
+``-ffp-contract=off``); the training oracle is numpy in ``train.py``.  Every
+function cites the section or equation of the paper it follows; readings of
+silent or ambiguous passages are listed in the C file header.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dsmc_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+KB = 1.380649e-23
+
+# Philox tags (reading R1 of the oracle header)
+TAG_NTC, TAG_CAND, TAG_ISO, TAG_JAGER, TAG_NOISE, TAG_HARVEST = 1, 2, 3, 4, 5, 6
+
+
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the C oracle with gcc (no FMA contraction)."""
+    with _lock:
+        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+            cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                   "-o", _LIB + ".tmp", _SRC, "-lm"]
+            subprocess.run(cmd, check=True)
+            os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+class Gas(C.Structure):
+    _fields_ = [("mass", C.c_double), ("d_ref", C.c_double), ("omega", C.c_double),
+                ("T_ref", C.c_double), ("fn_over_vc", C.c_double), ("dt", C.c_double),
+                ("seed", C.c_uint64), ("model", C.c_int32), ("pad_", C.c_int32),
+                ("b_max", C.c_double)]
+
+
+class Pot(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pad_", C.c_int32), ("A", C.c_double),
+                ("a1", C.c_double), ("a2", C.c_double), ("am1", C.c_double),
+                ("am2", C.c_double), ("beta", C.c_double), ("C", C.c_double * 6),
+                ("R_eps", C.c_double), ("At", C.c_double), ("at", C.c_double),
+                ("d_hs", C.c_double), ("kappa", C.c_double), ("p", C.c_double)]
+
+
+class Mlp(C.Structure):
+    _fields_ = [("d_in", C.c_int32), ("width", C.c_int32), ("n_hidden", C.c_int32),
+                ("d_out", C.c_int32), ("act", C.c_int32), ("pad_", C.c_int32),
+                ("sigma_v", C.c_double), ("T_ref", C.c_double), ("eps", C.c_double)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        P = C.POINTER
+        d, i32, i64, u32, u64 = C.c_double, C.c_int32, C.c_int64, C.c_uint32, C.c_uint64
+        vp = C.c_void_p
+        sig = {
+            "or_philox4x32_10": (None, [vp, vp, vp]),
+            "or_philox_stream": (None, [u64, u32, u64, u32, u32, i64, vp]),
+            "or_u53": (d, [u32, u32]),
+            "or_sigma": (d, [P(Gas), d]),
+            "or_sigma_g_max_init": (None, [P(Gas), i32, vp, d, vp]),
+            "or_sort_cells": (C.c_int, [i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+            "or_cell_moments": (None, [i32, vp, vp, vp, vp, vp]),
+            "or_select_pairs": (C.c_int, [P(Gas), i32, vp, vp, vp, vp, vp, u64, i64,
+                                          vp, vp, vp, vp, vp, vp, vp, vp]),
+            "or_collide_vhs": (None, [P(Gas), i64, vp, vp, vp, vp, u64, vp, vp, vp]),
+            "or_moment_match": (None, [i32, vp, vp, vp, vp, vp]),
+            "or_tt_damp": (d, [i32, d]),
+            "or_pot_V": (d, [P(Pot), d]),
+            "or_pot_dV": (d, [P(Pot), d]),
+            "or_rmin": (d, [P(Pot), d, d]),
+            "or_chi": (d, [P(Pot), d, d]),
+            "or_chi_batch": (None, [P(Gas), P(Pot), i64, vp, vp, vp]),
+            "or_deflect": (None, [vp, d, d, vp]),
+            "or_collide_jager": (None, [P(Gas), P(Pot), i64, vp, vp, vp, vp, u64, vp, vp, vp, vp]),
+            "or_bf16_round": (d, [d]),
+            "or_mlp_forward": (None, [P(Mlp), vp, vp, i64, vp, C.c_int, vp]),
+            "or_noise4": (None, [u64, i32, i32, u64, vp]),
+            "or_neural_features": (None, [P(Mlp), vp, d, vp, vp]),
+            "or_collide_neural": (None, [P(Gas), P(Mlp), vp, vp, vp, i64, vp, vp, vp, vp, u64,
+                                         C.c_int, vp, vp, vp]),
+            "or_harvest_jager": (None, [P(Gas), P(Pot), i64, vp, vp, vp, vp, vp, vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"], "oracle arrays must be C-contiguous"
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+# ----------------------------------------------------------------- struct helpers
+
+def make_gas(mass, d_ref, omega, T_ref, fn_over_vc, dt, seed, model=0, b_max=0.0) -> Gas:
+    return Gas(mass, d_ref, omega, T_ref, fn_over_vc, dt, seed, model, 0, b_max)
+
+
+def make_pot(p: dict) -> Pot:
+    P = Pot()
+    P.kind = int(p.get("kind", 0))
+    for k in ("A", "a1", "a2", "am1", "am2", "beta", "R_eps", "At", "at", "d_hs", "kappa", "p"):
+        setattr(P, k, float(p.get(k, 0.0)))
+    Cs = p.get("C", [0.0] * 6)
+    for q in range(6):
+        P.C[q] = float(Cs[q])
+    return P
+
+
+def make_mlp(d_in, width, n_hidden, d_out, act, sigma_v, T_ref, eps) -> Mlp:
+    return Mlp(d_in, width, n_hidden, d_out, act, 0, sigma_v, T_ref, eps)
+
+
+# ----------------------------------------------------------------- Philox (R1)
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().or_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def philox_stream(seed, cell, step, tag, sub, n) -> np.ndarray:
+    out = np.zeros((n, 4), np.uint32)
+    lib().or_philox_stream(seed, cell, step, tag, sub, n, _p(out))
+    return out
+
+
+def u53(a, b) -> float:
+    return lib().or_u53(int(a), int(b))
+
+
+# ----------------------------------------------------------------- step pieces
+
+def sigma(gas: Gas, g: float) -> float:
+    return lib().or_sigma(C.byref(gas), g)
+
+
+def sigma_g_max_init(gas: Gas, T: np.ndarray, factor: float = 5.0) -> np.ndarray:
+    T = _f64(T)
+    out = np.zeros_like(T)
+    lib().or_sigma_g_max_init(C.byref(gas), len(T), _p(T), factor, _p(out))
+    return out
+
+
+def sort_cells(cell_id, vx, vy, vz, n_cells):
+    """Stable counting sort by cell (Sec. 2.6 (1))."""
+    cid = _i32(cell_id)
+    vx, vy, vz = _f64(vx), _f64(vy), _f64(vz)
+    n = len(cid)
+    perm = np.zeros(n, np.int32)
+    cs = np.zeros(n_cells + 1, np.int32)
+    s = [np.zeros(n) for _ in range(3)]
+    rc = lib().or_sort_cells(n, n_cells, _p(cid), _p(vx), _p(vy), _p(vz), _p(perm), _p(cs),
+                             _p(s[0]), _p(s[1]), _p(s[2]))
+    if rc != 0:
+        raise ValueError("cell id out of range")
+    return perm, cs, s[0], s[1], s[2]
+
+
+def cell_moments(cell_start, vx, vy, vz) -> np.ndarray:
+    cs = _i32(cell_start)
+    nc = len(cs) - 1
+    mom = np.zeros((nc, 5))
+    lib().or_cell_moments(nc, _p(cs), _p(_f64(vx)), _p(_f64(vy)), _p(_f64(vz)), _p(mom))
+    return mom
+
+
+def select_pairs(gas: Gas, cell_start, vx, vy, vz, sgmax, step, capacity=None):
+    """NTC selection, readings R2-R4.  Returns a dict of cell-major pair
+    arrays (candidate order) and the updated (sigma g)_max."""
+    cs = _i32(cell_start)
+    nc = len(cs) - 1
+    sg = _f64(sgmax).copy()
+    if capacity is None:
+        capacity = 1 << 20
+    arrs = [np.zeros(capacity, np.int32) for _ in range(5)]
+    n_pairs = C.c_int64(0)
+    n_cand = C.c_int64(0)
+    n_rounds = C.c_int32(0)
+    rc = lib().or_select_pairs(C.byref(gas), nc, _p(cs), _p(_f64(vx)), _p(_f64(vy)), _p(_f64(vz)),
+                               _p(sg), step, capacity, *[_p(a) for a in arrs],
+                               C.byref(n_pairs), C.byref(n_cand), C.byref(n_rounds))
+    if rc != 0:
+        raise RuntimeError(f"oracle select: capacity {capacity} < {n_pairs.value}")
+    n = n_pairs.value
+    i, j, cell, m, rnd = (a[:n].copy() for a in arrs)
+    return dict(i=i, j=j, cell=cell, m=m, round=rnd, n_pairs=n, n_cand=n_cand.value,
+                n_rounds=n_rounds.value, sgmax=sg)
+
+
+def collide_vhs(gas: Gas, pairs: dict, step, vx, vy, vz):
+    vx, vy, vz = _f64(vx).copy(), _f64(vy).copy(), _f64(vz).copy()
+    lib().or_collide_vhs(C.byref(gas), pairs["n_pairs"], _p(pairs["i"]), _p(pairs["j"]),
+                         _p(pairs["cell"]), _p(pairs["m"]), step, _p(vx), _p(vy), _p(vz))
+    return vx, vy, vz
+
+
+def moment_match(cell_start, mom_pre, vx, vy, vz):
+    cs = _i32(cell_start)
+    vx, vy, vz = _f64(vx).copy(), _f64(vy).copy(), _f64(vz).copy()
+    lib().or_moment_match(len(cs) - 1, _p(cs), _p(_f64(mom_pre)), _p(vx), _p(vy), _p(vz))
+    return vx, vy, vz
+
+
+# ----------------------------------------------------------------- potentials / chi
+
+def tt_damp(n: int, x: float) -> float:
+    return lib().or_tt_damp(n, x)
+
+
+def pot_V(pot: Pot, r: float) -> float:
+    return lib().or_pot_V(C.byref(pot), r)
+
+
+def pot_dV(pot: Pot, r: float) -> float:
+    return lib().or_pot_dV(C.byref(pot), r)
+
+
+def rmin(pot: Pot, b: float, E: float) -> float:
+    return lib().or_rmin(C.byref(pot), b, E)
+
+
+def chi(pot: Pot, b: float, E: float) -> float:
+    """Signed deflection angle, b in Angstrom, E = E_r/k_B in Kelvin."""
+    return lib().or_chi(C.byref(pot), b, E)
+
+
+def chi_batch(gas: Gas, pot: Pot, b, g) -> np.ndarray:
+    b, g = _f64(b), _f64(g)
+    out = np.zeros_like(b)
+    lib().or_chi_batch(C.byref(gas), C.byref(pot), len(b), _p(b), _p(g), _p(out))
+    return out
+
+
+def e_kelvin(mass: float, g):
+    return 0.25 * mass * np.asarray(g, dtype=np.float64) ** 2 / KB
+
+
+def deflect(vr, chi_v, eps):
+    vr = _f64(vr)
+    out = np.zeros(3)
+    lib().or_deflect(_p(vr), chi_v, eps, _p(out))
+    return out
+
+
+def collide_jager(gas: Gas, pot: Pot, pairs: dict, step, vx, vy, vz, want_chi=False):
+    vx, vy, vz = _f64(vx).copy(), _f64(vy).copy(), _f64(vz).copy()
+    chi_out = np.zeros(max(pairs["n_pairs"], 1))
+    lib().or_collide_jager(C.byref(gas), C.byref(pot), pairs["n_pairs"], _p(pairs["i"]),
+                           _p(pairs["j"]), _p(pairs["cell"]), _p(pairs["m"]), step,
+                           _p(vx), _p(vy), _p(vz), _p(chi_out))
+    if want_chi:
+        return vx, vy, vz, chi_out[:pairs["n_pairs"]]
+    return vx, vy, vz
+
+
+def harvest_jager(gas: Gas, pot: Pot, vi, vj, b, eps):
+    vi, vj, b, eps = _f64(vi), _f64(vj), _f64(b), _f64(eps)
+    n = len(b)
+    vio, vjo = np.zeros((n, 3)), np.zeros((n, 3))
+    lib().or_harvest_jager(C.byref(gas), C.byref(pot), n, _p(vi), _p(vj), _p(b), _p(eps),
+                           _p(vio), _p(vjo))
+    return vio, vjo
+
+
+# ----------------------------------------------------------------- neural path
+
+def bf16_round(x: float) -> float:
+    return lib().or_bf16_round(x)
+
+
+def mlp_forward(mlp: Mlp, W: np.ndarray, bias: np.ndarray, x: np.ndarray, bf16=False):
+    x = _f64(x)
+    n = x.shape[0]
+    y = np.zeros((n, mlp.d_out))
+    lib().or_mlp_forward(C.byref(mlp), _p(_f64(W)), _p(_f64(bias)), n, _p(x), int(bf16), _p(y))
+    return y
+
+
+def noise4(seed, cell, m, step) -> np.ndarray:
+    z = np.zeros(4)
+    lib().or_noise4(seed, cell, m, step, _p(z))
+    return z
+
+
+def collide_neural(gas: Gas, mlp: Mlp, W, bias, mom_pre, pairs: dict, step, vx, vy, vz,
+                   bf16=False):
+    vx, vy, vz = _f64(vx).copy(), _f64(vy).copy(), _f64(vz).copy()
+    lib().or_collide_neural(C.byref(gas), C.byref(mlp), _p(_f64(W)), _p(_f64(bias)),
+                            _p(_f64(mom_pre)), pairs["n_pairs"], _p(pairs["i"]), _p(pairs["j"]),
+                            _p(pairs["cell"]), _p(pairs["m"]), step, int(bf16),
+                            _p(vx), _p(vy), _p(vz))
+    return vx, vy, vz
+
+
+# ----------------------------------------------------------------- whole step
+
+def step(gas: Gas, cell_id, vx, vy, vz, n_cells, sgmax, step_idx, path="vhs",
+         pot: Pot | None = None, mlp: Mlp | None = None, W=None, bias=None, bf16=False,
+         capacity=None):
+    """One collision step: sort, pre moments, NTC selection, collisions of
+    one path in candidate order, centred moment matching (Sec. 2.1-2.6)."""
+    perm, cs, sx, sy, sz = sort_cells(cell_id, vx, vy, vz, n_cells)
+    mom = cell_moments(cs, sx, sy, sz)
+    pairs = select_pairs(gas, cs, sx, sy, sz, sgmax, step_idx, capacity)
+    if path == "vhs":
+        cx, cy, cz = collide_vhs(gas, pairs, step_idx, sx, sy, sz)
+    elif path == "jager":
+        cx, cy, cz = collide_jager(gas, pot, pairs, step_idx, sx, sy, sz)
+    elif path == "neural":
+        cx, cy, cz = collide_neural(gas, mlp, W, bias, mom, pairs, step_idx, sx, sy, sz, bf16)
+    else:
+        raise ValueError(path)
+    ox, oy, oz = moment_match(cs, mom, cx, cy, cz)
+    return dict(perm=perm, cell_start=cs, mom=mom, pairs=pairs, vx=ox, vy=oy, vz=oz,
+                sgmax=pairs["sgmax"])

@@ -1,0 +1,686 @@
+/*
+ * dsmc_oracle.c -- plain, slow FP64 CPU oracle of the DSMC collision step of
+ * "Physics Constrained Neural Collision Operators for VHS Surrogates and Ab
+ * Initio Angle Prediction in DSMC" (arXiv 2602.21244).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this library.  The
+ * product (the CUDA library under paper_2602_21244_gb300/) never calls it and
+ * shares no code, header, table or constant generator with it.
+ *
+ * Everything is double precision, sequential in the order the method states,
+ * with no blocking or fusion.  Compile with -ffp-contract=off so that no
+ * a*b+c is fused into an FMA: the integer decisions of pair selection must be
+ * the same on every host.
+ *
+ * Citations are to the paper's sections and equations:
+ *   Sec. 2.1   DSMC collision step, NTC rate nu ~ n sigma v_r
+ *   Sec. 2.2   cell partition, NTC candidate count ~ N_k(N_k-1)(sigma v_r)_max,
+ *              uniform pair draw, acceptance ~ sigma v_r; Eq. (mlp_input),
+ *              Eq. (mlp_output)
+ *   Sec. 2.3   Eq. (energy_shell_projection) and the centre-of-mass update
+ *   Sec. 2.5   Eq. (cell_energy_clamp), cell-wise energy correction
+ *   Sec. 2.6   sort by cell index, batch per cell, parallel over cells
+ *   Sec. 3.4.1 Eq. (jager_potential), Eq. (damping), screened Coulomb core
+ *   Sec. 3.4.2 classical scattering integral chi(b, E_r)
+ *   Sec. 3.4.4 r_min = largest root, Brent-Dekker to 1e-14, u = r_min/r
+ *
+ * Readings where the paper is silent (all listed in the design notes):
+ *   R1  Philox4x32-10 (Salmon et al., SC'11) keyed by seed, counter
+ *       (idx, cell, step_lo, tag | sub<<8 | step_hi<<16).
+ *   R2  Bird's NTC constant: M~ = 1/2 N(N-1) (F_N/V_c) (sigma g)_max dt,
+ *       stochastic rounding M = floor(M~ + U).
+ *   R3  acceptance uses the pre-step (snapshot) velocities; (sigma g)_max is
+ *       raised after the step to the largest sigma g seen among candidates.
+ *   R4  accepted pairs act in candidate order on the current velocities
+ *       (classical sequential DSMC).  Their "round" is 1+max(last[i],last[j]).
+ *   R5  cell moment matching is centred: v <- u_pre + alpha (v - u_post),
+ *       alpha = sqrt(Theta_pre/Theta_post); it equals Eq. (cell_energy_clamp)
+ *       when the cell mean velocity is zero.
+ *   R6  energy-shell projection divides by ||y|| (not ||y||+eps) so the pair
+ *       energy is exact; ||y|| <= eps falls back to an isotropic direction.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_KB 1.380649e-23 /* Boltzmann constant, J/K (exact SI value) */
+#define OR_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, Sec. 3.3)         */
+/* ------------------------------------------------------------------ */
+enum { OR_TAG_NTC = 1, OR_TAG_CAND = 2, OR_TAG_ISO = 3, OR_TAG_JAGER = 4,
+       OR_TAG_NOISE = 5, OR_TAG_HARVEST = 6 };
+
+void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
+                      uint32_t out[4]) {
+  uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c[1] ^ k0;
+    uint32_t n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+  }
+  out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
+}
+
+static void draw(uint64_t seed, uint32_t idx, uint32_t cell, uint64_t step,
+                 uint32_t tag, uint32_t sub, uint32_t out[4]) {
+  uint32_t ctr[4] = {idx, cell, (uint32_t)step,
+                     tag | (sub << 8) | ((uint32_t)(step >> 32) << 16)};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  or_philox4x32_10(ctr, key, out);
+}
+
+/* uniform double in [0,1) from 53 bits of two words */
+double or_u53(uint32_t a, uint32_t b) {
+  uint64_t x = (((uint64_t)a << 32) | b) >> 11;
+  return (double)x * (1.0 / 9007199254740992.0);
+}
+
+/* integer in [0,n) by the high word of w*n (Lemire, no rejection) */
+static uint32_t mulhi_n(uint32_t w, uint32_t n) {
+  return (uint32_t)(((uint64_t)w * n) >> 32);
+}
+
+void or_philox_stream(uint64_t seed, uint32_t cell, uint64_t step,
+                      uint32_t tag, uint32_t sub, int64_t n, uint32_t* out) {
+  for (int64_t i = 0; i < n; ++i) draw(seed, (uint32_t)i, cell, step, tag, sub, out + 4 * i);
+}
+
+/* ------------------------------------------------------------------ */
+/* Gas description (the oracle's own copy; the CUDA library has its   */
+/* own).  Field order is the ABI order used by oracle/__init__.py.    */
+/* ------------------------------------------------------------------ */
+typedef struct {
+  double mass;        /* kg */
+  double d_ref;       /* m, VHS reference diameter */
+  double omega;       /* VHS viscosity index (0.5 = hard sphere) */
+  double T_ref;       /* K */
+  double fn_over_vc;  /* F_N / V_c, 1/m^3 (= n / mean particles per cell) */
+  double dt;          /* s */
+  uint64_t seed;
+  int32_t model;      /* 0: VHS cross section; 1: constant pi b_max^2 */
+  int32_t pad_;
+  double b_max;       /* m, impact-parameter cut-off for model 1 */
+} or_gas_t;
+
+/* Bird's VHS total cross section (Bird 1994, Eq. 4.63 form):
+ *   sigma(g) = pi d_ref^2 (2 k T_ref / (m_r g^2))^(omega-1/2) / Gamma(5/2-omega),
+ * m_r = m/2.  omega = 1/2 gives the hard-sphere pi d^2. */
+double or_sigma(const or_gas_t* gs, double g) {
+  if (gs->model == 1) return OR_PI * gs->b_max * gs->b_max;
+  double mr = 0.5 * gs->mass;
+  double x = 2.0 * OR_KB * gs->T_ref / (mr * g * g);
+  return OR_PI * gs->d_ref * gs->d_ref * pow(x, gs->omega - 0.5) / tgamma(2.5 - gs->omega);
+}
+
+/* initial (sigma g)_max of a cell at temperature T: sigma(g0) g0 with
+ * g0 = factor * sqrt(2 k T / m) */
+void or_sigma_g_max_init(const or_gas_t* gs, int32_t n_cells, const double* T,
+                         double factor, double* sgmax) {
+  for (int32_t k = 0; k < n_cells; ++k) {
+    double g0 = factor * sqrt(2.0 * OR_KB * T[k] / gs->mass);
+    sgmax[k] = or_sigma(gs, g0) * g0;
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 2.6 (1): stable counting sort by cell index                    */
+/* ------------------------------------------------------------------ */
+int or_sort_cells(int32_t n, int32_t n_cells, const int32_t* cell_id,
+                  const double* vx, const double* vy, const double* vz,
+                  int32_t* perm, int32_t* cell_start,
+                  double* svx, double* svy, double* svz) {
+  for (int32_t k = 0; k <= n_cells; ++k) cell_start[k] = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    if (cell_id[i] < 0 || cell_id[i] >= n_cells) return -1;
+    cell_start[cell_id[i] + 1] += 1;
+  }
+  for (int32_t k = 0; k < n_cells; ++k) cell_start[k + 1] += cell_start[k];
+  int32_t* cursor = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_cells > 0 ? n_cells : 1));
+  for (int32_t k = 0; k < n_cells; ++k) cursor[k] = cell_start[k];
+  for (int32_t i = 0; i < n; ++i) perm[cursor[cell_id[i]]++] = i;
+  free(cursor);
+  for (int32_t s = 0; s < n; ++s) {
+    svx[s] = vx[perm[s]]; svy[s] = vy[perm[s]]; svz[s] = vz[perm[s]];
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Cell moments, two passes: N, sum v, Theta = sum |v - u|^2, u = sum v/N */
+/* ------------------------------------------------------------------ */
+void or_cell_moments(int32_t n_cells, const int32_t* cs, const double* vx,
+                     const double* vy, const double* vz, double* mom) {
+  for (int32_t k = 0; k < n_cells; ++k) {
+    int32_t a = cs[k], b = cs[k + 1];
+    double sx = 0, sy = 0, sz = 0;
+    for (int32_t s = a; s < b; ++s) { sx += vx[s]; sy += vy[s]; sz += vz[s]; }
+    double n = (double)(b - a), th = 0;
+    if (b > a) {
+      double ux = sx / n, uy = sy / n, uz = sz / n;
+      for (int32_t s = a; s < b; ++s) {
+        double dx = vx[s] - ux, dy = vy[s] - uy, dz = vz[s] - uz;
+        th += dx * dx + dy * dy + dz * dz;
+      }
+    }
+    mom[5 * k + 0] = n; mom[5 * k + 1] = sx; mom[5 * k + 2] = sy;
+    mom[5 * k + 3] = sz; mom[5 * k + 4] = th;
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 2.2: NTC selection, readings R2-R4                             */
+/* Output pairs are cell-major in candidate order.                    */
+/* ------------------------------------------------------------------ */
+int or_select_pairs(const or_gas_t* gs, int32_t n_cells, const int32_t* cs,
+                    const double* vx, const double* vy, const double* vz,
+                    double* sgmax, uint64_t step, int64_t capacity,
+                    int32_t* pi, int32_t* pj, int32_t* pcell, int32_t* pm,
+                    int32_t* pround, int64_t* n_pairs, int64_t* n_cand,
+                    int32_t* n_rounds) {
+  int64_t np = 0, nc = 0;
+  int32_t rmax = 0;
+  int32_t* last = NULL;
+  int32_t last_cap = 0;
+  for (int32_t k = 0; k < n_cells; ++k) {
+    int32_t a = cs[k], N = cs[k + 1] - cs[k];
+    if (N < 2) continue;
+    uint32_t w[4];
+    draw(gs->seed, 0, (uint32_t)k, step, OR_TAG_NTC, 0, w);
+    double mt = 0.5 * (double)N * (double)(N - 1);
+    mt = mt * gs->fn_over_vc;
+    mt = mt * sgmax[k];
+    mt = mt * gs->dt;
+    double mf = floor(mt + or_u53(w[0], w[1]));
+    if (!(mf < 2147483647.0)) return -3; /* DSMC_ERR_CAPACITY */
+    int32_t M = (int32_t)mf;
+    nc += M;
+    if (N > last_cap) { free(last); last_cap = N; last = (int32_t*)malloc(sizeof(int32_t) * (size_t)N); }
+    for (int32_t q = 0; q < N; ++q) last[q] = -1;
+    double best = sgmax[k];
+    for (int32_t m = 0; m < M; ++m) {
+      draw(gs->seed, (uint32_t)m, (uint32_t)k, step, OR_TAG_CAND, 0, w);
+      uint32_t i = mulhi_n(w[0], (uint32_t)N);
+      uint32_t j = mulhi_n(w[1], (uint32_t)(N - 1));
+      if (j >= i) j += 1;
+      double dx = vx[a + i] - vx[a + j], dy = vy[a + i] - vy[a + j], dz = vz[a + i] - vz[a + j];
+      double g = sqrt((dx * dx + dy * dy) + dz * dz);
+      double sg = or_sigma(gs, g) * g;
+      if (sg > best) best = sg;
+      double U = or_u53(w[2], w[3]);
+      if (U < sg / sgmax[k]) {
+        int32_t r = 1 + (last[i] > last[j] ? last[i] : last[j]);
+        last[i] = r; last[j] = r;
+        if (r + 1 > rmax) rmax = r + 1;
+        if (np < capacity) {
+          pi[np] = a + (int32_t)i; pj[np] = a + (int32_t)j;
+          pcell[np] = k; pm[np] = m; pround[np] = r;
+        }
+        np++;
+      }
+    }
+    sgmax[k] = best;
+  }
+  free(last);
+  *n_pairs = np; *n_cand = nc; *n_rounds = rmax;
+  return np > capacity ? -3 : 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 2.3: centre-of-mass pair update with a given v_r'              */
+/* ------------------------------------------------------------------ */
+static void pair_update(double* vx, double* vy, double* vz, int32_t i, int32_t j,
+                        const double vrp[3]) {
+  double cx = 0.5 * (vx[i] + vx[j]), cy = 0.5 * (vy[i] + vy[j]), cz = 0.5 * (vz[i] + vz[j]);
+  vx[i] = cx + 0.5 * vrp[0]; vy[i] = cy + 0.5 * vrp[1]; vz[i] = cz + 0.5 * vrp[2];
+  vx[j] = cx - 0.5 * vrp[0]; vy[j] = cy - 0.5 * vrp[1]; vz[j] = cz - 0.5 * vrp[2];
+}
+
+/* isotropic unit vector from tag 3: cos chi = 2U1-1, eps = 2 pi U2 */
+static void iso_dir(uint64_t seed, int32_t cell, int32_t m, uint64_t step, double e[3]) {
+  uint32_t w[4];
+  draw(seed, (uint32_t)m, (uint32_t)cell, step, OR_TAG_ISO, 0, w);
+  double c = 2.0 * or_u53(w[0], w[1]) - 1.0;
+  double s = sqrt(1.0 - c * c);
+  double ep = 2.0 * OR_PI * or_u53(w[2], w[3]);
+  e[0] = c; e[1] = s * cos(ep); e[2] = s * sin(ep);
+}
+
+/* VHS isotropic scatter (the phenomenological kernel of Sec. 2.1),
+ * pairs applied one after another in the given (cell-major, candidate)
+ * order, reading the current velocities. */
+void or_collide_vhs(const or_gas_t* gs, int64_t n_pairs, const int32_t* pi,
+                    const int32_t* pj, const int32_t* pcell, const int32_t* pm,
+                    uint64_t step, double* vx, double* vy, double* vz) {
+  for (int64_t p = 0; p < n_pairs; ++p) {
+    int32_t i = pi[p], j = pj[p];
+    double dx = vx[i] - vx[j], dy = vy[i] - vy[j], dz = vz[i] - vz[j];
+    double g = sqrt((dx * dx + dy * dy) + dz * dz);
+    double e[3];
+    iso_dir(gs->seed, pcell[p], pm[p], step, e);
+    double vrp[3] = {g * e[0], g * e[1], g * e[2]};
+    pair_update(vx, vy, vz, i, j, vrp);
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 2.5 + reading R5: centred cell moment matching                 */
+/* ------------------------------------------------------------------ */
+void or_moment_match(int32_t n_cells, const int32_t* cs, const double* mom_pre,
+                     double* vx, double* vy, double* vz) {
+  for (int32_t k = 0; k < n_cells; ++k) {
+    int32_t a = cs[k], b = cs[k + 1];
+    if (b <= a) continue;
+    double n = (double)(b - a);
+    double sx = 0, sy = 0, sz = 0;
+    for (int32_t s = a; s < b; ++s) { sx += vx[s]; sy += vy[s]; sz += vz[s]; }
+    double ux = sx / n, uy = sy / n, uz = sz / n, th = 0;
+    for (int32_t s = a; s < b; ++s) {
+      double dx = vx[s] - ux, dy = vy[s] - uy, dz = vz[s] - uz;
+      th += dx * dx + dy * dy + dz * dz;
+    }
+    double px = mom_pre[5 * k + 1] / n, py = mom_pre[5 * k + 2] / n, pz = mom_pre[5 * k + 3] / n;
+    double alpha = 1.0;
+    if (b - a >= 2 && th > 0.0) alpha = sqrt(mom_pre[5 * k + 4] / th);
+    for (int32_t s = a; s < b; ++s) {
+      vx[s] = px + alpha * (vx[s] - ux);
+      vy[s] = py + alpha * (vy[s] - uy);
+      vz[s] = pz + alpha * (vz[s] - uz);
+    }
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 3.4.1: interaction potentials, r in Angstrom, V in Kelvin      */
+/* ------------------------------------------------------------------ */
+typedef struct {
+  int32_t kind;       /* 0 Jager form, 1 hard sphere, 2 inverse power k/r^p */
+  int32_t pad_;
+  double A, a1, a2, am1, am2; /* repulsive A exp(a1 r + a2 r^2 + am1/r + am2/r^2) */
+  double beta;        /* Tang-Toennies damping constant ("b" in Eq. damping) */
+  double C[6];        /* C6, C8, C10, C12, C14, C16 */
+  double R_eps;       /* position of the well minimum; core below 0.4 R_eps */
+  double At, at;      /* screened Coulomb core At exp(-at r)/r */
+  double d_hs;        /* hard-sphere diameter (kind 1) */
+  double kappa, p;    /* inverse power (kind 2) */
+} or_pot_t;
+
+/* Tang-Toennies damping f_n(x) = 1 - exp(-x) sum_{k=0}^{n} x^k/k!  (Eq. damping) */
+double or_tt_damp(int32_t n, double x) {
+  if (x > 700.0) return 1.0; /* exp(-x) x^k/k! < 1e-270 */
+  double term = 1.0, sum = 1.0;
+  for (int32_t k = 1; k <= n; ++k) { term *= x / (double)k; sum += term; }
+  return 1.0 - exp(-x) * sum;
+}
+
+/* its derivative, f_n'(x) = exp(-x) x^n / n! */
+static double tt_damp_d(int32_t n, double x) {
+  if (x > 700.0) return 0.0;
+  double term = 1.0;
+  for (int32_t k = 1; k <= n; ++k) term *= x / (double)k;
+  return exp(-x) * term;
+}
+
+double or_pot_V(const or_pot_t* P, double r) {
+  if (P->kind == 1) return r < P->d_hs ? INFINITY : 0.0;
+  if (P->kind == 2) return P->kappa / pow(r, P->p);
+  if (r < 0.4 * P->R_eps) return P->At * exp(-P->at * r) / r;
+  double rep = P->A * exp(P->a1 * r + P->a2 * r * r + P->am1 / r + P->am2 / (r * r));
+  double disp = 0.0;
+  for (int32_t n = 3; n <= 8; ++n)
+    disp += or_tt_damp(2 * n, P->beta * r) * P->C[n - 3] / pow(r, 2.0 * n);
+  return rep - disp;
+}
+
+double or_pot_dV(const or_pot_t* P, double r) {
+  if (P->kind == 1) return 0.0;
+  if (P->kind == 2) return -P->p * P->kappa / pow(r, P->p + 1.0);
+  if (r < 0.4 * P->R_eps) return -P->At * exp(-P->at * r) * (P->at * r + 1.0) / (r * r);
+  double e = P->A * exp(P->a1 * r + P->a2 * r * r + P->am1 / r + P->am2 / (r * r));
+  double de = e * (P->a1 + 2.0 * P->a2 * r - P->am1 / (r * r) - 2.0 * P->am2 / (r * r * r));
+  double dd = 0.0;
+  for (int32_t n = 3; n <= 8; ++n) {
+    double rn = pow(r, 2.0 * n);
+    dd += P->C[n - 3] * (P->beta * tt_damp_d(2 * n, P->beta * r) / rn
+                         - 2.0 * n * or_tt_damp(2 * n, P->beta * r) / (rn * r));
+  }
+  return de - dd;
+}
+
+/* Gauss-Legendre nodes on [0,1] by Newton on P_n (three-term recurrence) */
+static void gauss_legendre01(int n, double* x, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double z = cos(OR_PI * (i + 0.75) / (n + 0.5)), pp = 0;
+    for (int it = 0; it < 100; ++it) {
+      double p1 = 1.0, p2 = 0.0;
+      for (int k = 1; k <= n; ++k) {
+        double p3 = p2; p2 = p1;
+        p1 = ((2.0 * k - 1.0) * z * p2 - (k - 1.0) * p3) / k;
+      }
+      pp = n * (z * p1 - p2) / (z * z - 1.0);
+      double dz = p1 / pp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    x[i] = 0.5 * (1.0 - z);
+    w[i] = 1.0 / ((1.0 - z * z) * pp * pp);
+  }
+}
+
+/* V(r) - V(r0) for r >= r0 > 0 without cancellation: when r - r0 is small
+ * relative to r0 the difference is the integral of V' over [r0, r], taken by
+ * 12-point Gauss-Legendre; otherwise the plain difference. */
+static double pot_dV_between(const or_pot_t* P, double r0, double dr) {
+  if (P->kind == 1) return 0.0;
+  double rc = 0.4 * P->R_eps;
+  if (P->kind == 0 && r0 < rc && r0 + dr > rc) /* split at the core boundary */
+    return pot_dV_between(P, r0, rc - r0) + pot_dV_between(P, rc, r0 + dr - rc);
+  if (dr > 0.05 * r0) return or_pot_V(P, r0 + dr) - or_pot_V(P, r0);
+  static double gx[12], gw[12];
+  static int ready = 0;
+  if (!ready) { gauss_legendre01(12, gx, gw); ready = 1; }
+  double s = 0.0;
+  for (int q = 0; q < 12; ++q) s += gw[q] * or_pot_dV(P, r0 + gx[q] * dr);
+  return s * dr;
+}
+
+/* F(r) = 1 - b^2/r^2 - V(r)/E */
+static double F_of(const or_pot_t* P, double b, double E, double r) {
+  return 1.0 - (b * b) / (r * r) - or_pot_V(P, r) / E;
+}
+
+/* Brent-Dekker root finder (R. P. Brent, Algorithms for Minimization
+ * Without Derivatives, 1973, ch. 4): bisection safeguarded inverse
+ * quadratic / secant steps on a sign-changing bracket [a, c]. */
+static double brent(const or_pot_t* P, double bb, double E, double a, double c, double rtol) {
+  double fa = F_of(P, bb, E, a), fc = F_of(P, bb, E, c);
+  double b = c, fb = fc;
+  c = a; fc = fa;
+  double d = b - a, e = d;
+  for (int it = 0; it < 300; ++it) {
+    if ((fb > 0 && fc > 0) || (fb < 0 && fc < 0)) { c = a; fc = fa; d = b - a; e = d; }
+    if (fabs(fc) < fabs(fb)) { a = b; b = c; c = a; fa = fb; fb = fc; fc = fa; }
+    double tol = 2.0 * 2.220446049250313e-16 * fabs(b) + 0.5 * rtol * fabs(b);
+    double m = 0.5 * (c - b);
+    if (fabs(m) <= tol || fb == 0.0) return b;
+    if (fabs(e) >= tol && fabs(fa) > fabs(fb)) {
+      double s = fb / fa, p, q;
+      if (a == c) { p = 2.0 * m * s; q = 1.0 - s; }
+      else {
+        double qq = fa / fc, r = fb / fc;
+        p = s * (2.0 * m * qq * (qq - r) - (b - a) * (r - 1.0));
+        q = (qq - 1.0) * (r - 1.0) * (s - 1.0);
+      }
+      if (p > 0) q = -q; else p = -p;
+      if (2.0 * p < 3.0 * m * q - fabs(tol * q) && p < fabs(0.5 * e * q)) { e = d; d = p / q; }
+      else { d = m; e = m; }
+    } else { d = m; e = m; }
+    a = b; fa = fb;
+    b += fabs(d) > tol ? d : (m > 0 ? tol : -tol);
+    fb = F_of(P, bb, E, b);
+  }
+  return b;
+}
+
+/* Sec. 3.4.4: r_min = the largest root of F.  Scan inward on a geometric
+ * grid of 4096 points from r_hi down to 0.05 A for the first F < 0, then
+ * Brent to 1e-14 relative. */
+double or_rmin(const or_pot_t* P, double b, double E) {
+  if (P->kind == 1) return b > P->d_hs ? b : P->d_hs;
+  double r_hi = 2.0 * fmax(b, P->kind == 0 ? 3.0 * P->R_eps : 1.0);
+  for (int t = 0; t < 60 && F_of(P, b, E, r_hi) <= 0.0; ++t) r_hi *= 2.0;
+  const double r_lo = 0.05;
+  const int ngrid = 4096;
+  double q = pow(r_lo / r_hi, 1.0 / (ngrid - 1));
+  double r_prev = r_hi;
+  for (int t = 1; t < ngrid; ++t) {
+    double r = r_hi * pow(q, (double)t);
+    if (F_of(P, b, E, r) < 0.0) return brent(P, b, E, r, r_prev, 1e-14);
+    r_prev = r;
+  }
+  return NAN;
+}
+
+/* G(u) = F(r_min/u) written about r_min so that nothing cancels:
+ *   G(u) = F0 + (b/r_min)^2 (1-u)(1+u) - (V(r_min/u) - V(r_min))/E,
+ * given w = 1-u exactly.  F0 = F(r_min) is 0 at a root of a continuous
+ * potential and 1 - (b/d)^2 at the hard-sphere wall r_min = d. */
+static double G_of(const or_pot_t* P, double b, double E, double rmin, double F0, double w) {
+  double u = 1.0 - w;
+  double bt = b / rmin;
+  double dr = rmin * w / u;
+  return F0 + bt * bt * w * (1.0 + u) - pot_dV_between(P, rmin, dr) / E;
+}
+
+/* Sec. 3.4.2: chi = pi - 2 (b/r_min) int_0^1 du / sqrt(G(u)) (signed; an
+ * attractive deflection is negative).  The integral has a 1/sqrt(1-u)
+ * endpoint singularity; tanh-sinh quadrature (Takahasi-Mori 1974) in u
+ * handles it, level doubling to 1e-14 relative. */
+double or_chi(const or_pot_t* P, double b, double E) {
+  if (b <= 0.0) return OR_PI;
+  double rmin = or_rmin(P, b, E);
+  if (!(rmin > 0.0)) return NAN;
+  /* u = (1 + tanh(pi/2 sinh t))/2, 1-u = 1/(1+exp(pi sinh t)),
+     du/dt = (pi/4) cosh t / cosh^2(pi/2 sinh t) */
+  double F0 = P->kind == 1 ? 1.0 - (b / rmin) * (b / rmin) : 0.0;
+  double h = 0.5, tmax = 4.5, prev = 0.0, est = 0.0;
+  double sum = 0.0;
+  int level;
+  for (level = 0; level < 12; ++level) {
+    double step = level == 0 ? h : 2.0 * h;
+    double t0 = level == 0 ? 0.0 : h;
+    for (double t = t0; t <= tmax; t += step) {
+      for (int sgn = (t == 0.0 ? 1 : -1); sgn <= 1; sgn += 2) {
+        double tt = sgn * t;
+        double sh = OR_PI * sinh(tt);
+        double w = 1.0 / (1.0 + exp(sh));          /* 1-u */
+        if (w <= 0.0 || w >= 1.0) continue;
+        double ch = cosh(0.5 * sh);
+        double wt = 0.25 * OR_PI * cosh(tt) / (ch * ch);
+        if (wt == 0.0 || !isfinite(wt)) continue;
+        double G = G_of(P, b, E, rmin, F0, w);
+        if (G <= 0.0) continue;
+        sum += wt / sqrt(G);
+      }
+    }
+    est = sum * h;
+    if (level > 2 && fabs(est - prev) <= 1e-14 * fabs(est)) break;
+    prev = est;
+    h *= 0.5;
+  }
+  return OR_PI - 2.0 * (b / rmin) * est;
+}
+
+/* relative energy in Kelvin: E_r / k_B = (1/2) (m/2) g^2 / k_B */
+static double e_kelvin(const or_gas_t* gs, double g) {
+  return 0.25 * gs->mass * g * g / OR_KB;
+}
+
+/* C1 batch: b in Angstrom, g in m/s; chi for each pair */
+void or_chi_batch(const or_gas_t* gs, const or_pot_t* P, int64_t n, const double* b,
+                  const double* g, double* chi) {
+  for (int64_t q = 0; q < n; ++q) chi[q] = or_chi(P, b[q], e_kelvin(gs, g[q]));
+}
+
+/* Deflect v_r by chi with azimuth eps about v_r (Bird 1994, Eq. 2.22):
+ *   v_r' = cos chi v_r + g sin chi (cos eps c + sin eps a),
+ *   c = (0, w, -v)/q,  a = (q^2, -u v, -u w)/(g q),  q = sqrt(v^2+w^2);
+ * a = c x (v_r/g).  For q = 0 the frame is c = (0,1,0), a = c x (v_r/g). */
+void or_deflect(const double vr[3], double chi, double eps, double out[3]) {
+  double u = vr[0], v = vr[1], w = vr[2];
+  double g = sqrt((u * u + v * v) + w * w);
+  double q = sqrt(v * v + w * w);
+  double cx, cy, cz, ax, ay, az;
+  if (q > 1e-300 && q > 1e-12 * g) {
+    cx = 0.0; cy = w / q; cz = -v / q;
+    ax = q / g; ay = -u * v / (g * q); az = -u * w / (g * q);
+  } else {
+    cx = 0.0; cy = 1.0; cz = 0.0;
+    ax = 0.0; ay = 0.0; az = u >= 0 ? -1.0 : 1.0;
+  }
+  double cc = cos(chi), sc = sin(chi), ce = cos(eps), se = sin(eps);
+  out[0] = cc * u + g * sc * (ce * cx + se * ax);
+  out[1] = cc * v + g * sc * (ce * cy + se * ay);
+  out[2] = cc * w + g * sc * (ce * cz + se * az);
+}
+
+/* Jager-potential collision: b = b_max sqrt(U1) (b^2 uniform on
+ * [0, b_max^2]), eps = 2 pi U2 from tag 4; chi from the scattering
+ * integral; pairs in order.  chi_out (optional) receives each chi. */
+void or_collide_jager(const or_gas_t* gs, const or_pot_t* P, int64_t n_pairs,
+                      const int32_t* pi, const int32_t* pj, const int32_t* pcell,
+                      const int32_t* pm, uint64_t step, double* vx, double* vy,
+                      double* vz, double* chi_out) {
+  double bmax_A = gs->b_max * 1e10;
+  for (int64_t p = 0; p < n_pairs; ++p) {
+    int32_t i = pi[p], j = pj[p];
+    double vr[3] = {vx[i] - vx[j], vy[i] - vy[j], vz[i] - vz[j]};
+    double g = sqrt((vr[0] * vr[0] + vr[1] * vr[1]) + vr[2] * vr[2]);
+    uint32_t w[4];
+    draw(gs->seed, (uint32_t)pm[p], (uint32_t)pcell[p], step, OR_TAG_JAGER, 0, w);
+    double b = bmax_A * sqrt(or_u53(w[0], w[1]));
+    double eps = 2.0 * OR_PI * or_u53(w[2], w[3]);
+    double chi = g > 0.0 ? or_chi(P, b, e_kelvin(gs, g)) : 0.0;
+    if (chi_out) chi_out[p] = chi;
+    double vrp[3];
+    if (g > 0.0) or_deflect(vr, chi, eps, vrp); else { vrp[0] = vrp[1] = vrp[2] = 0.0; }
+    pair_update(vx, vy, vz, i, j, vrp);
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 2.2-2.3: conditional MLP + energy-shell projection             */
+/* ------------------------------------------------------------------ */
+typedef struct {
+  int32_t d_in, width, n_hidden, d_out, act; /* act: 0 SiLU, 1 ReLU */
+  int32_t pad_;
+  double sigma_v, T_ref, eps;
+} or_mlp_t;
+
+/* round-to-nearest-even to bfloat16, returned as a double */
+double or_bf16_round(double x) {
+  float f = (float)x;
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return (double)f;
+  uint32_t lsb = (u >> 16) & 1u;
+  u = (u + 0x7fffu + lsb) & 0xffff0000u;
+  memcpy(&f, &u, 4);
+  return (double)f;
+}
+
+static double act_f(int act, double z) {
+  if (act == 1) return z > 0 ? z : 0.0;
+  return z / (1.0 + exp(-z));
+}
+
+/* Plain layer-by-layer forward of one sample.  W holds each layer's
+ * row-major [out x in] matrix, one after another; bias likewise.  With
+ * bf16 != 0 the input and every hidden activation are rounded to bf16,
+ * as a bf16 tensor-core kernel stores them. */
+void or_mlp_forward1(const or_mlp_t* d, const double* W, const double* bias,
+                     const double* x, int bf16, double* y) {
+  double h[1024], z[1024];
+  int n_in = d->d_in;
+  for (int q = 0; q < n_in; ++q) h[q] = bf16 ? or_bf16_round(x[q]) : x[q];
+  const double* Wl = W;
+  const double* bl = bias;
+  for (int l = 0; l <= d->n_hidden; ++l) {
+    int n_out = l == d->n_hidden ? d->d_out : d->width;
+    for (int o = 0; o < n_out; ++o) {
+      double s = 0.0;
+      for (int q = 0; q < n_in; ++q) s += Wl[o * n_in + q] * h[q];
+      z[o] = s + bl[o];
+    }
+    Wl += n_out * n_in; bl += n_out;
+    if (l == d->n_hidden) { for (int o = 0; o < n_out; ++o) y[o] = z[o]; break; }
+    for (int o = 0; o < n_out; ++o) {
+      double a = act_f(d->act, z[o]);
+      h[o] = bf16 ? or_bf16_round(a) : a;
+    }
+    n_in = n_out;
+  }
+}
+
+void or_mlp_forward(const or_mlp_t* d, const double* W, const double* bias, int64_t n,
+                    const double* x, int bf16, double* y) {
+  for (int64_t s = 0; s < n; ++s) or_mlp_forward1(d, W, bias, x + s * d->d_in, bf16, y + s * d->d_out);
+}
+
+/* Box-Muller pair from two uniforms: rho = sqrt(-2 ln(1-U1)), theta = 2 pi U2 */
+static void box_muller(double u1, double u2, double* z0, double* z1) {
+  double rho = sqrt(-2.0 * log(1.0 - u1));
+  double th = 2.0 * OR_PI * u2;
+  *z0 = rho * cos(th); *z1 = rho * sin(th);
+}
+
+/* latent noise xi (Sec. 2.2): four N(0,1) values from tag 5, subs 0 and 1 */
+void or_noise4(uint64_t seed, int32_t cell, int32_t m, uint64_t step, double z[4]) {
+  uint32_t wa[4], wb[4];
+  draw(seed, (uint32_t)m, (uint32_t)cell, step, OR_TAG_NOISE, 0, wa);
+  draw(seed, (uint32_t)m, (uint32_t)cell, step, OR_TAG_NOISE, 1, wb);
+  box_muller(or_u53(wa[0], wa[1]), or_u53(wa[2], wa[3]), &z[0], &z[1]);
+  box_muller(or_u53(wb[0], wb[1]), or_u53(wb[2], wb[3]), &z[2], &z[3]);
+}
+
+/* MLP input of Eq. (mlp_input): [v_r/sigma_v, (T_cell/T_ref), xi] */
+void or_neural_features(const or_mlp_t* d, const double vr[3], double T_cell,
+                        const double z[4], double* x) {
+  x[0] = vr[0] / d->sigma_v; x[1] = vr[1] / d->sigma_v; x[2] = vr[2] / d->sigma_v;
+  if (d->d_in == 8) { x[3] = T_cell / d->T_ref; x[4] = z[0]; x[5] = z[1]; x[6] = z[2]; x[7] = z[3]; }
+  else { x[3] = z[0]; x[4] = z[1]; x[5] = z[2]; }
+}
+
+/* Neural collision: features, MLP, projection (reading R6), CM update,
+ * pairs in order.  T_cell of a cell = m Theta_pre / (3 k_B N). */
+void or_collide_neural(const or_gas_t* gs, const or_mlp_t* d, const double* W,
+                       const double* bias, const double* mom_pre, int64_t n_pairs,
+                       const int32_t* pi, const int32_t* pj, const int32_t* pcell,
+                       const int32_t* pm, uint64_t step, int bf16, double* vx,
+                       double* vy, double* vz) {
+  for (int64_t p = 0; p < n_pairs; ++p) {
+    int32_t i = pi[p], j = pj[p], k = pcell[p];
+    double vr[3] = {vx[i] - vx[j], vy[i] - vy[j], vz[i] - vz[j]};
+    double g = sqrt((vr[0] * vr[0] + vr[1] * vr[1]) + vr[2] * vr[2]);
+    double T = gs->mass * mom_pre[5 * k + 4] / (3.0 * OR_KB * mom_pre[5 * k + 0]);
+    double z[4], x[8], y[3];
+    or_noise4(gs->seed, k, pm[p], step, z);
+    or_neural_features(d, vr, T, z, x);
+    or_mlp_forward1(d, W, bias, x, bf16, y);
+    double ny = sqrt((y[0] * y[0] + y[1] * y[1]) + y[2] * y[2]);
+    double e[3];
+    if (ny > d->eps) { e[0] = y[0] / ny; e[1] = y[1] / ny; e[2] = y[2] / ny; }
+    else iso_dir(gs->seed, k, pm[p], step, e);
+    double vrp[3] = {g * e[0], g * e[1], g * e[2]};
+    pair_update(vx, vy, vz, i, j, vrp);
+  }
+}
+
+/* Jager harvest of training targets (Sec. 3.4.5 "physics harvesting"):
+ * per pair, deflect v_r = v_i - v_j by chi(b, E) with azimuth eps and
+ * apply the CM update.  b in Angstrom. */
+void or_harvest_jager(const or_gas_t* gs, const or_pot_t* P, int64_t n,
+                      const double* vi, const double* vj, const double* b,
+                      const double* eps, double* vi_out, double* vj_out) {
+  for (int64_t p = 0; p < n; ++p) {
+    double vr[3] = {vi[3 * p] - vj[3 * p], vi[3 * p + 1] - vj[3 * p + 1], vi[3 * p + 2] - vj[3 * p + 2]};
+    double g = sqrt((vr[0] * vr[0] + vr[1] * vr[1]) + vr[2] * vr[2]);
+    double chi = or_chi(P, b[p], e_kelvin(gs, g));
+    double vrp[3];
+    or_deflect(vr, chi, eps[p], vrp);
+    for (int c = 0; c < 3; ++c) {
+      double cm = 0.5 * (vi[3 * p + c] + vj[3 * p + c]);
+      vi_out[3 * p + c] = cm + 0.5 * vrp[c];
+      vj_out[3 * p + c] = cm - 0.5 * vrp[c];
+    }
+  }
+}
