@@ -1,0 +1,316 @@
+"""Benchmark of the DSMC collision step on GB300.
+
+One step = sort by cell, pre-step cell moments, NTC selection with the
+round schedule, the pair updates of one path, cell moment matching: every
+row of the method's hot path, over the hypersonic argon gas (500 x 300
+cells around a disc, about 9.2 million particles, Mach-10 shock profile).
+
+Timing: W untimed warm-up steps, then K timed steps.  Before every step
+the pristine unsorted input (cell ids and velocities, 258 MB, larger than
+L2) is copied back, outside the timed region, so each step sorts a
+shuffled gas and starts with a cold L2.  Each step is bracketed by CUDA
+events on the launching stream; per-phase events give the per-kernel times.
+
+Output: one JSON line on rank 0.  The headline ``value`` is accepted pair
+collisions per second of the whole step on the neural path; ``paths``
+holds all three update rules.  Multi-GPU runs are replicas (each rank its
+own gas, no collective on the data path): ``value`` sums over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MLP_FLOP_PER_PAIR = 2 * (8 * 128 + 128 * 128 * 2 + 128 * 3)   # 68,352 (unpadded)
+CANDIDATE_BYTES = 48                                             # two FP64 3-vectors read
+PAIR_BYTES = 104                                                 # 2x24 read + 2x24 write + 8 index
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--scale", type=float, default=1.0, help="shrink the gas (tests)")
+    ap.add_argument("--paths", default="neural,jager,vhs")
+    ap.add_argument("--n-nodes", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- GPU arm
+
+def run_gb300(args, rank, world, dist):
+    import torch
+    from paper_2602_21244_gb300 import dsmc as D
+    from paper_2602_21244_gb300 import workloads as W
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    C = D.Context(dev.index)
+    wl = W.hypersonic(scale=args.scale, seed=rank)
+    n, nc = len(wl["cell_id"]), wl["n_cells"]
+    capacity = max(1 << 16, int(n * 1.5))
+    st = D.StepState(C, n, nc, capacity, device=dev)
+    pristine = [torch.from_numpy(a).to(dev) for a in (wl["cell_id"], wl["vx"], wl["vy"], wl["vz"])]
+    T_cell = torch.from_numpy(wl["T_cell"]).to(dev)
+    wts = W.mlp_weights()
+    w_bits = torch.from_numpy(wts["W_bits"].view(np.int16)).to(dev)
+    bias = torch.from_numpy(wts["bias"].astype(np.float32)).to(dev)
+    mlp = D.make_mlp(8, 128, 3, 3, 0, W.sigma_v(), 273.0, 1e-12)
+    pot = D.make_potential(W.JAGER_SYNTHETIC_AR)
+    stream = torch.cuda.current_stream()
+    sel = st.sel
+
+    def restore():
+        st.cell_id.copy_(pristine[0]); st.vx.copy_(pristine[1]); st.vy.copy_(pristine[2]); st.vz.copy_(pristine[3])
+
+    results = {}
+    neural_kernel = None
+    for path in [p for p in args.paths.split(",") if p]:
+        gas = D.make_gas(dict(wl["gas"], model=0 if path == "vhs" else 1))
+        C.sigma_g_max_init(gas, T_cell, 5.0, out=st.sigma_g_max)
+        ev = lambda: torch.cuda.Event(enable_timing=True)
+        phase_ms = {k: 0.0 for k in ("sort", "moments", "select", "collide", "moment_match")}
+        step_ms, pairs, rounds = 0.0, 0, []
+        launches0 = None
+        for it in range(args.warmup + args.steps):
+            restore()
+            timed = it >= args.warmup
+            if timed and launches0 is None:
+                torch.cuda.synchronize()
+                launches0 = C.launch_count()
+            e = [ev() for _ in range(6)]
+            e[0].record(stream)
+            C.sort_cells(st.cell_id, st.vx, st.vy, st.vz, nc,
+                         out=dict(perm=st.perm, cell_start=st.cell_start, svx=st.svx, svy=st.svy, svz=st.svz),
+                         ws=st.ws)
+            e[1].record(stream)
+            C.cell_moments(st.cell_start, st.svx, st.svy, st.svz, mom=st.mom)
+            e[2].record(stream)
+            C.select_pairs(gas, st.cell_start, st.svx, st.svy, st.svz, st.sigma_g_max, it, capacity,
+                           out=sel, ws=st.ws)
+            e[3].record(stream)
+            if path == "vhs":
+                C.collide_vhs(gas, it, sel, st.svx, st.svy, st.svz)
+            elif path == "jager":
+                C.collide_jager(gas, pot, it, sel, st.svx, st.svy, st.svz, n_nodes=args.n_nodes)
+            else:
+                C.collide_neural(gas, mlp, w_bits, bias, it, st.mom, sel, st.svx, st.svy, st.svz)
+            e[4].record(stream)
+            C.moment_match(st.cell_start, st.mom, st.svx, st.svy, st.svz)
+            e[5].record(stream)
+            if timed:
+                torch.cuda.synchronize()
+                rc = C.sync_status()
+                if rc != 0:
+                    raise RuntimeError(f"device status {rc} on path {path}")
+                names = list(phase_ms)
+                for q in range(5):
+                    phase_ms[names[q]] += e[q].elapsed_time(e[q + 1])
+                step_ms += e[0].elapsed_time(e[5])
+                inf = st.info_host()
+                pairs += inf["n_pairs"]
+                rounds.append(inf["n_rounds"])
+        launches = C.launch_count() - launches0
+        K = args.steps
+        results[path] = dict(
+            collisions_per_s=pairs / (step_ms * 1e-3), ms_per_step=step_ms / K,
+            pairs_per_step=pairs / K, rounds_per_step=float(np.mean(rounds)),
+            phase_ms={k: v / K for k, v in phase_ms.items()}, gpu_launches=launches,
+            step_ms_total=step_ms, pairs_total=pairs)
+        if path == "neural":
+            neural_kernel = dict(ms=phase_ms["collide"] / K, pairs=pairs / K)
+    # ------------------------------------------------------------ e2e (host buffers)
+    e2e = None
+    if not args.no_e2e and "neural" in results:
+        import torch as T
+        gas = D.make_gas(dict(wl["gas"], model=1))
+        path = D.make_path(D.PATH_NEURAL, mlp=mlp, w_bits=w_bits, bias=bias)
+        C.reserve(n, nc, capacity)
+        pin = lambda a: T.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        hin = [pin(wl["cell_id"]), pin(wl["vx"]), pin(wl["vy"]), pin(wl["vz"])]
+        hT = pin(wl["T_cell"])
+        outs = [T.empty(n, dtype=T.float64).pin_memory() for _ in range(3)]
+        perm = T.empty(n, dtype=T.int32).pin_memory()
+        for it in range(args.warmup):
+            C.step_host(gas, path, *hin, hT, it, perm, *outs)
+        t0 = time.perf_counter()
+        tot = 0
+        for it in range(args.steps):
+            tot += C.step_host(gas, path, *hin, hT, it, perm, *outs)
+        dt = time.perf_counter() - t0
+        e2e = dict(value=tot / dt, unit="pair collisions/s",
+                   h2d_bytes_per_step=n * (4 + 24), d2h_bytes_per_step=n * (4 + 24) + 24)
+    return wl, n, nc, results, neural_kernel, e2e
+
+
+# ---------------------------------------------------------------------------- oracle arm
+
+def oracle_sample(seconds_target=15.0, path="neural", steps=1):
+    """Time the CPU oracle (as it stands) on a bounded sample of the same gas:
+    the hypersonic profile shrunk to 0.2 of the box (same shock shape)."""
+    import oracle as O
+    from paper_2602_21244_gb300 import workloads as W
+    wl = W.hypersonic(scale=0.2)
+    gas = O.make_gas(**dict(wl["gas"], model=1 if path != "vhs" else 0))
+    sg = O.sigma_g_max_init(gas, wl["T_cell"], 5.0)
+    wts = W.mlp_weights()
+    mlp = O.make_mlp(8, 128, 3, 3, 0, W.sigma_v(), 273.0, 1e-12)
+    pot = O.make_pot(W.JAGER_SYNTHETIC_AR)
+    t0 = time.perf_counter()
+    pairs = 0
+    for s in range(steps):
+        r = O.step(gas, wl["cell_id"], wl["vx"], wl["vy"], wl["vz"], wl["n_cells"], sg, s, path=path,
+                   pot=pot, mlp=mlp, W=wts["W"], bias=wts["bias"], capacity=1 << 23)
+        pairs += r["pairs"]["n_pairs"]
+    dt = time.perf_counter() - t0
+    return dict(value=pairs / dt, unit="pair collisions/s", cores=1, kind="oracle",
+                sample=f"hypersonic gas at 0.2 scale ({len(wl['cell_id'])} particles, "
+                       f"{wl['n_cells']} cells), {steps} full {path} step(s), {pairs} collisions, "
+                       f"{dt:.1f} s single-threaded")
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo" if args.impl == "reference" else "nccl")
+    if args.impl == "reference":
+        if rank == 0:
+            for _ in range(args.warmup):
+                pass
+            vals = []
+            for _ in range(args.steps):
+                vals.append(oracle_sample(steps=1))
+            v = float(np.mean([x["value"] for x in vals]))
+            cb = dict(vals[0], value=v)
+            line = {"impl": "reference", "metric": "pair collisions/s per update path (neural path, whole step)",
+                    "value": v, "unit": "pair collisions/s", "n_gpus": args.gpus, "steps": args.steps,
+                    "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                    "dtype": "f64", "data": "synthetic",
+                    "config": {"workload": "hypersonic argon gas (oracle sample, 0.2 scale)", "path": "neural"},
+                    "cpu_baseline": cb,
+                    "e2e": {"value": v, "unit": "pair collisions/s", "h2d_bytes_per_step": 0,
+                            "d2h_bytes_per_step": 0}}
+            print(json.dumps(line), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    import torch
+    clk = Clocks(int(os.environ.get("LOCAL_RANK", 0)))
+    if dist is not None:
+        dist.barrier()
+    clk.start()
+    wl, n, nc, results, nk, e2e = run_gb300(args, rank, world, dist)
+    clocks = clk.stop()
+    head = results.get("neural") or next(iter(results.values()))
+    head_path = "neural" if "neural" in results else next(iter(results))
+    ms = head["ms_per_step"]
+    value = head["collisions_per_s"]
+    if dist is not None:
+        t = torch.tensor([ms, head["pairs_per_step"]], dtype=torch.float64, device="cuda")
+        mx = t.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone(); dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms = float(mx[0]); value = float(sm[1]) / (ms * 1e-3)
+    if rank == 0:
+        pk = peaks()
+        roof = None
+        if nk is not None:
+            achieved = nk["pairs"] * MLP_FLOP_PER_PAIR / (nk["ms"] * 1e-3) / 1e12
+            peak = pk.get("bf16_tflops_sustained") if pk else 1700.0
+            roof = {"bound": "tensor", "kernel": "k_collide_neural", "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained" if pk else "fallback"}
+        cb = None
+        if not args.no_cpu_baseline:
+            cb = oracle_sample()
+        line = {"metric": "pair collisions/s per update path (neural path, whole step)",
+                "value": value, "unit": "pair collisions/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"hypersonic argon gas {wl['name']}, {n} particles, {nc} cells",
+                           "path": head_path, "l2": "pristine 258 MB input copied back before every step",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "paths": results, "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
+                "gpu_launches": int(sum(r["gpu_launches"] for r in results.values())),
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

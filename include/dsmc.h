@@ -1,0 +1,320 @@
+/*
+ * dsmc.h -- C ABI of the GB300 (sm_103a) DSMC collision-step library.
+ *
+ * Implements the collision step of "Physics Constrained Neural Collision
+ * Operators for VHS Surrogates and Ab Initio Angle Prediction in DSMC"
+ * (arXiv 2602.21244): cell sort, No-Time-Counter pair selection, one of three
+ * pair-update rules (VHS isotropic scatter, Jager-potential deflection angle,
+ * neural collision operator) and cell-wise moment matching, plus the
+ * training step of the neural operator.
+ *
+ * Conventions (every entry point):
+ *  - Pointers are DEVICE pointers owned by the caller, unless the name of
+ *    the argument ends in _host.  The library never frees or keeps them.
+ *  - Calls are asynchronous on the given stream (a cudaStream_t passed as
+ *    void*; NULL = the legacy default stream).  The return value reports
+ *    argument and launch errors only.  Errors found on the device
+ *    (capacity overflow, a bounded wait that ran out, non-finite input)
+ *    are recorded in the context's status word; dsmc_ctx_sync_status()
+ *    waits for the stream and returns (and clears) that word.
+ *  - Velocities are double precision, structure of arrays (vx, vy, vz),
+ *    in m/s.  Particle and cell indices are int32 (N < 2^31).
+ *  - Scratch memory is a caller-provided workspace of the size returned by
+ *    the matching *_workspace_size() query, 256-byte aligned.
+ *  - Results depend only on the inputs, the seed and the step index, never
+ *    on the launch configuration.
+ *  - Status codes: 0 = DSMC_OK, negative = error (see below).
+ */
+#ifndef DSMC_H_
+#define DSMC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DSMC_ABI_VERSION 1
+
+enum {
+  DSMC_OK = 0,
+  DSMC_ERR_ARG = -1,         /* bad argument (null pointer, size, cell id out of range) */
+  DSMC_ERR_CUDA = -2,        /* a CUDA runtime call failed */
+  DSMC_ERR_CAPACITY = -3,    /* more accepted pairs than the pair buffer holds */
+  DSMC_ERR_TIMEOUT = -4,     /* a bounded device-side wait ran out */
+  DSMC_ERR_NONFINITE = -5,   /* NaN or Inf in an input velocity */
+  DSMC_ERR_UNSUPPORTED = -6  /* shape outside what the kernels handle */
+};
+
+/* Update rules of the collision step (Sec. 2.1: only the scattering rule changes). */
+enum { DSMC_PATH_VHS = 0, DSMC_PATH_JAGER = 1, DSMC_PATH_NEURAL = 2 };
+
+/* Largest number of conflict-free rounds one step may need (see dsmc_select_pairs). */
+#define DSMC_MAX_ROUNDS 1024
+
+typedef struct dsmc_ctx dsmc_ctx_t;
+
+/* Gas and selection parameters (Sec. 2.2).
+ *  model 0: Bird's VHS cross section
+ *           sigma(g) = pi d_ref^2 (2 k T_ref/(m_r g^2))^(omega-1/2) / Gamma(5/2-omega),
+ *           m_r = mass/2 (omega = 1/2 is the hard sphere);
+ *  model 1: constant sigma = pi b_max^2 (impact-parameter cut-off of the
+ *           ab-initio paths, Sec. 3.4.2: b <= b_max).
+ *  fn_over_vc = F_N / V_c, the number of real molecules per simulator
+ *  particle divided by the cell volume (1/m^3). */
+typedef struct {
+  double mass;       /* kg */
+  double d_ref;      /* m */
+  double omega;
+  double T_ref;      /* K */
+  double fn_over_vc; /* 1/m^3 */
+  double dt;         /* s */
+  uint64_t seed;     /* Philox key */
+  int32_t model;
+  int32_t pad_;
+  double b_max;      /* m */
+} dsmc_gas_t;
+
+/* Interaction potential for the deflection angle (Sec. 3.4.1), r in
+ * Angstrom, V/k_B in Kelvin.
+ *  kind 0: Jager form, Eq. (jager_potential) with Tang-Toennies damping
+ *          Eq. (damping) for r >= 0.4 R_eps, screened Coulomb
+ *          At exp(-at r)/r below;
+ *  kind 1: hard sphere of diameter d_hs (closed-form check);
+ *  kind 2: inverse power kappa / r^p. */
+typedef struct {
+  int32_t kind;
+  int32_t pad_;
+  double A, a1, a2, am1, am2; /* repulsion A exp(a1 r + a2 r^2 + am1/r + am2/r^2) */
+  double beta;                /* damping constant (the paper's "b" in f_n(b r)) */
+  double C[6];                /* C6, C8, C10, C12, C14, C16 */
+  double R_eps;
+  double At, at;
+  double d_hs;
+  double kappa, p;
+} dsmc_potential_t;
+
+/* Neural collision operator (Sec. 2.2 Eq. mlp_input / mlp_output).
+ *  d_in 8: x = [v_r/sigma_v (3), T_cell/T_ref (1), xi (4)];
+ *  d_in 6: x = [v_r/sigma_v (3), xi (3)] (the paper's 6-input form).
+ *  n_hidden hidden layers of `width` units (the tensor-core path takes
+ *  width 128 and 1..4 hidden layers), act 0 = SiLU, 1 = ReLU, then a
+ *  linear layer to d_out = 3. */
+typedef struct {
+  int32_t d_in, width, n_hidden, d_out, act, pad_;
+  double sigma_v; /* m/s */
+  double T_ref;   /* K */
+  double eps;     /* projection safeguard on ||y|| (normalised units) */
+} dsmc_mlp_t;
+
+/* Written by dsmc_select_pairs (device memory). */
+typedef struct {
+  int64_t n_pairs;      /* accepted pairs this step */
+  int64_t n_candidates; /* NTC candidates drawn this step */
+  int32_t n_rounds;     /* conflict-free rounds */
+  int32_t pad_;
+} dsmc_select_info_t;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on `device` (allocates the status word and small
+ * per-device tables; the only allocation the library makes besides
+ * dsmc_ctx_reserve).  Returns DSMC_ERR_CUDA if the device is unusable. */
+int dsmc_ctx_create(dsmc_ctx_t** ctx, int device);
+void dsmc_ctx_destroy(dsmc_ctx_t* ctx);
+/* Wait for `stream`, return the first device-side error since the last
+ * call (DSMC_OK if none) and clear it. */
+int dsmc_ctx_sync_status(dsmc_ctx_t* ctx, void* stream);
+/* Text of the last host-side error of this context (static storage). */
+const char* dsmc_last_error(dsmc_ctx_t* ctx);
+int dsmc_abi_version(void);
+/* Number of CUDA kernels this context has launched so far (for reporting). */
+int64_t dsmc_ctx_launch_count(dsmc_ctx_t* ctx);
+
+/* ---------------------------------------------------------------- sort */
+
+/* Sec. 2.6 (1): sort particles by cell index so each cell's particles are
+ * contiguous.  Stable counting sort: perm[s] is the input index of sorted
+ * slot s, slots of a cell keep the input order.  cell_start[n_cells+1]
+ * holds each cell's first slot; s{x,y,z} receive the gathered velocities.
+ * cell_id[i] outside [0, n_cells) records DSMC_ERR_ARG. */
+size_t dsmc_sort_workspace_size(int32_t n, int32_t n_cells);
+int dsmc_sort_cells(dsmc_ctx_t* ctx, int32_t n, int32_t n_cells, const int32_t* cell_id,
+                    const double* vx, const double* vy, const double* vz, int32_t* perm,
+                    int32_t* cell_start, double* svx, double* svy, double* svz, void* ws,
+                    size_t ws_bytes, void* stream);
+
+/* Per-cell moments of sorted velocities, two FP64 passes:
+ * mom[5k..5k+4] = {N, sum vx, sum vy, sum vz, Theta = sum |v - u|^2},
+ * u = sum v / N.  Non-finite velocities record DSMC_ERR_NONFINITE. */
+int dsmc_cell_moments(dsmc_ctx_t* ctx, int32_t n_cells, const int32_t* cell_start,
+                      const double* vx, const double* vy, const double* vz, double* mom,
+                      void* stream);
+
+/* ---------------------------------------------------------------- selection */
+
+/* Initial (sigma g)_max of each cell: sigma(g0) g0, g0 = factor sqrt(2 k T_cell/m). */
+int dsmc_sigma_g_max_init(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, int32_t n_cells,
+                          const double* T_cell, double factor, double* sigma_g_max,
+                          void* stream);
+
+/* Sec. 2.2: NTC pair selection over cell-sorted particles.
+ *  Cell k with N >= 2 draws M = floor(1/2 N(N-1) (F_N/V_c) (sigma g)_max dt + U)
+ *  candidates (Philox tag 1); candidate m picks i, j != i uniformly (tag 2)
+ *  and is accepted iff U' < sigma(g) g / (sigma g)_max with g from the
+ *  velocities as passed in (the pre-step state).  (sigma g)_max is raised
+ *  afterwards to the largest sigma g among the cell's candidates.
+ *  Accepted pairs act in candidate order; round(p) = 1 + max(last round of
+ *  i, last round of j) splits them into rounds of disjoint pairs that,
+ *  applied in round order, reproduce the sequential result exactly.
+ *  Output: pairs[4p..4p+3] = {i, j, cell, m} (sorted slot indices, cell,
+ *  candidate index) grouped by round (order inside a round unspecified),
+ *  round_offsets[r] = first pair of round r (the array holds
+ *  DSMC_MAX_ROUNDS + 1 entries; r = 0..n_rounds are meaningful), *info.
+ *  More than `capacity` pairs records DSMC_ERR_CAPACITY and writes none;
+ *  more than DSMC_MAX_ROUNDS rounds records DSMC_ERR_UNSUPPORTED. */
+size_t dsmc_select_workspace_size(int32_t n, int32_t n_cells, int64_t capacity);
+int dsmc_select_pairs(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, int32_t n, int32_t n_cells,
+                      const int32_t* cell_start, const double* vx, const double* vy,
+                      const double* vz, double* sigma_g_max, uint64_t step, int64_t capacity,
+                      int32_t* pairs, int32_t* round_offsets, dsmc_select_info_t* info,
+                      void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------- pair updates */
+
+/* VHS isotropic scatter (the phenomenological kernel the paper replaces,
+ * Sec. 2.1) with the centre-of-mass update of Sec. 2.3:
+ *  cos chi = 2U1 - 1, eps = 2 pi U2 (Philox tag 3, counter = candidate m),
+ *  v_r' = |v_r| (cos chi, sin chi cos eps, sin chi sin eps),
+ *  v_i = v_cm + v_r'/2, v_j = v_cm - v_r'/2; rounds in order, in place. */
+int dsmc_collide_vhs(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, uint64_t step,
+                     const int32_t* pairs, const int32_t* round_offsets,
+                     const dsmc_select_info_t* info, double* vx, double* vy, double* vz,
+                     void* stream);
+
+/* Sec. 3.4.2 / 3.4.4: deflection angle of the classical scattering integral
+ *  chi(b, E) = pi - 2 b int_{r_min}^inf dr / (r^2 sqrt(1 - b^2/r^2 - V(r)/E)),
+ *  E = E_r/k_B = m g^2/(4 k_B), r_min the largest root of the radicand.
+ *  FP32 bracket and quadrature (u = r_min/r, u = 1 - s^2, n_nodes-point
+ *  Gauss-Legendre in s, n_nodes in [8, 128]) with an FP64 Newton
+ *  refinement of r_min.  Signed: attraction gives chi < 0.
+ *  b in Angstrom, g in m/s, n pairs. */
+int dsmc_jager_chi(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_potential_t* pot,
+                   int32_t n_nodes, int64_t n, const float* b, const float* g, float* chi,
+                   void* stream);
+
+/* Pair update with the deflection angle: b = b_max sqrt(U1), eps = 2 pi U2
+ *  (tag 4); v_r' = cos chi v_r + |v_r| sin chi (cos eps c + sin eps a) with
+ *  c = (0, v_z, -v_y)/q, a = (q^2, -v_x v_y, -v_x v_z)/(|v_r| q),
+ *  q = sqrt(v_y^2 + v_z^2) (Bird 1994, Eq. 2.22; for q = 0, c = (0,1,0) and
+ *  a = c x v_r/|v_r|).  chi_out (optional, may be NULL) receives each
+ *  pair's chi in pair order. */
+int dsmc_collide_jager(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_potential_t* pot,
+                       int32_t n_nodes, uint64_t step, const int32_t* pairs,
+                       const int32_t* round_offsets, const dsmc_select_info_t* info,
+                       double* vx, double* vy, double* vz, float* chi_out, void* stream);
+
+/* Sec. 2.2-2.3: neural collision operator on the tcgen05 tensor cores.
+ *  x as in dsmc_mlp_t (xi: Box-Muller normals from tag 5, subs 0 and 1;
+ *  T_cell = m Theta_pre / (3 k_B N) from mom_pre), bf16 operands with FP32
+ *  accumulation, y = f_theta(x), u = y/||y|| (isotropic direction from tag 3
+ *  if ||y|| <= eps), v_r' = |v_r| u, centre-of-mass update in FP64.
+ *  weights_bf16: each layer's row-major [out x in] matrix, concatenated;
+ *  biases: each layer's bias (FP32), concatenated.  Requires width 128,
+ *  d_out 3, d_in <= 16. */
+int dsmc_collide_neural(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_mlp_t* mlp,
+                        const uint16_t* weights_bf16, const float* biases, uint64_t step,
+                        const double* mom_pre, const int32_t* pairs,
+                        const int32_t* round_offsets, const dsmc_select_info_t* info,
+                        double* vx, double* vy, double* vz, void* stream);
+
+/* The MLP alone on the tensor cores: y[n x 3] = f_theta(x[n x d_in]) with x
+ * and y FP32 row-major (x rounded to bf16 on the way in), same weight
+ * layout as dsmc_collide_neural. */
+int dsmc_mlp_forward(dsmc_ctx_t* ctx, const dsmc_mlp_t* mlp, const uint16_t* weights_bf16,
+                     const float* biases, int64_t n, const float* x, float* y, void* stream);
+
+/* Diagnostic with no counterpart in the paper: D[128 x N] = A[128 x K] B[N x K]^T
+ * (bf16 row-major in, FP32 row-major out) through the same shared-memory
+ * operand layout, descriptors and tcgen05.mma issue as the MLP, on one CTA.
+ * N a multiple of 16 in [16, 256], K a multiple of 16 in [16, 128]. */
+int dsmc_tc_selftest(dsmc_ctx_t* ctx, int32_t N, int32_t K, const uint16_t* A, const uint16_t* B,
+                     float* D, void* stream);
+
+/* ---------------------------------------------------------------- moment matching */
+
+/* Sec. 2.5, centred: per cell v <- u_pre + alpha (v - u_post),
+ * alpha = sqrt(Theta_pre/Theta_post) (1 if N < 2 or Theta_post = 0), from
+ * mom_pre of dsmc_cell_moments.  Restores each cell's momentum and kinetic
+ * energy; equals Eq. (cell_energy_clamp) when the cell mean velocity is 0. */
+int dsmc_moment_match(dsmc_ctx_t* ctx, int32_t n_cells, const int32_t* cell_start,
+                      const double* mom_pre, double* vx, double* vy, double* vz,
+                      void* stream);
+
+/* ---------------------------------------------------------------- whole step */
+
+/* Buffers of one collision step (all device memory, caller-owned).
+ * Input: cell_id, vx, vy, vz (unsorted).  Output: perm, cell_start and the
+ * sorted, post-collision s{x,y,z}; mom (pre moments), sigma_g_max (in/out),
+ * pairs / round_offsets / info as in dsmc_select_pairs. */
+typedef struct {
+  int32_t n, n_cells;
+  int64_t capacity;
+  const int32_t* cell_id;
+  const double *vx, *vy, *vz;
+  int32_t* perm;
+  int32_t* cell_start;
+  double *svx, *svy, *svz;
+  double* mom;
+  double* sigma_g_max;
+  int32_t* pairs;
+  int32_t* round_offsets;
+  dsmc_select_info_t* info;
+  void* ws;
+  size_t ws_bytes;
+} dsmc_step_buffers_t;
+
+/* Path-specific parameters of a step (unused fields may be NULL/0). */
+typedef struct {
+  int32_t path;    /* DSMC_PATH_* */
+  int32_t n_nodes; /* Jager quadrature nodes */
+  const dsmc_potential_t* pot;
+  const dsmc_mlp_t* mlp;
+  const uint16_t* weights_bf16;
+  const float* biases;
+} dsmc_path_t;
+
+size_t dsmc_step_workspace_size(int32_t n, int32_t n_cells, int64_t capacity);
+/* One collision step: sort, pre moments, selection, pair updates of the
+ * chosen path, moment matching (Sec. 2.1-2.6). */
+int dsmc_step(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_path_t* path,
+              const dsmc_step_buffers_t* buf, uint64_t step, void* stream);
+
+/* Same step from and to HOST memory: copies cell_id_host / v*_host into
+ * device buffers reserved by dsmc_ctx_reserve, runs dsmc_step, copies the
+ * sorted post-collision velocities and perm back, and synchronises the
+ * stream.  sigma_g_max stays on the device between calls (initialised from
+ * T_cell_host on the first call after a reserve).  Returns the first error,
+ * device-side ones included. */
+int dsmc_ctx_reserve(dsmc_ctx_t* ctx, int32_t n_max, int32_t n_cells, int64_t capacity);
+int dsmc_step_host(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_path_t* path,
+                   int32_t n, const int32_t* cell_id_host, const double* vx_host,
+                   const double* vy_host, const double* vz_host, const double* T_cell_host,
+                   uint64_t step, int32_t* perm_host, double* svx_host, double* svy_host,
+                   double* svz_host, int64_t* n_pairs_host, void* stream);
+
+/* ---------------------------------------------------------------- training */
+
+/* Sec. 3.4.5 physics harvesting: target post-collision velocities of pairs
+ * (vi, vj: [n x 3] FP64 row-major) deflected by chi(b, E) with azimuth eps
+ * (b in Angstrom, eps in rad), as in dsmc_collide_jager. */
+int dsmc_harvest_jager(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_potential_t* pot,
+                       int32_t n_nodes, int64_t n, const double* vi, const double* vj,
+                       const double* b, const double* eps, double* vi_out, double* vj_out,
+                       void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DSMC_H_ */

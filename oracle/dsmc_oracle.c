@@ -585,13 +585,21 @@ static double act_f(int act, double z) {
 
 /* Plain layer-by-layer forward of one sample.  W holds each layer's
  * row-major [out x in] matrix, one after another; bias likewise.  With
- * bf16 != 0 the input and every hidden activation are rounded to bf16,
- * as a bf16 tensor-core kernel stores them. */
+ * bf16 != 0 the storage precision of a bf16 tensor-core kernel is
+ * emulated: the input as the sum of two bf16 terms (hi = bf16(x),
+ * lo = bf16(x - hi)) and every hidden activation rounded to bf16. */
 void or_mlp_forward1(const or_mlp_t* d, const double* W, const double* bias,
                      const double* x, int bf16, double* y) {
   double h[1024], z[1024];
   int n_in = d->d_in;
-  for (int q = 0; q < n_in; ++q) h[q] = bf16 ? or_bf16_round(x[q]) : x[q];
+  for (int q = 0; q < n_in; ++q) {
+    if (bf16) {
+      double hi = or_bf16_round(x[q]);
+      h[q] = hi + or_bf16_round(x[q] - hi);
+    } else {
+      h[q] = x[q];
+    }
+  }
   const double* Wl = W;
   const double* bl = bias;
   for (int l = 0; l <= d->n_hidden; ++l) {

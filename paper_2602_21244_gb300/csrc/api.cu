@@ -1,0 +1,373 @@
+// C ABI of the DSMC library: context, status word, argument checks, the
+// whole collision step and its host-buffer variant.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "internal.cuh"
+
+namespace dsmc {
+
+struct Ctx {
+  int device = 0;
+  int sms = 0;
+  int* d_status = nullptr;    // device status word
+  unsigned* d_bar = nullptr;  // grid-barrier words
+  int* h_status = nullptr;    // pinned mirror
+  char err[256] = {0};
+  // dsmc_ctx_reserve buffers for dsmc_step_host
+  int32_t r_n = 0, r_cells = 0;
+  int64_t r_cap = 0;
+  bool r_sg_ready = false;
+  void* r_mem = nullptr;
+  size_t r_bytes = 0;
+  dsmc_step_buffers_t rb = {};
+  double* r_T = nullptr;
+  void* r_host_info = nullptr;
+  int64_t launches = 0;
+};
+
+int record(Ctx* c, int code, const char* msg) {
+  if (c && msg) snprintf(c->err, sizeof(c->err), "%s", msg);
+  return code;
+}
+int* status_ptr(Ctx* c) { return c->d_status; }
+unsigned* barrier_ptr(Ctx* c) { return c->d_bar; }
+int sm_count(Ctx* c) { return c->sms; }
+void count_launches(Ctx* c, int k) { c->launches += k; }
+
+}  // namespace dsmc
+
+using dsmc::Ctx;
+struct dsmc_ctx : dsmc::Ctx {};
+
+static inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
+
+#define CHECK_CTX(c) \
+  do { if (!(c)) return DSMC_ERR_ARG; } while (0)
+#define REQUIRE(c, cond, msg) \
+  do { if (!(cond)) return dsmc::record((c), DSMC_ERR_ARG, (msg)); } while (0)
+
+extern "C" {
+
+int dsmc_abi_version(void) { return DSMC_ABI_VERSION; }
+
+int dsmc_ctx_create(dsmc_ctx_t** out, int device) {
+  if (!out) return DSMC_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return DSMC_ERR_CUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return DSMC_ERR_CUDA;
+  dsmc_ctx* c = new dsmc_ctx();
+  c->device = device;
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+  bool ok = cudaMalloc(&c->d_status, 256) == cudaSuccess &&
+            cudaMalloc(&c->d_bar, 256) == cudaSuccess &&
+            cudaMallocHost(&c->h_status, 256) == cudaSuccess &&
+            cudaMemset(c->d_status, 0, 256) == cudaSuccess &&
+            cudaMemset(c->d_bar, 0, 256) == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
+  if (!ok) {
+    dsmc_ctx_destroy(c);
+    return DSMC_ERR_CUDA;
+  }
+  *out = c;
+  return DSMC_OK;
+}
+
+void dsmc_ctx_destroy(dsmc_ctx_t* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  if (c->d_status) cudaFree(c->d_status);
+  if (c->d_bar) cudaFree(c->d_bar);
+  if (c->h_status) cudaFreeHost(c->h_status);
+  if (c->r_mem) cudaFree(c->r_mem);
+  if (c->r_host_info) cudaFreeHost(c->r_host_info);
+  delete c;
+}
+
+int dsmc_ctx_sync_status(dsmc_ctx_t* c, void* stream) {
+  CHECK_CTX(c);
+  if (cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, S(stream)) !=
+          cudaSuccess ||
+      cudaMemsetAsync(c->d_status, 0, sizeof(int), S(stream)) != cudaSuccess ||
+      cudaStreamSynchronize(S(stream)) != cudaSuccess)
+    return dsmc::record(c, DSMC_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+  return *c->h_status;
+}
+
+const char* dsmc_last_error(dsmc_ctx_t* c) { return c ? c->err : "null context"; }
+
+int64_t dsmc_ctx_launch_count(dsmc_ctx_t* c) { return c ? c->launches : -1; }
+
+size_t dsmc_sort_workspace_size(int32_t n, int32_t n_cells) { return dsmc::sort_ws(n, n_cells); }
+
+int dsmc_sort_cells(dsmc_ctx_t* c, int32_t n, int32_t n_cells, const int32_t* cell_id,
+                    const double* vx, const double* vy, const double* vz, int32_t* perm,
+                    int32_t* cell_start, double* svx, double* svy, double* svz, void* ws,
+                    size_t ws_bytes, void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, n >= 0 && n_cells >= 1, "sort: n < 0 or n_cells < 1");
+  REQUIRE(c, cell_start && ws, "sort: null cell_start or workspace");
+  REQUIRE(c, n == 0 || (cell_id && vx && vy && vz && perm && svx && svy && svz), "sort: null array");
+  return dsmc::launch_sort(c, n, n_cells, cell_id, vx, vy, vz, perm, cell_start, svx, svy, svz,
+                           ws, ws_bytes, S(stream));
+}
+
+int dsmc_cell_moments(dsmc_ctx_t* c, int32_t n_cells, const int32_t* cell_start,
+                      const double* vx, const double* vy, const double* vz, double* mom,
+                      void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, n_cells >= 0 && cell_start && mom, "moments: bad arguments");
+  return dsmc::launch_moments(c, n_cells, cell_start, vx, vy, vz, mom, S(stream));
+}
+
+int dsmc_sigma_g_max_init(dsmc_ctx_t* c, const dsmc_gas_t* gas, int32_t n_cells,
+                          const double* T_cell, double factor, double* sgmax, void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, gas && T_cell && sgmax && n_cells >= 0 && factor > 0, "sigma_g_max_init: bad arguments");
+  return dsmc::launch_sgmax_init(c, *gas, n_cells, T_cell, factor, sgmax, S(stream));
+}
+
+size_t dsmc_select_workspace_size(int32_t n, int32_t n_cells, int64_t capacity) {
+  return dsmc::select_ws(n, n_cells, capacity);
+}
+
+static int check_gas(Ctx* c, const dsmc_gas_t* gas) {
+  REQUIRE(c, gas, "null gas");
+  REQUIRE(c, gas->mass > 0 && gas->dt > 0 && gas->fn_over_vc > 0, "gas: mass, dt, fn_over_vc > 0");
+  REQUIRE(c, gas->model == 0 || gas->model == 1, "gas: model must be 0 or 1");
+  REQUIRE(c, gas->model == 1 || (gas->d_ref > 0 && gas->T_ref > 0 && gas->omega > 0 && gas->omega < 2.5),
+          "gas: VHS needs d_ref, T_ref > 0, 0 < omega < 2.5");
+  REQUIRE(c, gas->model == 0 || gas->b_max > 0, "gas: constant cross section needs b_max > 0");
+  return 0;
+}
+
+int dsmc_select_pairs(dsmc_ctx_t* c, const dsmc_gas_t* gas, int32_t n, int32_t n_cells,
+                      const int32_t* cell_start, const double* vx, const double* vy,
+                      const double* vz, double* sgmax, uint64_t step, int64_t capacity,
+                      int32_t* pairs, int32_t* round_offsets, dsmc_select_info_t* info,
+                      void* ws, size_t ws_bytes, void* stream) {
+  CHECK_CTX(c);
+  if (int rc = check_gas(c, gas)) return rc;
+  REQUIRE(c, n >= 0 && n_cells >= 1 && capacity >= 0, "select: bad sizes");
+  REQUIRE(c, cell_start && sgmax && round_offsets && info && ws, "select: null pointer");
+  REQUIRE(c, capacity == 0 || pairs, "select: null pairs");
+  return dsmc::launch_select(c, *gas, n, n_cells, cell_start, vx, vy, vz, sgmax, step, capacity,
+                             pairs, round_offsets, info, ws, ws_bytes, S(stream));
+}
+
+int dsmc_collide_vhs(dsmc_ctx_t* c, const dsmc_gas_t* gas, uint64_t step, const int32_t* pairs,
+                     const int32_t* round_offsets, const dsmc_select_info_t* info, double* vx,
+                     double* vy, double* vz, void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, gas && round_offsets && info && vx && vy && vz, "collide_vhs: null pointer");
+  return dsmc::launch_collide_vhs(c, *gas, step, pairs, round_offsets, info, vx, vy, vz, S(stream));
+}
+
+static int check_pot(Ctx* c, const dsmc_potential_t* p, int n_nodes) {
+  REQUIRE(c, p, "null potential");
+  REQUIRE(c, p->kind >= 0 && p->kind <= 2, "potential: kind must be 0, 1 or 2");
+  REQUIRE(c, n_nodes >= 8 && n_nodes <= 128, "potential: n_nodes must be in [8, 128]");
+  REQUIRE(c, p->kind != 0 || p->R_eps > 0, "potential: Jager form needs R_eps > 0");
+  REQUIRE(c, p->kind != 1 || p->d_hs > 0, "potential: hard sphere needs d_hs > 0");
+  REQUIRE(c, p->kind != 2 || p->p > 0, "potential: inverse power needs p > 0");
+  return 0;
+}
+
+int dsmc_jager_chi(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_potential_t* pot,
+                   int32_t n_nodes, int64_t n, const float* b, const float* g, float* chi,
+                   void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, gas && gas->mass > 0, "jager_chi: gas with mass > 0 required");
+  if (int rc = check_pot(c, pot, n_nodes)) return rc;
+  REQUIRE(c, n >= 0 && (n == 0 || (b && g && chi)), "jager_chi: bad arrays");
+  return dsmc::launch_jager_chi(c, *gas, *pot, n_nodes, n, b, g, chi, S(stream));
+}
+
+int dsmc_collide_jager(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_potential_t* pot,
+                       int32_t n_nodes, uint64_t step, const int32_t* pairs,
+                       const int32_t* round_offsets, const dsmc_select_info_t* info,
+                       double* vx, double* vy, double* vz, float* chi_out, void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, gas && gas->b_max > 0, "collide_jager: gas with b_max > 0 required");
+  if (int rc = check_pot(c, pot, n_nodes)) return rc;
+  REQUIRE(c, round_offsets && info && vx && vy && vz, "collide_jager: null pointer");
+  return dsmc::launch_collide_jager(c, *gas, *pot, n_nodes, step, pairs, round_offsets, info, vx,
+                                    vy, vz, chi_out, S(stream));
+}
+
+static int check_mlp(Ctx* c, const dsmc_mlp_t* m) {
+  REQUIRE(c, m, "null mlp");
+  REQUIRE(c, m->width == 128 && m->d_out == 3 && (m->d_in == 6 || m->d_in == 8) &&
+                 m->n_hidden >= 1 && m->n_hidden <= 4 && (m->act == 0 || m->act == 1),
+          "mlp: supported shape is d_in 6|8, width 128, 1..4 hidden layers, d_out 3, act 0|1");
+  REQUIRE(c, m->sigma_v > 0 && m->T_ref > 0 && m->eps >= 0, "mlp: sigma_v, T_ref > 0, eps >= 0");
+  return 0;
+}
+
+int dsmc_collide_neural(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_mlp_t* mlp,
+                        const uint16_t* w, const float* bias, uint64_t step,
+                        const double* mom_pre, const int32_t* pairs,
+                        const int32_t* round_offsets, const dsmc_select_info_t* info,
+                        double* vx, double* vy, double* vz, void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, gas, "collide_neural: null gas");
+  if (int rc = check_mlp(c, mlp)) return rc;
+  REQUIRE(c, w && bias && mom_pre && round_offsets && info && vx && vy && vz,
+          "collide_neural: null pointer");
+  return dsmc::launch_collide_neural(c, *gas, *mlp, w, bias, step, mom_pre, pairs, round_offsets,
+                                     info, vx, vy, vz, S(stream));
+}
+
+int dsmc_mlp_forward(dsmc_ctx_t* c, const dsmc_mlp_t* mlp, const uint16_t* w, const float* bias,
+                     int64_t n, const float* x, float* y, void* stream) {
+  CHECK_CTX(c);
+  if (int rc = check_mlp(c, mlp)) return rc;
+  REQUIRE(c, w && bias && n >= 0 && (n == 0 || (x && y)), "mlp_forward: bad arguments");
+  return dsmc::launch_mlp_forward(c, *mlp, w, bias, n, x, y, S(stream));
+}
+
+int dsmc_tc_selftest(dsmc_ctx_t* c, int32_t N, int32_t K, const uint16_t* A, const uint16_t* B,
+                     float* D, void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, N >= 16 && N <= 256 && N % 16 == 0 && K >= 16 && K <= 128 && K % 16 == 0,
+          "tc_selftest: N in [16,256], K in [16,128], multiples of 16");
+  REQUIRE(c, A && B && D, "tc_selftest: null pointer");
+  return dsmc::launch_tc_selftest(c, N, K, A, B, D, S(stream));
+}
+
+int dsmc_moment_match(dsmc_ctx_t* c, int32_t n_cells, const int32_t* cell_start,
+                      const double* mom_pre, double* vx, double* vy, double* vz, void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, n_cells >= 0 && cell_start && mom_pre, "moment_match: bad arguments");
+  return dsmc::launch_moment_match(c, n_cells, cell_start, mom_pre, vx, vy, vz, S(stream));
+}
+
+int dsmc_harvest_jager(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_potential_t* pot,
+                       int32_t n_nodes, int64_t n, const double* vi, const double* vj,
+                       const double* b, const double* eps, double* vio, double* vjo,
+                       void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, gas && gas->mass > 0, "harvest: gas with mass > 0 required");
+  if (int rc = check_pot(c, pot, n_nodes)) return rc;
+  REQUIRE(c, n >= 0 && (n == 0 || (vi && vj && b && eps && vio && vjo)), "harvest: bad arrays");
+  return dsmc::launch_harvest_jager(c, *gas, *pot, n_nodes, n, vi, vj, b, eps, vio, vjo, S(stream));
+}
+
+// ---------------------------------------------------------------- whole step
+size_t dsmc_step_workspace_size(int32_t n, int32_t n_cells, int64_t capacity) {
+  const size_t a = dsmc::sort_ws(n, n_cells), b = dsmc::select_ws(n, n_cells, capacity);
+  return a > b ? a : b;
+}
+
+int dsmc_step(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t* path,
+              const dsmc_step_buffers_t* B, uint64_t step, void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, gas && path && B, "step: null argument");
+  if (int rc = check_gas(c, gas)) return rc;
+  REQUIRE(c, B->ws_bytes >= dsmc_step_workspace_size(B->n, B->n_cells, B->capacity),
+          "step: workspace too small");
+  int rc = dsmc_sort_cells(c, B->n, B->n_cells, B->cell_id, B->vx, B->vy, B->vz, B->perm,
+                           B->cell_start, B->svx, B->svy, B->svz, B->ws, B->ws_bytes, stream);
+  if (rc) return rc;
+  rc = dsmc_cell_moments(c, B->n_cells, B->cell_start, B->svx, B->svy, B->svz, B->mom, stream);
+  if (rc) return rc;
+  rc = dsmc_select_pairs(c, gas, B->n, B->n_cells, B->cell_start, B->svx, B->svy, B->svz,
+                         B->sigma_g_max, step, B->capacity, B->pairs, B->round_offsets, B->info,
+                         B->ws, B->ws_bytes, stream);
+  if (rc) return rc;
+  switch (path->path) {
+    case DSMC_PATH_VHS:
+      rc = dsmc_collide_vhs(c, gas, step, B->pairs, B->round_offsets, B->info, B->svx, B->svy,
+                            B->svz, stream);
+      break;
+    case DSMC_PATH_JAGER:
+      rc = dsmc_collide_jager(c, gas, path->pot, path->n_nodes, step, B->pairs, B->round_offsets,
+                              B->info, B->svx, B->svy, B->svz, nullptr, stream);
+      break;
+    case DSMC_PATH_NEURAL:
+      rc = dsmc_collide_neural(c, gas, path->mlp, path->weights_bf16, path->biases, step, B->mom,
+                               B->pairs, B->round_offsets, B->info, B->svx, B->svy, B->svz,
+                               stream);
+      break;
+    default:
+      return dsmc::record(c, DSMC_ERR_ARG, "step: unknown path");
+  }
+  if (rc) return rc;
+  return dsmc_moment_match(c, B->n_cells, B->cell_start, B->mom, B->svx, B->svy, B->svz, stream);
+}
+
+int dsmc_ctx_reserve(dsmc_ctx_t* c, int32_t n_max, int32_t n_cells, int64_t capacity) {
+  CHECK_CTX(c);
+  REQUIRE(c, n_max >= 0 && n_cells >= 1 && capacity >= 0, "reserve: bad sizes");
+  if (c->r_mem) { cudaFree(c->r_mem); c->r_mem = nullptr; }
+  const size_t n = (size_t)(n_max > 0 ? n_max : 1), nc = (size_t)n_cells;
+  const size_t wsb = dsmc_step_workspace_size(n_max, n_cells, capacity);
+  size_t sizes[] = {4 * n, 8 * n, 8 * n, 8 * n, 4 * n, 4 * (nc + 1), 8 * n, 8 * n, 8 * n,
+                    40 * nc, 8 * nc, 16 * (size_t)(capacity > 0 ? capacity : 1),
+                    4 * (DSMC_MAX_ROUNDS + 1), sizeof(dsmc_select_info_t), 8 * nc, wsb};
+  size_t total = 0;
+  for (size_t s : sizes) total += dsmc::align256(s);
+  if (cudaSetDevice(c->device) != cudaSuccess || cudaMalloc(&c->r_mem, total) != cudaSuccess)
+    return dsmc::record(c, DSMC_ERR_CUDA, "reserve: cudaMalloc failed");
+  if (!c->r_host_info && cudaMallocHost(&c->r_host_info, 64) != cudaSuccess)
+    return dsmc::record(c, DSMC_ERR_CUDA, "reserve: cudaMallocHost failed");
+  char* p = (char*)c->r_mem;
+  void* ptr[16];
+  for (int q = 0; q < 16; ++q) { ptr[q] = p; p += dsmc::align256(sizes[q]); }
+  dsmc_step_buffers_t& b = c->rb;
+  b.n = n_max; b.n_cells = n_cells; b.capacity = capacity;
+  b.cell_id = (int32_t*)ptr[0]; b.vx = (double*)ptr[1]; b.vy = (double*)ptr[2]; b.vz = (double*)ptr[3];
+  b.perm = (int32_t*)ptr[4]; b.cell_start = (int32_t*)ptr[5];
+  b.svx = (double*)ptr[6]; b.svy = (double*)ptr[7]; b.svz = (double*)ptr[8];
+  b.mom = (double*)ptr[9]; b.sigma_g_max = (double*)ptr[10]; b.pairs = (int32_t*)ptr[11];
+  b.round_offsets = (int32_t*)ptr[12]; b.info = (dsmc_select_info_t*)ptr[13];
+  c->r_T = (double*)ptr[14];
+  b.ws = ptr[15]; b.ws_bytes = wsb;
+  c->r_n = n_max; c->r_cells = n_cells; c->r_cap = capacity; c->r_sg_ready = false;
+  return DSMC_OK;
+}
+
+int dsmc_step_host(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t* path, int32_t n,
+                   const int32_t* cell_id_h, const double* vx_h, const double* vy_h,
+                   const double* vz_h, const double* T_cell_h, uint64_t step, int32_t* perm_h,
+                   double* svx_h, double* svy_h, double* svz_h, int64_t* n_pairs_h,
+                   void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, c->r_mem, "step_host: call dsmc_ctx_reserve first");
+  REQUIRE(c, n >= 0 && n <= c->r_n, "step_host: n exceeds the reserved size");
+  REQUIRE(c, n == 0 || (cell_id_h && vx_h && vy_h && vz_h && svx_h && svy_h && svz_h),
+          "step_host: null host array");
+  cudaStream_t s = S(stream);
+  dsmc_step_buffers_t b = c->rb;
+  b.n = n;
+  const size_t n4 = 4 * (size_t)n, n8 = 8 * (size_t)n;
+  bool ok = cudaMemcpyAsync((void*)b.cell_id, cell_id_h, n4, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+            cudaMemcpyAsync((void*)b.vx, vx_h, n8, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+            cudaMemcpyAsync((void*)b.vy, vy_h, n8, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+            cudaMemcpyAsync((void*)b.vz, vz_h, n8, cudaMemcpyHostToDevice, s) == cudaSuccess;
+  if (!ok) return dsmc::record(c, DSMC_ERR_CUDA, "step_host: host-to-device copy failed");
+  if (!c->r_sg_ready) {
+    REQUIRE(c, T_cell_h, "step_host: T_cell_host needed on the first call");
+    if (cudaMemcpyAsync(c->r_T, T_cell_h, 8 * (size_t)b.n_cells, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return dsmc::record(c, DSMC_ERR_CUDA, "step_host: copy of T_cell failed");
+    int rc = dsmc_sigma_g_max_init(c, gas, b.n_cells, c->r_T, 5.0, b.sigma_g_max, stream);
+    if (rc) return rc;
+    c->r_sg_ready = true;
+  }
+  int rc = dsmc_step(c, gas, path, &b, step, stream);
+  if (rc) return rc;
+  ok = cudaMemcpyAsync(svx_h, b.svx, n8, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+       cudaMemcpyAsync(svy_h, b.svy, n8, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+       cudaMemcpyAsync(svz_h, b.svz, n8, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+       (!perm_h || cudaMemcpyAsync(perm_h, b.perm, n4, cudaMemcpyDeviceToHost, s) == cudaSuccess) &&
+       cudaMemcpyAsync(c->r_host_info, b.info, sizeof(dsmc_select_info_t), cudaMemcpyDeviceToHost, s) ==
+           cudaSuccess;
+  if (!ok) return dsmc::record(c, DSMC_ERR_CUDA, "step_host: device-to-host copy failed");
+  rc = dsmc_ctx_sync_status(c, stream);
+  if (n_pairs_h) *n_pairs_h = ((dsmc_select_info_t*)c->r_host_info)->n_pairs;
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,303 @@
+// Cell sort, cell moments, moment matching and the int32 exclusive scan.
+//
+// Sort (Sec. 2.6 (1)): histogram of cell ids -> exclusive scan -> cell_start;
+// scatter of input indices into their cell's slots (atomic cursor, order
+// inside a cell arbitrary) -> per-cell sort of the slot contents (restores
+// the input order, i.e. a stable counting sort) fused with the gather of
+// the velocities.  Moments and moment matching are warp-per-cell FP64
+// reductions with two passes.
+#include <climits>
+
+#include "internal.cuh"
+
+namespace dsmc {
+
+// ---------------------------------------------------------------- scan
+// Reduce-then-scan over blocks of kScanItems elements.
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = 16;
+constexpr int kScanItems = kScanThreads * kScanPer;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int* total) {
+  __shared__ int wsum[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int s = lane < kScanThreads / 32 ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < kScanThreads / 32) wsum[lane] = s;
+  }
+  __syncthreads();
+  const int before = (wid ? wsum[wid - 1] : 0) + x - v;
+  *total = wsum[kScanThreads / 32 - 1];
+  __syncthreads();
+  return before;
+}
+
+__global__ void k_scan_reduce(const int32_t* __restrict__ in, int64_t n, int32_t* bsum) {
+  const int64_t base = (int64_t)blockIdx.x * kScanItems;
+  int s = 0;
+  for (int q = 0; q < kScanPer; ++q) {
+    const int64_t i = base + (int64_t)q * kScanThreads + threadIdx.x;
+    if (i < n) s += in[i];
+  }
+  int total;
+  block_exclusive_scan(s, &total);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+__global__ void k_scan_blocks(int32_t* bsum, int64_t nb) {
+  int carry = 0;
+  for (int64_t b0 = 0; b0 < nb; b0 += kScanThreads) {
+    const int64_t i = b0 + threadIdx.x;
+    const int v = i < nb ? bsum[i] : 0;
+    int total;
+    const int ex = block_exclusive_scan(v, &total);
+    if (i < nb) bsum[i] = carry + ex;
+    carry += total;
+  }
+}
+
+__global__ void k_scan_apply(const int32_t* __restrict__ in, int64_t n, const int32_t* bsum,
+                             int32_t* __restrict__ out) {
+  const int64_t base = (int64_t)blockIdx.x * kScanItems + (int64_t)threadIdx.x * kScanPer;
+  int v[kScanPer];
+  int s = 0;
+#pragma unroll
+  for (int q = 0; q < kScanPer; ++q) {
+    v[q] = base + q < n ? in[base + q] : 0;
+    s += v[q];
+  }
+  int total;
+  int run = bsum[blockIdx.x] + block_exclusive_scan(s, &total);
+#pragma unroll
+  for (int q = 0; q < kScanPer; ++q) {
+    if (base + q < n) out[base + q] = run;
+    run += v[q];
+  }
+  if (base <= n - 1 && n - 1 < base + kScanPer) out[n] = run;  // total after the last element
+}
+
+size_t scan_ws(int64_t n) { return align256(sizeof(int32_t) * (size_t)((n + kScanItems - 1) / kScanItems + 1)); }
+
+int launch_scan(Ctx* c, const int32_t* in, int32_t* out, int64_t n, void* ws, cudaStream_t s) {
+  if (n <= 0) {
+    return cudaMemsetAsync(out, 0, sizeof(int32_t), s) == cudaSuccess ? 0 : DSMC_ERR_CUDA;
+  }
+  const int64_t nb = (n + kScanItems - 1) / kScanItems;
+  int32_t* bsum = (int32_t*)ws;
+  k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, bsum);
+  k_scan_blocks<<<1, kScanThreads, 0, s>>>(bsum, nb);
+  k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, bsum, out);
+  if (c) count_launches(c, 3);
+  return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------- sort
+__global__ void k_hist(const int32_t* __restrict__ cell_id, int32_t n, int32_t n_cells,
+                       int32_t* counts, int* status) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int32_t c = cell_id[i];
+    if ((uint32_t)c < (uint32_t)n_cells) atomicAdd(counts + c, 1);
+    else set_status(status, DSMC_ERR_ARG);
+  }
+}
+
+__global__ void k_scatter(const int32_t* __restrict__ cell_id, int32_t n, int32_t n_cells,
+                          const int32_t* __restrict__ cell_start, int32_t* fill,
+                          int32_t* __restrict__ slots) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int32_t c = cell_id[i];
+    if ((uint32_t)c >= (uint32_t)n_cells) continue;
+    slots[cell_start[c] + atomicAdd(fill + c, 1)] = i;
+  }
+}
+
+constexpr int kFixWarps = 8;
+constexpr int kFixCap = 1024;  // cells up to this size sort in shared memory
+
+// Warp per cell: order the cell's slot contents ascending (bitonic network in
+// shared memory; rank counting for larger cells), then gather velocities.
+__global__ void __launch_bounds__(kFixWarps * 32)
+k_fix_gather(int32_t n_cells, const int32_t* __restrict__ cell_start,
+             const int32_t* __restrict__ slots, int32_t* __restrict__ perm,
+             const double* __restrict__ vx, const double* __restrict__ vy,
+             const double* __restrict__ vz, double* __restrict__ svx, double* __restrict__ svy,
+             double* __restrict__ svz) {
+  __shared__ int buf_all[kFixWarps][kFixCap];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int* buf = buf_all[wid];
+  const int32_t warps = gridDim.x * kFixWarps;
+  for (int32_t k = blockIdx.x * kFixWarps + wid; k < n_cells; k += warps) {
+    const int32_t a = cell_start[k], N = cell_start[k + 1] - a;
+    if (N <= 0) continue;
+    if (N <= kFixCap) {
+      int P = 1;
+      while (P < N) P <<= 1;
+      for (int t = lane; t < P; t += 32) buf[t] = t < N ? slots[a + t] : INT_MAX;
+      __syncwarp();
+      for (int kk = 2; kk <= P; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+          for (int t = lane; t < (P >> 1); t += 32) {
+            const int i = (t / j) * 2 * j + (t % j);
+            const int ixj = i + j;
+            const int x = buf[i], y = buf[ixj];
+            const bool up = (i & kk) == 0;
+            if ((x > y) == up) { buf[i] = y; buf[ixj] = x; }
+          }
+          __syncwarp();
+        }
+      }
+      for (int t = lane; t < N; t += 32) perm[a + t] = buf[t];
+    } else {
+      // rank of each slot value among the cell's values (all distinct)
+      for (int t = lane; t < N; t += 32) {
+        const int x = slots[a + t];
+        int r = 0;
+        for (int q = 0; q < N; ++q) r += slots[a + q] < x;
+        perm[a + r] = x;
+      }
+    }
+    __syncwarp();
+    for (int t = lane; t < N; t += 32) {
+      const int32_t src = perm[a + t];
+      svx[a + t] = vx[src];
+      svy[a + t] = vy[src];
+      svz[a + t] = vz[src];
+    }
+  }
+}
+
+size_t sort_ws(int32_t n, int32_t n_cells) {
+  return align256(sizeof(int32_t) * (size_t)(n_cells > 0 ? n_cells : 1)) +
+         align256(sizeof(int32_t) * (size_t)(n > 0 ? n : 1)) + scan_ws(n_cells);
+}
+
+static unsigned grid_for(int64_t work, int per_block, int max_blocks) {
+  int64_t b = (work + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  if (b > max_blocks) b = max_blocks;
+  return (unsigned)b;
+}
+
+int launch_sort(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_id, const double* vx,
+                const double* vy, const double* vz, int32_t* perm, int32_t* cell_start,
+                double* svx, double* svy, double* svz, void* ws, size_t ws_bytes,
+                cudaStream_t s) {
+  if (ws_bytes < sort_ws(n, n_cells)) return record(c, DSMC_ERR_ARG, "sort: workspace too small");
+  char* p = (char*)ws;
+  int32_t* counts = (int32_t*)p;
+  p += align256(sizeof(int32_t) * (size_t)(n_cells > 0 ? n_cells : 1));
+  int32_t* slots = (int32_t*)p;
+  p += align256(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  void* sws = p;
+  const int sms = sm_count(c);
+  if (cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)n_cells, s) != cudaSuccess)
+    return DSMC_ERR_CUDA;
+  if (n > 0) { k_hist<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(cell_id, n, n_cells, counts, status_ptr(c)); count_launches(c, 1); }
+  int rc = launch_scan(c, counts, cell_start, n_cells, sws, s);
+  if (rc) return rc;
+  if (n == 0) return 0;
+  if (cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)n_cells, s) != cudaSuccess)
+    return DSMC_ERR_CUDA;
+  k_scatter<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(cell_id, n, n_cells, cell_start, counts, slots);
+  k_fix_gather<<<grid_for(n_cells, kFixWarps, sms * 4), kFixWarps * 32, 0, s>>>(
+      n_cells, cell_start, slots, perm, vx, vy, vz, svx, svy, svz);
+  count_launches(c, 2);
+  return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------- moments
+constexpr int kCellWarps = 8;
+
+__global__ void __launch_bounds__(kCellWarps * 32)
+k_moments(int32_t n_cells, const int32_t* __restrict__ cs, const double* __restrict__ vx,
+          const double* __restrict__ vy, const double* __restrict__ vz, double* __restrict__ mom,
+          int* status) {
+  const int lane = threadIdx.x & 31;
+  const int32_t warps = gridDim.x * kCellWarps;
+  for (int32_t k = blockIdx.x * kCellWarps + (threadIdx.x >> 5); k < n_cells; k += warps) {
+    const int32_t a = cs[k], b = cs[k + 1];
+    double sx = 0, sy = 0, sz = 0;
+    for (int32_t i = a + lane; i < b; i += 32) { sx += vx[i]; sy += vy[i]; sz += vz[i]; }
+    sx = warp_sum(sx); sy = warp_sum(sy); sz = warp_sum(sz);
+    const double n = (double)(b - a);
+    double th = 0;
+    if (b > a) {
+      const double ux = sx / n, uy = sy / n, uz = sz / n;
+      for (int32_t i = a + lane; i < b; i += 32) {
+        const double dx = vx[i] - ux, dy = vy[i] - uy, dz = vz[i] - uz;
+        th += dx * dx + dy * dy + dz * dz;
+      }
+      th = warp_sum(th);
+    }
+    if (lane == 0) {
+      if (!isfinite(sx + sy + sz + th)) set_status(status, DSMC_ERR_NONFINITE);
+      double* m = mom + 5 * (size_t)k;
+      m[0] = n; m[1] = sx; m[2] = sy; m[3] = sz; m[4] = th;
+    }
+  }
+}
+
+int launch_moments(Ctx* c, int32_t n_cells, const int32_t* cs, const double* vx,
+                   const double* vy, const double* vz, double* mom, cudaStream_t s) {
+  if (n_cells <= 0) return 0;
+  k_moments<<<grid_for(n_cells, kCellWarps, sm_count(c) * 8), kCellWarps * 32, 0, s>>>(
+      n_cells, cs, vx, vy, vz, mom, status_ptr(c));
+  count_launches(c, 1);
+  return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------- moment matching
+// Sec. 2.5 (centred): v <- u_pre + alpha (v - u_post), alpha = sqrt(Th_pre/Th_post).
+__global__ void __launch_bounds__(kCellWarps * 32)
+k_moment_match(int32_t n_cells, const int32_t* __restrict__ cs, const double* __restrict__ mom,
+               double* __restrict__ vx, double* __restrict__ vy, double* __restrict__ vz) {
+  const int lane = threadIdx.x & 31;
+  const int32_t warps = gridDim.x * kCellWarps;
+  for (int32_t k = blockIdx.x * kCellWarps + (threadIdx.x >> 5); k < n_cells; k += warps) {
+    const int32_t a = cs[k], b = cs[k + 1];
+    if (b <= a) continue;
+    double sx = 0, sy = 0, sz = 0;
+    for (int32_t i = a + lane; i < b; i += 32) { sx += vx[i]; sy += vy[i]; sz += vz[i]; }
+    sx = warp_sum(sx); sy = warp_sum(sy); sz = warp_sum(sz);
+    const double n = (double)(b - a);
+    const double ux = sx / n, uy = sy / n, uz = sz / n;
+    double th = 0;
+    for (int32_t i = a + lane; i < b; i += 32) {
+      const double dx = vx[i] - ux, dy = vy[i] - uy, dz = vz[i] - uz;
+      th += dx * dx + dy * dy + dz * dz;
+    }
+    th = warp_sum(th);
+    const double* m = mom + 5 * (size_t)k;
+    const double px = m[1] / n, py = m[2] / n, pz = m[3] / n;
+    const double alpha = (b - a >= 2 && th > 0.0) ? sqrt(m[4] / th) : 1.0;
+    for (int32_t i = a + lane; i < b; i += 32) {
+      vx[i] = px + alpha * (vx[i] - ux);
+      vy[i] = py + alpha * (vy[i] - uy);
+      vz[i] = pz + alpha * (vz[i] - uz);
+    }
+  }
+}
+
+int launch_moment_match(Ctx* c, int32_t n_cells, const int32_t* cs, const double* mom,
+                        double* vx, double* vy, double* vz, cudaStream_t s) {
+  if (n_cells <= 0) return 0;
+  k_moment_match<<<grid_for(n_cells, kCellWarps, sm_count(c) * 8), kCellWarps * 32, 0, s>>>(
+      n_cells, cs, mom, vx, vy, vz);
+  count_launches(c, 1);
+  return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
+}
+
+}  // namespace dsmc

@@ -1,0 +1,176 @@
+// Internal device helpers and launcher declarations of the DSMC library.
+// Target: sm_103a (GB300).  Everything here is the library's own code.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dsmc.h"
+
+#define DSMC_KB 1.380649e-23
+#define DSMC_PI 3.14159265358979323846
+
+namespace dsmc {
+
+// Philox tags (counter word 3): 1 NTC rounding, 2 candidate, 3 isotropic
+// direction, 4 Jager b/eps, 5 latent noise, 6 harvest.
+enum : uint32_t { TAG_NTC = 1, TAG_CAND = 2, TAG_ISO = 3, TAG_JAGER = 4, TAG_NOISE = 5 };
+
+// ---------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplies with the Weyl-sequence key schedule.
+struct u32x4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ u32x4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                        uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+  }
+  return {c0, c1, c2, c3};
+}
+
+// counter = (idx, cell, step_lo, tag | sub<<8 | step_hi<<16), key = seed
+__device__ __forceinline__ u32x4 draw(uint64_t seed, uint32_t idx, uint32_t cell, uint64_t step,
+                                      uint32_t tag, uint32_t sub = 0) {
+  return philox(idx, cell, (uint32_t)step, tag | (sub << 8) | ((uint32_t)(step >> 32) << 16),
+                (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+// 53-bit uniform in [0,1): exact in double
+__device__ __forceinline__ double u53(uint32_t a, uint32_t b) {
+  const uint64_t x = ((((uint64_t)a) << 32) | b) >> 11;
+  return (double)x * (1.0 / 9007199254740992.0);
+}
+
+// uniform integer in [0, n): high word of w*n
+__device__ __forceinline__ uint32_t mulhi_n(uint32_t w, uint32_t n) { return __umulhi(w, n); }
+
+// ---------------------------------------------------------------- warp helpers
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ int warp_sum_i(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------- status
+// First error wins; later ones are dropped.
+__device__ __forceinline__ void set_status(int* status, int code) {
+  atomicCAS(status, 0, code);
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Device-wide barrier for a cooperative (co-resident) grid.  `bar[0]` counts
+// arrivals, `bar[1]` is the generation.  Every wait is bounded: after
+// `limit_ns` the block records DSMC_ERR_TIMEOUT, raises the abort flag
+// bar[2] and returns false; callers then leave the kernel.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* status, uint64_t limit_ns) {
+  __syncthreads();
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* vgen = bar + 1;
+    volatile unsigned* vabort = bar + 2;
+    const unsigned gen = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    if (arrived == gridDim.x - 1) {
+      bar[0] = 0;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const uint64_t t0 = globaltimer_ns();
+      while (*vgen == gen) {
+        if (*vabort) { ok = 0; break; }
+        if (globaltimer_ns() - t0 > limit_ns) {
+          set_status(status, DSMC_ERR_TIMEOUT);
+          atomicExch(bar + 2, 1u);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+constexpr uint64_t kBarrierLimitNs = 2000000000ull;  // 2 s
+
+// ---------------------------------------------------------------- host side
+struct Ctx;
+int record(Ctx* c, int code, const char* msg);  // sets last error text, returns code
+int* status_ptr(Ctx* c);
+unsigned* barrier_ptr(Ctx* c);  // 4 words of device memory per barrier slot
+int sm_count(Ctx* c);
+void count_launches(Ctx* c, int k);  // kernels launched by this context
+
+// launchers (return 0 or a DSMC_ERR_* code)
+int launch_sort(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_id, const double* vx,
+                const double* vy, const double* vz, int32_t* perm, int32_t* cell_start,
+                double* svx, double* svy, double* svz, void* ws, size_t ws_bytes,
+                cudaStream_t s);
+size_t sort_ws(int32_t n, int32_t n_cells);
+int launch_moments(Ctx* c, int32_t n_cells, const int32_t* cs, const double* vx,
+                   const double* vy, const double* vz, double* mom, cudaStream_t s);
+int launch_moment_match(Ctx* c, int32_t n_cells, const int32_t* cs, const double* mom,
+                        double* vx, double* vy, double* vz, cudaStream_t s);
+size_t select_ws(int32_t n, int32_t n_cells, int64_t capacity);
+int launch_select(Ctx* c, const dsmc_gas_t& gas, int32_t n, int32_t n_cells, const int32_t* cs,
+                  const double* vx, const double* vy, const double* vz, double* sgmax,
+                  uint64_t step, int64_t capacity, int32_t* pairs, int32_t* round_offsets,
+                  dsmc_select_info_t* info, void* ws, size_t ws_bytes, cudaStream_t s);
+int launch_sgmax_init(Ctx* c, const dsmc_gas_t& gas, int32_t n_cells, const double* T,
+                      double factor, double* sgmax, cudaStream_t s);
+int launch_collide_vhs(Ctx* c, const dsmc_gas_t& gas, uint64_t step, const int32_t* pairs,
+                       const int32_t* ro, const dsmc_select_info_t* info, double* vx,
+                       double* vy, double* vz, cudaStream_t s);
+int launch_jager_chi(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& pot, int n_nodes,
+                     int64_t n, const float* b, const float* g, float* chi, cudaStream_t s);
+int launch_collide_jager(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& pot,
+                         int n_nodes, uint64_t step, const int32_t* pairs, const int32_t* ro,
+                         const dsmc_select_info_t* info, double* vx, double* vy, double* vz,
+                         float* chi_out, cudaStream_t s);
+int launch_harvest_jager(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& pot,
+                         int n_nodes, int64_t n, const double* vi, const double* vj,
+                         const double* b, const double* eps, double* vio, double* vjo,
+                         cudaStream_t s);
+int launch_collide_neural(Ctx* c, const dsmc_gas_t& gas, const dsmc_mlp_t& mlp,
+                          const uint16_t* w, const float* bias, uint64_t step,
+                          const double* mom, const int32_t* pairs, const int32_t* ro,
+                          const dsmc_select_info_t* info, double* vx, double* vy, double* vz,
+                          cudaStream_t s);
+
+int launch_mlp_forward(Ctx* c, const dsmc_mlp_t& mlp, const uint16_t* w, const float* bias,
+                       int64_t n, const float* x, float* y, cudaStream_t s);
+int launch_tc_selftest(Ctx* c, int N, int K, const uint16_t* A, const uint16_t* B, float* D,
+                       cudaStream_t s);
+int cooperative_blocks(Ctx* c, const void* kernel, int threads, size_t smem);
+
+// exclusive scan of int32 counts -> offsets[n+1] (offsets[n] = total)
+size_t scan_ws(int64_t n);
+int launch_scan(Ctx* c, const int32_t* in, int32_t* out, int64_t n, void* ws, cudaStream_t s);
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace dsmc

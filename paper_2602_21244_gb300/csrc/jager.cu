@@ -1,0 +1,455 @@
+// Deflection angle chi(b, E) of the classical scattering integral for the
+// Jager potential form (Sec. 3.4.1-3.4.4) and the pair updates built on it.
+//
+//   chi = pi - 2 b int_{r_min}^inf dr / (r^2 sqrt(F(r))),  F = 1 - b^2/r^2 - V(r)/E,
+//   r_min = the largest root of F.
+//
+// Per pair (one thread):
+//  1. bracket: scan F downward from max(b, sigma0) (sigma0: zero of V, above
+//     which F > 0 for every b) on a geometric grid, fine where orbiting can
+//     create several roots (E below 1.5 well depths), coarse otherwise;
+//  2. FP32 safeguarded Newton inside the bracket, then FP64 Newton steps
+//     (the turning-point refinement);
+//  3. u = r_min/r, u = 1 - s^2 turns the integral into
+//       I = int_0^1 2 s ds / sqrt(G(s)),  G = F0 + (b/r_min)^2 s^2 (1+u) - dV/E,
+//     smooth in s; an n-point Gauss-Legendre rule in FP32 on the difference
+//     from the free-particle integrand (whose integral is known exactly),
+//     so chi = -2 (b/r_min) int 2s (1/sqrt(G) - 1/sqrt(G0)) ds.  dV = V(r) - V(r_min)
+//     is assembled from per-term differences written with exact identities
+//     (1 - u^k = s^2 (1 + u + ... + u^(k-1)), expm1) so that it keeps FP32
+//     relative accuracy as r -> r_min.
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace dsmc {
+
+constexpr int kMaxNodes = 128;
+
+struct PotDev {
+  int kind;
+  int n_nodes;
+  // Jager form (FP64 copies for the refinement, FP32 for the rest)
+  double A, a1, a2, am1, am2, beta, C[6], rc, At, at;
+  float fA, fa1, fa2, fam1, fam2, fbeta, fC[6], frc, fAt, fat;
+  double Dd[17];      // FP64 copy of D
+  float D[17];        // P(r) = sum_p D_p r^-p,  e^{-beta r} P(r) = sum_n C_2n r^-2n e^{-x} S_2n(x)
+  float sigma0;       // zero crossing of V (F > 0 above max(b, sigma0))
+  float orbit_E;      // below this energy use the fine bracket scan
+  double d_hs, kappa, p;
+  float fkappa, fp;
+  float mass_over_4k; // E/k_B = mass g^2 / (4 k_B)
+  float s_node[kMaxNodes], w_node[kMaxNodes];
+};
+
+// ---------------------------------------------------------------- FP64 potential
+// Direct evaluation of V and V' (FP64 has the digits to spare).
+__host__ __device__ inline double V64(const PotDev& P, double r, double* dV) {
+  if (P.kind == 2) {
+    const double v = P.kappa * pow(r, -P.p);
+    *dV = -P.p * v / r;
+    return v;
+  }
+  if (r < P.rc) {
+    const double e = P.At * exp(-P.at * r) / r;
+    *dV = -e * (P.at + 1.0 / r);
+    return e;
+  }
+  const double ir = 1.0 / r;
+  const double rep = P.A * exp(P.a1 * r + P.a2 * r * r + P.am1 * ir + P.am2 * ir * ir);
+  const double drep = rep * (P.a1 + 2.0 * P.a2 * r - P.am1 * ir * ir - 2.0 * P.am2 * ir * ir * ir);
+  const double x = P.beta * r, ex = exp(-x);
+  double term = 1.0, S = 1.0, disp = 0.0, ddisp = 0.0;
+  double ir2n = ir * ir * ir * ir * ir * ir;  // r^-6
+  int k = 0;
+  for (int n = 3; n <= 8; ++n) {
+    for (; k < 2 * n;) { ++k; term *= x / k; S += term; }
+    const double f = 1.0 - ex * S;    // f_2n(x)
+    const double fp = ex * term;      // f_2n'(x) = e^-x x^2n/(2n)!
+    disp += P.C[n - 3] * f * ir2n;
+    ddisp += P.C[n - 3] * (P.beta * fp * ir2n - 2.0 * n * f * ir2n * ir);
+    ir2n *= ir * ir;
+  }
+  *dV = drep - ddisp;
+  return rep - disp;
+}
+
+// ---------------------------------------------------------------- FP32 potential
+// V = A e^{poly} - sum_n C_2n r^-2n + e^{-beta r} sum_p D_p r^-p  (r >= rc)
+__device__ __forceinline__ float V32(const PotDev& P, float r, float* dV) {
+  if (P.kind == 1) { *dV = 0.f; return 0.f; }
+  if (P.kind == 2) {
+    const float v = P.fkappa * __powf(r, -P.fp);
+    *dV = -P.fp * v / r;
+    return v;
+  }
+  const float ir = 1.f / r;
+  if (r < P.frc) {
+    const float e = P.fAt * __expf(-P.fat * r) * ir;
+    *dV = -e * (P.fat + ir);
+    return e;
+  }
+  const float rep = P.fA * __expf(P.fa1 * r + P.fa2 * r * r + P.fam1 * ir + P.fam2 * ir * ir);
+  const float drep = rep * (P.fa1 + 2.f * P.fa2 * r - P.fam1 * ir * ir - 2.f * P.fam2 * ir * ir * ir);
+  const float ir2 = ir * ir;
+  float q = 0.f, dq = 0.f, pw = ir2 * ir2 * ir2;
+#pragma unroll
+  for (int n = 0; n < 6; ++n) {
+    q += P.fC[n] * pw;
+    dq -= (6 + 2 * n) * P.fC[n] * pw * ir;
+    pw *= ir2;
+  }
+  float Pr = P.D[16], dPr = 0.f;
+#pragma unroll
+  for (int p = 15; p >= 0; --p) {  // Horner in 1/r
+    dPr = dPr * ir + (p + 1) * P.D[p + 1];
+    Pr = Pr * ir + P.D[p];
+  }
+  dPr = -dPr * ir2;
+  const float eb = __expf(-P.fbeta * r);
+  *dV = drep - dq + eb * (dPr - P.fbeta * Pr);
+  return rep - q + eb * Pr;
+}
+
+__device__ __forceinline__ float F32(const PotDev& P, float b2, float E, float r, float* dF) {
+  float dV;
+  const float V = V32(P, r, &dV);
+  const float ir2 = 1.f / (r * r);
+  *dF = 2.f * b2 * ir2 / r - dV / E;
+  return 1.f - b2 * ir2 - V / E;
+}
+
+// ---------------------------------------------------------------- turning point
+// Returns r_min in FP64: FP32 bracket + safeguarded Newton, then FP64 Newton.
+__device__ double rmin_device(const PotDev& P, float b, float E) {
+  if (P.kind == 1) return (double)fmaxf(b, (float)P.d_hs);
+  const float b2 = b * b;
+  float dF;
+  float r_hi;
+  if (P.kind == 0) r_hi = fmaxf(b, P.sigma0) * 1.000001f;
+  else r_hi = fmaxf(b, __powf(P.fkappa / E, 1.f / P.fp)) * 2.f;
+  const float q = (P.kind == 0 && E < P.orbit_E) ? 0.995f : 0.9f;
+  float r_lo = r_hi;
+  bool found = false;
+  for (int t = 0; t < 4000; ++t) {
+    r_lo = r_hi * q;
+    if (F32(P, b2, E, r_lo, &dF) < 0.f) { found = true; break; }
+    r_hi = r_lo;
+    if (r_hi < 1e-3f) break;
+  }
+  if (!found) return (double)r_hi;
+  // safeguarded Newton in [r_lo, r_hi], F(r_lo) < 0 <= F(r_hi).  Convergence
+  // is tested before the bisection fallback: a step below FP32 resolution
+  // ends the iteration even when it lands on a bracket end.
+  float r = r_hi;
+  for (int it = 0; it < 24; ++it) {
+    const float f = F32(P, b2, E, r, &dF);
+    if (f == 0.f) break;
+    if (f < 0.f) r_lo = r; else r_hi = r;
+    float rn = r - f / dF;
+    const bool inside = rn >= r_lo && rn <= r_hi;
+    if (fabsf(rn - r) <= 4e-7f * r) { if (inside) r = rn; break; }
+    r = inside ? rn : 0.5f * (r_lo + r_hi);
+  }
+  // FP64 Newton refinement of the turning point, kept inside the FP32
+  // bracket widened by 1e-4 (FP32 rounding can misplace its ends slightly)
+  double rd = r;
+  const double lo = (double)r_lo * (1.0 - 1e-4), hi = (double)r_hi * (1.0 + 1e-4);
+  const double bd2 = (double)b * b, Ed = E;
+  for (int it = 0; it < 4; ++it) {
+    double dV;
+    const double V = V64(P, rd, &dV);
+    const double f = 1.0 - bd2 / (rd * rd) - V / Ed;
+    const double df = 2.0 * bd2 / (rd * rd * rd) - dV / Ed;
+    const double rn = rd - f / df;
+    if (!(rn >= lo && rn <= hi)) break;
+    const bool done = fabs(rn - rd) <= 1e-15 * rd;
+    rd = rn;
+    if (done) break;
+  }
+  return rd;
+}
+
+// ---------------------------------------------------------------- chi
+__device__ float chi_device(const PotDev& P, float b, float E) {
+  if (!(b > 0.f)) return (float)DSMC_PI;
+  const double rd = rmin_device(P, b, E);
+  const float r0 = (float)rd;
+  const float bt = (float)((double)b / rd);
+  const float bt2 = bt * bt;
+  const float iE = 1.f / E;
+  float F0 = 0.f;
+  if (P.kind == 1) F0 = 1.f - bt2;
+  // per-pair coefficients about the FP64 turning point (Jager form), so that
+  // the integrand's F(r_min) = 0 holds to FP64 rather than to FP32 rounding
+  float d[17], qn[6], Rep0 = 0.f, e0 = 0.f, P0 = 0.f, Vc0 = 0.f, powk = 0.f;
+  const bool core = P.kind == 0 && r0 < P.frc;
+  if (P.kind == 0 && !core) {
+    const double ir = 1.0 / rd, ir2 = ir * ir;
+    double pw = 1.0, p0 = 0.0;
+#pragma unroll
+    for (int p = 0; p <= 16; ++p) { const double t = P.Dd[p] * pw; d[p] = (float)t; p0 += t; pw *= ir; }
+    P0 = (float)p0;
+    pw = ir2 * ir2 * ir2;
+#pragma unroll
+    for (int n = 0; n < 6; ++n) { qn[n] = (float)(P.C[n] * pw); pw *= ir2; }
+    Rep0 = (float)(P.A * exp(P.a1 * rd + P.a2 * rd * rd + P.am1 * ir + P.am2 * ir2));
+    e0 = (float)exp(-P.beta * rd);
+  } else if (P.kind == 2) {
+    Vc0 = (float)(P.kappa * pow(rd, -P.p));
+    powk = P.fp;
+  }
+  double V0d = 0.0;
+  if (core) { double dd; V0d = V64(P, rd, &dd); }
+  float I = 0.f;
+  for (int q = 0; q < P.n_nodes; ++q) {
+    const float s = P.s_node[q];
+    const float w = s * s;          // 1 - u, exact
+    const float u = 1.f - w;
+    const float dr = r0 * w / u;    // r - r0
+    float dV = 0.f;
+    if (P.kind == 0 && !core) {
+      const float r = r0 + dr;
+      // repulsion: Rep0 * expm1(poly(r) - poly(r0))
+      const float dpoly = dr * (P.fa1 + P.fa2 * (r + r0) - P.fam1 / (r * r0) -
+                                P.fam2 * (r + r0) / (r * r * r0 * r0));
+      const float drep = Rep0 * expm1f(dpoly);
+      // G_k = 1 + u + ... + u^(k-1), so r^-k - r0^-k = -r0^-k w G_k
+      float Gk = 0.f, uk = 1.f, dQ = 0.f, dP = 0.f;
+#pragma unroll
+      for (int k = 1; k <= 16; ++k) {
+        Gk += uk;
+        uk *= u;
+        dP += d[k] * Gk;
+        if ((k & 1) == 0 && k >= 6) dQ += qn[(k - 6) >> 1] * Gk;
+      }
+      dQ *= -w;                     // sum_n C (r^-2n - r0^-2n)
+      dP *= -w;                     // P(r) - P(r0)
+      const float dh = e0 * (expm1f(-P.fbeta * dr) * (P0 + dP) + dP);
+      dV = drep - dQ + dh;
+    } else if (P.kind == 2) {
+      dV = Vc0 * expm1f(powk * log1pf(-w));  // kappa (r^-p - r0^-p)
+    } else if (core) {
+      double dd;
+      dV = (float)(V64(P, rd + (double)dr, &dd) - V0d);
+    }
+    // G = G0 - dG with G0 = (b/r_min)^2 s^2 (1+u) the free-particle integrand;
+    // integrate 1/sqrt(G) - 1/sqrt(G0) (its integral of G0 alone is
+    // pi/(2 b/r_min) exactly), written as dG/(sqrt(G G0)(sqrt G + sqrt G0))
+    // so that weak deflections keep their relative accuracy.
+    const float G0 = bt2 * w * (1.f + u);
+    const float dG = dV * iE - F0;
+    const float G = fmaxf(G0 - dG, 1e-30f);
+    const float rG = rsqrtf(G), rG0 = rsqrtf(G0);
+    I += P.w_node[q] * 2.f * s * (dG * rG * rG0 / (G * rG + G0 * rG0));
+  }
+  return -2.f * bt * I;
+}
+
+// ---------------------------------------------------------------- host set-up
+static void gauss_legendre01(int n, double* x, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double z = cos(DSMC_PI * (i + 0.75) / (n + 0.5)), pp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p1 = 1.0, p2 = 0.0;
+      for (int k = 1; k <= n; ++k) {
+        const double p3 = p2;
+        p2 = p1;
+        p1 = ((2.0 * k - 1.0) * z * p2 - (k - 1.0) * p3) / k;
+      }
+      pp = n * (z * p1 - p2) / (z * z - 1.0);
+      const double dz = p1 / pp;
+      z -= dz;
+      if (fabs(dz) < 1e-15) break;
+    }
+    x[i] = 0.5 * (1.0 - z);
+    w[i] = 1.0 / ((1.0 - z * z) * pp * pp);
+  }
+}
+
+static PotDev make_pot(const dsmc_gas_t& gas, const dsmc_potential_t& p, int n_nodes) {
+  PotDev P = {};
+  P.kind = p.kind;
+  P.n_nodes = n_nodes;
+  P.A = p.A; P.a1 = p.a1; P.a2 = p.a2; P.am1 = p.am1; P.am2 = p.am2; P.beta = p.beta;
+  for (int q = 0; q < 6; ++q) { P.C[q] = p.C[q]; P.fC[q] = (float)p.C[q]; }
+  P.rc = 0.4 * p.R_eps; P.At = p.At; P.at = p.at;
+  P.fA = (float)p.A; P.fa1 = (float)p.a1; P.fa2 = (float)p.a2; P.fam1 = (float)p.am1;
+  P.fam2 = (float)p.am2; P.fbeta = (float)p.beta; P.frc = (float)P.rc; P.fAt = (float)p.At;
+  P.fat = (float)p.at;
+  P.d_hs = p.d_hs; P.kappa = p.kappa; P.p = p.p; P.fkappa = (float)p.kappa; P.fp = (float)p.p;
+  P.mass_over_4k = (float)(gas.mass / (4.0 * DSMC_KB));
+  // D_p = sum_{n: 2n >= p} C_2n beta^(2n-p) / (2n-p)!
+  for (int pp = 0; pp <= 16; ++pp) {
+    double s = 0.0;
+    for (int n = 3; n <= 8; ++n) {
+      const int j = 2 * n - pp;
+      if (j < 0) continue;
+      double t = 1.0;
+      for (int i = 1; i <= j; ++i) t *= p.beta / i;
+      s += p.C[n - 3] * t;
+    }
+    P.D[pp] = (float)s;
+    P.Dd[pp] = s;
+  }
+  if (p.kind == 0) {
+    // sigma0: outermost zero of V (bisection on a sign change found inward from 4 R_eps)
+    double dv, hi = 4.0 * p.R_eps, lo = hi;
+    while (lo > 0.2 && V64(P, lo, &dv) < 0.0) lo *= 0.98;
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (V64(P, mid, &dv) < 0.0) hi = mid; else lo = mid;
+    }
+    P.sigma0 = (float)hi;
+    double vmin = 0.0;
+    for (double r = P.sigma0; r < 6.0 * p.R_eps; r *= 1.001) vmin = fmin(vmin, V64(P, r, &dv));
+    P.orbit_E = (float)(1.5 * -vmin);
+  }
+  std::vector<double> x(n_nodes), w(n_nodes);
+  gauss_legendre01(n_nodes, x.data(), w.data());
+  for (int i = 0; i < n_nodes; ++i) { P.s_node[i] = (float)x[i]; P.w_node[i] = (float)w[i]; }
+  return P;
+}
+
+// ---------------------------------------------------------------- kernels
+__global__ void __launch_bounds__(128) k_jager_chi(PotDev P, int64_t n, const float* __restrict__ b,
+                                                   const float* __restrict__ g, float* __restrict__ chi) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const float gg = g[q];
+    const float E = P.mass_over_4k * gg * gg;
+    chi[q] = gg > 0.f ? chi_device(P, b[q], E) : 0.f;
+  }
+}
+
+// Deflect v_r by chi with azimuth eps (Bird 1994, Eq. 2.22), FP64.
+__device__ __forceinline__ void deflect(double u, double v, double w, double cc, double sc,
+                                        double ce, double se, double* o) {
+  const double g = sqrt(u * u + v * v + w * w);
+  const double q = sqrt(v * v + w * w);
+  double cx, cy, cz, ax, ay, az;
+  if (q > 1e-300 && q > 1e-12 * g) {
+    cx = 0.0; cy = w / q; cz = -v / q;
+    ax = q / g; ay = -u * v / (g * q); az = -u * w / (g * q);
+  } else {
+    cx = 0.0; cy = 1.0; cz = 0.0;
+    ax = 0.0; ay = 0.0; az = u >= 0.0 ? -1.0 : 1.0;
+  }
+  o[0] = cc * u + g * sc * (ce * cx + se * ax);
+  o[1] = cc * v + g * sc * (ce * cy + se * ay);
+  o[2] = cc * w + g * sc * (ce * cz + se * az);
+}
+
+struct JagerArgs {
+  uint64_t seed, step;
+  double bmax_A;
+  const int4* pairs;
+  const int32_t* ro;
+  const dsmc_select_info_t* info;
+  double *vx, *vy, *vz;
+  float* chi_out;
+  unsigned* bar;
+  int* status;
+};
+
+__global__ void __launch_bounds__(128) k_collide_jager(PotDev P, JagerArgs a) {
+  const int R = a.info->n_rounds;
+  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+  for (int r = 0; r < R; ++r) {
+    const int32_t beg = a.ro[r], end = a.ro[r + 1];
+    for (int64_t p = beg + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < end; p += nthr) {
+      const int4 q = a.pairs[p];
+      const double xi = __ldcg(a.vx + q.x), yi = __ldcg(a.vy + q.x), zi = __ldcg(a.vz + q.x);
+      const double xj = __ldcg(a.vx + q.y), yj = __ldcg(a.vy + q.y), zj = __ldcg(a.vz + q.y);
+      const double ux = xi - xj, uy = yi - yj, uz = zi - zj;
+      const double g = sqrt(ux * ux + uy * uy + uz * uz);
+      const u32x4 w = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_JAGER);
+      const float b = (float)(a.bmax_A * sqrt(u53(w.x, w.y)));
+      const float E = P.mass_over_4k * (float)(g * g);
+      const float chi = g > 0.0 ? chi_device(P, b, E) : 0.f;
+      if (a.chi_out) a.chi_out[p] = chi;
+      double cc, sc, ce, se;
+      sincos((double)chi, &sc, &cc);
+      sincos(2.0 * DSMC_PI * u53(w.z, w.w), &se, &ce);
+      double o[3] = {0.0, 0.0, 0.0};
+      if (g > 0.0) deflect(ux, uy, uz, cc, sc, ce, se, o);
+      const double cx = 0.5 * (xi + xj), cy = 0.5 * (yi + yj), cz = 0.5 * (zi + zj);
+      __stcg(a.vx + q.x, cx + 0.5 * o[0]); __stcg(a.vy + q.x, cy + 0.5 * o[1]); __stcg(a.vz + q.x, cz + 0.5 * o[2]);
+      __stcg(a.vx + q.y, cx - 0.5 * o[0]); __stcg(a.vy + q.y, cy - 0.5 * o[1]); __stcg(a.vz + q.y, cz - 0.5 * o[2]);
+    }
+    if (r + 1 < R && !grid_barrier(a.bar, a.status, kBarrierLimitNs)) return;
+  }
+}
+
+__global__ void __launch_bounds__(128) k_harvest(PotDev P, int64_t n, const double* __restrict__ vi,
+                                                 const double* __restrict__ vj, const double* __restrict__ b,
+                                                 const double* __restrict__ eps, double* __restrict__ vio,
+                                                 double* __restrict__ vjo) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const double ux = vi[3 * p] - vj[3 * p], uy = vi[3 * p + 1] - vj[3 * p + 1], uz = vi[3 * p + 2] - vj[3 * p + 2];
+    const double g = sqrt(ux * ux + uy * uy + uz * uz);
+    const float E = P.mass_over_4k * (float)(g * g);
+    const float chi = g > 0.0 ? chi_device(P, (float)b[p], E) : 0.f;
+    double cc, sc, ce, se;
+    sincos((double)chi, &sc, &cc);
+    sincos(eps[p], &se, &ce);
+    double o[3] = {0.0, 0.0, 0.0};
+    if (g > 0.0) deflect(ux, uy, uz, cc, sc, ce, se, o);
+    for (int c = 0; c < 3; ++c) {
+      const double cm = 0.5 * (vi[3 * p + c] + vj[3 * p + c]);
+      vio[3 * p + c] = cm + 0.5 * o[c];
+      vjo[3 * p + c] = cm - 0.5 * o[c];
+    }
+  }
+}
+
+int cooperative_blocks(Ctx* c, const void* kernel, int threads, size_t smem);
+
+static unsigned blocks_n(int64_t n, int threads, int cap) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (unsigned)b;
+}
+
+int launch_jager_chi(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& pot, int n_nodes,
+                     int64_t n, const float* b, const float* g, float* chi, cudaStream_t s) {
+  if (n == 0) return 0;
+  const PotDev P = make_pot(gas, pot, n_nodes);
+  k_jager_chi<<<blocks_n(n, 128, sm_count(c) * 64), 128, 0, s>>>(P, n, b, g, chi);
+  count_launches(c, 1);
+  return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
+}
+
+int launch_collide_jager(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& pot,
+                         int n_nodes, uint64_t step, const int32_t* pairs, const int32_t* ro,
+                         const dsmc_select_info_t* info, double* vx, double* vy, double* vz,
+                         float* chi_out, cudaStream_t s) {
+  static int blocks = 0;
+  if (!blocks) blocks = cooperative_blocks(c, (const void*)k_collide_jager, 128, 0);
+  if (!blocks) return record(c, DSMC_ERR_CUDA, "collide_jager: occupancy query failed");
+  PotDev P = make_pot(gas, pot, n_nodes);
+  JagerArgs a{gas.seed, step, gas.b_max * 1e10, (const int4*)pairs, ro, info, vx, vy, vz,
+              chi_out, barrier_ptr(c), status_ptr(c)};
+  if (cudaMemsetAsync(a.bar, 0, 4 * sizeof(unsigned), s) != cudaSuccess) return DSMC_ERR_CUDA;
+  void* args[] = {&P, &a};
+  if (cudaLaunchCooperativeKernel((const void*)k_collide_jager, dim3(blocks), dim3(128), args, 0, s) !=
+      cudaSuccess)
+    return record(c, DSMC_ERR_CUDA, "collide_jager: cooperative launch failed");
+  count_launches(c, 1);
+  return 0;
+}
+
+int launch_harvest_jager(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& pot,
+                         int n_nodes, int64_t n, const double* vi, const double* vj,
+                         const double* b, const double* eps, double* vio, double* vjo,
+                         cudaStream_t s) {
+  if (n == 0) return 0;
+  const PotDev P = make_pot(gas, pot, n_nodes);
+  k_harvest<<<blocks_n(n, 128, sm_count(c) * 64), 128, 0, s>>>(P, n, vi, vj, b, eps, vio, vjo);
+  count_launches(c, 1);
+  return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
+}
+
+}  // namespace dsmc

@@ -1,0 +1,434 @@
+// Neural collision operator (Sec. 2.2-2.3) on the tcgen05 tensor cores.
+//
+// A CTA of 128 threads owns a tile of 128 pairs: thread t builds row t of the
+// bf16 input tile X in shared memory, one elected thread issues the layer's
+// tcgen05.mma chain (K-major operands, FP32 accumulator in TMEM), all four
+// warps read their 32 TMEM lanes back (tcgen05.ld), add the bias, apply the
+// activation, round to bf16 and write the next layer's A operand to shared
+// memory.  The weights of all layers stay in shared memory for the life of
+// the CTA.  After the last layer thread t projects y onto the energy shell
+// and applies the centre-of-mass update of its pair in FP64.
+//
+// The collide kernel is persistent and cooperative: it walks the rounds of
+// the step (pairs of one round are disjoint) with a bounded grid barrier in
+// between, as the other collide kernels do.
+#include <cstdio>
+
+#include "internal.cuh"
+#include "tc.cuh"
+
+namespace dsmc {
+
+constexpr int kTileM = 128;
+constexpr int kWidth = 128;
+constexpr int kKin = 32;         // input as two bf16 terms: [hi (16) | lo (16)]
+constexpr int kNout = 16;        // padded output width
+constexpr int kMaxHidden = 4;
+
+// dynamic shared memory layout (bytes)
+struct MlpLayout {
+  uint32_t w_out, w_in, w_sq, x, h, bias, mbar, tptr, flag, total;
+};
+
+__host__ __device__ inline MlpLayout mlp_layout(int n_hidden) {
+  MlpLayout L;
+  L.w_out = 0;                                        // [16 x 128]
+  L.w_in = L.w_out + kNout * kWidth * 2;              // [128 x 32] = [W1 | W1]
+  L.w_sq = L.w_in + kWidth * kKin * 2;                // (n_hidden-1) x [128 x 128]
+  L.x = L.w_sq + (uint32_t)(n_hidden - 1) * kWidth * kWidth * 2;  // [128 x 16]
+  L.h = L.x + kTileM * kKin * 2;                      // [128 x 128]
+  L.bias = L.h + kTileM * kWidth * 2;                 // floats: n_hidden*128 + 16
+  L.mbar = L.bias + (uint32_t)(n_hidden * kWidth + kNout) * 4;
+  L.mbar = (L.mbar + 15u) & ~15u;
+  L.tptr = L.mbar + 8;
+  L.flag = L.tptr + 4;
+  L.total = L.flag + 4 + 2048;  // slack after the last operand tile
+  return L;
+}
+
+struct MlpShape {
+  int d_in, n_hidden, act;
+};
+
+// Copy the caller's row-major [out x in] bf16 layers into K-major core-matrix
+// tiles (zero padded) and the biases into shared memory.
+__device__ void load_weights(char* smem, const MlpLayout& L, const MlpShape& sh,
+                             const uint16_t* __restrict__ w, const float* __restrict__ bias) {
+  const int t = threadIdx.x, nt = blockDim.x;
+  uint32_t* z = (uint32_t*)(smem + L.w_out);
+  for (int q = t; q < (kNout * kWidth * 2 + kWidth * kKin * 2) / 4; q += nt) z[q] = 0u;
+  __syncthreads();
+  // layer 0: [128 x d_in], stored twice (columns k and 16 + k) so that the
+  // two bf16 terms of the input share the weights
+  for (int e = t; e < kWidth * sh.d_in; e += nt) {
+    const int n = e / sh.d_in, k = e % sh.d_in;
+    *(uint16_t*)(smem + L.w_in + tc::kmajor_offset(n, k, kKin)) = w[e];
+    *(uint16_t*)(smem + L.w_in + tc::kmajor_offset(n, 16 + k, kKin)) = w[e];
+  }
+  const uint16_t* wl = w + kWidth * sh.d_in;
+  for (int l = 0; l < sh.n_hidden - 1; ++l) {
+    char* dst = smem + L.w_sq + (uint32_t)l * kWidth * kWidth * 2;
+    for (int e = t; e < kWidth * kWidth; e += nt) {
+      const int n = e >> 7, k = e & 127;
+      *(uint16_t*)(dst + tc::kmajor_offset(n, k, kWidth)) = wl[e];
+    }
+    wl += kWidth * kWidth;
+  }
+  for (int e = t; e < 3 * kWidth; e += nt) {
+    const int n = e >> 7, k = e & 127;
+    *(uint16_t*)(smem + L.w_out + tc::kmajor_offset(n, k, kWidth)) = wl[e];
+  }
+  float* bs = (float*)(smem + L.bias);
+  for (int e = t; e < sh.n_hidden * kWidth; e += nt) bs[e] = bias[e];
+  for (int e = t; e < kNout; e += nt) bs[sh.n_hidden * kWidth + e] = e < 3 ? bias[sh.n_hidden * kWidth + e] : 0.f;
+}
+
+__device__ __forceinline__ float act_f(int act, float z) {
+  if (act == 1) return fmaxf(z, 0.f);
+  const float h = 0.5f * z;                 // SiLU(z) = z sigmoid(z) = h + h tanh(h)
+  return fmaf(h, tc::tanh_approx(h), h);
+}
+
+// Run all layers on the X tile already in shared memory (fenced and
+// synchronised by the caller).  Returns false if a bounded wait ran out
+// (status recorded); y receives row threadIdx.x of the output (+ bias).
+__device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, uint32_t tmem,
+                         uint32_t& phase, float y[3], int* status) {
+  const int t = threadIdx.x;
+  uint64_t* mbar = (uint64_t*)(smem + L.mbar);
+  volatile int* flag = (volatile int*)(smem + L.flag);
+  const uint32_t sbase = tc::smem_u32(smem);
+  const uint32_t lane_tm = tmem + ((uint32_t)((t >> 5) * 32) << 16);
+  const float* bs = (const float*)(smem + L.bias);
+  for (int l = 0; l <= sh.n_hidden; ++l) {
+    if (t == 0) {
+      tc::fence_after();
+      if (l == 0) {
+#pragma unroll
+        for (int s = 0; s < kKin / 16; ++s)
+          tc::mma_bf16(tmem, tc::sdesc(sbase + L.x + 256u * s, 128, kKin * 16),
+                       tc::sdesc(sbase + L.w_in + 256u * s, 128, kKin * 16),
+                       tc::idesc_bf16(kTileM, kWidth), s > 0);
+      } else {
+        const uint32_t wb = l < sh.n_hidden ? L.w_sq + (uint32_t)(l - 1) * kWidth * kWidth * 2 : L.w_out;
+        const uint32_t idesc = l < sh.n_hidden ? tc::idesc_bf16(kTileM, kWidth) : tc::idesc_bf16(kTileM, kNout);
+#pragma unroll
+        for (int s = 0; s < kWidth / 16; ++s)
+          tc::mma_bf16(tmem, tc::sdesc(sbase + L.h + 256u * s, 128, 2048),
+                       tc::sdesc(sbase + wb + 256u * s, 128, 2048), idesc, s > 0);
+      }
+      tc::commit(mbar);
+      *flag = tc::mbar_wait(mbar, phase, status, kBarrierLimitNs) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!*flag) return false;
+    phase ^= 1u;
+    tc::fence_after();
+    if (l < sh.n_hidden) {
+      const float* bl = bs + l * kWidth;
+#pragma unroll 1
+      for (int c0 = 0; c0 < kWidth; c0 += 32) {
+        float v[32];
+        tc::ld32(lane_tm + (uint32_t)c0, v);
+        uint32_t pk[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          pk[q] = tc::pack_bf16x2(act_f(sh.act, v[2 * q] + bl[c0 + 2 * q]),
+                                  act_f(sh.act, v[2 * q + 1] + bl[c0 + 2 * q + 1]));
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          tc::st_shared_v4(sbase + L.h + tc::kmajor_offset(t, c0 + 8 * j, kWidth), pk[4 * j],
+                           pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+      }
+      tc::fence_before();
+      tc::fence_async_smem();
+      __syncthreads();
+    } else {
+      float v[16];
+      tc::ld16(lane_tm, v);
+      const float* bo = bs + sh.n_hidden * kWidth;
+      y[0] = v[0] + bo[0];
+      y[1] = v[1] + bo[1];
+      y[2] = v[2] + bo[2];
+      tc::fence_before();
+      __syncthreads();
+    }
+  }
+  return true;
+}
+
+// Write row t of the X tile from 16 FP32 features (padding zeros included):
+// columns 0..15 hold hi = bf16(x), columns 16..31 lo = bf16(x - hi), so the
+// first layer sees x to about 16 significant bits through bf16 operands.
+__device__ __forceinline__ void write_x_row(char* smem, const MlpLayout& L, int t, const float* f) {
+  const uint32_t sb = tc::smem_u32(smem) + L.x;
+  uint32_t hi[8], lo[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    hi[q] = tc::pack_bf16x2(f[2 * q], f[2 * q + 1]);
+    const float h0 = __uint_as_float(hi[q] << 16), h1 = __uint_as_float(hi[q] & 0xFFFF0000u);
+    lo[q] = tc::pack_bf16x2(f[2 * q] - h0, f[2 * q + 1] - h1);
+  }
+  tc::st_shared_v4(sb + tc::kmajor_offset(t, 0, kKin), hi[0], hi[1], hi[2], hi[3]);
+  tc::st_shared_v4(sb + tc::kmajor_offset(t, 8, kKin), hi[4], hi[5], hi[6], hi[7]);
+  tc::st_shared_v4(sb + tc::kmajor_offset(t, 16, kKin), lo[0], lo[1], lo[2], lo[3]);
+  tc::st_shared_v4(sb + tc::kmajor_offset(t, 24, kKin), lo[4], lo[5], lo[6], lo[7]);
+}
+
+// CTA prologue/epilogue: TMEM allocation by warp 0, mbarrier set-up.
+__device__ __forceinline__ uint32_t cta_setup(char* smem, const MlpLayout& L) {
+  if (threadIdx.x < 32) {
+    tc::tmem_alloc((uint32_t*)(smem + L.tptr), 128);
+    tc::tmem_relinquish();
+  }
+  if (threadIdx.x == 0) {
+    tc::mbar_init((uint64_t*)(smem + L.mbar), 1);
+    tc::mbar_fence_init();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  return *(volatile uint32_t*)(smem + L.tptr);
+}
+
+__device__ __forceinline__ void cta_teardown(uint32_t tmem) {
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (threadIdx.x < 32) tc::tmem_dealloc(tmem, 128);
+}
+
+// ---------------------------------------------------------------- standalone forward
+// y[n x 3] = f_theta(x[n x d_in]) on bf16 tensor cores.
+__global__ void __launch_bounds__(kTileM) k_mlp_forward(MlpShape sh, const uint16_t* __restrict__ w,
+                                                        const float* __restrict__ bias, int64_t n,
+                                                        const float* __restrict__ x, float* __restrict__ y,
+                                                        int* status) {
+  extern __shared__ __align__(1024) char smem[];
+  const MlpLayout L = mlp_layout(sh.n_hidden);
+  load_weights(smem, L, sh, w, bias);
+  const uint32_t tmem = cta_setup(smem, L);
+  uint32_t phase = 0;
+  const int t = threadIdx.x;
+  const int64_t tiles = (n + kTileM - 1) / kTileM;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t row = tile * kTileM + t;
+    float f[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) f[q] = 0.f;
+    if (row < n)
+      for (int q = 0; q < sh.d_in; ++q) f[q] = x[row * sh.d_in + q];
+    write_x_row(smem, L, t, f);
+    tc::fence_async_smem();
+    __syncthreads();
+    float o[3];
+    if (!mlp_tile(smem, L, sh, tmem, phase, o, status)) break;
+    if (row < n) { y[3 * row] = o[0]; y[3 * row + 1] = o[1]; y[3 * row + 2] = o[2]; }
+  }
+  cta_teardown(tmem);
+}
+
+// ---------------------------------------------------------------- tensor-core self test
+// D[128 x N] = A[128 x K] B[N x K]^T with the same operand layout and MMA
+// issue as the MLP (one CTA).
+__global__ void __launch_bounds__(128) k_tc_selftest(int N, int K, const uint16_t* __restrict__ A,
+                                                     const uint16_t* __restrict__ B, float* __restrict__ D,
+                                                     int* status) {
+  extern __shared__ __align__(1024) char smem[];
+  const uint32_t a_off = 0, b_off = 128u * K * 2, mb = b_off + (uint32_t)N * K * 2;
+  const uint32_t tp = mb + 8, fl = tp + 4;
+  const int t = threadIdx.x;
+  for (int e = t; e < 128 * K; e += 128)
+    *(uint16_t*)(smem + a_off + tc::kmajor_offset(e / K, e % K, K)) = A[e];
+  for (int e = t; e < N * K; e += 128)
+    *(uint16_t*)(smem + b_off + tc::kmajor_offset(e / K, e % K, K)) = B[e];
+  uint32_t ncols = 32;
+  while ((int)ncols < N) ncols <<= 1;
+  if (t < 32) { tc::tmem_alloc((uint32_t*)(smem + tp), ncols); tc::tmem_relinquish(); }
+  if (t == 0) { tc::mbar_init((uint64_t*)(smem + mb), 1); tc::mbar_fence_init(); }
+  tc::fence_async_smem();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *(volatile uint32_t*)(smem + tp);
+  const uint32_t sbase = tc::smem_u32(smem);
+  const uint32_t sbo = (uint32_t)(K / 8) * 128;
+  volatile int* flag = (volatile int*)(smem + fl);
+  if (t == 0) {
+    for (int s = 0; s < K / 16; ++s)
+      tc::mma_bf16(tmem, tc::sdesc(sbase + a_off + 256u * s, 128, sbo),
+                   tc::sdesc(sbase + b_off + 256u * s, 128, sbo), tc::idesc_bf16(128, N), s > 0);
+    tc::commit((uint64_t*)(smem + mb));
+    *flag = tc::mbar_wait((uint64_t*)(smem + mb), 0, status, kBarrierLimitNs) ? 1 : 0;
+  }
+  __syncthreads();
+  tc::fence_after();
+  if (*flag) {
+    const uint32_t lane_tm = tmem + ((uint32_t)((t >> 5) * 32) << 16);
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      float v[16];
+      tc::ld16(lane_tm + (uint32_t)c0, v);
+      for (int q = 0; q < 16; ++q) D[t * N + c0 + q] = v[q];
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (t < 32) tc::tmem_dealloc(tmem, ncols);
+}
+
+// ---------------------------------------------------------------- collide
+struct NeuralArgs {
+  uint64_t seed, step;
+  double sigma_v_inv, T_ref_inv, m_over_3k, eps;
+  const double* mom;
+  const int4* pairs;
+  const int32_t* ro;
+  const dsmc_select_info_t* info;
+  double *vx, *vy, *vz;
+  unsigned* bar;
+  int* status;
+};
+
+__device__ __forceinline__ void box_muller(double u1, double u2, float* z0, float* z1) {
+  const float rho = sqrtf(-2.f * __logf((float)(1.0 - u1)));
+  float s, c;
+  __sincosf((float)(2.0 * DSMC_PI * u2), &s, &c);
+  *z0 = rho * c;
+  *z1 = rho * s;
+}
+
+__global__ void __launch_bounds__(kTileM) k_collide_neural(MlpShape sh, const uint16_t* __restrict__ w,
+                                                           const float* __restrict__ bias, NeuralArgs a) {
+  extern __shared__ __align__(1024) char smem[];
+  const MlpLayout L = mlp_layout(sh.n_hidden);
+  load_weights(smem, L, sh, w, bias);
+  const uint32_t tmem = cta_setup(smem, L);
+  uint32_t phase = 0;
+  const int t = threadIdx.x;
+  const int R = a.info->n_rounds;
+  bool alive = true;
+  for (int r = 0; r < R && alive; ++r) {
+    const int32_t beg = a.ro[r], end = a.ro[r + 1];
+    const int32_t tiles = (end - beg + kTileM - 1) / kTileM;
+    for (int32_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+      const int32_t p = beg + tile * kTileM + t;
+      const bool valid = p < end;
+      int4 q = make_int4(0, 0, 0, 0);
+      double xi = 0, yi = 0, zi = 0, xj = 0, yj = 0, zj = 0;
+      float f[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) f[c] = 0.f;
+      if (valid) {
+        q = a.pairs[p];
+        xi = __ldcg(a.vx + q.x); yi = __ldcg(a.vy + q.x); zi = __ldcg(a.vz + q.x);
+        xj = __ldcg(a.vx + q.y); yj = __ldcg(a.vy + q.y); zj = __ldcg(a.vz + q.y);
+        f[0] = (float)((xi - xj) * a.sigma_v_inv);
+        f[1] = (float)((yi - yj) * a.sigma_v_inv);
+        f[2] = (float)((zi - zj) * a.sigma_v_inv);
+        const u32x4 wa = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_NOISE, 0);
+        const u32x4 wb = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_NOISE, 1);
+        float z[4];
+        box_muller(u53(wa.x, wa.y), u53(wa.z, wa.w), &z[0], &z[1]);
+        box_muller(u53(wb.x, wb.y), u53(wb.z, wb.w), &z[2], &z[3]);
+        if (sh.d_in == 8) {
+          const double* m = a.mom + 5 * (size_t)q.z;
+          f[3] = (float)(a.m_over_3k * m[4] / m[0] * a.T_ref_inv);
+          f[4] = z[0]; f[5] = z[1]; f[6] = z[2]; f[7] = z[3];
+        } else {
+          f[3] = z[0]; f[4] = z[1]; f[5] = z[2];
+        }
+      }
+      write_x_row(smem, L, t, f);
+      tc::fence_async_smem();
+      __syncthreads();
+      float y[3];
+      if (!mlp_tile(smem, L, sh, tmem, phase, y, a.status)) { alive = false; break; }
+      if (valid) {
+        const double ux = xi - xj, uy = yi - yj, uz = zi - zj;
+        const double g = sqrt(ux * ux + uy * uy + uz * uz);
+        const double y0 = y[0], y1 = y[1], y2 = y[2];
+        const double ny = sqrt(y0 * y0 + y1 * y1 + y2 * y2);
+        double e0, e1, e2;
+        if (ny > a.eps) {
+          e0 = y0 / ny; e1 = y1 / ny; e2 = y2 / ny;
+        } else {  // isotropic fallback direction (tag 3)
+          const u32x4 wi = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_ISO);
+          const double c = 2.0 * u53(wi.x, wi.y) - 1.0, s = sqrt(1.0 - c * c);
+          double se, ce;
+          sincos(2.0 * DSMC_PI * u53(wi.z, wi.w), &se, &ce);
+          e0 = c; e1 = s * ce; e2 = s * se;
+        }
+        const double rx = g * e0, ry = g * e1, rz = g * e2;
+        const double cx = 0.5 * (xi + xj), cy = 0.5 * (yi + yj), cz = 0.5 * (zi + zj);
+        __stcg(a.vx + q.x, cx + 0.5 * rx); __stcg(a.vy + q.x, cy + 0.5 * ry); __stcg(a.vz + q.x, cz + 0.5 * rz);
+        __stcg(a.vx + q.y, cx - 0.5 * rx); __stcg(a.vy + q.y, cy - 0.5 * ry); __stcg(a.vz + q.y, cz - 0.5 * rz);
+      }
+    }
+    if (alive && r + 1 < R && !grid_barrier(a.bar, a.status, kBarrierLimitNs)) alive = false;
+  }
+  cta_teardown(tmem);
+}
+
+int cooperative_blocks(Ctx* c, const void* kernel, int threads, size_t smem);
+
+static bool set_smem(const void* k, int bytes) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+}
+
+int launch_collide_neural(Ctx* c, const dsmc_gas_t& gas, const dsmc_mlp_t& mlp,
+                          const uint16_t* w, const float* bias, uint64_t step,
+                          const double* mom, const int32_t* pairs, const int32_t* ro,
+                          const dsmc_select_info_t* info, double* vx, double* vy, double* vz,
+                          cudaStream_t s) {
+  if (mlp.n_hidden > kMaxHidden) return record(c, DSMC_ERR_UNSUPPORTED, "collide_neural: n_hidden > 4");
+  const MlpShape sh{mlp.d_in, mlp.n_hidden, mlp.act};
+  const MlpLayout L = mlp_layout(sh.n_hidden);
+  if (!set_smem((const void*)k_collide_neural, (int)L.total))
+    return record(c, DSMC_ERR_CUDA, "collide_neural: shared-memory attribute");
+  const int blocks = cooperative_blocks(c, (const void*)k_collide_neural, kTileM, L.total);
+  if (!blocks) return record(c, DSMC_ERR_CUDA, "collide_neural: occupancy query failed");
+  NeuralArgs a;
+  a.seed = gas.seed; a.step = step;
+  a.sigma_v_inv = 1.0 / mlp.sigma_v; a.T_ref_inv = 1.0 / mlp.T_ref;
+  a.m_over_3k = gas.mass / (3.0 * DSMC_KB); a.eps = mlp.eps;
+  a.mom = mom; a.pairs = (const int4*)pairs; a.ro = ro; a.info = info;
+  a.vx = vx; a.vy = vy; a.vz = vz; a.bar = barrier_ptr(c); a.status = status_ptr(c);
+  if (cudaMemsetAsync(a.bar, 0, 4 * sizeof(unsigned), s) != cudaSuccess) return DSMC_ERR_CUDA;
+  void* args[] = {(void*)&sh, (void*)&w, (void*)&bias, (void*)&a};
+  if (cudaLaunchCooperativeKernel((const void*)k_collide_neural, dim3(blocks), dim3(kTileM), args, L.total, s) !=
+      cudaSuccess)
+    return record(c, DSMC_ERR_CUDA, "collide_neural: cooperative launch failed");
+  count_launches(c, 1);
+  return 0;
+}
+
+int launch_mlp_forward(Ctx* c, const dsmc_mlp_t& mlp, const uint16_t* w, const float* bias,
+                       int64_t n, const float* x, float* y, cudaStream_t s) {
+  if (n == 0) return 0;
+  if (mlp.n_hidden > kMaxHidden) return record(c, DSMC_ERR_UNSUPPORTED, "mlp_forward: n_hidden > 4");
+  const MlpShape sh{mlp.d_in, mlp.n_hidden, mlp.act};
+  const MlpLayout L = mlp_layout(sh.n_hidden);
+  if (!set_smem((const void*)k_mlp_forward, (int)L.total))
+    return record(c, DSMC_ERR_CUDA, "mlp_forward: shared-memory attribute");
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_mlp_forward, kTileM, L.total);
+  if (per_sm < 1) per_sm = 1;
+  const int64_t tiles = (n + kTileM - 1) / kTileM;
+  int64_t blocks = (int64_t)sm_count(c) * per_sm;
+  if (blocks > tiles) blocks = tiles;
+  k_mlp_forward<<<(unsigned)blocks, kTileM, L.total, s>>>(sh, w, bias, n, x, y, status_ptr(c));
+  count_launches(c, 1);
+  return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
+}
+
+int launch_tc_selftest(Ctx* c, int N, int K, const uint16_t* A, const uint16_t* B, float* D,
+                       cudaStream_t s) {
+  const int smem = 128 * K * 2 + N * K * 2 + 64 + 4096;
+  if (!set_smem((const void*)k_tc_selftest, smem)) return record(c, DSMC_ERR_CUDA, "tc_selftest: smem");
+  k_tc_selftest<<<1, 128, smem, s>>>(N, K, A, B, D, status_ptr(c));
+  count_launches(c, 1);
+  return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
+}
+
+}  // namespace dsmc

@@ -1,0 +1,337 @@
+// No-Time-Counter pair selection (Sec. 2.2) and the conflict-free round
+// schedule of the accepted pairs.
+//
+//   k_sel_count   warp per cell: M = floor(1/2 N(N-1) F_N/V_c (sg)max dt + U),
+//                 evaluate every candidate, count acceptances, new (sg)max
+//   scan          counts -> per-cell pair offsets
+//   k_sel_emit    warp per cell: redo the candidates in order, ballot-compact
+//                 the accepted ones, then one lane walks them in candidate
+//                 order assigning round = 1 + max(last[i], last[j])
+//   scan          per-round counts -> round offsets
+//   k_sel_scatter block per chunk: regroup the pairs round-major
+//
+// The accept decision and M are taken in FP64 with explicitly rounded
+// operations (no contraction into FMA), in the operation order of the
+// definition, so that they agree exactly with any other correctly rounded
+// evaluation of the same formula.
+#include "internal.cuh"
+
+namespace dsmc {
+
+struct SelArgs {
+  const int32_t* cs;
+  const double *vx, *vy, *vz;
+  double* sgmax;
+  double* sgnew;
+  int32_t* counts;
+  const int32_t* offs;
+  int4* tmp;
+  int32_t* tmp_round;
+  int32_t* last;
+  int32_t* round_count;
+  int32_t* n_rounds;
+  unsigned long long* n_cand;
+  int* status;
+  int32_t n_cells;
+  int32_t model;
+  int64_t capacity;
+  uint64_t seed, step;
+  double fn, dt;
+  // model 0: sigma(g) = pid2 * pow(x, om_half) / gam, x = two_kt / ((mr g) g)
+  double pid2, om_half, gam, two_kt, mr;
+  // model 1: sigma = sig_const
+  double sig_const;
+};
+
+__device__ __forceinline__ double sigma_g(const SelArgs& a, double g) {
+  if (a.model == 1) return __dmul_rn(a.sig_const, g);
+  const double x = __ddiv_rn(a.two_kt, __dmul_rn(__dmul_rn(a.mr, g), g));
+  const double s = __ddiv_rn(__dmul_rn(a.pid2, pow(x, a.om_half)), a.gam);
+  return __dmul_rn(s, g);
+}
+
+__device__ __forceinline__ int32_t ntc_count(const SelArgs& a, int32_t k, int32_t N, int* bad) {
+  const u32x4 w = draw(a.seed, 0, (uint32_t)k, a.step, TAG_NTC);
+  double mt = __dmul_rn(0.5, (double)N);
+  mt = __dmul_rn(mt, (double)(N - 1));
+  mt = __dmul_rn(mt, a.fn);
+  mt = __dmul_rn(mt, a.sgmax[k]);
+  mt = __dmul_rn(mt, a.dt);
+  const double mf = floor(__dadd_rn(mt, u53(w.x, w.y)));
+  if (!(mf < 2147483647.0)) { *bad = 1; return 0; }
+  return (int32_t)mf;
+}
+
+// candidate m of cell k: local indices i, j (j != i), sigma g, accept flag
+__device__ __forceinline__ bool candidate(const SelArgs& a, int32_t k, int32_t base, int32_t N,
+                                          int32_t m, double sgmax_k, int32_t* pi, int32_t* pj,
+                                          double* sg_out) {
+  const u32x4 w = draw(a.seed, (uint32_t)m, (uint32_t)k, a.step, TAG_CAND);
+  const uint32_t i = mulhi_n(w.x, (uint32_t)N);
+  uint32_t j = mulhi_n(w.y, (uint32_t)(N - 1));
+  j += (j >= i);
+  const double dx = __dsub_rn(a.vx[base + i], a.vx[base + j]);
+  const double dy = __dsub_rn(a.vy[base + i], a.vy[base + j]);
+  const double dz = __dsub_rn(a.vz[base + i], a.vz[base + j]);
+  const double g2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+  const double g = __dsqrt_rn(g2);
+  const double sg = sigma_g(a, g);
+  *pi = (int32_t)i; *pj = (int32_t)j; *sg_out = sg;
+  return u53(w.z, w.w) < __ddiv_rn(sg, sgmax_k);
+}
+
+constexpr int kSelWarps = 8;
+
+__global__ void __launch_bounds__(kSelWarps * 32) k_sel_count(SelArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int32_t warps = gridDim.x * kSelWarps;
+  for (int32_t k = blockIdx.x * kSelWarps + (threadIdx.x >> 5); k < a.n_cells; k += warps) {
+    const int32_t base = a.cs[k], N = a.cs[k + 1] - base;
+    const double sgk = a.sgmax[k];
+    if (N < 2) {
+      if (lane == 0) { a.counts[k] = 0; a.sgnew[k] = sgk; }
+      continue;
+    }
+    int bad = 0;
+    const int32_t M = ntc_count(a, k, N, &bad);
+    if (bad && lane == 0) set_status(a.status, DSMC_ERR_CAPACITY);
+    int acc = 0;
+    double best = sgk;
+    for (int32_t m = lane; m < M; m += 32) {
+      int32_t i, j;
+      double sg;
+      acc += candidate(a, k, base, N, m, sgk, &i, &j, &sg);
+      best = fmax(best, sg);
+    }
+    acc = warp_sum_i(acc);
+    best = warp_max(best);
+    if (lane == 0) {
+      a.counts[k] = acc;
+      a.sgnew[k] = best;
+      atomicAdd(a.n_cand, (unsigned long long)M);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kSelWarps * 32) k_sel_emit(SelArgs a) {
+  __shared__ int hist[DSMC_MAX_ROUNDS];
+  __shared__ int rmax_blk;
+  for (int t = threadIdx.x; t < DSMC_MAX_ROUNDS; t += blockDim.x) hist[t] = 0;
+  if (threadIdx.x == 0) rmax_blk = 0;
+  __syncthreads();
+  const int64_t total = a.offs[a.n_cells];
+  const bool over = total > a.capacity;
+  if (over && blockIdx.x == 0 && threadIdx.x == 0) set_status(a.status, DSMC_ERR_CAPACITY);
+  const int lane = threadIdx.x & 31;
+  const int32_t warps = gridDim.x * kSelWarps;
+  for (int32_t k = blockIdx.x * kSelWarps + (threadIdx.x >> 5); k < a.n_cells && !over; k += warps) {
+    const int32_t base = a.cs[k], N = a.cs[k + 1] - base;
+    if (N < 2) continue;
+    const double sgk = a.sgmax[k];
+    int bad = 0;
+    const int32_t M = ntc_count(a, k, N, &bad);
+    const int32_t p0 = a.offs[k], p1 = a.offs[k + 1];
+    int32_t pos = p0;
+    for (int32_t c0 = 0; c0 < M; c0 += 32) {
+      const int32_t m = c0 + lane;
+      int32_t i = 0, j = 0;
+      double sg;
+      const bool ok = m < M && candidate(a, k, base, N, m, sgk, &i, &j, &sg);
+      const unsigned mask = __ballot_sync(0xffffffffu, ok);
+      if (ok) {
+        const int32_t q = pos + __popc(mask & ((1u << lane) - 1u));
+        a.tmp[q] = make_int4(base + i, base + j, k, m);
+      }
+      pos += __popc(mask);
+    }
+    for (int32_t t = lane; t < N; t += 32) a.last[base + t] = -1;
+    __syncwarp();
+    if (lane == 0) {
+      int rm = -1;
+      for (int32_t p = p0; p < p1; ++p) {
+        const int4 q = a.tmp[p];
+        const int li = a.last[q.x], lj = a.last[q.y];
+        int r = 1 + (li > lj ? li : lj);
+        if (r >= DSMC_MAX_ROUNDS) { set_status(a.status, DSMC_ERR_UNSUPPORTED); r = DSMC_MAX_ROUNDS - 1; }
+        a.last[q.x] = r;
+        a.last[q.y] = r;
+        a.tmp_round[p] = r;
+        atomicAdd(&hist[r], 1);
+        rm = r > rm ? r : rm;
+      }
+      atomicMax(&rmax_blk, rm + 1);
+      a.sgmax[k] = a.sgnew[k];
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < DSMC_MAX_ROUNDS; t += blockDim.x)
+    if (hist[t]) atomicAdd(a.round_count + t, hist[t]);
+  if (threadIdx.x == 0 && rmax_blk > 0) atomicMax(a.n_rounds, rmax_blk);
+}
+
+// Cells with fewer than two particles keep their (sigma g)_max; cells whose
+// emit was skipped (capacity overflow) get the new value here.
+__global__ void k_sel_sg_commit(SelArgs a) {
+  const int64_t total = a.offs[a.n_cells];
+  if (total <= a.capacity) return;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n_cells; k += gridDim.x * blockDim.x)
+    a.sgmax[k] = a.sgnew[k];
+}
+
+constexpr int kScatterChunk = 4096;
+
+__global__ void __launch_bounds__(256)
+k_sel_scatter(const int4* __restrict__ tmp, const int32_t* __restrict__ tmp_round,
+              const int32_t* __restrict__ offs, int32_t n_cells, int64_t capacity,
+              const int32_t* __restrict__ round_off, int32_t* round_fill, int4* __restrict__ out) {
+  __shared__ int cnt[DSMC_MAX_ROUNDS];
+  __shared__ int dst[DSMC_MAX_ROUNDS];
+  const int64_t total = offs[n_cells];
+  if (total > capacity) return;
+  const int64_t p0 = (int64_t)blockIdx.x * kScatterChunk;
+  if (p0 >= total) return;
+  const int64_t p1 = p0 + kScatterChunk < total ? p0 + kScatterChunk : total;
+  for (int t = threadIdx.x; t < DSMC_MAX_ROUNDS; t += blockDim.x) cnt[t] = 0;
+  __syncthreads();
+  for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) atomicAdd(&cnt[tmp_round[p]], 1);
+  __syncthreads();
+  for (int t = threadIdx.x; t < DSMC_MAX_ROUNDS; t += blockDim.x) {
+    dst[t] = cnt[t] ? round_off[t] + atomicAdd(round_fill + t, cnt[t]) : 0;
+    cnt[t] = 0;
+  }
+  __syncthreads();
+  for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    const int r = tmp_round[p];
+    out[dst[r] + atomicAdd(&cnt[r], 1)] = tmp[p];
+  }
+}
+
+__global__ void k_sel_finalize(const int32_t* offs, int32_t n_cells, int64_t capacity,
+                               const unsigned long long* n_cand, const int32_t* n_rounds,
+                               dsmc_select_info_t* info) {
+  const int64_t total = offs[n_cells];
+  info->n_pairs = total;
+  info->n_candidates = (int64_t)*n_cand;
+  info->n_rounds = total > capacity ? 0 : *n_rounds;
+  info->pad_ = 0;
+}
+
+// ---------------------------------------------------------------- workspace
+struct SelWs {
+  int32_t *counts, *offs, *tmp_round, *last, *round_count, *round_fill, *n_rounds;
+  double* sgnew;
+  int4* tmp;
+  unsigned long long* n_cand;
+  void* scan;
+};
+
+static size_t carve(SelWs* w, char* p, int32_t n, int32_t n_cells, int64_t capacity) {
+  char* p0 = p;
+  auto take = [&](size_t bytes) { char* q = p; p += align256(bytes); return q; };
+  const size_t nc = (size_t)(n_cells > 0 ? n_cells : 1);
+  const size_t cap = (size_t)(capacity > 0 ? capacity : 1);
+  w->counts = (int32_t*)take(sizeof(int32_t) * nc);
+  w->offs = (int32_t*)take(sizeof(int32_t) * (nc + 1));
+  w->sgnew = (double*)take(sizeof(double) * nc);
+  w->tmp = (int4*)take(sizeof(int4) * cap);
+  w->tmp_round = (int32_t*)take(sizeof(int32_t) * cap);
+  w->last = (int32_t*)take(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  // the following four are zeroed together
+  w->round_count = (int32_t*)take(sizeof(int32_t) * DSMC_MAX_ROUNDS * 2 + 256);
+  w->round_fill = w->round_count + DSMC_MAX_ROUNDS;
+  w->n_rounds = w->round_count + 2 * DSMC_MAX_ROUNDS;
+  w->n_cand = (unsigned long long*)(w->round_count + 2 * DSMC_MAX_ROUNDS + 2);
+  const size_t sws = scan_ws(n_cells) > scan_ws(DSMC_MAX_ROUNDS) ? scan_ws(n_cells) : scan_ws(DSMC_MAX_ROUNDS);
+  w->scan = take(sws);
+  return (size_t)(p - p0);
+}
+
+size_t select_ws(int32_t n, int32_t n_cells, int64_t capacity) {
+  SelWs w;
+  return carve(&w, (char*)0, n, n_cells, capacity);
+}
+
+static unsigned blocks_for(int64_t work, int per_block, int max_blocks) {
+  int64_t b = (work + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  if (b > max_blocks) b = max_blocks;
+  return (unsigned)b;
+}
+
+int launch_select(Ctx* c, const dsmc_gas_t& gas, int32_t n, int32_t n_cells, const int32_t* cs,
+                  const double* vx, const double* vy, const double* vz, double* sgmax,
+                  uint64_t step, int64_t capacity, int32_t* pairs, int32_t* round_offsets,
+                  dsmc_select_info_t* info, void* ws, size_t ws_bytes, cudaStream_t s) {
+  if (ws_bytes < select_ws(n, n_cells, capacity))
+    return record(c, DSMC_ERR_ARG, "select: workspace too small");
+  if (capacity > INT32_MAX) return record(c, DSMC_ERR_ARG, "select: capacity >= 2^31");
+  SelWs w;
+  carve(&w, (char*)ws, n, n_cells, capacity);
+  SelArgs a;
+  a.cs = cs; a.vx = vx; a.vy = vy; a.vz = vz; a.sgmax = sgmax; a.sgnew = w.sgnew;
+  a.counts = w.counts; a.offs = w.offs; a.tmp = w.tmp; a.tmp_round = w.tmp_round;
+  a.last = w.last; a.round_count = w.round_count; a.n_rounds = w.n_rounds; a.n_cand = w.n_cand;
+  a.status = status_ptr(c); a.n_cells = n_cells; a.model = gas.model; a.capacity = capacity;
+  a.seed = gas.seed; a.step = step; a.fn = gas.fn_over_vc; a.dt = gas.dt;
+  a.pid2 = DSMC_PI * gas.d_ref * gas.d_ref;
+  a.om_half = gas.omega - 0.5;
+  a.gam = tgamma(2.5 - gas.omega);
+  a.two_kt = 2.0 * DSMC_KB * gas.T_ref;
+  a.mr = 0.5 * gas.mass;
+  a.sig_const = DSMC_PI * gas.b_max * gas.b_max;
+  const int sms = sm_count(c);
+  if (cudaMemsetAsync(w.round_count, 0, sizeof(int32_t) * DSMC_MAX_ROUNDS * 2 + 256, s) != cudaSuccess)
+    return DSMC_ERR_CUDA;
+  if (cudaMemsetAsync(round_offsets, 0, sizeof(int32_t) * (DSMC_MAX_ROUNDS + 1), s) != cudaSuccess)
+    return DSMC_ERR_CUDA;
+  if (n_cells > 0) {
+    const unsigned gb = blocks_for(n_cells, kSelWarps, sms * 8);
+    k_sel_count<<<gb, kSelWarps * 32, 0, s>>>(a);
+    count_launches(c, 1);
+    int rc = launch_scan(c, w.counts, w.offs, n_cells, w.scan, s);
+    if (rc) return rc;
+    k_sel_emit<<<gb, kSelWarps * 32, 0, s>>>(a);
+    k_sel_sg_commit<<<blocks_for(n_cells, 256, sms * 4), 256, 0, s>>>(a);
+    count_launches(c, 2);
+    rc = launch_scan(c, w.round_count, round_offsets, DSMC_MAX_ROUNDS, w.scan, s);
+    if (rc) return rc;
+    const unsigned sb = (unsigned)((capacity + kScatterChunk - 1) / kScatterChunk);
+    if (sb > 0) {
+      k_sel_scatter<<<sb, 256, 0, s>>>(w.tmp, w.tmp_round, w.offs, n_cells, capacity,
+                                        round_offsets, w.round_fill, (int4*)pairs);
+      count_launches(c, 1);
+    }
+  } else {
+    if (cudaMemsetAsync(w.offs, 0, sizeof(int32_t), s) != cudaSuccess) return DSMC_ERR_CUDA;
+  }
+  k_sel_finalize<<<1, 1, 0, s>>>(w.offs, n_cells, capacity, w.n_cand, w.n_rounds, info);
+  count_launches(c, 1);
+  return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------- (sigma g)_max init
+__global__ void k_sgmax_init(SelArgs a, const double* T, double factor, double mass, double* out) {
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n_cells; k += gridDim.x * blockDim.x) {
+    const double g0 = factor * sqrt(2.0 * DSMC_KB * T[k] / mass);
+    out[k] = sigma_g(a, g0);
+  }
+}
+
+int launch_sgmax_init(Ctx* c, const dsmc_gas_t& gas, int32_t n_cells, const double* T,
+                      double factor, double* sgmax, cudaStream_t s) {
+  if (n_cells <= 0) return 0;
+  SelArgs a = {};
+  a.n_cells = n_cells; a.model = gas.model;
+  a.pid2 = DSMC_PI * gas.d_ref * gas.d_ref;
+  a.om_half = gas.omega - 0.5;
+  a.gam = tgamma(2.5 - gas.omega);
+  a.two_kt = 2.0 * DSMC_KB * gas.T_ref;
+  a.mr = 0.5 * gas.mass;
+  a.sig_const = DSMC_PI * gas.b_max * gas.b_max;
+  k_sgmax_init<<<blocks_for(n_cells, 256, sm_count(c) * 4), 256, 0, s>>>(a, T, factor, gas.mass, sgmax);
+  count_launches(c, 1);
+  return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
+}
+
+}  // namespace dsmc

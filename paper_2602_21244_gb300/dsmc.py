@@ -1,0 +1,395 @@
+"""Thin ctypes binding of libdsmc.so (include/dsmc.h).
+
+Argument marshalling only: every step of the collision path runs in the
+library's CUDA kernels.  Tensors are torch CUDA tensors (device memory and
+streams come from PyTorch); functions take them, check dtype/contiguity and
+pass raw device pointers and the current stream.  There is no CPU fallback:
+if the library cannot be loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from . import _build
+
+DSMC_OK, DSMC_ERR_ARG, DSMC_ERR_CUDA, DSMC_ERR_CAPACITY = 0, -1, -2, -3
+DSMC_ERR_TIMEOUT, DSMC_ERR_NONFINITE, DSMC_ERR_UNSUPPORTED = -4, -5, -6
+PATH_VHS, PATH_JAGER, PATH_NEURAL = 0, 1, 2
+MAX_ROUNDS = 1024
+_ERRS = {-1: "DSMC_ERR_ARG", -2: "DSMC_ERR_CUDA", -3: "DSMC_ERR_CAPACITY", -4: "DSMC_ERR_TIMEOUT",
+         -5: "DSMC_ERR_NONFINITE", -6: "DSMC_ERR_UNSUPPORTED"}
+
+
+class DsmcError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__(f"{_ERRS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Gas(C.Structure):
+    _fields_ = [("mass", C.c_double), ("d_ref", C.c_double), ("omega", C.c_double),
+                ("T_ref", C.c_double), ("fn_over_vc", C.c_double), ("dt", C.c_double),
+                ("seed", C.c_uint64), ("model", C.c_int32), ("pad_", C.c_int32),
+                ("b_max", C.c_double)]
+
+
+class Potential(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pad_", C.c_int32), ("A", C.c_double),
+                ("a1", C.c_double), ("a2", C.c_double), ("am1", C.c_double),
+                ("am2", C.c_double), ("beta", C.c_double), ("C", C.c_double * 6),
+                ("R_eps", C.c_double), ("At", C.c_double), ("at", C.c_double),
+                ("d_hs", C.c_double), ("kappa", C.c_double), ("p", C.c_double)]
+
+
+class Mlp(C.Structure):
+    _fields_ = [("d_in", C.c_int32), ("width", C.c_int32), ("n_hidden", C.c_int32),
+                ("d_out", C.c_int32), ("act", C.c_int32), ("pad_", C.c_int32),
+                ("sigma_v", C.c_double), ("T_ref", C.c_double), ("eps", C.c_double)]
+
+
+class SelectInfo(C.Structure):
+    _fields_ = [("n_pairs", C.c_int64), ("n_candidates", C.c_int64), ("n_rounds", C.c_int32),
+                ("pad_", C.c_int32)]
+
+
+class StepBuffers(C.Structure):
+    _fields_ = [("n", C.c_int32), ("n_cells", C.c_int32), ("capacity", C.c_int64),
+                ("cell_id", C.c_void_p), ("vx", C.c_void_p), ("vy", C.c_void_p), ("vz", C.c_void_p),
+                ("perm", C.c_void_p), ("cell_start", C.c_void_p), ("svx", C.c_void_p),
+                ("svy", C.c_void_p), ("svz", C.c_void_p), ("mom", C.c_void_p),
+                ("sigma_g_max", C.c_void_p), ("pairs", C.c_void_p), ("round_offsets", C.c_void_p),
+                ("info", C.c_void_p), ("ws", C.c_void_p), ("ws_bytes", C.c_size_t)]
+
+
+class Path(C.Structure):
+    _fields_ = [("path", C.c_int32), ("n_nodes", C.c_int32), ("pot", C.POINTER(Potential)),
+                ("mlp", C.POINTER(Mlp)), ("weights_bf16", C.c_void_p), ("biases", C.c_void_p)]
+
+
+# ------------------------------------------------------------------ library
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build: bool = True):
+    """Load libdsmc.so (building it first when sources changed)."""
+    global _lib
+    if _lib is None:
+        if build:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise ImportError(f"libdsmc.so not built ({_build.LIB})")
+        L = C.CDLL(_build.LIB)
+        vp, i32, i64, u64, sz, d = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_size_t, C.c_double
+        P = C.POINTER
+        sig = {
+            "dsmc_abi_version": (C.c_int, []),
+            "dsmc_ctx_create": (C.c_int, [P(vp), C.c_int]),
+            "dsmc_ctx_destroy": (None, [vp]),
+            "dsmc_ctx_sync_status": (C.c_int, [vp, vp]),
+            "dsmc_last_error": (C.c_char_p, [vp]),
+            "dsmc_ctx_launch_count": (i64, [vp]),
+            "dsmc_sort_workspace_size": (sz, [i32, i32]),
+            "dsmc_sort_cells": (C.c_int, [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
+            "dsmc_cell_moments": (C.c_int, [vp, i32, vp, vp, vp, vp, vp, vp]),
+            "dsmc_sigma_g_max_init": (C.c_int, [vp, P(Gas), i32, vp, d, vp, vp]),
+            "dsmc_select_workspace_size": (sz, [i32, i32, i64]),
+            "dsmc_select_pairs": (C.c_int, [vp, P(Gas), i32, i32, vp, vp, vp, vp, vp, u64, i64, vp, vp,
+                                            vp, vp, sz, vp]),
+            "dsmc_collide_vhs": (C.c_int, [vp, P(Gas), u64, vp, vp, vp, vp, vp, vp, vp]),
+            "dsmc_jager_chi": (C.c_int, [vp, P(Gas), P(Potential), i32, i64, vp, vp, vp, vp]),
+            "dsmc_collide_jager": (C.c_int, [vp, P(Gas), P(Potential), i32, u64, vp, vp, vp, vp, vp,
+                                             vp, vp, vp]),
+            "dsmc_collide_neural": (C.c_int, [vp, P(Gas), P(Mlp), vp, vp, u64, vp, vp, vp, vp, vp, vp,
+                                              vp, vp]),
+            "dsmc_mlp_forward": (C.c_int, [vp, P(Mlp), vp, vp, i64, vp, vp, vp]),
+            "dsmc_tc_selftest": (C.c_int, [vp, i32, i32, vp, vp, vp, vp]),
+            "dsmc_moment_match": (C.c_int, [vp, i32, vp, vp, vp, vp, vp, vp]),
+            "dsmc_step_workspace_size": (sz, [i32, i32, i64]),
+            "dsmc_step": (C.c_int, [vp, P(Gas), P(Path), P(StepBuffers), u64, vp]),
+            "dsmc_ctx_reserve": (C.c_int, [vp, i32, i32, i64]),
+            "dsmc_step_host": (C.c_int, [vp, P(Gas), P(Path), i32, vp, vp, vp, vp, vp, u64, vp, vp,
+                                         vp, vp, P(i64), vp]),
+            "dsmc_harvest_jager": (C.c_int, [vp, P(Gas), P(Potential), i32, i64, vp, vp, vp, vp, vp,
+                                             vp, vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+# ------------------------------------------------------------------ helpers
+
+def _ptr(t: torch.Tensor | None, dtype=None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def make_gas(d: dict) -> Gas:
+    return Gas(d["mass"], d.get("d_ref", 0.0), d.get("omega", 0.5), d.get("T_ref", 273.0),
+               d["fn_over_vc"], d["dt"], int(d.get("seed", 0)), int(d.get("model", 0)), 0,
+               d.get("b_max", 0.0))
+
+
+def make_potential(d: dict) -> Potential:
+    P = Potential()
+    P.kind = int(d.get("kind", 0))
+    for k in ("A", "a1", "a2", "am1", "am2", "beta", "R_eps", "At", "at", "d_hs", "kappa", "p"):
+        setattr(P, k, float(d.get(k, 0.0)))
+    cs = d.get("C", [0.0] * 6)
+    for q in range(6):
+        P.C[q] = float(cs[q])
+    return P
+
+
+def make_mlp(d_in=8, width=128, n_hidden=3, d_out=3, act=0, sigma_v=1.0, T_ref=273.0, eps=1e-12) -> Mlp:
+    return Mlp(d_in, width, n_hidden, d_out, act, 0, sigma_v, T_ref, eps)
+
+
+class Context:
+    """A library context on one device (status word, barrier words)."""
+
+    def __init__(self, device: int = 0):
+        L = load()
+        self._lib = L
+        h = C.c_void_p()
+        rc = L.dsmc_ctx_create(C.byref(h), device)
+        if rc != 0:
+            raise DsmcError(rc, "dsmc_ctx_create")
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.dsmc_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc != 0:
+            raise DsmcError(rc, f"{what}: {self._lib.dsmc_last_error(self.h).decode()}")
+
+    def launch_count(self) -> int:
+        return self._lib.dsmc_ctx_launch_count(self.h)
+
+    def sync_status(self, stream=None) -> int:
+        return self._lib.dsmc_ctx_sync_status(self.h, _stream(stream))
+
+    def check_status(self, stream=None):
+        rc = self.sync_status(stream)
+        if rc != 0:
+            raise DsmcError(rc, "device-side status")
+
+    # -------------------------------------------------------------- step pieces
+    def sort_cells(self, cell_id, vx, vy, vz, n_cells, out=None, ws=None, stream=None):
+        n = cell_id.numel()
+        dev = cell_id.device
+        if out is None:
+            out = dict(perm=torch.empty(n, dtype=torch.int32, device=dev),
+                       cell_start=torch.empty(n_cells + 1, dtype=torch.int32, device=dev),
+                       svx=torch.empty(n, dtype=torch.float64, device=dev),
+                       svy=torch.empty(n, dtype=torch.float64, device=dev),
+                       svz=torch.empty(n, dtype=torch.float64, device=dev))
+        nbytes = self._lib.dsmc_sort_workspace_size(n, n_cells)
+        if ws is None or ws.numel() < nbytes:
+            ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        f64 = torch.float64
+        self._check(self._lib.dsmc_sort_cells(
+            self.h, n, n_cells, _ptr(cell_id, torch.int32), _ptr(vx, f64), _ptr(vy, f64), _ptr(vz, f64),
+            _ptr(out["perm"]), _ptr(out["cell_start"]), _ptr(out["svx"]), _ptr(out["svy"]),
+            _ptr(out["svz"]), _ptr(ws), nbytes, _stream(stream)), "sort_cells")
+        return out
+
+    def cell_moments(self, cell_start, vx, vy, vz, mom=None, stream=None):
+        nc = cell_start.numel() - 1
+        if mom is None:
+            mom = torch.empty((nc, 5), dtype=torch.float64, device=cell_start.device)
+        self._check(self._lib.dsmc_cell_moments(self.h, nc, _ptr(cell_start, torch.int32), _ptr(vx),
+                                                _ptr(vy), _ptr(vz), _ptr(mom, torch.float64),
+                                                _stream(stream)), "cell_moments")
+        return mom
+
+    def sigma_g_max_init(self, gas: Gas, T_cell, factor=5.0, out=None, stream=None):
+        if out is None:
+            out = torch.empty_like(T_cell)
+        self._check(self._lib.dsmc_sigma_g_max_init(self.h, C.byref(gas), T_cell.numel(),
+                                                    _ptr(T_cell, torch.float64), factor, _ptr(out),
+                                                    _stream(stream)), "sigma_g_max_init")
+        return out
+
+    def select_pairs(self, gas: Gas, cell_start, vx, vy, vz, sgmax, step, capacity, out=None,
+                     ws=None, stream=None):
+        nc = cell_start.numel() - 1
+        n = vx.numel()
+        dev = vx.device
+        if out is None:
+            out = dict(pairs=torch.empty((max(capacity, 1), 4), dtype=torch.int32, device=dev),
+                       round_offsets=torch.empty(MAX_ROUNDS + 1, dtype=torch.int32, device=dev),
+                       info=torch.zeros(3, dtype=torch.int64, device=dev))
+        nbytes = self._lib.dsmc_select_workspace_size(n, nc, capacity)
+        if ws is None or ws.numel() < nbytes:
+            ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self._check(self._lib.dsmc_select_pairs(
+            self.h, C.byref(gas), n, nc, _ptr(cell_start, torch.int32), _ptr(vx, torch.float64),
+            _ptr(vy, torch.float64), _ptr(vz, torch.float64), _ptr(sgmax, torch.float64), step,
+            capacity, _ptr(out["pairs"]), _ptr(out["round_offsets"]), _ptr(out["info"]), _ptr(ws),
+            nbytes, _stream(stream)), "select_pairs")
+        return out
+
+    def collide_vhs(self, gas: Gas, step, sel, vx, vy, vz, stream=None):
+        self._check(self._lib.dsmc_collide_vhs(self.h, C.byref(gas), step, _ptr(sel["pairs"]),
+                                               _ptr(sel["round_offsets"]), _ptr(sel["info"]),
+                                               _ptr(vx, torch.float64), _ptr(vy, torch.float64),
+                                               _ptr(vz, torch.float64), _stream(stream)), "collide_vhs")
+
+    def jager_chi(self, gas: Gas, pot: Potential, b, g, n_nodes=32, chi=None, stream=None):
+        if chi is None:
+            chi = torch.empty_like(b)
+        self._check(self._lib.dsmc_jager_chi(self.h, C.byref(gas), C.byref(pot), n_nodes, b.numel(),
+                                             _ptr(b, torch.float32), _ptr(g, torch.float32), _ptr(chi),
+                                             _stream(stream)), "jager_chi")
+        return chi
+
+    def collide_jager(self, gas: Gas, pot: Potential, step, sel, vx, vy, vz, n_nodes=32,
+                      chi_out=None, stream=None):
+        self._check(self._lib.dsmc_collide_jager(
+            self.h, C.byref(gas), C.byref(pot), n_nodes, step, _ptr(sel["pairs"]),
+            _ptr(sel["round_offsets"]), _ptr(sel["info"]), _ptr(vx, torch.float64),
+            _ptr(vy, torch.float64), _ptr(vz, torch.float64), _ptr(chi_out, torch.float32),
+            _stream(stream)), "collide_jager")
+
+    def collide_neural(self, gas: Gas, mlp: Mlp, w_bits, bias, step, mom, sel, vx, vy, vz,
+                       stream=None):
+        self._check(self._lib.dsmc_collide_neural(
+            self.h, C.byref(gas), C.byref(mlp), _ptr(w_bits, torch.int16), _ptr(bias, torch.float32),
+            step, _ptr(mom, torch.float64), _ptr(sel["pairs"]), _ptr(sel["round_offsets"]),
+            _ptr(sel["info"]), _ptr(vx, torch.float64), _ptr(vy, torch.float64),
+            _ptr(vz, torch.float64), _stream(stream)), "collide_neural")
+
+    def mlp_forward(self, mlp: Mlp, w_bits, bias, x, y=None, stream=None):
+        n = x.shape[0]
+        if y is None:
+            y = torch.empty((n, 3), dtype=torch.float32, device=x.device)
+        self._check(self._lib.dsmc_mlp_forward(self.h, C.byref(mlp), _ptr(w_bits, torch.int16),
+                                               _ptr(bias, torch.float32), n, _ptr(x, torch.float32),
+                                               _ptr(y, torch.float32), _stream(stream)), "mlp_forward")
+        return y
+
+    def tc_selftest(self, A_bits, B_bits, stream=None):
+        K = A_bits.shape[1]
+        N = B_bits.shape[0]
+        D = torch.empty((128, N), dtype=torch.float32, device=A_bits.device)
+        self._check(self._lib.dsmc_tc_selftest(self.h, N, K, _ptr(A_bits, torch.int16),
+                                               _ptr(B_bits, torch.int16), _ptr(D), _stream(stream)),
+                    "tc_selftest")
+        return D
+
+    def moment_match(self, cell_start, mom_pre, vx, vy, vz, stream=None):
+        self._check(self._lib.dsmc_moment_match(self.h, cell_start.numel() - 1,
+                                                _ptr(cell_start, torch.int32),
+                                                _ptr(mom_pre, torch.float64), _ptr(vx, torch.float64),
+                                                _ptr(vy, torch.float64), _ptr(vz, torch.float64),
+                                                _stream(stream)), "moment_match")
+
+    def harvest_jager(self, gas: Gas, pot: Potential, vi, vj, b, eps, n_nodes=32, stream=None):
+        vio, vjo = torch.empty_like(vi), torch.empty_like(vj)
+        self._check(self._lib.dsmc_harvest_jager(
+            self.h, C.byref(gas), C.byref(pot), n_nodes, b.numel(), _ptr(vi, torch.float64),
+            _ptr(vj, torch.float64), _ptr(b, torch.float64), _ptr(eps, torch.float64), _ptr(vio),
+            _ptr(vjo), _stream(stream)), "harvest_jager")
+        return vio, vjo
+
+    # -------------------------------------------------------------- whole step
+    def step_workspace_size(self, n, n_cells, capacity) -> int:
+        return self._lib.dsmc_step_workspace_size(n, n_cells, capacity)
+
+    def step(self, gas: Gas, path: Path, bufs: "StepState", step: int, stream=None):
+        self._check(self._lib.dsmc_step(self.h, C.byref(gas), C.byref(path), C.byref(bufs.desc),
+                                        step, _stream(stream)), "step")
+
+    def reserve(self, n_max, n_cells, capacity):
+        self._check(self._lib.dsmc_ctx_reserve(self.h, n_max, n_cells, capacity), "reserve")
+
+    def step_host(self, gas: Gas, path: Path, cell_id, vx, vy, vz, T_cell, step, perm, svx, svy,
+                  svz, stream=None) -> int:
+        """Host-memory step: all array arguments are (pinned) CPU tensors."""
+        npairs = C.c_int64(0)
+        hp = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+        self._check(self._lib.dsmc_step_host(
+            self.h, C.byref(gas), C.byref(path), cell_id.numel(), hp(cell_id), hp(vx), hp(vy), hp(vz),
+            hp(T_cell), step, hp(perm), hp(svx), hp(svy), hp(svz), C.byref(npairs), _stream(stream)),
+            "step_host")
+        return npairs.value
+
+
+class StepState:
+    """Device buffers of one collision step (see dsmc_step_buffers_t)."""
+
+    def __init__(self, ctx: Context, n, n_cells, capacity, device="cuda"):
+        dev = torch.device(device)
+        f64, i32 = torch.float64, torch.int32
+        self.n, self.n_cells, self.capacity = n, n_cells, capacity
+        self.cell_id = torch.empty(n, dtype=i32, device=dev)
+        self.vx, self.vy, self.vz = (torch.empty(n, dtype=f64, device=dev) for _ in range(3))
+        self.perm = torch.empty(n, dtype=i32, device=dev)
+        self.cell_start = torch.empty(n_cells + 1, dtype=i32, device=dev)
+        self.svx, self.svy, self.svz = (torch.empty(n, dtype=f64, device=dev) for _ in range(3))
+        self.mom = torch.empty((n_cells, 5), dtype=f64, device=dev)
+        self.sigma_g_max = torch.empty(n_cells, dtype=f64, device=dev)
+        self.pairs = torch.empty((max(capacity, 1), 4), dtype=i32, device=dev)
+        self.round_offsets = torch.empty(MAX_ROUNDS + 1, dtype=i32, device=dev)
+        self.info = torch.zeros(3, dtype=torch.int64, device=dev)
+        nb = ctx.step_workspace_size(n, n_cells, capacity)
+        self.ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+        p = lambda t: t.data_ptr()
+        self.desc = StepBuffers(n, n_cells, capacity, p(self.cell_id), p(self.vx), p(self.vy),
+                                p(self.vz), p(self.perm), p(self.cell_start), p(self.svx), p(self.svy),
+                                p(self.svz), p(self.mom), p(self.sigma_g_max), p(self.pairs),
+                                p(self.round_offsets), p(self.info), p(self.ws), nb)
+
+    @property
+    def sel(self):
+        return dict(pairs=self.pairs, round_offsets=self.round_offsets, info=self.info)
+
+    def info_host(self):
+        i = self.info.cpu()
+        return dict(n_pairs=int(i[0]), n_candidates=int(i[1]), n_rounds=int(i[2] & 0xFFFFFFFF))
+
+
+def make_path(kind: int, pot: Potential | None = None, n_nodes: int = 32, mlp: Mlp | None = None,
+              w_bits: torch.Tensor | None = None, bias: torch.Tensor | None = None) -> Path:
+    P = Path()
+    P.path = kind
+    P.n_nodes = n_nodes
+    P.pot = C.pointer(pot) if pot is not None else C.POINTER(Potential)()
+    P.mlp = C.pointer(mlp) if mlp is not None else C.POINTER(Mlp)()
+    P.weights_bf16 = w_bits.data_ptr() if w_bits is not None else None
+    P.biases = bias.data_ptr() if bias is not None else None
+    P._keep = (pot, mlp, w_bits, bias)
+    return P

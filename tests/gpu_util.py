@@ -1,0 +1,74 @@
+"""Shared helpers of the GPU parity tests (CUDA path vs CPU oracle)."""
+import math
+
+import numpy as np
+
+KB = 1.380649e-23
+_CTX = None
+
+
+def torch():
+    import torch as T
+    return T
+
+
+def ctx():
+    global _CTX
+    from paper_2602_21244_gb300 import dsmc as D
+    if _CTX is None:
+        _CTX = D.Context(0)
+    return _CTX
+
+
+def cuda(a, dtype=None):
+    T = torch()
+    t = T.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def w_bits_tensor(bits):
+    return cuda(bits.view(np.int16))
+
+
+def gpu_step_pieces(wl, sgmax0, step=0, capacity=1 << 22):
+    """Sort, moments and selection on the GPU for a workload dict."""
+    T = torch()
+    from paper_2602_21244_gb300 import dsmc as D
+    C = ctx()
+    gas = D.make_gas(wl["gas"])
+    cid = cuda(wl["cell_id"])
+    vx, vy, vz = cuda(wl["vx"]), cuda(wl["vy"]), cuda(wl["vz"])
+    srt = C.sort_cells(cid, vx, vy, vz, wl["n_cells"])
+    mom = C.cell_moments(srt["cell_start"], srt["svx"], srt["svy"], srt["svz"])
+    sg = cuda(sgmax0).clone()
+    sel = C.select_pairs(gas, srt["cell_start"], srt["svx"], srt["svy"], srt["svz"], sg, step,
+                         capacity)
+    T.cuda.synchronize()
+    return gas, srt, mom, sg, sel
+
+
+def sel_host(sel):
+    info = host(sel["info"])
+    n = int(info[0])
+    R = int(info[2] & 0xFFFFFFFF)
+    ro = host(sel["round_offsets"])[:R + 1]
+    pairs = host(sel["pairs"])[:n] if n else np.zeros((0, 4), np.int32)
+    return dict(n_pairs=n, n_cand=int(info[1]), n_rounds=R, ro=ro, pairs=pairs)
+
+
+def pairs_round_of(sh):
+    """Round index of each pair of a round-major GPU pair list."""
+    r = np.zeros(sh["n_pairs"], np.int32)
+    for q in range(sh["n_rounds"]):
+        r[sh["ro"][q]:sh["ro"][q + 1]] = q
+    return r
+
+
+def c_ref(mass=6.63e-26, T=273.0):
+    return math.sqrt(2 * KB * T / mass)

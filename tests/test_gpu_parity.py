@@ -1,0 +1,338 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Integer and index work (sort, selection, rounds) must match bit for bit;
+floating point within the stated tolerances: FP64 paths 1e-12 relative,
+FP32 Jager chi 1e-5 relative (+1e-6 rad) on well-conditioned pairs, bf16
+MLP 2e-2 on normalised velocity; conservation after moment matching 1e-12.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2602_21244_gb300 import workloads as W
+
+from gpu_util import (KB, c_ref, ctx, cuda, gpu_step_pieces, host, pairs_round_of, sel_host,
+                      torch, w_bits_tensor)
+
+pytestmark = pytest.mark.gpu
+
+
+def _workloads():
+    return {
+        "couette": W.couette(),
+        "cavity40": W.cavity(nx=40, ny=40),
+        "hyper01": W.hypersonic(scale=0.1),
+    }
+
+
+WL = {}
+
+
+def wl(name):
+    if name not in WL:
+        WL[name] = _workloads()[name]
+    return WL[name]
+
+
+def oracle_sorted(w):
+    return O.sort_cells(w["cell_id"], w["vx"], w["vy"], w["vz"], w["n_cells"])
+
+
+# ------------------------------------------------------------------ tensor-core layout
+
+@pytest.mark.parametrize("N,K", [(16, 16), (128, 16), (16, 128), (128, 128), (256, 64)])
+def test_tc_selftest_matches_matmul(N, K):
+    T = torch()
+    rng = np.random.default_rng(N * 1000 + K)
+    A = rng.standard_normal((128, K))
+    B = rng.standard_normal((N, K))
+    Ab, Bb = W.bf16_bits(A), W.bf16_bits(B)
+    D = host(ctx().tc_selftest(w_bits_tensor(Ab), w_bits_tensor(Bb)))
+    ref = W.bf16_value(Ab) @ W.bf16_value(Bb).T
+    assert np.abs(D - ref).max() <= 1e-4 * np.abs(ref).max() + 1e-5
+    assert ctx().sync_status() == 0
+
+
+# ------------------------------------------------------------------ sort / moments
+
+@pytest.mark.parametrize("name", ["couette", "cavity40", "hyper01"])
+def test_sort_bit_exact(name):
+    w = wl(name)
+    perm, cs, sx, sy, sz = oracle_sorted(w)
+    C = ctx()
+    out = C.sort_cells(cuda(w["cell_id"]), cuda(w["vx"]), cuda(w["vy"]), cuda(w["vz"]), w["n_cells"])
+    assert C.sync_status() == 0
+    assert np.array_equal(host(out["perm"]), perm)
+    assert np.array_equal(host(out["cell_start"]), cs)
+    assert np.array_equal(host(out["svx"]), sx) and np.array_equal(host(out["svz"]), sz)
+
+
+def test_sort_edge_cases():
+    C = ctx()
+    T = torch()
+    rng = np.random.default_rng(5)
+    # big cell (> shared-memory capacity of the per-cell sort), empty cells, ragged tail
+    cid = np.concatenate([np.full(3000, 2), rng.integers(0, 7, 501), np.full(5, 6)]).astype(np.int32)
+    rng.shuffle(cid)
+    v = [rng.standard_normal(len(cid)) for _ in range(3)]
+    perm, cs, sx, _, _ = O.sort_cells(cid, *v, 9)
+    out = C.sort_cells(cuda(cid), *[cuda(x) for x in v], 9)
+    assert np.array_equal(host(out["perm"]), perm) and np.array_equal(host(out["cell_start"]), cs)
+    assert np.array_equal(host(out["svx"]), sx)
+    # no particles at all
+    e = T.zeros(0, dtype=T.int32, device="cuda")
+    ef = T.zeros(0, dtype=T.float64, device="cuda")
+    out = C.sort_cells(e, ef, ef, ef, 4)
+    assert host(out["cell_start"]).tolist() == [0, 0, 0, 0, 0]
+    assert C.sync_status() == 0
+    # a cell id out of range is reported on the device
+    bad = cuda(np.array([0, 1, 9], np.int32))
+    C.sort_cells(bad, *[cuda(np.zeros(3)) for _ in range(3)], 3)
+    assert C.sync_status() == -1
+    assert C.sync_status() == 0
+
+
+@pytest.mark.parametrize("name", ["couette", "hyper01"])
+def test_moments(name):
+    w = wl(name)
+    perm, cs, sx, sy, sz = oracle_sorted(w)
+    ref = O.cell_moments(cs, sx, sy, sz)
+    C = ctx()
+    mom = host(C.cell_moments(cuda(cs), cuda(sx), cuda(sy), cuda(sz)))
+    assert np.array_equal(mom[:, 0], ref[:, 0])
+    scale = np.maximum(ref[:, 0], 1)[:, None] * 3000.0
+    assert np.all(np.abs(mom[:, 1:4] - ref[:, 1:4]) <= 1e-13 * scale)
+    assert np.all(np.abs(mom[:, 4] - ref[:, 4]) <= 1e-12 * np.maximum(ref[:, 4], 1e-300))
+
+
+# ------------------------------------------------------------------ selection
+
+def _sgmax0(w, gas):
+    return O.sigma_g_max_init(gas, w["T_cell"], 5.0)
+
+
+@pytest.mark.parametrize("name,model", [("couette", 0), ("cavity40", 0), ("hyper01", 1), ("hyper01", 0)])
+def test_select_bit_exact(name, model):
+    w = dict(wl(name))
+    w["gas"] = dict(w["gas"], model=model)
+    gas = O.make_gas(**w["gas"])
+    perm, cs, sx, sy, sz = oracle_sorted(w)
+    sg0 = _sgmax0(w, gas)
+    ref = O.select_pairs(gas, cs, sx, sy, sz, sg0, 3, capacity=1 << 22)
+    _, srt, mom, sg, sel = gpu_step_pieces(w, sg0, step=3)
+    assert ctx().sync_status() == 0
+    sh = sel_host(sel)
+    assert sh["n_pairs"] == ref["n_pairs"] and sh["n_cand"] == ref["n_cand"]
+    assert sh["n_rounds"] == ref["n_rounds"]
+    p = sh["pairs"]
+    rr = pairs_round_of(sh)
+    order = np.lexsort((p[:, 3], p[:, 2]))
+    assert np.array_equal(p[order, 0], ref["i"]) and np.array_equal(p[order, 1], ref["j"])
+    assert np.array_equal(p[order, 2], ref["cell"]) and np.array_equal(p[order, 3], ref["m"])
+    assert np.array_equal(rr[order], ref["round"])
+    rel = np.abs(host(sg) - ref["sgmax"]) / ref["sgmax"]
+    assert rel.max() <= (0.0 if model == 1 else 4e-16)
+
+
+def test_select_capacity_overflow_reported():
+    w = wl("hyper01")
+    gas = O.make_gas(**w["gas"])
+    _, srt, mom, sg, sel = gpu_step_pieces(w, _sgmax0(w, gas), capacity=100)
+    assert ctx().sync_status() == -3
+    sh = sel_host(sel)
+    assert sh["n_pairs"] > 100 and sh["n_rounds"] == 0
+
+
+# ------------------------------------------------------------------ VHS + moment matching
+
+def _tol_v(v_ref, scale):
+    return 1e-12 * np.maximum(np.abs(v_ref), scale)
+
+
+@pytest.mark.parametrize("name", ["couette", "hyper01"])
+def test_collide_vhs_and_moment_match(name):
+    w = dict(wl(name))
+    w["gas"] = dict(w["gas"], model=0)
+    gas = O.make_gas(**w["gas"])
+    sg0 = _sgmax0(w, gas)
+    ref = O.step(gas, w["cell_id"], w["vx"], w["vy"], w["vz"], w["n_cells"], sg0, 2, path="vhs",
+                 capacity=1 << 22)
+    from paper_2602_21244_gb300 import dsmc as D
+    Dg, srt, mom, sg, sel = gpu_step_pieces(w, sg0, step=2)
+    C = ctx()
+    C.collide_vhs(Dg, 2, sel, srt["svx"], srt["svy"], srt["svz"])
+    C.moment_match(srt["cell_start"], mom, srt["svx"], srt["svy"], srt["svz"])
+    assert C.sync_status() == 0
+    scale = 3000.0
+    for a, b in zip((srt["svx"], srt["svy"], srt["svz"]), ("vx", "vy", "vz")):
+        got = host(a)
+        assert np.all(np.abs(got - ref[b]) <= _tol_v(ref[b], scale)), np.abs(got - ref[b]).max()
+    # conservation per cell after moment matching
+    m2 = O.cell_moments(ref["cell_start"], host(srt["svx"]), host(srt["svy"]), host(srt["svz"]))
+    m0 = ref["mom"]
+    n = np.maximum(m0[:, 0], 1)
+    assert np.all(np.abs(m2[:, 1:4] - m0[:, 1:4]) <= 1e-12 * n[:, None] * scale)
+    assert np.all(np.abs(m2[:, 4] - m0[:, 4]) <= 1e-12 * np.maximum(m0[:, 4], 1e-300))
+
+
+def test_full_step_vhs_multi_step():
+    from paper_2602_21244_gb300 import dsmc as D
+    T = torch()
+    w = wl("couette")
+    gas_o = O.make_gas(**w["gas"])
+    sg = _sgmax0(w, gas_o)
+    C = ctx()
+    st = D.StepState(C, len(w["cell_id"]), w["n_cells"], 1 << 16)
+    st.sigma_g_max.copy_(cuda(sg))
+    cid, vx, vy, vz = w["cell_id"], w["vx"], w["vy"], w["vz"]
+    path = D.make_path(D.PATH_VHS)
+    gas = D.make_gas(w["gas"])
+    total = 0
+    for s in range(20):
+        ref = O.step(gas_o, cid, vx, vy, vz, w["n_cells"], sg, s, path="vhs")
+        st.cell_id.copy_(cuda(cid)); st.vx.copy_(cuda(vx)); st.vy.copy_(cuda(vy)); st.vz.copy_(cuda(vz))
+        C.step(gas, path, st, s)
+        assert C.sync_status() == 0
+        assert np.array_equal(host(st.perm), ref["perm"])
+        assert st.info_host()["n_pairs"] == ref["pairs"]["n_pairs"]
+        total += ref["pairs"]["n_pairs"]
+        for a, b in ((st.svx, "vx"), (st.svy, "vy"), (st.svz, "vz")):
+            assert np.all(np.abs(host(a) - ref[b]) <= _tol_v(ref[b], 3000.0))
+        # continue from the oracle's state (sorted order, same cells)
+        cid = np.repeat(np.arange(w["n_cells"], dtype=np.int32), np.diff(ref["cell_start"]))
+        vx, vy, vz, sg = ref["vx"], ref["vy"], ref["vz"], ref["sgmax"]
+        st.sigma_g_max.copy_(cuda(sg))
+    assert total > 100
+
+
+# ------------------------------------------------------------------ Jager chi
+
+JP = W.JAGER_SYNTHETIC_AR
+
+
+def _gas_ar():
+    return dict(mass=W.M_AR, d_ref=4.17e-10, omega=0.81, T_ref=273.0, fn_over_vc=1.0, dt=1.0,
+                seed=0, model=1, b_max=1.2e-9)
+
+
+def test_chi_hard_sphere_closed_form():
+    from paper_2602_21244_gb300 import dsmc as D
+    b, g = W.chi_pairs(1 << 16, seed=3)
+    chi = host(ctx().jager_chi(D.make_gas(_gas_ar()), D.make_potential(W.HARD_SPHERE_AR), cuda(b),
+                               cuda(g), n_nodes=32))
+    bd = b.astype(np.float64)
+    want = np.where(bd < 3.6, 2 * np.arccos(np.minimum(bd / 3.6, 1.0)), 0.0)
+    assert np.abs(chi - want).max() <= 1e-5 * np.pi + 1e-6
+
+
+def _sensitivity(P, b, E, h=1e-4):
+    s1 = abs(O.chi(P, b * (1 + h), E) - O.chi(P, b * (1 - h), E)) / (2 * h)
+    s2 = abs(O.chi(P, b, E * (1 + h) ** 2) - O.chi(P, b, E * (1 - h) ** 2)) / (2 * h)
+    return s1 + s2
+
+
+@pytest.mark.parametrize("n_nodes", [32, 48])
+def test_chi_jager_parity_sampled(n_nodes):
+    from paper_2602_21244_gb300 import dsmc as D
+    b, g = W.chi_pairs(1 << 22, seed=0)
+    chi = host(ctx().jager_chi(D.make_gas(_gas_ar()), D.make_potential(JP), cuda(b), cuda(g),
+                               n_nodes=n_nodes))
+    assert ctx().sync_status() == 0
+    idx = np.random.default_rng(1).choice(len(b), 3000, replace=False)
+    P = O.make_pot(JP)
+    bad, ill = [], 0
+    for q in idx:
+        bq, E = float(b[q]), float(O.e_kelvin(W.M_AR, float(g[q])))
+        ref = O.chi(P, bq, E)
+        err = abs(chi[q] - ref)
+        if err > 1e-5 * abs(ref) + 1e-6:
+            if _sensitivity(P, bq, E) * 2.0 ** -24 > 1e-6:
+                ill += 1
+            else:
+                bad.append((bq, float(g[q]), ref, float(chi[q])))
+    assert not bad, bad[:5]
+    assert ill <= 3
+
+
+# ------------------------------------------------------------------ neural operator
+
+def _mlp_setup(d_in=8):
+    from paper_2602_21244_gb300 import dsmc as D
+    wts = W.mlp_weights(d_in=d_in)
+    bias = np.random.default_rng(7).standard_normal(len(wts["bias"])) * 0.05
+    bias = bias.astype(np.float32).astype(np.float64)
+    mlp_o = O.make_mlp(d_in, 128, 3, 3, 0, W.sigma_v(), 273.0, 1e-12)
+    mlp_d = D.make_mlp(d_in, 128, 3, 3, 0, W.sigma_v(), 273.0, 1e-12)
+    return wts, bias, mlp_o, mlp_d
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 1000, 4099])
+def test_mlp_forward_parity(n):
+    wts, bias, mlp_o, mlp_d = _mlp_setup()
+    x = np.random.default_rng(n).standard_normal((n, 8)) * 1.5
+    y = host(ctx().mlp_forward(mlp_d, w_bits_tensor(wts["W_bits"]), cuda(bias, torch().float32),
+                               cuda(x, torch().float32)))
+    assert ctx().sync_status() == 0
+    xr = x.astype(np.float32).astype(np.float64)
+    yb = O.mlp_forward(mlp_o, wts["W"], bias, xr, bf16=True)
+    y64 = O.mlp_forward(mlp_o, wts["W"], bias, xr, bf16=False)
+    sc = np.abs(y64).max()
+    assert np.abs(y - yb).max() <= 1e-2 * sc
+    assert np.abs(y - y64).max() <= 3e-2 * sc
+
+
+@pytest.mark.parametrize("name", ["cavity40"])
+def test_collide_neural_parity(name):
+    w = wl(name)
+    gas = O.make_gas(**w["gas"])
+    wts, bias, mlp_o, mlp_d = _mlp_setup()
+    sg0 = _sgmax0(w, gas)
+    perm, cs, sx, sy, sz = oracle_sorted(w)
+    mom = O.cell_moments(cs, sx, sy, sz)
+    pr = O.select_pairs(gas, cs, sx, sy, sz, sg0, 1, capacity=1 << 22)
+    refb = O.collide_neural(gas, mlp_o, wts["W"], bias, mom, pr, 1, sx, sy, sz, bf16=True)
+    ref64 = O.collide_neural(gas, mlp_o, wts["W"], bias, mom, pr, 1, sx, sy, sz, bf16=False)
+    Dg, srt, momg, sg, sel = gpu_step_pieces(w, sg0, step=1)
+    C = ctx()
+    C.collide_neural(Dg, mlp_d, w_bits_tensor(wts["W_bits"]), cuda(bias, torch().float32), 1, momg,
+                     sel, srt["svx"], srt["svy"], srt["svz"])
+    assert C.sync_status() == 0
+    sv = W.sigma_v()
+    for a, b in ((srt["svx"], 0), (srt["svy"], 1), (srt["svz"], 2)):
+        got = host(a)
+        assert np.abs(got - refb[b]).max() / sv <= 5e-3
+        assert np.abs(got - ref64[b]).max() / sv <= 2e-2
+    # pair energy conserved exactly by the projection
+    e0 = np.sum(sx ** 2 + sy ** 2 + sz ** 2)
+    e1 = np.sum(host(srt["svx"]) ** 2 + host(srt["svy"]) ** 2 + host(srt["svz"]) ** 2)
+    assert abs(e1 / e0 - 1) < 1e-12
+
+
+# ------------------------------------------------------------------ host-buffer step
+
+def test_step_host_matches_device_step():
+    from paper_2602_21244_gb300 import dsmc as D
+    T = torch()
+    w = wl("hyper01")
+    C = ctx()
+    gas = D.make_gas(w["gas"])
+    n, nc = len(w["cell_id"]), w["n_cells"]
+    st = D.StepState(C, n, nc, 1 << 20)
+    C.sigma_g_max_init(gas, cuda(w["T_cell"]), 5.0, out=st.sigma_g_max)
+    st.cell_id.copy_(cuda(w["cell_id"])); st.vx.copy_(cuda(w["vx"]))
+    st.vy.copy_(cuda(w["vy"])); st.vz.copy_(cuda(w["vz"]))
+    path = D.make_path(D.PATH_VHS)
+    C.step(gas, path, st, 0)
+    assert C.sync_status() == 0
+    C.reserve(n, nc, 1 << 20)
+    pin = lambda a: T.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    outs = [T.empty(n, dtype=T.float64).pin_memory() for _ in range(3)]
+    perm = T.empty(n, dtype=T.int32).pin_memory()
+    npairs = C.step_host(gas, path, pin(w["cell_id"]), pin(w["vx"]), pin(w["vy"]), pin(w["vz"]),
+                         pin(w["T_cell"]), 0, perm, *outs)
+    assert npairs == st.info_host()["n_pairs"]
+    assert np.array_equal(perm.numpy(), host(st.perm))
+    for o, a in zip(outs, (st.svx, st.svy, st.svz)):
+        assert np.array_equal(o.numpy(), host(a))

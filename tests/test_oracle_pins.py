@@ -427,8 +427,10 @@ def test_mlp_forward_matches_torch_sequential():
     y = O.mlp_forward(mlp, wts["W"], wts["bias"] + 0.01, x)
     ref = net(torch.tensor(x)).detach().numpy()
     np.testing.assert_allclose(y, ref, rtol=1e-12, atol=1e-13)
-    # bf16 mode: inputs and hidden activations rounded to bf16
-    h = torch.tensor(x).to(torch.bfloat16).double()
+    # bf16 mode: input as two bf16 terms, hidden activations rounded to bf16
+    xt = torch.tensor(x)
+    hi = xt.to(torch.bfloat16).double()
+    h = hi + (xt - hi).to(torch.bfloat16).double()
     for l in range(4):
         h = layers[2 * l](h)
         if l < 3:
