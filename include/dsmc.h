@@ -222,12 +222,15 @@ int dsmc_collide_jager(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_potent
  *  if ||y|| <= eps), v_r' = |v_r| u, centre-of-mass update in FP64.
  *  weights_bf16: each layer's row-major [out x in] matrix, concatenated;
  *  biases: each layer's bias (FP32), concatenated.  Requires width 128,
- *  d_out 3, d_in <= 16. */
+ *  d_out 3, d_in 6 or 8, 1..4 hidden layers.  The MLP input enters the
+ *  first layer as two bf16 terms (hi + lo) sharing the first layer's weights.
+ *  u_out (optional, may be NULL) receives each pair's unit direction u
+ *  (FP32 [n_pairs x 3], pair order). */
 int dsmc_collide_neural(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_mlp_t* mlp,
                         const uint16_t* weights_bf16, const float* biases, uint64_t step,
                         const double* mom_pre, const int32_t* pairs,
                         const int32_t* round_offsets, const dsmc_select_info_t* info,
-                        double* vx, double* vy, double* vz, void* stream);
+                        double* vx, double* vy, double* vz, float* u_out, void* stream);
 
 /* The MLP alone on the tensor cores: y[n x 3] = f_theta(x[n x d_in]) with x
  * and y FP32 row-major (x rounded to bf16 on the way in), same weight
@@ -241,6 +244,14 @@ int dsmc_mlp_forward(dsmc_ctx_t* ctx, const dsmc_mlp_t* mlp, const uint16_t* wei
  * N a multiple of 16 in [16, 256], K a multiple of 16 in [16, 128]. */
 int dsmc_tc_selftest(dsmc_ctx_t* ctx, int32_t N, int32_t K, const uint16_t* A, const uint16_t* B,
                      float* D, void* stream);
+
+/* Diagnostic with no counterpart in the paper (failure detection): runs a
+ * kernel whose bounded wait can never be satisfied -- which 0: a grid
+ * barrier that one block never reaches; which 1: an mbarrier that no
+ * tensor-core commit completes -- so that the wait runs out after limit_ns
+ * (at most 2 s) and records DSMC_ERR_TIMEOUT in the status word.  Nothing
+ * traps or spins without bound; the context stays usable. */
+int dsmc_selftest_timeout(dsmc_ctx_t* ctx, int32_t which, uint64_t limit_ns, void* stream);
 
 /* ---------------------------------------------------------------- moment matching */
 

@@ -95,7 +95,7 @@ def lib():
             "or_noise4": (None, [u64, i32, i32, u64, vp]),
             "or_neural_features": (None, [P(Mlp), vp, d, vp, vp]),
             "or_collide_neural": (None, [P(Gas), P(Mlp), vp, vp, vp, i64, vp, vp, vp, vp, u64,
-                                         C.c_int, vp, vp, vp]),
+                                         C.c_int, vp, vp, vp, vp]),
             "or_harvest_jager": (None, [P(Gas), P(Pot), i64, vp, vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
@@ -315,12 +315,15 @@ def noise4(seed, cell, m, step) -> np.ndarray:
 
 
 def collide_neural(gas: Gas, mlp: Mlp, W, bias, mom_pre, pairs: dict, step, vx, vy, vz,
-                   bf16=False):
+                   bf16=False, want_u=False):
     vx, vy, vz = _f64(vx).copy(), _f64(vy).copy(), _f64(vz).copy()
+    u = np.zeros((max(pairs["n_pairs"], 1), 3))
     lib().or_collide_neural(C.byref(gas), C.byref(mlp), _p(_f64(W)), _p(_f64(bias)),
                             _p(_f64(mom_pre)), pairs["n_pairs"], _p(pairs["i"]), _p(pairs["j"]),
                             _p(pairs["cell"]), _p(pairs["m"]), step, int(bf16),
-                            _p(vx), _p(vy), _p(vz))
+                            _p(vx), _p(vy), _p(vz), _p(u))
+    if want_u:
+        return vx, vy, vz, u[:pairs["n_pairs"]]
     return vx, vy, vz
 
 

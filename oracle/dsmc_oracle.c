@@ -649,12 +649,13 @@ void or_neural_features(const or_mlp_t* d, const double vr[3], double T_cell,
 }
 
 /* Neural collision: features, MLP, projection (reading R6), CM update,
- * pairs in order.  T_cell of a cell = m Theta_pre / (3 k_B N). */
+ * pairs in order.  T_cell of a cell = m Theta_pre / (3 k_B N).  u_out
+ * (optional) receives each pair's unit direction. */
 void or_collide_neural(const or_gas_t* gs, const or_mlp_t* d, const double* W,
                        const double* bias, const double* mom_pre, int64_t n_pairs,
                        const int32_t* pi, const int32_t* pj, const int32_t* pcell,
                        const int32_t* pm, uint64_t step, int bf16, double* vx,
-                       double* vy, double* vz) {
+                       double* vy, double* vz, double* u_out) {
   for (int64_t p = 0; p < n_pairs; ++p) {
     int32_t i = pi[p], j = pj[p], k = pcell[p];
     double vr[3] = {vx[i] - vx[j], vy[i] - vy[j], vz[i] - vz[j]};
@@ -668,6 +669,7 @@ void or_collide_neural(const or_gas_t* gs, const or_mlp_t* d, const double* W,
     double e[3];
     if (ny > d->eps) { e[0] = y[0] / ny; e[1] = y[1] / ny; e[2] = y[2] / ny; }
     else iso_dir(gs->seed, k, pm[p], step, e);
+    if (u_out) { u_out[3 * p] = e[0]; u_out[3 * p + 1] = e[1]; u_out[3 * p + 2] = e[2]; }
     double vrp[3] = {g * e[0], g * e[1], g * e[2]};
     pair_update(vx, vy, vz, i, j, vrp);
   }

@@ -210,14 +210,14 @@ int dsmc_collide_neural(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_mlp_t* 
                         const uint16_t* w, const float* bias, uint64_t step,
                         const double* mom_pre, const int32_t* pairs,
                         const int32_t* round_offsets, const dsmc_select_info_t* info,
-                        double* vx, double* vy, double* vz, void* stream) {
+                        double* vx, double* vy, double* vz, float* u_out, void* stream) {
   CHECK_CTX(c);
   REQUIRE(c, gas, "collide_neural: null gas");
   if (int rc = check_mlp(c, mlp)) return rc;
   REQUIRE(c, w && bias && mom_pre && round_offsets && info && vx && vy && vz,
           "collide_neural: null pointer");
   return dsmc::launch_collide_neural(c, *gas, *mlp, w, bias, step, mom_pre, pairs, round_offsets,
-                                     info, vx, vy, vz, S(stream));
+                                     info, vx, vy, vz, u_out, S(stream));
 }
 
 int dsmc_mlp_forward(dsmc_ctx_t* c, const dsmc_mlp_t* mlp, const uint16_t* w, const float* bias,
@@ -235,6 +235,14 @@ int dsmc_tc_selftest(dsmc_ctx_t* c, int32_t N, int32_t K, const uint16_t* A, con
           "tc_selftest: N in [16,256], K in [16,128], multiples of 16");
   REQUIRE(c, A && B && D, "tc_selftest: null pointer");
   return dsmc::launch_tc_selftest(c, N, K, A, B, D, S(stream));
+}
+
+int dsmc_selftest_timeout(dsmc_ctx_t* c, int32_t which, uint64_t limit_ns, void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, (which == 0 || which == 1) && limit_ns > 0 && limit_ns <= 2000000000ull,
+          "selftest_timeout: which 0|1, 0 < limit_ns <= 2e9");
+  return which == 0 ? dsmc::launch_selftest_barrier(c, limit_ns, S(stream))
+                    : dsmc::launch_selftest_mbar(c, limit_ns, S(stream));
 }
 
 int dsmc_moment_match(dsmc_ctx_t* c, int32_t n_cells, const int32_t* cell_start,
@@ -289,7 +297,7 @@ int dsmc_step(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t* path,
     case DSMC_PATH_NEURAL:
       rc = dsmc_collide_neural(c, gas, path->mlp, path->weights_bf16, path->biases, step, B->mom,
                                B->pairs, B->round_offsets, B->info, B->svx, B->svy, B->svz,
-                               stream);
+                               nullptr, stream);
       break;
     default:
       return dsmc::record(c, DSMC_ERR_ARG, "step: unknown path");

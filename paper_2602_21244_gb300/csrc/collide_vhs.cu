@@ -68,4 +68,25 @@ int launch_collide_vhs(Ctx* c, const dsmc_gas_t& gas, uint64_t step, const int32
   return 0;
 }
 
+// Failure-detection self test: every block but block 0 enters the grid
+// barrier; block 0 never arrives, so the others' bounded waits run out and
+// record DSMC_ERR_TIMEOUT.  No trap, no unbounded spin.
+__global__ void k_selftest_barrier(unsigned* bar, int* status, uint64_t limit_ns) {
+  if (blockIdx.x == 0) return;
+  grid_barrier(bar, status, limit_ns);
+}
+
+int launch_selftest_timeout(Ctx* c, int which, uint64_t limit_ns, cudaStream_t s);
+
+int launch_selftest_barrier(Ctx* c, uint64_t limit_ns, cudaStream_t s) {
+  if (cudaMemsetAsync(barrier_ptr(c), 0, 4 * sizeof(unsigned), s) != cudaSuccess) return DSMC_ERR_CUDA;
+  unsigned* bar = barrier_ptr(c);
+  int* st = status_ptr(c);
+  void* args[] = {&bar, &st, &limit_ns};
+  if (cudaLaunchCooperativeKernel((const void*)k_selftest_barrier, dim3(4), dim3(32), args, 0, s) != cudaSuccess)
+    return record(c, DSMC_ERR_CUDA, "selftest_barrier: launch failed");
+  count_launches(c, 1);
+  return 0;
+}
+
 }  // namespace dsmc

@@ -159,13 +159,15 @@ int launch_collide_neural(Ctx* c, const dsmc_gas_t& gas, const dsmc_mlp_t& mlp,
                           const uint16_t* w, const float* bias, uint64_t step,
                           const double* mom, const int32_t* pairs, const int32_t* ro,
                           const dsmc_select_info_t* info, double* vx, double* vy, double* vz,
-                          cudaStream_t s);
+                          float* u_out, cudaStream_t s);
 
 int launch_mlp_forward(Ctx* c, const dsmc_mlp_t& mlp, const uint16_t* w, const float* bias,
                        int64_t n, const float* x, float* y, cudaStream_t s);
 int launch_tc_selftest(Ctx* c, int N, int K, const uint16_t* A, const uint16_t* B, float* D,
                        cudaStream_t s);
 int cooperative_blocks(Ctx* c, const void* kernel, int threads, size_t smem);
+int launch_selftest_barrier(Ctx* c, uint64_t limit_ns, cudaStream_t s);
+int launch_selftest_mbar(Ctx* c, uint64_t limit_ns, cudaStream_t s);
 
 // exclusive scan of int32 counts -> offsets[n+1] (offsets[n] = total)
 size_t scan_ws(int64_t n);

@@ -85,8 +85,7 @@ __device__ void load_weights(char* smem, const MlpLayout& L, const MlpShape& sh,
 
 __device__ __forceinline__ float act_f(int act, float z) {
   if (act == 1) return fmaxf(z, 0.f);
-  const float h = 0.5f * z;                 // SiLU(z) = z sigmoid(z) = h + h tanh(h)
-  return fmaf(h, tc::tanh_approx(h), h);
+  return __fdividef(z, 1.f + __expf(-z));   // SiLU(z) = z / (1 + e^-z)
 }
 
 // Run all layers on the X tile already in shared memory (fenced and
@@ -282,6 +281,7 @@ struct NeuralArgs {
   uint64_t seed, step;
   double sigma_v_inv, T_ref_inv, m_over_3k, eps;
   const double* mom;
+  float* u_out;
   const int4* pairs;
   const int32_t* ro;
   const dsmc_select_info_t* info;
@@ -359,6 +359,7 @@ __global__ void __launch_bounds__(kTileM) k_collide_neural(MlpShape sh, const ui
           sincos(2.0 * DSMC_PI * u53(wi.z, wi.w), &se, &ce);
           e0 = c; e1 = s * ce; e2 = s * se;
         }
+        if (a.u_out) { a.u_out[3 * (size_t)p] = (float)e0; a.u_out[3 * (size_t)p + 1] = (float)e1; a.u_out[3 * (size_t)p + 2] = (float)e2; }
         const double rx = g * e0, ry = g * e1, rz = g * e2;
         const double cx = 0.5 * (xi + xj), cy = 0.5 * (yi + yj), cz = 0.5 * (zi + zj);
         __stcg(a.vx + q.x, cx + 0.5 * rx); __stcg(a.vy + q.x, cy + 0.5 * ry); __stcg(a.vz + q.x, cz + 0.5 * rz);
@@ -368,6 +369,23 @@ __global__ void __launch_bounds__(kTileM) k_collide_neural(MlpShape sh, const ui
     if (alive && r + 1 < R && !grid_barrier(a.bar, a.status, kBarrierLimitNs)) alive = false;
   }
   cta_teardown(tmem);
+}
+
+// Failure-detection self test: wait on an mbarrier that no MMA commit will
+// ever complete; the bounded wait must record DSMC_ERR_TIMEOUT and return.
+__global__ void k_selftest_mbar(int* status, uint64_t limit_ns) {
+  __shared__ __align__(8) uint64_t mbar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&mbar, 1);
+    tc::mbar_fence_init();
+    tc::mbar_wait(&mbar, 0, status, limit_ns);
+  }
+}
+
+int launch_selftest_mbar(Ctx* c, uint64_t limit_ns, cudaStream_t s) {
+  k_selftest_mbar<<<1, 32, 0, s>>>(status_ptr(c), limit_ns);
+  count_launches(c, 1);
+  return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
 }
 
 int cooperative_blocks(Ctx* c, const void* kernel, int threads, size_t smem);
@@ -380,7 +398,7 @@ int launch_collide_neural(Ctx* c, const dsmc_gas_t& gas, const dsmc_mlp_t& mlp,
                           const uint16_t* w, const float* bias, uint64_t step,
                           const double* mom, const int32_t* pairs, const int32_t* ro,
                           const dsmc_select_info_t* info, double* vx, double* vy, double* vz,
-                          cudaStream_t s) {
+                          float* u_out, cudaStream_t s) {
   if (mlp.n_hidden > kMaxHidden) return record(c, DSMC_ERR_UNSUPPORTED, "collide_neural: n_hidden > 4");
   const MlpShape sh{mlp.d_in, mlp.n_hidden, mlp.act};
   const MlpLayout L = mlp_layout(sh.n_hidden);
@@ -392,7 +410,7 @@ int launch_collide_neural(Ctx* c, const dsmc_gas_t& gas, const dsmc_mlp_t& mlp,
   a.seed = gas.seed; a.step = step;
   a.sigma_v_inv = 1.0 / mlp.sigma_v; a.T_ref_inv = 1.0 / mlp.T_ref;
   a.m_over_3k = gas.mass / (3.0 * DSMC_KB); a.eps = mlp.eps;
-  a.mom = mom; a.pairs = (const int4*)pairs; a.ro = ro; a.info = info;
+  a.mom = mom; a.u_out = u_out; a.pairs = (const int4*)pairs; a.ro = ro; a.info = info;
   a.vx = vx; a.vy = vy; a.vz = vz; a.bar = barrier_ptr(c); a.status = status_ptr(c);
   if (cudaMemsetAsync(a.bar, 0, 4 * sizeof(unsigned), s) != cudaSuccess) return DSMC_ERR_CUDA;
   void* args[] = {(void*)&sh, (void*)&w, (void*)&bias, (void*)&a};

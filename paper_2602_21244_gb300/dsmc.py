@@ -107,9 +107,10 @@ def load(build: bool = True):
             "dsmc_collide_jager": (C.c_int, [vp, P(Gas), P(Potential), i32, u64, vp, vp, vp, vp, vp,
                                              vp, vp, vp]),
             "dsmc_collide_neural": (C.c_int, [vp, P(Gas), P(Mlp), vp, vp, u64, vp, vp, vp, vp, vp, vp,
-                                              vp, vp]),
+                                              vp, vp, vp]),
             "dsmc_mlp_forward": (C.c_int, [vp, P(Mlp), vp, vp, i64, vp, vp, vp]),
             "dsmc_tc_selftest": (C.c_int, [vp, i32, i32, vp, vp, vp, vp]),
+            "dsmc_selftest_timeout": (C.c_int, [vp, i32, u64, vp]),
             "dsmc_moment_match": (C.c_int, [vp, i32, vp, vp, vp, vp, vp, vp]),
             "dsmc_step_workspace_size": (sz, [i32, i32, i64]),
             "dsmc_step": (C.c_int, [vp, P(Gas), P(Path), P(StepBuffers), u64, vp]),
@@ -285,12 +286,12 @@ class Context:
             _stream(stream)), "collide_jager")
 
     def collide_neural(self, gas: Gas, mlp: Mlp, w_bits, bias, step, mom, sel, vx, vy, vz,
-                       stream=None):
+                       u_out=None, stream=None):
         self._check(self._lib.dsmc_collide_neural(
             self.h, C.byref(gas), C.byref(mlp), _ptr(w_bits, torch.int16), _ptr(bias, torch.float32),
             step, _ptr(mom, torch.float64), _ptr(sel["pairs"]), _ptr(sel["round_offsets"]),
             _ptr(sel["info"]), _ptr(vx, torch.float64), _ptr(vy, torch.float64),
-            _ptr(vz, torch.float64), _stream(stream)), "collide_neural")
+            _ptr(vz, torch.float64), _ptr(u_out, torch.float32), _stream(stream)), "collide_neural")
 
     def mlp_forward(self, mlp: Mlp, w_bits, bias, x, y=None, stream=None):
         n = x.shape[0]
@@ -309,6 +310,10 @@ class Context:
                                                _ptr(B_bits, torch.int16), _ptr(D), _stream(stream)),
                     "tc_selftest")
         return D
+
+    def selftest_timeout(self, which: int, limit_ns: int = 10_000_000, stream=None):
+        self._check(self._lib.dsmc_selftest_timeout(self.h, which, limit_ns, _stream(stream)),
+                    "selftest_timeout")
 
     def moment_match(self, cell_start, mom_pre, vx, vy, vz, stream=None):
         self._check(self._lib.dsmc_moment_match(self.h, cell_start.numel() - 1,
