@@ -145,6 +145,33 @@ int dsmc_sort_cells(dsmc_ctx_t* ctx, int32_t n, int32_t n_cells, const int32_t* 
                     int32_t* cell_start, double* svx, double* svy, double* svz, void* ws,
                     size_t ws_bytes, void* stream);
 
+/* Allocation-free variant of dsmc_sort_cells; the paper has no counterpart.
+ * For callers that cannot allocate device memory at the point of the call:
+ * a solver that reserved all of the GPU's memory for its particle arrays up
+ * front, code that runs where cudaMalloc is not allowed or would stall the
+ * device (it can synchronise), or a host that hands the library only the
+ * arrays it owns.  It needs no context and no workspace: its scratch is one
+ * file-scope device array of about 5.2 MB that every GPU loading this
+ * library holds until the process exits, so it sorts at most
+ * DSMC_STATIC_SORT_MAX_N particles into at most DSMC_STATIC_SORT_MAX_CELLS
+ * cells and returns DSMC_ERR_UNSUPPORTED for anything larger.
+ *  - Arguments and results as dsmc_sort_cells (device pointers, caller-owned;
+ *    same stable order, bit for bit).  `status` (optional device int, may be
+ *    NULL) receives DSMC_ERR_ARG if a cell id is out of range; it must be
+ *    zeroed by the caller beforehand.
+ *  - The call makes no cudaMalloc/cudaFree and calls no allocating library
+ *    routine.  Its first call on a device looks up the scratch array's
+ *    device address with that device current (cudaGetSymbolAddress); make
+ *    that first call before any stream capture.
+ *  - Every call shares the one array: calls that overlap on the GPU (two
+ *    streams, two host threads) race and corrupt each other's result.
+ *    Serialise them on one stream. */
+#define DSMC_STATIC_SORT_MAX_N (1 << 20)
+#define DSMC_STATIC_SORT_MAX_CELLS (1 << 18)
+int dsmc_sort_cells_static(int32_t n, int32_t n_cells, const int32_t* cell_id, const double* vx,
+                           const double* vy, const double* vz, int32_t* perm, int32_t* cell_start,
+                           double* svx, double* svy, double* svz, int* status, void* stream);
+
 /* Per-cell moments of sorted velocities, two FP64 passes:
  * mom[5k..5k+4] = {N, sum vx, sum vy, sum vz, Theta = sum |v - u|^2},
  * u = sum v / N.  Non-finite velocities record DSMC_ERR_NONFINITE. */

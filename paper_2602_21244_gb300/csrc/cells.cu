@@ -301,3 +301,84 @@ int launch_moment_match(Ctx* c, int32_t n_cells, const int32_t* cs, const double
 }
 
 }  // namespace dsmc
+
+// ---------------------------------------------------------------- allocation-free sort
+// A variant of the cell sort for callers that cannot allocate device memory.
+// Its scratch (per-cell counters, the unsorted slot array, the scan's block
+// sums and a spare status word) is one file-scope device array, so the call
+// itself allocates nothing; every GPU that loads this library holds the
+// array until the process exits.
+#include <mutex>
+
+namespace dsmc {
+
+constexpr size_t kStaticCountsBytes = sizeof(int32_t) * (size_t)DSMC_STATIC_SORT_MAX_CELLS;
+constexpr size_t kStaticSlotsBytes = sizeof(int32_t) * (size_t)DSMC_STATIC_SORT_MAX_N;
+constexpr size_t kStaticScanBytes =
+    sizeof(int32_t) * (size_t)((DSMC_STATIC_SORT_MAX_CELLS + kScanItems - 1) / kScanItems + 1);
+constexpr size_t kStaticScanSlot = 512;  // block sums of the scan
+constexpr size_t kStaticScratchBytes = kStaticCountsBytes + kStaticSlotsBytes + kStaticScanSlot + 256;
+
+static __device__ __align__(256) unsigned char g_sort_scratch[kStaticScratchBytes];
+
+namespace {
+constexpr int kMaxDevices = 64;
+struct StaticSortDevice {
+  unsigned char* scratch = nullptr;  // device address of g_sort_scratch on this device
+  int sms = 0;
+};
+StaticSortDevice g_static_dev[kMaxDevices];
+std::mutex g_static_mu;
+}  // namespace
+
+// Once per device, with that device current: the device address of the
+// scratch array (in host code its name only stands for the symbol) and the
+// SM count used to size the grids.
+static int static_sort_setup(int dev, StaticSortDevice** out) {
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  StaticSortDevice& d = g_static_dev[dev];
+  if (!d.scratch) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_sort_scratch) != cudaSuccess || !ptr) return DSMC_ERR_CUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      return DSMC_ERR_CUDA;
+    d.sms = sms;
+    d.scratch = (unsigned char*)ptr;
+  }
+  *out = &d;
+  return 0;
+}
+
+}  // namespace dsmc
+
+extern "C" int dsmc_sort_cells_static(int32_t n, int32_t n_cells, const int32_t* cell_id,
+                                      const double* vx, const double* vy, const double* vz,
+                                      int32_t* perm, int32_t* cell_start, double* svx,
+                                      double* svy, double* svz, int* status, void* stream) {
+  using namespace dsmc;
+  if (n < 0 || n_cells < 1 || !cell_start) return DSMC_ERR_ARG;
+  if (n > DSMC_STATIC_SORT_MAX_N || n_cells > DSMC_STATIC_SORT_MAX_CELLS) return DSMC_ERR_UNSUPPORTED;
+  if (n > 0 && !(cell_id && vx && vy && vz && perm && svx && svy && svz)) return DSMC_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DSMC_ERR_CUDA;
+  StaticSortDevice* d = nullptr;
+  if (int rc = static_sort_setup(dev, &d)) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t* counts = (int32_t*)d->scratch;
+  int32_t* slots = (int32_t*)(d->scratch + kStaticCountsBytes);
+  int32_t* scan = (int32_t*)(d->scratch + kStaticCountsBytes + kStaticSlotsBytes);
+  int* st = status ? status : (int*)(d->scratch + kStaticCountsBytes + kStaticSlotsBytes + kStaticScanSlot);
+  static_assert(kStaticScanBytes <= kStaticScanSlot, "scan block sums must fit their slot");
+  // the counters must start at zero on every call (the array keeps the last call's contents)
+  if (cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)n_cells, s) != cudaSuccess) return DSMC_ERR_CUDA;
+  if (n > 0) k_hist<<<grid_for(n, 256, d->sms * 16), 256, 0, s>>>(cell_id, n, n_cells, counts, st);
+  if (int rc = launch_scan(nullptr, counts, cell_start, n_cells, scan, s)) return rc;
+  if (n > 0) {
+    if (cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)n_cells, s) != cudaSuccess) return DSMC_ERR_CUDA;
+    k_scatter<<<grid_for(n, 256, d->sms * 16), 256, 0, s>>>(cell_id, n, n_cells, cell_start, counts, slots);
+    k_fix_gather<<<grid_for(n_cells, kFixWarps, d->sms * 4), kFixWarps * 32, 0, s>>>(
+        n_cells, cell_start, slots, perm, vx, vy, vz, svx, svy, svz);
+  }
+  return cudaGetLastError() == cudaSuccess ? DSMC_OK : DSMC_ERR_CUDA;
+}

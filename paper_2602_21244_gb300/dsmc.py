@@ -97,6 +97,7 @@ def load(build: bool = True):
             "dsmc_ctx_launch_count": (i64, [vp]),
             "dsmc_sort_workspace_size": (sz, [i32, i32]),
             "dsmc_sort_cells": (C.c_int, [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
+            "dsmc_sort_cells_static": (C.c_int, [i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
             "dsmc_cell_moments": (C.c_int, [vp, i32, vp, vp, vp, vp, vp, vp]),
             "dsmc_sigma_g_max_init": (C.c_int, [vp, P(Gas), i32, vp, d, vp, vp]),
             "dsmc_select_workspace_size": (sz, [i32, i32, i64]),
@@ -351,6 +352,33 @@ class Context:
             hp(T_cell), step, hp(perm), hp(svx), hp(svy), hp(svz), C.byref(npairs), _stream(stream)),
             "step_host")
         return npairs.value
+
+
+STATIC_SORT_MAX_N, STATIC_SORT_MAX_CELLS = 1 << 20, 1 << 18
+
+
+def sort_cells_static(cell_id, vx, vy, vz, n_cells, out=None, status=None, stream=None):
+    """Allocation-free cell sort (dsmc_sort_cells_static): no context, no
+    workspace; at most STATIC_SORT_MAX_N particles and STATIC_SORT_MAX_CELLS
+    cells.  Output tensors may be passed in ``out`` so that nothing is
+    allocated around the call either."""
+    L = load()
+    n = cell_id.numel()
+    dev = cell_id.device
+    if out is None:
+        out = dict(perm=torch.empty(n, dtype=torch.int32, device=dev),
+                   cell_start=torch.empty(n_cells + 1, dtype=torch.int32, device=dev),
+                   svx=torch.empty(n, dtype=torch.float64, device=dev),
+                   svy=torch.empty(n, dtype=torch.float64, device=dev),
+                   svz=torch.empty(n, dtype=torch.float64, device=dev))
+    f64 = torch.float64
+    rc = L.dsmc_sort_cells_static(n, n_cells, _ptr(cell_id, torch.int32), _ptr(vx, f64), _ptr(vy, f64),
+                                  _ptr(vz, f64), _ptr(out["perm"]), _ptr(out["cell_start"]),
+                                  _ptr(out["svx"]), _ptr(out["svy"]), _ptr(out["svz"]),
+                                  _ptr(status, torch.int32), _stream(stream))
+    if rc != 0:
+        raise DsmcError(rc, "dsmc_sort_cells_static")
+    return out
 
 
 class StepState:
