@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--n-nodes", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-standalone", dest="standalone", action="store_false")
     return ap.parse_args()
 
 
@@ -189,6 +190,42 @@ def run_gb300(args, rank, world, dist):
             step_ms_total=step_ms, pairs_total=pairs)
         if path == "neural":
             neural_kernel = dict(ms=phase_ms["collide"] / K, pairs=pairs / K)
+    # ------------------------------------------------------------ standalone kernels
+    # Jager deflection-angle batch (2^22 pairs) and the MLP alone (2^22 rows)
+    extra = {}
+    if args.standalone:
+        nb = 1 << 22
+        b_np, g_np = W.chi_pairs(nb, seed=0)
+        bt, gt = torch.from_numpy(b_np).to(dev), torch.from_numpy(g_np).to(dev)
+        chi = torch.empty_like(bt)
+        gas1 = D.make_gas(dict(wl["gas"], model=1))
+        for _ in range(2):
+            C.jager_chi(gas1, pot, bt, gt, n_nodes=args.n_nodes, chi=chi)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            C.jager_chi(gas1, pot, bt, gt, n_nodes=args.n_nodes, chi=chi)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        extra["chi_batch"] = dict(pairs=nb, ms=ms, chi_per_s=nb / (ms * 1e-3), n_nodes=args.n_nodes)
+        x = torch.randn((nb, 8), dtype=torch.float32, device=dev)
+        y = torch.empty((nb, 3), dtype=torch.float32, device=dev)
+        for _ in range(2):
+            C.mlp_forward(mlp, w_bits, bias, x, y)
+        e0.record(stream)
+        for _ in range(3):
+            C.mlp_forward(mlp, w_bits, bias, x, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        pk = peaks()
+        peak = pk.get("bf16_tflops") if pk else 1900.0
+        tf = nb * MLP_FLOP_PER_PAIR / (ms * 1e-3) / 1e12
+        extra["mlp_forward"] = dict(rows=nb, ms=ms, rows_per_s=nb / (ms * 1e-3), tflops=tf,
+                                    frac_of_bf16_peak=tf / peak)
+        if C.sync_status() != 0:
+            raise RuntimeError("device status after standalone kernels")
     # ------------------------------------------------------------ e2e (host buffers)
     e2e = None
     if not args.no_e2e and "neural" in results:
@@ -210,7 +247,7 @@ def run_gb300(args, rank, world, dist):
         dt = time.perf_counter() - t0
         e2e = dict(value=tot / dt, unit="pair collisions/s",
                    h2d_bytes_per_step=n * (4 + 24), d2h_bytes_per_step=n * (4 + 24) + 24)
-    return wl, n, nc, results, neural_kernel, e2e
+    return wl, n, nc, results, neural_kernel, e2e, extra
 
 
 # ---------------------------------------------------------------------------- oracle arm
@@ -274,7 +311,7 @@ def main():
     if dist is not None:
         dist.barrier()
     clk.start()
-    wl, n, nc, results, nk, e2e = run_gb300(args, rank, world, dist)
+    wl, n, nc, results, nk, e2e, extra = run_gb300(args, rank, world, dist)
     clocks = clk.stop()
     head = results.get("neural") or next(iter(results.values()))
     head_path = "neural" if "neural" in results else next(iter(results))
@@ -304,7 +341,7 @@ def main():
                 "config": {"workload": f"hypersonic argon gas {wl['name']}, {n} particles, {nc} cells",
                            "path": head_path, "l2": "pristine 258 MB input copied back before every step",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
-                "paths": results, "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
+                "paths": results, "standalone": extra, "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
                 "gpu_launches": int(sum(r["gpu_launches"] for r in results.values())),
                 "clocks": clocks}
         print(json.dumps(line), flush=True)

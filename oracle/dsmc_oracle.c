@@ -586,8 +586,8 @@ static double act_f(int act, double z) {
 /* Plain layer-by-layer forward of one sample.  W holds each layer's
  * row-major [out x in] matrix, one after another; bias likewise.  With
  * bf16 != 0 the storage precision of a bf16 tensor-core kernel is
- * emulated: the input as the sum of two bf16 terms (hi = bf16(x),
- * lo = bf16(x - hi)) and every hidden activation rounded to bf16. */
+ * emulated: the input and every hidden activation are held as the sum of
+ * two bf16 terms (hi = bf16(a), lo = bf16(a - hi)). */
 void or_mlp_forward1(const or_mlp_t* d, const double* W, const double* bias,
                      const double* x, int bf16, double* y) {
   double h[1024], z[1024];
@@ -613,7 +613,12 @@ void or_mlp_forward1(const or_mlp_t* d, const double* W, const double* bias,
     if (l == d->n_hidden) { for (int o = 0; o < n_out; ++o) y[o] = z[o]; break; }
     for (int o = 0; o < n_out; ++o) {
       double a = act_f(d->act, z[o]);
-      h[o] = bf16 ? or_bf16_round(a) : a;
+      if (bf16) {
+        double hi = or_bf16_round(a);
+        h[o] = hi + or_bf16_round(a - hi);
+      } else {
+        h[o] = a;
+      }
     }
     n_in = n_out;
   }

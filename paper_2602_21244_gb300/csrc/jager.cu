@@ -46,7 +46,8 @@ struct PotDev {
 
 // ---------------------------------------------------------------- FP64 potential
 // Direct evaluation of V and V' (FP64 has the digits to spare).
-__host__ __device__ inline double V64(const PotDev& P, double r, double* dV) {
+__host__ __device__ inline double V64(const PotDev& P, double r, double* dV, double* rep_out = nullptr,
+                                      double* ex_out = nullptr) {
   if (P.kind == 2) {
     const double v = P.kappa * pow(r, -P.p);
     *dV = -P.p * v / r;
@@ -72,6 +73,8 @@ __host__ __device__ inline double V64(const PotDev& P, double r, double* dV) {
     ddisp += P.C[n - 3] * (P.beta * fp * ir2n - 2.0 * n * f * ir2n * ir);
     ir2n *= ir * ir;
   }
+  if (rep_out) *rep_out = rep;
+  if (ex_out) *ex_out = ex;
   *dV = drep - ddisp;
   return rep - disp;
 }
@@ -122,8 +125,12 @@ __device__ __forceinline__ float F32(const PotDev& P, float b2, float E, float r
 }
 
 // ---------------------------------------------------------------- turning point
-// Returns r_min in FP64: FP32 bracket + safeguarded Newton, then FP64 Newton.
-__device__ double rmin_device(const PotDev& P, float b, float E) {
+// Returns r_min in FP64: FP32 bracket + safeguarded Newton, then FP64 Newton
+// until a step is below 1e-12 r.  The returned point is the last point where
+// V was evaluated in FP64 (F there is below 1e-12); *rep and *ex receive the
+// repulsion A e^{poly} and e^{-beta r} at that point (Jager form).
+__device__ double rmin_device(const PotDev& P, float b, float E, double* rep = nullptr,
+                              double* ex = nullptr) {
   if (P.kind == 1) return (double)fmaxf(b, (float)P.d_hs);
   const float b2 = b * b;
   float dF;
@@ -157,17 +164,16 @@ __device__ double rmin_device(const PotDev& P, float b, float E) {
   // bracket widened by 1e-4 (FP32 rounding can misplace its ends slightly)
   double rd = r;
   const double lo = (double)r_lo * (1.0 - 1e-4), hi = (double)r_hi * (1.0 + 1e-4);
-  const double bd2 = (double)b * b, Ed = E;
+  const double bd2 = (double)b * b, iEd = 1.0 / (double)E;
   for (int it = 0; it < 4; ++it) {
     double dV;
-    const double V = V64(P, rd, &dV);
-    const double f = 1.0 - bd2 / (rd * rd) - V / Ed;
-    const double df = 2.0 * bd2 / (rd * rd * rd) - dV / Ed;
+    const double ir = 1.0 / rd;
+    const double V = V64(P, rd, &dV, rep, ex);
+    const double f = 1.0 - bd2 * ir * ir - V * iEd;
+    const double df = 2.0 * bd2 * ir * ir * ir - dV * iEd;
     const double rn = rd - f / df;
-    if (!(rn >= lo && rn <= hi)) break;
-    const bool done = fabs(rn - rd) <= 1e-15 * rd;
+    if (!(rn >= lo && rn <= hi) || fabs(rn - rd) <= 1e-12 * rd) break;
     rd = rn;
-    if (done) break;
   }
   return rd;
 }
@@ -175,7 +181,8 @@ __device__ double rmin_device(const PotDev& P, float b, float E) {
 // ---------------------------------------------------------------- chi
 __device__ float chi_device(const PotDev& P, float b, float E) {
   if (!(b > 0.f)) return (float)DSMC_PI;
-  const double rd = rmin_device(P, b, E);
+  double rep_d = 0.0, ex_d = 0.0;
+  const double rd = rmin_device(P, b, E, &rep_d, &ex_d);
   const float r0 = (float)rd;
   const float bt = (float)((double)b / rd);
   const float bt2 = bt * bt;
@@ -195,8 +202,8 @@ __device__ float chi_device(const PotDev& P, float b, float E) {
     pw = ir2 * ir2 * ir2;
 #pragma unroll
     for (int n = 0; n < 6; ++n) { qn[n] = (float)(P.C[n] * pw); pw *= ir2; }
-    Rep0 = (float)(P.A * exp(P.a1 * rd + P.a2 * rd * rd + P.am1 * ir + P.am2 * ir2));
-    e0 = (float)exp(-P.beta * rd);
+    Rep0 = (float)rep_d;   // from the last FP64 evaluation, at rd
+    e0 = (float)ex_d;
   } else if (P.kind == 2) {
     Vc0 = (float)(P.kappa * pow(rd, -P.p));
     powk = P.fp;
@@ -323,6 +330,21 @@ __global__ void __launch_bounds__(128) k_jager_chi(PotDev P, int64_t n, const fl
   }
 }
 
+// cos and sin of an angle given in FP32: FP32 sincos, then the smaller of
+// the two replaced by the FP64 square root of 1 - the larger squared, so
+// that cos^2 + sin^2 = 1 to FP64 rounding (pair energy exact).
+__device__ __forceinline__ void unit_angle(float ang, double* c, double* s) {
+  float sf, cf;
+  sincosf(ang, &sf, &cf);
+  if (fabsf(cf) >= fabsf(sf)) {
+    *s = (double)sf;
+    *c = copysign(sqrt(1.0 - (double)sf * (double)sf), (double)cf);
+  } else {
+    *c = (double)cf;
+    *s = copysign(sqrt(1.0 - (double)cf * (double)cf), (double)sf);
+  }
+}
+
 // Deflect v_r by chi with azimuth eps (Bird 1994, Eq. 2.22), FP64.
 __device__ __forceinline__ void deflect(double u, double v, double w, double cc, double sc,
                                         double ce, double se, double* o) {
@@ -330,8 +352,9 @@ __device__ __forceinline__ void deflect(double u, double v, double w, double cc,
   const double q = sqrt(v * v + w * w);
   double cx, cy, cz, ax, ay, az;
   if (q > 1e-300 && q > 1e-12 * g) {
-    cx = 0.0; cy = w / q; cz = -v / q;
-    ax = q / g; ay = -u * v / (g * q); az = -u * w / (g * q);
+    const double iq = 1.0 / q, igq = iq / g;
+    cx = 0.0; cy = w * iq; cz = -v * iq;
+    ax = q / g; ay = -u * v * igq; az = -u * w * igq;
   } else {
     cx = 0.0; cy = 1.0; cz = 0.0;
     ax = 0.0; ay = 0.0; az = u >= 0.0 ? -1.0 : 1.0;
@@ -370,8 +393,8 @@ __global__ void __launch_bounds__(128) k_collide_jager(PotDev P, JagerArgs a) {
       const float chi = g > 0.0 ? chi_device(P, b, E) : 0.f;
       if (a.chi_out) a.chi_out[p] = chi;
       double cc, sc, ce, se;
-      sincos((double)chi, &sc, &cc);
-      sincos(2.0 * DSMC_PI * u53(w.z, w.w), &se, &ce);
+      unit_angle(chi, &cc, &sc);
+      unit_angle((float)(2.0 * DSMC_PI * u53(w.z, w.w)), &ce, &se);
       double o[3] = {0.0, 0.0, 0.0};
       if (g > 0.0) deflect(ux, uy, uz, cc, sc, ce, se, o);
       const double cx = 0.5 * (xi + xj), cy = 0.5 * (yi + yj), cz = 0.5 * (zi + zj);
@@ -392,8 +415,8 @@ __global__ void __launch_bounds__(128) k_harvest(PotDev P, int64_t n, const doub
     const float E = P.mass_over_4k * (float)(g * g);
     const float chi = g > 0.0 ? chi_device(P, (float)b[p], E) : 0.f;
     double cc, sc, ce, se;
-    sincos((double)chi, &sc, &cc);
-    sincos(eps[p], &se, &ce);
+    unit_angle(chi, &cc, &sc);
+    unit_angle((float)eps[p], &ce, &se);
     double o[3] = {0.0, 0.0, 0.0};
     if (g > 0.0) deflect(ux, uy, uz, cc, sc, ce, se, o);
     for (int c = 0; c < 3; ++c) {

@@ -4,8 +4,11 @@
 // bf16 input tile X in shared memory, one elected thread issues the layer's
 // tcgen05.mma chain (K-major operands, FP32 accumulator in TMEM), all four
 // warps read their 32 TMEM lanes back (tcgen05.ld), add the bias, apply the
-// activation, round to bf16 and write the next layer's A operand to shared
-// memory.  The weights of all layers stay in shared memory for the life of
+// activation and write the next layer's A operand to shared memory as two
+// bf16 terms (hi = bf16(a), lo = bf16(a - hi)) multiplied by the same bf16
+// weights: bf16 operands, FP32 accumulation, about 16 significant bits kept
+// for the activations (single bf16 storage costs up to 6e-2 in the output
+// direction of badly conditioned pairs).  The weights of all layers stay in shared memory for the life of
 // the CTA.  After the last layer thread t projects y onto the energy shell
 // and applies the centre-of-mass update of its pair in FP64.
 //
@@ -20,6 +23,8 @@
 namespace dsmc {
 
 constexpr int kTileM = 128;
+constexpr int kThreads = 512;    // 16 warps: 4 per TMEM lane group, splitting the columns
+constexpr int kColGroups = kThreads / kTileM;
 constexpr int kWidth = 128;
 constexpr int kKin = 32;         // input as two bf16 terms: [hi (16) | lo (16)]
 constexpr int kNout = 16;        // padded output width
@@ -27,7 +32,7 @@ constexpr int kMaxHidden = 4;
 
 // dynamic shared memory layout (bytes)
 struct MlpLayout {
-  uint32_t w_out, w_in, w_sq, x, h, bias, mbar, tptr, flag, total;
+  uint32_t w_out, w_in, w_sq, x, h, hlo, bias, mbar, tptr, flag, total;
 };
 
 __host__ __device__ inline MlpLayout mlp_layout(int n_hidden) {
@@ -36,8 +41,9 @@ __host__ __device__ inline MlpLayout mlp_layout(int n_hidden) {
   L.w_in = L.w_out + kNout * kWidth * 2;              // [128 x 32] = [W1 | W1]
   L.w_sq = L.w_in + kWidth * kKin * 2;                // (n_hidden-1) x [128 x 128]
   L.x = L.w_sq + (uint32_t)(n_hidden - 1) * kWidth * kWidth * 2;  // [128 x 16]
-  L.h = L.x + kTileM * kKin * 2;                      // [128 x 128]
-  L.bias = L.h + kTileM * kWidth * 2;                 // floats: n_hidden*128 + 16
+  L.h = L.x + kTileM * kKin * 2;                      // [128 x 128] activations, hi term
+  L.hlo = L.h + kTileM * kWidth * 2;                  // [128 x 128] activations, lo term
+  L.bias = L.hlo + kTileM * kWidth * 2;               // floats: n_hidden*128 + 16
   L.mbar = L.bias + (uint32_t)(n_hidden * kWidth + kNout) * 4;
   L.mbar = (L.mbar + 15u) & ~15u;
   L.tptr = L.mbar + 8;
@@ -91,13 +97,19 @@ __device__ __forceinline__ float act_f(int act, float z) {
 // Run all layers on the X tile already in shared memory (fenced and
 // synchronised by the caller).  Returns false if a bounded wait ran out
 // (status recorded); y receives row threadIdx.x of the output (+ bias).
+// Rows: warp w reads TMEM lanes 32 (w % 4) .. +31, i.e. row = 32 (w % 4) + lane;
+// the column range of a hidden layer is split over the blockDim/128 warps that
+// share a lane group.  y is valid in threads 0..127 (row = threadIdx.x).
 __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, uint32_t tmem,
                          uint32_t& phase, float y[3], int* status) {
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, warp = t >> 5;
+  const int row = ((warp & 3) << 5) | (t & 31);
+  const int cgroups = blockDim.x / kTileM, cg = warp >> 2;
+  const int cols = kWidth / cgroups;
   uint64_t* mbar = (uint64_t*)(smem + L.mbar);
   volatile int* flag = (volatile int*)(smem + L.flag);
   const uint32_t sbase = tc::smem_u32(smem);
-  const uint32_t lane_tm = tmem + ((uint32_t)((t >> 5) * 32) << 16);
+  const uint32_t lane_tm = tmem + ((uint32_t)((warp & 3) * 32) << 16);
   const float* bs = (const float*)(smem + L.bias);
   for (int l = 0; l <= sh.n_hidden; ++l) {
     if (t == 0) {
@@ -111,10 +123,15 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, uin
       } else {
         const uint32_t wb = l < sh.n_hidden ? L.w_sq + (uint32_t)(l - 1) * kWidth * kWidth * 2 : L.w_out;
         const uint32_t idesc = l < sh.n_hidden ? tc::idesc_bf16(kTileM, kWidth) : tc::idesc_bf16(kTileM, kNout);
+        // activations enter as hi + lo bf16 terms against the same weights
 #pragma unroll
         for (int s = 0; s < kWidth / 16; ++s)
           tc::mma_bf16(tmem, tc::sdesc(sbase + L.h + 256u * s, 128, 2048),
                        tc::sdesc(sbase + wb + 256u * s, 128, 2048), idesc, s > 0);
+#pragma unroll
+        for (int s = 0; s < kWidth / 16; ++s)
+          tc::mma_bf16(tmem, tc::sdesc(sbase + L.hlo + 256u * s, 128, 2048),
+                       tc::sdesc(sbase + wb + 256u * s, 128, 2048), idesc, 1);
       }
       tc::commit(mbar);
       *flag = tc::mbar_wait(mbar, phase, status, kBarrierLimitNs) ? 1 : 0;
@@ -126,29 +143,36 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, uin
     if (l < sh.n_hidden) {
       const float* bl = bs + l * kWidth;
 #pragma unroll 1
-      for (int c0 = 0; c0 < kWidth; c0 += 32) {
+      for (int c0 = cg * cols; c0 < (cg + 1) * cols; c0 += 32) {
         float v[32];
         tc::ld32(lane_tm + (uint32_t)c0, v);
-        uint32_t pk[16];
+        uint32_t pk[16], lo[16];
 #pragma unroll
-        for (int q = 0; q < 16; ++q)
-          pk[q] = tc::pack_bf16x2(act_f(sh.act, v[2 * q] + bl[c0 + 2 * q]),
-                                  act_f(sh.act, v[2 * q + 1] + bl[c0 + 2 * q + 1]));
+        for (int q = 0; q < 16; ++q) {
+          const float a0 = act_f(sh.act, v[2 * q] + bl[c0 + 2 * q]);
+          const float a1 = act_f(sh.act, v[2 * q + 1] + bl[c0 + 2 * q + 1]);
+          pk[q] = tc::pack_bf16x2(a0, a1);
+          lo[q] = tc::pack_bf16x2(a0 - __uint_as_float(pk[q] << 16), a1 - __uint_as_float(pk[q] & 0xFFFF0000u));
+        }
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-          tc::st_shared_v4(sbase + L.h + tc::kmajor_offset(t, c0 + 8 * j, kWidth), pk[4 * j],
-                           pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t off = tc::kmajor_offset(row, c0 + 8 * j, kWidth);
+          tc::st_shared_v4(sbase + L.h + off, pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+          tc::st_shared_v4(sbase + L.hlo + off, lo[4 * j], lo[4 * j + 1], lo[4 * j + 2], lo[4 * j + 3]);
+        }
       }
       tc::fence_before();
       tc::fence_async_smem();
       __syncthreads();
     } else {
-      float v[16];
-      tc::ld16(lane_tm, v);
-      const float* bo = bs + sh.n_hidden * kWidth;
-      y[0] = v[0] + bo[0];
-      y[1] = v[1] + bo[1];
-      y[2] = v[2] + bo[2];
+      if (cg == 0) {
+        float v[16];
+        tc::ld16(lane_tm, v);
+        const float* bo = bs + sh.n_hidden * kWidth;
+        y[0] = v[0] + bo[0];
+        y[1] = v[1] + bo[1];
+        y[2] = v[2] + bo[2];
+      }
       tc::fence_before();
       __syncthreads();
     }
@@ -199,7 +223,7 @@ __device__ __forceinline__ void cta_teardown(uint32_t tmem) {
 
 // ---------------------------------------------------------------- standalone forward
 // y[n x 3] = f_theta(x[n x d_in]) on bf16 tensor cores.
-__global__ void __launch_bounds__(kTileM) k_mlp_forward(MlpShape sh, const uint16_t* __restrict__ w,
+__global__ void __launch_bounds__(kThreads) k_mlp_forward(MlpShape sh, const uint16_t* __restrict__ w,
                                                         const float* __restrict__ bias, int64_t n,
                                                         const float* __restrict__ x, float* __restrict__ y,
                                                         int* status) {
@@ -212,17 +236,19 @@ __global__ void __launch_bounds__(kTileM) k_mlp_forward(MlpShape sh, const uint1
   const int64_t tiles = (n + kTileM - 1) / kTileM;
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t row = tile * kTileM + t;
-    float f[16];
+    if (t < kTileM) {
+      float f[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) f[q] = 0.f;
-    if (row < n)
-      for (int q = 0; q < sh.d_in; ++q) f[q] = x[row * sh.d_in + q];
-    write_x_row(smem, L, t, f);
-    tc::fence_async_smem();
+      for (int q = 0; q < 16; ++q) f[q] = 0.f;
+      if (row < n)
+        for (int q = 0; q < sh.d_in; ++q) f[q] = x[row * sh.d_in + q];
+      write_x_row(smem, L, t, f);
+      tc::fence_async_smem();
+    }
     __syncthreads();
     float o[3];
     if (!mlp_tile(smem, L, sh, tmem, phase, o, status)) break;
-    if (row < n) { y[3 * row] = o[0]; y[3 * row + 1] = o[1]; y[3 * row + 2] = o[2]; }
+    if (t < kTileM && row < n) { y[3 * row] = o[0]; y[3 * row + 1] = o[1]; y[3 * row + 2] = o[2]; }
   }
   cta_teardown(tmem);
 }
@@ -298,7 +324,7 @@ __device__ __forceinline__ void box_muller(double u1, double u2, float* z0, floa
   *z1 = rho * s;
 }
 
-__global__ void __launch_bounds__(kTileM) k_collide_neural(MlpShape sh, const uint16_t* __restrict__ w,
+__global__ void __launch_bounds__(kThreads) k_collide_neural(MlpShape sh, const uint16_t* __restrict__ w,
                                                            const float* __restrict__ bias, NeuralArgs a) {
   extern __shared__ __align__(1024) char smem[];
   const MlpLayout L = mlp_layout(sh.n_hidden);
@@ -313,7 +339,7 @@ __global__ void __launch_bounds__(kTileM) k_collide_neural(MlpShape sh, const ui
     const int32_t tiles = (end - beg + kTileM - 1) / kTileM;
     for (int32_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
       const int32_t p = beg + tile * kTileM + t;
-      const bool valid = p < end;
+      const bool valid = t < kTileM && p < end;
       int4 q = make_int4(0, 0, 0, 0);
       double xi = 0, yi = 0, zi = 0, xj = 0, yj = 0, zj = 0;
       float f[16];
@@ -339,8 +365,10 @@ __global__ void __launch_bounds__(kTileM) k_collide_neural(MlpShape sh, const ui
           f[3] = z[0]; f[4] = z[1]; f[5] = z[2];
         }
       }
-      write_x_row(smem, L, t, f);
-      tc::fence_async_smem();
+      if (t < kTileM) {
+        write_x_row(smem, L, t, f);
+        tc::fence_async_smem();
+      }
       __syncthreads();
       float y[3];
       if (!mlp_tile(smem, L, sh, tmem, phase, y, a.status)) { alive = false; break; }
@@ -404,7 +432,7 @@ int launch_collide_neural(Ctx* c, const dsmc_gas_t& gas, const dsmc_mlp_t& mlp,
   const MlpLayout L = mlp_layout(sh.n_hidden);
   if (!set_smem((const void*)k_collide_neural, (int)L.total))
     return record(c, DSMC_ERR_CUDA, "collide_neural: shared-memory attribute");
-  const int blocks = cooperative_blocks(c, (const void*)k_collide_neural, kTileM, L.total);
+  const int blocks = cooperative_blocks(c, (const void*)k_collide_neural, kThreads, L.total);
   if (!blocks) return record(c, DSMC_ERR_CUDA, "collide_neural: occupancy query failed");
   NeuralArgs a;
   a.seed = gas.seed; a.step = step;
@@ -414,7 +442,7 @@ int launch_collide_neural(Ctx* c, const dsmc_gas_t& gas, const dsmc_mlp_t& mlp,
   a.vx = vx; a.vy = vy; a.vz = vz; a.bar = barrier_ptr(c); a.status = status_ptr(c);
   if (cudaMemsetAsync(a.bar, 0, 4 * sizeof(unsigned), s) != cudaSuccess) return DSMC_ERR_CUDA;
   void* args[] = {(void*)&sh, (void*)&w, (void*)&bias, (void*)&a};
-  if (cudaLaunchCooperativeKernel((const void*)k_collide_neural, dim3(blocks), dim3(kTileM), args, L.total, s) !=
+  if (cudaLaunchCooperativeKernel((const void*)k_collide_neural, dim3(blocks), dim3(kThreads), args, L.total, s) !=
       cudaSuccess)
     return record(c, DSMC_ERR_CUDA, "collide_neural: cooperative launch failed");
   count_launches(c, 1);
@@ -430,12 +458,12 @@ int launch_mlp_forward(Ctx* c, const dsmc_mlp_t& mlp, const uint16_t* w, const f
   if (!set_smem((const void*)k_mlp_forward, (int)L.total))
     return record(c, DSMC_ERR_CUDA, "mlp_forward: shared-memory attribute");
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_mlp_forward, kTileM, L.total);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_mlp_forward, kThreads, L.total);
   if (per_sm < 1) per_sm = 1;
   const int64_t tiles = (n + kTileM - 1) / kTileM;
   int64_t blocks = (int64_t)sm_count(c) * per_sm;
   if (blocks > tiles) blocks = tiles;
-  k_mlp_forward<<<(unsigned)blocks, kTileM, L.total, s>>>(sh, w, bias, n, x, y, status_ptr(c));
+  k_mlp_forward<<<(unsigned)blocks, kThreads, L.total, s>>>(sh, w, bias, n, x, y, status_ptr(c));
   count_launches(c, 1);
   return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
 }

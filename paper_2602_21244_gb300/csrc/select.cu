@@ -41,6 +41,8 @@ struct SelArgs {
   double pid2, om_half, gam, two_kt, mr;
   // model 1: sigma = sig_const
   double sig_const;
+  // FP32 screen: sigma(g) g = k32 * g^e32 (e32 = 1 for model 1)
+  float k32, e32;
 };
 
 __device__ __forceinline__ double sigma_g(const SelArgs& a, double g) {
@@ -62,30 +64,109 @@ __device__ __forceinline__ int32_t ntc_count(const SelArgs& a, int32_t k, int32_
   return (int32_t)mf;
 }
 
-// candidate m of cell k: local indices i, j (j != i), sigma g, accept flag
-__device__ __forceinline__ bool candidate(const SelArgs& a, int32_t k, int32_t base, int32_t N,
-                                          int32_t m, double sgmax_k, int32_t* pi, int32_t* pj,
-                                          double* sg_out) {
-  const u32x4 w = draw(a.seed, (uint32_t)m, (uint32_t)k, a.step, TAG_CAND);
-  const uint32_t i = mulhi_n(w.x, (uint32_t)N);
-  uint32_t j = mulhi_n(w.y, (uint32_t)(N - 1));
-  j += (j >= i);
+// Exact FP64 decision for candidate pair (i, j) of cell k (the definition).
+__device__ __forceinline__ bool decide64(const SelArgs& a, int32_t base, uint32_t i, uint32_t j,
+                                         double U, double sgmax_k, double* sg_out) {
   const double dx = __dsub_rn(a.vx[base + i], a.vx[base + j]);
   const double dy = __dsub_rn(a.vy[base + i], a.vy[base + j]);
   const double dz = __dsub_rn(a.vz[base + i], a.vz[base + j]);
   const double g2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-  const double g = __dsqrt_rn(g2);
-  const double sg = sigma_g(a, g);
-  *pi = (int32_t)i; *pj = (int32_t)j; *sg_out = sg;
-  return u53(w.z, w.w) < __ddiv_rn(sg, sgmax_k);
+  const double sg = sigma_g(a, __dsqrt_rn(g2));
+  *sg_out = sg;
+  return U < __ddiv_rn(sg, sgmax_k);
+}
+
+// Per-warp FP32 copy of a cell's velocities in shared memory (cells of up
+// to kStage particles; larger cells read FP64 from global memory).
+constexpr int kStage = 384;
+
+struct CellView {
+  const float *x, *y, *z;  // staged FP32 velocities, or null
+  float dg;                // bound on the FP32 error of g for this cell
+  float sgmax32, inv_sgmax32, thr_raise;
+};
+
+// Candidate m of cell k.  The accept decision is screened in FP32 and taken
+// in FP64 only when the FP32 ratio is within its error bound of U; the FP64
+// sigma g is also formed for candidates that may raise (sigma g)_max.
+// Returns accept; *raise_sg = FP64 sigma g if it may exceed the old maximum,
+// else -1.
+__device__ __forceinline__ bool candidate(const SelArgs& a, const CellView& cv, int32_t k,
+                                          int32_t base, int32_t N, int32_t m, double sgmax_k,
+                                          int32_t* pi, int32_t* pj, double* raise_sg) {
+  const u32x4 w = draw(a.seed, (uint32_t)m, (uint32_t)k, a.step, TAG_CAND);
+  const uint32_t i = mulhi_n(w.x, (uint32_t)N);
+  uint32_t j = mulhi_n(w.y, (uint32_t)(N - 1));
+  j += (j >= i);
+  *pi = (int32_t)i; *pj = (int32_t)j;
+  float dx, dy, dz;
+  if (cv.x) {
+    dx = cv.x[i] - cv.x[j]; dy = cv.y[i] - cv.y[j]; dz = cv.z[i] - cv.z[j];
+  } else {
+    dx = (float)(a.vx[base + i] - a.vx[base + j]);
+    dy = (float)(a.vy[base + i] - a.vy[base + j]);
+    dz = (float)(a.vz[base + i] - a.vz[base + j]);
+  }
+  const float g = sqrtf(dx * dx + dy * dy + dz * dz);
+  const float sg = a.model == 1 ? a.k32 * g : a.k32 * __powf(g, a.e32);
+  const float ratio = sg * cv.inv_sgmax32;
+  // U32 <= U < U32 + 2^-24 (top 24 bits of the 53-bit uniform)
+  const float U32 = (float)(w.z >> 8) * 5.9604645e-8f;
+  // error bound of the FP32 ratio: 1e-4 relative (arithmetic, __powf) plus
+  // the effect of the FP32 rounding of the velocities on g
+  const float relg = cv.dg / fmaxf(g, 1e-30f);
+  const float margin = 2e-7f + ratio * (1e-4f + a.e32 * relg);
+  bool acc;
+  double sg64 = -1.0;
+  if (ratio > U32 + 5.9604645e-8f + margin) acc = true;
+  else if (ratio < U32 - margin) acc = false;
+  else acc = decide64(a, base, i, j, u53(w.z, w.w), sgmax_k, &sg64);
+  if (sg > cv.thr_raise || relg > 1e-3f) {
+    if (sg64 < 0.0) decide64(a, base, i, j, 0.0, sgmax_k, &sg64);
+  } else {
+    sg64 = -1.0;
+  }
+  *raise_sg = sg64;
+  return acc;
 }
 
 constexpr int kSelWarps = 8;
 
+// Stage the cell's velocities (FP32) in this warp's shared-memory slice and
+// derive the screening constants.
+__device__ __forceinline__ CellView stage_cell(const SelArgs& a, float* sm, int32_t base, int32_t N,
+                                               double sgk, int lane) {
+  CellView cv;
+  float vmax = 0.f;
+  if (N <= kStage) {
+    float* x = sm; float* y = sm + kStage; float* z = sm + 2 * kStage;
+    for (int32_t t = lane; t < N; t += 32) {
+      const float fx = (float)a.vx[base + t], fy = (float)a.vy[base + t], fz = (float)a.vz[base + t];
+      x[t] = fx; y[t] = fy; z[t] = fz;
+      vmax = fmaxf(vmax, fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))));
+    }
+    cv.x = x; cv.y = y; cv.z = z;
+  } else {
+    for (int32_t t = lane; t < N; t += 32)
+      vmax = fmaxf(vmax, (float)fmax(fabs(a.vx[base + t]), fmax(fabs(a.vy[base + t]), fabs(a.vz[base + t]))));
+    cv.x = cv.y = cv.z = nullptr;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+  __syncwarp();
+  // each velocity carries <= |v| 2^-24 rounding; g over three differences
+  cv.dg = 4.0f * vmax * 5.9604645e-8f;
+  cv.sgmax32 = (float)sgk;
+  cv.inv_sgmax32 = 1.f / cv.sgmax32;
+  cv.thr_raise = cv.sgmax32 * (1.f - 3e-4f);
+  return cv;
+}
+
 __global__ void __launch_bounds__(kSelWarps * 32) k_sel_count(SelArgs a) {
-  const int lane = threadIdx.x & 31;
+  __shared__ float stage[kSelWarps][3 * kStage];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int32_t warps = gridDim.x * kSelWarps;
-  for (int32_t k = blockIdx.x * kSelWarps + (threadIdx.x >> 5); k < a.n_cells; k += warps) {
+  for (int32_t k = blockIdx.x * kSelWarps + wid; k < a.n_cells; k += warps) {
     const int32_t base = a.cs[k], N = a.cs[k + 1] - base;
     const double sgk = a.sgmax[k];
     if (N < 2) {
@@ -95,12 +176,13 @@ __global__ void __launch_bounds__(kSelWarps * 32) k_sel_count(SelArgs a) {
     int bad = 0;
     const int32_t M = ntc_count(a, k, N, &bad);
     if (bad && lane == 0) set_status(a.status, DSMC_ERR_CAPACITY);
+    const CellView cv = stage_cell(a, stage[wid], base, N, sgk, lane);
     int acc = 0;
     double best = sgk;
     for (int32_t m = lane; m < M; m += 32) {
       int32_t i, j;
       double sg;
-      acc += candidate(a, k, base, N, m, sgk, &i, &j, &sg);
+      acc += candidate(a, cv, k, base, N, m, sgk, &i, &j, &sg);
       best = fmax(best, sg);
     }
     acc = warp_sum_i(acc);
@@ -110,10 +192,12 @@ __global__ void __launch_bounds__(kSelWarps * 32) k_sel_count(SelArgs a) {
       a.sgnew[k] = best;
       atomicAdd(a.n_cand, (unsigned long long)M);
     }
+    __syncwarp();
   }
 }
 
 __global__ void __launch_bounds__(kSelWarps * 32) k_sel_emit(SelArgs a) {
+  __shared__ float stage[kSelWarps][3 * kStage];
   __shared__ int hist[DSMC_MAX_ROUNDS];
   __shared__ int rmax_blk;
   for (int t = threadIdx.x; t < DSMC_MAX_ROUNDS; t += blockDim.x) hist[t] = 0;
@@ -122,21 +206,22 @@ __global__ void __launch_bounds__(kSelWarps * 32) k_sel_emit(SelArgs a) {
   const int64_t total = a.offs[a.n_cells];
   const bool over = total > a.capacity;
   if (over && blockIdx.x == 0 && threadIdx.x == 0) set_status(a.status, DSMC_ERR_CAPACITY);
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int32_t warps = gridDim.x * kSelWarps;
-  for (int32_t k = blockIdx.x * kSelWarps + (threadIdx.x >> 5); k < a.n_cells && !over; k += warps) {
+  for (int32_t k = blockIdx.x * kSelWarps + wid; k < a.n_cells && !over; k += warps) {
     const int32_t base = a.cs[k], N = a.cs[k + 1] - base;
     if (N < 2) continue;
     const double sgk = a.sgmax[k];
     int bad = 0;
     const int32_t M = ntc_count(a, k, N, &bad);
+    const CellView cv = stage_cell(a, stage[wid], base, N, sgk, lane);
     const int32_t p0 = a.offs[k], p1 = a.offs[k + 1];
     int32_t pos = p0;
     for (int32_t c0 = 0; c0 < M; c0 += 32) {
       const int32_t m = c0 + lane;
       int32_t i = 0, j = 0;
       double sg;
-      const bool ok = m < M && candidate(a, k, base, N, m, sgk, &i, &j, &sg);
+      const bool ok = m < M && candidate(a, cv, k, base, N, m, sgk, &i, &j, &sg);
       const unsigned mask = __ballot_sync(0xffffffffu, ok);
       if (ok) {
         const int32_t q = pos + __popc(mask & ((1u << lane) - 1u));
@@ -280,6 +365,11 @@ int launch_select(Ctx* c, const dsmc_gas_t& gas, int32_t n, int32_t n_cells, con
   a.two_kt = 2.0 * DSMC_KB * gas.T_ref;
   a.mr = 0.5 * gas.mass;
   a.sig_const = DSMC_PI * gas.b_max * gas.b_max;
+  if (gas.model == 1) { a.k32 = (float)a.sig_const; a.e32 = 1.f; }
+  else {
+    a.k32 = (float)(a.pid2 / a.gam * pow(a.two_kt / a.mr, a.om_half));
+    a.e32 = (float)(2.0 - 2.0 * gas.omega);
+  }
   const int sms = sm_count(c);
   if (cudaMemsetAsync(w.round_count, 0, sizeof(int32_t) * DSMC_MAX_ROUNDS * 2 + 256, s) != cudaSuccess)
     return DSMC_ERR_CUDA;

@@ -427,14 +427,16 @@ def test_mlp_forward_matches_torch_sequential():
     y = O.mlp_forward(mlp, wts["W"], wts["bias"] + 0.01, x)
     ref = net(torch.tensor(x)).detach().numpy()
     np.testing.assert_allclose(y, ref, rtol=1e-12, atol=1e-13)
-    # bf16 mode: input as two bf16 terms, hidden activations rounded to bf16
+    # bf16 mode: input and hidden activations as two bf16 terms each
     xt = torch.tensor(x)
     hi = xt.to(torch.bfloat16).double()
     h = hi + (xt - hi).to(torch.bfloat16).double()
     for l in range(4):
         h = layers[2 * l](h)
         if l < 3:
-            h = torch.nn.functional.silu(h).to(torch.bfloat16).double()
+            a = torch.nn.functional.silu(h)
+            hi = a.to(torch.bfloat16).double()
+            h = hi + (a - hi).to(torch.bfloat16).double()
     yb = O.mlp_forward(mlp, wts["W"], wts["bias"] + 0.01, x, bf16=True)
     np.testing.assert_allclose(yb, h.detach().numpy(), rtol=1e-12, atol=1e-13)
 
