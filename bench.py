@@ -224,6 +224,31 @@ def run_gb300(args, rank, world, dist):
         tf = nb * MLP_FLOP_PER_PAIR / (ms * 1e-3) / 1e12
         extra["mlp_forward"] = dict(rows=nb, ms=ms, rows_per_s=nb / (ms * 1e-3), tflops=tf,
                                     frac_of_bf16_peak=tf / peak)
+        # training step on 2^20 pairs harvested by the Jager kernel (forward,
+        # recomputing backward, Adam)
+        nt = 1 << 20
+        hv = W.harvest_inputs(nt, seed=0)
+        hvi, hvj = torch.from_numpy(hv["vi"]).to(dev), torch.from_numpy(hv["vj"]).to(dev)
+        hT = torch.from_numpy(hv["T"]).to(dev)
+        vit, vjt = C.harvest_jager(gas1, pot, hvi, hvj, torch.from_numpy(hv["b"]).to(dev),
+                                   torch.from_numpy(hv["eps"]).to(dev), n_nodes=args.n_nodes)
+        theta = torch.from_numpy(np.concatenate([wts["W"], wts["bias"]]).astype(np.float32)).to(dev)
+        m_, v_ = torch.zeros_like(theta), torch.zeros_like(theta)
+        grad = torch.empty_like(theta)
+        lossb = torch.zeros(1, dtype=torch.float64, device=dev)
+        tws = C.train_workspace(dev)
+        for stp in (1, 2):
+            C.train_step(mlp, theta, m_, v_, stp, 1e-3, 0, hvi, hvj, hT, vit, vjt, grad, lossb, tws)
+        e0.record(stream)
+        for stp in range(3, 6):
+            C.train_step(mlp, theta, m_, v_, stp, 1e-3, 0, hvi, hvj, hT, vit, vjt, grad, lossb, tws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        # algorithmic MMA work: forward + recomputation + two backward GEMMs ~ 4 x the forward
+        tf = 4 * nt * MLP_FLOP_PER_PAIR / (ms * 1e-3) / 1e12
+        extra["train_step"] = dict(pairs=nt, ms=ms, steps_per_s=1e3 / ms, pairs_per_s=nt / (ms * 1e-3),
+                                   tflops=tf, loss=float(lossb.item()))
         if C.sync_status() != 0:
             raise RuntimeError("device status after standalone kernels")
     # ------------------------------------------------------------ e2e (host buffers)

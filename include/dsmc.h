@@ -268,9 +268,12 @@ int dsmc_mlp_forward(dsmc_ctx_t* ctx, const dsmc_mlp_t* mlp, const uint16_t* wei
 /* Diagnostic with no counterpart in the paper: D[128 x N] = A[128 x K] B[N x K]^T
  * (bf16 row-major in, FP32 row-major out) through the same shared-memory
  * operand layout, descriptors and tcgen05.mma issue as the MLP, on one CTA.
- * N a multiple of 16 in [16, 256], K a multiple of 16 in [16, 128]. */
-int dsmc_tc_selftest(dsmc_ctx_t* ctx, int32_t N, int32_t K, const uint16_t* A, const uint16_t* B,
-                     float* D, void* stream);
+ * N a multiple of 16 in [16, 256], K a multiple of 16 in [16, 128].
+ * layout bit 0: A held MN-major in shared memory, bit 1: B MN-major (as the
+ * backward pass reads them), bit 2: exchange the two descriptor offsets of
+ * MN-major operands (a check of the descriptor convention). */
+int dsmc_tc_selftest(dsmc_ctx_t* ctx, int32_t N, int32_t K, int32_t layout, const uint16_t* A,
+                     const uint16_t* B, float* D, void* stream);
 
 /* Diagnostic with no counterpart in the paper (failure detection): runs a
  * kernel whose bounded wait can never be satisfied -- which 0: a grid
@@ -351,6 +354,57 @@ int dsmc_harvest_jager(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_potent
                        int32_t n_nodes, int64_t n, const double* vi, const double* vj,
                        const double* b, const double* eps, double* vi_out, double* vj_out,
                        void* stream);
+
+/* ---------------------------------------------------------------- neural operator training */
+
+/* Parameters theta (FP32): each layer's row-major [out x in] weights,
+ * concatenated, then each layer's bias (the layout of dsmc_collide_neural's
+ * weights and biases).  34,563 for d_in 8, width 128, 3 hidden layers. */
+int32_t dsmc_mlp_param_count(const dsmc_mlp_t* mlp);
+/* Scratch of the backward kernels: one partial gradient per SM. */
+size_t dsmc_train_workspace_size(dsmc_ctx_t* ctx);
+
+/* The neural collision operator applied to a batch of n pairs (n a multiple
+ * of 16) grouped in pseudo-cells of 16 consecutive pairs (32 particles):
+ *   x = [v_r/sigma_v, T/T_ref, xi] (xi: Philox tag 5, counter (pair, 0, t)),
+ *   y = f_theta(x) (bf16 tcgen05, weights rounded from theta),
+ *   v_r' = |v_r| y/|y| (Eq. energy_shell_projection), centre-of-mass update
+ *   (Sec. 2.3), moment matching of each pseudo-cell to its pre-collision
+ *   momentum and energy (Sec. 2.5, centred).
+ * vi, vj, vi_new, vj_new: [n x 3] FP64 row-major; T: [n] FP64.
+ * Requires d_in 8, width 128, 3 hidden layers. */
+int dsmc_neural_operator_forward(dsmc_ctx_t* ctx, const dsmc_mlp_t* mlp, const float* theta, uint64_t seed,
+                                 uint64_t t, int64_t n, const double* vi, const double* vj, const double* T,
+                                 double* vi_new, double* vj_new, void* stream);
+/* Hand-written backward of the operator: given dL/dvi_new, dL/dvj_new
+ * ([n x 3] FP64), writes dL/dtheta (FP32, theta layout) to grad.  The
+ * moment-matching and projection backward are closed forms; the MLP
+ * backward recomputes each layer's pre-activation from the saved input of
+ * that layer (no activations stored in HBM); dW accumulates per SM in
+ * TMEM and the per-SM partials are summed in a fixed order. */
+int dsmc_neural_operator_backward(dsmc_ctx_t* ctx, const dsmc_mlp_t* mlp, const float* theta, uint64_t seed,
+                                  uint64_t t, int64_t n, const double* vi, const double* vj, const double* T,
+                                  const double* g_vi, const double* g_vj, float* grad, void* ws,
+                                  size_t ws_bytes, void* stream);
+/* Loss L = mean over the 2n particles of |v_new - v_target|^2 / sigma_v^2
+ * (the MSE of Sec. 2.6) and dL/dtheta in one pass; *loss (device FP64). */
+int dsmc_train_loss_grad(dsmc_ctx_t* ctx, const dsmc_mlp_t* mlp, const float* theta, uint64_t seed, uint64_t t,
+                         int64_t n, const double* vi, const double* vj, const double* T, const double* vi_target,
+                         const double* vj_target, float* grad, double* loss, void* ws, size_t ws_bytes,
+                         void* stream);
+/* Adam (Kingma & Ba 2015, Algorithm 1) on theta with moments m, v (FP32,
+ * n_params each); step counts from 1.  The first n_weights entries are
+ * weights: if weights_bf16 / biases are given, the updated weights are also
+ * written as bf16 and the biases as FP32 (the collide kernel's inputs). */
+int dsmc_adam_step(dsmc_ctx_t* ctx, int32_t n_params, int32_t n_weights, const float* grad, float* theta,
+                   float* m, float* v, int64_t step, float lr, float beta1, float beta2, float eps,
+                   uint16_t* weights_bf16, float* biases, void* stream);
+/* One training step (Sec. 2.6; Adam beta = (0.9, 0.999), eps = 1e-8):
+ * dsmc_train_loss_grad with noise counter t = step, then dsmc_adam_step. */
+int dsmc_train_step(dsmc_ctx_t* ctx, const dsmc_mlp_t* mlp, float* theta, float* m, float* v, int64_t step,
+                    float lr, uint64_t seed, int64_t n, const double* vi, const double* vj, const double* T,
+                    const double* vi_target, const double* vj_target, float* grad, double* loss,
+                    uint16_t* weights_bf16, float* biases, void* ws, size_t ws_bytes, void* stream);
 
 #ifdef __cplusplus
 }

@@ -228,13 +228,14 @@ int dsmc_mlp_forward(dsmc_ctx_t* c, const dsmc_mlp_t* mlp, const uint16_t* w, co
   return dsmc::launch_mlp_forward(c, *mlp, w, bias, n, x, y, S(stream));
 }
 
-int dsmc_tc_selftest(dsmc_ctx_t* c, int32_t N, int32_t K, const uint16_t* A, const uint16_t* B,
-                     float* D, void* stream) {
+int dsmc_tc_selftest(dsmc_ctx_t* c, int32_t N, int32_t K, int32_t layout, const uint16_t* A,
+                     const uint16_t* B, float* D, void* stream) {
   CHECK_CTX(c);
   REQUIRE(c, N >= 16 && N <= 256 && N % 16 == 0 && K >= 16 && K <= 128 && K % 16 == 0,
           "tc_selftest: N in [16,256], K in [16,128], multiples of 16");
+  REQUIRE(c, layout >= 0 && layout <= 7, "tc_selftest: layout in [0, 7]");
   REQUIRE(c, A && B && D, "tc_selftest: null pointer");
-  return dsmc::launch_tc_selftest(c, N, K, A, B, D, S(stream));
+  return dsmc::launch_tc_selftest(c, N, K, layout, A, B, D, S(stream));
 }
 
 int dsmc_selftest_timeout(dsmc_ctx_t* c, int32_t which, uint64_t limit_ns, void* stream) {
@@ -261,6 +262,79 @@ int dsmc_harvest_jager(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_potentia
   if (int rc = check_pot(c, pot, n_nodes)) return rc;
   REQUIRE(c, n >= 0 && (n == 0 || (vi && vj && b && eps && vio && vjo)), "harvest: bad arrays");
   return dsmc::launch_harvest_jager(c, *gas, *pot, n_nodes, n, vi, vj, b, eps, vio, vjo, S(stream));
+}
+
+// ---------------------------------------------------------------- training
+static int check_train(Ctx* c, const dsmc_mlp_t* mlp, int64_t n) {
+  if (int rc = check_mlp(c, mlp)) return rc;
+  REQUIRE(c, mlp->d_in == 8 && mlp->n_hidden == 3, "train: d_in 8 and 3 hidden layers");
+  REQUIRE(c, n >= 0 && n % 16 == 0, "train: n_pairs must be a multiple of 16 (pseudo-cells)");
+  return 0;
+}
+
+int32_t dsmc_mlp_param_count(const dsmc_mlp_t* mlp) {
+  if (!mlp) return -1;
+  const int32_t w = mlp->width * mlp->d_in + (mlp->n_hidden - 1) * mlp->width * mlp->width + mlp->d_out * mlp->width;
+  return w + mlp->n_hidden * mlp->width + mlp->d_out;
+}
+
+size_t dsmc_train_workspace_size(dsmc_ctx_t* c) { return c ? dsmc::train_ws(c->sms) : 0; }
+
+int dsmc_neural_operator_forward(dsmc_ctx_t* c, const dsmc_mlp_t* mlp, const float* theta, uint64_t seed,
+                                 uint64_t t, int64_t n, const double* vi, const double* vj, const double* T,
+                                 double* vi_new, double* vj_new, void* stream) {
+  CHECK_CTX(c);
+  if (int rc = check_train(c, mlp, n)) return rc;
+  REQUIRE(c, theta && (n == 0 || (vi && vj && T && vi_new && vj_new)), "operator_forward: null pointer");
+  if (n == 0) return 0;
+  return dsmc::launch_train(c, *mlp, 0, seed, t, n, theta, vi, vj, T, nullptr, nullptr, nullptr, nullptr,
+                            vi_new, vj_new, nullptr, nullptr, nullptr, 0, S(stream));
+}
+
+int dsmc_neural_operator_backward(dsmc_ctx_t* c, const dsmc_mlp_t* mlp, const float* theta, uint64_t seed,
+                                  uint64_t t, int64_t n, const double* vi, const double* vj, const double* T,
+                                  const double* g_vi, const double* g_vj, float* grad, void* ws, size_t ws_bytes,
+                                  void* stream) {
+  CHECK_CTX(c);
+  if (int rc = check_train(c, mlp, n)) return rc;
+  REQUIRE(c, theta && grad && ws && (n == 0 || (vi && vj && T && g_vi && g_vj)), "operator_backward: null pointer");
+  return dsmc::launch_train(c, *mlp, 1, seed, t, n, theta, vi, vj, T, nullptr, nullptr, g_vi, g_vj, nullptr,
+                            nullptr, grad, nullptr, ws, ws_bytes, S(stream));
+}
+
+int dsmc_train_loss_grad(dsmc_ctx_t* c, const dsmc_mlp_t* mlp, const float* theta, uint64_t seed, uint64_t t,
+                         int64_t n, const double* vi, const double* vj, const double* T, const double* vi_target,
+                         const double* vj_target, float* grad, double* loss, void* ws, size_t ws_bytes,
+                         void* stream) {
+  CHECK_CTX(c);
+  if (int rc = check_train(c, mlp, n)) return rc;
+  REQUIRE(c, theta && grad && loss && ws && (n == 0 || (vi && vj && T && vi_target && vj_target)),
+          "train_loss_grad: null pointer");
+  return dsmc::launch_train(c, *mlp, 2, seed, t, n, theta, vi, vj, T, vi_target, vj_target, nullptr, nullptr,
+                            nullptr, nullptr, grad, loss, ws, ws_bytes, S(stream));
+}
+
+int dsmc_adam_step(dsmc_ctx_t* c, int32_t n_params, int32_t n_weights, const float* grad, float* theta,
+                   float* m, float* v, int64_t step, float lr, float beta1, float beta2, float eps,
+                   uint16_t* weights_bf16, float* biases, void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, n_params > 0 && n_weights >= 0 && n_weights <= n_params && step >= 1, "adam: bad sizes");
+  REQUIRE(c, grad && theta && m && v, "adam: null pointer");
+  return dsmc::launch_adam(c, n_weights, n_params - n_weights, grad, theta, m, v, weights_bf16, biases, lr, beta1,
+                           beta2, eps, step, S(stream));
+}
+
+int dsmc_train_step(dsmc_ctx_t* c, const dsmc_mlp_t* mlp, float* theta, float* m, float* v, int64_t step,
+                    float lr, uint64_t seed, int64_t n, const double* vi, const double* vj, const double* T,
+                    const double* vi_target, const double* vj_target, float* grad, double* loss,
+                    uint16_t* weights_bf16, float* biases, void* ws, size_t ws_bytes, void* stream) {
+  int rc = dsmc_train_loss_grad(c, mlp, theta, seed, (uint64_t)step, n, vi, vj, T, vi_target, vj_target, grad,
+                                loss, ws, ws_bytes, stream);
+  if (rc) return rc;
+  const int32_t np = dsmc_mlp_param_count(mlp);
+  const int32_t nw = np - (mlp->n_hidden * mlp->width + mlp->d_out);
+  return dsmc_adam_step(c, np, nw, grad, theta, m, v, step, lr, 0.9f, 0.999f, 1e-8f, weights_bf16, biases,
+                        stream);
 }
 
 // ---------------------------------------------------------------- whole step

@@ -163,11 +163,19 @@ int launch_collide_neural(Ctx* c, const dsmc_gas_t& gas, const dsmc_mlp_t& mlp,
 
 int launch_mlp_forward(Ctx* c, const dsmc_mlp_t& mlp, const uint16_t* w, const float* bias,
                        int64_t n, const float* x, float* y, cudaStream_t s);
-int launch_tc_selftest(Ctx* c, int N, int K, const uint16_t* A, const uint16_t* B, float* D,
+int launch_tc_selftest(Ctx* c, int N, int K, int layout, const uint16_t* A, const uint16_t* B, float* D,
                        cudaStream_t s);
 int cooperative_blocks(Ctx* c, const void* kernel, int threads, size_t smem);
 int launch_selftest_barrier(Ctx* c, uint64_t limit_ns, cudaStream_t s);
 int launch_selftest_mbar(Ctx* c, uint64_t limit_ns, cudaStream_t s);
+
+size_t train_ws(int sms);
+int launch_train(Ctx* c, const dsmc_mlp_t& mlp, int mode, uint64_t seed, uint64_t t, int64_t n,
+                 const float* theta, const double* vi, const double* vj, const double* T,
+                 const double* ti, const double* tj, const double* gi, const double* gj, double* oi, double* oj,
+                 float* grad, double* loss, void* ws, size_t ws_bytes, cudaStream_t s);
+int launch_adam(Ctx* c, int n_w, int n_b, const float* grad, float* master, float* m, float* v, uint16_t* w,
+                float* bias, float lr, double b1, double b2, double eps, int64_t step, cudaStream_t s);
 
 // exclusive scan of int32 counts -> offsets[n+1] (offsets[n] = total)
 size_t scan_ws(int64_t n);

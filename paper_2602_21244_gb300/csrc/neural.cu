@@ -255,18 +255,33 @@ __global__ void __launch_bounds__(kThreads) k_mlp_forward(MlpShape sh, const uin
 
 // ---------------------------------------------------------------- tensor-core self test
 // D[128 x N] = A[128 x K] B[N x K]^T with the same operand layout and MMA
-// issue as the MLP (one CTA).
-__global__ void __launch_bounds__(128) k_tc_selftest(int N, int K, const uint16_t* __restrict__ A,
+// issue as the MLP (one CTA).  layout bit 0: A stored MN-major (the tile of
+// A^T, rows = k), bit 1: B stored MN-major, bit 2: exchange the roles of the
+// two descriptor offsets for MN-major operands (diagnostic).
+__device__ __forceinline__ uint64_t operand_desc(uint32_t base, int mn_major, int swap, int MN, int K, int s) {
+  if (!mn_major) return tc::sdesc(base + 256u * s, 128, (uint32_t)(K / 8) * 128);
+  // MN-major: core matrices along MN are 128 B apart, along K (8 rows) MN/8*128 B
+  const uint32_t mn_stride = 128, k_stride = (uint32_t)(MN / 8) * 128;
+  const uint32_t start = base + 2u * k_stride * s;
+  return swap ? tc::sdesc(start, mn_stride, k_stride) : tc::sdesc(start, k_stride, mn_stride);
+}
+
+__global__ void __launch_bounds__(128) k_tc_selftest(int N, int K, int layout, const uint16_t* __restrict__ A,
                                                      const uint16_t* __restrict__ B, float* __restrict__ D,
                                                      int* status) {
   extern __shared__ __align__(1024) char smem[];
   const uint32_t a_off = 0, b_off = 128u * K * 2, mb = b_off + (uint32_t)N * K * 2;
   const uint32_t tp = mb + 8, fl = tp + 4;
   const int t = threadIdx.x;
-  for (int e = t; e < 128 * K; e += 128)
-    *(uint16_t*)(smem + a_off + tc::kmajor_offset(e / K, e % K, K)) = A[e];
-  for (int e = t; e < N * K; e += 128)
-    *(uint16_t*)(smem + b_off + tc::kmajor_offset(e / K, e % K, K)) = B[e];
+  const int a_mn = layout & 1, b_mn = (layout >> 1) & 1, swap = (layout >> 2) & 1;
+  for (int e = t; e < 128 * K; e += 128) {
+    const int m = e / K, k = e % K;
+    *(uint16_t*)(smem + a_off + (a_mn ? tc::kmajor_offset(k, m, 128) : tc::kmajor_offset(m, k, K))) = A[e];
+  }
+  for (int e = t; e < N * K; e += 128) {
+    const int n = e / K, k = e % K;
+    *(uint16_t*)(smem + b_off + (b_mn ? tc::kmajor_offset(k, n, N) : tc::kmajor_offset(n, k, K))) = B[e];
+  }
   uint32_t ncols = 32;
   while ((int)ncols < N) ncols <<= 1;
   if (t < 32) { tc::tmem_alloc((uint32_t*)(smem + tp), ncols); tc::tmem_relinquish(); }
@@ -277,12 +292,12 @@ __global__ void __launch_bounds__(128) k_tc_selftest(int N, int K, const uint16_
   tc::fence_after();
   const uint32_t tmem = *(volatile uint32_t*)(smem + tp);
   const uint32_t sbase = tc::smem_u32(smem);
-  const uint32_t sbo = (uint32_t)(K / 8) * 128;
   volatile int* flag = (volatile int*)(smem + fl);
   if (t == 0) {
+    const uint32_t idesc = tc::idesc_bf16(128, N) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16);
     for (int s = 0; s < K / 16; ++s)
-      tc::mma_bf16(tmem, tc::sdesc(sbase + a_off + 256u * s, 128, sbo),
-                   tc::sdesc(sbase + b_off + 256u * s, 128, sbo), tc::idesc_bf16(128, N), s > 0);
+      tc::mma_bf16(tmem, operand_desc(sbase + a_off, a_mn, swap, 128, K, s),
+                   operand_desc(sbase + b_off, b_mn, swap, N, K, s), idesc, s > 0);
     tc::commit((uint64_t*)(smem + mb));
     *flag = tc::mbar_wait((uint64_t*)(smem + mb), 0, status, kBarrierLimitNs) ? 1 : 0;
   }
@@ -468,11 +483,12 @@ int launch_mlp_forward(Ctx* c, const dsmc_mlp_t& mlp, const uint16_t* w, const f
   return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
 }
 
-int launch_tc_selftest(Ctx* c, int N, int K, const uint16_t* A, const uint16_t* B, float* D,
+int launch_tc_selftest(Ctx* c, int N, int K, int layout, const uint16_t* A, const uint16_t* B, float* D,
                        cudaStream_t s) {
-  const int smem = 128 * K * 2 + N * K * 2 + 64 + 4096;
+  // generous allocation: every reading of the descriptor offsets stays inside it
+  const int smem = 200 * 1024;
   if (!set_smem((const void*)k_tc_selftest, smem)) return record(c, DSMC_ERR_CUDA, "tc_selftest: smem");
-  k_tc_selftest<<<1, 128, smem, s>>>(N, K, A, B, D, status_ptr(c));
+  k_tc_selftest<<<1, 128, smem, s>>>(N, K, layout, A, B, D, status_ptr(c));
   count_launches(c, 1);
   return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
 }

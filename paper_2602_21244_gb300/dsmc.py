@@ -110,7 +110,7 @@ def load(build: bool = True):
             "dsmc_collide_neural": (C.c_int, [vp, P(Gas), P(Mlp), vp, vp, u64, vp, vp, vp, vp, vp, vp,
                                               vp, vp, vp]),
             "dsmc_mlp_forward": (C.c_int, [vp, P(Mlp), vp, vp, i64, vp, vp, vp]),
-            "dsmc_tc_selftest": (C.c_int, [vp, i32, i32, vp, vp, vp, vp]),
+            "dsmc_tc_selftest": (C.c_int, [vp, i32, i32, i32, vp, vp, vp, vp]),
             "dsmc_selftest_timeout": (C.c_int, [vp, i32, u64, vp]),
             "dsmc_moment_match": (C.c_int, [vp, i32, vp, vp, vp, vp, vp, vp]),
             "dsmc_step_workspace_size": (sz, [i32, i32, i64]),
@@ -120,6 +120,17 @@ def load(build: bool = True):
                                          vp, vp, P(i64), vp]),
             "dsmc_harvest_jager": (C.c_int, [vp, P(Gas), P(Potential), i32, i64, vp, vp, vp, vp, vp,
                                              vp, vp]),
+            "dsmc_mlp_param_count": (i32, [P(Mlp)]),
+            "dsmc_train_workspace_size": (sz, [vp]),
+            "dsmc_neural_operator_forward": (C.c_int, [vp, P(Mlp), vp, u64, u64, i64, vp, vp, vp, vp, vp, vp]),
+            "dsmc_neural_operator_backward": (C.c_int, [vp, P(Mlp), vp, u64, u64, i64, vp, vp, vp, vp, vp, vp,
+                                                        vp, sz, vp]),
+            "dsmc_train_loss_grad": (C.c_int, [vp, P(Mlp), vp, u64, u64, i64, vp, vp, vp, vp, vp, vp, vp, vp,
+                                               sz, vp]),
+            "dsmc_adam_step": (C.c_int, [vp, i32, i32, vp, vp, vp, vp, i64, C.c_float, C.c_float, C.c_float,
+                                         C.c_float, vp, vp, vp]),
+            "dsmc_train_step": (C.c_int, [vp, P(Mlp), vp, vp, vp, i64, C.c_float, u64, i64, vp, vp, vp, vp,
+                                          vp, vp, vp, vp, vp, vp, sz, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -303,11 +314,11 @@ class Context:
                                                _ptr(y, torch.float32), _stream(stream)), "mlp_forward")
         return y
 
-    def tc_selftest(self, A_bits, B_bits, stream=None):
+    def tc_selftest(self, A_bits, B_bits, layout=0, stream=None):
         K = A_bits.shape[1]
         N = B_bits.shape[0]
         D = torch.empty((128, N), dtype=torch.float32, device=A_bits.device)
-        self._check(self._lib.dsmc_tc_selftest(self.h, N, K, _ptr(A_bits, torch.int16),
+        self._check(self._lib.dsmc_tc_selftest(self.h, N, K, layout, _ptr(A_bits, torch.int16),
                                                _ptr(B_bits, torch.int16), _ptr(D), _stream(stream)),
                     "tc_selftest")
         return D
@@ -330,6 +341,60 @@ class Context:
             _ptr(vj, torch.float64), _ptr(b, torch.float64), _ptr(eps, torch.float64), _ptr(vio),
             _ptr(vjo), _stream(stream)), "harvest_jager")
         return vio, vjo
+
+    # -------------------------------------------------------------- training
+    def param_count(self, mlp: Mlp) -> int:
+        return self._lib.dsmc_mlp_param_count(C.byref(mlp))
+
+    def train_workspace(self, device="cuda"):
+        nb = self._lib.dsmc_train_workspace_size(self.h)
+        return torch.empty(nb, dtype=torch.uint8, device=device)
+
+    def neural_operator_forward(self, mlp: Mlp, theta, seed, t, vi, vj, T, stream=None):
+        vin, vjn = torch.empty_like(vi), torch.empty_like(vj)
+        f64 = torch.float64
+        self._check(self._lib.dsmc_neural_operator_forward(
+            self.h, C.byref(mlp), _ptr(theta, torch.float32), seed, t, vi.shape[0], _ptr(vi, f64),
+            _ptr(vj, f64), _ptr(T, f64), _ptr(vin), _ptr(vjn), _stream(stream)), "neural_operator_forward")
+        return vin, vjn
+
+    def neural_operator_backward(self, mlp: Mlp, theta, seed, t, vi, vj, T, g_vi, g_vj, ws=None,
+                                 stream=None):
+        grad = torch.empty_like(theta)
+        ws = ws if ws is not None else self.train_workspace(theta.device)
+        f64 = torch.float64
+        self._check(self._lib.dsmc_neural_operator_backward(
+            self.h, C.byref(mlp), _ptr(theta, torch.float32), seed, t, vi.shape[0], _ptr(vi, f64),
+            _ptr(vj, f64), _ptr(T, f64), _ptr(g_vi, f64), _ptr(g_vj, f64), _ptr(grad), _ptr(ws),
+            ws.numel(), _stream(stream)), "neural_operator_backward")
+        return grad
+
+    def train_loss_grad(self, mlp: Mlp, theta, seed, t, vi, vj, T, vi_t, vj_t, ws=None, stream=None):
+        grad = torch.empty_like(theta)
+        loss = torch.zeros(1, dtype=torch.float64, device=theta.device)
+        ws = ws if ws is not None else self.train_workspace(theta.device)
+        f64 = torch.float64
+        self._check(self._lib.dsmc_train_loss_grad(
+            self.h, C.byref(mlp), _ptr(theta, torch.float32), seed, t, vi.shape[0], _ptr(vi, f64),
+            _ptr(vj, f64), _ptr(T, f64), _ptr(vi_t, f64), _ptr(vj_t, f64), _ptr(grad), _ptr(loss),
+            _ptr(ws), ws.numel(), _stream(stream)), "train_loss_grad")
+        return grad, loss
+
+    def adam_step(self, n_weights, grad, theta, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                  w_bits=None, bias=None, stream=None):
+        self._check(self._lib.dsmc_adam_step(
+            self.h, theta.numel(), n_weights, _ptr(grad, torch.float32), _ptr(theta, torch.float32),
+            _ptr(m, torch.float32), _ptr(v, torch.float32), step, lr, beta1, beta2, eps,
+            _ptr(w_bits, torch.int16), _ptr(bias, torch.float32), _stream(stream)), "adam_step")
+
+    def train_step(self, mlp: Mlp, theta, m, v, step, lr, seed, vi, vj, T, vi_t, vj_t, grad, loss,
+                   ws, w_bits=None, bias=None, stream=None):
+        f64 = torch.float64
+        self._check(self._lib.dsmc_train_step(
+            self.h, C.byref(mlp), _ptr(theta, torch.float32), _ptr(m), _ptr(v), step, lr, seed,
+            vi.shape[0], _ptr(vi, f64), _ptr(vj, f64), _ptr(T, f64), _ptr(vi_t, f64), _ptr(vj_t, f64),
+            _ptr(grad), _ptr(loss), _ptr(w_bits, torch.int16), _ptr(bias, torch.float32), _ptr(ws),
+            ws.numel(), _stream(stream)), "train_step")
 
     # -------------------------------------------------------------- whole step
     def step_workspace_size(self, n, n_cells, capacity) -> int:
@@ -426,3 +491,31 @@ def make_path(kind: int, pot: Potential | None = None, n_nodes: int = 32, mlp: M
     P.biases = bias.data_ptr() if bias is not None else None
     P._keep = (pot, mlp, w_bits, bias)
     return P
+
+
+class NeuralCollisionOperator(torch.autograd.Function):
+    """The neural collision operator on a batch of pairs in pseudo-cells of 16
+    (MLP, shell projection, centre-of-mass update, moment matching) as a
+    differentiable function of the FP32 parameters theta.  Forward and the
+    hand-written backward both run in the library (dsmc_neural_operator_*);
+    this class only hands tensors across."""
+
+    @staticmethod
+    def forward(ctx, theta, vi, vj, T, context, mlp, seed, t):
+        vin, vjn = context.neural_operator_forward(mlp, theta, seed, t, vi, vj, T)
+        ctx.save_for_backward(theta, vi, vj, T)
+        ctx.args = (context, mlp, seed, t)
+        return vin, vjn
+
+    @staticmethod
+    def backward(ctx, g_vi, g_vj):
+        theta, vi, vj, T = ctx.saved_tensors
+        context, mlp, seed, t = ctx.args
+        if g_vi is None:
+            g_vi = torch.zeros_like(vi)
+        if g_vj is None:
+            g_vj = torch.zeros_like(vj)
+        grad = context.neural_operator_backward(mlp, theta, seed, t, vi, vj, T,
+                                                g_vi.contiguous().to(torch.float64),
+                                                g_vj.contiguous().to(torch.float64))
+        return grad, None, None, None, None, None, None, None

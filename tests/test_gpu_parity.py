@@ -42,14 +42,15 @@ def oracle_sorted(w):
 
 # ------------------------------------------------------------------ tensor-core layout
 
-@pytest.mark.parametrize("N,K", [(16, 16), (128, 16), (16, 128), (128, 128), (256, 64)])
-def test_tc_selftest_matches_matmul(N, K):
+@pytest.mark.parametrize("layout", [0, 1, 2, 3])
+@pytest.mark.parametrize("N,K", [(16, 16), (128, 16), (16, 128), (128, 128), (256, 64), (32, 128)])
+def test_tc_selftest_matches_matmul(N, K, layout):
     T = torch()
     rng = np.random.default_rng(N * 1000 + K)
     A = rng.standard_normal((128, K))
     B = rng.standard_normal((N, K))
     Ab, Bb = W.bf16_bits(A), W.bf16_bits(B)
-    D = host(ctx().tc_selftest(w_bits_tensor(Ab), w_bits_tensor(Bb)))
+    D = host(ctx().tc_selftest(w_bits_tensor(Ab), w_bits_tensor(Bb), layout=layout))
     ref = W.bf16_value(Ab) @ W.bf16_value(Bb).T
     assert np.abs(D - ref).max() <= 1e-4 * np.abs(ref).max() + 1e-5
     assert ctx().sync_status() == 0
