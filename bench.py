@@ -8,8 +8,10 @@ cells around a disc, about 9.2 million particles, Mach-10 shock profile).
 Timing: W untimed warm-up steps, then K timed steps.  Before every step
 the pristine unsorted input (cell ids and velocities, 258 MB, larger than
 L2) is copied back, outside the timed region, so each step sorts a
-shuffled gas and starts with a cold L2.  Each step is bracketed by CUDA
-events on the launching stream; per-phase events give the per-kernel times.
+shuffled gas and starts with a cold L2.  The headline times the whole step
+as one CUDA graph (dsmc_step_graph_launch) between CUDA events on its
+stream; a second, un-graphed pass with events between the phases gives the
+per-phase (per-kernel) times.
 
 Output: one JSON line on rank 0.  The headline ``value`` is accepted pair
 collisions per second of the whole step on the neural path; ``paths``
@@ -183,10 +185,38 @@ def run_gb300(args, rank, world, dist):
                 rounds.append(inf["n_rounds"])
         launches = C.launch_count() - launches0
         K = args.steps
+        # the same step as one CUDA graph (the production path): timed alone
+        path_d = D.make_path({"vhs": D.PATH_VHS, "jager": D.PATH_JAGER, "neural": D.PATH_NEURAL}[path],
+                             pot=pot, n_nodes=args.n_nodes, mlp=mlp, w_bits=w_bits, bias=bias)
+        gstream = torch.cuda.Stream(device=dev)
+        torch.cuda.synchronize()
+        C.sigma_g_max_init(gas, T_cell, 5.0, out=st.sigma_g_max)
+        C.step_graph_capture(gas, path_d, st, gstream)
+        g_ms, g_pairs, lg0 = 0.0, 0, None
+        for it in range(args.warmup + args.steps):
+            if it == args.warmup:
+                torch.cuda.synchronize()
+                lg0 = C.launch_count()
+            with torch.cuda.stream(gstream):
+                restore()
+                e0, e1 = ev(), ev()
+                e0.record(gstream)
+                C.step_graph_launch(it, gstream)
+                e1.record(gstream)
+            if it >= args.warmup:
+                torch.cuda.synchronize()
+                if C.sync_status(gstream) != 0:
+                    raise RuntimeError(f"device status on graph path {path}")
+                g_ms += e0.elapsed_time(e1)
+                g_pairs += st.info_host()["n_pairs"]
+        torch.cuda.synchronize()
+        g_launches = C.launch_count() - lg0
         results[path] = dict(
-            collisions_per_s=pairs / (step_ms * 1e-3), ms_per_step=step_ms / K,
+            collisions_per_s=g_pairs / (g_ms * 1e-3), ms_per_step=g_ms / K,
+            phased=dict(collisions_per_s=pairs / (step_ms * 1e-3), ms_per_step=step_ms / K),
             pairs_per_step=pairs / K, rounds_per_step=float(np.mean(rounds)),
-            phase_ms={k: v / K for k, v in phase_ms.items()}, gpu_launches=launches,
+            phase_ms={k: v / K for k, v in phase_ms.items()}, gpu_launches=g_launches,
+            phased_gpu_launches=launches,
             step_ms_total=step_ms, pairs_total=pairs)
         if path == "neural":
             neural_kernel = dict(ms=phase_ms["collide"] / K, pairs=pairs / K)

@@ -332,6 +332,17 @@ size_t dsmc_step_workspace_size(int32_t n, int32_t n_cells, int64_t capacity);
 int dsmc_step(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_path_t* path,
               const dsmc_step_buffers_t* buf, uint64_t step, void* stream);
 
+/* Capture one whole step -- dsmc_step with these arguments -- as a CUDA
+ * graph owned by the context (replacing any earlier one).  The buffers must
+ * stay allocated while the graph is used.  `stream` must be a non-default
+ * stream; nothing runs during the capture.  In the graph the kernels read the
+ * step index from device memory, so one graph serves every step. */
+int dsmc_step_graph_capture(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_path_t* path,
+                            const dsmc_step_buffers_t* buf, void* stream);
+/* Run the captured step for step index `step` on `stream`: same results as
+ * dsmc_step(..., step, ...). */
+int dsmc_step_graph_launch(dsmc_ctx_t* ctx, uint64_t step, void* stream);
+
 /* Same step from and to HOST memory: copies cell_id_host / v*_host into
  * device buffers reserved by dsmc_ctx_reserve, runs dsmc_step, copies the
  * sorted post-collision velocities and perm back, and synchronises the

@@ -25,6 +25,10 @@ struct Ctx {
   double* r_T = nullptr;
   void* r_host_info = nullptr;
   int64_t launches = 0;
+  int64_t graph_launches = 0;
+  // step graph
+  cudaGraphExec_t graph_exec = nullptr;
+  bool capturing = false;
 };
 
 int record(Ctx* c, int code, const char* msg) {
@@ -35,6 +39,11 @@ int* status_ptr(Ctx* c) { return c->d_status; }
 unsigned* barrier_ptr(Ctx* c) { return c->d_bar; }
 int sm_count(Ctx* c) { return c->sms; }
 void count_launches(Ctx* c, int k) { c->launches += k; }
+// the step index of a graph replay lives 64 bytes into the barrier block
+static uint64_t* step_slot(Ctx* c) { return (uint64_t*)((char*)c->d_bar + 64); }
+const uint64_t* graph_step_ptr(Ctx* c) { return c->capturing ? step_slot(c) : nullptr; }
+
+__global__ void k_set_step(uint64_t* slot, uint64_t step) { *slot = step; }
 
 }  // namespace dsmc
 
@@ -83,6 +92,7 @@ void dsmc_ctx_destroy(dsmc_ctx_t* c) {
   if (c->h_status) cudaFreeHost(c->h_status);
   if (c->r_mem) cudaFree(c->r_mem);
   if (c->r_host_info) cudaFreeHost(c->r_host_info);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   delete c;
 }
 
@@ -378,6 +388,41 @@ int dsmc_step(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t* path,
   }
   if (rc) return rc;
   return dsmc_moment_match(c, B->n_cells, B->cell_start, B->mom, B->svx, B->svy, B->svz, stream);
+}
+
+int dsmc_step_graph_capture(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t* path,
+                            const dsmc_step_buffers_t* B, void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, gas && path && B, "graph_capture: null argument");
+  REQUIRE(c, stream, "graph_capture: needs a non-default stream");
+  if (c->graph_exec) { cudaGraphExecDestroy(c->graph_exec); c->graph_exec = nullptr; }
+  cudaStream_t s = S(stream);
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+    return dsmc::record(c, DSMC_ERR_CUDA, "graph_capture: cudaStreamBeginCapture failed");
+  c->capturing = true;
+  const int64_t launches0 = c->launches;
+  const int rc = dsmc_step(c, gas, path, B, 0, stream);
+  c->capturing = false;
+  c->graph_launches = c->launches - launches0;
+  c->launches = launches0;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+  if (e != cudaSuccess || !g) return dsmc::record(c, DSMC_ERR_CUDA, "graph_capture: cudaStreamEndCapture failed");
+  const cudaError_t ei = cudaGraphInstantiate(&c->graph_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) { c->graph_exec = nullptr; return dsmc::record(c, DSMC_ERR_CUDA, "graph_capture: instantiate failed"); }
+  return DSMC_OK;
+}
+
+int dsmc_step_graph_launch(dsmc_ctx_t* c, uint64_t step, void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, c->graph_exec, "graph_launch: no captured step (dsmc_step_graph_capture)");
+  dsmc::k_set_step<<<1, 1, 0, S(stream)>>>(dsmc::step_slot(c), step);
+  if (cudaGraphLaunch(c->graph_exec, S(stream)) != cudaSuccess)
+    return dsmc::record(c, DSMC_ERR_CUDA, "graph_launch: cudaGraphLaunch failed");
+  c->launches += 1 + c->graph_launches;
+  return DSMC_OK;
 }
 
 int dsmc_ctx_reserve(dsmc_ctx_t* c, int32_t n_max, int32_t n_cells, int64_t capacity) {

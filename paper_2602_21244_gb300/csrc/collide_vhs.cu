@@ -11,6 +11,7 @@ namespace dsmc {
 
 struct VhsArgs {
   uint64_t seed, step;
+  const uint64_t* step_dev;
   const int4* pairs;
   const int32_t* ro;
   const dsmc_select_info_t* info;
@@ -20,6 +21,7 @@ struct VhsArgs {
 };
 
 __global__ void __launch_bounds__(256) k_collide_vhs(VhsArgs a) {
+  if (a.step_dev) a.step = *a.step_dev;
   const int R = a.info->n_rounds;
   const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
   for (int r = 0; r < R; ++r) {
@@ -58,7 +60,7 @@ int launch_collide_vhs(Ctx* c, const dsmc_gas_t& gas, uint64_t step, const int32
   static int blocks = 0;
   if (!blocks) blocks = cooperative_blocks(c, (const void*)k_collide_vhs, 256, 0);
   if (!blocks) return record(c, DSMC_ERR_CUDA, "collide_vhs: occupancy query failed");
-  VhsArgs a{gas.seed, step, (const int4*)pairs, ro, info, vx, vy, vz, barrier_ptr(c), status_ptr(c)};
+  VhsArgs a{gas.seed, step, graph_step_ptr(c), (const int4*)pairs, ro, info, vx, vy, vz, barrier_ptr(c), status_ptr(c)};
   if (cudaMemsetAsync(a.bar, 0, 4 * sizeof(unsigned), s) != cudaSuccess) return DSMC_ERR_CUDA;
   void* args[] = {&a};
   if (cudaLaunchCooperativeKernel((const void*)k_collide_vhs, dim3(blocks), dim3(256), args, 0, s) !=

@@ -124,6 +124,9 @@ int* status_ptr(Ctx* c);
 unsigned* barrier_ptr(Ctx* c);  // 4 words of device memory per barrier slot
 int sm_count(Ctx* c);
 void count_launches(Ctx* c, int k);  // kernels launched by this context
+// Device address the kernels read the step index from while a step graph is
+// being captured (null otherwise: the step is then a kernel argument).
+const uint64_t* graph_step_ptr(Ctx* c);
 
 // launchers (return 0 or a DSMC_ERR_* code)
 int launch_sort(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_id, const double* vx,

@@ -366,6 +366,7 @@ __device__ __forceinline__ void deflect(double u, double v, double w, double cc,
 
 struct JagerArgs {
   uint64_t seed, step;
+  const uint64_t* step_dev;
   double bmax_A;
   const int4* pairs;
   const int32_t* ro;
@@ -377,6 +378,7 @@ struct JagerArgs {
 };
 
 __global__ void __launch_bounds__(128) k_collide_jager(PotDev P, JagerArgs a) {
+  if (a.step_dev) a.step = *a.step_dev;
   const int R = a.info->n_rounds;
   const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
   for (int r = 0; r < R; ++r) {
@@ -453,7 +455,7 @@ int launch_collide_jager(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& 
   if (!blocks) blocks = cooperative_blocks(c, (const void*)k_collide_jager, 128, 0);
   if (!blocks) return record(c, DSMC_ERR_CUDA, "collide_jager: occupancy query failed");
   PotDev P = make_pot(gas, pot, n_nodes);
-  JagerArgs a{gas.seed, step, gas.b_max * 1e10, (const int4*)pairs, ro, info, vx, vy, vz,
+  JagerArgs a{gas.seed, step, graph_step_ptr(c), gas.b_max * 1e10, (const int4*)pairs, ro, info, vx, vy, vz,
               chi_out, barrier_ptr(c), status_ptr(c)};
   if (cudaMemsetAsync(a.bar, 0, 4 * sizeof(unsigned), s) != cudaSuccess) return DSMC_ERR_CUDA;
   void* args[] = {&P, &a};

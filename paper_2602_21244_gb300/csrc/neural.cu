@@ -320,6 +320,7 @@ __global__ void __launch_bounds__(128) k_tc_selftest(int N, int K, int layout, c
 // ---------------------------------------------------------------- collide
 struct NeuralArgs {
   uint64_t seed, step;
+  const uint64_t* step_dev;
   double sigma_v_inv, T_ref_inv, m_over_3k, eps;
   const double* mom;
   float* u_out;
@@ -341,6 +342,7 @@ __device__ __forceinline__ void box_muller(double u1, double u2, float* z0, floa
 
 __global__ void __launch_bounds__(kThreads) k_collide_neural(MlpShape sh, const uint16_t* __restrict__ w,
                                                            const float* __restrict__ bias, NeuralArgs a) {
+  if (a.step_dev) a.step = *a.step_dev;
   extern __shared__ __align__(1024) char smem[];
   const MlpLayout L = mlp_layout(sh.n_hidden);
   load_weights(smem, L, sh, w, bias);
@@ -450,7 +452,7 @@ int launch_collide_neural(Ctx* c, const dsmc_gas_t& gas, const dsmc_mlp_t& mlp,
   const int blocks = cooperative_blocks(c, (const void*)k_collide_neural, kThreads, L.total);
   if (!blocks) return record(c, DSMC_ERR_CUDA, "collide_neural: occupancy query failed");
   NeuralArgs a;
-  a.seed = gas.seed; a.step = step;
+  a.seed = gas.seed; a.step = step; a.step_dev = graph_step_ptr(c);
   a.sigma_v_inv = 1.0 / mlp.sigma_v; a.T_ref_inv = 1.0 / mlp.T_ref;
   a.m_over_3k = gas.mass / (3.0 * DSMC_KB); a.eps = mlp.eps;
   a.mom = mom; a.u_out = u_out; a.pairs = (const int4*)pairs; a.ro = ro; a.info = info;

@@ -36,6 +36,7 @@ struct SelArgs {
   int32_t model;
   int64_t capacity;
   uint64_t seed, step;
+  const uint64_t* step_dev;  // if set, the step index is read here (graph replay)
   double fn, dt;
   // model 0: sigma(g) = pid2 * pow(x, om_half) / gam, x = two_kt / ((mr g) g)
   double pid2, om_half, gam, two_kt, mr;
@@ -163,6 +164,7 @@ __device__ __forceinline__ CellView stage_cell(const SelArgs& a, float* sm, int3
 }
 
 __global__ void __launch_bounds__(kSelWarps * 32) k_sel_count(SelArgs a) {
+  if (a.step_dev) a.step = *a.step_dev;
   __shared__ float stage[kSelWarps][3 * kStage];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int32_t warps = gridDim.x * kSelWarps;
@@ -197,6 +199,7 @@ __global__ void __launch_bounds__(kSelWarps * 32) k_sel_count(SelArgs a) {
 }
 
 __global__ void __launch_bounds__(kSelWarps * 32) k_sel_emit(SelArgs a) {
+  if (a.step_dev) a.step = *a.step_dev;
   __shared__ float stage[kSelWarps][3 * kStage];
   __shared__ int hist[DSMC_MAX_ROUNDS];
   __shared__ int rmax_blk;
@@ -358,7 +361,7 @@ int launch_select(Ctx* c, const dsmc_gas_t& gas, int32_t n, int32_t n_cells, con
   a.counts = w.counts; a.offs = w.offs; a.tmp = w.tmp; a.tmp_round = w.tmp_round;
   a.last = w.last; a.round_count = w.round_count; a.n_rounds = w.n_rounds; a.n_cand = w.n_cand;
   a.status = status_ptr(c); a.n_cells = n_cells; a.model = gas.model; a.capacity = capacity;
-  a.seed = gas.seed; a.step = step; a.fn = gas.fn_over_vc; a.dt = gas.dt;
+  a.seed = gas.seed; a.step = step; a.step_dev = graph_step_ptr(c); a.fn = gas.fn_over_vc; a.dt = gas.dt;
   a.pid2 = DSMC_PI * gas.d_ref * gas.d_ref;
   a.om_half = gas.omega - 0.5;
   a.gam = tgamma(2.5 - gas.omega);

@@ -116,6 +116,8 @@ def load(build: bool = True):
             "dsmc_step_workspace_size": (sz, [i32, i32, i64]),
             "dsmc_step": (C.c_int, [vp, P(Gas), P(Path), P(StepBuffers), u64, vp]),
             "dsmc_ctx_reserve": (C.c_int, [vp, i32, i32, i64]),
+            "dsmc_step_graph_capture": (C.c_int, [vp, P(Gas), P(Path), P(StepBuffers), vp]),
+            "dsmc_step_graph_launch": (C.c_int, [vp, u64, vp]),
             "dsmc_step_host": (C.c_int, [vp, P(Gas), P(Path), i32, vp, vp, vp, vp, vp, u64, vp, vp,
                                          vp, vp, P(i64), vp]),
             "dsmc_harvest_jager": (C.c_int, [vp, P(Gas), P(Potential), i32, i64, vp, vp, vp, vp, vp,
@@ -403,6 +405,16 @@ class Context:
     def step(self, gas: Gas, path: Path, bufs: "StepState", step: int, stream=None):
         self._check(self._lib.dsmc_step(self.h, C.byref(gas), C.byref(path), C.byref(bufs.desc),
                                         step, _stream(stream)), "step")
+
+    def step_graph_capture(self, gas: Gas, path: Path, bufs: "StepState", stream):
+        """Capture a whole step as a CUDA graph (stream: a non-default torch stream)."""
+        self._graph_keep = (gas, path, bufs)
+        self._check(self._lib.dsmc_step_graph_capture(self.h, C.byref(gas), C.byref(path),
+                                                      C.byref(bufs.desc), _stream(stream)),
+                    "step_graph_capture")
+
+    def step_graph_launch(self, step: int, stream=None):
+        self._check(self._lib.dsmc_step_graph_launch(self.h, step, _stream(stream)), "step_graph_launch")
 
     def reserve(self, n_max, n_cells, capacity):
         self._check(self._lib.dsmc_ctx_reserve(self.h, n_max, n_cells, capacity), "reserve")

@@ -404,3 +404,38 @@ def test_bounded_waits_time_out_without_hanging(which):
     w = wl("couette")
     out = C.sort_cells(cuda(w["cell_id"]), cuda(w["vx"]), cuda(w["vy"]), cuda(w["vz"]), w["n_cells"])
     assert C.sync_status() == 0
+
+
+# ------------------------------------------------------------------ CUDA graph of the step
+
+@pytest.mark.parametrize("kind", ["vhs", "jager", "neural"])
+def test_step_graph_replay_equals_direct_step(kind):
+    from paper_2602_21244_gb300 import dsmc as D
+    T = torch()
+    w = wl("hyper01")
+    C = ctx()
+    n, nc = len(w["cell_id"]), w["n_cells"]
+    gas = D.make_gas(dict(w["gas"], model=0 if kind == "vhs" else 1))
+    wts, bias, _, mlp_d = _mlp_setup()
+    path = D.make_path({"vhs": D.PATH_VHS, "jager": D.PATH_JAGER, "neural": D.PATH_NEURAL}[kind],
+                       pot=D.make_potential(JP), n_nodes=32, mlp=mlp_d,
+                       w_bits=w_bits_tensor(wts["W_bits"]), bias=cuda(bias, T.float32))
+    sts = [D.StepState(C, n, nc, 1 << 21) for _ in range(2)]
+    for st in sts:
+        C.sigma_g_max_init(gas, cuda(w["T_cell"]), 5.0, out=st.sigma_g_max)
+    s = T.cuda.Stream()
+    T.cuda.synchronize()
+    C.step_graph_capture(gas, path, sts[1], s)
+    for step in (0, 1, 2):
+        for st in sts:
+            st.cell_id.copy_(cuda(w["cell_id"])); st.vx.copy_(cuda(w["vx"]))
+            st.vy.copy_(cuda(w["vy"])); st.vz.copy_(cuda(w["vz"]))
+        T.cuda.synchronize()
+        C.step(gas, path, sts[0], step)
+        C.step_graph_launch(step, s)
+        T.cuda.synchronize()
+        assert C.sync_status() == 0
+        a, b = sts
+        assert a.info_host() == b.info_host()
+        for k in ("perm", "cell_start", "svx", "svy", "svz", "sigma_g_max", "mom"):
+            assert T.equal(getattr(a, k), getattr(b, k)), (kind, step, k)
