@@ -24,6 +24,10 @@
  *  - Results depend only on the inputs, the seed and the step index, never
  *    on the launch configuration.
  *  - Status codes: 0 = DSMC_OK, negative = error (see below).
+ *  - The collide kernels of one context share its grid-barrier words: direct
+ *    collide calls of one context must not overlap on the GPU (issue them on
+ *    one stream, or use one context per stream).  A captured step graph has
+ *    words of its own and may overlap direct calls.
  */
 #ifndef DSMC_H_
 #define DSMC_H_

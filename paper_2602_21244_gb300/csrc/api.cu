@@ -36,7 +36,9 @@ int record(Ctx* c, int code, const char* msg) {
   return code;
 }
 int* status_ptr(Ctx* c) { return c->d_status; }
-unsigned* barrier_ptr(Ctx* c) { return c->d_bar; }
+// grid-barrier words: one slot for direct calls, another for graph replays,
+// so that a replay and a direct call on another stream do not share counters
+unsigned* barrier_ptr(Ctx* c) { return c->capturing ? c->d_bar + 32 : c->d_bar; }
 int sm_count(Ctx* c) { return c->sms; }
 void count_launches(Ctx* c, int k) { c->launches += k; }
 // the step index of a graph replay lives 64 bytes into the barrier block

@@ -128,7 +128,7 @@ constexpr int kFixWarps = 8;
 constexpr int kFixCap = 1024;  // cells up to this size sort in shared memory
 
 // Warp per cell: order the cell's slot contents ascending (bitonic network in
-// shared memory; rank counting for larger cells), then gather velocities.
+// shared memory; rank counting for larger cells).
 __global__ void __launch_bounds__(kFixWarps * 32)
 k_fix_gather(int32_t n_cells, const int32_t* __restrict__ cell_start,
              const int32_t* __restrict__ slots, int32_t* __restrict__ perm,
@@ -169,13 +169,18 @@ k_fix_gather(int32_t n_cells, const int32_t* __restrict__ cell_start,
         perm[a + r] = x;
       }
     }
-    __syncwarp();
-    for (int t = lane; t < N; t += 32) {
-      const int32_t src = perm[a + t];
-      svx[a + t] = vx[src];
-      svy[a + t] = vy[src];
-      svz[a + t] = vz[src];
-    }
+  }
+}
+
+// Thread per sorted slot: gather the velocities (independent random loads).
+__global__ void k_gather(int32_t n, const int32_t* __restrict__ perm, const double* __restrict__ vx,
+                         const double* __restrict__ vy, const double* __restrict__ vz,
+                         double* __restrict__ svx, double* __restrict__ svy, double* __restrict__ svz) {
+  for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const int32_t src = perm[s];
+    svx[s] = vx[src];
+    svy[s] = vy[src];
+    svz[s] = vz[src];
   }
 }
 
@@ -214,35 +219,49 @@ int launch_sort(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_id, cons
   k_scatter<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(cell_id, n, n_cells, cell_start, counts, slots);
   k_fix_gather<<<grid_for(n_cells, kFixWarps, sms * 4), kFixWarps * 32, 0, s>>>(
       n_cells, cell_start, slots, perm, vx, vy, vz, svx, svy, svz);
-  count_launches(c, 2);
+  k_gather<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(n, perm, vx, vy, vz, svx, svy, svz);
+  count_launches(c, 3);
   return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
 }
 
 // ---------------------------------------------------------------- moments
+// Eight lanes per cell (four cells per warp): the FP64 reduction trees have
+// three levels, and GB300's FP64 pipe is the bound of these kernels.
 constexpr int kCellWarps = 8;
+constexpr int kSeg = 8;
+
+__device__ __forceinline__ double seg_sum(double v) {
+#pragma unroll
+  for (int o = kSeg / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
 __global__ void __launch_bounds__(kCellWarps * 32)
 k_moments(int32_t n_cells, const int32_t* __restrict__ cs, const double* __restrict__ vx,
           const double* __restrict__ vy, const double* __restrict__ vz, double* __restrict__ mom,
           int* status) {
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, sl = lane & (kSeg - 1), seg = lane / kSeg;
+  const int32_t per_warp = 32 / kSeg;
   const int32_t warps = gridDim.x * kCellWarps;
-  for (int32_t k = blockIdx.x * kCellWarps + (threadIdx.x >> 5); k < n_cells; k += warps) {
-    const int32_t a = cs[k], b = cs[k + 1];
+  for (int32_t k0 = (blockIdx.x * kCellWarps + (threadIdx.x >> 5)) * per_warp; k0 < n_cells;
+       k0 += warps * per_warp) {
+    const int32_t k = k0 + seg;
+    const bool has = k < n_cells;
+    const int32_t a = has ? cs[k] : 0, b = has ? cs[k + 1] : 0;
     double sx = 0, sy = 0, sz = 0;
-    for (int32_t i = a + lane; i < b; i += 32) { sx += vx[i]; sy += vy[i]; sz += vz[i]; }
-    sx = warp_sum(sx); sy = warp_sum(sy); sz = warp_sum(sz);
+    for (int32_t i = a + sl; i < b; i += kSeg) { sx += vx[i]; sy += vy[i]; sz += vz[i]; }
+    sx = seg_sum(sx); sy = seg_sum(sy); sz = seg_sum(sz);
     const double n = (double)(b - a);
     double th = 0;
     if (b > a) {
       const double ux = sx / n, uy = sy / n, uz = sz / n;
-      for (int32_t i = a + lane; i < b; i += 32) {
+      for (int32_t i = a + sl; i < b; i += kSeg) {
         const double dx = vx[i] - ux, dy = vy[i] - uy, dz = vz[i] - uz;
         th += dx * dx + dy * dy + dz * dz;
       }
-      th = warp_sum(th);
     }
-    if (lane == 0) {
+    th = seg_sum(th);
+    if (has && sl == 0) {
       if (!isfinite(sx + sy + sz + th)) set_status(status, DSMC_ERR_NONFINITE);
       double* m = mom + 5 * (size_t)k;
       m[0] = n; m[1] = sx; m[2] = sy; m[3] = sz; m[4] = th;
@@ -253,40 +272,46 @@ k_moments(int32_t n_cells, const int32_t* __restrict__ cs, const double* __restr
 int launch_moments(Ctx* c, int32_t n_cells, const int32_t* cs, const double* vx,
                    const double* vy, const double* vz, double* mom, cudaStream_t s) {
   if (n_cells <= 0) return 0;
-  k_moments<<<grid_for(n_cells, kCellWarps, sm_count(c) * 8), kCellWarps * 32, 0, s>>>(
+  k_moments<<<grid_for((n_cells + 3) / 4, kCellWarps, sm_count(c) * 8), kCellWarps * 32, 0, s>>>(
       n_cells, cs, vx, vy, vz, mom, status_ptr(c));
   count_launches(c, 1);
   return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
 }
 
 // ---------------------------------------------------------------- moment matching
-// Sec. 2.5 (centred): v <- u_pre + alpha (v - u_post), alpha = sqrt(Th_pre/Th_post).
+// Sec. 2.5 (centred): v <- u_pre + alpha (v - u_post), alpha = sqrt(Th_pre/Th_post),
+// applied as v <- alpha v + (u_pre - alpha u_post).
 __global__ void __launch_bounds__(kCellWarps * 32)
 k_moment_match(int32_t n_cells, const int32_t* __restrict__ cs, const double* __restrict__ mom,
                double* __restrict__ vx, double* __restrict__ vy, double* __restrict__ vz) {
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, sl = lane & (kSeg - 1), seg = lane / kSeg;
+  const int32_t per_warp = 32 / kSeg;
   const int32_t warps = gridDim.x * kCellWarps;
-  for (int32_t k = blockIdx.x * kCellWarps + (threadIdx.x >> 5); k < n_cells; k += warps) {
-    const int32_t a = cs[k], b = cs[k + 1];
-    if (b <= a) continue;
+  for (int32_t k0 = (blockIdx.x * kCellWarps + (threadIdx.x >> 5)) * per_warp; k0 < n_cells;
+       k0 += warps * per_warp) {
+    const int32_t k = k0 + seg;
+    const bool has = k < n_cells;
+    const int32_t a = has ? cs[k] : 0, b = has ? cs[k + 1] : 0;
     double sx = 0, sy = 0, sz = 0;
-    for (int32_t i = a + lane; i < b; i += 32) { sx += vx[i]; sy += vy[i]; sz += vz[i]; }
-    sx = warp_sum(sx); sy = warp_sum(sy); sz = warp_sum(sz);
+    for (int32_t i = a + sl; i < b; i += kSeg) { sx += vx[i]; sy += vy[i]; sz += vz[i]; }
+    sx = seg_sum(sx); sy = seg_sum(sy); sz = seg_sum(sz);
     const double n = (double)(b - a);
-    const double ux = sx / n, uy = sy / n, uz = sz / n;
+    const double ux = b > a ? sx / n : 0.0, uy = b > a ? sy / n : 0.0, uz = b > a ? sz / n : 0.0;
     double th = 0;
-    for (int32_t i = a + lane; i < b; i += 32) {
+    for (int32_t i = a + sl; i < b; i += kSeg) {
       const double dx = vx[i] - ux, dy = vy[i] - uy, dz = vz[i] - uz;
       th += dx * dx + dy * dy + dz * dz;
     }
-    th = warp_sum(th);
+    th = seg_sum(th);
+    if (b <= a) continue;
     const double* m = mom + 5 * (size_t)k;
     const double px = m[1] / n, py = m[2] / n, pz = m[3] / n;
     const double alpha = (b - a >= 2 && th > 0.0) ? sqrt(m[4] / th) : 1.0;
-    for (int32_t i = a + lane; i < b; i += 32) {
-      vx[i] = px + alpha * (vx[i] - ux);
-      vy[i] = py + alpha * (vy[i] - uy);
-      vz[i] = pz + alpha * (vz[i] - uz);
+    const double ox = px - alpha * ux, oy = py - alpha * uy, oz = pz - alpha * uz;
+    for (int32_t i = a + sl; i < b; i += kSeg) {
+      vx[i] = fma(alpha, vx[i], ox);
+      vy[i] = fma(alpha, vy[i], oy);
+      vz[i] = fma(alpha, vz[i], oz);
     }
   }
 }
@@ -294,7 +319,7 @@ k_moment_match(int32_t n_cells, const int32_t* __restrict__ cs, const double* __
 int launch_moment_match(Ctx* c, int32_t n_cells, const int32_t* cs, const double* mom,
                         double* vx, double* vy, double* vz, cudaStream_t s) {
   if (n_cells <= 0) return 0;
-  k_moment_match<<<grid_for(n_cells, kCellWarps, sm_count(c) * 8), kCellWarps * 32, 0, s>>>(
+  k_moment_match<<<grid_for((n_cells + 3) / 4, kCellWarps, sm_count(c) * 8), kCellWarps * 32, 0, s>>>(
       n_cells, cs, mom, vx, vy, vz);
   count_launches(c, 1);
   return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
@@ -379,6 +404,7 @@ extern "C" int dsmc_sort_cells_static(int32_t n, int32_t n_cells, const int32_t*
     k_scatter<<<grid_for(n, 256, d->sms * 16), 256, 0, s>>>(cell_id, n, n_cells, cell_start, counts, slots);
     k_fix_gather<<<grid_for(n_cells, kFixWarps, d->sms * 4), kFixWarps * 32, 0, s>>>(
         n_cells, cell_start, slots, perm, vx, vy, vz, svx, svy, svz);
+    k_gather<<<grid_for(n, 256, d->sms * 16), 256, 0, s>>>(n, perm, vx, vy, vz, svx, svy, svz);
   }
   return cudaGetLastError() == cudaSuccess ? DSMC_OK : DSMC_ERR_CUDA;
 }

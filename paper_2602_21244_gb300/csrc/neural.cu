@@ -322,6 +322,7 @@ struct NeuralArgs {
   uint64_t seed, step;
   const uint64_t* step_dev;
   double sigma_v_inv, T_ref_inv, m_over_3k, eps;
+  float sigma_v_inv_f, T_feat_f;  // 1/sigma_v and m/(3 k T_ref) in FP32 for the MLP inputs
   const double* mom;
   float* u_out;
   const int4* pairs;
@@ -332,10 +333,14 @@ struct NeuralArgs {
   int* status;
 };
 
-__device__ __forceinline__ void box_muller(double u1, double u2, float* z0, float* z1) {
-  const float rho = sqrtf(-2.f * __logf((float)(1.0 - u1)));
+// Box-Muller pair in FP32 from the top 24 bits of two Philox words:
+// rho = sqrt(-2 ln(1 - U1)), theta = 2 pi U2 (U1, U2 in [0, 1)).  The MLP
+// sees the normals through bf16 terms, far coarser than FP32.
+__device__ __forceinline__ void box_muller_f(uint32_t w1, uint32_t w2, float* z0, float* z1) {
+  const float u1 = (float)(w1 >> 8) * 5.9604645e-8f, u2 = (float)(w2 >> 8) * 5.9604645e-8f;
+  const float rho = sqrtf(-2.f * __logf(1.f - u1));
   float s, c;
-  __sincosf((float)(2.0 * DSMC_PI * u2), &s, &c);
+  __sincosf(6.2831853f * u2, &s, &c);
   *z0 = rho * c;
   *z1 = rho * s;
 }
@@ -358,7 +363,7 @@ __global__ void __launch_bounds__(kThreads) k_collide_neural(MlpShape sh, const 
       const int32_t p = beg + tile * kTileM + t;
       const bool valid = t < kTileM && p < end;
       int4 q = make_int4(0, 0, 0, 0);
-      double xi = 0, yi = 0, zi = 0, xj = 0, yj = 0, zj = 0;
+      double xi = 0, yi = 0, zi = 0, xj = 0, yj = 0, zj = 0, ux = 0, uy = 0, uz = 0;
       float f[16];
 #pragma unroll
       for (int c = 0; c < 16; ++c) f[c] = 0.f;
@@ -366,17 +371,19 @@ __global__ void __launch_bounds__(kThreads) k_collide_neural(MlpShape sh, const 
         q = a.pairs[p];
         xi = __ldcg(a.vx + q.x); yi = __ldcg(a.vy + q.x); zi = __ldcg(a.vz + q.x);
         xj = __ldcg(a.vx + q.y); yj = __ldcg(a.vy + q.y); zj = __ldcg(a.vz + q.y);
-        f[0] = (float)((xi - xj) * a.sigma_v_inv);
-        f[1] = (float)((yi - yj) * a.sigma_v_inv);
-        f[2] = (float)((zi - zj) * a.sigma_v_inv);
+        ux = xi - xj; uy = yi - yj; uz = zi - zj;
+        // MLP inputs need FP32 only: convert, then scale in FP32
+        f[0] = (float)ux * a.sigma_v_inv_f;
+        f[1] = (float)uy * a.sigma_v_inv_f;
+        f[2] = (float)uz * a.sigma_v_inv_f;
         const u32x4 wa = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_NOISE, 0);
         const u32x4 wb = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_NOISE, 1);
         float z[4];
-        box_muller(u53(wa.x, wa.y), u53(wa.z, wa.w), &z[0], &z[1]);
-        box_muller(u53(wb.x, wb.y), u53(wb.z, wb.w), &z[2], &z[3]);
+        box_muller_f(wa.x, wa.z, &z[0], &z[1]);
+        box_muller_f(wb.x, wb.z, &z[2], &z[3]);
         if (sh.d_in == 8) {
           const double* m = a.mom + 5 * (size_t)q.z;
-          f[3] = (float)(a.m_over_3k * m[4] / m[0] * a.T_ref_inv);
+          f[3] = (float)m[4] / (float)m[0] * a.T_feat_f;
           f[4] = z[0]; f[5] = z[1]; f[6] = z[2]; f[7] = z[3];
         } else {
           f[3] = z[0]; f[4] = z[1]; f[5] = z[2];
@@ -390,25 +397,35 @@ __global__ void __launch_bounds__(kThreads) k_collide_neural(MlpShape sh, const 
       float y[3];
       if (!mlp_tile(smem, L, sh, tmem, phase, y, a.status)) { alive = false; break; }
       if (valid) {
-        const double ux = xi - xj, uy = yi - yj, uz = zi - zj;
-        const double g = sqrt(ux * ux + uy * uy + uz * uz);
-        const double y0 = y[0], y1 = y[1], y2 = y[2];
-        const double ny = sqrt(y0 * y0 + y1 * y1 + y2 * y2);
-        double e0, e1, e2;
-        if (ny > a.eps) {
-          e0 = y0 / ny; e1 = y1 / ny; e2 = y2 / ny;
+        // shell projection v_r' = |v_r| y/|y| and centre-of-mass update in FP64.
+        // s = |v_r|/|y| from an FP32 estimate and one FP64 Newton step on
+        // s^2 |y|^2 = |v_r|^2 (relative error ~1e-14), so |v_r'| = |v_r|.
+        const double g2 = ux * ux + uy * uy + uz * uz;
+        double y0 = y[0], y1 = y[1], y2 = y[2];
+        const double ny2 = y0 * y0 + y1 * y1 + y2 * y2;
+        if (ny2 > a.eps * a.eps) {
+          const float g2f = (float)g2, ny2f = (float)ny2;
+          const float sf = sqrtf(g2f / ny2f);
+          const double s0 = sf;
+          const double res = g2 - s0 * s0 * ny2;           // g2 - s0^2 ny2
+          const double sc = s0 + res * (double)(0.5f * sf / g2f);
+          y0 *= sc; y1 *= sc; y2 *= sc;                    // v_r'
         } else {  // isotropic fallback direction (tag 3)
           const u32x4 wi = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_ISO);
-          const double c = 2.0 * u53(wi.x, wi.y) - 1.0, s = sqrt(1.0 - c * c);
+          const double c = 2.0 * u53(wi.x, wi.y) - 1.0, sn = sqrt(1.0 - c * c);
           double se, ce;
           sincos(2.0 * DSMC_PI * u53(wi.z, wi.w), &se, &ce);
-          e0 = c; e1 = s * ce; e2 = s * se;
+          const double g = sqrt(g2);
+          y0 = g * c; y1 = g * sn * ce; y2 = g * sn * se;
         }
-        if (a.u_out) { a.u_out[3 * (size_t)p] = (float)e0; a.u_out[3 * (size_t)p + 1] = (float)e1; a.u_out[3 * (size_t)p + 2] = (float)e2; }
-        const double rx = g * e0, ry = g * e1, rz = g * e2;
+        if (a.u_out) {
+          const double ig = g2 > 0.0 ? 1.0 / sqrt(g2) : 0.0;
+          a.u_out[3 * (size_t)p] = (float)(y0 * ig); a.u_out[3 * (size_t)p + 1] = (float)(y1 * ig);
+          a.u_out[3 * (size_t)p + 2] = (float)(y2 * ig);
+        }
         const double cx = 0.5 * (xi + xj), cy = 0.5 * (yi + yj), cz = 0.5 * (zi + zj);
-        __stcg(a.vx + q.x, cx + 0.5 * rx); __stcg(a.vy + q.x, cy + 0.5 * ry); __stcg(a.vz + q.x, cz + 0.5 * rz);
-        __stcg(a.vx + q.y, cx - 0.5 * rx); __stcg(a.vy + q.y, cy - 0.5 * ry); __stcg(a.vz + q.y, cz - 0.5 * rz);
+        __stcg(a.vx + q.x, fma(0.5, y0, cx)); __stcg(a.vy + q.x, fma(0.5, y1, cy)); __stcg(a.vz + q.x, fma(0.5, y2, cz));
+        __stcg(a.vx + q.y, fma(-0.5, y0, cx)); __stcg(a.vy + q.y, fma(-0.5, y1, cy)); __stcg(a.vz + q.y, fma(-0.5, y2, cz));
       }
     }
     if (alive && r + 1 < R && !grid_barrier(a.bar, a.status, kBarrierLimitNs)) alive = false;
@@ -455,6 +472,8 @@ int launch_collide_neural(Ctx* c, const dsmc_gas_t& gas, const dsmc_mlp_t& mlp,
   a.seed = gas.seed; a.step = step; a.step_dev = graph_step_ptr(c);
   a.sigma_v_inv = 1.0 / mlp.sigma_v; a.T_ref_inv = 1.0 / mlp.T_ref;
   a.m_over_3k = gas.mass / (3.0 * DSMC_KB); a.eps = mlp.eps;
+  a.sigma_v_inv_f = (float)a.sigma_v_inv;
+  a.T_feat_f = (float)(a.m_over_3k * a.T_ref_inv);
   a.mom = mom; a.u_out = u_out; a.pairs = (const int4*)pairs; a.ro = ro; a.info = info;
   a.vx = vx; a.vy = vy; a.vz = vz; a.bar = barrier_ptr(c); a.status = status_ptr(c);
   if (cudaMemsetAsync(a.bar, 0, 4 * sizeof(unsigned), s) != cudaSuccess) return DSMC_ERR_CUDA;

@@ -198,9 +198,14 @@ __global__ void __launch_bounds__(kSelWarps * 32) k_sel_count(SelArgs a) {
   }
 }
 
-__global__ void __launch_bounds__(kSelWarps * 32) k_sel_emit(SelArgs a) {
+constexpr int kEmitWarps = 4;
+constexpr int kEmitPairs = 1024;  // accepted pairs of a cell kept in shared memory
+
+__global__ void __launch_bounds__(kEmitWarps * 32) k_sel_emit(SelArgs a) {
   if (a.step_dev) a.step = *a.step_dev;
-  __shared__ float stage[kSelWarps][3 * kStage];
+  __shared__ float stage[kEmitWarps][3 * kStage];
+  __shared__ uint32_t spairs[kEmitWarps][kEmitPairs];   // local i | local j << 16, candidate order
+  __shared__ uint16_t slast[kEmitWarps][kStage];         // last round of each particle (+1; 0 = none)
   __shared__ int hist[DSMC_MAX_ROUNDS];
   __shared__ int rmax_blk;
   for (int t = threadIdx.x; t < DSMC_MAX_ROUNDS; t += blockDim.x) hist[t] = 0;
@@ -210,8 +215,8 @@ __global__ void __launch_bounds__(kSelWarps * 32) k_sel_emit(SelArgs a) {
   const bool over = total > a.capacity;
   if (over && blockIdx.x == 0 && threadIdx.x == 0) set_status(a.status, DSMC_ERR_CAPACITY);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int32_t warps = gridDim.x * kSelWarps;
-  for (int32_t k = blockIdx.x * kSelWarps + wid; k < a.n_cells && !over; k += warps) {
+  const int32_t warps = gridDim.x * kEmitWarps;
+  for (int32_t k = blockIdx.x * kEmitWarps + wid; k < a.n_cells && !over; k += warps) {
     const int32_t base = a.cs[k], N = a.cs[k + 1] - base;
     if (N < 2) continue;
     const double sgk = a.sgmax[k];
@@ -219,6 +224,7 @@ __global__ void __launch_bounds__(kSelWarps * 32) k_sel_emit(SelArgs a) {
     const int32_t M = ntc_count(a, k, N, &bad);
     const CellView cv = stage_cell(a, stage[wid], base, N, sgk, lane);
     const int32_t p0 = a.offs[k], p1 = a.offs[k + 1];
+    const bool local = N <= kStage && p1 - p0 <= kEmitPairs;
     int32_t pos = p0;
     for (int32_t c0 = 0; c0 < M; c0 += 32) {
       const int32_t m = c0 + lane;
@@ -229,23 +235,45 @@ __global__ void __launch_bounds__(kSelWarps * 32) k_sel_emit(SelArgs a) {
       if (ok) {
         const int32_t q = pos + __popc(mask & ((1u << lane) - 1u));
         a.tmp[q] = make_int4(base + i, base + j, k, m);
+        if (local) spairs[wid][q - p0] = (uint32_t)i | ((uint32_t)j << 16);
       }
       pos += __popc(mask);
     }
-    for (int32_t t = lane; t < N; t += 32) a.last[base + t] = -1;
+    if (local) {
+      for (int32_t t = lane; t < N; t += 32) slast[wid][t] = 0;
+    } else {
+      for (int32_t t = lane; t < N; t += 32) a.last[base + t] = -1;
+    }
     __syncwarp();
+    // rounds in candidate order: round = 1 + max(last round of i, of j)
     if (lane == 0) {
       int rm = -1;
-      for (int32_t p = p0; p < p1; ++p) {
-        const int4 q = a.tmp[p];
-        const int li = a.last[q.x], lj = a.last[q.y];
-        int r = 1 + (li > lj ? li : lj);
-        if (r >= DSMC_MAX_ROUNDS) { set_status(a.status, DSMC_ERR_UNSUPPORTED); r = DSMC_MAX_ROUNDS - 1; }
-        a.last[q.x] = r;
-        a.last[q.y] = r;
-        a.tmp_round[p] = r;
-        atomicAdd(&hist[r], 1);
-        rm = r > rm ? r : rm;
+      if (local) {
+        uint16_t* last = slast[wid];
+        for (int32_t p = p0; p < p1; ++p) {
+          const uint32_t ij = spairs[wid][p - p0];
+          const uint32_t i = ij & 0xFFFFu, j = ij >> 16;
+          const int li = last[i], lj = last[j];            // stored as round + 1
+          int r = li > lj ? li : lj;                        // = 1 + max(round) in 0-based rounds
+          if (r >= DSMC_MAX_ROUNDS) { set_status(a.status, DSMC_ERR_UNSUPPORTED); r = DSMC_MAX_ROUNDS - 1; }
+          last[i] = (uint16_t)(r + 1);
+          last[j] = (uint16_t)(r + 1);
+          a.tmp_round[p] = r;
+          atomicAdd(&hist[r], 1);
+          rm = r > rm ? r : rm;
+        }
+      } else {
+        for (int32_t p = p0; p < p1; ++p) {
+          const int4 q = a.tmp[p];
+          const int li = a.last[q.x], lj = a.last[q.y];
+          int r = 1 + (li > lj ? li : lj);
+          if (r >= DSMC_MAX_ROUNDS) { set_status(a.status, DSMC_ERR_UNSUPPORTED); r = DSMC_MAX_ROUNDS - 1; }
+          a.last[q.x] = r;
+          a.last[q.y] = r;
+          a.tmp_round[p] = r;
+          atomicAdd(&hist[r], 1);
+          rm = r > rm ? r : rm;
+        }
       }
       atomicMax(&rmax_blk, rm + 1);
       a.sgmax[k] = a.sgnew[k];
@@ -384,7 +412,7 @@ int launch_select(Ctx* c, const dsmc_gas_t& gas, int32_t n, int32_t n_cells, con
     count_launches(c, 1);
     int rc = launch_scan(c, w.counts, w.offs, n_cells, w.scan, s);
     if (rc) return rc;
-    k_sel_emit<<<gb, kSelWarps * 32, 0, s>>>(a);
+    k_sel_emit<<<blocks_for(n_cells, kEmitWarps, sms * 16), kEmitWarps * 32, 0, s>>>(a);
     k_sel_sg_commit<<<blocks_for(n_cells, 256, sms * 4), 256, 0, s>>>(a);
     count_launches(c, 2);
     rc = launch_scan(c, w.round_count, round_offsets, DSMC_MAX_ROUNDS, w.scan, s);
