@@ -35,6 +35,8 @@ struct PotDev {
   double A, a1, a2, am1, am2, beta, C[6], rc, At, at;
   float fA, fa1, fa2, fam1, fam2, fbeta, fC[6], frc, fAt, fat;
   double Dd[17];      // FP64 copy of D
+  double Dp[16];      // (p + 1) D_{p+1}: P'(r) = -r^-2 sum_p Dp_p r^-p
+  double Cd[6];       // (6 + 2n) C_n
   float D[17];        // P(r) = sum_p D_p r^-p,  e^{-beta r} P(r) = sum_n C_2n r^-2n e^{-x} S_2n(x)
   float sigma0;       // zero crossing of V (F > 0 above max(b, sigma0))
   float orbit_E;      // below this energy use the fine bracket scan
@@ -45,7 +47,11 @@ struct PotDev {
 };
 
 // ---------------------------------------------------------------- FP64 potential
-// Direct evaluation of V and V' (FP64 has the digits to spare).
+// V and V' in FP64, with the damped dispersion expanded into
+//   -sum_n C_2n r^-2n + e^{-beta r} P(r),   P(r) = sum_p D_p r^-p,
+// (exact: f_2n(x) = 1 - e^-x sum_{k<=2n} x^k/k!), evaluated by Horner in 1/r:
+// one reciprocal and no other division.  The two parts cancel to at most
+// about two decimal digits for r above the core radius, which FP64 absorbs.
 __host__ __device__ inline double V64(const PotDev& P, double r, double* dV, double* rep_out = nullptr,
                                       double* ex_out = nullptr) {
   if (P.kind == 2) {
@@ -53,30 +59,34 @@ __host__ __device__ inline double V64(const PotDev& P, double r, double* dV, dou
     *dV = -P.p * v / r;
     return v;
   }
+  const double ir = 1.0 / r;
   if (r < P.rc) {
-    const double e = P.At * exp(-P.at * r) / r;
-    *dV = -e * (P.at + 1.0 / r);
+    const double e = P.At * exp(-P.at * r) * ir;
+    *dV = -e * (P.at + ir);
     return e;
   }
-  const double ir = 1.0 / r;
-  const double rep = P.A * exp(P.a1 * r + P.a2 * r * r + P.am1 * ir + P.am2 * ir * ir);
-  const double drep = rep * (P.a1 + 2.0 * P.a2 * r - P.am1 * ir * ir - 2.0 * P.am2 * ir * ir * ir);
-  const double x = P.beta * r, ex = exp(-x);
-  double term = 1.0, S = 1.0, disp = 0.0, ddisp = 0.0;
-  double ir2n = ir * ir * ir * ir * ir * ir;  // r^-6
-  int k = 0;
-  for (int n = 3; n <= 8; ++n) {
-    for (; k < 2 * n;) { ++k; term *= x / k; S += term; }
-    const double f = 1.0 - ex * S;    // f_2n(x)
-    const double fp = ex * term;      // f_2n'(x) = e^-x x^2n/(2n)!
-    disp += P.C[n - 3] * f * ir2n;
-    ddisp += P.C[n - 3] * (P.beta * fp * ir2n - 2.0 * n * f * ir2n * ir);
-    ir2n *= ir * ir;
+  const double ir2 = ir * ir;
+  const double rep = P.A * exp(P.a1 * r + P.a2 * r * r + P.am1 * ir + P.am2 * ir2);
+  const double drep = rep * (P.a1 + 2.0 * P.a2 * r - P.am1 * ir2 - 2.0 * P.am2 * ir2 * ir);
+  double q = 0.0, dq = 0.0, pw = ir2 * ir2 * ir2;  // sum C r^-2n and its derivative
+#pragma unroll
+  for (int n = 0; n < 6; ++n) {
+    q = fma(P.C[n], pw, q);
+    dq = fma(P.Cd[n], pw, dq);
+    pw *= ir2;
   }
+  dq *= -ir;
+  double Pr = P.Dd[16], dPr = P.Dp[15];
+#pragma unroll
+  for (int k = 15; k >= 0; --k) Pr = fma(Pr, ir, P.Dd[k]);
+#pragma unroll
+  for (int k = 14; k >= 0; --k) dPr = fma(dPr, ir, P.Dp[k]);
+  dPr *= -ir2;                                     // P'(r) = -sum p D_p r^-(p+1)
+  const double ex = exp(-P.beta * r);
   if (rep_out) *rep_out = rep;
   if (ex_out) *ex_out = ex;
-  *dV = drep - ddisp;
-  return rep - disp;
+  *dV = drep - dq + ex * (dPr - P.beta * Pr);
+  return rep - q + ex * Pr;
 }
 
 // ---------------------------------------------------------------- FP32 potential
@@ -301,6 +311,8 @@ static PotDev make_pot(const dsmc_gas_t& gas, const dsmc_potential_t& p, int n_n
     P.D[pp] = (float)s;
     P.Dd[pp] = s;
   }
+  for (int pp = 0; pp < 16; ++pp) P.Dp[pp] = (pp + 1) * P.Dd[pp + 1];
+  for (int q = 0; q < 6; ++q) P.Cd[q] = (6 + 2 * q) * p.C[q];
   if (p.kind == 0) {
     // sigma0: outermost zero of V (bisection on a sign change found inward from 4 R_eps)
     double dv, hi = 4.0 * p.R_eps, lo = hi;
@@ -345,16 +357,16 @@ __device__ __forceinline__ void unit_angle(float ang, double* c, double* s) {
   }
 }
 
-// Deflect v_r by chi with azimuth eps (Bird 1994, Eq. 2.22), FP64.
-__device__ __forceinline__ void deflect(double u, double v, double w, double cc, double sc,
-                                        double ce, double se, double* o) {
-  const double g = sqrt(u * u + v * v + w * w);
-  const double q = sqrt(v * v + w * w);
+// Deflect v_r = (u, v, w), |v_r| = g, 1/g = ig, by chi with azimuth eps
+// (Bird 1994, Eq. 2.22), FP64; reciprocal square roots instead of divisions.
+__device__ __forceinline__ void deflect(double u, double v, double w, double g, double ig, double cc,
+                                        double sc, double ce, double se, double* o) {
+  const double q2 = v * v + w * w;
   double cx, cy, cz, ax, ay, az;
-  if (q > 1e-300 && q > 1e-12 * g) {
-    const double iq = 1.0 / q, igq = iq / g;
+  if (q2 > 0.0 && q2 > 1e-24 * (g * g)) {   // q > 1e-12 g
+    const double iq = rsqrt(q2), q = q2 * iq, igq = iq * ig;
     cx = 0.0; cy = w * iq; cz = -v * iq;
-    ax = q / g; ay = -u * v * igq; az = -u * w * igq;
+    ax = q * ig; ay = -u * v * igq; az = -u * w * igq;
   } else {
     cx = 0.0; cy = 1.0; cz = 0.0;
     ax = 0.0; ay = 0.0; az = u >= 0.0 ? -1.0 : 1.0;
@@ -388,17 +400,20 @@ __global__ void __launch_bounds__(128) k_collide_jager(PotDev P, JagerArgs a) {
       const double xi = __ldcg(a.vx + q.x), yi = __ldcg(a.vy + q.x), zi = __ldcg(a.vz + q.x);
       const double xj = __ldcg(a.vx + q.y), yj = __ldcg(a.vy + q.y), zj = __ldcg(a.vz + q.y);
       const double ux = xi - xj, uy = yi - yj, uz = zi - zj;
-      const double g = sqrt(ux * ux + uy * uy + uz * uz);
+      const double g2 = ux * ux + uy * uy + uz * uz;
       const u32x4 w = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_JAGER);
       const float b = (float)(a.bmax_A * sqrt(u53(w.x, w.y)));
-      const float E = P.mass_over_4k * (float)(g * g);
-      const float chi = g > 0.0 ? chi_device(P, b, E) : 0.f;
+      const float E = P.mass_over_4k * (float)g2;
+      const float chi = g2 > 0.0 ? chi_device(P, b, E) : 0.f;
       if (a.chi_out) a.chi_out[p] = chi;
       double cc, sc, ce, se;
       unit_angle(chi, &cc, &sc);
       unit_angle((float)(2.0 * DSMC_PI * u53(w.z, w.w)), &ce, &se);
       double o[3] = {0.0, 0.0, 0.0};
-      if (g > 0.0) deflect(ux, uy, uz, cc, sc, ce, se, o);
+      if (g2 > 0.0) {
+        const double ig = rsqrt(g2);
+        deflect(ux, uy, uz, g2 * ig, ig, cc, sc, ce, se, o);
+      }
       const double cx = 0.5 * (xi + xj), cy = 0.5 * (yi + yj), cz = 0.5 * (zi + zj);
       __stcg(a.vx + q.x, cx + 0.5 * o[0]); __stcg(a.vy + q.x, cy + 0.5 * o[1]); __stcg(a.vz + q.x, cz + 0.5 * o[2]);
       __stcg(a.vx + q.y, cx - 0.5 * o[0]); __stcg(a.vy + q.y, cy - 0.5 * o[1]); __stcg(a.vz + q.y, cz - 0.5 * o[2]);
@@ -413,14 +428,17 @@ __global__ void __launch_bounds__(128) k_harvest(PotDev P, int64_t n, const doub
                                                  double* __restrict__ vjo) {
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
     const double ux = vi[3 * p] - vj[3 * p], uy = vi[3 * p + 1] - vj[3 * p + 1], uz = vi[3 * p + 2] - vj[3 * p + 2];
-    const double g = sqrt(ux * ux + uy * uy + uz * uz);
-    const float E = P.mass_over_4k * (float)(g * g);
-    const float chi = g > 0.0 ? chi_device(P, (float)b[p], E) : 0.f;
+    const double g2 = ux * ux + uy * uy + uz * uz;
+    const float E = P.mass_over_4k * (float)g2;
+    const float chi = g2 > 0.0 ? chi_device(P, (float)b[p], E) : 0.f;
     double cc, sc, ce, se;
     unit_angle(chi, &cc, &sc);
     unit_angle((float)eps[p], &ce, &se);
     double o[3] = {0.0, 0.0, 0.0};
-    if (g > 0.0) deflect(ux, uy, uz, cc, sc, ce, se, o);
+    if (g2 > 0.0) {
+      const double ig = rsqrt(g2);
+      deflect(ux, uy, uz, g2 * ig, ig, cc, sc, ce, se, o);
+    }
     for (int c = 0; c < 3; ++c) {
       const double cm = 0.5 * (vi[3 * p + c] + vj[3 * p + c]);
       vio[3 * p + c] = cm + 0.5 * o[c];

@@ -1,16 +1,22 @@
 // Neural collision operator (Sec. 2.2-2.3) on the tcgen05 tensor cores.
 //
-// A CTA of 128 threads owns a tile of 128 pairs: thread t builds row t of the
-// bf16 input tile X in shared memory, one elected thread issues the layer's
-// tcgen05.mma chain (K-major operands, FP32 accumulator in TMEM), all four
-// warps read their 32 TMEM lanes back (tcgen05.ld), add the bias, apply the
+// A CTA of 512 threads runs two warp groups of 8 warps, each owning a tile
+// of 128 pairs in its own shared-memory slot and its own 128 TMEM columns,
+// so that one group's feature build, activation epilogue and pair update run
+// while the tensor core works on the other group's layer (ping-pong; a
+// single 16-warp group when two slots do not fit in shared memory).  Within
+// a group: thread t < 128 builds row t of the bf16 input tile X, one elected
+// thread issues the layer's tcgen05.mma chain (K-major operands, FP32
+// accumulator in TMEM) and waits on the group's mbarrier, the group's warps
+// read their 32 TMEM lanes back (tcgen05.ld), add the bias, apply the
 // activation and write the next layer's A operand to shared memory as two
 // bf16 terms (hi = bf16(a), lo = bf16(a - hi)) multiplied by the same bf16
 // weights: bf16 operands, FP32 accumulation, about 16 significant bits kept
 // for the activations (single bf16 storage costs up to 6e-2 in the output
-// direction of badly conditioned pairs).  The weights of all layers stay in shared memory for the life of
-// the CTA.  After the last layer thread t projects y onto the energy shell
-// and applies the centre-of-mass update of its pair in FP64.
+// direction of badly conditioned pairs).  The weights of all layers stay in
+// shared memory for the life of the CTA.  After the last layer thread t
+// projects y onto the energy shell and applies the centre-of-mass update of
+// its pair in FP64.
 //
 // The collide kernel is persistent and cooperative: it walks the rounds of
 // the step (pairs of one round are disjoint) with a bounded grid barrier in
@@ -30,30 +36,43 @@ constexpr int kKin = 32;         // input as two bf16 terms: [hi (16) | lo (16)]
 constexpr int kNout = 16;        // padded output width
 constexpr int kMaxHidden = 4;
 
-// dynamic shared memory layout (bytes)
+// dynamic shared memory layout (bytes).  The weights are shared; each of the
+// `slots` tile slots (one per warp group) has its own X, activation tiles,
+// mbarrier and flag.
 struct MlpLayout {
-  uint32_t w_out, w_in, w_sq, x, h, hlo, bias, mbar, tptr, flag, total;
+  uint32_t w_out, w_in, w_sq, slot0, slot_bytes, bias, mbar, tptr, flag, total;
+  int slots;
+  __host__ __device__ uint32_t x(int g) const { return slot0 + (uint32_t)g * slot_bytes; }
+  __host__ __device__ uint32_t h(int g) const { return x(g) + kTileM * kKin * 2; }
+  __host__ __device__ uint32_t hlo(int g) const { return h(g) + kTileM * kWidth * 2; }
 };
 
-__host__ __device__ inline MlpLayout mlp_layout(int n_hidden) {
+constexpr uint32_t kMaxSmem = 232448 - 1024;  // 227 KB opt-in per CTA, less the static shared memory
+
+__host__ __device__ inline MlpLayout mlp_layout(int n_hidden, int slots) {
   MlpLayout L;
+  L.slots = slots;
   L.w_out = 0;                                        // [16 x 128]
   L.w_in = L.w_out + kNout * kWidth * 2;              // [128 x 32] = [W1 | W1]
   L.w_sq = L.w_in + kWidth * kKin * 2;                // (n_hidden-1) x [128 x 128]
-  L.x = L.w_sq + (uint32_t)(n_hidden - 1) * kWidth * kWidth * 2;  // [128 x 16]
-  L.h = L.x + kTileM * kKin * 2;                      // [128 x 128] activations, hi term
-  L.hlo = L.h + kTileM * kWidth * 2;                  // [128 x 128] activations, lo term
-  L.bias = L.hlo + kTileM * kWidth * 2;               // floats: n_hidden*128 + 16
+  L.slot0 = L.w_sq + (uint32_t)(n_hidden - 1) * kWidth * kWidth * 2;
+  L.slot_bytes = kTileM * kKin * 2 + 2 * kTileM * kWidth * 2;  // X [128 x 32], hi and lo [128 x 128]
+  L.bias = L.slot0 + (uint32_t)slots * L.slot_bytes;  // floats: n_hidden*128 + 16
   L.mbar = L.bias + (uint32_t)(n_hidden * kWidth + kNout) * 4;
-  L.mbar = (L.mbar + 15u) & ~15u;
-  L.tptr = L.mbar + 8;
-  L.flag = L.tptr + 4;
-  L.total = L.flag + 4 + 2048;  // slack after the last operand tile
+  L.mbar = (L.mbar + 15u) & ~15u;                     // slots x 8 bytes
+  L.tptr = L.mbar + 16;
+  L.flag = L.tptr + 4;                                // slots x 4 bytes
+  L.total = L.flag + 8 + 2048;  // slack after the last operand tile
   return L;
 }
 
+// two tile slots (ping-pong warp groups) when they fit in shared memory
+__host__ __device__ inline int mlp_slots(int n_hidden) {
+  return mlp_layout(n_hidden, 2).total <= kMaxSmem ? 2 : 1;
+}
+
 struct MlpShape {
-  int d_in, n_hidden, act;
+  int d_in, n_hidden, act, slots;
 };
 
 // Copy the caller's row-major [out x in] bf16 layers into K-major core-matrix
@@ -94,30 +113,47 @@ __device__ __forceinline__ float act_f(int act, float z) {
   return __fdividef(z, 1.f + __expf(-z));   // SiLU(z) = z / (1 + e^-z)
 }
 
-// Run all layers on the X tile already in shared memory (fenced and
+// The warp group a thread belongs to: G groups of blockDim/G threads, group g
+// owning tile slot g, TMEM columns [128 g, 128 g + 128) and named barrier 1 + g.
+struct Group {
+  int g, G, t, nthr;  // group index, group count, thread index in the group, threads per group
+};
+
+__device__ __forceinline__ Group my_group(int G) {
+  const int nthr = blockDim.x / G;
+  return Group{(int)threadIdx.x / nthr, G, (int)threadIdx.x % nthr, nthr};
+}
+
+__device__ __forceinline__ void group_sync(const Group& q) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + q.g), "r"(q.nthr) : "memory");
+}
+
+// Run all layers on the X tile already in the group's slot (fenced and
 // synchronised by the caller).  Returns false if a bounded wait ran out
-// (status recorded); y receives row threadIdx.x of the output (+ bias).
-// Rows: warp w reads TMEM lanes 32 (w % 4) .. +31, i.e. row = 32 (w % 4) + lane;
-// the column range of a hidden layer is split over the blockDim/128 warps that
-// share a lane group.  y is valid in threads 0..127 (row = threadIdx.x).
-__device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, uint32_t tmem,
-                         uint32_t& phase, float y[3], int* status) {
-  const int t = threadIdx.x, warp = t >> 5;
-  const int row = ((warp & 3) << 5) | (t & 31);
-  const int cgroups = blockDim.x / kTileM, cg = warp >> 2;
+// (status recorded); y receives the output row (+ bias) of group thread q.t
+// for q.t < 128.  Rows: warp w of the group reads TMEM lanes 32 (w % 4) ..
+// +31, i.e. row = 32 (w % 4) + lane; the columns of a hidden layer are split
+// over the group's warps that share a lane group.
+__device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, const Group& q,
+                         uint32_t tmem, uint32_t& phase, float y[3], int* status) {
+  const int gw = q.t >> 5;
+  const int row = ((gw & 3) << 5) | (q.t & 31);
+  const int cgroups = q.nthr / kTileM, cg = gw >> 2;
   const int cols = kWidth / cgroups;
-  uint64_t* mbar = (uint64_t*)(smem + L.mbar);
-  volatile int* flag = (volatile int*)(smem + L.flag);
+  uint64_t* mbar = (uint64_t*)(smem + L.mbar) + q.g;
+  volatile int* flag = (volatile int*)(smem + L.flag) + q.g;
   const uint32_t sbase = tc::smem_u32(smem);
-  const uint32_t lane_tm = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+  const uint32_t xs = L.x(q.g), hs = L.h(q.g), hls = L.hlo(q.g);
+  const uint32_t acc = tmem + (uint32_t)(q.g * kWidth);
+  const uint32_t lane_tm = acc + ((uint32_t)((gw & 3) * 32) << 16);
   const float* bs = (const float*)(smem + L.bias);
   for (int l = 0; l <= sh.n_hidden; ++l) {
-    if (t == 0) {
+    if (q.t == 0) {
       tc::fence_after();
       if (l == 0) {
 #pragma unroll
         for (int s = 0; s < kKin / 16; ++s)
-          tc::mma_bf16(tmem, tc::sdesc(sbase + L.x + 256u * s, 128, kKin * 16),
+          tc::mma_bf16(acc, tc::sdesc(sbase + xs + 256u * s, 128, kKin * 16),
                        tc::sdesc(sbase + L.w_in + 256u * s, 128, kKin * 16),
                        tc::idesc_bf16(kTileM, kWidth), s > 0);
       } else {
@@ -126,17 +162,17 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, uin
         // activations enter as hi + lo bf16 terms against the same weights
 #pragma unroll
         for (int s = 0; s < kWidth / 16; ++s)
-          tc::mma_bf16(tmem, tc::sdesc(sbase + L.h + 256u * s, 128, 2048),
+          tc::mma_bf16(acc, tc::sdesc(sbase + hs + 256u * s, 128, 2048),
                        tc::sdesc(sbase + wb + 256u * s, 128, 2048), idesc, s > 0);
 #pragma unroll
         for (int s = 0; s < kWidth / 16; ++s)
-          tc::mma_bf16(tmem, tc::sdesc(sbase + L.hlo + 256u * s, 128, 2048),
+          tc::mma_bf16(acc, tc::sdesc(sbase + hls + 256u * s, 128, 2048),
                        tc::sdesc(sbase + wb + 256u * s, 128, 2048), idesc, 1);
       }
       tc::commit(mbar);
       *flag = tc::mbar_wait(mbar, phase, status, kBarrierLimitNs) ? 1 : 0;
     }
-    __syncthreads();
+    group_sync(q);
     if (!*flag) return false;
     phase ^= 1u;
     tc::fence_after();
@@ -148,22 +184,22 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, uin
         tc::ld32(lane_tm + (uint32_t)c0, v);
         uint32_t pk[16], lo[16];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const float a0 = act_f(sh.act, v[2 * q] + bl[c0 + 2 * q]);
-          const float a1 = act_f(sh.act, v[2 * q + 1] + bl[c0 + 2 * q + 1]);
-          pk[q] = tc::pack_bf16x2(a0, a1);
-          lo[q] = tc::pack_bf16x2(a0 - __uint_as_float(pk[q] << 16), a1 - __uint_as_float(pk[q] & 0xFFFF0000u));
+        for (int k = 0; k < 16; ++k) {
+          const float a0 = act_f(sh.act, v[2 * k] + bl[c0 + 2 * k]);
+          const float a1 = act_f(sh.act, v[2 * k + 1] + bl[c0 + 2 * k + 1]);
+          pk[k] = tc::pack_bf16x2(a0, a1);
+          lo[k] = tc::pack_bf16x2(a0 - __uint_as_float(pk[k] << 16), a1 - __uint_as_float(pk[k] & 0xFFFF0000u));
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const uint32_t off = tc::kmajor_offset(row, c0 + 8 * j, kWidth);
-          tc::st_shared_v4(sbase + L.h + off, pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
-          tc::st_shared_v4(sbase + L.hlo + off, lo[4 * j], lo[4 * j + 1], lo[4 * j + 2], lo[4 * j + 3]);
+          tc::st_shared_v4(sbase + hs + off, pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+          tc::st_shared_v4(sbase + hls + off, lo[4 * j], lo[4 * j + 1], lo[4 * j + 2], lo[4 * j + 3]);
         }
       }
       tc::fence_before();
       tc::fence_async_smem();
-      __syncthreads();
+      group_sync(q);
     } else {
       if (cg == 0) {
         float v[16];
@@ -174,7 +210,7 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, uin
         y[2] = v[2] + bo[2];
       }
       tc::fence_before();
-      __syncthreads();
+      group_sync(q);
     }
   }
   return true;
@@ -183,8 +219,8 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, uin
 // Write row t of the X tile from 16 FP32 features (padding zeros included):
 // columns 0..15 hold hi = bf16(x), columns 16..31 lo = bf16(x - hi), so the
 // first layer sees x to about 16 significant bits through bf16 operands.
-__device__ __forceinline__ void write_x_row(char* smem, const MlpLayout& L, int t, const float* f) {
-  const uint32_t sb = tc::smem_u32(smem) + L.x;
+__device__ __forceinline__ void write_x_row(char* smem, const MlpLayout& L, int g, int t, const float* f) {
+  const uint32_t sb = tc::smem_u32(smem) + L.x(g);
   uint32_t hi[8], lo[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
@@ -198,14 +234,17 @@ __device__ __forceinline__ void write_x_row(char* smem, const MlpLayout& L, int 
   tc::st_shared_v4(sb + tc::kmajor_offset(t, 24, kKin), lo[4], lo[5], lo[6], lo[7]);
 }
 
-// CTA prologue/epilogue: TMEM allocation by warp 0, mbarrier set-up.
+// CTA prologue/epilogue: TMEM allocation by warp 0 (128 columns per tile
+// slot), one mbarrier per slot.
+__device__ __forceinline__ uint32_t tmem_cols(int slots) { return slots > 1 ? 256u : 128u; }
+
 __device__ __forceinline__ uint32_t cta_setup(char* smem, const MlpLayout& L) {
   if (threadIdx.x < 32) {
-    tc::tmem_alloc((uint32_t*)(smem + L.tptr), 128);
+    tc::tmem_alloc((uint32_t*)(smem + L.tptr), tmem_cols(L.slots));
     tc::tmem_relinquish();
   }
   if (threadIdx.x == 0) {
-    tc::mbar_init((uint64_t*)(smem + L.mbar), 1);
+    for (int g = 0; g < L.slots; ++g) tc::mbar_init((uint64_t*)(smem + L.mbar) + g, 1);
     tc::mbar_fence_init();
   }
   tc::fence_before();
@@ -214,11 +253,11 @@ __device__ __forceinline__ uint32_t cta_setup(char* smem, const MlpLayout& L) {
   return *(volatile uint32_t*)(smem + L.tptr);
 }
 
-__device__ __forceinline__ void cta_teardown(uint32_t tmem) {
+__device__ __forceinline__ void cta_teardown(uint32_t tmem, const MlpLayout& L) {
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
-  if (threadIdx.x < 32) tc::tmem_dealloc(tmem, 128);
+  if (threadIdx.x < 32) tc::tmem_dealloc(tmem, tmem_cols(L.slots));
 }
 
 // ---------------------------------------------------------------- standalone forward
@@ -228,29 +267,31 @@ __global__ void __launch_bounds__(kThreads) k_mlp_forward(MlpShape sh, const uin
                                                         const float* __restrict__ x, float* __restrict__ y,
                                                         int* status) {
   extern __shared__ __align__(1024) char smem[];
-  const MlpLayout L = mlp_layout(sh.n_hidden);
+  const MlpLayout L = mlp_layout(sh.n_hidden, sh.slots);
   load_weights(smem, L, sh, w, bias);
   const uint32_t tmem = cta_setup(smem, L);
+  const Group q = my_group(L.slots);
   uint32_t phase = 0;
-  const int t = threadIdx.x;
   const int64_t tiles = (n + kTileM - 1) / kTileM;
-  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const int64_t row = tile * kTileM + t;
-    if (t < kTileM) {
+  bool alive = true;
+  for (int64_t tile = blockIdx.x + (int64_t)gridDim.x * q.g; tile < tiles; tile += (int64_t)gridDim.x * q.G) {
+    const int64_t row = tile * kTileM + q.t;
+    if (q.t < kTileM) {
       float f[16];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) f[q] = 0.f;
+      for (int k = 0; k < 16; ++k) f[k] = 0.f;
       if (row < n)
-        for (int q = 0; q < sh.d_in; ++q) f[q] = x[row * sh.d_in + q];
-      write_x_row(smem, L, t, f);
+        for (int k = 0; k < sh.d_in; ++k) f[k] = x[row * sh.d_in + k];
+      write_x_row(smem, L, q.g, q.t, f);
       tc::fence_async_smem();
     }
-    __syncthreads();
+    group_sync(q);
     float o[3];
-    if (!mlp_tile(smem, L, sh, tmem, phase, o, status)) break;
-    if (t < kTileM && row < n) { y[3 * row] = o[0]; y[3 * row + 1] = o[1]; y[3 * row + 2] = o[2]; }
+    if (!mlp_tile(smem, L, sh, q, tmem, phase, o, status)) { alive = false; break; }
+    if (q.t < kTileM && row < n) { y[3 * row] = o[0]; y[3 * row + 1] = o[1]; y[3 * row + 2] = o[2]; }
   }
-  cta_teardown(tmem);
+  (void)alive;
+  cta_teardown(tmem, L);
 }
 
 // ---------------------------------------------------------------- tensor-core self test
@@ -349,17 +390,20 @@ __global__ void __launch_bounds__(kThreads) k_collide_neural(MlpShape sh, const 
                                                            const float* __restrict__ bias, NeuralArgs a) {
   if (a.step_dev) a.step = *a.step_dev;
   extern __shared__ __align__(1024) char smem[];
-  const MlpLayout L = mlp_layout(sh.n_hidden);
+  const MlpLayout L = mlp_layout(sh.n_hidden, sh.slots);
   load_weights(smem, L, sh, w, bias);
   const uint32_t tmem = cta_setup(smem, L);
+  const Group gq = my_group(L.slots);
   uint32_t phase = 0;
-  const int t = threadIdx.x;
+  const int t = gq.t;
   const int R = a.info->n_rounds;
   bool alive = true;
   for (int r = 0; r < R && alive; ++r) {
     const int32_t beg = a.ro[r], end = a.ro[r + 1];
     const int32_t tiles = (end - beg + kTileM - 1) / kTileM;
-    for (int32_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    // tile k of the round goes to CTA k % grid, group (k / grid) % G: small
+    // rounds spread over the SMs before a second group of a CTA takes a tile
+    for (int32_t tile = blockIdx.x + gridDim.x * gq.g; tile < tiles && alive; tile += gridDim.x * gq.G) {
       const int32_t p = beg + tile * kTileM + t;
       const bool valid = t < kTileM && p < end;
       int4 q = make_int4(0, 0, 0, 0);
@@ -390,12 +434,12 @@ __global__ void __launch_bounds__(kThreads) k_collide_neural(MlpShape sh, const 
         }
       }
       if (t < kTileM) {
-        write_x_row(smem, L, t, f);
+        write_x_row(smem, L, gq.g, t, f);
         tc::fence_async_smem();
       }
-      __syncthreads();
+      group_sync(gq);
       float y[3];
-      if (!mlp_tile(smem, L, sh, tmem, phase, y, a.status)) { alive = false; break; }
+      if (!mlp_tile(smem, L, sh, gq, tmem, phase, y, a.status)) { alive = false; break; }
       if (valid) {
         // shell projection v_r' = |v_r| y/|y| and centre-of-mass update in FP64.
         // s = |v_r|/|y| from an FP32 estimate and one FP64 Newton step on
@@ -428,9 +472,11 @@ __global__ void __launch_bounds__(kThreads) k_collide_neural(MlpShape sh, const 
         __stcg(a.vx + q.y, fma(-0.5, y0, cx)); __stcg(a.vy + q.y, fma(-0.5, y1, cy)); __stcg(a.vz + q.y, fma(-0.5, y2, cz));
       }
     }
+    // both groups agree on whether to go on before the grid barrier
+    alive = __syncthreads_and(alive) != 0;
     if (alive && r + 1 < R && !grid_barrier(a.bar, a.status, kBarrierLimitNs)) alive = false;
   }
-  cta_teardown(tmem);
+  cta_teardown(tmem, L);
 }
 
 // Failure-detection self test: wait on an mbarrier that no MMA commit will
@@ -462,8 +508,8 @@ int launch_collide_neural(Ctx* c, const dsmc_gas_t& gas, const dsmc_mlp_t& mlp,
                           const dsmc_select_info_t* info, double* vx, double* vy, double* vz,
                           float* u_out, cudaStream_t s) {
   if (mlp.n_hidden > kMaxHidden) return record(c, DSMC_ERR_UNSUPPORTED, "collide_neural: n_hidden > 4");
-  const MlpShape sh{mlp.d_in, mlp.n_hidden, mlp.act};
-  const MlpLayout L = mlp_layout(sh.n_hidden);
+  const MlpShape sh{mlp.d_in, mlp.n_hidden, mlp.act, mlp_slots(mlp.n_hidden)};
+  const MlpLayout L = mlp_layout(sh.n_hidden, sh.slots);
   if (!set_smem((const void*)k_collide_neural, (int)L.total))
     return record(c, DSMC_ERR_CUDA, "collide_neural: shared-memory attribute");
   const int blocks = cooperative_blocks(c, (const void*)k_collide_neural, kThreads, L.total);
@@ -489,8 +535,8 @@ int launch_mlp_forward(Ctx* c, const dsmc_mlp_t& mlp, const uint16_t* w, const f
                        int64_t n, const float* x, float* y, cudaStream_t s) {
   if (n == 0) return 0;
   if (mlp.n_hidden > kMaxHidden) return record(c, DSMC_ERR_UNSUPPORTED, "mlp_forward: n_hidden > 4");
-  const MlpShape sh{mlp.d_in, mlp.n_hidden, mlp.act};
-  const MlpLayout L = mlp_layout(sh.n_hidden);
+  const MlpShape sh{mlp.d_in, mlp.n_hidden, mlp.act, mlp_slots(mlp.n_hidden)};
+  const MlpLayout L = mlp_layout(sh.n_hidden, sh.slots);
   if (!set_smem((const void*)k_mlp_forward, (int)L.total))
     return record(c, DSMC_ERR_CUDA, "mlp_forward: shared-memory attribute");
   int per_sm = 0;
