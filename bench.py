@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-standalone", dest="standalone", action="store_false")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the built-in launch shapes")
     return ap.parse_args()
 
 
@@ -140,6 +142,18 @@ def run_gb300(args, rank, world, dist):
     neural_kernel = None
     for path in [p for p in args.paths.split(",") if p]:
         gas = D.make_gas(dict(wl["gas"], model=0 if path == "vhs" else 1))
+        path_d = D.make_path({"vhs": D.PATH_VHS, "jager": D.PATH_JAGER, "neural": D.PATH_NEURAL}[path],
+                             pot=pot, n_nodes=args.n_nodes, mlp=mlp, w_bits=w_bits, bias=bias)
+        tuned = None
+        if args.autotune:
+            # launch shapes of this path's tunable kernels, measured on this gas (untimed)
+            restore()
+            C.sigma_g_max_init(gas, T_cell, 5.0, out=st.sigma_g_max)
+            t0 = time.time()
+            trials = C.autotune_step(gas, path_d, st, step=0, reps=2)
+            tuned = dict(seconds=round(time.time() - t0, 3), trials=len(trials),
+                         shapes={D.TUNE_KERNELS[k]: list(C.tune_get(k))
+                                 for k in sorted({D.TUNE_KERNELS.index(t["kernel"]) for t in trials})})
         C.sigma_g_max_init(gas, T_cell, 5.0, out=st.sigma_g_max)
         ev = lambda: torch.cuda.Event(enable_timing=True)
         phase_ms = {k: 0.0 for k in ("sort", "moments", "select", "collide", "moment_match")}
@@ -186,8 +200,6 @@ def run_gb300(args, rank, world, dist):
         launches = C.launch_count() - launches0
         K = args.steps
         # the same step as one CUDA graph (the production path): timed alone
-        path_d = D.make_path({"vhs": D.PATH_VHS, "jager": D.PATH_JAGER, "neural": D.PATH_NEURAL}[path],
-                             pot=pot, n_nodes=args.n_nodes, mlp=mlp, w_bits=w_bits, bias=bias)
         gstream = torch.cuda.Stream(device=dev)
         torch.cuda.synchronize()
         C.sigma_g_max_init(gas, T_cell, 5.0, out=st.sigma_g_max)
@@ -217,7 +229,7 @@ def run_gb300(args, rank, world, dist):
             pairs_per_step=pairs / K, rounds_per_step=float(np.mean(rounds)),
             phase_ms={k: v / K for k, v in phase_ms.items()}, gpu_launches=g_launches,
             phased_gpu_launches=launches,
-            step_ms_total=step_ms, pairs_total=pairs)
+            step_ms_total=step_ms, pairs_total=pairs, autotune=tuned)
         if path == "neural":
             neural_kernel = dict(ms=phase_ms["collide"] / K, pairs=pairs / K)
     # ------------------------------------------------------------ standalone kernels
@@ -229,6 +241,10 @@ def run_gb300(args, rank, world, dist):
         bt, gt = torch.from_numpy(b_np).to(dev), torch.from_numpy(g_np).to(dev)
         chi = torch.empty_like(bt)
         gas1 = D.make_gas(dict(wl["gas"], model=1))
+        chi_tuned = None
+        if args.autotune:
+            C.autotune_chi(gas1, pot, bt, gt, n_nodes=args.n_nodes, chi=chi, reps=2)
+            chi_tuned = list(C.tune_get(D.TUNE_KERNELS.index("jager_chi")))
         for _ in range(2):
             C.jager_chi(gas1, pot, bt, gt, n_nodes=args.n_nodes, chi=chi)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -238,7 +254,8 @@ def run_gb300(args, rank, world, dist):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / 3
-        extra["chi_batch"] = dict(pairs=nb, ms=ms, chi_per_s=nb / (ms * 1e-3), n_nodes=args.n_nodes)
+        extra["chi_batch"] = dict(pairs=nb, ms=ms, chi_per_s=nb / (ms * 1e-3), n_nodes=args.n_nodes,
+                                  shape=chi_tuned)
         x = torch.randn((nb, 8), dtype=torch.float32, device=dev)
         y = torch.empty((nb, 3), dtype=torch.float32, device=dev)
         for _ in range(2):

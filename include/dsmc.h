@@ -142,7 +142,8 @@ int64_t dsmc_ctx_launch_count(dsmc_ctx_t* ctx);
  * contiguous.  Stable counting sort: perm[s] is the input index of sorted
  * slot s, slots of a cell keep the input order.  cell_start[n_cells+1]
  * holds each cell's first slot; s{x,y,z} receive the gathered velocities.
- * cell_id[i] outside [0, n_cells) records DSMC_ERR_ARG. */
+ * cell_id[i] outside [0, n_cells) records DSMC_ERR_ARG; such a particle gets
+ * no slot, and perm / s{x,y,z} past cell_start[n_cells] are left unwritten. */
 size_t dsmc_sort_workspace_size(int32_t n, int32_t n_cells);
 int dsmc_sort_cells(dsmc_ctx_t* ctx, int32_t n, int32_t n_cells, const int32_t* cell_id,
                     const double* vx, const double* vy, const double* vz, int32_t* perm,
@@ -346,6 +347,65 @@ int dsmc_step_graph_capture(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_p
 /* Run the captured step for step index `step` on `stream`: same results as
  * dsmc_step(..., step, ...). */
 int dsmc_step_graph_launch(dsmc_ctx_t* ctx, uint64_t step, void* stream);
+
+/* ---------------------------------------------------------------- launch shapes
+ * The block size and the number of resident blocks per SM of the kernels
+ * listed below are settings of the context, chosen by dsmc_autotune_step or
+ * set directly.  No setting changes a result: each of these kernels gives a
+ * thread whole work items (a sorted slot, a group of cells, a pair of a
+ * round, one chi) through a grid-stride loop, so every item is computed by
+ * the same arithmetic in the same order whatever the shape.  (The paper
+ * fixes no launch configuration; the tuned kernels are those of Sec. 2.1,
+ * 2.3 and 2.5 and of the scattering integral, Sec. 3.4.) */
+enum {
+  DSMC_TUNE_GATHER = 0,        /* cell sort: gather of the velocities into sorted order */
+  DSMC_TUNE_MOMENTS = 1,       /* cell moments */
+  DSMC_TUNE_MOMENT_MATCH = 2,  /* moment matching */
+  DSMC_TUNE_COLLIDE_VHS = 3,   /* VHS collide (persistent, cooperative) */
+  DSMC_TUNE_COLLIDE_JAGER = 4, /* Jager collide (persistent, cooperative) */
+  DSMC_TUNE_JAGER_CHI = 5,     /* chi batch */
+  DSMC_TUNE_KERNELS = 6
+};
+
+/* One launch shape and, from dsmc_autotune_step, its measured time. */
+typedef struct {
+  int32_t kernel;        /* DSMC_TUNE_* */
+  int32_t threads;       /* threads per block: a multiple of 32 up to the kernel's limit */
+  int32_t blocks_per_sm; /* blocks per SM of the grid (1..64): the grid is this many
+                            blocks per SM, or fewer when the work is smaller; for the
+                            cooperative collides at most what the occupancy allows
+                            (clamped there at launch) */
+  float ms;              /* mean time of one launch, ms (0 when not measured) */
+} dsmc_tune_entry_t;
+
+/* Set (threads, blocks_per_sm) of one kernel for later launches of this
+ * context; (0, 0) restores the built-in shape.  DSMC_ERR_ARG for an unknown
+ * kernel, a block size that is not a multiple of 32 or above the kernel's
+ * limit, or more than 64 blocks per SM.  A captured step graph keeps the
+ * shapes it was captured with. */
+int dsmc_tune_set(dsmc_ctx_t* ctx, int32_t kernel, int32_t threads, int32_t blocks_per_sm);
+/* Current shape of one kernel (the built-in one if none was set). */
+int dsmc_tune_get(dsmc_ctx_t* ctx, int32_t kernel, int32_t* threads, int32_t* blocks_per_sm);
+/* Candidate shapes the autotuner tries for `kernel` (at most `cap`; *n gets
+ * the count).  Host only. */
+int dsmc_tune_candidates(dsmc_ctx_t* ctx, int32_t kernel, dsmc_tune_entry_t* out, int32_t cap, int32_t* n);
+/* Autotune the kernels of one step of `path` on the caller's buffers: runs
+ * dsmc_step once (step index `step`), then times each candidate shape of
+ * the step's tunable kernels (one untimed launch, then `reps` launches
+ * between CUDA events on `stream`) and keeps the fastest shape of each in
+ * the context.  Synchronises `stream`.  The buffers are left holding the
+ * state after an unspecified number of collide and moment-matching passes
+ * over that step's pairs (each pass conserves momentum and energy), so tune
+ * on a copy or before loading the state to be advanced.  trials (may be
+ * NULL) receives up to `cap` measured entries; *n_trials their count. */
+int dsmc_autotune_step(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_path_t* path,
+                       const dsmc_step_buffers_t* buf, uint64_t step, int32_t reps,
+                       dsmc_tune_entry_t* trials, int32_t cap, int32_t* n_trials, void* stream);
+/* Autotune the chi batch kernel (dsmc_jager_chi) on the caller's arrays the
+ * same way; chi receives the batch's deflection angles.  Synchronises. */
+int dsmc_autotune_chi(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_potential_t* pot, int32_t n_nodes,
+                      int64_t n, const float* b, const float* g, float* chi, int32_t reps,
+                      dsmc_tune_entry_t* trials, int32_t cap, int32_t* n_trials, void* stream);
 
 /* Same step from and to HOST memory: copies cell_id_host / v*_host into
  * device buffers reserved by dsmc_ctx_reserve, runs dsmc_step, copies the

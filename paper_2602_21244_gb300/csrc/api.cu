@@ -29,6 +29,9 @@ struct Ctx {
   // step graph
   cudaGraphExec_t graph_exec = nullptr;
   bool capturing = false;
+  // launch shapes (dsmc_tune_set); 0 = built-in
+  int tune_threads[DSMC_TUNE_KERNELS] = {0};
+  int tune_bps[DSMC_TUNE_KERNELS] = {0};
 };
 
 int record(Ctx* c, int code, const char* msg) {
@@ -40,12 +43,69 @@ int* status_ptr(Ctx* c) { return c->d_status; }
 // so that a replay and a direct call on another stream do not share counters
 unsigned* barrier_ptr(Ctx* c) { return c->capturing ? c->d_bar + 32 : c->d_bar; }
 int sm_count(Ctx* c) { return c->sms; }
+Shape tune_shape(Ctx* c, int k) { return Shape{c->tune_threads[k], c->tune_bps[k]}; }
 void count_launches(Ctx* c, int k) { c->launches += k; }
 // the step index of a graph replay lives 64 bytes into the barrier block
 static uint64_t* step_slot(Ctx* c) { return (uint64_t*)((char*)c->d_bar + 64); }
 const uint64_t* graph_step_ptr(Ctx* c) { return c->capturing ? step_slot(c) : nullptr; }
 
 __global__ void k_set_step(uint64_t* slot, uint64_t step) { *slot = step; }
+
+// built-in launch shapes; blocks_per_sm 0 = as many as the occupancy allows
+ShapeInfo shape_info(int k) {
+  switch (k) {
+    case DSMC_TUNE_GATHER: return ShapeInfo{256, 16, 1024};
+    case DSMC_TUNE_MOMENTS: return ShapeInfo{256, 8, 256};
+    case DSMC_TUNE_MOMENT_MATCH: return ShapeInfo{256, 8, 256};
+    case DSMC_TUNE_COLLIDE_VHS: return ShapeInfo{256, 0, 256};
+    case DSMC_TUNE_COLLIDE_JAGER: return ShapeInfo{128, 0, 128};
+    case DSMC_TUNE_JAGER_CHI: return ShapeInfo{128, 64, 128};
+    default: return ShapeInfo{0, 0, 0};
+  }
+}
+
+// Candidate shapes of one kernel: block sizes up to the kernel's limit with
+// at most 2048 threads and 32 blocks per SM (the chi batch grid-strides over up to
+// 64 blocks per SM); for the cooperative collides
+// the full occupancy at each block size and half of it.
+static int tune_candidates(int k, dsmc_tune_entry_t* out, int cap) {
+  int n = 0;
+  auto push = [&](int t, int b) {
+    if (n < cap && out) out[n] = dsmc_tune_entry_t{k, t, b, 0.f};
+    ++n;
+  };
+  switch (k) {
+    case DSMC_TUNE_GATHER:
+      for (int t : {128, 256, 512})
+        for (int b : {2, 4, 8, 16})
+          if (t * b <= 2048) push(t, b);
+      break;
+    case DSMC_TUNE_MOMENTS:
+    case DSMC_TUNE_MOMENT_MATCH:
+      for (int t : {64, 128, 256})
+        for (int b : {4, 8, 16, 32})
+          if (t * b <= 2048) push(t, b);
+      break;
+    case DSMC_TUNE_COLLIDE_VHS:
+    case DSMC_TUNE_COLLIDE_JAGER: {
+      const bool vhs = k == DSMC_TUNE_COLLIDE_VHS;
+      for (int t : {32, 64, 128, 256}) {
+        if (t > shape_info(k).max_threads || (vhs && t < 64)) continue;
+        const int occ = vhs ? occupancy_collide_vhs(t) : occupancy_collide_jager(t);
+        if (occ < 1) continue;
+        push(t, occ > 32 ? 32 : occ);
+        if (occ / 2 >= 1) push(t, occ / 2 > 32 ? 32 : occ / 2);
+      }
+      break;
+    }
+    case DSMC_TUNE_JAGER_CHI:
+      for (int t : {64, 128})
+        for (int b : {8, 16, 32, 64}) push(t, b);
+      break;
+    default: break;
+  }
+  return n;
+}
 
 }  // namespace dsmc
 
@@ -496,6 +556,142 @@ int dsmc_step_host(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t* path
   if (!ok) return dsmc::record(c, DSMC_ERR_CUDA, "step_host: device-to-host copy failed");
   rc = dsmc_ctx_sync_status(c, stream);
   if (n_pairs_h) *n_pairs_h = ((dsmc_select_info_t*)c->r_host_info)->n_pairs;
+  return rc;
+}
+
+/* ---------------------------------------------------------------- launch shapes */
+
+int dsmc_tune_set(dsmc_ctx_t* c, int32_t kernel, int32_t threads, int32_t blocks_per_sm) {
+  CHECK_CTX(c);
+  REQUIRE(c, kernel >= 0 && kernel < DSMC_TUNE_KERNELS, "tune_set: unknown kernel");
+  if (threads == 0 && blocks_per_sm == 0) {
+    c->tune_threads[kernel] = 0;
+    c->tune_bps[kernel] = 0;
+    return DSMC_OK;
+  }
+  REQUIRE(c, threads >= 32 && threads % 32 == 0 && threads <= dsmc::shape_info(kernel).max_threads,
+          "tune_set: block size must be a multiple of 32 within the kernel's limit");
+  REQUIRE(c, blocks_per_sm >= 1 && blocks_per_sm <= 64, "tune_set: blocks per SM must be 1..64");
+  c->tune_threads[kernel] = threads;
+  c->tune_bps[kernel] = blocks_per_sm;
+  return DSMC_OK;
+}
+
+int dsmc_tune_get(dsmc_ctx_t* c, int32_t kernel, int32_t* threads, int32_t* blocks_per_sm) {
+  CHECK_CTX(c);
+  REQUIRE(c, kernel >= 0 && kernel < DSMC_TUNE_KERNELS && threads && blocks_per_sm, "tune_get: bad argument");
+  const dsmc::Shape s = dsmc::shape_or_default(c, kernel);
+  *threads = s.threads;
+  *blocks_per_sm = s.blocks_per_sm;
+  return DSMC_OK;
+}
+
+int dsmc_tune_candidates(dsmc_ctx_t* c, int32_t kernel, dsmc_tune_entry_t* out, int32_t cap, int32_t* n) {
+  CHECK_CTX(c);
+  REQUIRE(c, kernel >= 0 && kernel < DSMC_TUNE_KERNELS && n && cap >= 0 && (cap == 0 || out),
+          "tune_candidates: bad argument");
+  if (cudaSetDevice(c->device) != cudaSuccess) return DSMC_ERR_CUDA;
+  *n = dsmc::tune_candidates(kernel, out, cap);
+  return DSMC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Time every candidate shape of `kernel` with `launch` (one untimed launch,
+// then `reps` between events), keep the fastest; entries go to trials.
+template <class F>
+int tune_kernel(dsmc_ctx* c, int kernel, int reps, cudaStream_t s, F&& launch, dsmc_tune_entry_t* trials,
+                int cap, int* nt) {
+  dsmc_tune_entry_t cand[64];
+  const int nc = dsmc::tune_candidates(kernel, cand, 64);
+  if (nc < 1) return DSMC_OK;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return dsmc::record(c, DSMC_ERR_CUDA, "autotune: event");
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return dsmc::record(c, DSMC_ERR_CUDA, "autotune: event"); }
+  const int t0 = c->tune_threads[kernel], b0 = c->tune_bps[kernel];
+  int best = -1, rc = DSMC_OK;
+  for (int q = 0; q < nc && q < 64; ++q) {
+    c->tune_threads[kernel] = cand[q].threads;
+    c->tune_bps[kernel] = cand[q].blocks_per_sm;
+    rc = launch();
+    if (!rc && cudaEventRecord(e0, s) != cudaSuccess) rc = DSMC_ERR_CUDA;
+    for (int r = 0; r < reps && !rc; ++r) rc = launch();
+    if (!rc && cudaEventRecord(e1, s) != cudaSuccess) rc = DSMC_ERR_CUDA;
+    if (!rc) rc = dsmc_ctx_sync_status(c, s);
+    if (rc) break;
+    float el = 0.f;
+    cudaEventElapsedTime(&el, e0, e1);
+    cand[q].ms = el / (float)reps;
+    if (trials && *nt < cap) trials[*nt] = cand[q];
+    ++*nt;
+    if (best < 0 || cand[q].ms < cand[best].ms) best = q;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc || best < 0) {
+    c->tune_threads[kernel] = t0;
+    c->tune_bps[kernel] = b0;
+    return rc;
+  }
+  c->tune_threads[kernel] = cand[best].threads;
+  c->tune_bps[kernel] = cand[best].blocks_per_sm;
+  return DSMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dsmc_autotune_step(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t* path,
+                       const dsmc_step_buffers_t* B, uint64_t step, int32_t reps,
+                       dsmc_tune_entry_t* trials, int32_t cap, int32_t* n_trials, void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, gas && path && B && n_trials && reps >= 1 && cap >= 0, "autotune_step: bad argument");
+  REQUIRE(c, !c->capturing, "autotune_step: not during a graph capture");
+  *n_trials = 0;
+  cudaStream_t s = S(stream);
+  int rc = dsmc_step(c, gas, path, B, step, stream);
+  if (!rc) rc = dsmc_ctx_sync_status(c, stream);
+  if (rc) return rc;
+  if (B->n == 0 || B->n_cells == 0) return DSMC_OK;
+  int nt = 0;
+  rc = tune_kernel(c, DSMC_TUNE_GATHER, reps, s, [&] {
+    return dsmc::launch_gather(c, B->n, B->n_cells, B->cell_start, B->perm, B->vx, B->vy, B->vz, B->svx,
+                               B->svy, B->svz, s);
+  }, trials, cap, &nt);
+  if (!rc) rc = tune_kernel(c, DSMC_TUNE_MOMENTS, reps, s, [&] {
+    return dsmc::launch_moments(c, B->n_cells, B->cell_start, B->svx, B->svy, B->svz, B->mom, s);
+  }, trials, cap, &nt);
+  if (!rc && path->path == DSMC_PATH_VHS)
+    rc = tune_kernel(c, DSMC_TUNE_COLLIDE_VHS, reps, s, [&] {
+      return dsmc_collide_vhs(c, gas, step, B->pairs, B->round_offsets, B->info, B->svx, B->svy, B->svz, stream);
+    }, trials, cap, &nt);
+  if (!rc && path->path == DSMC_PATH_JAGER)
+    rc = tune_kernel(c, DSMC_TUNE_COLLIDE_JAGER, reps, s, [&] {
+      return dsmc_collide_jager(c, gas, path->pot, path->n_nodes, step, B->pairs, B->round_offsets, B->info,
+                                B->svx, B->svy, B->svz, nullptr, stream);
+    }, trials, cap, &nt);
+  if (!rc) rc = tune_kernel(c, DSMC_TUNE_MOMENT_MATCH, reps, s, [&] {
+    return dsmc::launch_moment_match(c, B->n_cells, B->cell_start, B->mom, B->svx, B->svy, B->svz, s);
+  }, trials, cap, &nt);
+  *n_trials = nt;
+  return rc;
+}
+
+int dsmc_autotune_chi(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_potential_t* pot, int32_t n_nodes,
+                      int64_t n, const float* b, const float* g, float* chi, int32_t reps,
+                      dsmc_tune_entry_t* trials, int32_t cap, int32_t* n_trials, void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, n_trials && reps >= 1 && cap >= 0, "autotune_chi: bad argument");
+  *n_trials = 0;
+  if (n == 0) return DSMC_OK;
+  int nt = 0;
+  const int rc = tune_kernel(c, DSMC_TUNE_JAGER_CHI, reps, S(stream), [&] {
+    return dsmc_jager_chi(c, gas, pot, n_nodes, n, b, g, chi, stream);
+  }, trials, cap, &nt);
+  *n_trials = nt;
   return rc;
 }
 

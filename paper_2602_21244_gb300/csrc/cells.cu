@@ -173,10 +173,15 @@ k_fix_gather(int32_t n_cells, const int32_t* __restrict__ cell_start,
 }
 
 // Thread per sorted slot: gather the velocities (independent random loads).
-__global__ void k_gather(int32_t n, const int32_t* __restrict__ perm, const double* __restrict__ vx,
+// Only the cell_start[n_cells] slots that the scatter filled are read: a
+// particle with an out-of-range cell id (reported as DSMC_ERR_ARG) has no
+// slot, and the perm entries past the filled ones are never written.
+__global__ void k_gather(int32_t n, const int32_t* __restrict__ cell_start, int32_t n_cells,
+                         const int32_t* __restrict__ perm, const double* __restrict__ vx,
                          const double* __restrict__ vy, const double* __restrict__ vz,
                          double* __restrict__ svx, double* __restrict__ svy, double* __restrict__ svz) {
-  for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+  const int32_t filled = min(n, cell_start[n_cells]);
+  for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < filled; s += gridDim.x * blockDim.x) {
     const int32_t src = perm[s];
     svx[s] = vx[src];
     svy[s] = vy[src];
@@ -219,8 +224,18 @@ int launch_sort(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_id, cons
   k_scatter<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(cell_id, n, n_cells, cell_start, counts, slots);
   k_fix_gather<<<grid_for(n_cells, kFixWarps, sms * 4), kFixWarps * 32, 0, s>>>(
       n_cells, cell_start, slots, perm, vx, vy, vz, svx, svy, svz);
-  k_gather<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(n, perm, vx, vy, vz, svx, svy, svz);
-  count_launches(c, 3);
+  count_launches(c, 2);
+  return launch_gather(c, n, n_cells, cell_start, perm, vx, vy, vz, svx, svy, svz, s);
+}
+
+int launch_gather(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_start, const int32_t* perm,
+                  const double* vx, const double* vy, const double* vz, double* svx, double* svy,
+                  double* svz, cudaStream_t s) {
+  if (n <= 0) return 0;
+  const Shape sh = shape_or_default(c, DSMC_TUNE_GATHER);
+  k_gather<<<grid_for(n, sh.threads, sm_count(c) * sh.blocks_per_sm), sh.threads, 0, s>>>(
+      n, cell_start, n_cells, perm, vx, vy, vz, svx, svy, svz);
+  count_launches(c, 1);
   return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
 }
 
@@ -241,9 +256,9 @@ k_moments(int32_t n_cells, const int32_t* __restrict__ cs, const double* __restr
           const double* __restrict__ vy, const double* __restrict__ vz, double* __restrict__ mom,
           int* status) {
   const int lane = threadIdx.x & 31, sl = lane & (kSeg - 1), seg = lane / kSeg;
-  const int32_t per_warp = 32 / kSeg;
-  const int32_t warps = gridDim.x * kCellWarps;
-  for (int32_t k0 = (blockIdx.x * kCellWarps + (threadIdx.x >> 5)) * per_warp; k0 < n_cells;
+  const int32_t per_warp = 32 / kSeg, wpb = blockDim.x >> 5;
+  const int32_t warps = gridDim.x * wpb;
+  for (int32_t k0 = (blockIdx.x * wpb + (threadIdx.x >> 5)) * per_warp; k0 < n_cells;
        k0 += warps * per_warp) {
     const int32_t k = k0 + seg;
     const bool has = k < n_cells;
@@ -272,7 +287,8 @@ k_moments(int32_t n_cells, const int32_t* __restrict__ cs, const double* __restr
 int launch_moments(Ctx* c, int32_t n_cells, const int32_t* cs, const double* vx,
                    const double* vy, const double* vz, double* mom, cudaStream_t s) {
   if (n_cells <= 0) return 0;
-  k_moments<<<grid_for((n_cells + 3) / 4, kCellWarps, sm_count(c) * 8), kCellWarps * 32, 0, s>>>(
+  const Shape sh = shape_or_default(c, DSMC_TUNE_MOMENTS);
+  k_moments<<<grid_for((n_cells + 3) / 4, sh.threads / 32, sm_count(c) * sh.blocks_per_sm), sh.threads, 0, s>>>(
       n_cells, cs, vx, vy, vz, mom, status_ptr(c));
   count_launches(c, 1);
   return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
@@ -285,9 +301,9 @@ __global__ void __launch_bounds__(kCellWarps * 32)
 k_moment_match(int32_t n_cells, const int32_t* __restrict__ cs, const double* __restrict__ mom,
                double* __restrict__ vx, double* __restrict__ vy, double* __restrict__ vz) {
   const int lane = threadIdx.x & 31, sl = lane & (kSeg - 1), seg = lane / kSeg;
-  const int32_t per_warp = 32 / kSeg;
-  const int32_t warps = gridDim.x * kCellWarps;
-  for (int32_t k0 = (blockIdx.x * kCellWarps + (threadIdx.x >> 5)) * per_warp; k0 < n_cells;
+  const int32_t per_warp = 32 / kSeg, wpb = blockDim.x >> 5;
+  const int32_t warps = gridDim.x * wpb;
+  for (int32_t k0 = (blockIdx.x * wpb + (threadIdx.x >> 5)) * per_warp; k0 < n_cells;
        k0 += warps * per_warp) {
     const int32_t k = k0 + seg;
     const bool has = k < n_cells;
@@ -319,8 +335,9 @@ k_moment_match(int32_t n_cells, const int32_t* __restrict__ cs, const double* __
 int launch_moment_match(Ctx* c, int32_t n_cells, const int32_t* cs, const double* mom,
                         double* vx, double* vy, double* vz, cudaStream_t s) {
   if (n_cells <= 0) return 0;
-  k_moment_match<<<grid_for((n_cells + 3) / 4, kCellWarps, sm_count(c) * 8), kCellWarps * 32, 0, s>>>(
-      n_cells, cs, mom, vx, vy, vz);
+  const Shape sh = shape_or_default(c, DSMC_TUNE_MOMENT_MATCH);
+  k_moment_match<<<grid_for((n_cells + 3) / 4, sh.threads / 32, sm_count(c) * sh.blocks_per_sm), sh.threads, 0,
+                   s>>>(n_cells, cs, mom, vx, vy, vz);
   count_launches(c, 1);
   return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
 }
@@ -404,7 +421,8 @@ extern "C" int dsmc_sort_cells_static(int32_t n, int32_t n_cells, const int32_t*
     k_scatter<<<grid_for(n, 256, d->sms * 16), 256, 0, s>>>(cell_id, n, n_cells, cell_start, counts, slots);
     k_fix_gather<<<grid_for(n_cells, kFixWarps, d->sms * 4), kFixWarps * 32, 0, s>>>(
         n_cells, cell_start, slots, perm, vx, vy, vz, svx, svy, svz);
-    k_gather<<<grid_for(n, 256, d->sms * 16), 256, 0, s>>>(n, perm, vx, vy, vz, svx, svy, svz);
+    k_gather<<<grid_for(n, 256, d->sms * 16), 256, 0, s>>>(n, cell_start, n_cells, perm, vx, vy, vz, svx,
+                                                           svy, svz);
   }
   return cudaGetLastError() == cudaSuccess ? DSMC_OK : DSMC_ERR_CUDA;
 }

@@ -54,16 +54,25 @@ int cooperative_blocks(Ctx* c, const void* kernel, int threads, size_t smem) {
   return per_sm * sm_count(c);
 }
 
+// resident blocks per SM of the VHS collide at a block size (0 on failure)
+int occupancy_collide_vhs(int threads) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_collide_vhs, threads, 0) != cudaSuccess)
+    return 0;
+  return per_sm;
+}
+
 int launch_collide_vhs(Ctx* c, const dsmc_gas_t& gas, uint64_t step, const int32_t* pairs,
                        const int32_t* ro, const dsmc_select_info_t* info, double* vx,
                        double* vy, double* vz, cudaStream_t s) {
-  static int blocks = 0;
-  if (!blocks) blocks = cooperative_blocks(c, (const void*)k_collide_vhs, 256, 0);
-  if (!blocks) return record(c, DSMC_ERR_CUDA, "collide_vhs: occupancy query failed");
+  const Shape sh = shape_or_default(c, DSMC_TUNE_COLLIDE_VHS);
+  const int occ = occupancy_collide_vhs(sh.threads);
+  if (occ < 1) return record(c, DSMC_ERR_CUDA, "collide_vhs: occupancy query failed");
+  const int blocks = sm_count(c) * (sh.blocks_per_sm > 0 && sh.blocks_per_sm < occ ? sh.blocks_per_sm : occ);
   VhsArgs a{gas.seed, step, graph_step_ptr(c), (const int4*)pairs, ro, info, vx, vy, vz, barrier_ptr(c), status_ptr(c)};
   if (cudaMemsetAsync(a.bar, 0, 4 * sizeof(unsigned), s) != cudaSuccess) return DSMC_ERR_CUDA;
   void* args[] = {&a};
-  if (cudaLaunchCooperativeKernel((const void*)k_collide_vhs, dim3(blocks), dim3(256), args, 0, s) !=
+  if (cudaLaunchCooperativeKernel((const void*)k_collide_vhs, dim3(blocks), dim3(sh.threads), args, 0, s) !=
       cudaSuccess)
     return record(c, DSMC_ERR_CUDA, "collide_vhs: cooperative launch failed");
   count_launches(c, 1);

@@ -82,6 +82,8 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 // arrivals, `bar[1]` is the generation.  Every wait is bounded: after
 // `limit_ns` the block records DSMC_ERR_TIMEOUT, raises the abort flag
 // bar[2] and returns false; callers then leave the kernel.
+// bar[3] is a work cursor that the last block to arrive resets to 0 before
+// releasing the others (every block has stopped claiming work by then).
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* status, uint64_t limit_ns) {
   __syncthreads();
   __shared__ int ok;
@@ -94,6 +96,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* status, uint64_
     const unsigned arrived = atomicAdd(bar, 1u);
     if (arrived == gridDim.x - 1) {
       bar[0] = 0;
+      bar[3] = 0;
       __threadfence();
       atomicAdd(bar + 1, 1u);
     } else {
@@ -169,6 +172,34 @@ int launch_mlp_forward(Ctx* c, const dsmc_mlp_t& mlp, const uint16_t* w, const f
 int launch_tc_selftest(Ctx* c, int N, int K, int layout, const uint16_t* A, const uint16_t* B, float* D,
                        cudaStream_t s);
 int cooperative_blocks(Ctx* c, const void* kernel, int threads, size_t smem);
+
+// Launch shapes of the tunable kernels (DSMC_TUNE_*): threads per block and
+// blocks per SM, {0, 0} while the built-in shape is in force.
+struct Shape {
+  int threads, blocks_per_sm;
+};
+Shape tune_shape(Ctx* c, int kernel);
+// threads per block, blocks per SM and the block-size limit of the built-in shapes
+struct ShapeInfo {
+  int threads, blocks_per_sm, max_threads;
+};
+ShapeInfo shape_info(int kernel);
+// the shape a launch uses: the tuned one, else the built-in one
+inline Shape shape_or_default(Ctx* c, int kernel) {
+  Shape s = tune_shape(c, kernel);
+  if (s.threads <= 0) {
+    const ShapeInfo d = shape_info(kernel);
+    s = Shape{d.threads, d.blocks_per_sm};
+  }
+  return s;
+}
+// resident blocks per SM of the cooperative collide kernels at a block size
+int occupancy_collide_vhs(int threads);
+int occupancy_collide_jager(int threads);
+// the gather step of the cell sort alone (autotuning)
+int launch_gather(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_start, const int32_t* perm,
+                  const double* vx, const double* vy, const double* vz, double* svx, double* svy,
+                  double* svz, cudaStream_t s);
 int launch_selftest_barrier(Ctx* c, uint64_t limit_ns, cudaStream_t s);
 int launch_selftest_mbar(Ctx* c, uint64_t limit_ns, cudaStream_t s);
 

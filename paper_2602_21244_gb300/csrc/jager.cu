@@ -389,34 +389,52 @@ struct JagerArgs {
   int* status;
 };
 
+// One pair: chi(b, E) for its impact parameter and energy, rotation of v_r
+// (Bird 1994, Eq. 2.22), centre-of-mass update; velocities through L2.
+__device__ __forceinline__ void collide_pair(const PotDev& P, const JagerArgs& a, int64_t p) {
+  const int4 q = a.pairs[p];
+  const double xi = __ldcg(a.vx + q.x), yi = __ldcg(a.vy + q.x), zi = __ldcg(a.vz + q.x);
+  const double xj = __ldcg(a.vx + q.y), yj = __ldcg(a.vy + q.y), zj = __ldcg(a.vz + q.y);
+  const double ux = xi - xj, uy = yi - yj, uz = zi - zj;
+  const double g2 = ux * ux + uy * uy + uz * uz;
+  const u32x4 w = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_JAGER);
+  const float b = (float)(a.bmax_A * sqrt(u53(w.x, w.y)));
+  const float E = P.mass_over_4k * (float)g2;
+  const float chi = g2 > 0.0 ? chi_device(P, b, E) : 0.f;
+  if (a.chi_out) a.chi_out[p] = chi;
+  double cc, sc, ce, se;
+  unit_angle(chi, &cc, &sc);
+  unit_angle((float)(2.0 * DSMC_PI * u53(w.z, w.w)), &ce, &se);
+  double o[3] = {0.0, 0.0, 0.0};
+  if (g2 > 0.0) {
+    const double ig = rsqrt(g2);
+    deflect(ux, uy, uz, g2 * ig, ig, cc, sc, ce, se, o);
+  }
+  const double cx = 0.5 * (xi + xj), cy = 0.5 * (yi + yj), cz = 0.5 * (zi + zj);
+  __stcg(a.vx + q.x, cx + 0.5 * o[0]); __stcg(a.vy + q.x, cy + 0.5 * o[1]); __stcg(a.vz + q.x, cz + 0.5 * o[2]);
+  __stcg(a.vx + q.y, cx - 0.5 * o[0]); __stcg(a.vy + q.y, cy - 0.5 * o[1]); __stcg(a.vz + q.y, cz - 0.5 * o[2]);
+}
+
+// Pairs of a round are claimed dynamically, 32 at a time per warp, from the
+// cursor in bar[3] (reset by the grid barrier between rounds): the cost of a
+// pair varies by an order of magnitude (bracket scan, Newton iterations), and
+// a static split leaves most warps waiting at the barrier for the slowest.
+// Which thread handles a pair does not change its result.
 __global__ void __launch_bounds__(128) k_collide_jager(PotDev P, JagerArgs a) {
   if (a.step_dev) a.step = *a.step_dev;
   const int R = a.info->n_rounds;
-  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  unsigned* cursor = a.bar + 3;
   for (int r = 0; r < R; ++r) {
     const int32_t beg = a.ro[r], end = a.ro[r + 1];
-    for (int64_t p = beg + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < end; p += nthr) {
-      const int4 q = a.pairs[p];
-      const double xi = __ldcg(a.vx + q.x), yi = __ldcg(a.vy + q.x), zi = __ldcg(a.vz + q.x);
-      const double xj = __ldcg(a.vx + q.y), yj = __ldcg(a.vy + q.y), zj = __ldcg(a.vz + q.y);
-      const double ux = xi - xj, uy = yi - yj, uz = zi - zj;
-      const double g2 = ux * ux + uy * uy + uz * uz;
-      const u32x4 w = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_JAGER);
-      const float b = (float)(a.bmax_A * sqrt(u53(w.x, w.y)));
-      const float E = P.mass_over_4k * (float)g2;
-      const float chi = g2 > 0.0 ? chi_device(P, b, E) : 0.f;
-      if (a.chi_out) a.chi_out[p] = chi;
-      double cc, sc, ce, se;
-      unit_angle(chi, &cc, &sc);
-      unit_angle((float)(2.0 * DSMC_PI * u53(w.z, w.w)), &ce, &se);
-      double o[3] = {0.0, 0.0, 0.0};
-      if (g2 > 0.0) {
-        const double ig = rsqrt(g2);
-        deflect(ux, uy, uz, g2 * ig, ig, cc, sc, ce, se, o);
-      }
-      const double cx = 0.5 * (xi + xj), cy = 0.5 * (yi + yj), cz = 0.5 * (zi + zj);
-      __stcg(a.vx + q.x, cx + 0.5 * o[0]); __stcg(a.vy + q.x, cy + 0.5 * o[1]); __stcg(a.vz + q.x, cz + 0.5 * o[2]);
-      __stcg(a.vx + q.y, cx - 0.5 * o[0]); __stcg(a.vy + q.y, cy - 0.5 * o[1]); __stcg(a.vz + q.y, cz - 0.5 * o[2]);
+    const unsigned n_r = (unsigned)(end - beg);
+    for (;;) {
+      unsigned base = 0;
+      if (lane == 0) base = atomicAdd(cursor, 32u);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (base >= n_r) break;
+      const int64_t p = (int64_t)beg + base + lane;
+      if (p < end) collide_pair(P, a, p);
     }
     if (r + 1 < R && !grid_barrier(a.bar, a.status, kBarrierLimitNs)) return;
   }
@@ -460,24 +478,34 @@ int launch_jager_chi(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& pot,
                      int64_t n, const float* b, const float* g, float* chi, cudaStream_t s) {
   if (n == 0) return 0;
   const PotDev P = make_pot(gas, pot, n_nodes);
-  k_jager_chi<<<blocks_n(n, 128, sm_count(c) * 64), 128, 0, s>>>(P, n, b, g, chi);
+  const Shape sh = shape_or_default(c, DSMC_TUNE_JAGER_CHI);
+  k_jager_chi<<<blocks_n(n, sh.threads, sm_count(c) * sh.blocks_per_sm), sh.threads, 0, s>>>(P, n, b, g, chi);
   count_launches(c, 1);
   return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
+}
+
+// resident blocks per SM of the Jager collide at a block size (0 on failure)
+int occupancy_collide_jager(int threads) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_collide_jager, threads, 0) != cudaSuccess)
+    return 0;
+  return per_sm;
 }
 
 int launch_collide_jager(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& pot,
                          int n_nodes, uint64_t step, const int32_t* pairs, const int32_t* ro,
                          const dsmc_select_info_t* info, double* vx, double* vy, double* vz,
                          float* chi_out, cudaStream_t s) {
-  static int blocks = 0;
-  if (!blocks) blocks = cooperative_blocks(c, (const void*)k_collide_jager, 128, 0);
-  if (!blocks) return record(c, DSMC_ERR_CUDA, "collide_jager: occupancy query failed");
+  const Shape sh = shape_or_default(c, DSMC_TUNE_COLLIDE_JAGER);
+  const int occ = occupancy_collide_jager(sh.threads);
+  if (occ < 1) return record(c, DSMC_ERR_CUDA, "collide_jager: occupancy query failed");
+  const int blocks = sm_count(c) * (sh.blocks_per_sm > 0 && sh.blocks_per_sm < occ ? sh.blocks_per_sm : occ);
   PotDev P = make_pot(gas, pot, n_nodes);
   JagerArgs a{gas.seed, step, graph_step_ptr(c), gas.b_max * 1e10, (const int4*)pairs, ro, info, vx, vy, vz,
               chi_out, barrier_ptr(c), status_ptr(c)};
   if (cudaMemsetAsync(a.bar, 0, 4 * sizeof(unsigned), s) != cudaSuccess) return DSMC_ERR_CUDA;
   void* args[] = {&P, &a};
-  if (cudaLaunchCooperativeKernel((const void*)k_collide_jager, dim3(blocks), dim3(128), args, 0, s) !=
+  if (cudaLaunchCooperativeKernel((const void*)k_collide_jager, dim3(blocks), dim3(sh.threads), args, 0, s) !=
       cudaSuccess)
     return record(c, DSMC_ERR_CUDA, "collide_jager: cooperative launch failed");
   count_launches(c, 1);

@@ -64,6 +64,15 @@ class StepBuffers(C.Structure):
                 ("info", C.c_void_p), ("ws", C.c_void_p), ("ws_bytes", C.c_size_t)]
 
 
+class TuneEntry(C.Structure):
+    _fields_ = [("kernel", C.c_int32), ("threads", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("ms", C.c_float)]
+
+
+# DSMC_TUNE_* kernel ids and their names in the autotune cache
+TUNE_KERNELS = ("gather", "moments", "moment_match", "collide_vhs", "collide_jager", "jager_chi")
+
+
 class Path(C.Structure):
     _fields_ = [("path", C.c_int32), ("n_nodes", C.c_int32), ("pot", C.POINTER(Potential)),
                 ("mlp", C.POINTER(Mlp)), ("weights_bf16", C.c_void_p), ("biases", C.c_void_p)]
@@ -131,6 +140,13 @@ def load(build: bool = True):
                                                sz, vp]),
             "dsmc_adam_step": (C.c_int, [vp, i32, i32, vp, vp, vp, vp, i64, C.c_float, C.c_float, C.c_float,
                                          C.c_float, vp, vp, vp]),
+            "dsmc_tune_set": (C.c_int, [vp, i32, i32, i32]),
+            "dsmc_tune_get": (C.c_int, [vp, i32, P(i32), P(i32)]),
+            "dsmc_tune_candidates": (C.c_int, [vp, i32, P(TuneEntry), i32, P(i32)]),
+            "dsmc_autotune_step": (C.c_int, [vp, P(Gas), P(Path), P(StepBuffers), u64, i32, P(TuneEntry), i32,
+                                             P(i32), vp]),
+            "dsmc_autotune_chi": (C.c_int, [vp, P(Gas), P(Potential), i32, i64, vp, vp, vp, i32, P(TuneEntry),
+                                            i32, P(i32), vp]),
             "dsmc_train_step": (C.c_int, [vp, P(Mlp), vp, vp, vp, i64, C.c_float, u64, i64, vp, vp, vp, vp,
                                           vp, vp, vp, vp, vp, vp, sz, vp]),
         }
@@ -429,6 +445,97 @@ class Context:
             hp(T_cell), step, hp(perm), hp(svx), hp(svy), hp(svz), C.byref(npairs), _stream(stream)),
             "step_host")
         return npairs.value
+
+
+    # -------------------------------------------------------------- launch shapes
+    def tune_set(self, kernel: int, threads: int = 0, blocks_per_sm: int = 0):
+        self._check(self._lib.dsmc_tune_set(self.h, kernel, threads, blocks_per_sm), "tune_set")
+
+    def tune_get(self, kernel: int) -> tuple[int, int]:
+        t, b = C.c_int32(0), C.c_int32(0)
+        self._check(self._lib.dsmc_tune_get(self.h, kernel, C.byref(t), C.byref(b)), "tune_get")
+        return t.value, b.value
+
+    def tune_candidates(self, kernel: int) -> list[tuple[int, int]]:
+        buf, n = (TuneEntry * 64)(), C.c_int32(0)
+        self._check(self._lib.dsmc_tune_candidates(self.h, kernel, buf, 64, C.byref(n)), "tune_candidates")
+        return [(buf[q].threads, buf[q].blocks_per_sm) for q in range(min(n.value, 64))]
+
+    @staticmethod
+    def _trials(buf, n):
+        return [dict(kernel=TUNE_KERNELS[buf[q].kernel], threads=buf[q].threads,
+                     blocks_per_sm=buf[q].blocks_per_sm, ms=float(buf[q].ms)) for q in range(n)]
+
+    def autotune_step(self, gas: Gas, path: Path, bufs: "StepState", step: int = 0, reps: int = 3,
+                      stream=None) -> list[dict]:
+        """dsmc_autotune_step: time the candidate shapes of the step's tunable
+        kernels on these buffers (their contents are consumed) and keep the
+        fastest in the context.  Returns every measured trial."""
+        buf, n = (TuneEntry * 256)(), C.c_int32(0)
+        self._check(self._lib.dsmc_autotune_step(self.h, C.byref(gas), C.byref(path), C.byref(bufs.desc), step,
+                                                 reps, buf, 256, C.byref(n), _stream(stream)), "autotune_step")
+        return self._trials(buf, min(n.value, 256))
+
+    def autotune_chi(self, gas: Gas, pot: Potential, b, g, n_nodes=32, chi=None, reps=3, stream=None):
+        chi = torch.empty_like(b) if chi is None else chi
+        buf, n = (TuneEntry * 64)(), C.c_int32(0)
+        self._check(self._lib.dsmc_autotune_chi(self.h, C.byref(gas), C.byref(pot), n_nodes, b.numel(),
+                                                _ptr(b, torch.float32), _ptr(g, torch.float32),
+                                                _ptr(chi, torch.float32), reps, buf, 64, C.byref(n),
+                                                _stream(stream)), "autotune_chi")
+        return self._trials(buf, min(n.value, 64))
+
+    def tuned_shapes(self) -> dict:
+        return {name: self.tune_get(k) for k, name in enumerate(TUNE_KERNELS)}
+
+
+# ------------------------------------------------------------------ autotune cache
+# JSON: {device name: {kernel name: {size bucket: {"threads": t, "blocks_per_sm": b, "ms": m}}}},
+# the bucket being floor(log2(particles)) (pairs for the chi batch).
+
+def size_bucket(n: int) -> str:
+    return str(max(int(n), 1).bit_length() - 1)
+
+
+def tune_cache_store(path: str, ctx: Context, n: int, trials: list[dict], device_name: str | None = None):
+    """Record the fastest measured shape of each kernel in ``trials`` under
+    (device, kernel, size bucket) in the JSON file at ``path``."""
+    import json
+    dev = device_name or torch.cuda.get_device_name(ctx.device)
+    try:
+        with open(path) as f:
+            cache = json.load(f)
+    except (OSError, ValueError):
+        cache = {}
+    best = {}
+    for t in trials:
+        if t["kernel"] not in best or t["ms"] < best[t["kernel"]]["ms"]:
+            best[t["kernel"]] = t
+    for k, t in best.items():
+        cache.setdefault(dev, {}).setdefault(k, {})[size_bucket(n)] = dict(
+            threads=t["threads"], blocks_per_sm=t["blocks_per_sm"], ms=t["ms"])
+    with open(path, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    return cache
+
+
+def tune_cache_apply(path: str, ctx: Context, n: int, device_name: str | None = None) -> dict:
+    """Set the context's shapes from the cache entries of this device and
+    size bucket; returns what was applied."""
+    import json
+    dev = device_name or torch.cuda.get_device_name(ctx.device)
+    try:
+        with open(path) as f:
+            cache = json.load(f).get(dev, {})
+    except (OSError, ValueError):
+        return {}
+    applied = {}
+    for k, name in enumerate(TUNE_KERNELS):
+        e = cache.get(name, {}).get(size_bucket(n))
+        if e:
+            ctx.tune_set(k, int(e["threads"]), int(e["blocks_per_sm"]))
+            applied[name] = (int(e["threads"]), int(e["blocks_per_sm"]))
+    return applied
 
 
 STATIC_SORT_MAX_N, STATIC_SORT_MAX_CELLS = 1 << 20, 1 << 18

@@ -49,6 +49,7 @@ int main(void) {
          sizeof(dsmc_path_t));
   printf("%zu %zu %zu %zu\n", offsetof(dsmc_gas_t, b_max), offsetof(dsmc_potential_t, C),
          offsetof(dsmc_potential_t, p), offsetof(dsmc_step_buffers_t, ws_bytes));
+  printf("%zu %zu %d\n", sizeof(dsmc_tune_entry_t), offsetof(dsmc_tune_entry_t, ms), (int)DSMC_TUNE_KERNELS);
   return 0;
 }'''
     with tempfile.TemporaryDirectory() as td:
@@ -60,8 +61,9 @@ int main(void) {
     sizes = [int(x) for x in out]
     assert sizes[:6] == [C.sizeof(D.Gas), C.sizeof(D.Potential), C.sizeof(D.Mlp),
                          C.sizeof(D.SelectInfo), C.sizeof(D.StepBuffers), C.sizeof(D.Path)]
-    assert sizes[6:] == [D.Gas.b_max.offset, D.Potential.C.offset, D.Potential.p.offset,
-                         D.StepBuffers.ws_bytes.offset]
+    assert sizes[6:10] == [D.Gas.b_max.offset, D.Potential.C.offset, D.Potential.p.offset,
+                           D.StepBuffers.ws_bytes.offset]
+    assert sizes[10:] == [C.sizeof(D.TuneEntry), D.TuneEntry.ms.offset, len(D.TUNE_KERNELS)]
 
 
 def test_context_create_fails_cleanly_without_gpu():
