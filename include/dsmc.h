@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define DSMC_ABI_VERSION 1
+#define DSMC_ABI_VERSION 2
 
 enum {
   DSMC_OK = 0,
@@ -202,6 +202,8 @@ int dsmc_sigma_g_max_init(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, int32_t n_cell
  *  applied in round order, reproduce the sequential result exactly.
  *  Output: pairs[4p..4p+3] = {i, j, cell, m} (sorted slot indices, cell,
  *  candidate index) grouped by round (order inside a round unspecified),
+ *  deps[p] = (1-based round of the previous pair of particle i) | (that of
+ *  j) << 16, 0 = none (the collide kernels order their work by it),
  *  round_offsets[r] = first pair of round r (the array holds
  *  DSMC_MAX_ROUNDS + 1 entries; r = 0..n_rounds are meaningful), *info.
  *  More than `capacity` pairs records DSMC_ERR_CAPACITY and writes none;
@@ -210,20 +212,29 @@ size_t dsmc_select_workspace_size(int32_t n, int32_t n_cells, int64_t capacity);
 int dsmc_select_pairs(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, int32_t n, int32_t n_cells,
                       const int32_t* cell_start, const double* vx, const double* vy,
                       const double* vz, double* sigma_g_max, uint64_t step, int64_t capacity,
-                      int32_t* pairs, int32_t* round_offsets, dsmc_select_info_t* info,
+                      int32_t* pairs, uint32_t* deps, int32_t* round_offsets, dsmc_select_info_t* info,
                       void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------- pair updates */
+
+/* Common to the three collide calls: n particles (the sorted slots the
+ * pairs index), pairs / deps / round_offsets / info from dsmc_select_pairs.
+ * The kernels apply the pairs in round order without grid-wide barriers: a
+ * pair waits (bounded; DSMC_ERR_TIMEOUT if it runs out) until the previous
+ * pairs of its two particles are done, which gives the result of applying
+ * the rounds one after another.  ws: dsmc_collide_workspace_size(n) bytes
+ * of scratch (one done stamp per particle, cleared by each call). */
+size_t dsmc_collide_workspace_size(int32_t n);
 
 /* VHS isotropic scatter (the phenomenological kernel the paper replaces,
  * Sec. 2.1) with the centre-of-mass update of Sec. 2.3:
  *  cos chi = 2U1 - 1, eps = 2 pi U2 (Philox tag 3, counter = candidate m),
  *  v_r' = |v_r| (cos chi, sin chi cos eps, sin chi sin eps),
- *  v_i = v_cm + v_r'/2, v_j = v_cm - v_r'/2; rounds in order, in place. */
-int dsmc_collide_vhs(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, uint64_t step,
-                     const int32_t* pairs, const int32_t* round_offsets,
+ *  v_i = v_cm + v_r'/2, v_j = v_cm - v_r'/2; in place. */
+int dsmc_collide_vhs(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, uint64_t step, int32_t n,
+                     const int32_t* pairs, const uint32_t* deps, const int32_t* round_offsets,
                      const dsmc_select_info_t* info, double* vx, double* vy, double* vz,
-                     void* stream);
+                     void* ws, size_t ws_bytes, void* stream);
 
 /* Sec. 3.4.2 / 3.4.4: deflection angle of the classical scattering integral
  *  chi(b, E) = pi - 2 b int_{r_min}^inf dr / (r^2 sqrt(1 - b^2/r^2 - V(r)/E)),
@@ -243,9 +254,10 @@ int dsmc_jager_chi(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_potential_
  *  a = c x v_r/|v_r|).  chi_out (optional, may be NULL) receives each
  *  pair's chi in pair order. */
 int dsmc_collide_jager(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_potential_t* pot,
-                       int32_t n_nodes, uint64_t step, const int32_t* pairs,
-                       const int32_t* round_offsets, const dsmc_select_info_t* info,
-                       double* vx, double* vy, double* vz, float* chi_out, void* stream);
+                       int32_t n_nodes, uint64_t step, int32_t n, const int32_t* pairs,
+                       const uint32_t* deps, const int32_t* round_offsets, const dsmc_select_info_t* info,
+                       double* vx, double* vy, double* vz, float* chi_out, void* ws, size_t ws_bytes,
+                       void* stream);
 
 /* Sec. 2.2-2.3: neural collision operator on the tcgen05 tensor cores.
  *  x as in dsmc_mlp_t (xi: Box-Muller normals from tag 5, subs 0 and 1;
@@ -260,9 +272,10 @@ int dsmc_collide_jager(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_potent
  *  (FP32 [n_pairs x 3], pair order). */
 int dsmc_collide_neural(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_mlp_t* mlp,
                         const uint16_t* weights_bf16, const float* biases, uint64_t step,
-                        const double* mom_pre, const int32_t* pairs,
+                        const double* mom_pre, int32_t n, const int32_t* pairs, const uint32_t* deps,
                         const int32_t* round_offsets, const dsmc_select_info_t* info,
-                        double* vx, double* vy, double* vz, float* u_out, void* stream);
+                        double* vx, double* vy, double* vz, float* u_out, void* ws, size_t ws_bytes,
+                        void* stream);
 
 /* The MLP alone on the tensor cores: y[n x 3] = f_theta(x[n x d_in]) with x
  * and y FP32 row-major (x rounded to bf16 on the way in), same weight
@@ -283,7 +296,8 @@ int dsmc_tc_selftest(dsmc_ctx_t* ctx, int32_t N, int32_t K, int32_t layout, cons
 /* Diagnostic with no counterpart in the paper (failure detection): runs a
  * kernel whose bounded wait can never be satisfied -- which 0: a grid
  * barrier that one block never reaches; which 1: an mbarrier that no
- * tensor-core commit completes -- so that the wait runs out after limit_ns
+ * tensor-core commit completes; which 2: a pair-dependency wait on a done
+ * stamp that nothing sets -- so that the wait runs out after limit_ns
  * (at most 2 s) and records DSMC_ERR_TIMEOUT in the status word.  Nothing
  * traps or spins without bound; the context stays usable. */
 int dsmc_selftest_timeout(dsmc_ctx_t* ctx, int32_t which, uint64_t limit_ns, void* stream);
@@ -303,7 +317,9 @@ int dsmc_moment_match(dsmc_ctx_t* ctx, int32_t n_cells, const int32_t* cell_star
 /* Buffers of one collision step (all device memory, caller-owned).
  * Input: cell_id, vx, vy, vz (unsorted).  Output: perm, cell_start and the
  * sorted, post-collision s{x,y,z}; mom (pre moments), sigma_g_max (in/out),
- * pairs / round_offsets / info as in dsmc_select_pairs. */
+ * pairs / deps / round_offsets / info as in dsmc_select_pairs (deps:
+ * `capacity` uint32).  ws: dsmc_step_workspace_size bytes, shared by the
+ * phases. */
 typedef struct {
   int32_t n, n_cells;
   int64_t capacity;
@@ -319,6 +335,7 @@ typedef struct {
   dsmc_select_info_t* info;
   void* ws;
   size_t ws_bytes;
+  uint32_t* deps;
 } dsmc_step_buffers_t;
 
 /* Path-specific parameters of a step (unused fields may be NULL/0). */

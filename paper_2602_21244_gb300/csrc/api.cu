@@ -218,23 +218,26 @@ static int check_gas(Ctx* c, const dsmc_gas_t* gas) {
 int dsmc_select_pairs(dsmc_ctx_t* c, const dsmc_gas_t* gas, int32_t n, int32_t n_cells,
                       const int32_t* cell_start, const double* vx, const double* vy,
                       const double* vz, double* sgmax, uint64_t step, int64_t capacity,
-                      int32_t* pairs, int32_t* round_offsets, dsmc_select_info_t* info,
+                      int32_t* pairs, uint32_t* deps, int32_t* round_offsets, dsmc_select_info_t* info,
                       void* ws, size_t ws_bytes, void* stream) {
   CHECK_CTX(c);
   if (int rc = check_gas(c, gas)) return rc;
   REQUIRE(c, n >= 0 && n_cells >= 1 && capacity >= 0, "select: bad sizes");
   REQUIRE(c, cell_start && sgmax && round_offsets && info && ws, "select: null pointer");
-  REQUIRE(c, capacity == 0 || pairs, "select: null pairs");
+  REQUIRE(c, capacity == 0 || (pairs && deps), "select: null pairs or deps");
   return dsmc::launch_select(c, *gas, n, n_cells, cell_start, vx, vy, vz, sgmax, step, capacity,
-                             pairs, round_offsets, info, ws, ws_bytes, S(stream));
+                             pairs, deps, round_offsets, info, ws, ws_bytes, S(stream));
 }
 
-int dsmc_collide_vhs(dsmc_ctx_t* c, const dsmc_gas_t* gas, uint64_t step, const int32_t* pairs,
-                     const int32_t* round_offsets, const dsmc_select_info_t* info, double* vx,
-                     double* vy, double* vz, void* stream) {
+size_t dsmc_collide_workspace_size(int32_t n) { return dsmc::collide_ws(n); }
+
+int dsmc_collide_vhs(dsmc_ctx_t* c, const dsmc_gas_t* gas, uint64_t step, int32_t n, const int32_t* pairs,
+                     const uint32_t* deps, const int32_t* round_offsets, const dsmc_select_info_t* info,
+                     double* vx, double* vy, double* vz, void* ws, size_t ws_bytes, void* stream) {
   CHECK_CTX(c);
-  REQUIRE(c, gas && round_offsets && info && vx && vy && vz, "collide_vhs: null pointer");
-  return dsmc::launch_collide_vhs(c, *gas, step, pairs, round_offsets, info, vx, vy, vz, S(stream));
+  REQUIRE(c, gas && round_offsets && info && vx && vy && vz && ws && n >= 0, "collide_vhs: null pointer");
+  return dsmc::launch_collide_vhs(c, *gas, step, n, pairs, deps, round_offsets, info, vx, vy, vz, ws, ws_bytes,
+                                  S(stream));
 }
 
 static int check_pot(Ctx* c, const dsmc_potential_t* p, int n_nodes) {
@@ -258,15 +261,16 @@ int dsmc_jager_chi(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_potential_t*
 }
 
 int dsmc_collide_jager(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_potential_t* pot,
-                       int32_t n_nodes, uint64_t step, const int32_t* pairs,
+                       int32_t n_nodes, uint64_t step, int32_t n, const int32_t* pairs, const uint32_t* deps,
                        const int32_t* round_offsets, const dsmc_select_info_t* info,
-                       double* vx, double* vy, double* vz, float* chi_out, void* stream) {
+                       double* vx, double* vy, double* vz, float* chi_out, void* ws, size_t ws_bytes,
+                       void* stream) {
   CHECK_CTX(c);
   REQUIRE(c, gas && gas->b_max > 0, "collide_jager: gas with b_max > 0 required");
   if (int rc = check_pot(c, pot, n_nodes)) return rc;
-  REQUIRE(c, round_offsets && info && vx && vy && vz, "collide_jager: null pointer");
-  return dsmc::launch_collide_jager(c, *gas, *pot, n_nodes, step, pairs, round_offsets, info, vx,
-                                    vy, vz, chi_out, S(stream));
+  REQUIRE(c, round_offsets && info && vx && vy && vz && ws && n >= 0, "collide_jager: null pointer");
+  return dsmc::launch_collide_jager(c, *gas, *pot, n_nodes, step, n, pairs, deps, round_offsets, info, vx,
+                                    vy, vz, chi_out, ws, ws_bytes, S(stream));
 }
 
 static int check_mlp(Ctx* c, const dsmc_mlp_t* m) {
@@ -280,16 +284,17 @@ static int check_mlp(Ctx* c, const dsmc_mlp_t* m) {
 
 int dsmc_collide_neural(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_mlp_t* mlp,
                         const uint16_t* w, const float* bias, uint64_t step,
-                        const double* mom_pre, const int32_t* pairs,
+                        const double* mom_pre, int32_t n, const int32_t* pairs, const uint32_t* deps,
                         const int32_t* round_offsets, const dsmc_select_info_t* info,
-                        double* vx, double* vy, double* vz, float* u_out, void* stream) {
+                        double* vx, double* vy, double* vz, float* u_out, void* ws, size_t ws_bytes,
+                        void* stream) {
   CHECK_CTX(c);
   REQUIRE(c, gas, "collide_neural: null gas");
   if (int rc = check_mlp(c, mlp)) return rc;
-  REQUIRE(c, w && bias && mom_pre && round_offsets && info && vx && vy && vz,
+  REQUIRE(c, w && bias && mom_pre && round_offsets && info && vx && vy && vz && ws && n >= 0,
           "collide_neural: null pointer");
-  return dsmc::launch_collide_neural(c, *gas, *mlp, w, bias, step, mom_pre, pairs, round_offsets,
-                                     info, vx, vy, vz, u_out, S(stream));
+  return dsmc::launch_collide_neural(c, *gas, *mlp, w, bias, step, mom_pre, n, pairs, deps, round_offsets,
+                                     info, vx, vy, vz, u_out, ws, ws_bytes, S(stream));
 }
 
 int dsmc_mlp_forward(dsmc_ctx_t* c, const dsmc_mlp_t* mlp, const uint16_t* w, const float* bias,
@@ -312,8 +317,9 @@ int dsmc_tc_selftest(dsmc_ctx_t* c, int32_t N, int32_t K, int32_t layout, const 
 
 int dsmc_selftest_timeout(dsmc_ctx_t* c, int32_t which, uint64_t limit_ns, void* stream) {
   CHECK_CTX(c);
-  REQUIRE(c, (which == 0 || which == 1) && limit_ns > 0 && limit_ns <= 2000000000ull,
-          "selftest_timeout: which 0|1, 0 < limit_ns <= 2e9");
+  REQUIRE(c, which >= 0 && which <= 2 && limit_ns > 0 && limit_ns <= 2000000000ull,
+          "selftest_timeout: which 0|1|2, 0 < limit_ns <= 2e9");
+  if (which == 2) return dsmc::launch_selftest_deps(c, limit_ns, S(stream));
   return which == 0 ? dsmc::launch_selftest_barrier(c, limit_ns, S(stream))
                     : dsmc::launch_selftest_mbar(c, limit_ns, S(stream));
 }
@@ -411,8 +417,35 @@ int dsmc_train_step(dsmc_ctx_t* c, const dsmc_mlp_t* mlp, float* theta, float* m
 
 // ---------------------------------------------------------------- whole step
 size_t dsmc_step_workspace_size(int32_t n, int32_t n_cells, int64_t capacity) {
-  const size_t a = dsmc::sort_ws(n, n_cells), b = dsmc::select_ws(n, n_cells, capacity);
-  return a > b ? a : b;
+  // the phases run one after another and share the workspace
+  const size_t a = dsmc::sort_ws(n, n_cells), b = dsmc::select_ws(n, n_cells, capacity),
+               d = dsmc::collide_ws(n);
+  const size_t ab = a > b ? a : b;
+  return ab > d ? ab : d;
+}
+
+// the pair update of one step's path (after selection)
+static int collide_step(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t* path,
+                        const dsmc_step_buffers_t* B, uint64_t step, void* stream) {
+  int rc = 0;
+  switch (path->path) {
+    case DSMC_PATH_VHS:
+      rc = dsmc_collide_vhs(c, gas, step, B->n, B->pairs, B->deps, B->round_offsets, B->info, B->svx, B->svy,
+                            B->svz, B->ws, B->ws_bytes, stream);
+      break;
+    case DSMC_PATH_JAGER:
+      rc = dsmc_collide_jager(c, gas, path->pot, path->n_nodes, step, B->n, B->pairs, B->deps, B->round_offsets,
+                              B->info, B->svx, B->svy, B->svz, nullptr, B->ws, B->ws_bytes, stream);
+      break;
+    case DSMC_PATH_NEURAL:
+      rc = dsmc_collide_neural(c, gas, path->mlp, path->weights_bf16, path->biases, step, B->mom, B->n,
+                               B->pairs, B->deps, B->round_offsets, B->info, B->svx, B->svy, B->svz,
+                               nullptr, B->ws, B->ws_bytes, stream);
+      break;
+    default:
+      return dsmc::record(c, DSMC_ERR_ARG, "step: unknown path");
+  }
+  return rc;
 }
 
 int dsmc_step(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t* path,
@@ -428,26 +461,10 @@ int dsmc_step(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t* path,
   rc = dsmc_cell_moments(c, B->n_cells, B->cell_start, B->svx, B->svy, B->svz, B->mom, stream);
   if (rc) return rc;
   rc = dsmc_select_pairs(c, gas, B->n, B->n_cells, B->cell_start, B->svx, B->svy, B->svz,
-                         B->sigma_g_max, step, B->capacity, B->pairs, B->round_offsets, B->info,
+                         B->sigma_g_max, step, B->capacity, B->pairs, B->deps, B->round_offsets, B->info,
                          B->ws, B->ws_bytes, stream);
   if (rc) return rc;
-  switch (path->path) {
-    case DSMC_PATH_VHS:
-      rc = dsmc_collide_vhs(c, gas, step, B->pairs, B->round_offsets, B->info, B->svx, B->svy,
-                            B->svz, stream);
-      break;
-    case DSMC_PATH_JAGER:
-      rc = dsmc_collide_jager(c, gas, path->pot, path->n_nodes, step, B->pairs, B->round_offsets,
-                              B->info, B->svx, B->svy, B->svz, nullptr, stream);
-      break;
-    case DSMC_PATH_NEURAL:
-      rc = dsmc_collide_neural(c, gas, path->mlp, path->weights_bf16, path->biases, step, B->mom,
-                               B->pairs, B->round_offsets, B->info, B->svx, B->svy, B->svz,
-                               nullptr, stream);
-      break;
-    default:
-      return dsmc::record(c, DSMC_ERR_ARG, "step: unknown path");
-  }
+  rc = collide_step(c, gas, path, B, step, stream);
   if (rc) return rc;
   return dsmc_moment_match(c, B->n_cells, B->cell_start, B->mom, B->svx, B->svy, B->svz, stream);
 }
@@ -493,9 +510,10 @@ int dsmc_ctx_reserve(dsmc_ctx_t* c, int32_t n_max, int32_t n_cells, int64_t capa
   if (c->r_mem) { cudaFree(c->r_mem); c->r_mem = nullptr; }
   const size_t n = (size_t)(n_max > 0 ? n_max : 1), nc = (size_t)n_cells;
   const size_t wsb = dsmc_step_workspace_size(n_max, n_cells, capacity);
+  const size_t cap = (size_t)(capacity > 0 ? capacity : 1);
   size_t sizes[] = {4 * n, 8 * n, 8 * n, 8 * n, 4 * n, 4 * (nc + 1), 8 * n, 8 * n, 8 * n,
-                    40 * nc, 8 * nc, 16 * (size_t)(capacity > 0 ? capacity : 1),
-                    4 * (DSMC_MAX_ROUNDS + 1), sizeof(dsmc_select_info_t), 8 * nc, wsb};
+                    40 * nc, 8 * nc, 16 * cap,
+                    4 * (DSMC_MAX_ROUNDS + 1), sizeof(dsmc_select_info_t), 8 * nc, wsb, 4 * cap};
   size_t total = 0;
   for (size_t s : sizes) total += dsmc::align256(s);
   if (cudaSetDevice(c->device) != cudaSuccess || cudaMalloc(&c->r_mem, total) != cudaSuccess)
@@ -503,8 +521,8 @@ int dsmc_ctx_reserve(dsmc_ctx_t* c, int32_t n_max, int32_t n_cells, int64_t capa
   if (!c->r_host_info && cudaMallocHost(&c->r_host_info, 64) != cudaSuccess)
     return dsmc::record(c, DSMC_ERR_CUDA, "reserve: cudaMallocHost failed");
   char* p = (char*)c->r_mem;
-  void* ptr[16];
-  for (int q = 0; q < 16; ++q) { ptr[q] = p; p += dsmc::align256(sizes[q]); }
+  void* ptr[17];
+  for (int q = 0; q < 17; ++q) { ptr[q] = p; p += dsmc::align256(sizes[q]); }
   dsmc_step_buffers_t& b = c->rb;
   b.n = n_max; b.n_cells = n_cells; b.capacity = capacity;
   b.cell_id = (int32_t*)ptr[0]; b.vx = (double*)ptr[1]; b.vy = (double*)ptr[2]; b.vz = (double*)ptr[3];
@@ -514,6 +532,7 @@ int dsmc_ctx_reserve(dsmc_ctx_t* c, int32_t n_max, int32_t n_cells, int64_t capa
   b.round_offsets = (int32_t*)ptr[12]; b.info = (dsmc_select_info_t*)ptr[13];
   c->r_T = (double*)ptr[14];
   b.ws = ptr[15]; b.ws_bytes = wsb;
+  b.deps = (uint32_t*)ptr[16];
   c->r_n = n_max; c->r_cells = n_cells; c->r_cap = capacity; c->r_sg_ready = false;
   return DSMC_OK;
 }
@@ -666,12 +685,13 @@ int dsmc_autotune_step(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t* 
   }, trials, cap, &nt);
   if (!rc && path->path == DSMC_PATH_VHS)
     rc = tune_kernel(c, DSMC_TUNE_COLLIDE_VHS, reps, s, [&] {
-      return dsmc_collide_vhs(c, gas, step, B->pairs, B->round_offsets, B->info, B->svx, B->svy, B->svz, stream);
+      return dsmc_collide_vhs(c, gas, step, B->n, B->pairs, B->deps, B->round_offsets, B->info, B->svx, B->svy,
+                              B->svz, B->ws, B->ws_bytes, stream);
     }, trials, cap, &nt);
   if (!rc && path->path == DSMC_PATH_JAGER)
     rc = tune_kernel(c, DSMC_TUNE_COLLIDE_JAGER, reps, s, [&] {
-      return dsmc_collide_jager(c, gas, path->pot, path->n_nodes, step, B->pairs, B->round_offsets, B->info,
-                                B->svx, B->svy, B->svz, nullptr, stream);
+      return dsmc_collide_jager(c, gas, path->pot, path->n_nodes, step, B->n, B->pairs, B->deps, B->round_offsets,
+                                B->info, B->svx, B->svy, B->svz, nullptr, B->ws, B->ws_bytes, stream);
     }, trials, cap, &nt);
   if (!rc) rc = tune_kernel(c, DSMC_TUNE_MOMENT_MATCH, reps, s, [&] {
     return dsmc::launch_moment_match(c, B->n_cells, B->cell_start, B->mom, B->svx, B->svy, B->svz, s);

@@ -1,10 +1,11 @@
 // VHS isotropic scatter with the centre-of-mass update (Sec. 2.1, 2.3).
 //
-// One persistent cooperative launch walks the rounds of the step: the pairs
-// of a round are disjoint, so its threads update them independently; a
-// bounded grid barrier separates rounds.  Velocities are read and written
-// through L2 (ld/st .cg) so that a round sees the previous round's writes
-// from other SMs.
+// One persistent launch walks the pairs of the step in round-major order:
+// each warp claims 32 pairs of one round at a time from a global cursor and
+// each lane waits (bounded) until the previous pairs of its two particles
+// are done, then updates its pair and stamps both particles done.  The
+// pairs of a round are disjoint, so no two lanes of a unit touch the same
+// particle.  Velocities are read and written through L2 (ld/st .cg).
 #include "internal.cuh"
 
 namespace dsmc {
@@ -13,36 +14,50 @@ struct VhsArgs {
   uint64_t seed, step;
   const uint64_t* step_dev;
   const int4* pairs;
+  const uint32_t* deps;
   const int32_t* ro;
   const dsmc_select_info_t* info;
   double *vx, *vy, *vz;
-  unsigned* bar;
+  unsigned* done;
+  unsigned* bar;   // [2] abort word, [3] unit cursor
   int* status;
 };
 
 __global__ void __launch_bounds__(256) k_collide_vhs(VhsArgs a) {
   if (a.step_dev) a.step = *a.step_dev;
   const int R = a.info->n_rounds;
-  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-  for (int r = 0; r < R; ++r) {
-    const int32_t beg = a.ro[r], end = a.ro[r + 1];
-    for (int64_t p = beg + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < end; p += nthr) {
+  const int lane = threadIdx.x & 31;
+  int r = 0;
+  int64_t base = 0;
+  for (;;) {
+    unsigned unit = 0;
+    if (lane == 0) unit = atomicAdd(a.bar + 3, 1u);
+    unit = __shfl_sync(0xffffffffu, unit, 0);
+    int32_t p0, p1;
+    if (!unit_range(a.ro, R, 32, r, base, unit, &p0, &p1)) break;
+    const int32_t p = p0 + lane;
+    bool ok = true;
+    if (p < p1) {
       const int4 q = a.pairs[p];
-      const double xi = __ldcg(a.vx + q.x), yi = __ldcg(a.vy + q.x), zi = __ldcg(a.vz + q.x);
-      const double xj = __ldcg(a.vx + q.y), yj = __ldcg(a.vy + q.y), zj = __ldcg(a.vz + q.y);
-      const double dx = xi - xj, dy = yi - yj, dz = zi - zj;
-      const double g = sqrt(dx * dx + dy * dy + dz * dz);
-      const u32x4 w = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_ISO);
-      const double c = 2.0 * u53(w.x, w.y) - 1.0;
-      const double s = sqrt(1.0 - c * c);
-      double se, ce;
-      sincos(2.0 * DSMC_PI * u53(w.z, w.w), &se, &ce);
-      const double rx = g * c, ry = g * s * ce, rz = g * s * se;
-      const double cx = 0.5 * (xi + xj), cy = 0.5 * (yi + yj), cz = 0.5 * (zi + zj);
-      __stcg(a.vx + q.x, cx + 0.5 * rx); __stcg(a.vy + q.x, cy + 0.5 * ry); __stcg(a.vz + q.x, cz + 0.5 * rz);
-      __stcg(a.vx + q.y, cx - 0.5 * rx); __stcg(a.vy + q.y, cy - 0.5 * ry); __stcg(a.vz + q.y, cz - 0.5 * rz);
+      ok = wait_deps(a.done, q.x, q.y, a.deps[p], a.bar + 2, a.status);
+      if (ok) {
+        const double xi = __ldcg(a.vx + q.x), yi = __ldcg(a.vy + q.x), zi = __ldcg(a.vz + q.x);
+        const double xj = __ldcg(a.vx + q.y), yj = __ldcg(a.vy + q.y), zj = __ldcg(a.vz + q.y);
+        const double dx = xi - xj, dy = yi - yj, dz = zi - zj;
+        const double g = sqrt(dx * dx + dy * dy + dz * dz);
+        const u32x4 w = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_ISO);
+        const double c = 2.0 * u53(w.x, w.y) - 1.0;
+        const double s = sqrt(1.0 - c * c);
+        double se, ce;
+        sincos(2.0 * DSMC_PI * u53(w.z, w.w), &se, &ce);
+        const double rx = g * c, ry = g * s * ce, rz = g * s * se;
+        const double cx = 0.5 * (xi + xj), cy = 0.5 * (yi + yj), cz = 0.5 * (zi + zj);
+        __stcg(a.vx + q.x, cx + 0.5 * rx); __stcg(a.vy + q.x, cy + 0.5 * ry); __stcg(a.vz + q.x, cz + 0.5 * rz);
+        __stcg(a.vx + q.y, cx - 0.5 * rx); __stcg(a.vy + q.y, cy - 0.5 * ry); __stcg(a.vz + q.y, cz - 0.5 * rz);
+        release_pair(a.done, q.x, q.y, (unsigned)(r + 1));
+      }
     }
-    if (r + 1 < R && !grid_barrier(a.bar, a.status, kBarrierLimitNs)) return;
+    if (!__all_sync(0xffffffffu, ok)) break;
   }
 }
 
@@ -62,21 +77,24 @@ int occupancy_collide_vhs(int threads) {
   return per_sm;
 }
 
-int launch_collide_vhs(Ctx* c, const dsmc_gas_t& gas, uint64_t step, const int32_t* pairs,
-                       const int32_t* ro, const dsmc_select_info_t* info, double* vx,
-                       double* vy, double* vz, cudaStream_t s) {
+size_t collide_ws(int32_t n) { return align256(sizeof(unsigned) * (size_t)(n > 0 ? n : 1)); }
+
+int launch_collide_vhs(Ctx* c, const dsmc_gas_t& gas, uint64_t step, int32_t n, const int32_t* pairs,
+                       const uint32_t* deps, const int32_t* ro, const dsmc_select_info_t* info, double* vx,
+                       double* vy, double* vz, void* ws, size_t ws_bytes, cudaStream_t s) {
+  if (ws_bytes < collide_ws(n)) return record(c, DSMC_ERR_ARG, "collide_vhs: workspace too small");
   const Shape sh = shape_or_default(c, DSMC_TUNE_COLLIDE_VHS);
   const int occ = occupancy_collide_vhs(sh.threads);
   if (occ < 1) return record(c, DSMC_ERR_CUDA, "collide_vhs: occupancy query failed");
   const int blocks = sm_count(c) * (sh.blocks_per_sm > 0 && sh.blocks_per_sm < occ ? sh.blocks_per_sm : occ);
-  VhsArgs a{gas.seed, step, graph_step_ptr(c), (const int4*)pairs, ro, info, vx, vy, vz, barrier_ptr(c), status_ptr(c)};
-  if (cudaMemsetAsync(a.bar, 0, 4 * sizeof(unsigned), s) != cudaSuccess) return DSMC_ERR_CUDA;
-  void* args[] = {&a};
-  if (cudaLaunchCooperativeKernel((const void*)k_collide_vhs, dim3(blocks), dim3(sh.threads), args, 0, s) !=
-      cudaSuccess)
-    return record(c, DSMC_ERR_CUDA, "collide_vhs: cooperative launch failed");
+  VhsArgs a{gas.seed, step, graph_step_ptr(c), (const int4*)pairs, deps, ro, info, vx, vy, vz,
+            (unsigned*)ws, barrier_ptr(c), status_ptr(c)};
+  if (cudaMemsetAsync(a.bar, 0, 4 * sizeof(unsigned), s) != cudaSuccess ||
+      cudaMemsetAsync(a.done, 0, sizeof(unsigned) * (size_t)(n > 0 ? n : 1), s) != cudaSuccess)
+    return DSMC_ERR_CUDA;
+  k_collide_vhs<<<blocks, sh.threads, 0, s>>>(a);
   count_launches(c, 1);
-  return 0;
+  return cudaGetLastError() == cudaSuccess ? 0 : record(c, DSMC_ERR_CUDA, "collide_vhs: launch failed");
 }
 
 // Failure-detection self test: every block but block 0 enters the grid
@@ -87,7 +105,20 @@ __global__ void k_selftest_barrier(unsigned* bar, int* status, uint64_t limit_ns
   grid_barrier(bar, status, limit_ns);
 }
 
-int launch_selftest_timeout(Ctx* c, int which, uint64_t limit_ns, cudaStream_t s);
+// Failure-detection self test of the pair-dependency wait: one thread waits
+// for a done stamp that nothing ever sets (word 0 of the zeroed barrier
+// words); the bounded wait must record DSMC_ERR_TIMEOUT and return.
+__global__ void k_selftest_deps(unsigned* bar, int* status, uint64_t limit_ns) {
+  if (threadIdx.x == 0) wait_deps(bar, 0, 0, 1u, bar + 2, status, limit_ns);
+}
+
+int launch_selftest_deps(Ctx* c, uint64_t limit_ns, cudaStream_t s) {
+  unsigned* bar = barrier_ptr(c);
+  if (cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), s) != cudaSuccess) return DSMC_ERR_CUDA;
+  k_selftest_deps<<<1, 32, 0, s>>>(bar, status_ptr(c), limit_ns);
+  count_launches(c, 1);
+  return cudaGetLastError() == cudaSuccess ? 0 : record(c, DSMC_ERR_CUDA, "selftest_deps: launch failed");
+}
 
 int launch_selftest_barrier(Ctx* c, uint64_t limit_ns, cudaStream_t s) {
   if (cudaMemsetAsync(barrier_ptr(c), 0, 4 * sizeof(unsigned), s) != cudaSuccess) return DSMC_ERR_CUDA;

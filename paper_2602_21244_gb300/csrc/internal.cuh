@@ -120,6 +120,80 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* status, uint64_
 
 constexpr uint64_t kBarrierLimitNs = 2000000000ull;  // 2 s
 
+// ---------------------------------------------------------------- pair dependencies
+// The collide kernels walk the pairs of a step in round-major order without
+// grid-wide barriers.  Work units (a warp's 32 pairs, a 128-pair MLP tile)
+// never span two rounds and are claimed in order from one global cursor; a
+// pair starts once the previous pairs of its two particles are done.
+// done[i] is the 1-based round of the last completed pair of particle i
+// (zeroed before the launch); a pair's deps word holds the 1-based rounds of
+// the previous pairs of its particles (low / high 16 bits, 0 = none), all
+// below its own round.  A wait only ever points at pairs of units claimed
+// earlier, so the earliest unfinished unit always has its inputs done: the
+// scheme cannot deadlock, and every wait is bounded besides.
+
+// Map claimed unit `unit` to its pair range [*p0, *p1) and round *r.  (r,
+// base) is the caller's running position: round r starts at unit `base`;
+// units are claimed in increasing order, so it only moves forward.  False
+// once past the last round.
+__device__ __forceinline__ bool unit_range(const int32_t* __restrict__ ro, int R, int usize, int& r,
+                                           int64_t& base, int64_t unit, int32_t* p0, int32_t* p1) {
+  while (r < R) {
+    const int32_t b = ro[r], e = ro[r + 1];
+    const int64_t nu = (e - b + usize - 1) / usize;
+    if (unit < base + nu) {
+      *p0 = b + (int32_t)((unit - base) * usize);
+      *p1 = min(e, *p0 + usize);
+      return true;
+    }
+    base += nu;
+    ++r;
+  }
+  return false;
+}
+
+// Release / acquire at GPU scope (PTX memory model): a relaxed load of a
+// stamp followed by fence.acq_rel is an acquire; fence.acq_rel followed by
+// a relaxed store of the stamp is a release.  Lighter than fence.sc.
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(unsigned* p, unsigned v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+// Wait until the previous pairs of particles i and j are done (bounded; on
+// timeout, or once another thread has aborted, records DSMC_ERR_TIMEOUT,
+// raises the abort word and returns false).
+__device__ __forceinline__ bool wait_deps(const unsigned* done, int32_t i, int32_t j, uint32_t dep,
+                                          unsigned* abort_word, int* status,
+                                          uint64_t limit_ns = kBarrierLimitNs) {
+  const unsigned ni = dep & 0xFFFFu, nj = dep >> 16;
+  if (ni == 0 && nj == 0) return true;
+  if (ld_relaxed(done + i) >= ni && ld_relaxed(done + j) >= nj) { fence_acq_rel(); return true; }
+  const uint64_t t0 = globaltimer_ns();
+  for (;;) {
+    __nanosleep(32);
+    if (ld_relaxed(done + i) >= ni && ld_relaxed(done + j) >= nj) { fence_acq_rel(); return true; }
+    if (ld_relaxed(abort_word) || globaltimer_ns() - t0 > limit_ns) {
+      set_status(status, DSMC_ERR_TIMEOUT);
+      atomicExch(abort_word, 1u);
+      return false;
+    }
+  }
+}
+
+// Publish that the pair of particles i and j (1-based round `round1`) is
+// done: its velocity stores become visible before the stamps.
+__device__ __forceinline__ void release_pair(unsigned* done, int32_t i, int32_t j, unsigned round1) {
+  fence_acq_rel();
+  st_relaxed(done + i, round1);
+  st_relaxed(done + j, round1);
+}
+
 // ---------------------------------------------------------------- host side
 struct Ctx;
 int record(Ctx* c, int code, const char* msg);  // sets last error text, returns code
@@ -144,28 +218,30 @@ int launch_moment_match(Ctx* c, int32_t n_cells, const int32_t* cs, const double
 size_t select_ws(int32_t n, int32_t n_cells, int64_t capacity);
 int launch_select(Ctx* c, const dsmc_gas_t& gas, int32_t n, int32_t n_cells, const int32_t* cs,
                   const double* vx, const double* vy, const double* vz, double* sgmax,
-                  uint64_t step, int64_t capacity, int32_t* pairs, int32_t* round_offsets,
+                  uint64_t step, int64_t capacity, int32_t* pairs, uint32_t* deps, int32_t* round_offsets,
                   dsmc_select_info_t* info, void* ws, size_t ws_bytes, cudaStream_t s);
 int launch_sgmax_init(Ctx* c, const dsmc_gas_t& gas, int32_t n_cells, const double* T,
                       double factor, double* sgmax, cudaStream_t s);
-int launch_collide_vhs(Ctx* c, const dsmc_gas_t& gas, uint64_t step, const int32_t* pairs,
-                       const int32_t* ro, const dsmc_select_info_t* info, double* vx,
-                       double* vy, double* vz, cudaStream_t s);
+// per-particle done stamps of the collide kernels
+size_t collide_ws(int32_t n);
+int launch_collide_vhs(Ctx* c, const dsmc_gas_t& gas, uint64_t step, int32_t n, const int32_t* pairs,
+                       const uint32_t* deps, const int32_t* ro, const dsmc_select_info_t* info, double* vx,
+                       double* vy, double* vz, void* ws, size_t ws_bytes, cudaStream_t s);
 int launch_jager_chi(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& pot, int n_nodes,
                      int64_t n, const float* b, const float* g, float* chi, cudaStream_t s);
 int launch_collide_jager(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& pot,
-                         int n_nodes, uint64_t step, const int32_t* pairs, const int32_t* ro,
-                         const dsmc_select_info_t* info, double* vx, double* vy, double* vz,
-                         float* chi_out, cudaStream_t s);
+                         int n_nodes, uint64_t step, int32_t n, const int32_t* pairs, const uint32_t* deps,
+                         const int32_t* ro, const dsmc_select_info_t* info, double* vx, double* vy,
+                         double* vz, float* chi_out, void* ws, size_t ws_bytes, cudaStream_t s);
 int launch_harvest_jager(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& pot,
                          int n_nodes, int64_t n, const double* vi, const double* vj,
                          const double* b, const double* eps, double* vio, double* vjo,
                          cudaStream_t s);
 int launch_collide_neural(Ctx* c, const dsmc_gas_t& gas, const dsmc_mlp_t& mlp,
                           const uint16_t* w, const float* bias, uint64_t step,
-                          const double* mom, const int32_t* pairs, const int32_t* ro,
-                          const dsmc_select_info_t* info, double* vx, double* vy, double* vz,
-                          float* u_out, cudaStream_t s);
+                          const double* mom, int32_t n, const int32_t* pairs, const uint32_t* deps,
+                          const int32_t* ro, const dsmc_select_info_t* info, double* vx, double* vy,
+                          double* vz, float* u_out, void* ws, size_t ws_bytes, cudaStream_t s);
 
 int launch_mlp_forward(Ctx* c, const dsmc_mlp_t& mlp, const uint16_t* w, const float* bias,
                        int64_t n, const float* x, float* y, cudaStream_t s);
@@ -201,6 +277,7 @@ int launch_gather(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_start,
                   const double* vx, const double* vy, const double* vz, double* svx, double* svy,
                   double* svz, cudaStream_t s);
 int launch_selftest_barrier(Ctx* c, uint64_t limit_ns, cudaStream_t s);
+int launch_selftest_deps(Ctx* c, uint64_t limit_ns, cudaStream_t s);
 int launch_selftest_mbar(Ctx* c, uint64_t limit_ns, cudaStream_t s);
 
 size_t train_ws(int sms);

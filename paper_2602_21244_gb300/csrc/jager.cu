@@ -36,7 +36,9 @@ struct PotDev {
   float fA, fa1, fa2, fam1, fam2, fbeta, fC[6], frc, fAt, fat;
   double Dd[17];      // FP64 copy of D
   double Dp[16];      // (p + 1) D_{p+1}: P'(r) = -r^-2 sum_p Dp_p r^-p
+  double Dpp[16];     // (p + 1)(p + 2) D_{p+1}: P''(r) = r^-3 sum_p Dpp_p r^-p
   double Cd[6];       // (6 + 2n) C_n
+  double Cdd[6];      // (6 + 2n)(7 + 2n) C_n
   float D[17];        // P(r) = sum_p D_p r^-p,  e^{-beta r} P(r) = sum_n C_2n r^-2n e^{-x} S_2n(x)
   float sigma0;       // zero crossing of V (F > 0 above max(b, sigma0))
   float orbit_E;      // below this energy use the fine bracket scan
@@ -86,6 +88,51 @@ __host__ __device__ inline double V64(const PotDev& P, double r, double* dV, dou
   if (rep_out) *rep_out = rep;
   if (ex_out) *ex_out = ex;
   *dV = drep - dq + ex * (dPr - P.beta * Pr);
+  return rep - q + ex * Pr;
+}
+
+// V, V' and V'' in FP64 at r (ir = 1/r given), the same expansion as V64;
+// *rep, *ex receive A e^{poly} and e^{-beta r} (Jager form).
+__host__ __device__ inline double V64_d2(const PotDev& P, double r, double ir, double* dV, double* d2V,
+                                         double* rep_out, double* ex_out) {
+  const double ir2 = ir * ir;
+  if (P.kind == 2) {
+    const double v = P.kappa * pow(r, -P.p);
+    *dV = -P.p * v * ir;
+    *d2V = P.p * (P.p + 1.0) * v * ir2;
+    return v;
+  }
+  if (r < P.rc) {
+    const double e = P.At * exp(-P.at * r) * ir, k = P.at + ir;
+    *dV = -e * k;
+    *d2V = e * (k * k + ir2);
+    return e;
+  }
+  const double rep = P.A * exp(P.a1 * r + P.a2 * r * r + P.am1 * ir + P.am2 * ir2);
+  const double pp = P.a1 + 2.0 * P.a2 * r - P.am1 * ir2 - 2.0 * P.am2 * ir2 * ir;   // poly'
+  const double ppp = 2.0 * P.a2 + 2.0 * P.am1 * ir2 * ir + 6.0 * P.am2 * ir2 * ir2;  // poly''
+  double q = 0.0, dq = 0.0, d2q = 0.0, pw = ir2 * ir2 * ir2;
+#pragma unroll
+  for (int n = 0; n < 6; ++n) {
+    q = fma(P.C[n], pw, q);
+    dq = fma(P.Cd[n], pw, dq);
+    d2q = fma(P.Cdd[n], pw, d2q);
+    pw *= ir2;
+  }
+  dq *= -ir;
+  d2q *= ir2;
+  double Pr = P.Dd[16], dPr = P.Dp[15], d2Pr = P.Dpp[15];
+#pragma unroll
+  for (int k = 15; k >= 0; --k) Pr = fma(Pr, ir, P.Dd[k]);
+#pragma unroll
+  for (int k = 14; k >= 0; --k) { dPr = fma(dPr, ir, P.Dp[k]); d2Pr = fma(d2Pr, ir, P.Dpp[k]); }
+  dPr *= -ir2;
+  d2Pr *= ir2 * ir;
+  const double ex = exp(-P.beta * r);
+  *rep_out = rep;
+  *ex_out = ex;
+  *dV = rep * pp - dq + ex * (dPr - P.beta * Pr);
+  *d2V = rep * (pp * pp + ppp) - d2q + ex * (d2Pr - P.beta * (2.0 * dPr - P.beta * Pr));
   return rep - q + ex * Pr;
 }
 
@@ -170,20 +217,41 @@ __device__ double rmin_device(const PotDev& P, float b, float E, double* rep = n
     if (fabsf(rn - r) <= 4e-7f * r) { if (inside) r = rn; break; }
     r = inside ? rn : 0.5f * (r_lo + r_hi);
   }
-  // FP64 Newton refinement of the turning point, kept inside the FP32
-  // bracket widened by 1e-4 (FP32 rounding can misplace its ends slightly)
+  // FP64 Halley refinement of the turning point (cubic convergence: from the
+  // FP32 root, relative error ~1e-7, one step leaves ~1e-20 times the
+  // curvature constant), kept inside the FP32 bracket widened by 1e-4 (FP32
+  // rounding can misplace its ends slightly).  A step above 1e-6 r (the FP32
+  // stage ended away from the root) is followed by more steps.  The
+  // exponentials of the last evaluation are carried to the returned point
+  // by their Taylor series in the step (|beta dr|, |dpoly| < 1e-5).
   double rd = r;
   const double lo = (double)r_lo * (1.0 - 1e-4), hi = (double)r_hi * (1.0 + 1e-4);
   const double bd2 = (double)b * b, iEd = 1.0 / (double)E;
+  double rep0 = 0.0, ex0 = 0.0, dpoly = 0.0, dr = 0.0;
   for (int it = 0; it < 4; ++it) {
-    double dV;
-    const double ir = 1.0 / rd;
-    const double V = V64(P, rd, &dV, rep, ex);
-    const double f = 1.0 - bd2 * ir * ir - V * iEd;
-    const double df = 2.0 * bd2 * ir * ir * ir - dV * iEd;
-    const double rn = rd - f / df;
-    if (!(rn >= lo && rn <= hi) || fabs(rn - rd) <= 1e-12 * rd) break;
+    double dV, d2V;
+    const double ir = 1.0 / rd, ir2 = ir * ir;
+    const double V = V64_d2(P, rd, ir, &dV, &d2V, &rep0, &ex0);
+    const double f = 1.0 - bd2 * ir2 - V * iEd;
+    const double df = 2.0 * bd2 * ir2 * ir - dV * iEd;
+    const double d2f = -6.0 * bd2 * ir2 * ir2 - d2V * iEd;
+    const double step = -2.0 * f * df / (2.0 * df * df - f * d2f);
+    const double rn = rd + step;
+    if (!(rn >= lo && rn <= hi)) { dr = 0.0; break; }
+    dr = step;
+    dpoly = step * (P.a1 + 2.0 * P.a2 * rd - P.am1 * ir2 - 2.0 * P.am2 * ir2 * ir);
     rd = rn;
+    if (fabs(step) <= 1e-6 * rd) break;
+  }
+  if (rep) {
+    if (fabs(dr) <= 1e-4 * rd) {
+      const double eb = -P.beta * dr;
+      *rep = rep0 * (1.0 + dpoly * (1.0 + 0.5 * dpoly));
+      *ex = ex0 * (1.0 + eb * (1.0 + 0.5 * eb));
+    } else {  // a long last step (not converged): evaluate at rd
+      double dV;
+      V64(P, rd, &dV, rep, ex);
+    }
   }
   return rd;
 }
@@ -194,7 +262,8 @@ __device__ float chi_device(const PotDev& P, float b, float E) {
   double rep_d = 0.0, ex_d = 0.0;
   const double rd = rmin_device(P, b, E, &rep_d, &ex_d);
   const float r0 = (float)rd;
-  const float bt = (float)((double)b / rd);
+  const double ird = 1.0 / rd;
+  const float bt = (float)((double)b * ird);
   const float bt2 = bt * bt;
   const float iE = 1.f / E;
   float F0 = 0.f;
@@ -204,7 +273,7 @@ __device__ float chi_device(const PotDev& P, float b, float E) {
   float d[17], qn[6], Rep0 = 0.f, e0 = 0.f, P0 = 0.f, Vc0 = 0.f, powk = 0.f;
   const bool core = P.kind == 0 && r0 < P.frc;
   if (P.kind == 0 && !core) {
-    const double ir = 1.0 / rd, ir2 = ir * ir;
+    const double ir = ird, ir2 = ir * ir;
     double pw = 1.0, p0 = 0.0;
 #pragma unroll
     for (int p = 0; p <= 16; ++p) { const double t = P.Dd[p] * pw; d[p] = (float)t; p0 += t; pw *= ir; }
@@ -312,7 +381,9 @@ static PotDev make_pot(const dsmc_gas_t& gas, const dsmc_potential_t& p, int n_n
     P.Dd[pp] = s;
   }
   for (int pp = 0; pp < 16; ++pp) P.Dp[pp] = (pp + 1) * P.Dd[pp + 1];
+  for (int pp = 0; pp < 16; ++pp) P.Dpp[pp] = (double)(pp + 1) * (pp + 2) * P.Dd[pp + 1];
   for (int q = 0; q < 6; ++q) P.Cd[q] = (6 + 2 * q) * p.C[q];
+  for (int q = 0; q < 6; ++q) P.Cdd[q] = (double)(6 + 2 * q) * (7 + 2 * q) * p.C[q];
   if (p.kind == 0) {
     // sigma0: outermost zero of V (bisection on a sign change found inward from 4 R_eps)
     double dv, hi = 4.0 * p.R_eps, lo = hi;
@@ -381,18 +452,19 @@ struct JagerArgs {
   const uint64_t* step_dev;
   double bmax_A;
   const int4* pairs;
+  const uint32_t* deps;
   const int32_t* ro;
   const dsmc_select_info_t* info;
   double *vx, *vy, *vz;
   float* chi_out;
-  unsigned* bar;
+  unsigned* done;
+  unsigned* bar;   // [2] abort word, [3] unit cursor
   int* status;
 };
 
 // One pair: chi(b, E) for its impact parameter and energy, rotation of v_r
 // (Bird 1994, Eq. 2.22), centre-of-mass update; velocities through L2.
-__device__ __forceinline__ void collide_pair(const PotDev& P, const JagerArgs& a, int64_t p) {
-  const int4 q = a.pairs[p];
+__device__ __forceinline__ void collide_pair(const PotDev& P, const JagerArgs& a, int64_t p, int4 q) {
   const double xi = __ldcg(a.vx + q.x), yi = __ldcg(a.vy + q.x), zi = __ldcg(a.vz + q.x);
   const double xj = __ldcg(a.vx + q.y), yj = __ldcg(a.vy + q.y), zj = __ldcg(a.vz + q.y);
   const double ux = xi - xj, uy = yi - yj, uz = zi - zj;
@@ -415,28 +487,36 @@ __device__ __forceinline__ void collide_pair(const PotDev& P, const JagerArgs& a
   __stcg(a.vx + q.y, cx - 0.5 * o[0]); __stcg(a.vy + q.y, cy - 0.5 * o[1]); __stcg(a.vz + q.y, cz - 0.5 * o[2]);
 }
 
-// Pairs of a round are claimed dynamically, 32 at a time per warp, from the
-// cursor in bar[3] (reset by the grid barrier between rounds): the cost of a
-// pair varies by an order of magnitude (bracket scan, Newton iterations), and
-// a static split leaves most warps waiting at the barrier for the slowest.
-// Which thread handles a pair does not change its result.
-__global__ void __launch_bounds__(128) k_collide_jager(PotDev P, JagerArgs a) {
+// Pairs are claimed 32 at a time per warp, in round-major order, from one
+// global cursor (units never span two rounds); each lane waits (bounded)
+// until the previous pairs of its two particles are done, updates its pair
+// and stamps both particles.  The cost of a pair varies by an order of
+// magnitude (bracket scan, Newton iterations), so no warp waits for a round
+// to end: only true dependencies order the work.  Which thread handles a
+// pair does not change its result.
+__global__ void __launch_bounds__(128, 4) k_collide_jager(PotDev P, JagerArgs a) {
   if (a.step_dev) a.step = *a.step_dev;
   const int R = a.info->n_rounds;
   const int lane = threadIdx.x & 31;
-  unsigned* cursor = a.bar + 3;
-  for (int r = 0; r < R; ++r) {
-    const int32_t beg = a.ro[r], end = a.ro[r + 1];
-    const unsigned n_r = (unsigned)(end - beg);
-    for (;;) {
-      unsigned base = 0;
-      if (lane == 0) base = atomicAdd(cursor, 32u);
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (base >= n_r) break;
-      const int64_t p = (int64_t)beg + base + lane;
-      if (p < end) collide_pair(P, a, p);
+  int r = 0;
+  int64_t base = 0;
+  for (;;) {
+    unsigned unit = 0;
+    if (lane == 0) unit = atomicAdd(a.bar + 3, 1u);
+    unit = __shfl_sync(0xffffffffu, unit, 0);
+    int32_t p0, p1;
+    if (!unit_range(a.ro, R, 32, r, base, unit, &p0, &p1)) break;
+    const int32_t p = p0 + lane;
+    bool ok = true;
+    if (p < p1) {
+      const int4 q = a.pairs[p];
+      ok = wait_deps(a.done, q.x, q.y, a.deps[p], a.bar + 2, a.status);
+      if (ok) {
+        collide_pair(P, a, p, q);
+        release_pair(a.done, q.x, q.y, (unsigned)(r + 1));
+      }
     }
-    if (r + 1 < R && !grid_barrier(a.bar, a.status, kBarrierLimitNs)) return;
+    if (!__all_sync(0xffffffffu, ok)) break;
   }
 }
 
@@ -493,23 +573,23 @@ int occupancy_collide_jager(int threads) {
 }
 
 int launch_collide_jager(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& pot,
-                         int n_nodes, uint64_t step, const int32_t* pairs, const int32_t* ro,
-                         const dsmc_select_info_t* info, double* vx, double* vy, double* vz,
-                         float* chi_out, cudaStream_t s) {
+                         int n_nodes, uint64_t step, int32_t n, const int32_t* pairs, const uint32_t* deps,
+                         const int32_t* ro, const dsmc_select_info_t* info, double* vx, double* vy,
+                         double* vz, float* chi_out, void* ws, size_t ws_bytes, cudaStream_t s) {
+  if (ws_bytes < collide_ws(n)) return record(c, DSMC_ERR_ARG, "collide_jager: workspace too small");
   const Shape sh = shape_or_default(c, DSMC_TUNE_COLLIDE_JAGER);
   const int occ = occupancy_collide_jager(sh.threads);
   if (occ < 1) return record(c, DSMC_ERR_CUDA, "collide_jager: occupancy query failed");
   const int blocks = sm_count(c) * (sh.blocks_per_sm > 0 && sh.blocks_per_sm < occ ? sh.blocks_per_sm : occ);
   PotDev P = make_pot(gas, pot, n_nodes);
-  JagerArgs a{gas.seed, step, graph_step_ptr(c), gas.b_max * 1e10, (const int4*)pairs, ro, info, vx, vy, vz,
-              chi_out, barrier_ptr(c), status_ptr(c)};
-  if (cudaMemsetAsync(a.bar, 0, 4 * sizeof(unsigned), s) != cudaSuccess) return DSMC_ERR_CUDA;
-  void* args[] = {&P, &a};
-  if (cudaLaunchCooperativeKernel((const void*)k_collide_jager, dim3(blocks), dim3(sh.threads), args, 0, s) !=
-      cudaSuccess)
-    return record(c, DSMC_ERR_CUDA, "collide_jager: cooperative launch failed");
+  JagerArgs a{gas.seed, step, graph_step_ptr(c), gas.b_max * 1e10, (const int4*)pairs, deps, ro, info, vx, vy, vz,
+              chi_out, (unsigned*)ws, barrier_ptr(c), status_ptr(c)};
+  if (cudaMemsetAsync(a.bar, 0, 4 * sizeof(unsigned), s) != cudaSuccess ||
+      cudaMemsetAsync(a.done, 0, sizeof(unsigned) * (size_t)(n > 0 ? n : 1), s) != cudaSuccess)
+    return DSMC_ERR_CUDA;
+  k_collide_jager<<<blocks, sh.threads, 0, s>>>(P, a);
   count_launches(c, 1);
-  return 0;
+  return cudaGetLastError() == cudaSuccess ? 0 : record(c, DSMC_ERR_CUDA, "collide_jager: launch failed");
 }
 
 int launch_harvest_jager(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& pot,

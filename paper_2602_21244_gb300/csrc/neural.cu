@@ -35,12 +35,13 @@ constexpr int kWidth = 128;
 constexpr int kKin = 32;         // input as two bf16 terms: [hi (16) | lo (16)]
 constexpr int kNout = 16;        // padded output width
 constexpr int kMaxHidden = 4;
+constexpr int kStashCols = 16;   // per-row pair data handed from builder to updater threads
 
 // dynamic shared memory layout (bytes).  The weights are shared; each of the
 // `slots` tile slots (one per warp group) has its own X, activation tiles,
 // mbarrier and flag.
 struct MlpLayout {
-  uint32_t w_out, w_in, w_sq, slot0, slot_bytes, bias, mbar, tptr, flag, total;
+  uint32_t w_out, w_in, w_sq, slot0, slot_bytes, bias, mbar, tptr, flag, claim, fail, total;
   int slots;
   __host__ __device__ uint32_t x(int g) const { return slot0 + (uint32_t)g * slot_bytes; }
   __host__ __device__ uint32_t h(int g) const { return x(g) + kTileM * kKin * 2; }
@@ -61,8 +62,10 @@ __host__ __device__ inline MlpLayout mlp_layout(int n_hidden, int slots) {
   L.mbar = L.bias + (uint32_t)(n_hidden * kWidth + kNout) * 4;
   L.mbar = (L.mbar + 15u) & ~15u;                     // slots x 8 bytes
   L.tptr = L.mbar + 16;
-  L.flag = L.tptr + 4;                                // slots x 4 bytes
-  L.total = L.flag + 8 + 2048;  // slack after the last operand tile
+  L.flag = L.tptr + 4;                                // slots x 4 bytes: mbarrier wait result
+  L.claim = L.flag + 8;                               // slots x 4 bytes: next claimed unit
+  L.fail = L.claim + 8;                               // slots x 4 bytes: a dependency wait failed
+  L.total = L.fail + 8 + 2048;  // slack after the last operand tile
   return L;
 }
 
@@ -111,6 +114,31 @@ __device__ void load_weights(char* smem, const MlpLayout& L, const MlpShape& sh,
 __device__ __forceinline__ float act_f(int act, float z) {
   if (act == 1) return fmaxf(z, 0.f);
   return __fdividef(z, 1.f + __expf(-z));   // SiLU(z) = z / (1 + e^-z)
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// SiLU of four values with one reciprocal: d_k = 1 + e^{-z_k} (z_k clamped
+// below at -20, where SiLU is below 5e-8 in magnitude, so that the product
+// of the four d_k stays finite), r = 1/(d0 d1 d2 d3), 1/d0 = d1 (d2 d3 r) and
+// so on.  The special-function unit, which bounds the activation epilogue,
+// does 1.25 operations per value instead of 2; the extra multiplications
+// cost a few FP32 roundings.
+__device__ __forceinline__ void silu4(float* z) {
+  float d[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) d[k] = 1.f + __expf(-fmaxf(z[k], -20.f));
+  const float d01 = d[0] * d[1], d23 = d[2] * d[3];
+  const float r = rcp_approx(d01 * d23);
+  const float r01 = r * d23, r23 = r * d01;   // 1/(d0 d1), 1/(d2 d3)
+  z[0] *= d[1] * r01;
+  z[1] *= d[0] * r01;
+  z[2] *= d[3] * r23;
+  z[3] *= d[2] * r23;
 }
 
 // The warp group a thread belongs to: G groups of blockDim/G threads, group g
@@ -182,11 +210,19 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
       for (int c0 = cg * cols; c0 < (cg + 1) * cols; c0 += 32) {
         float v[32];
         tc::ld32(lane_tm + (uint32_t)c0, v);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] += bl[c0 + k];
+        if (sh.act == 0) {
+#pragma unroll
+          for (int k = 0; k < 32; k += 4) silu4(v + k);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 32; ++k) v[k] = act_f(sh.act, v[k]);
+        }
         uint32_t pk[16], lo[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-          const float a0 = act_f(sh.act, v[2 * k] + bl[c0 + 2 * k]);
-          const float a1 = act_f(sh.act, v[2 * k + 1] + bl[c0 + 2 * k + 1]);
+          const float a0 = v[2 * k], a1 = v[2 * k + 1];
           pk[k] = tc::pack_bf16x2(a0, a1);
           lo[k] = tc::pack_bf16x2(a0 - __uint_as_float(pk[k] << 16), a1 - __uint_as_float(pk[k] & 0xFFFF0000u));
         }
@@ -236,7 +272,8 @@ __device__ __forceinline__ void write_x_row(char* smem, const MlpLayout& L, int 
 
 // CTA prologue/epilogue: TMEM allocation by warp 0 (128 columns per tile
 // slot), one mbarrier per slot.
-__device__ __forceinline__ uint32_t tmem_cols(int slots) { return slots > 1 ? 256u : 128u; }
+// accumulators (128 per slot) then two stashes of 16 columns per slot
+__device__ __forceinline__ uint32_t tmem_cols(int slots) { return slots > 1 ? 512u : 256u; }
 
 __device__ __forceinline__ uint32_t cta_setup(char* smem, const MlpLayout& L) {
   if (threadIdx.x < 32) {
@@ -367,10 +404,12 @@ struct NeuralArgs {
   const double* mom;
   float* u_out;
   const int4* pairs;
+  const uint32_t* deps;
   const int32_t* ro;
   const dsmc_select_info_t* info;
   double *vx, *vy, *vz;
-  unsigned* bar;
+  unsigned* done;
+  unsigned* bar;   // [2] abort word, [3] unit cursor
   int* status;
 };
 
@@ -386,6 +425,113 @@ __device__ __forceinline__ void box_muller_f(uint32_t w1, uint32_t w2, float* z0
   *z1 = rho * s;
 }
 
+// Build the MLP input row of pair p (features in FP32, Sec. 2.2 Eq. (mlp_input))
+// into the group's X tile and stash what the pair update needs -- p, the
+// particle slots and the six velocity components -- in this row's TMEM lane
+// (16 columns at `stash`).  p < 0 marks a padding row.
+__device__ __forceinline__ void build_row(char* smem, const MlpLayout& L, const MlpShape& sh,
+                                          const NeuralArgs& a, int g, int row, int32_t p, uint32_t stash) {
+  float f[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) f[c] = 0.f;
+  uint32_t st[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) st[c] = 0u;
+  st[0] = (uint32_t)-1;
+  int4 q = make_int4(0, 0, 0, 0);
+  if (p >= 0) {
+    q = a.pairs[p];
+    // the previous pairs of both particles must be done (bounded wait)
+    if (!wait_deps(a.done, q.x, q.y, a.deps[p], a.bar + 2, a.status)) {
+      *((volatile int*)(smem + L.fail) + g) = 1;
+      p = -1;
+    }
+  }
+  if (p >= 0) {
+    const double xi = __ldcg(a.vx + q.x), yi = __ldcg(a.vy + q.x), zi = __ldcg(a.vz + q.x);
+    const double xj = __ldcg(a.vx + q.y), yj = __ldcg(a.vy + q.y), zj = __ldcg(a.vz + q.y);
+    // MLP inputs need FP32 only: convert, then scale in FP32
+    f[0] = (float)(xi - xj) * a.sigma_v_inv_f;
+    f[1] = (float)(yi - yj) * a.sigma_v_inv_f;
+    f[2] = (float)(zi - zj) * a.sigma_v_inv_f;
+    const u32x4 wa = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_NOISE, 0);
+    const u32x4 wb = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_NOISE, 1);
+    float z[4];
+    box_muller_f(wa.x, wa.z, &z[0], &z[1]);
+    box_muller_f(wb.x, wb.z, &z[2], &z[3]);
+    if (sh.d_in == 8) {
+      const double* m = a.mom + 5 * (size_t)q.z;
+      f[3] = (float)m[4] / (float)m[0] * a.T_feat_f;
+      f[4] = z[0]; f[5] = z[1]; f[6] = z[2]; f[7] = z[3];
+    } else {
+      f[3] = z[0]; f[4] = z[1]; f[5] = z[2];
+    }
+    st[0] = (uint32_t)p; st[1] = (uint32_t)q.x; st[2] = (uint32_t)q.y;
+    const double v[6] = {xi, yi, zi, xj, yj, zj};
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      st[4 + 2 * c] = __double2loint(v[c]);
+      st[5 + 2 * c] = __double2hiint(v[c]);
+    }
+  }
+  write_x_row(smem, L, g, row, f);
+  tc::fence_async_smem();
+  tc::st16(stash, st);
+}
+
+// Pair update of one row from the MLP output y and the row's TMEM stash:
+// shell projection v_r' = |v_r| y/|y| and centre-of-mass update in FP64.
+// s = |v_r|/|y| from an FP32 estimate and one FP64 Newton step on
+// s^2 |y|^2 = |v_r|^2 (relative error ~1e-14), so |v_r'| = |v_r|.
+__device__ __forceinline__ void update_row(const NeuralArgs& a, const float y[3], uint32_t stash,
+                                           unsigned round1) {
+  uint32_t st[16];
+  tc::ld16u(stash, st);
+  const int32_t p = (int32_t)st[0];
+  if (p < 0) return;
+  const int32_t qi = (int32_t)st[1], qj = (int32_t)st[2];
+  double v[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) v[c] = __hiloint2double((int)st[5 + 2 * c], (int)st[4 + 2 * c]);
+  const double ux = v[0] - v[3], uy = v[1] - v[4], uz = v[2] - v[5];
+  const double g2 = ux * ux + uy * uy + uz * uz;
+  double y0 = y[0], y1 = y[1], y2 = y[2];
+  const double ny2 = y0 * y0 + y1 * y1 + y2 * y2;
+  if (ny2 > a.eps * a.eps) {
+    const float g2f = (float)g2, ny2f = (float)ny2;
+    const float sf = sqrtf(g2f / ny2f);
+    const double s0 = sf;
+    const double res = g2 - s0 * s0 * ny2;           // g2 - s0^2 ny2
+    const double sc = s0 + res * (double)(0.5f * sf / g2f);
+    y0 *= sc; y1 *= sc; y2 *= sc;                    // v_r'
+  } else {  // isotropic fallback direction (tag 3)
+    const int4 q = a.pairs[p];
+    const u32x4 wi = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_ISO);
+    const double c = 2.0 * u53(wi.x, wi.y) - 1.0, sn = sqrt(1.0 - c * c);
+    double se, ce;
+    sincos(2.0 * DSMC_PI * u53(wi.z, wi.w), &se, &ce);
+    const double g = sqrt(g2);
+    y0 = g * c; y1 = g * sn * ce; y2 = g * sn * se;
+  }
+  if (a.u_out) {
+    const double ig = g2 > 0.0 ? 1.0 / sqrt(g2) : 0.0;
+    a.u_out[3 * (size_t)p] = (float)(y0 * ig); a.u_out[3 * (size_t)p + 1] = (float)(y1 * ig);
+    a.u_out[3 * (size_t)p + 2] = (float)(y2 * ig);
+  }
+  const double cx = 0.5 * (v[0] + v[3]), cy = 0.5 * (v[1] + v[4]), cz = 0.5 * (v[2] + v[5]);
+  __stcg(a.vx + qi, fma(0.5, y0, cx)); __stcg(a.vy + qi, fma(0.5, y1, cy)); __stcg(a.vz + qi, fma(0.5, y2, cz));
+  __stcg(a.vx + qj, fma(-0.5, y0, cx)); __stcg(a.vy + qj, fma(-0.5, y1, cy)); __stcg(a.vz + qj, fma(-0.5, y2, cz));
+  release_pair(a.done, qi, qj, round1);
+}
+
+// Tiles of 128 pairs of one round are claimed in round-major order from a
+// global cursor, one group at a time (no grid-wide barrier between rounds:
+// a row waits, bounded, until the previous pairs of its two particles are
+// done).  Within a group, threads 128..255 (the builders) prepare the next
+// tile's input rows while threads 0..127 (the updaters) apply this tile's
+// pair updates and stamp its particles done, the per-row data passing
+// through two alternating 16-column TMEM stashes; so the global loads of
+// the next tile overlap the FP64 update of this one.
 __global__ void __launch_bounds__(kThreads) k_collide_neural(MlpShape sh, const uint16_t* __restrict__ w,
                                                            const float* __restrict__ bias, NeuralArgs a) {
   if (a.step_dev) a.step = *a.step_dev;
@@ -396,85 +542,44 @@ __global__ void __launch_bounds__(kThreads) k_collide_neural(MlpShape sh, const 
   const Group gq = my_group(L.slots);
   uint32_t phase = 0;
   const int t = gq.t;
+  const bool builder = t >= kTileM && t < 2 * kTileM, updater = t < kTileM;
+  // this thread's TMEM lane quadrant; stash columns after the accumulators
+  const uint32_t lane_off = (uint32_t)((((int)threadIdx.x >> 5) & 3) * 32) << 16;
+  const uint32_t stash0 = tmem + lane_off + (uint32_t)(L.slots * kWidth + gq.g * 2 * kStashCols);
+  volatile int* claim = (volatile int*)(smem + L.claim) + gq.g;
+  volatile int* fail = (volatile int*)(smem + L.fail) + gq.g;
   const int R = a.info->n_rounds;
-  bool alive = true;
-  for (int r = 0; r < R && alive; ++r) {
-    const int32_t beg = a.ro[r], end = a.ro[r + 1];
-    const int32_t tiles = (end - beg + kTileM - 1) / kTileM;
-    // tile k of the round goes to CTA k % grid, group (k / grid) % G: small
-    // rounds spread over the SMs before a second group of a CTA takes a tile
-    for (int32_t tile = blockIdx.x + gridDim.x * gq.g; tile < tiles && alive; tile += gridDim.x * gq.G) {
-      const int32_t p = beg + tile * kTileM + t;
-      const bool valid = t < kTileM && p < end;
-      int4 q = make_int4(0, 0, 0, 0);
-      double xi = 0, yi = 0, zi = 0, xj = 0, yj = 0, zj = 0, ux = 0, uy = 0, uz = 0;
-      float f[16];
-#pragma unroll
-      for (int c = 0; c < 16; ++c) f[c] = 0.f;
-      if (valid) {
-        q = a.pairs[p];
-        xi = __ldcg(a.vx + q.x); yi = __ldcg(a.vy + q.x); zi = __ldcg(a.vz + q.x);
-        xj = __ldcg(a.vx + q.y); yj = __ldcg(a.vy + q.y); zj = __ldcg(a.vz + q.y);
-        ux = xi - xj; uy = yi - yj; uz = zi - zj;
-        // MLP inputs need FP32 only: convert, then scale in FP32
-        f[0] = (float)ux * a.sigma_v_inv_f;
-        f[1] = (float)uy * a.sigma_v_inv_f;
-        f[2] = (float)uz * a.sigma_v_inv_f;
-        const u32x4 wa = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_NOISE, 0);
-        const u32x4 wb = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_NOISE, 1);
-        float z[4];
-        box_muller_f(wa.x, wa.z, &z[0], &z[1]);
-        box_muller_f(wb.x, wb.z, &z[2], &z[3]);
-        if (sh.d_in == 8) {
-          const double* m = a.mom + 5 * (size_t)q.z;
-          f[3] = (float)m[4] / (float)m[0] * a.T_feat_f;
-          f[4] = z[0]; f[5] = z[1]; f[6] = z[2]; f[7] = z[3];
-        } else {
-          f[3] = z[0]; f[4] = z[1]; f[5] = z[2];
-        }
-      }
-      if (t < kTileM) {
-        write_x_row(smem, L, gq.g, t, f);
-        tc::fence_async_smem();
-      }
-      group_sync(gq);
-      float y[3];
-      if (!mlp_tile(smem, L, sh, gq, tmem, phase, y, a.status)) { alive = false; break; }
-      if (valid) {
-        // shell projection v_r' = |v_r| y/|y| and centre-of-mass update in FP64.
-        // s = |v_r|/|y| from an FP32 estimate and one FP64 Newton step on
-        // s^2 |y|^2 = |v_r|^2 (relative error ~1e-14), so |v_r'| = |v_r|.
-        const double g2 = ux * ux + uy * uy + uz * uz;
-        double y0 = y[0], y1 = y[1], y2 = y[2];
-        const double ny2 = y0 * y0 + y1 * y1 + y2 * y2;
-        if (ny2 > a.eps * a.eps) {
-          const float g2f = (float)g2, ny2f = (float)ny2;
-          const float sf = sqrtf(g2f / ny2f);
-          const double s0 = sf;
-          const double res = g2 - s0 * s0 * ny2;           // g2 - s0^2 ny2
-          const double sc = s0 + res * (double)(0.5f * sf / g2f);
-          y0 *= sc; y1 *= sc; y2 *= sc;                    // v_r'
-        } else {  // isotropic fallback direction (tag 3)
-          const u32x4 wi = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_ISO);
-          const double c = 2.0 * u53(wi.x, wi.y) - 1.0, sn = sqrt(1.0 - c * c);
-          double se, ce;
-          sincos(2.0 * DSMC_PI * u53(wi.z, wi.w), &se, &ce);
-          const double g = sqrt(g2);
-          y0 = g * c; y1 = g * sn * ce; y2 = g * sn * se;
-        }
-        if (a.u_out) {
-          const double ig = g2 > 0.0 ? 1.0 / sqrt(g2) : 0.0;
-          a.u_out[3 * (size_t)p] = (float)(y0 * ig); a.u_out[3 * (size_t)p + 1] = (float)(y1 * ig);
-          a.u_out[3 * (size_t)p + 2] = (float)(y2 * ig);
-        }
-        const double cx = 0.5 * (xi + xj), cy = 0.5 * (yi + yj), cz = 0.5 * (zi + zj);
-        __stcg(a.vx + q.x, fma(0.5, y0, cx)); __stcg(a.vy + q.x, fma(0.5, y1, cy)); __stcg(a.vz + q.x, fma(0.5, y2, cz));
-        __stcg(a.vx + q.y, fma(-0.5, y0, cx)); __stcg(a.vy + q.y, fma(-0.5, y1, cy)); __stcg(a.vz + q.y, fma(-0.5, y2, cz));
-      }
+  int r = 0;            // round of the last unit mapped (group-uniform)
+  int64_t base = 0;     // first unit of round r
+  if (t == 0) { *claim = (int)atomicAdd(a.bar + 3, 1u); *fail = 0; }
+  group_sync(gq);
+  int32_t p0 = 0, p1 = 0;
+  bool have = unit_range(a.ro, R, kTileM, r, base, (unsigned)*claim, &p0, &p1);
+  int r_cur = r;
+  if (have) {
+    if (builder) build_row(smem, L, sh, a, gq.g, t - kTileM, p0 + (t - kTileM) < p1 ? p0 + (t - kTileM) : -1, stash0);
+    tc::fence_before();
+    group_sync(gq);
+    if (*fail) have = false;
+  }
+  uint32_t buf = 0;
+  while (have) {
+    if (t == 0) *claim = (int)atomicAdd(a.bar + 3, 1u);  // read after the tile's barriers
+    float y[3];
+    if (!mlp_tile(smem, L, sh, gq, tmem, phase, y, a.status)) break;
+    int32_t n0 = 0, n1 = 0;
+    const bool have_next = unit_range(a.ro, R, kTileM, r, base, (unsigned)*claim, &n0, &n1);
+    if (builder && have_next) {
+      const int32_t p = n0 + (t - kTileM);
+      build_row(smem, L, sh, a, gq.g, t - kTileM, p < n1 ? p : -1, stash0 + (buf ^ 1u) * kStashCols);
     }
-    // both groups agree on whether to go on before the grid barrier
-    alive = __syncthreads_and(alive) != 0;
-    if (alive && r + 1 < R && !grid_barrier(a.bar, a.status, kBarrierLimitNs)) alive = false;
+    if (updater) update_row(a, y, stash0 + buf * kStashCols, (unsigned)(r_cur + 1));
+    tc::fence_before();
+    group_sync(gq);
+    tc::fence_after();
+    if (*fail) break;
+    buf ^= 1u;
+    p0 = n0; p1 = n1; r_cur = r; have = have_next;
   }
   cta_teardown(tmem, L);
 }
@@ -504,31 +609,33 @@ static bool set_smem(const void* k, int bytes) {
 
 int launch_collide_neural(Ctx* c, const dsmc_gas_t& gas, const dsmc_mlp_t& mlp,
                           const uint16_t* w, const float* bias, uint64_t step,
-                          const double* mom, const int32_t* pairs, const int32_t* ro,
-                          const dsmc_select_info_t* info, double* vx, double* vy, double* vz,
-                          float* u_out, cudaStream_t s) {
+                          const double* mom, int32_t n, const int32_t* pairs, const uint32_t* deps,
+                          const int32_t* ro, const dsmc_select_info_t* info, double* vx, double* vy,
+                          double* vz, float* u_out, void* ws, size_t ws_bytes, cudaStream_t s) {
   if (mlp.n_hidden > kMaxHidden) return record(c, DSMC_ERR_UNSUPPORTED, "collide_neural: n_hidden > 4");
+  if (ws_bytes < collide_ws(n)) return record(c, DSMC_ERR_ARG, "collide_neural: workspace too small");
   const MlpShape sh{mlp.d_in, mlp.n_hidden, mlp.act, mlp_slots(mlp.n_hidden)};
   const MlpLayout L = mlp_layout(sh.n_hidden, sh.slots);
   if (!set_smem((const void*)k_collide_neural, (int)L.total))
     return record(c, DSMC_ERR_CUDA, "collide_neural: shared-memory attribute");
-  const int blocks = cooperative_blocks(c, (const void*)k_collide_neural, kThreads, L.total);
-  if (!blocks) return record(c, DSMC_ERR_CUDA, "collide_neural: occupancy query failed");
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_collide_neural, kThreads, L.total) !=
+          cudaSuccess || per_sm < 1)
+    return record(c, DSMC_ERR_CUDA, "collide_neural: occupancy query failed");
   NeuralArgs a;
   a.seed = gas.seed; a.step = step; a.step_dev = graph_step_ptr(c);
   a.sigma_v_inv = 1.0 / mlp.sigma_v; a.T_ref_inv = 1.0 / mlp.T_ref;
   a.m_over_3k = gas.mass / (3.0 * DSMC_KB); a.eps = mlp.eps;
   a.sigma_v_inv_f = (float)a.sigma_v_inv;
   a.T_feat_f = (float)(a.m_over_3k * a.T_ref_inv);
-  a.mom = mom; a.u_out = u_out; a.pairs = (const int4*)pairs; a.ro = ro; a.info = info;
-  a.vx = vx; a.vy = vy; a.vz = vz; a.bar = barrier_ptr(c); a.status = status_ptr(c);
-  if (cudaMemsetAsync(a.bar, 0, 4 * sizeof(unsigned), s) != cudaSuccess) return DSMC_ERR_CUDA;
-  void* args[] = {(void*)&sh, (void*)&w, (void*)&bias, (void*)&a};
-  if (cudaLaunchCooperativeKernel((const void*)k_collide_neural, dim3(blocks), dim3(kThreads), args, L.total, s) !=
-      cudaSuccess)
-    return record(c, DSMC_ERR_CUDA, "collide_neural: cooperative launch failed");
+  a.mom = mom; a.u_out = u_out; a.pairs = (const int4*)pairs; a.deps = deps; a.ro = ro; a.info = info;
+  a.vx = vx; a.vy = vy; a.vz = vz; a.done = (unsigned*)ws; a.bar = barrier_ptr(c); a.status = status_ptr(c);
+  if (cudaMemsetAsync(a.bar, 0, 4 * sizeof(unsigned), s) != cudaSuccess ||
+      cudaMemsetAsync(a.done, 0, sizeof(unsigned) * (size_t)(n > 0 ? n : 1), s) != cudaSuccess)
+    return DSMC_ERR_CUDA;
+  k_collide_neural<<<sm_count(c) * per_sm, kThreads, L.total, s>>>(sh, w, bias, a);
   count_launches(c, 1);
-  return 0;
+  return cudaGetLastError() == cudaSuccess ? 0 : record(c, DSMC_ERR_CUDA, "collide_neural: launch failed");
 }
 
 int launch_mlp_forward(Ctx* c, const dsmc_mlp_t& mlp, const uint16_t* w, const float* bias,

@@ -8,7 +8,8 @@
 //                 the accepted ones, then one lane walks them in candidate
 //                 order assigning round = 1 + max(last[i], last[j])
 //   scan          per-round counts -> round offsets
-//   k_sel_scatter block per chunk: regroup the pairs round-major
+//   k_sel_scatter block per chunk: regroup the pairs round-major, each with
+//                 the rounds of the previous pairs of its two particles
 //
 // The accept decision and M are taken in FP64 with explicitly rounded
 // operations (no contraction into FMA), in the operation order of the
@@ -27,6 +28,7 @@ struct SelArgs {
   const int32_t* offs;
   int4* tmp;
   int32_t* tmp_round;
+  uint32_t* tmp_dep;   // rounds (1-based, 0 = none) of the previous pair of i | of j << 16
   int32_t* last;
   int32_t* round_count;
   int32_t* n_rounds;
@@ -259,6 +261,7 @@ __global__ void __launch_bounds__(kEmitWarps * 32) k_sel_emit(SelArgs a) {
           last[i] = (uint16_t)(r + 1);
           last[j] = (uint16_t)(r + 1);
           a.tmp_round[p] = r;
+          a.tmp_dep[p] = (uint32_t)li | ((uint32_t)lj << 16);
           atomicAdd(&hist[r], 1);
           rm = r > rm ? r : rm;
         }
@@ -271,6 +274,7 @@ __global__ void __launch_bounds__(kEmitWarps * 32) k_sel_emit(SelArgs a) {
           a.last[q.x] = r;
           a.last[q.y] = r;
           a.tmp_round[p] = r;
+          a.tmp_dep[p] = (uint32_t)(li + 1) | ((uint32_t)(lj + 1) << 16);
           atomicAdd(&hist[r], 1);
           rm = r > rm ? r : rm;
         }
@@ -299,8 +303,9 @@ constexpr int kScatterChunk = 4096;
 
 __global__ void __launch_bounds__(256)
 k_sel_scatter(const int4* __restrict__ tmp, const int32_t* __restrict__ tmp_round,
-              const int32_t* __restrict__ offs, int32_t n_cells, int64_t capacity,
-              const int32_t* __restrict__ round_off, int32_t* round_fill, int4* __restrict__ out) {
+              const uint32_t* __restrict__ tmp_dep, const int32_t* __restrict__ offs, int32_t n_cells,
+              int64_t capacity, const int32_t* __restrict__ round_off, int32_t* round_fill,
+              int4* __restrict__ out, uint32_t* __restrict__ deps) {
   __shared__ int cnt[DSMC_MAX_ROUNDS];
   __shared__ int dst[DSMC_MAX_ROUNDS];
   const int64_t total = offs[n_cells];
@@ -319,7 +324,9 @@ k_sel_scatter(const int4* __restrict__ tmp, const int32_t* __restrict__ tmp_roun
   __syncthreads();
   for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
     const int r = tmp_round[p];
-    out[dst[r] + atomicAdd(&cnt[r], 1)] = tmp[p];
+    const int q = dst[r] + atomicAdd(&cnt[r], 1);
+    out[q] = tmp[p];
+    deps[q] = tmp_dep[p];
   }
 }
 
@@ -336,6 +343,7 @@ __global__ void k_sel_finalize(const int32_t* offs, int32_t n_cells, int64_t cap
 // ---------------------------------------------------------------- workspace
 struct SelWs {
   int32_t *counts, *offs, *tmp_round, *last, *round_count, *round_fill, *n_rounds;
+  uint32_t* tmp_dep;
   double* sgnew;
   int4* tmp;
   unsigned long long* n_cand;
@@ -352,6 +360,7 @@ static size_t carve(SelWs* w, char* p, int32_t n, int32_t n_cells, int64_t capac
   w->sgnew = (double*)take(sizeof(double) * nc);
   w->tmp = (int4*)take(sizeof(int4) * cap);
   w->tmp_round = (int32_t*)take(sizeof(int32_t) * cap);
+  w->tmp_dep = (uint32_t*)take(sizeof(uint32_t) * cap);
   w->last = (int32_t*)take(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
   // the following four are zeroed together
   w->round_count = (int32_t*)take(sizeof(int32_t) * DSMC_MAX_ROUNDS * 2 + 256);
@@ -377,7 +386,7 @@ static unsigned blocks_for(int64_t work, int per_block, int max_blocks) {
 
 int launch_select(Ctx* c, const dsmc_gas_t& gas, int32_t n, int32_t n_cells, const int32_t* cs,
                   const double* vx, const double* vy, const double* vz, double* sgmax,
-                  uint64_t step, int64_t capacity, int32_t* pairs, int32_t* round_offsets,
+                  uint64_t step, int64_t capacity, int32_t* pairs, uint32_t* deps, int32_t* round_offsets,
                   dsmc_select_info_t* info, void* ws, size_t ws_bytes, cudaStream_t s) {
   if (ws_bytes < select_ws(n, n_cells, capacity))
     return record(c, DSMC_ERR_ARG, "select: workspace too small");
@@ -386,7 +395,7 @@ int launch_select(Ctx* c, const dsmc_gas_t& gas, int32_t n, int32_t n_cells, con
   carve(&w, (char*)ws, n, n_cells, capacity);
   SelArgs a;
   a.cs = cs; a.vx = vx; a.vy = vy; a.vz = vz; a.sgmax = sgmax; a.sgnew = w.sgnew;
-  a.counts = w.counts; a.offs = w.offs; a.tmp = w.tmp; a.tmp_round = w.tmp_round;
+  a.counts = w.counts; a.offs = w.offs; a.tmp = w.tmp; a.tmp_round = w.tmp_round; a.tmp_dep = w.tmp_dep;
   a.last = w.last; a.round_count = w.round_count; a.n_rounds = w.n_rounds; a.n_cand = w.n_cand;
   a.status = status_ptr(c); a.n_cells = n_cells; a.model = gas.model; a.capacity = capacity;
   a.seed = gas.seed; a.step = step; a.step_dev = graph_step_ptr(c); a.fn = gas.fn_over_vc; a.dt = gas.dt;
@@ -419,8 +428,8 @@ int launch_select(Ctx* c, const dsmc_gas_t& gas, int32_t n, int32_t n_cells, con
     if (rc) return rc;
     const unsigned sb = (unsigned)((capacity + kScatterChunk - 1) / kScatterChunk);
     if (sb > 0) {
-      k_sel_scatter<<<sb, 256, 0, s>>>(w.tmp, w.tmp_round, w.offs, n_cells, capacity,
-                                        round_offsets, w.round_fill, (int4*)pairs);
+      k_sel_scatter<<<sb, 256, 0, s>>>(w.tmp, w.tmp_round, w.tmp_dep, w.offs, n_cells, capacity,
+                                        round_offsets, w.round_fill, (int4*)pairs, deps);
       count_launches(c, 1);
     }
   } else {

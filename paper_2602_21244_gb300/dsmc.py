@@ -61,7 +61,7 @@ class StepBuffers(C.Structure):
                 ("perm", C.c_void_p), ("cell_start", C.c_void_p), ("svx", C.c_void_p),
                 ("svy", C.c_void_p), ("svz", C.c_void_p), ("mom", C.c_void_p),
                 ("sigma_g_max", C.c_void_p), ("pairs", C.c_void_p), ("round_offsets", C.c_void_p),
-                ("info", C.c_void_p), ("ws", C.c_void_p), ("ws_bytes", C.c_size_t)]
+                ("info", C.c_void_p), ("ws", C.c_void_p), ("ws_bytes", C.c_size_t), ("deps", C.c_void_p)]
 
 
 class TuneEntry(C.Structure):
@@ -110,14 +110,15 @@ def load(build: bool = True):
             "dsmc_cell_moments": (C.c_int, [vp, i32, vp, vp, vp, vp, vp, vp]),
             "dsmc_sigma_g_max_init": (C.c_int, [vp, P(Gas), i32, vp, d, vp, vp]),
             "dsmc_select_workspace_size": (sz, [i32, i32, i64]),
-            "dsmc_select_pairs": (C.c_int, [vp, P(Gas), i32, i32, vp, vp, vp, vp, vp, u64, i64, vp, vp,
+            "dsmc_select_pairs": (C.c_int, [vp, P(Gas), i32, i32, vp, vp, vp, vp, vp, u64, i64, vp, vp, vp,
                                             vp, vp, sz, vp]),
-            "dsmc_collide_vhs": (C.c_int, [vp, P(Gas), u64, vp, vp, vp, vp, vp, vp, vp]),
+            "dsmc_collide_workspace_size": (sz, [i32]),
+            "dsmc_collide_vhs": (C.c_int, [vp, P(Gas), u64, i32, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
             "dsmc_jager_chi": (C.c_int, [vp, P(Gas), P(Potential), i32, i64, vp, vp, vp, vp]),
-            "dsmc_collide_jager": (C.c_int, [vp, P(Gas), P(Potential), i32, u64, vp, vp, vp, vp, vp,
-                                             vp, vp, vp]),
-            "dsmc_collide_neural": (C.c_int, [vp, P(Gas), P(Mlp), vp, vp, u64, vp, vp, vp, vp, vp, vp,
-                                              vp, vp, vp]),
+            "dsmc_collide_jager": (C.c_int, [vp, P(Gas), P(Potential), i32, u64, i32, vp, vp, vp, vp, vp,
+                                             vp, vp, vp, vp, sz, vp]),
+            "dsmc_collide_neural": (C.c_int, [vp, P(Gas), P(Mlp), vp, vp, u64, vp, i32, vp, vp, vp, vp, vp,
+                                              vp, vp, vp, vp, sz, vp]),
             "dsmc_mlp_forward": (C.c_int, [vp, P(Mlp), vp, vp, i64, vp, vp, vp]),
             "dsmc_tc_selftest": (C.c_int, [vp, i32, i32, i32, vp, vp, vp, vp]),
             "dsmc_selftest_timeout": (C.c_int, [vp, i32, u64, vp]),
@@ -281,6 +282,7 @@ class Context:
         dev = vx.device
         if out is None:
             out = dict(pairs=torch.empty((max(capacity, 1), 4), dtype=torch.int32, device=dev),
+                       deps=torch.empty(max(capacity, 1), dtype=torch.int32, device=dev),
                        round_offsets=torch.empty(MAX_ROUNDS + 1, dtype=torch.int32, device=dev),
                        info=torch.zeros(3, dtype=torch.int64, device=dev))
         nbytes = self._lib.dsmc_select_workspace_size(n, nc, capacity)
@@ -289,15 +291,32 @@ class Context:
         self._check(self._lib.dsmc_select_pairs(
             self.h, C.byref(gas), n, nc, _ptr(cell_start, torch.int32), _ptr(vx, torch.float64),
             _ptr(vy, torch.float64), _ptr(vz, torch.float64), _ptr(sgmax, torch.float64), step,
-            capacity, _ptr(out["pairs"]), _ptr(out["round_offsets"]), _ptr(out["info"]), _ptr(ws),
-            nbytes, _stream(stream)), "select_pairs")
+            capacity, _ptr(out["pairs"]), _ptr(out["deps"]), _ptr(out["round_offsets"]), _ptr(out["info"]),
+            _ptr(ws), nbytes, _stream(stream)), "select_pairs")
         return out
 
-    def collide_vhs(self, gas: Gas, step, sel, vx, vy, vz, stream=None):
-        self._check(self._lib.dsmc_collide_vhs(self.h, C.byref(gas), step, _ptr(sel["pairs"]),
-                                               _ptr(sel["round_offsets"]), _ptr(sel["info"]),
+    def _collide_ws(self, n, device, ws=None):
+        """Workspace of the collide calls (one done stamp per particle): the
+        caller's, else one kept by this object per device."""
+        nbytes = self._lib.dsmc_collide_workspace_size(n)
+        if ws is not None:
+            if ws.numel() < nbytes:
+                raise ValueError("collide workspace too small")
+            return ws, nbytes
+        key = ("collide_ws", str(device))
+        cur = getattr(self, "_ws_cache", {}).get(key)
+        if cur is None or cur.numel() < nbytes:
+            cur = torch.empty(nbytes, dtype=torch.uint8, device=device)
+            self._ws_cache = getattr(self, "_ws_cache", {})
+            self._ws_cache[key] = cur
+        return cur, nbytes
+
+    def collide_vhs(self, gas: Gas, step, sel, vx, vy, vz, ws=None, stream=None):
+        w, nb = self._collide_ws(vx.numel(), vx.device, ws)
+        self._check(self._lib.dsmc_collide_vhs(self.h, C.byref(gas), step, vx.numel(), _ptr(sel["pairs"]),
+                                               _ptr(sel["deps"]), _ptr(sel["round_offsets"]), _ptr(sel["info"]),
                                                _ptr(vx, torch.float64), _ptr(vy, torch.float64),
-                                               _ptr(vz, torch.float64), _stream(stream)), "collide_vhs")
+                                               _ptr(vz, torch.float64), _ptr(w), nb, _stream(stream)), "collide_vhs")
 
     def jager_chi(self, gas: Gas, pot: Potential, b, g, n_nodes=32, chi=None, stream=None):
         if chi is None:
@@ -308,20 +327,22 @@ class Context:
         return chi
 
     def collide_jager(self, gas: Gas, pot: Potential, step, sel, vx, vy, vz, n_nodes=32,
-                      chi_out=None, stream=None):
+                      chi_out=None, ws=None, stream=None):
+        w, nb = self._collide_ws(vx.numel(), vx.device, ws)
         self._check(self._lib.dsmc_collide_jager(
-            self.h, C.byref(gas), C.byref(pot), n_nodes, step, _ptr(sel["pairs"]),
+            self.h, C.byref(gas), C.byref(pot), n_nodes, step, vx.numel(), _ptr(sel["pairs"]), _ptr(sel["deps"]),
             _ptr(sel["round_offsets"]), _ptr(sel["info"]), _ptr(vx, torch.float64),
             _ptr(vy, torch.float64), _ptr(vz, torch.float64), _ptr(chi_out, torch.float32),
-            _stream(stream)), "collide_jager")
+            _ptr(w), nb, _stream(stream)), "collide_jager")
 
     def collide_neural(self, gas: Gas, mlp: Mlp, w_bits, bias, step, mom, sel, vx, vy, vz,
-                       u_out=None, stream=None):
+                       u_out=None, ws=None, stream=None):
+        w, nb = self._collide_ws(vx.numel(), vx.device, ws)
         self._check(self._lib.dsmc_collide_neural(
             self.h, C.byref(gas), C.byref(mlp), _ptr(w_bits, torch.int16), _ptr(bias, torch.float32),
-            step, _ptr(mom, torch.float64), _ptr(sel["pairs"]), _ptr(sel["round_offsets"]),
-            _ptr(sel["info"]), _ptr(vx, torch.float64), _ptr(vy, torch.float64),
-            _ptr(vz, torch.float64), _ptr(u_out, torch.float32), _stream(stream)), "collide_neural")
+            step, _ptr(mom, torch.float64), vx.numel(), _ptr(sel["pairs"]), _ptr(sel["deps"]),
+            _ptr(sel["round_offsets"]), _ptr(sel["info"]), _ptr(vx, torch.float64), _ptr(vy, torch.float64),
+            _ptr(vz, torch.float64), _ptr(u_out, torch.float32), _ptr(w), nb, _stream(stream)), "collide_neural")
 
     def mlp_forward(self, mlp: Mlp, w_bits, bias, x, y=None, stream=None):
         n = x.shape[0]
@@ -580,6 +601,7 @@ class StepState:
         self.mom = torch.empty((n_cells, 5), dtype=f64, device=dev)
         self.sigma_g_max = torch.empty(n_cells, dtype=f64, device=dev)
         self.pairs = torch.empty((max(capacity, 1), 4), dtype=i32, device=dev)
+        self.deps = torch.empty(max(capacity, 1), dtype=i32, device=dev)
         self.round_offsets = torch.empty(MAX_ROUNDS + 1, dtype=i32, device=dev)
         self.info = torch.zeros(3, dtype=torch.int64, device=dev)
         nb = ctx.step_workspace_size(n, n_cells, capacity)
@@ -588,11 +610,11 @@ class StepState:
         self.desc = StepBuffers(n, n_cells, capacity, p(self.cell_id), p(self.vx), p(self.vy),
                                 p(self.vz), p(self.perm), p(self.cell_start), p(self.svx), p(self.svy),
                                 p(self.svz), p(self.mom), p(self.sigma_g_max), p(self.pairs),
-                                p(self.round_offsets), p(self.info), p(self.ws), nb)
+                                p(self.round_offsets), p(self.info), p(self.ws), nb, p(self.deps))
 
     @property
     def sel(self):
-        return dict(pairs=self.pairs, round_offsets=self.round_offsets, info=self.info)
+        return dict(pairs=self.pairs, deps=self.deps, round_offsets=self.round_offsets, info=self.info)
 
     def info_host(self):
         i = self.info.cpu()

@@ -133,6 +133,15 @@ def test_select_bit_exact(name, model):
     assert np.array_equal(p[order, 0], ref["i"]) and np.array_equal(p[order, 1], ref["j"])
     assert np.array_equal(p[order, 2], ref["cell"]) and np.array_equal(p[order, 3], ref["m"])
     assert np.array_equal(rr[order], ref["round"])
+    # deps: 1-based rounds of the previous pair of each particle, derived here
+    # from the oracle's pairs in candidate order and its rounds
+    deps = host(sel["deps"])[:sh["n_pairs"]].view(np.uint32)
+    want = np.zeros(len(ref["i"]), np.uint32)
+    last = {}
+    for k, (i, j, r) in enumerate(zip(ref["i"].tolist(), ref["j"].tolist(), ref["round"].tolist())):
+        want[k] = last.get(i, 0) | (last.get(j, 0) << 16)
+        last[i] = last[j] = r + 1
+    assert np.array_equal(deps[order], want)
     rel = np.abs(host(sg) - ref["sgmax"]) / ref["sgmax"]
     assert rel.max() <= (0.0 if model == 1 else 4e-16)
 
@@ -392,7 +401,7 @@ def test_collide_jager_parity():
 
 # ------------------------------------------------------------------ failure detection
 
-@pytest.mark.parametrize("which", [0, 1])
+@pytest.mark.parametrize("which", [0, 1, 2])
 def test_bounded_waits_time_out_without_hanging(which):
     C = ctx()
     import time
