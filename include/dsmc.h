@@ -201,7 +201,8 @@ int dsmc_sigma_g_max_init(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, int32_t n_cell
  *  i, last round of j) splits them into rounds of disjoint pairs that,
  *  applied in round order, reproduce the sequential result exactly.
  *  Output: pairs[4p..4p+3] = {i, j, cell, m} (sorted slot indices, cell,
- *  candidate index) grouped by round (order inside a round unspecified),
+ *  candidate index) grouped by round (inside a round in cell order, and in
+ *  candidate order within a cell),
  *  deps[p] = (1-based round of the previous pair of particle i) | (that of
  *  j) << 16, 0 = none (the collide kernels order their work by it),
  *  round_offsets[r] = first pair of round r (the array holds

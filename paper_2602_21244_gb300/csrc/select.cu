@@ -8,8 +8,9 @@
 //                 the accepted ones, then one lane walks them in candidate
 //                 order assigning round = 1 + max(last[i], last[j])
 //   scan          per-round counts -> round offsets
-//   k_sel_scatter block per chunk: regroup the pairs round-major, each with
-//                 the rounds of the previous pairs of its two particles
+//   k_sel_rcount, k_sel_rscan, k_sel_scatter: stable round-major regrouping
+//                 of the pairs (cell-major candidate order inside a round),
+//                 each with the rounds of the previous pairs of its particles
 //
 // The accept decision and M are taken in FP64 with explicitly rounded
 // operations (no contraction into FMA), in the operation order of the
@@ -301,32 +302,108 @@ __global__ void k_sel_sg_commit(SelArgs a) {
 
 constexpr int kScatterChunk = 4096;
 
+// Stable round-major regrouping of the cell-major pair list, in three
+// kernels over chunks of kScatterChunk pairs: per chunk and round counts
+// (cnt[r][chunk]), their exclusive scan along the chunks of each round plus
+// the round's offset, then each chunk writes its pairs in order.  Inside a
+// round the pairs keep the cell-major candidate order, so the list is
+// deterministic and the pairs of a round's first cells come first.
 __global__ void __launch_bounds__(256)
-k_sel_scatter(const int4* __restrict__ tmp, const int32_t* __restrict__ tmp_round,
-              const uint32_t* __restrict__ tmp_dep, const int32_t* __restrict__ offs, int32_t n_cells,
-              int64_t capacity, const int32_t* __restrict__ round_off, int32_t* round_fill,
-              int4* __restrict__ out, uint32_t* __restrict__ deps) {
-  __shared__ int cnt[DSMC_MAX_ROUNDS];
-  __shared__ int dst[DSMC_MAX_ROUNDS];
+k_sel_rcount(const int32_t* __restrict__ tmp_round, const int32_t* __restrict__ offs, int32_t n_cells,
+             int64_t capacity, const int32_t* __restrict__ n_rounds, int32_t n_chunks, int32_t* __restrict__ cnt) {
+  __shared__ int hist[DSMC_MAX_ROUNDS];
   const int64_t total = offs[n_cells];
   if (total > capacity) return;
   const int64_t p0 = (int64_t)blockIdx.x * kScatterChunk;
   if (p0 >= total) return;
   const int64_t p1 = p0 + kScatterChunk < total ? p0 + kScatterChunk : total;
-  for (int t = threadIdx.x; t < DSMC_MAX_ROUNDS; t += blockDim.x) cnt[t] = 0;
+  const int R = *n_rounds;
+  for (int t = threadIdx.x; t < R; t += blockDim.x) hist[t] = 0;
   __syncthreads();
-  for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) atomicAdd(&cnt[tmp_round[p]], 1);
+  for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) atomicAdd(&hist[tmp_round[p]], 1);
   __syncthreads();
-  for (int t = threadIdx.x; t < DSMC_MAX_ROUNDS; t += blockDim.x) {
-    dst[t] = cnt[t] ? round_off[t] + atomicAdd(round_fill + t, cnt[t]) : 0;
-    cnt[t] = 0;
+  for (int t = threadIdx.x; t < R; t += blockDim.x) cnt[(size_t)t * n_chunks + blockIdx.x] = hist[t];
+}
+
+// Block r: exclusive scan of cnt[r][0..chunks) + round_off[r] (in place).
+__global__ void __launch_bounds__(256)
+k_sel_rscan(const int32_t* __restrict__ offs, int32_t n_cells, int64_t capacity,
+            const int32_t* __restrict__ n_rounds, const int32_t* __restrict__ round_off, int32_t n_chunks,
+            int32_t* __restrict__ cnt) {
+  __shared__ int warp_tot[8];
+  __shared__ int carry;
+  const int64_t total = offs[n_cells];
+  if (total > capacity || (int)blockIdx.x >= *n_rounds) return;
+  const int chunks = (int)((total + kScatterChunk - 1) / kScatterChunk);
+  int32_t* row = cnt + (size_t)blockIdx.x * n_chunks;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = round_off[blockIdx.x];
+  __syncthreads();
+  for (int c0 = 0; c0 < chunks; c0 += blockDim.x) {
+    const int c = c0 + threadIdx.x;
+    const int v = c < chunks ? row[c] : 0;
+    int x = v;  // inclusive scan in the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    int before = carry;
+    for (int q = 0; q < w; ++q) before += warp_tot[q];
+    if (c < chunks) row[c] = before + x - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = before + x;
+    __syncthreads();
+  }
+}
+
+// Block (8 warps) per chunk; warp w owns the chunk's w-th eighth.  Each
+// warp counts its rounds, the counts are turned into per-warp starting
+// positions (warps in order after the chunk's base), then each warp writes
+// its pairs in order, the rank among equal rounds within 32 lanes coming
+// from __match_any_sync.
+constexpr int kScatterWarps = 8;
+
+__global__ void __launch_bounds__(kScatterWarps * 32)
+k_sel_scatter(const int4* __restrict__ tmp, const int32_t* __restrict__ tmp_round,
+              const uint32_t* __restrict__ tmp_dep, const int32_t* __restrict__ offs, int32_t n_cells,
+              int64_t capacity, const int32_t* __restrict__ n_rounds, int32_t n_chunks,
+              const int32_t* __restrict__ base, int4* __restrict__ out, uint32_t* __restrict__ deps) {
+  __shared__ int wh[kScatterWarps][DSMC_MAX_ROUNDS];
+  const int64_t total = offs[n_cells];
+  if (total > capacity) return;
+  const int64_t p0 = (int64_t)blockIdx.x * kScatterChunk;
+  if (p0 >= total) return;
+  const int64_t p1 = p0 + kScatterChunk < total ? p0 + kScatterChunk : total;
+  const int R = *n_rounds;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  constexpr int kSub = kScatterChunk / kScatterWarps;
+  const int64_t s0 = p0 + (int64_t)w * kSub, s1 = s0 + kSub < p1 ? s0 + kSub : p1;
+  for (int t = threadIdx.x; t < kScatterWarps * R; t += blockDim.x) wh[t / R][t % R] = 0;
+  __syncthreads();
+  for (int64_t p = s0 + lane; p < s1; p += 32) atomicAdd(&wh[w][tmp_round[p]], 1);
+  __syncthreads();
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    int acc = base[(size_t)r * n_chunks + blockIdx.x];
+    for (int q = 0; q < kScatterWarps; ++q) { const int c = wh[q][r]; wh[q][r] = acc; acc += c; }
   }
   __syncthreads();
-  for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-    const int r = tmp_round[p];
-    const int q = dst[r] + atomicAdd(&cnt[r], 1);
-    out[q] = tmp[p];
-    deps[q] = tmp_dep[p];
+  const unsigned lt = (1u << lane) - 1u;
+  for (int64_t q0 = s0; q0 < s1; q0 += 32) {
+    const int64_t p = q0 + lane;
+    const bool has = p < s1;
+    const int r = has ? tmp_round[p] : -1;
+    const unsigned same = __match_any_sync(0xffffffffu, r);
+    if (has) {
+      const int q = wh[w][r] + __popc(same & lt);
+      out[q] = tmp[p];
+      deps[q] = tmp_dep[p];
+    }
+    __syncwarp();
+    if (has && (same & lt) == 0) wh[w][r] += __popc(same);
+    __syncwarp();
   }
 }
 
@@ -343,6 +420,8 @@ __global__ void k_sel_finalize(const int32_t* offs, int32_t n_cells, int64_t cap
 // ---------------------------------------------------------------- workspace
 struct SelWs {
   int32_t *counts, *offs, *tmp_round, *last, *round_count, *round_fill, *n_rounds;
+  int32_t* chunk_cnt;  // [DSMC_MAX_ROUNDS][n_chunks] counts, then scatter bases
+  int32_t n_chunks;
   uint32_t* tmp_dep;
   double* sgnew;
   int4* tmp;
@@ -361,6 +440,8 @@ static size_t carve(SelWs* w, char* p, int32_t n, int32_t n_cells, int64_t capac
   w->tmp = (int4*)take(sizeof(int4) * cap);
   w->tmp_round = (int32_t*)take(sizeof(int32_t) * cap);
   w->tmp_dep = (uint32_t*)take(sizeof(uint32_t) * cap);
+  w->n_chunks = (int32_t)((cap + kScatterChunk - 1) / kScatterChunk);
+  w->chunk_cnt = (int32_t*)take(sizeof(int32_t) * (size_t)DSMC_MAX_ROUNDS * (size_t)w->n_chunks);
   w->last = (int32_t*)take(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
   // the following four are zeroed together
   w->round_count = (int32_t*)take(sizeof(int32_t) * DSMC_MAX_ROUNDS * 2 + 256);
@@ -428,9 +509,12 @@ int launch_select(Ctx* c, const dsmc_gas_t& gas, int32_t n, int32_t n_cells, con
     if (rc) return rc;
     const unsigned sb = (unsigned)((capacity + kScatterChunk - 1) / kScatterChunk);
     if (sb > 0) {
-      k_sel_scatter<<<sb, 256, 0, s>>>(w.tmp, w.tmp_round, w.tmp_dep, w.offs, n_cells, capacity,
-                                        round_offsets, w.round_fill, (int4*)pairs, deps);
-      count_launches(c, 1);
+      k_sel_rcount<<<sb, 256, 0, s>>>(w.tmp_round, w.offs, n_cells, capacity, w.n_rounds, w.n_chunks, w.chunk_cnt);
+      k_sel_rscan<<<DSMC_MAX_ROUNDS, 256, 0, s>>>(w.offs, n_cells, capacity, w.n_rounds, round_offsets,
+                                                 w.n_chunks, w.chunk_cnt);
+      k_sel_scatter<<<sb, kScatterWarps * 32, 0, s>>>(w.tmp, w.tmp_round, w.tmp_dep, w.offs, n_cells, capacity,
+                                                       w.n_rounds, w.n_chunks, w.chunk_cnt, (int4*)pairs, deps);
+      count_launches(c, 3);
     }
   } else {
     if (cudaMemsetAsync(w.offs, 0, sizeof(int32_t), s) != cudaSuccess) return DSMC_ERR_CUDA;

@@ -133,6 +133,9 @@ def test_select_bit_exact(name, model):
     assert np.array_equal(p[order, 0], ref["i"]) and np.array_equal(p[order, 1], ref["j"])
     assert np.array_equal(p[order, 2], ref["cell"]) and np.array_equal(p[order, 3], ref["m"])
     assert np.array_equal(rr[order], ref["round"])
+    # inside a round the list is in cell order, candidate order within a cell
+    ro_ = np.lexsort((ref["m"], ref["cell"], ref["round"]))
+    assert np.array_equal(p[:, 2], ref["cell"][ro_]) and np.array_equal(p[:, 3], ref["m"][ro_])
     # deps: 1-based rounds of the previous pair of each particle, derived here
     # from the oracle's pairs in candidate order and its rounds
     deps = host(sel["deps"])[:sh["n_pairs"]].view(np.uint32)
