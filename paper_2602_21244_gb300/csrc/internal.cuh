@@ -120,6 +120,22 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* status, uint64_
 
 constexpr uint64_t kBarrierLimitNs = 2000000000ull;  // 2 s
 
+// FP64 -> FP32 with round-to-nearest-even on the integer pipe (GB300's FP64
+// pipe, which also does the conversion instruction, is ~1/64 of FP32): keep
+// the top 23 mantissa bits, round on the 29 dropped ones; results below the
+// FP32 normal range become a signed zero.  Equal to the hardware conversion
+// for every input of magnitude in [2^-126, FLT_MAX].
+__device__ __forceinline__ float f64_to_f32(double v) {
+  const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
+  const uint32_t sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  const uint32_t m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  const uint32_t rest = lo & 0x1FFFFFFFu;
+  uint32_t f = sign | ((uint32_t)(e - 896) << 23) | m;
+  f += (rest > 0x10000000u) || (rest == 0x10000000u && (m & 1u));
+  return __uint_as_float(e < 897 ? sign : f);
+}
+
 // ---------------------------------------------------------------- pair dependencies
 // The collide kernels walk the pairs of a step in round-major order without
 // grid-wide barriers.  Work units (a warp's 32 pairs, a 128-pair MLP tile)

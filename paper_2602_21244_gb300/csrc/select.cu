@@ -30,6 +30,10 @@ struct SelArgs {
   int4* tmp;
   int32_t* tmp_round;
   uint32_t* tmp_dep;   // rounds (1-based, 0 = none) of the previous pair of i | of j << 16
+  int32_t* wcnt;       // per cell: 32-candidate words of accept bits (ceil(M/32))
+  const int32_t* wofs; // their exclusive scan (first word of each cell; [n_cells] = total)
+  uint32_t* bits;      // accept bit of candidate m of cell k: bits[wofs[k] + m/32] >> (m % 32)
+  int64_t words_cap;   // capacity of bits; a cell whose words do not fit is re-evaluated
   int32_t* last;
   int32_t* round_count;
   int32_t* n_rounds;
@@ -90,6 +94,24 @@ struct CellView {
   float sgmax32, inv_sgmax32, thr_raise;
 };
 
+// Whether cell k's accept bits were kept: its word range lies inside the
+// buffer and holds all M candidates (a range past the buffer, or a cell
+// whose count was capped, is re-evaluated instead).
+__device__ __forceinline__ bool bits_kept(const SelArgs& a, int32_t k, int32_t M) {
+  const int64_t w0 = a.wofs[k], w1 = a.wofs[k + 1];
+  return w0 >= 0 && w1 >= w0 && w1 <= a.words_cap && (w1 - w0) * 32 >= M;
+}
+
+// Particles (local indices) of candidate m of cell k (tag 2).
+__device__ __forceinline__ void cand_ij(const SelArgs& a, int32_t k, int32_t N, int32_t m, int32_t* pi,
+                                        int32_t* pj) {
+  const u32x4 w = draw(a.seed, (uint32_t)m, (uint32_t)k, a.step, TAG_CAND);
+  const uint32_t i = mulhi_n(w.x, (uint32_t)N);
+  uint32_t j = mulhi_n(w.y, (uint32_t)(N - 1));
+  j += (j >= i);
+  *pi = (int32_t)i; *pj = (int32_t)j;
+}
+
 // Candidate m of cell k.  The accept decision is screened in FP32 and taken
 // in FP64 only when the FP32 ratio is within its error bound of U; the FP64
 // sigma g is also formed for candidates that may raise (sigma g)_max.
@@ -136,6 +158,18 @@ __device__ __forceinline__ bool candidate(const SelArgs& a, const CellView& cv, 
 
 constexpr int kSelWarps = 8;
 
+// Words of accept bits per cell: ceil(M/32) for the cell's candidate count M.
+__global__ void k_sel_nwords(SelArgs a) {
+  if (a.step_dev) a.step = *a.step_dev;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n_cells; k += gridDim.x * blockDim.x) {
+    const int32_t N = a.cs[k + 1] - a.cs[k];
+    int bad = 0;
+    const int32_t M = N < 2 ? 0 : ntc_count(a, k, N, &bad);
+    const int64_t words = ((int64_t)M + 31) / 32;
+    a.wcnt[k] = (int32_t)(words <= a.words_cap ? words : 0);  // too many: never kept
+  }
+}
+
 // Stage the cell's velocities (FP32) in this warp's shared-memory slice and
 // derive the screening constants.
 __device__ __forceinline__ CellView stage_cell(const SelArgs& a, float* sm, int32_t base, int32_t N,
@@ -145,7 +179,7 @@ __device__ __forceinline__ CellView stage_cell(const SelArgs& a, float* sm, int3
   if (N <= kStage) {
     float* x = sm; float* y = sm + kStage; float* z = sm + 2 * kStage;
     for (int32_t t = lane; t < N; t += 32) {
-      const float fx = (float)a.vx[base + t], fy = (float)a.vy[base + t], fz = (float)a.vz[base + t];
+      const float fx = f64_to_f32(a.vx[base + t]), fy = f64_to_f32(a.vy[base + t]), fz = f64_to_f32(a.vz[base + t]);
       x[t] = fx; y[t] = fy; z[t] = fz;
       vmax = fmaxf(vmax, fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))));
     }
@@ -184,11 +218,17 @@ __global__ void __launch_bounds__(kSelWarps * 32) k_sel_count(SelArgs a) {
     const CellView cv = stage_cell(a, stage[wid], base, N, sgk, lane);
     int acc = 0;
     double best = sgk;
-    for (int32_t m = lane; m < M; m += 32) {
+    const int64_t w0 = a.wofs[k];
+    const bool keep = bits_kept(a, k, M);
+    for (int32_t c0 = 0; c0 < M; c0 += 32) {
+      const int32_t m = c0 + lane;
       int32_t i, j;
-      double sg;
-      acc += candidate(a, cv, k, base, N, m, sgk, &i, &j, &sg);
+      double sg = -1.0;
+      const bool ok = m < M && candidate(a, cv, k, base, N, m, sgk, &i, &j, &sg);
+      acc += ok;
       best = fmax(best, sg);
+      const unsigned mask = __ballot_sync(0xffffffffu, ok);
+      if (keep && lane == 0) a.bits[w0 + c0 / 32] = mask;
     }
     acc = warp_sum_i(acc);
     best = warp_max(best);
@@ -225,7 +265,11 @@ __global__ void __launch_bounds__(kEmitWarps * 32) k_sel_emit(SelArgs a) {
     const double sgk = a.sgmax[k];
     int bad = 0;
     const int32_t M = ntc_count(a, k, N, &bad);
-    const CellView cv = stage_cell(a, stage[wid], base, N, sgk, lane);
+    // accept bits from the count pass when they were kept, else re-evaluate
+    const bool from_bits = bits_kept(a, k, M);
+    const int64_t w0 = a.wofs[k];
+    CellView cv{};
+    if (!from_bits) cv = stage_cell(a, stage[wid], base, N, sgk, lane);
     const int32_t p0 = a.offs[k], p1 = a.offs[k + 1];
     const bool local = N <= kStage && p1 - p0 <= kEmitPairs;
     int32_t pos = p0;
@@ -233,7 +277,13 @@ __global__ void __launch_bounds__(kEmitWarps * 32) k_sel_emit(SelArgs a) {
       const int32_t m = c0 + lane;
       int32_t i = 0, j = 0;
       double sg;
-      const bool ok = m < M && candidate(a, cv, k, base, N, m, sgk, &i, &j, &sg);
+      bool ok;
+      if (from_bits) {
+        ok = (a.bits[w0 + c0 / 32] >> lane) & 1u;
+        if (ok) cand_ij(a, k, N, m, &i, &j);
+      } else {
+        ok = m < M && candidate(a, cv, k, base, N, m, sgk, &i, &j, &sg);
+      }
       const unsigned mask = __ballot_sync(0xffffffffu, ok);
       if (ok) {
         const int32_t q = pos + __popc(mask & ((1u << lane) - 1u));
@@ -422,6 +472,9 @@ struct SelWs {
   int32_t *counts, *offs, *tmp_round, *last, *round_count, *round_fill, *n_rounds;
   int32_t* chunk_cnt;  // [DSMC_MAX_ROUNDS][n_chunks] counts, then scatter bases
   int32_t n_chunks;
+  int32_t *wcnt, *wofs;
+  uint32_t* bits;
+  int64_t words_cap;
   uint32_t* tmp_dep;
   double* sgnew;
   int4* tmp;
@@ -441,6 +494,11 @@ static size_t carve(SelWs* w, char* p, int32_t n, int32_t n_cells, int64_t capac
   w->tmp_round = (int32_t*)take(sizeof(int32_t) * cap);
   w->tmp_dep = (uint32_t*)take(sizeof(uint32_t) * cap);
   w->n_chunks = (int32_t)((cap + kScatterChunk - 1) / kScatterChunk);
+  w->wcnt = (int32_t*)take(sizeof(int32_t) * nc);
+  w->wofs = (int32_t*)take(sizeof(int32_t) * (nc + 1));
+  // accept bits for up to 32 candidates per accepted-pair slot
+  w->words_cap = (int64_t)cap;
+  w->bits = (uint32_t*)take(sizeof(uint32_t) * cap);
   w->chunk_cnt = (int32_t*)take(sizeof(int32_t) * (size_t)DSMC_MAX_ROUNDS * (size_t)w->n_chunks);
   w->last = (int32_t*)take(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
   // the following four are zeroed together
@@ -477,6 +535,7 @@ int launch_select(Ctx* c, const dsmc_gas_t& gas, int32_t n, int32_t n_cells, con
   SelArgs a;
   a.cs = cs; a.vx = vx; a.vy = vy; a.vz = vz; a.sgmax = sgmax; a.sgnew = w.sgnew;
   a.counts = w.counts; a.offs = w.offs; a.tmp = w.tmp; a.tmp_round = w.tmp_round; a.tmp_dep = w.tmp_dep;
+  a.wcnt = w.wcnt; a.wofs = w.wofs; a.bits = w.bits; a.words_cap = w.words_cap;
   a.last = w.last; a.round_count = w.round_count; a.n_rounds = w.n_rounds; a.n_cand = w.n_cand;
   a.status = status_ptr(c); a.n_cells = n_cells; a.model = gas.model; a.capacity = capacity;
   a.seed = gas.seed; a.step = step; a.step_dev = graph_step_ptr(c); a.fn = gas.fn_over_vc; a.dt = gas.dt;
@@ -497,6 +556,10 @@ int launch_select(Ctx* c, const dsmc_gas_t& gas, int32_t n, int32_t n_cells, con
   if (cudaMemsetAsync(round_offsets, 0, sizeof(int32_t) * (DSMC_MAX_ROUNDS + 1), s) != cudaSuccess)
     return DSMC_ERR_CUDA;
   if (n_cells > 0) {
+    k_sel_nwords<<<blocks_for(n_cells, 256, sms * 4), 256, 0, s>>>(a);
+    count_launches(c, 1);
+    int rcw = launch_scan(c, w.wcnt, w.wofs, n_cells, w.scan, s);
+    if (rcw) return rcw;
     const unsigned gb = blocks_for(n_cells, kSelWarps, sms * 8);
     k_sel_count<<<gb, kSelWarps * 32, 0, s>>>(a);
     count_launches(c, 1);
