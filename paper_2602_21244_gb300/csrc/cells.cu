@@ -269,7 +269,8 @@ k_moments(int32_t n_cells, const int32_t* __restrict__ cs, const double* __restr
     const double n = (double)(b - a);
     double th = 0;
     if (b > a) {
-      const double ux = sx / n, uy = sy / n, uz = sz / n;
+      const double inv = 1.0 / n;
+      const double ux = sx * inv, uy = sy * inv, uz = sz * inv;
       for (int32_t i = a + sl; i < b; i += kSeg) {
         const double dx = vx[i] - ux, dy = vy[i] - uy, dz = vz[i] - uz;
         th += dx * dx + dy * dy + dz * dz;
@@ -312,7 +313,9 @@ k_moment_match(int32_t n_cells, const int32_t* __restrict__ cs, const double* __
     for (int32_t i = a + sl; i < b; i += kSeg) { sx += vx[i]; sy += vy[i]; sz += vz[i]; }
     sx = seg_sum(sx); sy = seg_sum(sy); sz = seg_sum(sz);
     const double n = (double)(b - a);
-    const double ux = b > a ? sx / n : 0.0, uy = b > a ? sy / n : 0.0, uz = b > a ? sz / n : 0.0;
+    // one division per cell (the FP64 pipe bounds this kernel)
+    const double inv = b > a ? 1.0 / n : 0.0;
+    const double ux = sx * inv, uy = sy * inv, uz = sz * inv;
     double th = 0;
     for (int32_t i = a + sl; i < b; i += kSeg) {
       const double dx = vx[i] - ux, dy = vy[i] - uy, dz = vz[i] - uz;
@@ -321,7 +324,7 @@ k_moment_match(int32_t n_cells, const int32_t* __restrict__ cs, const double* __
     th = seg_sum(th);
     if (b <= a) continue;
     const double* m = mom + 5 * (size_t)k;
-    const double px = m[1] / n, py = m[2] / n, pz = m[3] / n;
+    const double px = m[1] * inv, py = m[2] * inv, pz = m[3] * inv;
     const double alpha = (b - a >= 2 && th > 0.0) ? sqrt(m[4] / th) : 1.0;
     const double ox = px - alpha * ux, oy = py - alpha * uy, oz = pz - alpha * uz;
     for (int32_t i = a + sl; i < b; i += kSeg) {

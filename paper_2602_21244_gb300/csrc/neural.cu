@@ -450,10 +450,11 @@ __device__ __forceinline__ void build_row(char* smem, const MlpLayout& L, const 
   if (p >= 0) {
     const double xi = __ldcg(a.vx + q.x), yi = __ldcg(a.vy + q.x), zi = __ldcg(a.vz + q.x);
     const double xj = __ldcg(a.vx + q.y), yj = __ldcg(a.vy + q.y), zj = __ldcg(a.vz + q.y);
-    // MLP inputs need FP32 only: convert, then scale in FP32
-    f[0] = (float)(xi - xj) * a.sigma_v_inv_f;
-    f[1] = (float)(yi - yj) * a.sigma_v_inv_f;
-    f[2] = (float)(zi - zj) * a.sigma_v_inv_f;
+    // MLP inputs need FP32 only: convert on the integer pipe, subtract and
+    // scale in FP32 (error ~ |v| 2^-24, far below the bf16 input terms)
+    f[0] = (f64_to_f32(xi) - f64_to_f32(xj)) * a.sigma_v_inv_f;
+    f[1] = (f64_to_f32(yi) - f64_to_f32(yj)) * a.sigma_v_inv_f;
+    f[2] = (f64_to_f32(zi) - f64_to_f32(zj)) * a.sigma_v_inv_f;
     const u32x4 wa = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_NOISE, 0);
     const u32x4 wb = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_NOISE, 1);
     float z[4];
@@ -461,7 +462,7 @@ __device__ __forceinline__ void build_row(char* smem, const MlpLayout& L, const 
     box_muller_f(wb.x, wb.z, &z[2], &z[3]);
     if (sh.d_in == 8) {
       const double* m = a.mom + 5 * (size_t)q.z;
-      f[3] = (float)m[4] / (float)m[0] * a.T_feat_f;
+      f[3] = f64_to_f32(m[4]) / f64_to_f32(m[0]) * a.T_feat_f;
       f[4] = z[0]; f[5] = z[1]; f[6] = z[2]; f[7] = z[3];
     } else {
       f[3] = z[0]; f[4] = z[1]; f[5] = z[2];
