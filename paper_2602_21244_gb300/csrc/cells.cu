@@ -1,11 +1,12 @@
 // Cell sort, cell moments, moment matching and the int32 exclusive scan.
 //
-// Sort (Sec. 2.6 (1)): histogram of cell ids -> exclusive scan -> cell_start;
-// scatter of input indices into their cell's slots (atomic cursor, order
-// inside a cell arbitrary) -> per-cell sort of the slot contents (restores
-// the input order, i.e. a stable counting sort) fused with the gather of
-// the velocities.  Moments and moment matching are warp-per-cell FP64
-// reductions with two passes.
+// Sort (Sec. 2.6 (1)): a stable LSD radix sort of (cell id, input index) on
+// 9-bit digits (two passes for up to 2^18 cells), each pass a per-chunk
+// digit count, one exclusive scan over (digit, chunk) and an ordered
+// per-chunk scatter; cell_start from the sorted ids; then the gather of the
+// velocities.  (The allocation-free variant keeps an atomic histogram +
+// cursor scatter + per-cell sort of the slots.)  Moments and moment
+// matching are FP64 reductions with 8 lanes per cell.
 #include <climits>
 
 #include "internal.cuh"
@@ -189,9 +190,103 @@ __global__ void k_gather(int32_t n, const int32_t* __restrict__ cell_start, int3
   }
 }
 
+// ---------------------------------------------------------------- radix sort
+constexpr int kRadixBits = 9;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kRsChunk = 4096;   // elements per block
+constexpr int kRsWarps = 8;
+
+// key of input element i: its cell id, or n_cells for an id out of range
+// (recorded as DSMC_ERR_ARG; such particles sort after every cell)
+__device__ __forceinline__ uint32_t rs_key(const int32_t* cell_id, const uint32_t* keys, int64_t i,
+                                           int32_t n_cells, int* status) {
+  if (keys) return keys[i];
+  const int32_t c = cell_id[i];
+  if ((uint32_t)c < (uint32_t)n_cells) return (uint32_t)c;
+  if (status) set_status(status, DSMC_ERR_ARG);
+  return (uint32_t)n_cells;
+}
+
+// cnt[d * chunks + block] = elements of the block's chunk with digit d
+__global__ void __launch_bounds__(256)
+k_rs_count(const int32_t* __restrict__ cell_id, const uint32_t* __restrict__ keys, int32_t n, int32_t n_cells,
+           int shift, int32_t chunks, int32_t* __restrict__ cnt, int* status) {
+  __shared__ int hist[kRadix];
+  for (int t = threadIdx.x; t < kRadix; t += blockDim.x) hist[t] = 0;
+  __syncthreads();
+  const int64_t p0 = (int64_t)blockIdx.x * kRsChunk, p1 = min((int64_t)n, p0 + kRsChunk);
+  for (int64_t i = p0 + threadIdx.x; i < p1; i += blockDim.x)
+    atomicAdd(&hist[(rs_key(cell_id, keys, i, n_cells, status) >> shift) & (kRadix - 1)], 1);
+  __syncthreads();
+  for (int t = threadIdx.x; t < kRadix; t += blockDim.x) cnt[(size_t)t * chunks + blockIdx.x] = hist[t];
+}
+
+// Ordered scatter of one chunk: warp w owns the chunk's w-th eighth; each
+// warp counts its digits, the counts become per-warp starting positions
+// (warps in order after the chunk's base from the scan), then each warp
+// writes its elements in order, ranks among equal digits within 32 lanes
+// from __match_any_sync.  Values: the input index (first pass) or vals.
+__global__ void __launch_bounds__(kRsWarps * 32)
+k_rs_scatter(const int32_t* __restrict__ cell_id, const uint32_t* __restrict__ keys,
+             const int32_t* __restrict__ vals, int32_t n, int32_t n_cells, int shift, int32_t chunks,
+             const int32_t* __restrict__ base, uint32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out) {
+  __shared__ int wh[kRsWarps][kRadix];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int t = threadIdx.x; t < kRsWarps * kRadix; t += blockDim.x) wh[t / kRadix][t % kRadix] = 0;
+  __syncthreads();
+  constexpr int kSub = kRsChunk / kRsWarps;
+  const int64_t p0 = (int64_t)blockIdx.x * kRsChunk;
+  const int64_t s0 = min((int64_t)n, p0 + (int64_t)w * kSub), s1 = min((int64_t)n, s0 + kSub);
+  for (int64_t i = s0 + lane; i < s1; i += 32)
+    atomicAdd(&wh[w][(rs_key(cell_id, keys, i, n_cells, nullptr) >> shift) & (kRadix - 1)], 1);
+  __syncthreads();
+  for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
+    int acc = base[(size_t)d * chunks + blockIdx.x];
+    for (int q = 0; q < kRsWarps; ++q) { const int c = wh[q][d]; wh[q][d] = acc; acc += c; }
+  }
+  __syncthreads();
+  const unsigned lt = (1u << lane) - 1u;
+  for (int64_t q0 = s0; q0 < s1; q0 += 32) {
+    const int64_t i = q0 + lane;
+    const bool has = i < s1;
+    const uint32_t key = has ? rs_key(cell_id, keys, i, n_cells, nullptr) : 0u;
+    const int d = has ? (int)((key >> shift) & (kRadix - 1)) : -1;
+    const unsigned same = __match_any_sync(0xffffffffu, d);
+    if (has) {
+      const int q = wh[w][d] + __popc(same & lt);
+      if (keys_out) keys_out[q] = key;
+      vals_out[q] = vals ? vals[i] : (int32_t)i;
+    }
+    __syncwarp();
+    if (has && (same & lt) == 0) wh[w][d] += __popc(same);
+    __syncwarp();
+  }
+}
+
+// cell_start from the sorted keys: slot s starts every cell in (key[s-1], key[s]]
+// (slot n closes the list with key n_cells).
+__global__ void k_cell_start(const uint32_t* __restrict__ skeys, int32_t n, int32_t n_cells,
+                             int32_t* __restrict__ cell_start) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s <= n; s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t hi = s < n ? (int64_t)skeys[s] : (int64_t)n_cells;
+    const int64_t lo = s > 0 ? (int64_t)skeys[s - 1] : -1;
+    for (int64_t c = lo + 1; c <= hi && c <= n_cells; ++c) cell_start[c] = (int32_t)s;
+  }
+}
+
+static int radix_passes(int32_t n_cells) {
+  int bits = 1;
+  while (bits < 31 && ((int64_t)1 << bits) <= (int64_t)n_cells) ++bits;  // keys up to n_cells
+  return (bits + kRadixBits - 1) / kRadixBits;
+}
+
 size_t sort_ws(int32_t n, int32_t n_cells) {
-  return align256(sizeof(int32_t) * (size_t)(n_cells > 0 ? n_cells : 1)) +
-         align256(sizeof(int32_t) * (size_t)(n > 0 ? n : 1)) + scan_ws(n_cells);
+  const size_t nn = (size_t)(n > 0 ? n : 1);
+  const size_t chunks = (nn + kRsChunk - 1) / kRsChunk;
+  const size_t tab = (size_t)kRadix * chunks;
+  return 4 * align256(sizeof(uint32_t) * nn)        // keys and values, two buffers each
+         + 2 * align256(sizeof(int32_t) * (tab + 1)) // digit counts and their scan
+         + scan_ws((int64_t)tab);
 }
 
 static unsigned grid_for(int64_t work, int per_block, int max_blocks) {
@@ -206,25 +301,43 @@ int launch_sort(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_id, cons
                 double* svx, double* svy, double* svz, void* ws, size_t ws_bytes,
                 cudaStream_t s) {
   if (ws_bytes < sort_ws(n, n_cells)) return record(c, DSMC_ERR_ARG, "sort: workspace too small");
+  const size_t nn = (size_t)(n > 0 ? n : 1);
+  const int32_t chunks = (int32_t)((nn + kRsChunk - 1) / kRsChunk);
+  const size_t tab = (size_t)kRadix * chunks;
   char* p = (char*)ws;
-  int32_t* counts = (int32_t*)p;
-  p += align256(sizeof(int32_t) * (size_t)(n_cells > 0 ? n_cells : 1));
-  int32_t* slots = (int32_t*)p;
-  p += align256(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  auto take = [&](size_t bytes) { char* q = p; p += align256(bytes); return q; };
+  uint32_t* ka = (uint32_t*)take(4 * nn);
+  int32_t* va = (int32_t*)take(4 * nn);
+  uint32_t* kb = (uint32_t*)take(4 * nn);
+  int32_t* vb = (int32_t*)take(4 * nn);
+  int32_t* cnt = (int32_t*)take(4 * (tab + 1));
+  int32_t* off = (int32_t*)take(4 * (tab + 1));
   void* sws = p;
-  const int sms = sm_count(c);
-  if (cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)n_cells, s) != cudaSuccess)
-    return DSMC_ERR_CUDA;
-  if (n > 0) { k_hist<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(cell_id, n, n_cells, counts, status_ptr(c)); count_launches(c, 1); }
-  int rc = launch_scan(c, counts, cell_start, n_cells, sws, s);
-  if (rc) return rc;
-  if (n == 0) return 0;
-  if (cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)n_cells, s) != cudaSuccess)
-    return DSMC_ERR_CUDA;
-  k_scatter<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(cell_id, n, n_cells, cell_start, counts, slots);
-  k_fix_gather<<<grid_for(n_cells, kFixWarps, sms * 4), kFixWarps * 32, 0, s>>>(
-      n_cells, cell_start, slots, perm, vx, vy, vz, svx, svy, svz);
-  count_launches(c, 2);
+  if (n == 0) {
+    k_cell_start<<<1, 256, 0, s>>>(kb, 0, n_cells, cell_start);
+    count_launches(c, 1);
+    return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
+  }
+  const int passes = radix_passes(n_cells);
+  const uint32_t* kin = nullptr;   // first pass: keys from cell_id
+  const int32_t* vin = nullptr;    // first pass: values = input index
+  for (int q = 0; q < passes; ++q) {
+    const bool last = q + 1 == passes;
+    uint32_t* kout = (q & 1) ? kb : ka;
+    int32_t* vout = last ? perm : ((q & 1) ? vb : va);
+    k_rs_count<<<chunks, 256, 0, s>>>(cell_id, kin, n, n_cells, q * kRadixBits, chunks, cnt,
+                                      q == 0 ? status_ptr(c) : nullptr);
+    count_launches(c, 1);
+    int rc = launch_scan(c, cnt, off, (int64_t)tab, sws, s);
+    if (rc) return rc;
+    k_rs_scatter<<<chunks, kRsWarps * 32, 0, s>>>(cell_id, kin, vin, n, n_cells, q * kRadixBits, chunks, off,
+                                                  kout, vout);
+    count_launches(c, 1);
+    kin = kout;
+    vin = vout;
+  }
+  k_cell_start<<<grid_for((int64_t)n + 1, 256, sm_count(c) * 8), 256, 0, s>>>(kin, n, n_cells, cell_start);
+  count_launches(c, 1);
   return launch_gather(c, n, n_cells, cell_start, perm, vx, vy, vz, svx, svy, svz, s);
 }
 
