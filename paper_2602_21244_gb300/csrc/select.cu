@@ -299,24 +299,51 @@ __global__ void __launch_bounds__(kEmitWarps * 32) k_sel_emit(SelArgs a) {
     }
     __syncwarp();
     // rounds in candidate order: round = 1 + max(last round of i, of j)
-    if (lane == 0) {
+    if (local) {
+      // Warp-parallel: in each batch of 32 pairs (candidate order), a lane
+      // commits once it is the lowest uncommitted lane of the batch touching
+      // each of its two particles (atomicMin claims), so every earlier pair
+      // sharing a particle has already updated `last`; lanes committing
+      // together share no particle.  Same rounds as the sequential rule.
+      uint16_t* last = slast[wid];
+      int* claim = (int*)stage[wid];   // the velocity staging is no longer needed
+      for (int32_t t = lane; t < N; t += 32) claim[t] = 32;
+      __syncwarp();
       int rm = -1;
-      if (local) {
-        uint16_t* last = slast[wid];
-        for (int32_t p = p0; p < p1; ++p) {
-          const uint32_t ij = spairs[wid][p - p0];
-          const uint32_t i = ij & 0xFFFFu, j = ij >> 16;
-          const int li = last[i], lj = last[j];            // stored as round + 1
-          int r = li > lj ? li : lj;                        // = 1 + max(round) in 0-based rounds
-          if (r >= DSMC_MAX_ROUNDS) { set_status(a.status, DSMC_ERR_UNSUPPORTED); r = DSMC_MAX_ROUNDS - 1; }
-          last[i] = (uint16_t)(r + 1);
-          last[j] = (uint16_t)(r + 1);
-          a.tmp_round[p] = r;
-          a.tmp_dep[p] = (uint32_t)li | ((uint32_t)lj << 16);
-          atomicAdd(&hist[r], 1);
-          rm = r > rm ? r : rm;
+      for (int32_t b0 = p0; b0 < p1; b0 += 32) {
+        const int32_t p = b0 + lane;
+        bool done = p >= p1;
+        const uint32_t ij = done ? 0u : spairs[wid][p - p0];
+        const uint32_t i = ij & 0xFFFFu, j = ij >> 16;
+        while (__any_sync(0xffffffffu, !done)) {
+          if (!done) { atomicMin(&claim[i], lane); atomicMin(&claim[j], lane); }
+          __syncwarp();
+          const bool go = !done && claim[i] == lane && claim[j] == lane;
+          if (go) {
+            const int li = last[i], lj = last[j];            // stored as round + 1
+            int r = li > lj ? li : lj;                        // = 1 + max(round) in 0-based rounds
+            if (r >= DSMC_MAX_ROUNDS) { set_status(a.status, DSMC_ERR_UNSUPPORTED); r = DSMC_MAX_ROUNDS - 1; }
+            last[i] = (uint16_t)(r + 1);
+            last[j] = (uint16_t)(r + 1);
+            a.tmp_round[p] = r;
+            a.tmp_dep[p] = (uint32_t)li | ((uint32_t)lj << 16);
+            atomicAdd(&hist[r], 1);
+            rm = r > rm ? r : rm;
+          }
+          __syncwarp();
+          if (!done) { claim[i] = 32; claim[j] = 32; }
+          done = done || go;
+          __syncwarp();
         }
-      } else {
+      }
+      rm = __reduce_max_sync(0xffffffffu, rm);
+      if (lane == 0) {
+        atomicMax(&rmax_blk, rm + 1);
+        a.sgmax[k] = a.sgnew[k];
+      }
+    } else if (lane == 0) {
+      int rm = -1;
+      {
         for (int32_t p = p0; p < p1; ++p) {
           const int4 q = a.tmp[p];
           const int li = a.last[q.x], lj = a.last[q.y];
