@@ -41,7 +41,7 @@ constexpr int kStashCols = 16;   // per-row pair data handed from builder to upd
 // `slots` tile slots (one per warp group) has its own X, activation tiles,
 // mbarrier and flag.
 struct MlpLayout {
-  uint32_t w_out, w_in, w_sq, slot0, slot_bytes, bias, mbar, tptr, flag, claim, fail, total;
+  uint32_t w_out, w_in, w_sq, slot0, slot_bytes, bias, ybuf, ybuf_bytes, mbar, tptr, flag, claim, fail, total;
   int slots;
   __host__ __device__ uint32_t x(int g) const { return slot0 + (uint32_t)g * slot_bytes; }
   __host__ __device__ uint32_t h(int g) const { return x(g) + kTileM * kKin * 2; }
@@ -53,13 +53,16 @@ constexpr uint32_t kMaxSmem = 232448 - 1024;  // 227 KB opt-in per CTA, less the
 __host__ __device__ inline MlpLayout mlp_layout(int n_hidden, int slots) {
   MlpLayout L;
   L.slots = slots;
-  L.w_out = 0;                                        // [16 x 128]
-  L.w_in = L.w_out + kNout * kWidth * 2;              // [128 x 32] = [W1 | W1]
+  L.w_out = 0;                                        // FP32 [3 x 128] output layer
+  L.w_in = L.w_out + 3 * kWidth * 4;                  // [128 x 32] = [W1 | W1]
   L.w_sq = L.w_in + kWidth * kKin * 2;                // (n_hidden-1) x [128 x 128]
   L.slot0 = L.w_sq + (uint32_t)(n_hidden - 1) * kWidth * kWidth * 2;
   L.slot_bytes = kTileM * kKin * 2 + 2 * kTileM * kWidth * 2;  // X [128 x 32], hi and lo [128 x 128]
   L.bias = L.slot0 + (uint32_t)slots * L.slot_bytes;  // floats: n_hidden*128 + 16
-  L.mbar = L.bias + (uint32_t)(n_hidden * kWidth + kNout) * 4;
+  // per slot: partial outputs of the column groups other than the first
+  L.ybuf = L.bias + (uint32_t)(n_hidden * kWidth + kNout) * 4;
+  L.ybuf_bytes = (uint32_t)(kThreads / slots / kTileM - 1) * kTileM * 3 * 4;
+  L.mbar = L.ybuf + (uint32_t)slots * L.ybuf_bytes;
   L.mbar = (L.mbar + 15u) & ~15u;                     // slots x 8 bytes
   L.tptr = L.mbar + 16;
   L.flag = L.tptr + 4;                                // slots x 4 bytes: mbarrier wait result
@@ -83,8 +86,8 @@ struct MlpShape {
 __device__ void load_weights(char* smem, const MlpLayout& L, const MlpShape& sh,
                              const uint16_t* __restrict__ w, const float* __restrict__ bias) {
   const int t = threadIdx.x, nt = blockDim.x;
-  uint32_t* z = (uint32_t*)(smem + L.w_out);
-  for (int q = t; q < (kNout * kWidth * 2 + kWidth * kKin * 2) / 4; q += nt) z[q] = 0u;
+  uint32_t* z = (uint32_t*)(smem + L.w_in);
+  for (int q = t; q < (kWidth * kKin * 2) / 4; q += nt) z[q] = 0u;
   __syncthreads();
   // layer 0: [128 x d_in], stored twice (columns k and 16 + k) so that the
   // two bf16 terms of the input share the weights
@@ -102,10 +105,9 @@ __device__ void load_weights(char* smem, const MlpLayout& L, const MlpShape& sh,
     }
     wl += kWidth * kWidth;
   }
-  for (int e = t; e < 3 * kWidth; e += nt) {
-    const int n = e >> 7, k = e & 127;
-    *(uint16_t*)(smem + L.w_out + tc::kmajor_offset(n, k, kWidth)) = wl[e];
-  }
+  // output layer in FP32 [3 x 128] for the CUDA-core dot products
+  float* wo = (float*)(smem + L.w_out);
+  for (int e = t; e < 3 * kWidth; e += nt) wo[e] = __uint_as_float((uint32_t)wl[e] << 16);
   float* bs = (float*)(smem + L.bias);
   for (int e = t; e < sh.n_hidden * kWidth; e += nt) bs[e] = bias[e];
   for (int e = t; e < kNout; e += nt) bs[sh.n_hidden * kWidth + e] = e < 3 ? bias[sh.n_hidden * kWidth + e] : 0.f;
@@ -161,9 +163,14 @@ __device__ __forceinline__ void group_sync(const Group& q) {
 // (status recorded); y receives the output row (+ bias) of group thread q.t
 // for q.t < 128.  Rows: warp w of the group reads TMEM lanes 32 (w % 4) ..
 // +31, i.e. row = 32 (w % 4) + lane; the columns of a hidden layer are split
-// over the group's warps that share a lane group.
+// over the group's warps that share a lane group.  The hidden layers run on
+// the tensor cores; the 3-wide output layer is a dot product on the CUDA
+// cores inside the last hidden layer's epilogue (FP32 activations times the
+// bf16 weights, summed in FP32), its column-group partials combined through
+// shared memory -- no tensor-core pass, barrier and TMEM read for 3 outputs.
 __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, const Group& q,
-                         uint32_t tmem, uint32_t& phase, float y[3], int* status) {
+                         uint32_t tmem, uint32_t& phase, float y[3], int* status,
+                         unsigned* cursor = nullptr, volatile int* claim = nullptr) {
   const int gw = q.t >> 5;
   const int row = ((gw & 3) << 5) | (q.t & 31);
   const int cgroups = q.nthr / kTileM, cg = gw >> 2;
@@ -175,7 +182,9 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
   const uint32_t acc = tmem + (uint32_t)(q.g * kWidth);
   const uint32_t lane_tm = acc + ((uint32_t)((gw & 3) * 32) << 16);
   const float* bs = (const float*)(smem + L.bias);
-  for (int l = 0; l <= sh.n_hidden; ++l) {
+  const float* wo = (const float*)(smem + L.w_out);
+  float yp0 = 0.f, yp1 = 0.f, yp2 = 0.f;
+  for (int l = 0; l < sh.n_hidden; ++l) {
     if (q.t == 0) {
       tc::fence_after();
       if (l == 0) {
@@ -185,8 +194,8 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
                        tc::sdesc(sbase + L.w_in + 256u * s, 128, kKin * 16),
                        tc::idesc_bf16(kTileM, kWidth), s > 0);
       } else {
-        const uint32_t wb = l < sh.n_hidden ? L.w_sq + (uint32_t)(l - 1) * kWidth * kWidth * 2 : L.w_out;
-        const uint32_t idesc = l < sh.n_hidden ? tc::idesc_bf16(kTileM, kWidth) : tc::idesc_bf16(kTileM, kNout);
+        const uint32_t wb = L.w_sq + (uint32_t)(l - 1) * kWidth * kWidth * 2;
+        const uint32_t idesc = tc::idesc_bf16(kTileM, kWidth);
         // activations enter as hi + lo bf16 terms against the same weights
 #pragma unroll
         for (int s = 0; s < kWidth / 16; ++s)
@@ -198,56 +207,89 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
                        tc::sdesc(sbase + wb + 256u * s, 128, 2048), idesc, 1);
       }
       tc::commit(mbar);
+      if (l == 0 && cursor) *claim = (int)atomicAdd(cursor, 1u);
       *flag = tc::mbar_wait(mbar, phase, status, kBarrierLimitNs) ? 1 : 0;
     }
     group_sync(q);
     if (!*flag) return false;
     phase ^= 1u;
     tc::fence_after();
-    if (l < sh.n_hidden) {
-      const float* bl = bs + l * kWidth;
+    const float* bl = bs + l * kWidth;
+    const bool last = l == sh.n_hidden - 1;
+    // this warp's columns in 16-wide pieces, the TMEM read of the next piece
+    // in flight while the current one is processed
+    const int cbeg = cg * cols, npieces = cols / 16;
+    uint32_t ra[16], rb[16];
+    tc::ld16_async(lane_tm + (uint32_t)cbeg, ra);
+    tc::wait_ld16(ra);
 #pragma unroll 1
-      for (int c0 = cg * cols; c0 < (cg + 1) * cols; c0 += 32) {
-        float v[32];
-        tc::ld32(lane_tm + (uint32_t)c0, v);
+    for (int pc = 0; pc < npieces; pc += 2) {
 #pragma unroll
-        for (int k = 0; k < 32; ++k) v[k] += bl[c0 + k];
+      for (int half = 0; half < 2; ++half) {
+        uint32_t* cur = half ? rb : ra;
+        uint32_t* nxt = half ? ra : rb;
+        const int c0 = cbeg + 16 * (pc + half);
+        const bool more = pc + half + 1 < npieces;
+        if (more) tc::ld16_async(lane_tm + (uint32_t)(c0 + 16), nxt);
+        float v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(cur[k]) + bl[c0 + k];
         if (sh.act == 0) {
 #pragma unroll
-          for (int k = 0; k < 32; k += 4) silu4(v + k);
+          for (int k = 0; k < 16; k += 4) silu4(v + k);
         } else {
 #pragma unroll
-          for (int k = 0; k < 32; ++k) v[k] = act_f(sh.act, v[k]);
+          for (int k = 0; k < 16; ++k) v[k] = act_f(sh.act, v[k]);
         }
-        uint32_t pk[16], lo[16];
+        if (last) {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const float a0 = v[2 * k], a1 = v[2 * k + 1];
-          pk[k] = tc::pack_bf16x2(a0, a1);
-          lo[k] = tc::pack_bf16x2(a0 - __uint_as_float(pk[k] << 16), a1 - __uint_as_float(pk[k] & 0xFFFF0000u));
-        }
+          for (int k = 0; k < 16; ++k) {
+            yp0 = fmaf(v[k], wo[c0 + k], yp0);
+            yp1 = fmaf(v[k], wo[kWidth + c0 + k], yp1);
+            yp2 = fmaf(v[k], wo[2 * kWidth + c0 + k], yp2);
+          }
+        } else {
+          uint32_t pk[8], lo[8];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const uint32_t off = tc::kmajor_offset(row, c0 + 8 * j, kWidth);
-          tc::st_shared_v4(sbase + hs + off, pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
-          tc::st_shared_v4(sbase + hls + off, lo[4 * j], lo[4 * j + 1], lo[4 * j + 2], lo[4 * j + 3]);
+          for (int k = 0; k < 8; ++k) {
+            const float a0 = v[2 * k], a1 = v[2 * k + 1];
+            pk[k] = tc::pack_bf16x2(a0, a1);
+            lo[k] = tc::pack_bf16x2(a0 - __uint_as_float(pk[k] << 16), a1 - __uint_as_float(pk[k] & 0xFFFF0000u));
+          }
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const uint32_t off = tc::kmajor_offset(row, c0 + 8 * j, kWidth);
+            tc::st_shared_v4(sbase + hs + off, pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+            tc::st_shared_v4(sbase + hls + off, lo[4 * j], lo[4 * j + 1], lo[4 * j + 2], lo[4 * j + 3]);
+          }
         }
+        if (more) tc::wait_ld16(nxt);
       }
+    }
+    if (!last) {
       tc::fence_before();
       tc::fence_async_smem();
       group_sync(q);
-    } else {
-      if (cg == 0) {
-        float v[16];
-        tc::ld16(lane_tm, v);
-        const float* bo = bs + sh.n_hidden * kWidth;
-        y[0] = v[0] + bo[0];
-        y[1] = v[1] + bo[1];
-        y[2] = v[2] + bo[2];
-      }
-      tc::fence_before();
-      group_sync(q);
     }
+  }
+  // combine the column groups' partial outputs (column group 0 = the updaters)
+  float* yb = (float*)(smem + L.ybuf + (uint32_t)q.g * L.ybuf_bytes);
+  if (cg > 0) {
+    float* d = yb + ((cg - 1) * kTileM + row) * 3;
+    d[0] = yp0; d[1] = yp1; d[2] = yp2;
+  }
+  tc::fence_before();
+  group_sync(q);
+  if (cg == 0) {
+    const float* bo = bs + sh.n_hidden * kWidth;
+    float s0 = yp0, s1 = yp1, s2 = yp2;
+    for (int g2 = 1; g2 < cgroups; ++g2) {
+      const float* d = yb + ((g2 - 1) * kTileM + row) * 3;
+      s0 += d[0]; s1 += d[1]; s2 += d[2];
+    }
+    y[0] = s0 + bo[0];
+    y[1] = s1 + bo[1];
+    y[2] = s2 + bo[2];
   }
   return true;
 }
@@ -565,9 +607,10 @@ __global__ void __launch_bounds__(kThreads) k_collide_neural(MlpShape sh, const 
   }
   uint32_t buf = 0;
   while (have) {
-    if (t == 0) *claim = (int)atomicAdd(a.bar + 3, 1u);  // read after the tile's barriers
     float y[3];
-    if (!mlp_tile(smem, L, sh, gq, tmem, phase, y, a.status)) break;
+    // the leader claims the next unit while the first layer's MMA runs (read
+    // after the tile's barriers)
+    if (!mlp_tile(smem, L, sh, gq, tmem, phase, y, a.status, a.bar + 3, claim)) break;
     int32_t n0 = 0, n1 = 0;
     const bool have_next = unit_range(a.ro, R, kTileM, r, base, (unsigned)*claim, &n0, &n1);
     if (builder && have_next) {
