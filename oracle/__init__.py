@@ -97,6 +97,9 @@ def lib():
             "or_collide_neural": (None, [P(Gas), P(Mlp), vp, vp, vp, i64, vp, vp, vp, vp, u64,
                                          C.c_int, vp, vp, vp, vp]),
             "or_harvest_jager": (None, [P(Gas), P(Pot), i64, vp, vp, vp, vp, vp, vp]),
+            "or_chi_table": (None, [P(Pot), d, i32, i32, d, d, vp]),
+            "or_chi_lookup": (d, [vp, i32, i32, d, d, d, d]),
+            "or_collide_table": (None, [P(Gas), vp, i32, i32, d, d, i64, vp, vp, vp, vp, u64, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -280,6 +283,33 @@ def collide_jager(gas: Gas, pot: Pot, pairs: dict, step, vx, vy, vz, want_chi=Fa
     lib().or_collide_jager(C.byref(gas), C.byref(pot), pairs["n_pairs"], _p(pairs["i"]),
                            _p(pairs["j"]), _p(pairs["cell"]), _p(pairs["m"]), step,
                            _p(vx), _p(vy), _p(vz), _p(chi_out))
+    if want_chi:
+        return vx, vy, vz, chi_out[:pairs["n_pairs"]]
+    return vx, vy, vz
+
+
+def chi_table(pot: Pot, bmax_A: float, nb: int, nE: int, lnE_min: float, lnE_max: float) -> np.ndarray:
+    """[nE x nb] table of chi on the uniform (b/b_max, ln E) grid (FP64)."""
+    out = np.zeros((nE, nb))
+    lib().or_chi_table(C.byref(pot), bmax_A, nb, nE, lnE_min, lnE_max, _p(out))
+    return out
+
+
+def chi_lookup(table, lnE_min: float, lnE_max: float, bt: float, lnE: float) -> float:
+    t = np.ascontiguousarray(table, dtype=np.float32)
+    nE, nb = t.shape
+    return lib().or_chi_lookup(_p(t), nb, nE, lnE_min, lnE_max, bt, lnE)
+
+
+def collide_table(gas: Gas, table, lnE_min: float, lnE_max: float, pairs: dict, step, vx, vy, vz,
+                  want_chi=False):
+    t = np.ascontiguousarray(table, dtype=np.float32)
+    nE, nb = t.shape
+    vx, vy, vz = _f64(vx).copy(), _f64(vy).copy(), _f64(vz).copy()
+    chi_out = np.zeros(max(pairs["n_pairs"], 1))
+    lib().or_collide_table(C.byref(gas), _p(t), nb, nE, lnE_min, lnE_max, pairs["n_pairs"], _p(pairs["i"]),
+                           _p(pairs["j"]), _p(pairs["cell"]), _p(pairs["m"]), step, _p(vx), _p(vy), _p(vz),
+                           _p(chi_out))
     if want_chi:
         return vx, vy, vz, chi_out[:pairs["n_pairs"]]
     return vx, vy, vz

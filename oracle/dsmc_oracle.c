@@ -24,6 +24,7 @@
  *   Sec. 3.4.1 Eq. (jager_potential), Eq. (damping), screened Coulomb core
  *   Sec. 3.4.2 classical scattering integral chi(b, E_r)
  *   Sec. 3.4.4 r_min = largest root, Brent-Dekker to 1e-14, u = r_min/r
+ *   Sec. 3.4.5 look-up table over (b/b_max, ln E_r/k_B), bilinear interpolation
  *
  * Readings where the paper is silent (all listed in the design notes):
  *   R1  Philox4x32-10 (Salmon et al., SC'11) keyed by seed, counter
@@ -39,6 +40,9 @@
  *       when the cell mean velocity is zero.
  *   R6  energy-shell projection divides by ||y|| (not ||y||+eps) so the pair
  *       energy is exact; ||y|| <= eps falls back to an isotropic direction.
+ *   R7  the chi table of the look-up path (Sec. 3.4.5: b~ = b/b_max,
+ *       E~ = ln(E_r/k_B), bilinear interpolation) has uniform nodes including
+ *       both ends of each axis; E~ outside the table is clamped to it.
  */
 #include <math.h>
 #include <stdint.h>
@@ -550,6 +554,63 @@ void or_collide_jager(const or_gas_t* gs, const or_pot_t* P, int64_t n_pairs,
     double b = bmax_A * sqrt(or_u53(w[0], w[1]));
     double eps = 2.0 * OR_PI * or_u53(w[2], w[3]);
     double chi = g > 0.0 ? or_chi(P, b, e_kelvin(gs, g)) : 0.0;
+    if (chi_out) chi_out[p] = chi;
+    double vrp[3];
+    if (g > 0.0) or_deflect(vr, chi, eps, vrp); else { vrp[0] = vrp[1] = vrp[2] = 0.0; }
+    pair_update(vx, vy, vz, i, j, vrp);
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 3.4.5 (look-up strategy): chi table and collision by look-up    */
+/* ------------------------------------------------------------------ */
+/* The table of the paper's look-up path, filled here by the exact chi: a
+ * uniform grid in b~ = b/b_max over [0, 1] (nb nodes) and in E~ = ln(E_r/k_B)
+ * over [lnE_min, lnE_max] (nE nodes), T[j nb + i] = chi(b_max i/(nb-1),
+ * exp(lnE_min + j (lnE_max - lnE_min)/(nE-1))) (reading R7). */
+void or_chi_table(const or_pot_t* P, double bmax_A, int32_t nb, int32_t nE, double lnE_min,
+                  double lnE_max, double* T) {
+  for (int32_t j = 0; j < nE; ++j) {
+    const double E = exp(lnE_min + j * (lnE_max - lnE_min) / (nE - 1));
+    for (int32_t i = 0; i < nb; ++i) T[(int64_t)j * nb + i] = or_chi(P, bmax_A * i / (nb - 1), E);
+  }
+}
+
+/* Bilinear interpolation in that table at (b~, E~); E~ outside the table's
+ * range is clamped to it (reading R7). */
+double or_chi_lookup(const float* T, int32_t nb, int32_t nE, double lnE_min, double lnE_max, double bt,
+                     double lnE) {
+  double x = bt * (nb - 1);
+  if (x < 0.0) x = 0.0;
+  if (x > nb - 1) x = nb - 1;
+  double y = (lnE - lnE_min) / (lnE_max - lnE_min) * (nE - 1);
+  if (y < 0.0) y = 0.0;
+  if (y > nE - 1) y = nE - 1;
+  int32_t i0 = (int32_t)floor(x), j0 = (int32_t)floor(y);
+  if (i0 > nb - 2) i0 = nb - 2;
+  if (j0 > nE - 2) j0 = nE - 2;
+  const double fx = x - i0, fy = y - j0;
+  const double t00 = T[(int64_t)j0 * nb + i0], t01 = T[(int64_t)j0 * nb + i0 + 1];
+  const double t10 = T[(int64_t)(j0 + 1) * nb + i0], t11 = T[(int64_t)(j0 + 1) * nb + i0 + 1];
+  return (1.0 - fy) * ((1.0 - fx) * t00 + fx * t01) + fy * ((1.0 - fx) * t10 + fx * t11);
+}
+
+/* Pair update with chi from the table: b~ = sqrt(U1), eps = 2 pi U2 (tag 4,
+ * as the Jager path), E~ = ln(m g^2/(4 k_B)); rotation and centre-of-mass
+ * update as or_collide_jager; pairs in order. */
+void or_collide_table(const or_gas_t* gs, const float* T, int32_t nb, int32_t nE, double lnE_min,
+                      double lnE_max, int64_t n_pairs, const int32_t* pi, const int32_t* pj,
+                      const int32_t* pcell, const int32_t* pm, uint64_t step, double* vx, double* vy,
+                      double* vz, double* chi_out) {
+  for (int64_t p = 0; p < n_pairs; ++p) {
+    int32_t i = pi[p], j = pj[p];
+    double vr[3] = {vx[i] - vx[j], vy[i] - vy[j], vz[i] - vz[j]};
+    double g = sqrt((vr[0] * vr[0] + vr[1] * vr[1]) + vr[2] * vr[2]);
+    uint32_t w[4];
+    draw(gs->seed, (uint32_t)pm[p], (uint32_t)pcell[p], step, OR_TAG_JAGER, 0, w);
+    double bt = sqrt(or_u53(w[0], w[1]));
+    double eps = 2.0 * OR_PI * or_u53(w[2], w[3]);
+    double chi = g > 0.0 ? or_chi_lookup(T, nb, nE, lnE_min, lnE_max, bt, log(e_kelvin(gs, g))) : 0.0;
     if (chi_out) chi_out[p] = chi;
     double vrp[3];
     if (g > 0.0) or_deflect(vr, chi, eps, vrp); else { vrp[0] = vrp[1] = vrp[2] = 0.0; }

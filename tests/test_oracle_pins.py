@@ -565,3 +565,76 @@ def test_adam_matches_torch():
         p.grad = torch.tensor(g)
         opt.step()
     np.testing.assert_allclose(th, p.detach().numpy(), rtol=1e-12, atol=1e-14)
+
+
+# ------------------------------------------------------------------ look-up table (Sec. 3.4.5)
+
+def test_chi_table_nodes_hard_sphere_closed_form():
+    """Table nodes: b = b_max i/(nb-1) and E = exp(lnE_min + j dE); the hard
+    sphere's chi = 2 arccos(b/d) for b < d, independent of E, pins both maps."""
+    hs = O.make_pot(W.HARD_SPHERE_AR)
+    nb, nE, bmax = 13, 5, 6.0
+    T = O.chi_table(hs, bmax, nb, nE, math.log(5.0), math.log(6e4))
+    for j in range(nE):
+        for i in range(nb):
+            b = bmax * i / (nb - 1)
+            want = 2 * math.acos(b / 3.6) if b < 3.6 else 0.0
+            assert abs(T[j, i] - want) < 1e-12
+
+
+def test_chi_table_energy_axis_coulomb_closed_form():
+    """The energy axis: Coulomb chi = 2 atan(kappa/(2 E b)) at each node."""
+    P = O.make_pot(dict(kind=2, kappa=500.0, p=1.0))
+    nb, nE, bmax, lo, hi = 5, 7, 8.0, math.log(10.0), math.log(1e4)
+    T = O.chi_table(P, bmax, nb, nE, lo, hi)
+    for j in range(nE):
+        E = math.exp(lo + j * (hi - lo) / (nE - 1))
+        for i in range(1, nb):
+            b = bmax * i / (nb - 1)
+            assert abs(T[j, i] - 2 * math.atan(500.0 / (2 * E * b))) < 1e-12
+
+
+def test_chi_lookup_is_bilinear():
+    """Bilinear interpolation reproduces a bilinear function of the grid
+    coordinates exactly, returns node values at nodes, and clamps ln E."""
+    nb, nE, lo, hi = 9, 6, 1.0, 4.0
+    jj, ii = np.meshgrid(np.arange(nE), np.arange(nb), indexing="ij")
+    T = (1.0 + 2.0 * ii + 3.0 * jj + 0.5 * ii * jj).astype(np.float32)   # exact in float
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        bt, lnE = rng.random(), lo + (hi - lo) * rng.random()
+        x, y = bt * (nb - 1), (lnE - lo) / (hi - lo) * (nE - 1)
+        assert abs(O.chi_lookup(T, lo, hi, bt, lnE) - (1 + 2 * x + 3 * y + 0.5 * x * y)) < 1e-12
+    assert O.chi_lookup(T, lo, hi, 0.5, lo) == T[0, 4]
+    assert O.chi_lookup(T, lo, hi, 1.0, hi) == T[-1, -1]
+    assert O.chi_lookup(T, lo, hi, 0.25, lo - 5.0) == O.chi_lookup(T, lo, hi, 0.25, lo)
+    assert O.chi_lookup(T, lo, hi, 0.25, hi + 5.0) == O.chi_lookup(T, lo, hi, 0.25, hi)
+
+
+def test_collide_table_with_constant_chi_is_the_rotation():
+    """A table holding one angle everywhere: every pair is the Bird rotation
+    by that angle (checked against or_deflect), energy and momentum kept."""
+    w = W.couette()
+    gas = O.make_gas(**dict(w["gas"], model=1))
+    perm, cs, sx, sy, sz = O.sort_cells(w["cell_id"], w["vx"], w["vy"], w["vz"], w["n_cells"])
+    sg = O.sigma_g_max_init(gas, w["T_cell"], 5.0)
+    pr = O.select_pairs(gas, cs, sx, sy, sz, sg, 2, capacity=1 << 16)
+    T = np.full((4, 4), 0.7, np.float32)
+    vx, vy, vz, chi = O.collide_table(gas, T, 0.0, 10.0, pr, 2, sx, sy, sz, want_chi=True)
+    assert np.all(chi == np.float32(0.7))
+    e0 = np.sum(sx ** 2 + sy ** 2 + sz ** 2)
+    assert abs(np.sum(vx ** 2 + vy ** 2 + vz ** 2) / e0 - 1) < 1e-13
+    assert abs(np.sum(vx) - np.sum(sx)) < 1e-9 * np.abs(sx).sum()
+    # the first pair of the step sees the input velocities: rotation by 0.7
+    p0 = 0
+    i, j = pr["i"][p0], pr["j"][p0]
+    vr = np.array([sx[i] - sx[j], sy[i] - sy[j], sz[i] - sz[j]])
+    g = np.linalg.norm(vr)
+    assert g > 0
+    vrp_out = np.array([vx[i] - vx[j], vy[i] - vy[j], vz[i] - vz[j]])
+    # the rotated vector keeps |v_r| and makes the angle 0.7 with v_r (if i, j
+    # take part in no later pair of the step)
+    later = np.concatenate([pr["i"][1:], pr["j"][1:]])
+    if i not in later and j not in later:
+        assert abs(np.linalg.norm(vrp_out) - g) < 1e-10 * g
+        assert abs(np.dot(vr, vrp_out) / g ** 2 - math.cos(float(np.float32(0.7)))) < 1e-12
