@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the gas (tests)")
-    ap.add_argument("--paths", default="neural,jager,vhs")
+    ap.add_argument("--paths", default="neural,jager,table,vhs")
     ap.add_argument("--n-nodes", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -140,10 +140,27 @@ def run_gb300(args, rank, world, dist):
 
     results = {}
     neural_kernel = None
+    # the look-up path's table (Sec. 3.4.5): 512 x 512 nodes over b/b_max and
+    # ln(E_r/k_B) in [ln 5, ln 6e4], filled with the exact chi (128 nodes)
+    table, table_info = None, None
+    if "table" in args.paths.split(","):
+        gas_t = D.make_gas(dict(wl["gas"], model=1))
+        tab_args = dict(nb=512, nE=512, lnE_min=math.log(5.0), lnE_max=math.log(6.0e4), n_nodes=128)
+        table = C.chi_table_build(gas_t, pot, **tab_args)  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        table = C.chi_table_build(gas_t, pot, **tab_args)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        table_info = dict(nodes=[512, 512], n_nodes=128, ms=e0.elapsed_time(e1),
+                          lnE_range=[tab_args["lnE_min"], tab_args["lnE_max"]])
     for path in [p for p in args.paths.split(",") if p]:
         gas = D.make_gas(dict(wl["gas"], model=0 if path == "vhs" else 1))
-        path_d = D.make_path({"vhs": D.PATH_VHS, "jager": D.PATH_JAGER, "neural": D.PATH_NEURAL}[path],
-                             pot=pot, n_nodes=args.n_nodes, mlp=mlp, w_bits=w_bits, bias=bias)
+        path_d = D.make_path({"vhs": D.PATH_VHS, "jager": D.PATH_JAGER, "neural": D.PATH_NEURAL,
+                              "table": D.PATH_TABLE}[path],
+                             pot=pot, n_nodes=args.n_nodes, mlp=mlp, w_bits=w_bits, bias=bias,
+                             table=table if path == "table" else None)
         tuned = None
         if args.autotune:
             # launch shapes of this path's tunable kernels, measured on this gas (untimed)
@@ -180,6 +197,8 @@ def run_gb300(args, rank, world, dist):
                 C.collide_vhs(gas, it, sel, st.svx, st.svy, st.svz)
             elif path == "jager":
                 C.collide_jager(gas, pot, it, sel, st.svx, st.svy, st.svz, n_nodes=args.n_nodes)
+            elif path == "table":
+                C.collide_table(gas, table, it, sel, st.svx, st.svy, st.svz)
             else:
                 C.collide_neural(gas, mlp, w_bits, bias, it, st.mom, sel, st.svx, st.svy, st.svz)
             e[4].record(stream)
@@ -235,6 +254,8 @@ def run_gb300(args, rank, world, dist):
     # ------------------------------------------------------------ standalone kernels
     # Jager deflection-angle batch (2^22 pairs) and the MLP alone (2^22 rows)
     extra = {}
+    if table_info is not None:
+        extra["chi_table"] = table_info
     if args.standalone:
         nb = 1 << 22
         b_np, g_np = W.chi_pairs(nb, seed=0)

@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define DSMC_ABI_VERSION 2
+#define DSMC_ABI_VERSION 3
 
 enum {
   DSMC_OK = 0,
@@ -52,7 +52,7 @@ enum {
 };
 
 /* Update rules of the collision step (Sec. 2.1: only the scattering rule changes). */
-enum { DSMC_PATH_VHS = 0, DSMC_PATH_JAGER = 1, DSMC_PATH_NEURAL = 2 };
+enum { DSMC_PATH_VHS = 0, DSMC_PATH_JAGER = 1, DSMC_PATH_NEURAL = 2, DSMC_PATH_TABLE = 3 };
 
 /* Largest number of conflict-free rounds one step may need (see dsmc_select_pairs). */
 #define DSMC_MAX_ROUNDS 1024
@@ -111,6 +111,16 @@ typedef struct {
   double T_ref;   /* K */
   double eps;     /* projection safeguard on ||y|| (normalised units) */
 } dsmc_mlp_t;
+
+/* Deflection-angle table of the look-up path (Sec. 3.4.5): chi[j nb + i] =
+ * chi(b_max i/(nb-1), exp(lnE_min + j (lnE_max - lnE_min)/(nE-1))), i.e. a
+ * uniform grid in b/b_max over [0, 1] and in ln(E_r/k_B) over [lnE_min,
+ * lnE_max], both ends included.  chi: device memory, FP32. */
+typedef struct {
+  const float* chi;
+  int32_t nb, nE;      /* nodes along b/b_max and along ln E, each 2..4096 */
+  double lnE_min, lnE_max;
+} dsmc_chi_table_t;
 
 /* Written by dsmc_select_pairs (device memory). */
 typedef struct {
@@ -241,8 +251,9 @@ int dsmc_collide_vhs(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, uint64_t step, int3
  *  chi(b, E) = pi - 2 b int_{r_min}^inf dr / (r^2 sqrt(1 - b^2/r^2 - V(r)/E)),
  *  E = E_r/k_B = m g^2/(4 k_B), r_min the largest root of the radicand.
  *  FP32 bracket and quadrature (u = r_min/r, u = 1 - s^2, n_nodes-point
- *  Gauss-Legendre in s, n_nodes in [8, 128]) with an FP64 Newton
- *  refinement of r_min.  Signed: attraction gives chi < 0.
+ *  Gauss-Legendre in s, n_nodes in [8, 128]; min(4 n_nodes, 128) points for
+ *  energies below 1.5 well depths of the Jager form, where near-orbiting
+ *  pairs make the integrand steep) with an FP64 Halley refinement of r_min.  Signed: attraction gives chi < 0.
  *  b in Angstrom, g in m/s, n pairs. */
 int dsmc_jager_chi(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_potential_t* pot,
                    int32_t n_nodes, int64_t n, const float* b, const float* g, float* chi,
@@ -259,6 +270,20 @@ int dsmc_collide_jager(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_potent
                        const uint32_t* deps, const int32_t* round_offsets, const dsmc_select_info_t* info,
                        double* vx, double* vy, double* vz, float* chi_out, void* ws, size_t ws_bytes,
                        void* stream);
+
+/* Sec. 3.4.5: fill a chi table with the exact deflection angle (the
+ * computation of dsmc_jager_chi at every node; b_max from gas->b_max).
+ * table: nE x nb FP32, device memory. */
+int dsmc_chi_table_build(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_potential_t* pot, int32_t n_nodes,
+                         int32_t nb, int32_t nE, double lnE_min, double lnE_max, float* table, void* stream);
+/* Sec. 3.4.5 look-up path: the pair update of dsmc_collide_jager with chi by
+ * bilinear interpolation in `table` at (b/b_max, ln(E_r/k_B)); ln E outside
+ * the table is clamped to its range.  b/b_max = sqrt(U1) and eps = 2 pi U2
+ * from tag 4, as the Jager path.  chi_out (optional) as dsmc_collide_jager. */
+int dsmc_collide_table(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_chi_table_t* table, uint64_t step,
+                       int32_t n, const int32_t* pairs, const uint32_t* deps, const int32_t* round_offsets,
+                       const dsmc_select_info_t* info, double* vx, double* vy, double* vz, float* chi_out,
+                       void* ws, size_t ws_bytes, void* stream);
 
 /* Sec. 2.2-2.3: neural collision operator on the tcgen05 tensor cores.
  *  x as in dsmc_mlp_t (xi: Box-Muller normals from tag 5, subs 0 and 1;
@@ -347,6 +372,7 @@ typedef struct {
   const dsmc_mlp_t* mlp;
   const uint16_t* weights_bf16;
   const float* biases;
+  const dsmc_chi_table_t* table; /* DSMC_PATH_TABLE */
 } dsmc_path_t;
 
 size_t dsmc_step_workspace_size(int32_t n, int32_t n_cells, int64_t capacity);
@@ -382,7 +408,8 @@ enum {
   DSMC_TUNE_COLLIDE_VHS = 3,   /* VHS collide (persistent, cooperative) */
   DSMC_TUNE_COLLIDE_JAGER = 4, /* Jager collide (persistent, cooperative) */
   DSMC_TUNE_JAGER_CHI = 5,     /* chi batch */
-  DSMC_TUNE_KERNELS = 6
+  DSMC_TUNE_COLLIDE_TABLE = 6, /* look-up collide */
+  DSMC_TUNE_KERNELS = 7
 };
 
 /* One launch shape and, from dsmc_autotune_step, its measured time. */

@@ -60,6 +60,7 @@ ShapeInfo shape_info(int k) {
     case DSMC_TUNE_COLLIDE_VHS: return ShapeInfo{256, 0, 256};
     case DSMC_TUNE_COLLIDE_JAGER: return ShapeInfo{128, 0, 128};
     case DSMC_TUNE_JAGER_CHI: return ShapeInfo{128, 64, 128};
+    case DSMC_TUNE_COLLIDE_TABLE: return ShapeInfo{256, 0, 256};
     default: return ShapeInfo{0, 0, 0};
   }
 }
@@ -87,11 +88,13 @@ static int tune_candidates(int k, dsmc_tune_entry_t* out, int cap) {
           if (t * b <= 2048) push(t, b);
       break;
     case DSMC_TUNE_COLLIDE_VHS:
-    case DSMC_TUNE_COLLIDE_JAGER: {
-      const bool vhs = k == DSMC_TUNE_COLLIDE_VHS;
+    case DSMC_TUNE_COLLIDE_JAGER:
+    case DSMC_TUNE_COLLIDE_TABLE: {
+      const bool wide = k != DSMC_TUNE_COLLIDE_JAGER;
       for (int t : {32, 64, 128, 256}) {
-        if (t > shape_info(k).max_threads || (vhs && t < 64)) continue;
-        const int occ = vhs ? occupancy_collide_vhs(t) : occupancy_collide_jager(t);
+        if (t > shape_info(k).max_threads || (wide && t < 64)) continue;
+        const int occ = k == DSMC_TUNE_COLLIDE_VHS ? occupancy_collide_vhs(t)
+                        : k == DSMC_TUNE_COLLIDE_JAGER ? occupancy_collide_jager(t) : occupancy_collide_table(t);
         if (occ < 1) continue;
         push(t, occ > 32 ? 32 : occ);
         if (occ / 2 >= 1) push(t, occ / 2 > 32 ? 32 : occ / 2);
@@ -273,6 +276,35 @@ int dsmc_collide_jager(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_potentia
                                     vy, vz, chi_out, ws, ws_bytes, S(stream));
 }
 
+static int check_table(Ctx* c, const dsmc_chi_table_t* t) {
+  REQUIRE(c, t && t->chi, "null chi table");
+  REQUIRE(c, t->nb >= 2 && t->nb <= 4096 && t->nE >= 2 && t->nE <= 4096, "chi table: nb, nE must be 2..4096");
+  REQUIRE(c, t->lnE_max > t->lnE_min, "chi table: lnE_max must exceed lnE_min");
+  return 0;
+}
+
+int dsmc_chi_table_build(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_potential_t* pot, int32_t n_nodes,
+                         int32_t nb, int32_t nE, double lnE_min, double lnE_max, float* table, void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, gas && gas->mass > 0 && gas->b_max > 0, "chi_table: gas with mass and b_max > 0 required");
+  if (int rc = check_pot(c, pot, n_nodes)) return rc;
+  const dsmc_chi_table_t t{table, nb, nE, lnE_min, lnE_max};
+  if (int rc = check_table(c, &t)) return rc;
+  return dsmc::launch_chi_table(c, *gas, *pot, n_nodes, nb, nE, lnE_min, lnE_max, table, S(stream));
+}
+
+int dsmc_collide_table(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_chi_table_t* table, uint64_t step,
+                       int32_t n, const int32_t* pairs, const uint32_t* deps, const int32_t* round_offsets,
+                       const dsmc_select_info_t* info, double* vx, double* vy, double* vz, float* chi_out,
+                       void* ws, size_t ws_bytes, void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, gas && gas->mass > 0, "collide_table: gas with mass > 0 required");
+  if (int rc = check_table(c, table)) return rc;
+  REQUIRE(c, round_offsets && info && vx && vy && vz && ws && n >= 0, "collide_table: null pointer");
+  return dsmc::launch_collide_table(c, *gas, *table, step, n, pairs, deps, round_offsets, info, vx, vy, vz, chi_out,
+                                    ws, ws_bytes, S(stream));
+}
+
 static int check_mlp(Ctx* c, const dsmc_mlp_t* m) {
   REQUIRE(c, m, "null mlp");
   REQUIRE(c, m->width == 128 && m->d_out == 3 && (m->d_in == 6 || m->d_in == 8) &&
@@ -441,6 +473,10 @@ static int collide_step(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t*
       rc = dsmc_collide_neural(c, gas, path->mlp, path->weights_bf16, path->biases, step, B->mom, B->n,
                                B->pairs, B->deps, B->round_offsets, B->info, B->svx, B->svy, B->svz,
                                nullptr, B->ws, B->ws_bytes, stream);
+      break;
+    case DSMC_PATH_TABLE:
+      rc = dsmc_collide_table(c, gas, path->table, step, B->n, B->pairs, B->deps, B->round_offsets, B->info,
+                              B->svx, B->svy, B->svz, nullptr, B->ws, B->ws_bytes, stream);
       break;
     default:
       return dsmc::record(c, DSMC_ERR_ARG, "step: unknown path");
@@ -687,6 +723,11 @@ int dsmc_autotune_step(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t* 
     rc = tune_kernel(c, DSMC_TUNE_COLLIDE_VHS, reps, s, [&] {
       return dsmc_collide_vhs(c, gas, step, B->n, B->pairs, B->deps, B->round_offsets, B->info, B->svx, B->svy,
                               B->svz, B->ws, B->ws_bytes, stream);
+    }, trials, cap, &nt);
+  if (!rc && path->path == DSMC_PATH_TABLE)
+    rc = tune_kernel(c, DSMC_TUNE_COLLIDE_TABLE, reps, s, [&] {
+      return dsmc_collide_table(c, gas, path->table, step, B->n, B->pairs, B->deps, B->round_offsets, B->info,
+                                B->svx, B->svy, B->svz, nullptr, B->ws, B->ws_bytes, stream);
     }, trials, cap, &nt);
   if (!rc && path->path == DSMC_PATH_JAGER)
     rc = tune_kernel(c, DSMC_TUNE_COLLIDE_JAGER, reps, s, [&] {

@@ -249,6 +249,13 @@ int launch_collide_jager(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& 
                          int n_nodes, uint64_t step, int32_t n, const int32_t* pairs, const uint32_t* deps,
                          const int32_t* ro, const dsmc_select_info_t* info, double* vx, double* vy,
                          double* vz, float* chi_out, void* ws, size_t ws_bytes, cudaStream_t s);
+int launch_chi_table(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& pot, int n_nodes, int32_t nb,
+                     int32_t nE, double lnE_min, double lnE_max, float* T, cudaStream_t s);
+int launch_collide_table(Ctx* c, const dsmc_gas_t& gas, const dsmc_chi_table_t& tab, uint64_t step, int32_t n,
+                         const int32_t* pairs, const uint32_t* deps, const int32_t* ro,
+                         const dsmc_select_info_t* info, double* vx, double* vy, double* vz, float* chi_out,
+                         void* ws, size_t ws_bytes, cudaStream_t s);
+int occupancy_collide_table(int threads);
 int launch_harvest_jager(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& pot,
                          int n_nodes, int64_t n, const double* vi, const double* vj,
                          const double* b, const double* eps, double* vio, double* vjo,

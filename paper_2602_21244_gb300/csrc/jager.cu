@@ -45,7 +45,11 @@ struct PotDev {
   double d_hs, kappa, p;
   float fkappa, fp;
   float mass_over_4k; // E/k_B = mass g^2 / (4 k_B)
-  float s_node[kMaxNodes], w_node[kMaxNodes];
+  // Gauss-Legendre nodes: [0, n_nodes) for every energy, [kMaxNodes,
+  // kMaxNodes + n_low) with more nodes below orbit_E, where near-orbiting
+  // pairs make the integrand steep (n_low = min(4 n_nodes, kMaxNodes))
+  int n_low;
+  float s_node[2 * kMaxNodes], w_node[2 * kMaxNodes];
 };
 
 // ---------------------------------------------------------------- FP64 potential
@@ -290,7 +294,9 @@ __device__ float chi_device(const PotDev& P, float b, float E) {
   double V0d = 0.0;
   if (core) { double dd; V0d = V64(P, rd, &dd); }
   float I = 0.f;
-  for (int q = 0; q < P.n_nodes; ++q) {
+  const bool low = P.kind == 0 && E < P.orbit_E;
+  const int q0 = low ? kMaxNodes : 0, q1 = q0 + (low ? P.n_low : P.n_nodes);
+  for (int q = q0; q < q1; ++q) {
     const float s = P.s_node[q];
     const float w = s * s;          // 1 - u, exact
     const float u = 1.f - w;
@@ -400,6 +406,10 @@ static PotDev make_pot(const dsmc_gas_t& gas, const dsmc_potential_t& p, int n_n
   std::vector<double> x(n_nodes), w(n_nodes);
   gauss_legendre01(n_nodes, x.data(), w.data());
   for (int i = 0; i < n_nodes; ++i) { P.s_node[i] = (float)x[i]; P.w_node[i] = (float)w[i]; }
+  P.n_low = 4 * n_nodes < kMaxNodes ? 4 * n_nodes : kMaxNodes;
+  std::vector<double> xl(P.n_low), wl(P.n_low);
+  gauss_legendre01(P.n_low, xl.data(), wl.data());
+  for (int i = 0; i < P.n_low; ++i) { P.s_node[kMaxNodes + i] = (float)xl[i]; P.w_node[kMaxNodes + i] = (float)wl[i]; }
   return P;
 }
 
@@ -447,6 +457,42 @@ __device__ __forceinline__ void deflect(double u, double v, double w, double g, 
   o[2] = cc * w + g * sc * (ce * cz + se * az);
 }
 
+// The rotation of v_r = (ux, uy, uz) by chi with azimuth eps (Bird 1994,
+// Eq. 2.22) with the direction in FP32 -- chi itself carries FP32 accuracy
+// -- then scaled in FP64 to |v_r'| = |v_r| exactly: s = |v_r|/|y| from an
+// FP32 estimate and one FP64 Newton step on s^2 |y|^2 = |v_r|^2 (relative
+// error ~1e-14).  About a third of the FP64 work of deflect().
+__device__ __forceinline__ void deflect_shell(double ux, double uy, double uz, double g2, float chi, float eps,
+                                              double* o) {
+  const float fx = f64_to_f32(ux), fy = f64_to_f32(uy), fz = f64_to_f32(uz);
+  float sc, cc, se, ce;
+  sincosf(chi, &sc, &cc);
+  sincosf(eps, &se, &ce);
+  const float q2 = fy * fy + fz * fz, gf2 = fx * fx + q2;
+  const float gf = sqrtf(gf2);
+  float cx, cy, cz, ax, ay, az;
+  if (q2 > 1e-24f * gf2 && q2 > 0.f) {
+    const float iq = rsqrtf(q2), q = q2 * iq, ig = 1.f / gf;
+    cx = 0.f; cy = fz * iq; cz = -fy * iq;
+    ax = q * ig; ay = -fx * fy * iq * ig; az = -fx * fz * iq * ig;
+  } else {
+    cx = 0.f; cy = 1.f; cz = 0.f;
+    ax = 0.f; ay = 0.f; az = fx >= 0.f ? -1.f : 1.f;
+  }
+  const float y0 = cc * fx + gf * sc * (ce * cx + se * ax);
+  const float y1 = cc * fy + gf * sc * (ce * cy + se * ay);
+  const float y2 = cc * fz + gf * sc * (ce * cz + se * az);
+  const double Y0 = y0, Y1 = y1, Y2 = y2;
+  const double ny2 = Y0 * Y0 + Y1 * Y1 + Y2 * Y2;
+  if (!(ny2 > 0.0)) { o[0] = o[1] = o[2] = 0.0; return; }
+  const float ny2f = (float)ny2, g2f = (float)g2;
+  const float sf = sqrtf(g2f / ny2f);
+  const double s0 = sf;
+  const double res = g2 - s0 * s0 * ny2;
+  const double sfin = s0 + res * (double)(0.5f * sf / g2f);
+  o[0] = sfin * Y0; o[1] = sfin * Y1; o[2] = sfin * Y2;
+}
+
 struct JagerArgs {
   uint64_t seed, step;
   const uint64_t* step_dev;
@@ -474,14 +520,8 @@ __device__ __forceinline__ void collide_pair(const PotDev& P, const JagerArgs& a
   const float E = P.mass_over_4k * (float)g2;
   const float chi = g2 > 0.0 ? chi_device(P, b, E) : 0.f;
   if (a.chi_out) a.chi_out[p] = chi;
-  double cc, sc, ce, se;
-  unit_angle(chi, &cc, &sc);
-  unit_angle((float)(2.0 * DSMC_PI * u53(w.z, w.w)), &ce, &se);
   double o[3] = {0.0, 0.0, 0.0};
-  if (g2 > 0.0) {
-    const double ig = rsqrt(g2);
-    deflect(ux, uy, uz, g2 * ig, ig, cc, sc, ce, se, o);
-  }
+  if (g2 > 0.0) deflect_shell(ux, uy, uz, g2, chi, (float)(2.0 * DSMC_PI * u53(w.z, w.w)), o);
   const double cx = 0.5 * (xi + xj), cy = 0.5 * (yi + yj), cz = 0.5 * (zi + zj);
   __stcg(a.vx + q.x, cx + 0.5 * o[0]); __stcg(a.vy + q.x, cy + 0.5 * o[1]); __stcg(a.vz + q.x, cz + 0.5 * o[2]);
   __stcg(a.vx + q.y, cx - 0.5 * o[0]); __stcg(a.vy + q.y, cy - 0.5 * o[1]); __stcg(a.vz + q.y, cz - 0.5 * o[2]);
@@ -513,6 +553,96 @@ __global__ void __launch_bounds__(128, 4) k_collide_jager(PotDev P, JagerArgs a)
       ok = wait_deps(a.done, q.x, q.y, a.deps[p], a.bar + 2, a.status);
       if (ok) {
         collide_pair(P, a, p, q);
+        release_pair(a.done, q.x, q.y, (unsigned)(r + 1));
+      }
+    }
+    if (!__all_sync(0xffffffffu, ok)) break;
+  }
+}
+
+// ---------------------------------------------------------------- look-up table
+// Sec. 3.4.5: the table of the look-up path over b~ = b/b_max (nb uniform
+// nodes on [0, 1]) and E~ = ln(E_r/k_B) (nE uniform nodes on [lnE_min,
+// lnE_max]), both ends included; filled here with the exact chi.
+__global__ void __launch_bounds__(128) k_chi_table(PotDev P, int32_t nb, int32_t nE, double bmax_A, double lnE_min,
+                                                   double dlnE, float* __restrict__ T) {
+  const int64_t total = (int64_t)nb * nE;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t i = (int32_t)(q % nb), j = (int32_t)(q / nb);
+    const float b = (float)(bmax_A * i / (nb - 1));
+    const float E = (float)exp(lnE_min + j * dlnE);
+    T[q] = chi_device(P, b, E);
+  }
+}
+
+struct TableArgs {
+  uint64_t seed, step;
+  const uint64_t* step_dev;
+  const float* T;
+  int32_t nb, nE;
+  float lnE_min, inv_dlnE;   // y = (ln E - lnE_min) inv_dlnE
+  float mass_over_4k;
+  const int4* pairs;
+  const uint32_t* deps;
+  const int32_t* ro;
+  const dsmc_select_info_t* info;
+  double *vx, *vy, *vz;
+  float* chi_out;
+  unsigned* done;
+  unsigned* bar;   // [2] abort word, [3] unit cursor
+  int* status;
+};
+
+// chi by bilinear interpolation at (x, y) in node units, y clamped to the table
+__device__ __forceinline__ float chi_lookup(const TableArgs& a, float x, float y) {
+  x = fminf(fmaxf(x, 0.f), (float)(a.nb - 1));
+  y = fminf(fmaxf(y, 0.f), (float)(a.nE - 1));
+  const int i0 = min((int)x, a.nb - 2), j0 = min((int)y, a.nE - 2);
+  const float fx = x - (float)i0, fy = y - (float)j0;
+  const float* r0 = a.T + (size_t)j0 * a.nb + i0;
+  const float* r1 = r0 + a.nb;
+  const float t00 = __ldg(r0), t01 = __ldg(r0 + 1), t10 = __ldg(r1), t11 = __ldg(r1 + 1);
+  return (1.f - fy) * ((1.f - fx) * t00 + fx * t01) + fy * ((1.f - fx) * t10 + fx * t11);
+}
+
+// The Jager pair update with chi from the table (b~ = sqrt(U1), eps = 2 pi U2
+// from tag 4, E~ = ln(m g^2 / (4 k_B))); work claimed and ordered as in
+// k_collide_jager.
+__global__ void __launch_bounds__(256) k_collide_table(TableArgs a) {
+  if (a.step_dev) a.step = *a.step_dev;
+  const int R = a.info->n_rounds;
+  const int lane = threadIdx.x & 31;
+  int r = 0;
+  int64_t base = 0;
+  for (;;) {
+    unsigned unit = 0;
+    if (lane == 0) unit = atomicAdd(a.bar + 3, 1u);
+    unit = __shfl_sync(0xffffffffu, unit, 0);
+    int32_t p0, p1;
+    if (!unit_range(a.ro, R, 32, r, base, unit, &p0, &p1)) break;
+    const int32_t p = p0 + lane;
+    bool ok = true;
+    if (p < p1) {
+      const int4 q = a.pairs[p];
+      ok = wait_deps(a.done, q.x, q.y, a.deps[p], a.bar + 2, a.status);
+      if (ok) {
+        const double xi = __ldcg(a.vx + q.x), yi = __ldcg(a.vy + q.x), zi = __ldcg(a.vz + q.x);
+        const double xj = __ldcg(a.vx + q.y), yj = __ldcg(a.vy + q.y), zj = __ldcg(a.vz + q.y);
+        const double ux = xi - xj, uy = yi - yj, uz = zi - zj;
+        const double g2 = ux * ux + uy * uy + uz * uz;
+        const u32x4 w = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_JAGER);
+        float chi = 0.f;
+        if (g2 > 0.0) {
+          const float x = (float)(sqrt(u53(w.x, w.y)) * (a.nb - 1));
+          const float y = (logf(a.mass_over_4k * (float)g2) - a.lnE_min) * a.inv_dlnE;
+          chi = chi_lookup(a, x, y);
+        }
+        if (a.chi_out) a.chi_out[p] = chi;
+        double o[3] = {0.0, 0.0, 0.0};
+        if (g2 > 0.0) deflect_shell(ux, uy, uz, g2, chi, (float)(2.0 * DSMC_PI * u53(w.z, w.w)), o);
+        const double cx = 0.5 * (xi + xj), cy = 0.5 * (yi + yj), cz = 0.5 * (zi + zj);
+        __stcg(a.vx + q.x, cx + 0.5 * o[0]); __stcg(a.vy + q.x, cy + 0.5 * o[1]); __stcg(a.vz + q.x, cz + 0.5 * o[2]);
+        __stcg(a.vx + q.y, cx - 0.5 * o[0]); __stcg(a.vy + q.y, cy - 0.5 * o[1]); __stcg(a.vz + q.y, cz - 0.5 * o[2]);
         release_pair(a.done, q.x, q.y, (unsigned)(r + 1));
       }
     }
@@ -590,6 +720,49 @@ int launch_collide_jager(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& 
   k_collide_jager<<<blocks, sh.threads, 0, s>>>(P, a);
   count_launches(c, 1);
   return cudaGetLastError() == cudaSuccess ? 0 : record(c, DSMC_ERR_CUDA, "collide_jager: launch failed");
+}
+
+int launch_chi_table(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& pot, int n_nodes, int32_t nb,
+                     int32_t nE, double lnE_min, double lnE_max, float* T, cudaStream_t s) {
+  const PotDev P = make_pot(gas, pot, n_nodes);
+  const int64_t total = (int64_t)nb * nE;
+  k_chi_table<<<blocks_n(total, 128, sm_count(c) * 64), 128, 0, s>>>(P, nb, nE, gas.b_max * 1e10, lnE_min,
+                                                                     (lnE_max - lnE_min) / (nE - 1), T);
+  count_launches(c, 1);
+  return cudaGetLastError() == cudaSuccess ? 0 : record(c, DSMC_ERR_CUDA, "chi_table: launch failed");
+}
+
+int occupancy_collide_table(int threads) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_collide_table, threads, 0) != cudaSuccess)
+    return 0;
+  return per_sm;
+}
+
+int launch_collide_table(Ctx* c, const dsmc_gas_t& gas, const dsmc_chi_table_t& tab, uint64_t step, int32_t n,
+                         const int32_t* pairs, const uint32_t* deps, const int32_t* ro,
+                         const dsmc_select_info_t* info, double* vx, double* vy, double* vz, float* chi_out,
+                         void* ws, size_t ws_bytes, cudaStream_t s) {
+  if (ws_bytes < collide_ws(n)) return record(c, DSMC_ERR_ARG, "collide_table: workspace too small");
+  const Shape sh = shape_or_default(c, DSMC_TUNE_COLLIDE_TABLE);
+  const int occ = occupancy_collide_table(sh.threads);
+  if (occ < 1) return record(c, DSMC_ERR_CUDA, "collide_table: occupancy query failed");
+  const int blocks = sm_count(c) * (sh.blocks_per_sm > 0 && sh.blocks_per_sm < occ ? sh.blocks_per_sm : occ);
+  TableArgs a;
+  a.seed = gas.seed; a.step = step; a.step_dev = graph_step_ptr(c);
+  a.T = tab.chi; a.nb = tab.nb; a.nE = tab.nE;
+  a.lnE_min = (float)tab.lnE_min;
+  a.inv_dlnE = (float)((tab.nE - 1) / (tab.lnE_max - tab.lnE_min));
+  a.mass_over_4k = (float)(gas.mass / (4.0 * DSMC_KB));
+  a.pairs = (const int4*)pairs; a.deps = deps; a.ro = ro; a.info = info;
+  a.vx = vx; a.vy = vy; a.vz = vz; a.chi_out = chi_out;
+  a.done = (unsigned*)ws; a.bar = barrier_ptr(c); a.status = status_ptr(c);
+  if (cudaMemsetAsync(a.bar, 0, 4 * sizeof(unsigned), s) != cudaSuccess ||
+      cudaMemsetAsync(a.done, 0, sizeof(unsigned) * (size_t)(n > 0 ? n : 1), s) != cudaSuccess)
+    return DSMC_ERR_CUDA;
+  k_collide_table<<<blocks, sh.threads, 0, s>>>(a);
+  count_launches(c, 1);
+  return cudaGetLastError() == cudaSuccess ? 0 : record(c, DSMC_ERR_CUDA, "collide_table: launch failed");
 }
 
 int launch_harvest_jager(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& pot,

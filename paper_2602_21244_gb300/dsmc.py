@@ -9,6 +9,7 @@ if the library cannot be loaded, importing this module raises.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 
 import torch
@@ -17,7 +18,7 @@ from . import _build
 
 DSMC_OK, DSMC_ERR_ARG, DSMC_ERR_CUDA, DSMC_ERR_CAPACITY = 0, -1, -2, -3
 DSMC_ERR_TIMEOUT, DSMC_ERR_NONFINITE, DSMC_ERR_UNSUPPORTED = -4, -5, -6
-PATH_VHS, PATH_JAGER, PATH_NEURAL = 0, 1, 2
+PATH_VHS, PATH_JAGER, PATH_NEURAL, PATH_TABLE = 0, 1, 2, 3
 MAX_ROUNDS = 1024
 _ERRS = {-1: "DSMC_ERR_ARG", -2: "DSMC_ERR_CUDA", -3: "DSMC_ERR_CAPACITY", -4: "DSMC_ERR_TIMEOUT",
          -5: "DSMC_ERR_NONFINITE", -6: "DSMC_ERR_UNSUPPORTED"}
@@ -64,18 +65,35 @@ class StepBuffers(C.Structure):
                 ("info", C.c_void_p), ("ws", C.c_void_p), ("ws_bytes", C.c_size_t), ("deps", C.c_void_p)]
 
 
+class ChiTableDesc(C.Structure):
+    _fields_ = [("chi", C.c_void_p), ("nb", C.c_int32), ("nE", C.c_int32), ("lnE_min", C.c_double),
+                ("lnE_max", C.c_double)]
+
+
+class ChiTable:
+    """A chi table over (b/b_max, ln(E_r/k_B)) in device memory (dsmc_chi_table_t)."""
+
+    def __init__(self, chi: torch.Tensor, lnE_min: float, lnE_max: float):
+        if chi.dtype != torch.float32 or chi.dim() != 2 or not chi.is_cuda or not chi.is_contiguous():
+            raise ValueError("chi table: contiguous float32 CUDA tensor [nE x nb]")
+        self.chi = chi
+        self.lnE_min, self.lnE_max = float(lnE_min), float(lnE_max)
+        self.desc = ChiTableDesc(chi.data_ptr(), chi.shape[1], chi.shape[0], self.lnE_min, self.lnE_max)
+
+
 class TuneEntry(C.Structure):
     _fields_ = [("kernel", C.c_int32), ("threads", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("ms", C.c_float)]
 
 
 # DSMC_TUNE_* kernel ids and their names in the autotune cache
-TUNE_KERNELS = ("gather", "moments", "moment_match", "collide_vhs", "collide_jager", "jager_chi")
+TUNE_KERNELS = ("gather", "moments", "moment_match", "collide_vhs", "collide_jager", "jager_chi", "collide_table")
 
 
 class Path(C.Structure):
     _fields_ = [("path", C.c_int32), ("n_nodes", C.c_int32), ("pot", C.POINTER(Potential)),
-                ("mlp", C.POINTER(Mlp)), ("weights_bf16", C.c_void_p), ("biases", C.c_void_p)]
+                ("mlp", C.POINTER(Mlp)), ("weights_bf16", C.c_void_p), ("biases", C.c_void_p),
+                ("table", C.POINTER(ChiTableDesc))]
 
 
 # ------------------------------------------------------------------ library
@@ -117,6 +135,9 @@ def load(build: bool = True):
             "dsmc_jager_chi": (C.c_int, [vp, P(Gas), P(Potential), i32, i64, vp, vp, vp, vp]),
             "dsmc_collide_jager": (C.c_int, [vp, P(Gas), P(Potential), i32, u64, i32, vp, vp, vp, vp, vp,
                                              vp, vp, vp, vp, sz, vp]),
+            "dsmc_chi_table_build": (C.c_int, [vp, P(Gas), P(Potential), i32, i32, i32, d, d, vp, vp]),
+            "dsmc_collide_table": (C.c_int, [vp, P(Gas), P(ChiTableDesc), u64, i32, vp, vp, vp, vp, vp, vp, vp, vp,
+                                             vp, sz, vp]),
             "dsmc_collide_neural": (C.c_int, [vp, P(Gas), P(Mlp), vp, vp, u64, vp, i32, vp, vp, vp, vp, vp,
                                               vp, vp, vp, vp, sz, vp]),
             "dsmc_mlp_forward": (C.c_int, [vp, P(Mlp), vp, vp, i64, vp, vp, vp]),
@@ -334,6 +355,22 @@ class Context:
             _ptr(sel["round_offsets"]), _ptr(sel["info"]), _ptr(vx, torch.float64),
             _ptr(vy, torch.float64), _ptr(vz, torch.float64), _ptr(chi_out, torch.float32),
             _ptr(w), nb, _stream(stream)), "collide_jager")
+
+    def chi_table_build(self, gas: Gas, pot: Potential, nb=512, nE=512, lnE_min=math.log(5.0),
+                        lnE_max=math.log(6.0e4), n_nodes=32, stream=None) -> "ChiTable":
+        """dsmc_chi_table_build: the exact chi on the (b/b_max, ln E) grid."""
+        chi = torch.empty((nE, nb), dtype=torch.float32, device=torch.device("cuda", self.device))
+        self._check(self._lib.dsmc_chi_table_build(self.h, C.byref(gas), C.byref(pot), n_nodes, nb, nE, lnE_min,
+                                                   lnE_max, _ptr(chi), _stream(stream)), "chi_table_build")
+        return ChiTable(chi, lnE_min, lnE_max)
+
+    def collide_table(self, gas: Gas, table: "ChiTable", step, sel, vx, vy, vz, chi_out=None, ws=None,
+                      stream=None):
+        w, nb = self._collide_ws(vx.numel(), vx.device, ws)
+        self._check(self._lib.dsmc_collide_table(
+            self.h, C.byref(gas), C.byref(table.desc), step, vx.numel(), _ptr(sel["pairs"]), _ptr(sel["deps"]),
+            _ptr(sel["round_offsets"]), _ptr(sel["info"]), _ptr(vx, torch.float64), _ptr(vy, torch.float64),
+            _ptr(vz, torch.float64), _ptr(chi_out, torch.float32), _ptr(w), nb, _stream(stream)), "collide_table")
 
     def collide_neural(self, gas: Gas, mlp: Mlp, w_bits, bias, step, mom, sel, vx, vy, vz,
                        u_out=None, ws=None, stream=None):
@@ -622,7 +659,8 @@ class StepState:
 
 
 def make_path(kind: int, pot: Potential | None = None, n_nodes: int = 32, mlp: Mlp | None = None,
-              w_bits: torch.Tensor | None = None, bias: torch.Tensor | None = None) -> Path:
+              w_bits: torch.Tensor | None = None, bias: torch.Tensor | None = None,
+              table: "ChiTable | None" = None) -> Path:
     P = Path()
     P.path = kind
     P.n_nodes = n_nodes
@@ -630,7 +668,8 @@ def make_path(kind: int, pot: Potential | None = None, n_nodes: int = 32, mlp: M
     P.mlp = C.pointer(mlp) if mlp is not None else C.POINTER(Mlp)()
     P.weights_bf16 = w_bits.data_ptr() if w_bits is not None else None
     P.biases = bias.data_ptr() if bias is not None else None
-    P._keep = (pot, mlp, w_bits, bias)
+    P.table = C.pointer(table.desc) if table is not None else C.POINTER(ChiTableDesc)()
+    P._keep = (pot, mlp, w_bits, bias, table)
     return P
 
 

@@ -29,7 +29,7 @@ def test_library_builds_and_exports_every_declared_symbol():
     missing = [n for n in names if not hasattr(L, n)]
     assert not missing, missing
     L.dsmc_abi_version.restype = C.c_int
-    assert L.dsmc_abi_version() == 2
+    assert L.dsmc_abi_version() == 3
 
 
 def test_library_targets_sm_103a():

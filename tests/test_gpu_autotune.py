@@ -30,13 +30,23 @@ def _wl():
     return _W["w"]
 
 
+def _table(D):
+    if "table" not in _W:
+        w = _wl()
+        gas = D.make_gas(dict(w["gas"], model=1))
+        _W["table"] = ctx().chi_table_build(gas, D.make_potential(JP), nb=96, nE=96)
+    return _W["table"]
+
+
 def _path(D, kind):
     wts = W.mlp_weights()
     bias = (np.random.default_rng(7).standard_normal(len(wts["bias"])) * 0.05).astype(np.float32)
     mlp = D.make_mlp(8, 128, 3, 3, 0, W.sigma_v(), 273.0, 1e-12)
-    return D.make_path({"vhs": D.PATH_VHS, "jager": D.PATH_JAGER, "neural": D.PATH_NEURAL}[kind],
+    return D.make_path({"vhs": D.PATH_VHS, "jager": D.PATH_JAGER, "neural": D.PATH_NEURAL,
+                        "table": D.PATH_TABLE}[kind],
                        pot=D.make_potential(JP), n_nodes=32, mlp=mlp,
-                       w_bits=w_bits_tensor(wts["W_bits"]), bias=cuda(bias))
+                       w_bits=w_bits_tensor(wts["W_bits"]), bias=cuda(bias),
+                       table=_table(D) if kind == "table" else None)
 
 
 def _run_step(C, D, kind, st, step=2):
@@ -71,12 +81,12 @@ def _reset(C, D):
 
 # non-default shapes: small blocks, few blocks per SM, large blocks
 SHAPES = [
-    {0: (128, 2), 1: (64, 4), 2: (64, 32), 3: (64, 1), 4: (32, 1)},
-    {0: (512, 4), 1: (128, 16), 2: (256, 4), 3: (128, 2), 4: (64, 2)},
+    {0: (128, 2), 1: (64, 4), 2: (64, 32), 3: (64, 1), 4: (32, 1), 6: (64, 1)},
+    {0: (512, 4), 1: (128, 16), 2: (256, 4), 3: (128, 2), 4: (64, 2), 6: (128, 2)},
 ]
 
 
-@pytest.mark.parametrize("kind", ["vhs", "jager", "neural"])
+@pytest.mark.parametrize("kind", ["vhs", "jager", "neural", "table"])
 def test_launch_shape_does_not_change_the_step(kind):
     from paper_2602_21244_gb300 import dsmc as D
     C = ctx()
@@ -101,7 +111,7 @@ def test_tune_set_rejects_bad_shapes_and_resets():
     C = ctx()
     default = C.tune_get(D.TUNE_KERNELS.index("collide_jager"))
     assert default == (128, 0)  # full occupancy
-    for args in [(6, 128, 1), (-1, 128, 1), (0, 48, 4), (0, 2048, 1), (1, 512, 4), (0, 128, 0),
+    for args in [(7, 128, 1), (-1, 128, 1), (0, 48, 4), (0, 2048, 1), (1, 512, 4), (0, 128, 0),
                  (0, 128, 65), (4, 256, 1)]:
         with pytest.raises(D.DsmcError) as e:
             C.tune_set(*args)
@@ -115,7 +125,7 @@ def test_tune_set_rejects_bad_shapes_and_resets():
         assert cands and all(t % 32 == 0 and 1 <= b <= 64 for t, b in cands)
 
 
-@pytest.mark.parametrize("kind", ["jager", "neural"])
+@pytest.mark.parametrize("kind", ["jager", "neural", "table"])
 def test_autotune_keeps_the_fastest_measured_shape(kind):
     from paper_2602_21244_gb300 import dsmc as D
     C = ctx()
@@ -127,7 +137,8 @@ def test_autotune_keeps_the_fastest_measured_shape(kind):
     try:
         trials = C.autotune_step(gas, _path(D, kind), st, step=2, reps=2)
         assert C.sync_status() == 0
-        tuned = {"gather", "moments", "moment_match"} | ({"collide_jager"} if kind == "jager" else set())
+        tuned = {"gather", "moments", "moment_match"} | {"jager": {"collide_jager"}, "table": {"collide_table"},
+                                                          "neural": set()}[kind]
         assert {t["kernel"] for t in trials} == tuned
         for name in tuned:
             mine = [t for t in trials if t["kernel"] == name]
