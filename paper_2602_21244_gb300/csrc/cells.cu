@@ -353,15 +353,109 @@ int launch_gather(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_start,
 }
 
 // ---------------------------------------------------------------- moments
-// Eight lanes per cell (four cells per warp): the FP64 reduction trees have
-// three levels, and GB300's FP64 pipe is the bound of these kernels.
+// Eight lanes per cell (four cells per warp).  The sums are exact integer
+// sums, not FP64 ones (GB300's FP64 pipe, ~1/64 of FP32, bounded the FP64
+// version): each velocity component of a cell becomes the integer
+// x = round(v / 2^p), 2^p = the unit in the last place of the cell's largest
+// component (coarser by 2^c for cells of 1024 or more particles, so that a
+// cell's sum fits in 64 bits), formed from the bits of v on the integer
+// pipe.  Sums of x are exact in int64, sums of (x - round(mean))^2 in 128
+// bits; only the per-cell results are converted back to FP64.  The only
+// rounding is each component's to the cell's resolution (at most half its
+// largest ulp), the same order as one FP64 addition per term, and the result
+// does not depend on the order of the sums.
 constexpr int kCellWarps = 8;
 constexpr int kSeg = 8;
 
-__device__ __forceinline__ double seg_sum(double v) {
+__device__ __forceinline__ int seg_max_i(int v) {
+#pragma unroll
+  for (int o = kSeg / 2; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ long long seg_sum_ll(long long v) {
 #pragma unroll
   for (int o = kSeg / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+__device__ __forceinline__ unsigned __int128 seg_sum_u128(unsigned __int128 v) {
+#pragma unroll
+  for (int o = kSeg / 2; o > 0; o >>= 1) {
+    const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+    const unsigned long long lo2 = __shfl_xor_sync(0xffffffffu, lo, o), hi2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    v += ((unsigned __int128)hi2 << 64) | lo2;
+  }
+  return v;
+}
+
+// biased exponent field of a double (2047: inf or nan)
+__device__ __forceinline__ int dexp(double v) { return (__double2hiint(v) >> 20) & 0x7FF; }
+
+// Cell scale: E = largest biased exponent of the cell's components, c the
+// coarsening for large cells; the integer unit is 2^(E - 1075 + c).
+struct FixScale {
+  int E, c;
+};
+
+__device__ __forceinline__ FixScale cell_scale(int E, int32_t N) {
+  const int bits = 32 - __clz(N > 0 ? N : 1);   // N < 2^bits
+  return FixScale{E, bits > 10 ? bits - 10 : 0};
+}
+
+// round(v / unit) for the cell's unit (integer pipe only)
+__device__ __forceinline__ long long to_fix(double v, const FixScale& f) {
+  const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  if (e == 0) return 0;  // zero (or subnormal: below any normal cell's unit)
+  const unsigned long long m = ((unsigned long long)((hi & 0xFFFFFu) | 0x100000u) << 32) | lo;
+  const int sh = f.E - e + f.c;
+  unsigned long long x;
+  if (sh <= 0) x = m;
+  else if (sh >= 64) x = 0;
+  else x = (m + (1ull << (sh - 1))) >> sh;
+  return (hi & 0x80000000u) ? -(long long)x : (long long)x;
+}
+
+// the cell's unit 2^(E - 1075 + c) as a double
+__device__ __forceinline__ double fix_unit(const FixScale& f) { return ldexp(1.0, f.E - 1075 + f.c); }
+
+__device__ __forceinline__ double u128_to_double(unsigned __int128 v) {
+  return fma((double)(unsigned long long)(v >> 64), 18446744073709551616.0, (double)(unsigned long long)v);
+}
+
+// round(s / n) for n > 0
+__device__ __forceinline__ long long div_round(long long s, long long n) {
+  return s >= 0 ? (s + n / 2) / n : -((-s + n / 2) / n);
+}
+
+// The exact integer moments of one cell (8 lanes): sums and centred sum of
+// squares in the cell's integer unit.
+struct CellFix {
+  FixScale f;
+  long long sx, sy, sz, mx, my, mz;  // sums and rounded means (integer units)
+  unsigned __int128 th;              // sum of squared deviations (units^2)
+};
+
+__device__ __forceinline__ CellFix cell_fix(const double* __restrict__ vx, const double* __restrict__ vy,
+                                            const double* __restrict__ vz, int32_t a, int32_t b, int sl) {
+  CellFix C;
+  int E = 0;
+  for (int32_t i = a + sl; i < b; i += kSeg) E = max(E, max(dexp(vx[i]), max(dexp(vy[i]), dexp(vz[i]))));
+  C.f = cell_scale(seg_max_i(E), b - a);
+  long long sx = 0, sy = 0, sz = 0;
+  for (int32_t i = a + sl; i < b; i += kSeg) { sx += to_fix(vx[i], C.f); sy += to_fix(vy[i], C.f); sz += to_fix(vz[i], C.f); }
+  C.sx = seg_sum_ll(sx); C.sy = seg_sum_ll(sy); C.sz = seg_sum_ll(sz);
+  const long long n = b - a;
+  C.mx = n > 0 ? div_round(C.sx, n) : 0;
+  C.my = n > 0 ? div_round(C.sy, n) : 0;
+  C.mz = n > 0 ? div_round(C.sz, n) : 0;
+  unsigned __int128 th = 0;
+  for (int32_t i = a + sl; i < b; i += kSeg) {
+    const long long dx = to_fix(vx[i], C.f) - C.mx, dy = to_fix(vy[i], C.f) - C.my, dz = to_fix(vz[i], C.f) - C.mz;
+    th += (unsigned __int128)((__int128)dx * dx) + (unsigned __int128)((__int128)dy * dy) +
+          (unsigned __int128)((__int128)dz * dz);
+  }
+  C.th = seg_sum_u128(th);
+  return C;
 }
 
 __global__ void __launch_bounds__(kCellWarps * 32)
@@ -376,24 +470,14 @@ k_moments(int32_t n_cells, const int32_t* __restrict__ cs, const double* __restr
     const int32_t k = k0 + seg;
     const bool has = k < n_cells;
     const int32_t a = has ? cs[k] : 0, b = has ? cs[k + 1] : 0;
-    double sx = 0, sy = 0, sz = 0;
-    for (int32_t i = a + sl; i < b; i += kSeg) { sx += vx[i]; sy += vy[i]; sz += vz[i]; }
-    sx = seg_sum(sx); sy = seg_sum(sy); sz = seg_sum(sz);
-    const double n = (double)(b - a);
-    double th = 0;
-    if (b > a) {
-      const double inv = 1.0 / n;
-      const double ux = sx * inv, uy = sy * inv, uz = sz * inv;
-      for (int32_t i = a + sl; i < b; i += kSeg) {
-        const double dx = vx[i] - ux, dy = vy[i] - uy, dz = vz[i] - uz;
-        th += dx * dx + dy * dy + dz * dz;
-      }
-    }
-    th = seg_sum(th);
+    const CellFix C = cell_fix(vx, vy, vz, a, b, sl);
     if (has && sl == 0) {
-      if (!isfinite(sx + sy + sz + th)) set_status(status, DSMC_ERR_NONFINITE);
+      if (C.f.E == 0x7FF) set_status(status, DSMC_ERR_NONFINITE);
+      const double unit = fix_unit(C.f);
       double* m = mom + 5 * (size_t)k;
-      m[0] = n; m[1] = sx; m[2] = sy; m[3] = sz; m[4] = th;
+      m[0] = (double)(b - a);
+      m[1] = (double)C.sx * unit; m[2] = (double)C.sy * unit; m[3] = (double)C.sz * unit;
+      m[4] = u128_to_double(C.th) * unit * unit;
     }
   }
 }
@@ -410,7 +494,8 @@ int launch_moments(Ctx* c, int32_t n_cells, const int32_t* cs, const double* vx,
 
 // ---------------------------------------------------------------- moment matching
 // Sec. 2.5 (centred): v <- u_pre + alpha (v - u_post), alpha = sqrt(Th_pre/Th_post),
-// applied as v <- alpha v + (u_pre - alpha u_post).
+// applied as v <- alpha v + (u_pre - alpha u_post) (FP64); u_post and Th_post
+// from the exact integer moments above.
 __global__ void __launch_bounds__(kCellWarps * 32)
 k_moment_match(int32_t n_cells, const int32_t* __restrict__ cs, const double* __restrict__ mom,
                double* __restrict__ vx, double* __restrict__ vy, double* __restrict__ vz) {
@@ -422,20 +507,11 @@ k_moment_match(int32_t n_cells, const int32_t* __restrict__ cs, const double* __
     const int32_t k = k0 + seg;
     const bool has = k < n_cells;
     const int32_t a = has ? cs[k] : 0, b = has ? cs[k + 1] : 0;
-    double sx = 0, sy = 0, sz = 0;
-    for (int32_t i = a + sl; i < b; i += kSeg) { sx += vx[i]; sy += vy[i]; sz += vz[i]; }
-    sx = seg_sum(sx); sy = seg_sum(sy); sz = seg_sum(sz);
-    const double n = (double)(b - a);
-    // one division per cell (the FP64 pipe bounds this kernel)
-    const double inv = b > a ? 1.0 / n : 0.0;
-    const double ux = sx * inv, uy = sy * inv, uz = sz * inv;
-    double th = 0;
-    for (int32_t i = a + sl; i < b; i += kSeg) {
-      const double dx = vx[i] - ux, dy = vy[i] - uy, dz = vz[i] - uz;
-      th += dx * dx + dy * dy + dz * dz;
-    }
-    th = seg_sum(th);
+    const CellFix C = cell_fix(vx, vy, vz, a, b, sl);
     if (b <= a) continue;
+    const double unit = fix_unit(C.f), n = (double)(b - a), inv = 1.0 / n;
+    const double ux = (double)C.sx * unit * inv, uy = (double)C.sy * unit * inv, uz = (double)C.sz * unit * inv;
+    const double th = u128_to_double(C.th) * unit * unit;
     const double* m = mom + 5 * (size_t)k;
     const double px = m[1] * inv, py = m[2] * inv, pz = m[3] * inv;
     const double alpha = (b - a >= 2 && th > 0.0) ? sqrt(m[4] / th) : 1.0;
