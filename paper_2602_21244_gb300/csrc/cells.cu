@@ -221,11 +221,14 @@ k_rs_count(const int32_t* __restrict__ cell_id, const uint32_t* __restrict__ key
   for (int t = threadIdx.x; t < kRadix; t += blockDim.x) cnt[(size_t)t * chunks + blockIdx.x] = hist[t];
 }
 
-// Ordered scatter of one chunk: warp w owns the chunk's w-th eighth; each
-// warp counts its digits, the counts become per-warp starting positions
-// (warps in order after the chunk's base from the scan), then each warp
-// writes its elements in order, ranks among equal digits within 32 lanes
-// from __match_any_sync.  Values: the input index (first pass) or vals.
+// Ordered scatter of one chunk: warp w owns the chunk's w-th eighth, its 16
+// elements per lane loaded into registers first; each warp counts its
+// digits, the counts become per-warp starting positions (warps in order
+// after the chunk's base from the scan), then each warp writes its elements
+// in order, ranks among equal digits within 32 lanes from __match_any_sync.
+// Values: the input index (first pass) or vals.
+constexpr int kRsPer = kRsChunk / kRsWarps / 32;
+
 __global__ void __launch_bounds__(kRsWarps * 32)
 k_rs_scatter(const int32_t* __restrict__ cell_id, const uint32_t* __restrict__ keys,
              const int32_t* __restrict__ vals, int32_t n, int32_t n_cells, int shift, int32_t chunks,
@@ -233,12 +236,20 @@ k_rs_scatter(const int32_t* __restrict__ cell_id, const uint32_t* __restrict__ k
   __shared__ int wh[kRsWarps][kRadix];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int t = threadIdx.x; t < kRsWarps * kRadix; t += blockDim.x) wh[t / kRadix][t % kRadix] = 0;
+  const int64_t s0 = (int64_t)blockIdx.x * kRsChunk + (int64_t)w * (kRsPer * 32);
+  uint32_t key[kRsPer];
+  int32_t val[kRsPer];
+#pragma unroll
+  for (int j = 0; j < kRsPer; ++j) {
+    const int64_t i = s0 + j * 32 + lane;
+    const bool has = i < n;
+    key[j] = has ? rs_key(cell_id, keys, i, n_cells, nullptr) : 0u;
+    val[j] = has ? (vals ? vals[i] : (int32_t)i) : 0;
+  }
   __syncthreads();
-  constexpr int kSub = kRsChunk / kRsWarps;
-  const int64_t p0 = (int64_t)blockIdx.x * kRsChunk;
-  const int64_t s0 = min((int64_t)n, p0 + (int64_t)w * kSub), s1 = min((int64_t)n, s0 + kSub);
-  for (int64_t i = s0 + lane; i < s1; i += 32)
-    atomicAdd(&wh[w][(rs_key(cell_id, keys, i, n_cells, nullptr) >> shift) & (kRadix - 1)], 1);
+#pragma unroll
+  for (int j = 0; j < kRsPer; ++j)
+    if (s0 + j * 32 + lane < n) atomicAdd(&wh[w][(key[j] >> shift) & (kRadix - 1)], 1);
   __syncthreads();
   for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
     int acc = base[(size_t)d * chunks + blockIdx.x];
@@ -246,16 +257,15 @@ k_rs_scatter(const int32_t* __restrict__ cell_id, const uint32_t* __restrict__ k
   }
   __syncthreads();
   const unsigned lt = (1u << lane) - 1u;
-  for (int64_t q0 = s0; q0 < s1; q0 += 32) {
-    const int64_t i = q0 + lane;
-    const bool has = i < s1;
-    const uint32_t key = has ? rs_key(cell_id, keys, i, n_cells, nullptr) : 0u;
-    const int d = has ? (int)((key >> shift) & (kRadix - 1)) : -1;
+#pragma unroll
+  for (int j = 0; j < kRsPer; ++j) {
+    const bool has = s0 + j * 32 + lane < n;
+    const int d = has ? (int)((key[j] >> shift) & (kRadix - 1)) : -1;
     const unsigned same = __match_any_sync(0xffffffffu, d);
     if (has) {
       const int q = wh[w][d] + __popc(same & lt);
-      if (keys_out) keys_out[q] = key;
-      vals_out[q] = vals ? vals[i] : (int32_t)i;
+      if (keys_out) keys_out[q] = key[j];
+      vals_out[q] = val[j];
     }
     __syncwarp();
     if (has && (same & lt) == 0) wh[w][d] += __popc(same);
