@@ -182,11 +182,27 @@ __global__ void k_gather(int32_t n, const int32_t* __restrict__ cell_start, int3
                          const double* __restrict__ vy, const double* __restrict__ vz,
                          double* __restrict__ svx, double* __restrict__ svy, double* __restrict__ svz) {
   const int32_t filled = min(n, cell_start[n_cells]);
-  for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < filled; s += gridDim.x * blockDim.x) {
-    const int32_t src = perm[s];
-    svx[s] = vx[src];
-    svy[s] = vy[src];
-    svz[s] = vz[src];
+  // four slots per thread per pass, their loads issued before any store, so
+  // that twelve independent random reads per thread are in flight
+  constexpr int kIlp = 4;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t s0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s0 < filled; s0 += kIlp * stride) {
+    int32_t src[kIlp];
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u) {
+      const int64_t s = s0 + u * stride;
+      src[u] = s < filled ? __ldcs(perm + s) : -1;
+    }
+    double x[kIlp], y[kIlp], z[kIlp];
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u) {
+      if (src[u] >= 0) { x[u] = __ldg(vx + src[u]); y[u] = __ldg(vy + src[u]); z[u] = __ldg(vz + src[u]); }
+    }
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u) {
+      const int64_t s = s0 + u * stride;
+      if (src[u] >= 0) { svx[s] = x[u]; svy[s] = y[u]; svz[s] = z[u]; }
+    }
   }
 }
 

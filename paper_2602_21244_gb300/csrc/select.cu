@@ -31,6 +31,7 @@ struct SelArgs {
   int32_t* tmp_round;
   uint32_t* tmp_dep;   // rounds (1-based, 0 = none) of the previous pair of i | of j << 16
   int32_t* wcnt;       // per cell: 32-candidate words of accept bits (ceil(M/32))
+  int32_t* ncand;      // per cell: the NTC candidate count M (k_sel_nwords)
   const int32_t* wofs; // their exclusive scan (first word of each cell; [n_cells] = total)
   uint32_t* bits;      // accept bit of candidate m of cell k: bits[wofs[k] + m/32] >> (m % 32)
   int64_t words_cap;   // capacity of bits; a cell whose words do not fit is re-evaluated
@@ -161,13 +162,21 @@ constexpr int kSelWarps = 8;
 // Words of accept bits per cell: ceil(M/32) for the cell's candidate count M.
 __global__ void k_sel_nwords(SelArgs a) {
   if (a.step_dev) a.step = *a.step_dev;
+  unsigned long long total = 0;
   for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n_cells; k += gridDim.x * blockDim.x) {
     const int32_t N = a.cs[k + 1] - a.cs[k];
     int bad = 0;
     const int32_t M = N < 2 ? 0 : ntc_count(a, k, N, &bad);
+    if (bad) set_status(a.status, DSMC_ERR_CAPACITY);
+    a.ncand[k] = M;
+    total += (unsigned long long)M;
     const int64_t words = ((int64_t)M + 31) / 32;
     a.wcnt[k] = (int32_t)(words <= a.words_cap ? words : 0);  // too many: never kept
   }
+  // one atomic per warp for the step's candidate count
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+  if ((threadIdx.x & 31) == 0 && total) atomicAdd(a.n_cand, total);
 }
 
 // Stage the cell's velocities (FP32) in this warp's shared-memory slice and
@@ -194,7 +203,7 @@ __device__ __forceinline__ CellView stage_cell(const SelArgs& a, float* sm, int3
   __syncwarp();
   // each velocity carries <= |v| 2^-24 rounding; g over three differences
   cv.dg = 4.0f * vmax * 5.9604645e-8f;
-  cv.sgmax32 = (float)sgk;
+  cv.sgmax32 = f64_to_f32(sgk);
   cv.inv_sgmax32 = 1.f / cv.sgmax32;
   cv.thr_raise = cv.sgmax32 * (1.f - 3e-4f);
   return cv;
@@ -212,12 +221,13 @@ __global__ void __launch_bounds__(kSelWarps * 32) k_sel_count(SelArgs a) {
       if (lane == 0) { a.counts[k] = 0; a.sgnew[k] = sgk; }
       continue;
     }
-    int bad = 0;
-    const int32_t M = ntc_count(a, k, N, &bad);
-    if (bad && lane == 0) set_status(a.status, DSMC_ERR_CAPACITY);
+    const int32_t M = a.ncand[k];   // from k_sel_nwords (which reports an overflow)
     const CellView cv = stage_cell(a, stage[wid], base, N, sgk, lane);
     int acc = 0;
-    double best = sgk;
+    // The maximum is taken on the bit patterns: for non-negative doubles the
+    // int64 order is the numeric order, and it keeps the FP64 pipe free
+    // (candidates that cannot raise the maximum carry -1.0, a negative int64).
+    long long best = __double_as_longlong(sgk);
     const int64_t w0 = a.wofs[k];
     const bool keep = bits_kept(a, k, M);
     for (int32_t c0 = 0; c0 < M; c0 += 32) {
@@ -226,16 +236,16 @@ __global__ void __launch_bounds__(kSelWarps * 32) k_sel_count(SelArgs a) {
       double sg = -1.0;
       const bool ok = m < M && candidate(a, cv, k, base, N, m, sgk, &i, &j, &sg);
       acc += ok;
-      best = fmax(best, sg);
+      best = max(best, __double_as_longlong(sg));
       const unsigned mask = __ballot_sync(0xffffffffu, ok);
       if (keep && lane == 0) a.bits[w0 + c0 / 32] = mask;
     }
     acc = warp_sum_i(acc);
-    best = warp_max(best);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
     if (lane == 0) {
       a.counts[k] = acc;
-      a.sgnew[k] = best;
-      atomicAdd(a.n_cand, (unsigned long long)M);
+      a.sgnew[k] = __longlong_as_double(best);
     }
     __syncwarp();
   }
@@ -263,8 +273,7 @@ __global__ void __launch_bounds__(kEmitWarps * 32) k_sel_emit(SelArgs a) {
     const int32_t base = a.cs[k], N = a.cs[k + 1] - base;
     if (N < 2) continue;
     const double sgk = a.sgmax[k];
-    int bad = 0;
-    const int32_t M = ntc_count(a, k, N, &bad);
+    const int32_t M = a.ncand[k];
     // accept bits from the count pass when they were kept, else re-evaluate
     const bool from_bits = bits_kept(a, k, M);
     const int64_t w0 = a.wofs[k];
@@ -499,7 +508,7 @@ struct SelWs {
   int32_t *counts, *offs, *tmp_round, *last, *round_count, *round_fill, *n_rounds;
   int32_t* chunk_cnt;  // [DSMC_MAX_ROUNDS][n_chunks] counts, then scatter bases
   int32_t n_chunks;
-  int32_t *wcnt, *wofs;
+  int32_t *wcnt, *wofs, *ncand;
   uint32_t* bits;
   int64_t words_cap;
   uint32_t* tmp_dep;
@@ -522,6 +531,7 @@ static size_t carve(SelWs* w, char* p, int32_t n, int32_t n_cells, int64_t capac
   w->tmp_dep = (uint32_t*)take(sizeof(uint32_t) * cap);
   w->n_chunks = (int32_t)((cap + kScatterChunk - 1) / kScatterChunk);
   w->wcnt = (int32_t*)take(sizeof(int32_t) * nc);
+  w->ncand = (int32_t*)take(sizeof(int32_t) * nc);
   w->wofs = (int32_t*)take(sizeof(int32_t) * (nc + 1));
   // accept bits for up to 32 candidates per accepted-pair slot
   w->words_cap = (int64_t)cap;
@@ -562,7 +572,7 @@ int launch_select(Ctx* c, const dsmc_gas_t& gas, int32_t n, int32_t n_cells, con
   SelArgs a;
   a.cs = cs; a.vx = vx; a.vy = vy; a.vz = vz; a.sgmax = sgmax; a.sgnew = w.sgnew;
   a.counts = w.counts; a.offs = w.offs; a.tmp = w.tmp; a.tmp_round = w.tmp_round; a.tmp_dep = w.tmp_dep;
-  a.wcnt = w.wcnt; a.wofs = w.wofs; a.bits = w.bits; a.words_cap = w.words_cap;
+  a.wcnt = w.wcnt; a.wofs = w.wofs; a.bits = w.bits; a.words_cap = w.words_cap; a.ncand = w.ncand;
   a.last = w.last; a.round_count = w.round_count; a.n_rounds = w.n_rounds; a.n_cand = w.n_cand;
   a.status = status_ptr(c); a.n_cells = n_cells; a.model = gas.model; a.capacity = capacity;
   a.seed = gas.seed; a.step = step; a.step_dev = graph_step_ptr(c); a.fn = gas.fn_over_vc; a.dt = gas.dt;
