@@ -143,6 +143,20 @@ __device__ __forceinline__ void silu4(float* z) {
   z[3] *= d[2] * r23;
 }
 
+// silu4 on two packed pairs (z0, z1), (z2, z3): the same operations in the
+// same order, the additions and the final products as FP32x2 instructions
+// (Blackwell's paired FP32 pipe), so the results equal silu4's bit for bit.
+__device__ __forceinline__ void silu4x2(float2& za, float2& zb) {
+  const float2 one = make_float2(1.f, 1.f);
+  const float2 da = __fadd2_rn(make_float2(__expf(-fmaxf(za.x, -20.f)), __expf(-fmaxf(za.y, -20.f))), one);
+  const float2 db = __fadd2_rn(make_float2(__expf(-fmaxf(zb.x, -20.f)), __expf(-fmaxf(zb.y, -20.f))), one);
+  const float d01 = da.x * da.y, d23 = db.x * db.y;
+  const float r = rcp_approx(d01 * d23);
+  const float r01 = r * d23, r23 = r * d01;
+  za = __fmul2_rn(za, make_float2(da.y * r01, da.x * r01));
+  zb = __fmul2_rn(zb, make_float2(db.y * r23, db.x * r23));
+}
+
 // The warp group a thread belongs to: G groups of blockDim/G threads, group g
 // owning tile slot g, TMEM columns [128 g, 128 g + 128) and named barrier 1 + g.
 struct Group {
@@ -183,7 +197,8 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
   const uint32_t lane_tm = acc + ((uint32_t)((gw & 3) * 32) << 16);
   const float* bs = (const float*)(smem + L.bias);
   const float* wo = (const float*)(smem + L.w_out);
-  float yp0 = 0.f, yp1 = 0.f, yp2 = 0.f;
+  // output-layer partial sums, even and odd columns apart
+  float2 yq0 = make_float2(0.f, 0.f), yq1 = yq0, yq2 = yq0;
   for (int l = 0; l < sh.n_hidden; ++l) {
     if (q.t == 0) {
       tc::fence_after();
@@ -231,30 +246,41 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
         const int c0 = cbeg + 16 * (pc + half);
         const bool more = pc + half + 1 < npieces;
         if (more) tc::ld16_async(lane_tm + (uint32_t)(c0 + 16), nxt);
-        float v[16];
+        // values in packed pairs (columns 2k, 2k + 1): bias additions,
+        // activation products, residuals and output-layer FMAs run two per
+        // instruction
+        float2 v[8];
+        const float2* b2 = (const float2*)(bl + c0);
 #pragma unroll
-        for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(cur[k]) + bl[c0 + k];
+        for (int k = 0; k < 8; ++k)
+          v[k] = __fadd2_rn(make_float2(__uint_as_float(cur[2 * k]), __uint_as_float(cur[2 * k + 1])), b2[k]);
         if (sh.act == 0) {
 #pragma unroll
-          for (int k = 0; k < 16; k += 4) silu4(v + k);
+          for (int k = 0; k < 8; k += 2) silu4x2(v[k], v[k + 1]);
         } else {
 #pragma unroll
-          for (int k = 0; k < 16; ++k) v[k] = act_f(sh.act, v[k]);
+          for (int k = 0; k < 8; ++k) v[k] = make_float2(act_f(sh.act, v[k].x), act_f(sh.act, v[k].y));
         }
         if (last) {
+          const float2* w0 = (const float2*)(wo + c0);
+          const float2* w1 = (const float2*)(wo + kWidth + c0);
+          const float2* w2 = (const float2*)(wo + 2 * kWidth + c0);
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            yp0 = fmaf(v[k], wo[c0 + k], yp0);
-            yp1 = fmaf(v[k], wo[kWidth + c0 + k], yp1);
-            yp2 = fmaf(v[k], wo[2 * kWidth + c0 + k], yp2);
+          for (int k = 0; k < 8; ++k) {
+            yq0 = __ffma2_rn(v[k], w0[k], yq0);
+            yq1 = __ffma2_rn(v[k], w1[k], yq1);
+            yq2 = __ffma2_rn(v[k], w2[k], yq2);
           }
         } else {
           uint32_t pk[8], lo[8];
+          const float2 m1 = make_float2(-1.f, -1.f);
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
-            const float a0 = v[2 * k], a1 = v[2 * k + 1];
-            pk[k] = tc::pack_bf16x2(a0, a1);
-            lo[k] = tc::pack_bf16x2(a0 - __uint_as_float(pk[k] << 16), a1 - __uint_as_float(pk[k] & 0xFFFF0000u));
+            pk[k] = tc::pack_bf16x2(v[k].x, v[k].y);
+            // a - hi is exact (hi is a rounding of a); as an FMA with -1
+            const float2 r = __ffma2_rn(make_float2(__uint_as_float(pk[k] << 16), __uint_as_float(pk[k] & 0xFFFF0000u)),
+                                        m1, v[k]);
+            lo[k] = tc::pack_bf16x2(r.x, r.y);
           }
 #pragma unroll
           for (int j = 0; j < 2; ++j) {
@@ -272,6 +298,7 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
       group_sync(q);
     }
   }
+  const float yp0 = yq0.x + yq0.y, yp1 = yq1.x + yq1.y, yp2 = yq2.x + yq2.y;
   // combine the column groups' partial outputs (column group 0 = the updaters)
   float* yb = (float*)(smem + L.ybuf + (uint32_t)q.g * L.ybuf_bytes);
   if (cg > 0) {
