@@ -379,14 +379,14 @@ int launch_gather(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_start,
 }
 
 // ---------------------------------------------------------------- moments
-// Eight lanes per cell (four cells per warp).  The sums are exact integer
+// Eight lanes per cell (four cells at a time per warp).  The sums are exact integer
 // sums, not FP64 ones (GB300's FP64 pipe, ~1/64 of FP32, bounded the FP64
 // version): each velocity component of a cell becomes the integer
 // x = round(v / 2^p), 2^p = the unit in the last place of the cell's largest
 // component (coarser by 2^c for cells of 1024 or more particles, so that a
 // cell's sum fits in 64 bits), formed from the bits of v on the integer
-// pipe.  Sums of x are exact in int64, sums of (x - round(mean))^2 in 128
-// bits; only the per-cell results are converted back to FP64.  The only
+// pipe.  Sums of x are exact in int64, sums of x^2 and the centred sum of
+// squares in 128 bits; only the per-cell results are converted back to FP64.  The only
 // rounding is each component's to the cell's resolution (at most half its
 // largest ulp), the same order as one FP64 addition per term, and the result
 // does not depend on the order of the sums.
@@ -441,47 +441,63 @@ __device__ __forceinline__ long long to_fix(double v, const FixScale& f) {
   return (hi & 0x80000000u) ? -(long long)x : (long long)x;
 }
 
-// the cell's unit 2^(E - 1075 + c) as a double
-__device__ __forceinline__ double fix_unit(const FixScale& f) { return ldexp(1.0, f.E - 1075 + f.c); }
-
-__device__ __forceinline__ double u128_to_double(unsigned __int128 v) {
-  return fma((double)(unsigned long long)(v >> 64), 18446744073709551616.0, (double)(unsigned long long)v);
-}
-
 // round(s / n) for n > 0
 __device__ __forceinline__ long long div_round(long long s, long long n) {
   return s >= 0 ? (s + n / 2) / n : -((-s + n / 2) / n);
 }
 
 // The exact integer moments of one cell (8 lanes): sums and centred sum of
-// squares in the cell's integer unit.
+// squares in the cell's integer unit.  Two passes over the cell: the largest
+// exponent, then the sums of x and of x^2; the centred sum follows exactly
+// from sum (x - m)^2 = sum x^2 - m (2 sum x - n m) in 128-bit integers.
 struct CellFix {
   FixScale f;
   long long sx, sy, sz, mx, my, mz;  // sums and rounded means (integer units)
   unsigned __int128 th;              // sum of squared deviations (units^2)
 };
 
+__device__ __forceinline__ unsigned __int128 sq128(long long x) {
+  const unsigned long long u = (unsigned long long)(x < 0 ? -x : x);
+  return (unsigned __int128)u * u;
+}
+
 __device__ __forceinline__ CellFix cell_fix(const double* __restrict__ vx, const double* __restrict__ vy,
                                             const double* __restrict__ vz, int32_t a, int32_t b, int sl) {
   CellFix C;
   int E = 0;
+#pragma unroll 4
   for (int32_t i = a + sl; i < b; i += kSeg) E = max(E, max(dexp(vx[i]), max(dexp(vy[i]), dexp(vz[i]))));
   C.f = cell_scale(seg_max_i(E), b - a);
   long long sx = 0, sy = 0, sz = 0;
-  for (int32_t i = a + sl; i < b; i += kSeg) { sx += to_fix(vx[i], C.f); sy += to_fix(vy[i], C.f); sz += to_fix(vz[i], C.f); }
+  unsigned __int128 s2 = 0;
+#pragma unroll 4
+  for (int32_t i = a + sl; i < b; i += kSeg) {
+    const long long x = to_fix(vx[i], C.f), y = to_fix(vy[i], C.f), z = to_fix(vz[i], C.f);
+    sx += x; sy += y; sz += z;
+    s2 += sq128(x) + sq128(y) + sq128(z);
+  }
   C.sx = seg_sum_ll(sx); C.sy = seg_sum_ll(sy); C.sz = seg_sum_ll(sz);
+  s2 = seg_sum_u128(s2);
   const long long n = b - a;
   C.mx = n > 0 ? div_round(C.sx, n) : 0;
   C.my = n > 0 ? div_round(C.sy, n) : 0;
   C.mz = n > 0 ? div_round(C.sz, n) : 0;
-  unsigned __int128 th = 0;
-  for (int32_t i = a + sl; i < b; i += kSeg) {
-    const long long dx = to_fix(vx[i], C.f) - C.mx, dy = to_fix(vy[i], C.f) - C.my, dz = to_fix(vz[i], C.f) - C.mz;
-    th += (unsigned __int128)((__int128)dx * dx) + (unsigned __int128)((__int128)dy * dy) +
-          (unsigned __int128)((__int128)dz * dz);
-  }
-  C.th = seg_sum_u128(th);
+  const __int128 corr = (__int128)C.mx * (2 * (__int128)C.sx - (__int128)n * C.mx) +
+                        (__int128)C.my * (2 * (__int128)C.sy - (__int128)n * C.my) +
+                        (__int128)C.mz * (2 * (__int128)C.sz - (__int128)n * C.mz);
+  C.th = s2 - (unsigned __int128)corr;
   return C;
+}
+
+__device__ __forceinline__ double th_double(unsigned __int128 v) {
+  return fma((double)(unsigned long long)(v >> 64), 18446744073709551616.0, (double)(unsigned long long)v);
+}
+
+// 2^(E - 1075 + c) built from its bits (integer pipe): normal for
+// E + c > 52, else subnormal
+__device__ __forceinline__ double unit_bits(const FixScale& f) {
+  const int e = f.E + f.c - 52;  // biased exponent of the unit
+  return e > 0 ? __longlong_as_double((long long)e << 52) : __longlong_as_double(1ll << (f.E + f.c - 1));
 }
 
 __global__ void __launch_bounds__(kCellWarps * 32)
@@ -497,13 +513,16 @@ k_moments(int32_t n_cells, const int32_t* __restrict__ cs, const double* __restr
     const bool has = k < n_cells;
     const int32_t a = has ? cs[k] : 0, b = has ? cs[k + 1] : 0;
     const CellFix C = cell_fix(vx, vy, vz, a, b, sl);
-    if (has && sl == 0) {
-      if (C.f.E == 0x7FF) set_status(status, DSMC_ERR_NONFINITE);
-      const double unit = fix_unit(C.f);
-      double* m = mom + 5 * (size_t)k;
-      m[0] = (double)(b - a);
-      m[1] = (double)C.sx * unit; m[2] = (double)C.sy * unit; m[3] = (double)C.sz * unit;
-      m[4] = u128_to_double(C.th) * unit * unit;
+    // lane c < 3 of the cell writes component c, lane 3 Theta, lane 4 N
+    if (has && sl < 5) {
+      if (sl == 0 && C.f.E == 0x7FF) set_status(status, DSMC_ERR_NONFINITE);
+      const double unit = unit_bits(C.f);
+      const long long sc = sl == 0 ? C.sx : sl == 1 ? C.sy : C.sz;
+      double val;
+      if (sl < 3) val = (double)sc * unit;
+      else if (sl == 3) val = th_double(C.th) * unit * unit;
+      else val = (double)(b - a);
+      mom[5 * (size_t)k + (sl < 4 ? 1 + sl : 0)] = val;
     }
   }
 }
@@ -521,7 +540,10 @@ int launch_moments(Ctx* c, int32_t n_cells, const int32_t* cs, const double* vx,
 // ---------------------------------------------------------------- moment matching
 // Sec. 2.5 (centred): v <- u_pre + alpha (v - u_post), alpha = sqrt(Th_pre/Th_post),
 // applied as v <- alpha v + (u_pre - alpha u_post) (FP64); u_post and Th_post
-// from the exact integer moments above.
+// from the exact integer moments above.  The three components' offsets are
+// formed by lanes 0..2 of the cell together (GB300's FP64 pipe costs a whole
+// warp instruction however few lanes are active) and passed to the cell's
+// eight lanes by shuffles.
 __global__ void __launch_bounds__(kCellWarps * 32)
 k_moment_match(int32_t n_cells, const int32_t* __restrict__ cs, const double* __restrict__ mom,
                double* __restrict__ vx, double* __restrict__ vy, double* __restrict__ vz) {
@@ -534,14 +556,21 @@ k_moment_match(int32_t n_cells, const int32_t* __restrict__ cs, const double* __
     const bool has = k < n_cells;
     const int32_t a = has ? cs[k] : 0, b = has ? cs[k + 1] : 0;
     const CellFix C = cell_fix(vx, vy, vz, a, b, sl);
-    if (b <= a) continue;
-    const double unit = fix_unit(C.f), n = (double)(b - a), inv = 1.0 / n;
-    const double ux = (double)C.sx * unit * inv, uy = (double)C.sy * unit * inv, uz = (double)C.sz * unit * inv;
-    const double th = u128_to_double(C.th) * unit * unit;
-    const double* m = mom + 5 * (size_t)k;
-    const double px = m[1] * inv, py = m[2] * inv, pz = m[3] * inv;
-    const double alpha = (b - a >= 2 && th > 0.0) ? sqrt(m[4] / th) : 1.0;
-    const double ox = px - alpha * ux, oy = py - alpha * uy, oz = pz - alpha * uz;
+    double alpha = 1.0, o = 0.0;
+    if (b > a) {
+      const int cmp = sl < 3 ? sl : 0;
+      const double unit = unit_bits(C.f), inv = 1.0 / (double)(b - a);
+      const long long sc = cmp == 0 ? C.sx : cmp == 1 ? C.sy : C.sz;
+      const double u = (double)sc * unit * inv;
+      const double th = th_double(C.th) * unit * unit;
+      const double* m = mom + 5 * (size_t)k;
+      alpha = (b - a >= 2 && th > 0.0) ? sqrt(m[4] / th) : 1.0;
+      o = m[1 + cmp] * inv - alpha * u;
+    }
+    const int l0 = seg * kSeg;
+    const double ox = __shfl_sync(0xffffffffu, o, l0), oy = __shfl_sync(0xffffffffu, o, l0 + 1),
+                 oz = __shfl_sync(0xffffffffu, o, l0 + 2);
+#pragma unroll 4
     for (int32_t i = a + sl; i < b; i += kSeg) {
       vx[i] = fma(alpha, vx[i], ox);
       vy[i] = fma(alpha, vy[i], oy);

@@ -108,6 +108,65 @@ def test_moments(name):
     assert np.all(np.abs(mom[:, 4] - ref[:, 4]) <= 1e-12 * np.maximum(ref[:, 4], 1e-300))
 
 
+def _ragged_cells(seed=11):
+    """Cells of sizes 0, 1, 2, 7, 33, 1023, 1024 (the coarsened integer unit
+    starts there), 4099, and 29 small ones: 37 cells, not a multiple of the
+    32-cell batch; mean velocities from 0 to 1e4 m/s over thermal spreads from
+    1e-3 to 1e3 m/s, one cell with components of very different magnitude."""
+    rng = np.random.default_rng(seed)
+    sizes = [0, 1, 2, 7, 33, 1023, 1024, 4099] + list(rng.integers(0, 80, 29))
+    vs, cs = [], [0]
+    for q, N in enumerate(sizes):
+        u = rng.uniform(-1e4, 1e4, 3) * (q % 3 == 0)
+        sd = 10.0 ** rng.uniform(-3, 3)
+        v = u + sd * rng.standard_normal((N, 3))
+        if q == 6 and N:
+            v[:, 2] *= 1e-9
+        vs.append(v)
+        cs.append(cs[-1] + N)
+    v = np.concatenate(vs)
+    return np.array(cs, np.int32), v[:, 0].copy(), v[:, 1].copy(), v[:, 2].copy()
+
+
+def test_moments_and_match_ragged_cells():
+    cs, vx, vy, vz = _ragged_cells()
+    C = ctx()
+    ref = O.cell_moments(cs, vx, vy, vz)
+    mom = host(C.cell_moments(cuda(cs), cuda(vx), cuda(vy), cuda(vz)))
+    assert C.sync_status() == 0
+    assert np.array_equal(mom[:, 0], ref[:, 0])
+    scale = np.maximum(ref[:, 0], 1)[:, None] * np.abs(np.stack([vx, vy, vz], 1)).max()
+    assert np.all(np.abs(mom[:, 1:4] - ref[:, 1:4]) <= 1e-13 * scale)
+    # Theta: 1e-12, plus the documented rounding of each component to the
+    # cell's integer unit (the ulp of its largest component, 2^c coarser for
+    # cells of 2^(10+c-1) or more particles): |dTheta| <= unit sqrt(3 n Theta) + 3 n unit^2 / 4
+    n = ref[:, 0]
+    vmax = np.array([np.abs(np.stack([vx, vy, vz], 1)[cs[k]:cs[k + 1]]).max() if cs[k + 1] > cs[k] else 0.0
+                     for k in range(len(cs) - 1)])
+    c = np.array([max(0, int(q).bit_length() - 10) for q in n])
+    unit = np.spacing(vmax) * 2.0 ** c
+    gate = 1e-12 * ref[:, 4] + unit * np.sqrt(3 * n * ref[:, 4]) + 0.75 * n * unit ** 2
+    assert np.all(np.abs(mom[:, 4] - ref[:, 4]) <= gate)
+    # match the moments of a perturbed copy back to the originals
+    rng = np.random.default_rng(3)
+    px, py, pz = (a * (1 + 0.1 * rng.standard_normal(len(a))) + 5.0 for a in (vx, vy, vz))
+    rx, ry, rz = O.moment_match(cs, ref, px, py, pz)
+    gx, gy, gz = cuda(px), cuda(py), cuda(pz)
+    C.moment_match(cuda(cs), cuda(ref), gx, gy, gz)
+    assert C.sync_status() == 0
+    for g_, r_ in ((gx, rx), (gy, ry), (gz, rz)):
+        g_ = host(g_)
+        assert np.all(np.abs(g_ - r_) <= 1e-12 * np.maximum(np.abs(r_), np.abs(r_).max() * 1e-3))
+    m2 = O.cell_moments(cs, host(gx), host(gy), host(gz))
+    assert np.all(np.abs(m2[:, 1:4] - ref[:, 1:4]) <= 1e-12 * scale)
+    # energy: 1e-12, plus the FP64 rounding of the stored velocities, which
+    # moves Theta by up to 2 |v| 2^-53 sd per particle (n sd^2 in all)
+    big = ref[:, 0] >= 2
+    sd = np.sqrt(ref[:, 4] / np.maximum(ref[:, 0], 1))
+    gate = 1e-12 + 8 * 2.0 ** -53 * vmax[big] / sd[big]
+    assert np.all(np.abs(m2[big, 4] - ref[big, 4]) <= gate * ref[big, 4])
+
+
 # ------------------------------------------------------------------ selection
 
 def _sgmax0(w, gas):
