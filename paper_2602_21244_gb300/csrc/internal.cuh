@@ -46,6 +46,12 @@ __device__ __forceinline__ double u53(uint32_t a, uint32_t b) {
   return (double)x * (1.0 / 9007199254740992.0);
 }
 
+// the same uniform rounded to FP32 (within 2^-23 relative of u53(a, b);
+// the low word matters below 2^-8)
+__device__ __forceinline__ float u_f32(uint32_t a, uint32_t b) {
+  return fmaf(__uint2float_rn(b >> 11), 0x1p-53f, __uint2float_rn(a) * 0x1p-32f);
+}
+
 // uniform integer in [0, n): high word of w*n
 __device__ __forceinline__ uint32_t mulhi_n(uint32_t w, uint32_t n) { return __umulhi(w, n); }
 

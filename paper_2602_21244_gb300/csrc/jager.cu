@@ -462,8 +462,21 @@ __device__ __forceinline__ void deflect(double u, double v, double w, double g, 
 // -- then scaled in FP64 to |v_r'| = |v_r| exactly: s = |v_r|/|y| from an
 // FP32 estimate and one FP64 Newton step on s^2 |y|^2 = |v_r|^2 (relative
 // error ~1e-14).  About a third of the FP64 work of deflect().
+__device__ __forceinline__ void deflect_shell_h(double ux, double uy, double uz, double g2, float chi, float eps,
+                                                double* h, double* Y);
+
 __device__ __forceinline__ void deflect_shell(double ux, double uy, double uz, double g2, float chi, float eps,
                                               double* o) {
+  double h, Y[3];
+  deflect_shell_h(ux, uy, uz, g2, chi, eps, &h, Y);
+  o[0] = 2.0 * h * Y[0]; o[1] = 2.0 * h * Y[1]; o[2] = 2.0 * h * Y[2];
+}
+
+// The same rotation, returned as v_r' = 2 h Y (Y the FP32 rotated direction
+// widened to FP64, h half the FP64 shell scale), so that a caller can form
+// the post-collision velocities as c +- h Y with one FMA each.
+__device__ __forceinline__ void deflect_shell_h(double ux, double uy, double uz, double g2, float chi, float eps,
+                                                double* h, double* Yo) {
   const float fx = f64_to_f32(ux), fy = f64_to_f32(uy), fz = f64_to_f32(uz);
   float sc, cc, se, ce;
   sincosf(chi, &sc, &cc);
@@ -483,14 +496,15 @@ __device__ __forceinline__ void deflect_shell(double ux, double uy, double uz, d
   const float y1 = cc * fy + gf * sc * (ce * cy + se * ay);
   const float y2 = cc * fz + gf * sc * (ce * cz + se * az);
   const double Y0 = y0, Y1 = y1, Y2 = y2;
+  Yo[0] = Y0; Yo[1] = Y1; Yo[2] = Y2;
   const double ny2 = Y0 * Y0 + Y1 * Y1 + Y2 * Y2;
-  if (!(ny2 > 0.0)) { o[0] = o[1] = o[2] = 0.0; return; }
+  if (!(ny2 > 0.0)) { *h = 0.0; return; }
   const float ny2f = (float)ny2, g2f = (float)g2;
   const float sf = sqrtf(g2f / ny2f);
   const double s0 = sf;
   const double res = g2 - s0 * s0 * ny2;
-  const double sfin = s0 + res * (double)(0.5f * sf / g2f);
-  o[0] = sfin * Y0; o[1] = sfin * Y1; o[2] = sfin * Y2;
+  // one Newton step on s^2 ny2 = g2 from s0, halved: h = s / 2
+  *h = 0.5 * s0 + res * (double)(0.25f * sf / g2f);
 }
 
 struct JagerArgs {
@@ -580,6 +594,7 @@ struct TableArgs {
   const uint64_t* step_dev;
   const float* T;
   int32_t nb, nE;
+  float nb1;                 // nb - 1: x = b~ (nb - 1)
   float lnE_min, inv_dlnE;   // y = (ln E - lnE_min) inv_dlnE
   float mass_over_4k;
   const int4* pairs;
@@ -632,17 +647,20 @@ __global__ void __launch_bounds__(256) k_collide_table(TableArgs a) {
         const double g2 = ux * ux + uy * uy + uz * uz;
         const u32x4 w = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_JAGER);
         float chi = 0.f;
+        double h = 0.0, Y[3] = {0.0, 0.0, 0.0};
         if (g2 > 0.0) {
-          const float x = (float)(sqrt(u53(w.x, w.y)) * (a.nb - 1));
+          // the table coordinate and the azimuth only ever enter in FP32:
+          // their uniforms are formed in FP32 too (GB300's FP64 pipe bounds
+          // this kernel), to within one FP32 rounding of the FP64 values
+          const float x = sqrtf(u_f32(w.x, w.y)) * a.nb1;
           const float y = (logf(a.mass_over_4k * (float)g2) - a.lnE_min) * a.inv_dlnE;
           chi = chi_lookup(a, x, y);
+          deflect_shell_h(ux, uy, uz, g2, chi, u_f32(w.z, w.w) * 6.2831855f, &h, Y);
         }
         if (a.chi_out) a.chi_out[p] = chi;
-        double o[3] = {0.0, 0.0, 0.0};
-        if (g2 > 0.0) deflect_shell(ux, uy, uz, g2, chi, (float)(2.0 * DSMC_PI * u53(w.z, w.w)), o);
-        const double cx = 0.5 * (xi + xj), cy = 0.5 * (yi + yj), cz = 0.5 * (zi + zj);
-        __stcg(a.vx + q.x, cx + 0.5 * o[0]); __stcg(a.vy + q.x, cy + 0.5 * o[1]); __stcg(a.vz + q.x, cz + 0.5 * o[2]);
-        __stcg(a.vx + q.y, cx - 0.5 * o[0]); __stcg(a.vy + q.y, cy - 0.5 * o[1]); __stcg(a.vz + q.y, cz - 0.5 * o[2]);
+        const double sx = 0.5 * (xi + xj), sy = 0.5 * (yi + yj), sz = 0.5 * (zi + zj);
+        __stcg(a.vx + q.x, fma(h, Y[0], sx)); __stcg(a.vy + q.x, fma(h, Y[1], sy)); __stcg(a.vz + q.x, fma(h, Y[2], sz));
+        __stcg(a.vx + q.y, fma(-h, Y[0], sx)); __stcg(a.vy + q.y, fma(-h, Y[1], sy)); __stcg(a.vz + q.y, fma(-h, Y[2], sz));
         release_pair(a.done, q.x, q.y, (unsigned)(r + 1));
       }
     }
@@ -750,7 +768,7 @@ int launch_collide_table(Ctx* c, const dsmc_gas_t& gas, const dsmc_chi_table_t& 
   const int blocks = sm_count(c) * (sh.blocks_per_sm > 0 && sh.blocks_per_sm < occ ? sh.blocks_per_sm : occ);
   TableArgs a;
   a.seed = gas.seed; a.step = step; a.step_dev = graph_step_ptr(c);
-  a.T = tab.chi; a.nb = tab.nb; a.nE = tab.nE;
+  a.T = tab.chi; a.nb = tab.nb; a.nE = tab.nE; a.nb1 = (float)(tab.nb - 1);
   a.lnE_min = (float)tab.lnE_min;
   a.inv_dlnE = (float)((tab.nE - 1) / (tab.lnE_max - tab.lnE_min));
   a.mass_over_4k = (float)(gas.mass / (4.0 * DSMC_KB));
