@@ -4,9 +4,10 @@
 //   k_sel_count   warp per cell: M = floor(1/2 N(N-1) F_N/V_c (sg)max dt + U),
 //                 evaluate every candidate, count acceptances, new (sg)max
 //   scan          counts -> per-cell pair offsets
-//   k_sel_emit    warp per cell: redo the candidates in order, ballot-compact
-//                 the accepted ones, then one lane walks them in candidate
-//                 order assigning round = 1 + max(last[i], last[j])
+//   k_sel_emit    warp per cell: the accepted candidates (from the count
+//                 pass's accept bits) compacted in candidate order and their
+//                 particles drawn, then rounds in candidate order:
+//                 round = 1 + max(last[i], last[j])
 //   scan          per-round counts -> round offsets
 //   k_sel_rcount, k_sel_rscan, k_sel_scatter: stable round-major regrouping
 //                 of the pairs (cell-major candidate order inside a round),
@@ -254,7 +255,8 @@ __global__ void __launch_bounds__(kSelWarps * 32) k_sel_count(SelArgs a) {
 constexpr int kEmitWarps = 4;
 constexpr int kEmitPairs = 1024;  // accepted pairs of a cell kept in shared memory
 
-__global__ void __launch_bounds__(kEmitWarps * 32) k_sel_emit(SelArgs a) {
+// five blocks per SM (shared memory allows five): registers capped to match
+__global__ void __launch_bounds__(kEmitWarps * 32, 5) k_sel_emit(SelArgs a) {
   if (a.step_dev) a.step = *a.step_dev;
   __shared__ float stage[kEmitWarps][3 * kStage];
   __shared__ uint32_t spairs[kEmitWarps][kEmitPairs];   // local i | local j << 16, candidate order
@@ -282,17 +284,50 @@ __global__ void __launch_bounds__(kEmitWarps * 32) k_sel_emit(SelArgs a) {
     const int32_t p0 = a.offs[k], p1 = a.offs[k + 1];
     const bool local = N <= kStage && p1 - p0 <= kEmitPairs;
     int32_t pos = p0;
-    for (int32_t c0 = 0; c0 < M; c0 += 32) {
+    if (from_bits) {
+      // Accepted candidates first compacted in candidate order (32 words at a
+      // time, lane L expanding word L into the staging slice, unused on this
+      // path), then drawn 32 at a time: the generator runs once per accepted
+      // candidate with every lane busy.
+      uint32_t* list = (uint32_t*)stage[wid];
+      const int32_t nwords = (M + 31) / 32;
+      for (int32_t wb = 0; wb < nwords; wb += 32) {
+        const int32_t wi = wb + lane;
+        uint32_t bw = wi < nwords ? a.bits[w0 + wi] : 0u;
+        const int cnt = __popc(bw);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += v;
+        }
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        int r = incl - cnt;
+        while (bw) {
+          list[r++] = (uint32_t)(wi * 32 + __ffs(bw) - 1);
+          bw &= bw - 1u;
+        }
+        __syncwarp();
+        for (int t0 = 0; t0 < tot; t0 += 32) {
+          const int t = t0 + lane;
+          if (t < tot) {
+            const int32_t m = (int32_t)list[t];
+            int32_t i, j;
+            cand_ij(a, k, N, m, &i, &j);
+            const int32_t q = pos + t;
+            a.tmp[q] = make_int4(base + i, base + j, k, m);
+            if (local) spairs[wid][q - p0] = (uint32_t)i | ((uint32_t)j << 16);
+          }
+        }
+        pos += tot;
+        __syncwarp();
+      }
+    }
+    for (int32_t c0 = 0; c0 < M && !from_bits; c0 += 32) {
       const int32_t m = c0 + lane;
       int32_t i = 0, j = 0;
       double sg;
-      bool ok;
-      if (from_bits) {
-        ok = (a.bits[w0 + c0 / 32] >> lane) & 1u;
-        if (ok) cand_ij(a, k, N, m, &i, &j);
-      } else {
-        ok = m < M && candidate(a, cv, k, base, N, m, sgk, &i, &j, &sg);
-      }
+      const bool ok = m < M && candidate(a, cv, k, base, N, m, sgk, &i, &j, &sg);
       const unsigned mask = __ballot_sync(0xffffffffu, ok);
       if (ok) {
         const int32_t q = pos + __popc(mask & ((1u << lane) - 1u));
@@ -309,41 +344,61 @@ __global__ void __launch_bounds__(kEmitWarps * 32) k_sel_emit(SelArgs a) {
     __syncwarp();
     // rounds in candidate order: round = 1 + max(last round of i, of j)
     if (local) {
-      // Warp-parallel: in each batch of 32 pairs (candidate order), a lane
-      // commits once it is the lowest uncommitted lane of the batch touching
-      // each of its two particles (atomicMin claims), so every earlier pair
-      // sharing a particle has already updated `last`; lanes committing
-      // together share no particle.  Same rounds as the sequential rule.
+      // Warp-parallel, batch of 32 pairs (candidate order) at a time.  Each
+      // lane finds the nearest earlier lane of the batch touching each of its
+      // particles (per-particle lane masks), and the rounds follow from
+      // round = max(L_i, L_j), L = round + 1 of that lane, or the particle's
+      // round + 1 before the batch, by fixed-point iteration over shuffles:
+      // the links point to earlier lanes only, so it ends after (depth + 1)
+      // steps with the rounds of the sequential rule.
       uint16_t* last = slast[wid];
-      int* claim = (int*)stage[wid];   // the velocity staging is no longer needed
-      for (int32_t t = lane; t < N; t += 32) claim[t] = 32;
+      uint32_t* msk = (uint32_t*)stage[wid];   // the velocity staging is no longer needed
+      for (int32_t t = lane; t < N; t += 32) msk[t] = 0u;
       __syncwarp();
       int rm = -1;
+      const unsigned below = (1u << lane) - 1u;
       for (int32_t b0 = p0; b0 < p1; b0 += 32) {
         const int32_t p = b0 + lane;
-        bool done = p >= p1;
-        const uint32_t ij = done ? 0u : spairs[wid][p - p0];
+        const bool act = p < p1;
+        const uint32_t ij = act ? spairs[wid][p - p0] : 0u;
         const uint32_t i = ij & 0xFFFFu, j = ij >> 16;
-        while (__any_sync(0xffffffffu, !done)) {
-          if (!done) { atomicMin(&claim[i], lane); atomicMin(&claim[j], lane); }
-          __syncwarp();
-          const bool go = !done && claim[i] == lane && claim[j] == lane;
-          if (go) {
-            const int li = last[i], lj = last[j];            // stored as round + 1
-            int r = li > lj ? li : lj;                        // = 1 + max(round) in 0-based rounds
-            if (r >= DSMC_MAX_ROUNDS) { set_status(a.status, DSMC_ERR_UNSUPPORTED); r = DSMC_MAX_ROUNDS - 1; }
-            last[i] = (uint16_t)(r + 1);
-            last[j] = (uint16_t)(r + 1);
-            a.tmp_round[p] = r;
-            a.tmp_dep[p] = (uint32_t)li | ((uint32_t)lj << 16);
-            atomicAdd(&hist[r], 1);
-            rm = r > rm ? r : rm;
-          }
-          __syncwarp();
-          if (!done) { claim[i] = 32; claim[j] = 32; }
-          done = done || go;
-          __syncwarp();
+        if (act) { atomicOr(&msk[i], 1u << lane); atomicOr(&msk[j], 1u << lane); }
+        __syncwarp();
+        int pi = lane, pj = lane, lpi = 0, lpj = 0;
+        bool lasti = false, lastj = false;
+        if (act) {
+          const uint32_t mi = msk[i], mj = msk[j];
+          if (mi & below) pi = 31 - __clz(mi & below);
+          if (mj & below) pj = 31 - __clz(mj & below);
+          lasti = (mi >> lane) == 1u;   // no later lane of the batch touches i
+          lastj = (mj >> lane) == 1u;
+          lpi = last[i]; lpj = last[j];  // round + 1 before the batch (0 = none)
         }
+        int r = max(lpi, lpj), Li = lpi, Lj = lpj;
+        for (;;) {
+          const int ri = __shfl_sync(0xffffffffu, r, pi), rj = __shfl_sync(0xffffffffu, r, pj);
+          Li = pi == lane ? lpi : ri + 1;
+          Lj = pj == lane ? lpj : rj + 1;
+          const int rn = max(Li, Lj);
+          const bool ch = act && rn != r;
+          if (act) r = rn;
+          if (!__any_sync(0xffffffffu, ch)) break;
+        }
+        if (act) {
+          if (r >= DSMC_MAX_ROUNDS) { set_status(a.status, DSMC_ERR_UNSUPPORTED); r = DSMC_MAX_ROUNDS - 1; }
+          a.tmp_round[p] = r;
+          a.tmp_dep[p] = (uint32_t)Li | ((uint32_t)Lj << 16);
+          rm = r > rm ? r : rm;
+          if (lasti) last[i] = (uint16_t)(r + 1);
+          if (lastj) last[j] = (uint16_t)(r + 1);
+          msk[i] = 0u; msk[j] = 0u;
+        }
+        const unsigned am = __ballot_sync(0xffffffffu, act);
+        if (act) {
+          const unsigned same = __match_any_sync(am, r);
+          if ((same & below) == 0) atomicAdd(&hist[r], __popc(same));
+        }
+        __syncwarp();
       }
       rm = __reduce_max_sync(0xffffffffu, rm);
       if (lane == 0) {
