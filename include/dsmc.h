@@ -151,9 +151,10 @@ int64_t dsmc_ctx_launch_count(dsmc_ctx_t* ctx);
 /* Sec. 2.6 (1): sort particles by cell index so each cell's particles are
  * contiguous.  Stable counting sort: perm[s] is the input index of sorted
  * slot s, slots of a cell keep the input order.  cell_start[n_cells+1]
- * holds each cell's first slot; s{x,y,z} receive the gathered velocities.
- * cell_id[i] outside [0, n_cells) records DSMC_ERR_ARG; such a particle gets
- * no slot, and perm / s{x,y,z} past cell_start[n_cells] are left unwritten. */
+ * holds each cell's first slot; s{x,y,z} receive the gathered velocities
+ * (s{x,y,z} must not overlap v{x,y,z}).  cell_id[i] outside
+ * [0, n_cells) records DSMC_ERR_ARG; such a particle belongs to no cell, and
+ * the entries of perm and s{x,y,z} past cell_start[n_cells] are unspecified. */
 size_t dsmc_sort_workspace_size(int32_t n, int32_t n_cells);
 int dsmc_sort_cells(dsmc_ctx_t* ctx, int32_t n, int32_t n_cells, const int32_t* cell_id,
                     const double* vx, const double* vy, const double* vz, int32_t* perm,
