@@ -456,9 +456,12 @@ int dsmc_autotune_chi(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_potenti
 /* Same step from and to HOST memory: copies cell_id_host / v*_host into
  * device buffers reserved by dsmc_ctx_reserve, runs dsmc_step, copies the
  * sorted post-collision velocities and perm back, and synchronises the
- * stream.  sigma_g_max stays on the device between calls (initialised from
- * T_cell_host on the first call after a reserve).  Returns the first error,
- * device-side ones included. */
+ * stream.  The velocity upload runs on a side stream of the context while
+ * the cell ids are sorted, and perm downloads while the pairs are selected
+ * and updated; all of it has completed when the call returns.  sigma_g_max
+ * stays on the device between calls (initialised from T_cell_host on the
+ * first call after a reserve).  Returns the first error, device-side ones
+ * included.  Host arrays should be page-locked for the copies to overlap. */
 int dsmc_ctx_reserve(dsmc_ctx_t* ctx, int32_t n_max, int32_t n_cells, int64_t capacity);
 int dsmc_step_host(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_path_t* path,
                    int32_t n, const int32_t* cell_id_host, const double* vx_host,

@@ -24,6 +24,9 @@ struct Ctx {
   dsmc_step_buffers_t rb = {};
   double* r_T = nullptr;
   void* r_host_info = nullptr;
+  // dsmc_step_host: a side stream for the copies that overlap the step
+  cudaStream_t r_side = nullptr;
+  cudaEvent_t r_ev[4] = {nullptr, nullptr, nullptr, nullptr};
   int64_t launches = 0;
   int64_t graph_launches = 0;
   // step graph
@@ -157,6 +160,9 @@ void dsmc_ctx_destroy(dsmc_ctx_t* c) {
   if (c->h_status) cudaFreeHost(c->h_status);
   if (c->r_mem) cudaFree(c->r_mem);
   if (c->r_host_info) cudaFreeHost(c->r_host_info);
+  for (cudaEvent_t e : c->r_ev)
+    if (e) cudaEventDestroy(e);
+  if (c->r_side) cudaStreamDestroy(c->r_side);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   delete c;
 }
@@ -484,6 +490,9 @@ static int collide_step(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t*
   return rc;
 }
 
+static int step_after_sort(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t* path,
+                           const dsmc_step_buffers_t* B, uint64_t step, void* stream);
+
 int dsmc_step(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t* path,
               const dsmc_step_buffers_t* B, uint64_t step, void* stream) {
   CHECK_CTX(c);
@@ -494,7 +503,14 @@ int dsmc_step(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t* path,
   int rc = dsmc_sort_cells(c, B->n, B->n_cells, B->cell_id, B->vx, B->vy, B->vz, B->perm,
                            B->cell_start, B->svx, B->svy, B->svz, B->ws, B->ws_bytes, stream);
   if (rc) return rc;
-  rc = dsmc_cell_moments(c, B->n_cells, B->cell_start, B->svx, B->svy, B->svz, B->mom, stream);
+  return step_after_sort(c, gas, path, B, step, stream);
+}
+
+// the step from the sorted velocities on: moments, selection, pair update,
+// moment matching
+static int step_after_sort(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t* path,
+                           const dsmc_step_buffers_t* B, uint64_t step, void* stream) {
+  int rc = dsmc_cell_moments(c, B->n_cells, B->cell_start, B->svx, B->svy, B->svz, B->mom, stream);
   if (rc) return rc;
   rc = dsmc_select_pairs(c, gas, B->n, B->n_cells, B->cell_start, B->svx, B->svy, B->svz,
                          B->sigma_g_max, step, B->capacity, B->pairs, B->deps, B->round_offsets, B->info,
@@ -583,14 +599,28 @@ int dsmc_step_host(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t* path
   REQUIRE(c, n >= 0 && n <= c->r_n, "step_host: n exceeds the reserved size");
   REQUIRE(c, n == 0 || (cell_id_h && vx_h && vy_h && vz_h && svx_h && svy_h && svz_h),
           "step_host: null host array");
+  if (int rc = check_gas(c, gas)) return rc;
   cudaStream_t s = S(stream);
   dsmc_step_buffers_t b = c->rb;
   b.n = n;
   const size_t n4 = 4 * (size_t)n, n8 = 8 * (size_t)n;
-  bool ok = cudaMemcpyAsync((void*)b.cell_id, cell_id_h, n4, cudaMemcpyHostToDevice, s) == cudaSuccess &&
-            cudaMemcpyAsync((void*)b.vx, vx_h, n8, cudaMemcpyHostToDevice, s) == cudaSuccess &&
-            cudaMemcpyAsync((void*)b.vy, vy_h, n8, cudaMemcpyHostToDevice, s) == cudaSuccess &&
-            cudaMemcpyAsync((void*)b.vz, vz_h, n8, cudaMemcpyHostToDevice, s) == cudaSuccess;
+  if (!c->r_side) {
+    if (cudaStreamCreateWithFlags(&c->r_side, cudaStreamNonBlocking) != cudaSuccess)
+      return dsmc::record(c, DSMC_ERR_CUDA, "step_host: side stream");
+    for (cudaEvent_t& e : c->r_ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+        return dsmc::record(c, DSMC_ERR_CUDA, "step_host: event");
+  }
+  cudaStream_t s2 = c->r_side;
+  // Copies overlap the step: the velocities upload on the side stream while
+  // the radix passes sort the cell ids, and perm downloads while the pairs
+  // are selected and updated.
+  bool ok = cudaEventRecord(c->r_ev[0], s) == cudaSuccess && cudaStreamWaitEvent(s2, c->r_ev[0], 0) == cudaSuccess &&
+            cudaMemcpyAsync((void*)b.vx, vx_h, n8, cudaMemcpyHostToDevice, s2) == cudaSuccess &&
+            cudaMemcpyAsync((void*)b.vy, vy_h, n8, cudaMemcpyHostToDevice, s2) == cudaSuccess &&
+            cudaMemcpyAsync((void*)b.vz, vz_h, n8, cudaMemcpyHostToDevice, s2) == cudaSuccess &&
+            cudaEventRecord(c->r_ev[1], s2) == cudaSuccess &&
+            cudaMemcpyAsync((void*)b.cell_id, cell_id_h, n4, cudaMemcpyHostToDevice, s) == cudaSuccess;
   if (!ok) return dsmc::record(c, DSMC_ERR_CUDA, "step_host: host-to-device copy failed");
   if (!c->r_sg_ready) {
     REQUIRE(c, T_cell_h, "step_host: T_cell_host needed on the first call");
@@ -600,12 +630,21 @@ int dsmc_step_host(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t* path
     if (rc) return rc;
     c->r_sg_ready = true;
   }
-  int rc = dsmc_step(c, gas, path, &b, step, stream);
+  int rc = dsmc::launch_sort_keys(c, n, b.n_cells, b.cell_id, b.perm, b.cell_start, b.ws, b.ws_bytes, s);
   if (rc) return rc;
+  ok = cudaEventRecord(c->r_ev[2], s) == cudaSuccess && cudaStreamWaitEvent(s2, c->r_ev[2], 0) == cudaSuccess &&
+       (!perm_h || cudaMemcpyAsync(perm_h, b.perm, n4, cudaMemcpyDeviceToHost, s2) == cudaSuccess) &&
+       cudaEventRecord(c->r_ev[3], s2) == cudaSuccess && cudaStreamWaitEvent(s, c->r_ev[1], 0) == cudaSuccess;
+  if (!ok) return dsmc::record(c, DSMC_ERR_CUDA, "step_host: stream ordering failed");
+  rc = dsmc::launch_gather(c, n, b.n_cells, b.cell_start, b.perm, b.vx, b.vy, b.vz, b.svx, b.svy, b.svz, s);
+  if (!rc) rc = step_after_sort(c, gas, path, &b, step, stream);
+  // the side stream's copies join the caller's stream whatever happened
+  const bool joined = cudaStreamWaitEvent(s, c->r_ev[3], 0) == cudaSuccess;
+  if (rc) return rc;
+  if (!joined) return dsmc::record(c, DSMC_ERR_CUDA, "step_host: stream ordering failed");
   ok = cudaMemcpyAsync(svx_h, b.svx, n8, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
        cudaMemcpyAsync(svy_h, b.svy, n8, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
        cudaMemcpyAsync(svz_h, b.svz, n8, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
-       (!perm_h || cudaMemcpyAsync(perm_h, b.perm, n4, cudaMemcpyDeviceToHost, s) == cudaSuccess) &&
        cudaMemcpyAsync(c->r_host_info, b.info, sizeof(dsmc_select_info_t), cudaMemcpyDeviceToHost, s) ==
            cudaSuccess;
   if (!ok) return dsmc::record(c, DSMC_ERR_CUDA, "step_host: device-to-host copy failed");

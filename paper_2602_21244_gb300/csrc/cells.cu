@@ -326,6 +326,14 @@ int launch_sort(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_id, cons
                 const double* vy, const double* vz, int32_t* perm, int32_t* cell_start,
                 double* svx, double* svy, double* svz, void* ws, size_t ws_bytes,
                 cudaStream_t s) {
+  if (int rc = launch_sort_keys(c, n, n_cells, cell_id, perm, cell_start, ws, ws_bytes, s)) return rc;
+  return launch_gather(c, n, n_cells, cell_start, perm, vx, vy, vz, svx, svy, svz, s);
+}
+
+// The radix passes on the cell ids alone: perm and cell_start (the velocities
+// are not read, so their upload may still be in flight).
+int launch_sort_keys(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_id, int32_t* perm,
+                     int32_t* cell_start, void* ws, size_t ws_bytes, cudaStream_t s) {
   if (ws_bytes < sort_ws(n, n_cells)) return record(c, DSMC_ERR_ARG, "sort: workspace too small");
   const size_t nn = (size_t)(n > 0 ? n : 1);
   const int32_t chunks = (int32_t)((nn + kRsChunk - 1) / kRsChunk);
@@ -364,7 +372,7 @@ int launch_sort(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_id, cons
   }
   k_cell_start<<<grid_for((int64_t)n + 1, 256, sm_count(c) * 8), 256, 0, s>>>(kin, n, n_cells, cell_start);
   count_launches(c, 1);
-  return launch_gather(c, n, n_cells, cell_start, perm, vx, vy, vz, svx, svy, svz, s);
+  return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
 }
 
 int launch_gather(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_start, const int32_t* perm,

@@ -232,6 +232,8 @@ int launch_sort(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_id, cons
                 const double* vy, const double* vz, int32_t* perm, int32_t* cell_start,
                 double* svx, double* svy, double* svz, void* ws, size_t ws_bytes,
                 cudaStream_t s);
+int launch_sort_keys(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_id, int32_t* perm,
+                     int32_t* cell_start, void* ws, size_t ws_bytes, cudaStream_t s);
 size_t sort_ws(int32_t n, int32_t n_cells);
 int launch_moments(Ctx* c, int32_t n_cells, const int32_t* cs, const double* vx,
                    const double* vy, const double* vz, double* mom, cudaStream_t s);
