@@ -197,8 +197,10 @@ __device__ __forceinline__ bool wait_deps(const unsigned* done, int32_t i, int32
   if (ni == 0 && nj == 0) return true;
   if (ld_relaxed(done + i) >= ni && ld_relaxed(done + j) >= nj) { fence_acq_rel(); return true; }
   const uint64_t t0 = globaltimer_ns();
+  unsigned sleep_ns = 32;   // doubling up to 1 us: a waiting lane costs few issue slots
   for (;;) {
-    __nanosleep(32);
+    __nanosleep(sleep_ns);
+    if (sleep_ns < 1024) sleep_ns <<= 1;
     if (ld_relaxed(done + i) >= ni && ld_relaxed(done + j) >= nj) { fence_acq_rel(); return true; }
     if (ld_relaxed(abort_word) || globaltimer_ns() - t0 > limit_ns) {
       set_status(status, DSMC_ERR_TIMEOUT);

@@ -80,13 +80,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// The same with a suspend-time hint: the thread may sleep in the
+// instruction until the phase completes or about hint_ns pass, instead of
+// polling (a polling lane takes issue slots from the warps doing work).
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* mbar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(mbar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
 // Bounded wait: false (and DSMC_ERR_TIMEOUT recorded) if the phase did not
 // complete within limit_ns.
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, int* status,
                                           uint64_t limit_ns) {
   if (mbar_try_wait(mbar, parity)) return true;
   const uint64_t t0 = globaltimer_ns();
-  while (!mbar_try_wait(mbar, parity)) {
+  while (!mbar_try_wait_hint(mbar, parity, 20000u)) {
     if (globaltimer_ns() - t0 > limit_ns) {
       set_status(status, DSMC_ERR_TIMEOUT);
       return false;
