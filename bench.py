@@ -35,6 +35,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 MLP_FLOP_PER_PAIR = 2 * (8 * 128 + 128 * 128 * 2 + 128 * 3)   # 68,352 (unpadded)
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per pair of
+# k_collide_neural, from one ncu capture of a full-size launch on the
+# hypersonic gas: 984.7 + 948.6 MB for about 6.882 million pairs
+# (profiles/step_kernels_hypersonic.md); the roofline's traffic is this times
+# the pairs of the timed launch.
+NEURAL_DRAM_BYTES_PER_PAIR = (984.74e6 + 948.55e6) / 6.882e6
 CANDIDATE_BYTES = 48                                             # two FP64 3-vectors read
 PAIR_BYTES = 104                                                 # 2x24 read + 2x24 write + 8 index
 
@@ -422,7 +428,8 @@ def main():
             achieved = nk["pairs"] * MLP_FLOP_PER_PAIR / (nk["ms"] * 1e-3) / 1e12
             peak = pk.get("bf16_tflops_sustained") if pk else 1700.0
             roof = {"bound": "tensor", "kernel": "k_collide_neural", "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                    "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": NEURAL_DRAM_BYTES_PER_PAIR * nk["pairs"],
                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained" if pk else "fallback"}
         cb = None
         if not args.no_cpu_baseline:
