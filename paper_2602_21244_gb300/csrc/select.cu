@@ -135,14 +135,17 @@ __device__ __forceinline__ bool candidate(const SelArgs& a, const CellView& cv, 
     dy = (float)(a.vy[base + i] - a.vy[base + j]);
     dz = (float)(a.vz[base + i] - a.vz[base + j]);
   }
-  const float g = sqrtf(dx * dx + dy * dy + dz * dz);
+  // approximate square root and quotient (errors ~2^-22, far inside the
+  // screen's 1e-4 relative margin; every decision near U is taken in FP64)
+  float g;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(g) : "f"(dx * dx + dy * dy + dz * dz));
   const float sg = a.model == 1 ? a.k32 * g : a.k32 * __powf(g, a.e32);
   const float ratio = sg * cv.inv_sgmax32;
   // U32 <= U < U32 + 2^-24 (top 24 bits of the 53-bit uniform)
   const float U32 = (float)(w.z >> 8) * 5.9604645e-8f;
   // error bound of the FP32 ratio: 1e-4 relative (arithmetic, __powf) plus
   // the effect of the FP32 rounding of the velocities on g
-  const float relg = cv.dg / fmaxf(g, 1e-30f);
+  const float relg = __fdividef(cv.dg, fmaxf(g, 1e-30f));
   const float margin = 2e-7f + ratio * (1e-4f + a.e32 * relg);
   bool acc;
   double sg64 = -1.0;
