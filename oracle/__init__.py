@@ -100,6 +100,8 @@ def lib():
             "or_chi_table": (None, [P(Pot), d, i32, i32, d, d, vp]),
             "or_chi_lookup": (d, [vp, i32, i32, d, d, d, d]),
             "or_collide_table": (None, [P(Gas), vp, i32, i32, d, d, i64, vp, vp, vp, vp, u64, vp, vp, vp, vp]),
+            "or_transport_q2": (d, [P(Pot), d, d, i32, vp, vp]),
+            "or_transport_viscosity": (None, [P(Pot), d, i32, vp, d, i32, vp, vp, i32, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -378,3 +380,36 @@ def step(gas: Gas, cell_id, vx, vy, vz, n_cells, sgmax, step_idx, path="vhs",
     ox, oy, oz = moment_match(cs, mom, cx, cy, cz)
     return dict(perm=perm, cell_start=cs, mom=mom, pairs=pairs, vx=ox, vy=oy, vz=oz,
                 sgmax=pairs["sgmax"])
+
+
+# ------------------------------------------------------------------ transport integrals (reading R8)
+X_MAX = 60.0   # x = E/(kT) range of the Omega(2,2) rule; x^3 e^-x beyond it is below 1e-20
+
+
+def composite_gl(panels: int, lo: float, hi: float, n: int = 16):
+    """Composite Gauss-Legendre rule: `panels` equal panels of [lo, hi], n
+    nodes each (numpy's leggauss for the nodes on [-1, 1])."""
+    t, w = np.polynomial.legendre.leggauss(n)
+    h = (hi - lo) / panels
+    xs = np.concatenate([lo + h * (p + 0.5 * (t + 1.0)) for p in range(panels)])
+    ws = np.concatenate([0.5 * h * w for _ in range(panels)])
+    return xs, ws
+
+
+def transport_q2(pot: Pot, E_kelvin, bmax_A: float, b_panels: int = 32) -> np.ndarray:
+    """Q2(E) in m^2 (reading R8), rule in u = (b/b_max)^2 on [0, 1]."""
+    u, wu = composite_gl(b_panels, 0.0, 1.0)
+    E = np.atleast_1d(np.asarray(E_kelvin, dtype=np.float64))
+    return np.array([lib().or_transport_q2(C.byref(pot), float(e), bmax_A, len(u), _p(u), _p(wu)) for e in E])
+
+
+def transport_viscosity(pot: Pot, mass: float, T_kelvin, bmax_A: float, b_panels: int = 32,
+                        x_panels: int = 8):
+    """(Omega22 in m^2, mu in Pa s) at the temperatures T (reading R8)."""
+    u, wu = composite_gl(b_panels, 0.0, 1.0)
+    x, wx = composite_gl(x_panels, 0.0, X_MAX)
+    T = _f64(np.atleast_1d(np.asarray(T_kelvin, dtype=np.float64)))
+    om = np.zeros(len(T)); mu = np.zeros(len(T))
+    lib().or_transport_viscosity(C.byref(pot), mass, len(T), _p(T), bmax_A, len(u), _p(u), _p(wu),
+                                 len(x), _p(x), _p(wx), _p(om), _p(mu))
+    return om, mu

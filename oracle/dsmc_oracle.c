@@ -43,6 +43,15 @@
  *   R7  the chi table of the look-up path (Sec. 3.4.5: b~ = b/b_max,
  *       E~ = ln(E_r/k_B), bilinear interpolation) has uniform nodes including
  *       both ends of each axis; E~ outside the table is clamped to it.
+ *   R8  transport integrals (Eq. chapman_enskog and the two integrals after
+ *       it): Q2(E) = 2 pi int_0^bmax (1 - cos^2 chi) b db with the b-integral
+ *       cut at b_max; the Maxwellian average that makes Eq. (chapman_enskog)
+ *       give the rigid-sphere viscosity is the Chapman-Cowling one,
+ *       Omega22(T) = 1/(4 (kT)^4) int_0^inf E^3 Q2(E) exp(-E/kT) dE
+ *       (the printed E^2/(2 (kT)^3) weighting would make the hard-sphere mu
+ *       1.5 times the textbook value).  Both integrals by composite
+ *       Gauss-Legendre rules whose nodes the caller passes: in u = (b/b_max)^2
+ *       on [0, 1] and in x = E/(kT) on [0, x_max].
  */
 #include <math.h>
 #include <stdint.h>
@@ -758,5 +767,42 @@ void or_harvest_jager(const or_gas_t* gs, const or_pot_t* P, int64_t n,
       vi_out[3 * p + c] = cm + 0.5 * vrp[c];
       vj_out[3 * p + c] = cm - 0.5 * vrp[c];
     }
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Macroscopic validation: transport cross-section, Omega(2,2), mu(T)   */
+/* (Eq. chapman_enskog and the two integrals after it; reading R8)      */
+/* ------------------------------------------------------------------ */
+
+/* Q2(E) in m^2 for E = E_r/k_B in Kelvin, b_max in Angstrom:
+ * Q2 = 2 pi int_0^bmax sin^2 chi b db = pi bmax^2 int_0^1 sin^2 chi(bmax sqrt(u), E) du,
+ * by the rule (u[k], wu[k]), k < nb, on [0, 1]. */
+double or_transport_q2(const or_pot_t* P, double E, double bmax, int32_t nb, const double* u,
+                       const double* wu) {
+  double acc = 0.0;
+  for (int32_t k = 0; k < nb; ++k) {
+    double chi = or_chi(P, bmax * sqrt(u[k]), E);
+    double s = sin(chi);
+    acc += wu[k] * (s * s);
+  }
+  return OR_PI * bmax * bmax * acc * 1e-20;
+}
+
+/* Omega22(T) (m^2) and mu(T) (Pa s) for n_T temperatures; the x-rule
+ * (x[j], wx[j]), j < nx, integrates over x = E/(kT) on [0, x_max]:
+ * Omega22 = 1/4 int x^3 exp(-x) Q2(x T) dx,  mu = 5/16 sqrt(pi m k T) / Omega22. */
+void or_transport_viscosity(const or_pot_t* P, double mass, int32_t n_T, const double* T, double bmax,
+                            int32_t nb, const double* u, const double* wu, int32_t nx, const double* x,
+                            const double* wx, double* omega22, double* mu) {
+  for (int32_t i = 0; i < n_T; ++i) {
+    double om = 0.0;
+    for (int32_t j = 0; j < nx; ++j) {
+      double q = or_transport_q2(P, x[j] * T[i], bmax, nb, u, wu);
+      om += wx[j] * x[j] * x[j] * x[j] * exp(-x[j]) * q;
+    }
+    om *= 0.25;
+    omega22[i] = om;
+    mu[i] = 5.0 / 16.0 * sqrt(OR_PI * mass * OR_KB * T[i]) / om;
   }
 }

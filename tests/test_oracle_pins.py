@@ -638,3 +638,39 @@ def test_collide_table_with_constant_chi_is_the_rotation():
     if i not in later and j not in later:
         assert abs(np.linalg.norm(vrp_out) - g) < 1e-10 * g
         assert abs(np.dot(vr, vrp_out) / g ** 2 - math.cos(float(np.float32(0.7)))) < 1e-12
+
+
+# ------------------------------------------------------------------ transport integrals (reading R8)
+
+def test_transport_hard_sphere_closed_forms():
+    """Rigid spheres (b_max = d, so the u-integrand is a polynomial and the rule
+    exact): Q2 = (2/3) pi d^2, Omega22 = pi d^2 and Eq. (chapman_enskog) gives the
+    textbook first-order viscosity 5/16 sqrt(pi m k T) / (pi d^2)."""
+    hs = O.make_pot(W.HARD_SPHERE_AR)
+    d = 3.6e-10
+    q = O.transport_q2(hs, [10.0, 1e3, 1e5], 3.6, b_panels=4)
+    assert np.allclose(q, 2 / 3 * math.pi * d * d, rtol=1e-12, atol=0)
+    T = np.array([300.0, 3000.0])
+    om, mu = O.transport_viscosity(hs, W.M_AR, T, 3.6, b_panels=4, x_panels=8)
+    assert np.allclose(om, math.pi * d * d, rtol=1e-12, atol=0)
+    want = 5 / 16 * np.sqrt(math.pi * W.M_AR * KB * T) / (math.pi * d * d)
+    assert np.allclose(mu, want, rtol=1e-12, atol=0)
+
+
+def test_transport_inverse_power_scaling():
+    """V = kappa/r^p: chi depends on b (E/kappa)^(1/p) only, so Q2 ~ E^(-2/p),
+    and the Maxwellian average gives Omega22(T) = Q2(E = kT) Gamma(4 - 2/p)/4
+    exactly; mu ~ T^(1/2 + 2/p).  (b_max = 12 A, where sin^2 chi < 1e-12.)"""
+    p = 12.0
+    P = O.make_pot(dict(kind=2, kappa=1.3e9, p=p))
+    q = O.transport_q2(P, [300.0, 3000.0], 12.0, b_panels=8)
+    assert abs(q[1] / q[0] - 10.0 ** (-2 / p)) < 1e-8
+    om, mu = O.transport_viscosity(P, W.M_AR, [1000.0], 12.0, b_panels=8, x_panels=8)
+    q1000 = O.transport_q2(P, [1000.0], 12.0, b_panels=8)[0]
+    # the rule applied to the scaled integrand (implementation: weights, x^3 e^-x, 1/4)
+    x, wx = O.composite_gl(8, 0.0, O.X_MAX)
+    assert abs(om[0] / (q1000 * np.sum(wx * x ** (3 - 2 / p) * np.exp(-x)) / 4) - 1) < 1e-9
+    # and against the closed form (the 8-panel rule's own error on x^(3-2/p) e^-x is 2.9e-8)
+    assert abs(om[0] / (q1000 * math.gamma(4 - 2 / p) / 4) - 1) < 1e-7
+    want = 5 / 16 * math.sqrt(math.pi * W.M_AR * KB * 1000.0) / om[0]
+    assert abs(mu[0] / want - 1) < 1e-14
