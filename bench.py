@@ -283,6 +283,21 @@ def run_gb300(args, rank, world, dist):
         ms = e0.elapsed_time(e1) / 3
         extra["chi_batch"] = dict(pairs=nb, ms=ms, chi_per_s=nb / (ms * 1e-3), n_nodes=args.n_nodes,
                                   shape=chi_tuned)
+        # transport integrals: Omega(2,2)(T) and mu(T) at 64 temperatures (500 K to 20,000 K),
+        # 32 b-panels x 8 x-panels of 16 nodes: 65,536 chi per temperature
+        Tt = torch.from_numpy(np.geomspace(500.0, 2.0e4, 64)).to(dev)
+        gas_m = D.make_gas(dict(wl["gas"], model=1))
+        for _ in range(2):
+            om, mu_t = C.transport_viscosity(gas_m, pot, Tt, n_nodes=args.n_nodes)
+        e0.record(stream)
+        om, mu_t = C.transport_viscosity(gas_m, pot, Tt, n_nodes=args.n_nodes)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        mu_h = mu_t.cpu().numpy()
+        extra["transport"] = dict(temperatures=64, chi_evaluations=64 * 128 * 512, ms=ms,
+                                  chi_per_s=64 * 128 * 512 / (ms * 1e-3), n_nodes=args.n_nodes,
+                                  mu_Pa_s={"500K": float(mu_h[0]), "20000K": float(mu_h[-1])})
         x = torch.randn((nb, 8), dtype=torch.float32, device=dev)
         y = torch.empty((nb, 3), dtype=torch.float32, device=dev)
         for _ in range(2):

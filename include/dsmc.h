@@ -272,6 +272,31 @@ int dsmc_collide_jager(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_potent
                        double* vx, double* vy, double* vz, float* chi_out, void* ws, size_t ws_bytes,
                        void* stream);
 
+/* Macroscopic validation (Eq. chapman_enskog and the two integrals after
+ * it), reading R8.  Transport cross-section
+ *   Q2(E) = 2 pi int_0^{b_max} (1 - cos^2 chi(b, E)) b db
+ *         = pi b_max^2 int_0^1 sin^2 chi(b_max sqrt(u), E) du
+ * by a composite 16-point Gauss-Legendre rule (b_panels equal panels of
+ * [0, 1] in u = (b/b_max)^2), chi at every node as in dsmc_jager_chi.
+ * E_kelvin: n_E energies E_r/k_B > 0 (K), device memory; b_max_A in Angstrom;
+ * q2: n_E values in m^2, device memory.  An energy that is not positive and
+ * finite records DSMC_ERR_ARG on the device.  Deterministic. */
+int dsmc_transport_q2(dsmc_ctx_t* ctx, const dsmc_potential_t* pot, int32_t n_nodes, int32_t n_E,
+                      const double* E_kelvin, double b_max_A, int32_t b_panels, double* q2, void* stream);
+/* Collision integral and first-order Chapman-Enskog viscosity at n_T
+ * temperatures (device memory, K):
+ *   Omega22(T) = 1/(4 (kT)^4) int_0^inf E^3 Q2(E) exp(-E/kT) dE
+ *              = 1/4 int_0^60 x^3 e^-x Q2(x kT) dx   (x_panels 16-point panels),
+ *   mu(T) = 5/16 sqrt(pi m k T) / Omega22(T),  m = gas->mass.
+ * omega22 (m^2) and mu (Pa s): n_T values each, device memory.  ws: caller
+ * workspace of dsmc_transport_workspace_size(n_T, x_panels) bytes (Q2 at the
+ * n_T x 16 x_panels energies of the rule). */
+size_t dsmc_transport_workspace_size(int32_t n_T, int32_t x_panels);
+int dsmc_transport_viscosity(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_potential_t* pot, int32_t n_nodes,
+                             int32_t n_T, const double* T_kelvin, double b_max_A, int32_t b_panels,
+                             int32_t x_panels, double* omega22, double* mu, void* ws, size_t ws_bytes,
+                             void* stream);
+
 /* Sec. 3.4.5: fill a chi table with the exact deflection angle (the
  * computation of dsmc_jager_chi at every node; b_max from gas->b_max).
  * table: nE x nb FP32, device memory. */

@@ -269,6 +269,34 @@ int dsmc_jager_chi(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_potential_t*
   return dsmc::launch_jager_chi(c, *gas, *pot, n_nodes, n, b, g, chi, S(stream));
 }
 
+int dsmc_transport_q2(dsmc_ctx_t* c, const dsmc_potential_t* pot, int32_t n_nodes, int32_t n_E,
+                      const double* E_kelvin, double b_max_A, int32_t b_panels, double* q2, void* stream) {
+  CHECK_CTX(c);
+  if (int rc = check_pot(c, pot, n_nodes)) return rc;
+  REQUIRE(c, n_E >= 0 && (n_E == 0 || (E_kelvin && q2)), "transport_q2: bad arrays");
+  REQUIRE(c, b_max_A > 0 && b_panels >= 1 && b_panels <= 4096, "transport_q2: b_max > 0, b_panels in [1, 4096]");
+  return dsmc::launch_transport_q2(c, *pot, n_nodes, n_E, E_kelvin, b_max_A, b_panels, q2, S(stream));
+}
+
+size_t dsmc_transport_workspace_size(int32_t n_T, int32_t x_panels) {
+  if (n_T < 0 || x_panels < 1) return 0;
+  return dsmc::transport_ws(n_T, x_panels);
+}
+
+int dsmc_transport_viscosity(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_potential_t* pot, int32_t n_nodes,
+                             int32_t n_T, const double* T_kelvin, double b_max_A, int32_t b_panels,
+                             int32_t x_panels, double* omega22, double* mu, void* ws, size_t ws_bytes,
+                             void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, gas && gas->mass > 0, "transport_viscosity: gas with mass > 0 required");
+  if (int rc = check_pot(c, pot, n_nodes)) return rc;
+  REQUIRE(c, n_T >= 0 && (n_T == 0 || (T_kelvin && omega22 && mu && ws)), "transport_viscosity: bad arrays");
+  REQUIRE(c, b_max_A > 0 && b_panels >= 1 && b_panels <= 4096 && x_panels >= 1 && x_panels <= 1024,
+          "transport_viscosity: b_max > 0, b_panels in [1, 4096], x_panels in [1, 1024]");
+  return dsmc::launch_transport_viscosity(c, *gas, *pot, n_nodes, n_T, T_kelvin, b_max_A, b_panels, x_panels,
+                                          omega22, mu, ws, ws_bytes, S(stream));
+}
+
 int dsmc_collide_jager(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_potential_t* pot,
                        int32_t n_nodes, uint64_t step, int32_t n, const int32_t* pairs, const uint32_t* deps,
                        const int32_t* round_offsets, const dsmc_select_info_t* info,

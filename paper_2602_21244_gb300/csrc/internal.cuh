@@ -266,6 +266,12 @@ int launch_collide_table(Ctx* c, const dsmc_gas_t& gas, const dsmc_chi_table_t& 
                          const dsmc_select_info_t* info, double* vx, double* vy, double* vz, float* chi_out,
                          void* ws, size_t ws_bytes, cudaStream_t s);
 int occupancy_collide_table(int threads);
+size_t transport_ws(int32_t n_T, int32_t x_panels);
+int launch_transport_q2(Ctx* c, const dsmc_potential_t& pot, int n_nodes, int32_t n_E, const double* E,
+                        double bmax, int32_t b_panels, double* q2, cudaStream_t s);
+int launch_transport_viscosity(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& pot, int n_nodes,
+                               int32_t n_T, const double* T, double bmax, int32_t b_panels, int32_t x_panels,
+                               double* omega22, double* mu, void* ws, size_t ws_bytes, cudaStream_t s);
 int launch_harvest_jager(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& pot,
                          int n_nodes, int64_t n, const double* vi, const double* vj,
                          const double* b, const double* eps, double* vio, double* vjo,

@@ -794,4 +794,119 @@ int launch_harvest_jager(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& 
   return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
 }
 
+// ---------------------------------------------------------------- transport integrals
+// Macroscopic validation (Eq. chapman_enskog and the two integrals after it;
+// reading R8): Q2(E) = pi b_max^2 int_0^1 sin^2 chi(b_max sqrt(u), E) du by a
+// composite 16-point Gauss-Legendre rule (b_panels equal panels of [0, 1]);
+// Omega22(T) = 1/4 int_0^60 x^3 e^-x Q2(x T) dx by the same kind of rule
+// (x_panels panels); mu = 5/16 sqrt(pi m k T) / Omega22.  One block per
+// energy, chi at every node by the routine of the collide kernels, the
+// block's sum in a fixed order (deterministic).
+constexpr int kTrNodes = 16;
+constexpr int kTrThreads = 256;
+constexpr double kTrXmax = 60.0;
+
+struct TransportArgs {
+  int32_t n_e;
+  const double* E;   // energies E_r/k_B (list mode), or null
+  const double* T;   // temperatures (grid mode: energy e is x_j T_i, j = e % nx, i = e / nx)
+  int32_t nx, x_panels, nb, b_panels;
+  double bmax;
+  double gl_x[kTrNodes], gl_w[kTrNodes];   // 16-point rule on [0, 1]
+  double* q2;        // [n_e], m^2
+  int* status;
+};
+
+__device__ __forceinline__ double tr_x(const TransportArgs& a, int32_t j) {
+  return (j / kTrNodes + a.gl_x[j % kTrNodes]) * (kTrXmax / a.x_panels);
+}
+
+__global__ void __launch_bounds__(kTrThreads) k_transport_q2(PotDev P, TransportArgs a) {
+  __shared__ double red[kTrThreads / 32];
+  for (int32_t e = blockIdx.x; e < a.n_e; e += gridDim.x) {
+    const double E = a.T ? tr_x(a, e % a.nx) * a.T[e / a.nx] : a.E[e];
+    double acc = 0.0;
+    if (E > 0.0 && E < 1e30) {   // chi takes E in FP32
+      for (int32_t k = threadIdx.x; k < a.nb; k += kTrThreads) {
+        const int q = k % kTrNodes;
+        const double u = (k / kTrNodes + a.gl_x[q]) / a.b_panels;
+        const float chi = chi_device(P, (float)(a.bmax * sqrt(u)), (float)E);
+        const float sn = sinf(chi);
+        acc += a.gl_w[q] * (double)(sn * sn);
+      }
+    } else if (threadIdx.x == 0) {
+      set_status(a.status, DSMC_ERR_ARG);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+      for (int w = 0; w < kTrThreads / 32; ++w) sum += red[w];
+      a.q2[e] = DSMC_PI * a.bmax * a.bmax * (sum / a.b_panels) * 1e-20;
+    }
+    __syncthreads();
+  }
+}
+
+// thread per temperature: Omega22 and mu from Q2 at the x nodes
+__global__ void k_transport_finish(TransportArgs a, int32_t n_T, double mass, double* omega22, double* mu) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_T; i += gridDim.x * blockDim.x) {
+    double om = 0.0;
+    for (int32_t j = 0; j < a.nx; ++j) {
+      const double x = tr_x(a, j);
+      om += a.gl_w[j % kTrNodes] * (kTrXmax / a.x_panels) * x * x * x * exp(-x) * a.q2[(size_t)i * a.nx + j];
+    }
+    om *= 0.25;
+    omega22[i] = om;
+    mu[i] = 5.0 / 16.0 * sqrt(DSMC_PI * mass * DSMC_KB * a.T[i]) / om;
+  }
+}
+
+static TransportArgs transport_args(Ctx* c, int32_t b_panels, double bmax) {
+  TransportArgs a = {};
+  std::vector<double> x(kTrNodes), w(kTrNodes);
+  gauss_legendre01(kTrNodes, x.data(), w.data());
+  for (int q = 0; q < kTrNodes; ++q) { a.gl_x[q] = x[q]; a.gl_w[q] = w[q]; }
+  a.b_panels = b_panels;
+  a.nb = b_panels * kTrNodes;
+  a.bmax = bmax;
+  a.status = status_ptr(c);
+  return a;
+}
+
+size_t transport_ws(int32_t n_T, int32_t x_panels) {
+  return align256(sizeof(double) * (size_t)(n_T > 0 ? n_T : 1) * kTrNodes * (size_t)x_panels);
+}
+
+int launch_transport_q2(Ctx* c, const dsmc_potential_t& pot, int n_nodes, int32_t n_E, const double* E,
+                        double bmax, int32_t b_panels, double* q2, cudaStream_t s) {
+  if (n_E == 0) return 0;
+  dsmc_gas_t g = {};
+  g.mass = 1.0;   // the mass enters only the energy of a velocity, unused here
+  const PotDev P = make_pot(g, pot, n_nodes);
+  TransportArgs a = transport_args(c, b_panels, bmax);
+  a.n_e = n_E; a.E = E; a.q2 = q2;
+  k_transport_q2<<<blocks_n(n_E, 1, sm_count(c) * 8), kTrThreads, 0, s>>>(P, a);
+  count_launches(c, 1);
+  return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
+}
+
+int launch_transport_viscosity(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& pot, int n_nodes,
+                               int32_t n_T, const double* T, double bmax, int32_t b_panels, int32_t x_panels,
+                               double* omega22, double* mu, void* ws, size_t ws_bytes, cudaStream_t s) {
+  if (n_T == 0) return 0;
+  if (ws_bytes < transport_ws(n_T, x_panels)) return record(c, DSMC_ERR_ARG, "transport: workspace too small");
+  const PotDev P = make_pot(gas, pot, n_nodes);
+  TransportArgs a = transport_args(c, b_panels, bmax);
+  a.T = T; a.x_panels = x_panels; a.nx = x_panels * kTrNodes;
+  a.n_e = n_T * a.nx;
+  a.q2 = (double*)ws;
+  k_transport_q2<<<blocks_n(a.n_e, 1, sm_count(c) * 8), kTrThreads, 0, s>>>(P, a);
+  k_transport_finish<<<blocks_n(n_T, 128, sm_count(c)), 128, 0, s>>>(a, n_T, gas.mass, omega22, mu);
+  count_launches(c, 2);
+  return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
+}
+
 }  // namespace dsmc

@@ -136,6 +136,10 @@ def load(build: bool = True):
             "dsmc_collide_jager": (C.c_int, [vp, P(Gas), P(Potential), i32, u64, i32, vp, vp, vp, vp, vp,
                                              vp, vp, vp, vp, sz, vp]),
             "dsmc_chi_table_build": (C.c_int, [vp, P(Gas), P(Potential), i32, i32, i32, d, d, vp, vp]),
+            "dsmc_transport_q2": (C.c_int, [vp, P(Potential), i32, i32, vp, d, i32, vp, vp]),
+            "dsmc_transport_workspace_size": (C.c_size_t, [i32, i32]),
+            "dsmc_transport_viscosity": (C.c_int, [vp, P(Gas), P(Potential), i32, i32, vp, d, i32, i32, vp, vp,
+                                                   vp, C.c_size_t, vp]),
             "dsmc_collide_table": (C.c_int, [vp, P(Gas), P(ChiTableDesc), u64, i32, vp, vp, vp, vp, vp, vp, vp, vp,
                                              vp, sz, vp]),
             "dsmc_collide_neural": (C.c_int, [vp, P(Gas), P(Mlp), vp, vp, u64, vp, i32, vp, vp, vp, vp, vp,
@@ -363,6 +367,30 @@ class Context:
         self._check(self._lib.dsmc_chi_table_build(self.h, C.byref(gas), C.byref(pot), n_nodes, nb, nE, lnE_min,
                                                    lnE_max, _ptr(chi), _stream(stream)), "chi_table_build")
         return ChiTable(chi, lnE_min, lnE_max)
+
+    def transport_q2(self, pot: Potential, E_kelvin, b_max_A=12.0, b_panels=32, n_nodes=32, out=None,
+                     stream=None):
+        """dsmc_transport_q2: Q2(E) in m^2 at the energies E_kelvin (float64, device)."""
+        if out is None:
+            out = torch.empty_like(E_kelvin)
+        self._check(self._lib.dsmc_transport_q2(self.h, C.byref(pot), n_nodes, E_kelvin.numel(),
+                                                _ptr(E_kelvin, torch.float64), b_max_A, b_panels,
+                                                _ptr(out, torch.float64), _stream(stream)), "transport_q2")
+        return out
+
+    def transport_viscosity(self, gas: Gas, pot: Potential, T_kelvin, b_max_A=12.0, b_panels=32, x_panels=8,
+                            n_nodes=32, stream=None):
+        """dsmc_transport_viscosity: (Omega22 in m^2, mu in Pa s) at the temperatures T_kelvin."""
+        n = T_kelvin.numel()
+        om = torch.empty_like(T_kelvin)
+        mu = torch.empty_like(T_kelvin)
+        nb = self._lib.dsmc_transport_workspace_size(n, x_panels)
+        ws = torch.empty(max(nb, 1), dtype=torch.uint8, device=T_kelvin.device)
+        self._check(self._lib.dsmc_transport_viscosity(self.h, C.byref(gas), C.byref(pot), n_nodes, n,
+                                                       _ptr(T_kelvin, torch.float64), b_max_A, b_panels, x_panels,
+                                                       _ptr(om, torch.float64), _ptr(mu, torch.float64), _ptr(ws),
+                                                       nb, _stream(stream)), "transport_viscosity")
+        return om, mu
 
     def collide_table(self, gas: Gas, table: "ChiTable", step, sel, vx, vy, vz, chi_out=None, ws=None,
                       stream=None):
