@@ -12,6 +12,7 @@ silent or ambiguous passages are listed in the C file header.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -102,6 +103,7 @@ def lib():
             "or_collide_table": (None, [P(Gas), vp, i32, i32, d, d, i64, vp, vp, vp, vp, u64, vp, vp, vp, vp]),
             "or_transport_q2": (d, [P(Pot), d, d, i32, vp, vp]),
             "or_transport_viscosity": (None, [P(Pot), d, i32, vp, d, i32, vp, vp, i32, vp, vp, vp, vp]),
+            "or_chi_mlp_forward": (None, [vp, vp, i64, vp, C.c_int, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -413,3 +415,25 @@ def transport_viscosity(pot: Pot, mass: float, T_kelvin, bmax_A: float, b_panels
     lib().or_transport_viscosity(C.byref(pot), mass, len(T), _p(T), bmax_A, len(u), _p(u), _p(wu),
                                  len(x), _p(x), _p(wx), _p(om), _p(mu))
     return om, mu
+
+
+# ------------------------------------------------------------------ chi-MLP surrogate (reading R9)
+CHI_LNE_MIN, CHI_LNE_MAX = math.log(5.0), math.log(6.0e4)
+
+
+def chi_mlp_forward(W, bias, x, bf16=False) -> np.ndarray:
+    """Softplus output y (~ ln(1 + chi)) of the chi-MLP for inputs x [n x 2] =
+    [ln(E_r)*, b/b_max]."""
+    x = _f64(np.asarray(x, dtype=np.float64).reshape(-1, 2))
+    y = np.zeros(len(x))
+    lib().or_chi_mlp_forward(_p(_f64(W)), _p(_f64(bias)), len(x), _p(x), int(bf16), _p(y))
+    return y
+
+
+def chi_mlp_table(W, bias, nb: int, nE: int, bf16=False) -> np.ndarray:
+    """The look-up table of Sec. 3.4.5 synthesised by the chi-MLP: node (j, i)
+    at ln(E_r)* = j/(nE-1), b/b_max = i/(nb-1), chi = e^y - 1; [nE x nb]."""
+    xe = np.repeat(np.arange(nE) / (nE - 1), nb)
+    xb = np.tile(np.arange(nb) / (nb - 1), nE)
+    y = chi_mlp_forward(W, bias, np.stack([xe, xb], 1), bf16)
+    return np.expm1(y).reshape(nE, nb)

@@ -52,6 +52,10 @@
  *       1.5 times the textbook value).  Both integrals by composite
  *       Gauss-Legendre rules whose nodes the caller passes: in u = (b/b_max)^2
  *       on [0, 1] and in x = E/(kT) on [0, x_max].
+ *   R9  chi-MLP surrogate (Fig. nn_architecture): inputs x0 = ln(E_r)* =
+ *       (ln(E_r/k_B) - ln 5)/(ln 60000 - ln 5) (min-max over the training
+ *       range, as the table of R7) and x1 = b/b_max; the Softplus output is
+ *       y ~ ln(1 + chi) (the training target), so chi = e^y - 1.
  */
 #include <math.h>
 #include <stdint.h>
@@ -805,4 +809,49 @@ void or_transport_viscosity(const or_pot_t* P, double mass, int32_t n_T, const d
     omega22[i] = om;
     mu[i] = 5.0 / 16.0 * sqrt(OR_PI * mass * OR_KB * T[i]) / om;
   }
+}
+
+/* ------------------------------------------------------------------ */
+/* chi-MLP surrogate (Fig. nn_architecture; reading R9)                 */
+/* ------------------------------------------------------------------ */
+static const int32_t or_chi_dims[7] = {2, 512, 512, 512, 256, 128, 1};
+
+static double or_softplus(double z) { return fmax(z, 0.0) + log1p(exp(-fabs(z))); }
+
+/* y = Softplus(W6 h5 + b6), h_l = SiLU(W_l h_{l-1} + b_l), h0 = x; W row-major
+ * [out x in] per layer, concatenated; bias concatenated.  emul != 0 emulates
+ * the storage of a bf16 tensor-core kernel: the input as two bf16 terms
+ * (hi + lo), the activations of hidden layers 1-4 rounded to bf16 once, the
+ * fifth hidden layer's activations exact (an FP32 dot product follows). */
+void or_chi_mlp_forward(const double* W, const double* bias, int64_t n, const double* x, int emul, double* y) {
+  double* a = (double*)malloc(sizeof(double) * 512);
+  double* b = (double*)malloc(sizeof(double) * 512);
+  for (int64_t s = 0; s < n; ++s) {
+    for (int q = 0; q < 2; ++q) {
+      double v = x[2 * s + q];
+      if (emul) { double hi = or_bf16_round(v); v = hi + or_bf16_round(v - hi); }
+      a[q] = v;
+    }
+    const double* w = W;
+    const double* bb = bias;
+    for (int l = 0; l < 6; ++l) {
+      const int din = or_chi_dims[l], dout = or_chi_dims[l + 1];
+      for (int o = 0; o < dout; ++o) {
+        double z = bb[o];
+        for (int i = 0; i < din; ++i) z += w[(int64_t)o * din + i] * a[i];
+        if (l < 5) {
+          double h = z / (1.0 + exp(-z));
+          if (emul && l < 4) h = or_bf16_round(h);
+          b[o] = h;
+        } else {
+          y[s] = or_softplus(z);
+        }
+      }
+      w += (int64_t)din * dout;
+      bb += dout;
+      double* t = a; a = b; b = t;
+    }
+  }
+  free(a);
+  free(b);
 }

@@ -186,6 +186,28 @@ def mlp_weights(d_in=8, width=128, n_hidden=3, d_out=3, seed=1):
                 bias=np.concatenate(bs).astype(np.float32).astype(np.float64))
 
 
+# chi-MLP surrogate (Fig. nn_architecture): inputs [ln(E_r)*, b/b_max], five
+# SiLU hidden layers, one Softplus output
+CHI_MLP_DIMS = [2, 512, 512, 512, 256, 128, 1]
+
+
+def chi_mlp_weights(seed=3):
+    """Xavier-uniform weights rounded to bf16 and small uniform biases (the
+    trained weights are not available), layers row-major [out x in],
+    concatenated."""
+    rng = np.random.default_rng(seed)
+    dims = CHI_MLP_DIMS
+    ws, bs = [], []
+    for l in range(len(dims) - 1):
+        a = math.sqrt(6.0 / (dims[l] + dims[l + 1]))
+        ws.append(rng.uniform(-a, a, size=(dims[l + 1], dims[l])).ravel())
+        bs.append(rng.uniform(-0.1, 0.1, size=dims[l + 1]))
+    W = np.concatenate(ws)
+    bits = bf16_bits(W)
+    return dict(dims=dims, W_bits=bits, W=bf16_value(bits),
+                bias=np.concatenate(bs).astype(np.float32).astype(np.float64))
+
+
 def sigma_v(T_ref=273.0, mass=M_AR):
     """Scale of one relative-velocity component at T_ref: sqrt(2 k T_ref / m)."""
     return math.sqrt(2.0 * KB * T_ref / mass)

@@ -674,3 +674,48 @@ def test_transport_inverse_power_scaling():
     assert abs(om[0] / (q1000 * math.gamma(4 - 2 / p) / 4) - 1) < 1e-7
     want = 5 / 16 * math.sqrt(math.pi * W.M_AR * KB * 1000.0) / om[0]
     assert abs(mu[0] / want - 1) < 1e-14
+
+
+# ------------------------------------------------------------------ chi-MLP surrogate (reading R9)
+
+def _chi_torch(torch, wts):
+    from oracle.train import split_layers, split_bias
+    Ws, bs = split_layers(wts["dims"], wts["W"]), split_bias(wts["dims"], wts["bias"])
+    layers = []
+    for l in range(6):
+        lin = torch.nn.Linear(wts["dims"][l], wts["dims"][l + 1]).double()
+        lin.weight.data = torch.tensor(Ws[l]); lin.bias.data = torch.tensor(bs[l])
+        layers += [lin, torch.nn.SiLU() if l < 5 else torch.nn.Softplus()]
+    return layers
+
+
+def test_chi_mlp_forward_matches_torch_sequential():
+    """Fig. nn_architecture: 2 -> 512, 512, 512, 256, 128 (SiLU) -> 1 (Softplus);
+    FP64 against torch nn.Sequential, and the bf16-storage emulation against the
+    same network with torch's bf16 rounding applied where the kernel stores."""
+    torch = pytest.importorskip("torch")
+    wts = W.chi_mlp_weights()
+    layers = _chi_torch(torch, wts)
+    x = np.random.default_rng(4).uniform(0, 1, (40, 2))
+    y = O.chi_mlp_forward(wts["W"], wts["bias"], x)
+    ref = torch.nn.Sequential(*layers)(torch.tensor(x)).detach().numpy()[:, 0]
+    np.testing.assert_allclose(y, ref, rtol=1e-12, atol=1e-14)
+    assert np.all(y >= 0)
+    xt = torch.tensor(x)
+    hi = xt.to(torch.bfloat16).double()
+    h = hi + (xt - hi).to(torch.bfloat16).double()
+    for l in range(6):
+        h = layers[2 * l + 1](layers[2 * l](h))
+        if l < 4:
+            h = h.to(torch.bfloat16).double()
+    yb = O.chi_mlp_forward(wts["W"], wts["bias"], x, bf16=True)
+    np.testing.assert_allclose(yb, h.detach().numpy()[:, 0], rtol=1e-12, atol=1e-14)
+
+
+def test_chi_mlp_table_is_forward_at_the_nodes():
+    wts = W.chi_mlp_weights()
+    T = O.chi_mlp_table(wts["W"], wts["bias"], 5, 3)
+    y = O.chi_mlp_forward(wts["W"], wts["bias"], [[1.0, 0.25], [0.0, 1.0]])
+    assert T.shape == (3, 5)
+    np.testing.assert_allclose([T[2, 1], T[0, 4]], np.expm1(y), rtol=1e-15)
+    assert np.all(T >= 0)
