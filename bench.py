@@ -35,6 +35,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 MLP_FLOP_PER_PAIR = 2 * (8 * 128 + 128 * 128 * 2 + 128 * 3)   # 68,352 (unpadded)
+# chi-MLP 2 -> 512, 512, 512, 256, 128 -> 1: 1,378,560 FLOP per query (unpadded)
+CHI_MLP_FLOP_PER_QUERY = 2 * (2 * 512 + 512 * 512 * 2 + 512 * 256 + 256 * 128 + 128)
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per pair of
 # k_collide_neural, from one ncu capture of a full-size launch on the
 # hypersonic gas: 984.7 + 948.6 MB for about 6.882 million pairs
@@ -298,6 +300,24 @@ def run_gb300(args, rank, world, dist):
         extra["transport"] = dict(temperatures=64, chi_evaluations=64 * 128 * 512, ms=ms,
                                   chi_per_s=64 * 128 * 512 / (ms * 1e-3), n_nodes=args.n_nodes,
                                   mu_Pa_s={"500K": float(mu_h[0]), "20000K": float(mu_h[-1])})
+        # chi-MLP surrogate: the 512 x 512 look-up table synthesised on the tensor cores
+        cw = W.chi_mlp_weights()
+        cpk = C.chi_mlp_pack(torch.from_numpy(cw["W_bits"].view(np.int16)).to(dev))
+        cb = torch.from_numpy(cw["bias"].astype(np.float32)).to(dev)
+        ct = C.chi_mlp_table(cpk, cb, 512, 512)
+        for _ in range(2):
+            C.chi_mlp_table(cpk, cb, 512, 512, out=ct)
+        e0.record(stream)
+        for _ in range(5):
+            C.chi_mlp_table(cpk, cb, 512, 512, out=ct)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        pk = peaks()
+        peak = pk.get("bf16_tflops") if pk else 1900.0
+        tf = 512 * 512 * CHI_MLP_FLOP_PER_QUERY / (ms * 1e-3) / 1e12
+        extra["chi_mlp_table"] = dict(nodes=[512, 512], ms=ms, queries_per_s=512 * 512 / (ms * 1e-3), tflops=tf,
+                                      frac_of_bf16_peak=tf / peak)
         x = torch.randn((nb, 8), dtype=torch.float32, device=dev)
         y = torch.empty((nb, 3), dtype=torch.float32, device=dev)
         for _ in range(2):

@@ -297,6 +297,28 @@ int dsmc_transport_viscosity(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_
                              int32_t x_panels, double* omega22, double* mu, void* ws, size_t ws_bytes,
                              void* stream);
 
+/* chi-MLP surrogate (Sec. 3.4, Fig. nn_architecture; reading R9): inputs
+ * x = [ln(E_r)*, b/b_max] with ln(E_r)* = (ln(E_r/k_B) - ln 5)/(ln 60000 - ln 5),
+ * hidden layers 512, 512, 512, 256, 128 with SiLU, one Softplus output
+ * y ~ ln(1 + chi), chi = e^y - 1.  Weights: bf16 bits, layers row-major
+ * [out x in] concatenated (512x2, 512x512, 512x512, 256x512, 128x256, 1x128);
+ * bias: FP32, concatenated (1921 values).  On the tensor cores with the input
+ * as two bf16 terms and hidden activations 1-4 as single bf16 terms, FP32
+ * accumulation; the output layer an FP32 dot product.
+ *
+ * dsmc_chi_mlp_pack writes the weights once into `packed` (device memory of
+ * dsmc_chi_mlp_packed_size() bytes, 16-byte aligned) in the operand layout
+ * the kernel streams.  dsmc_chi_mlp_forward: n rows x [2] (FP32, device) ->
+ * y (Softplus output) and/or chi (e^y - 1), either may be NULL.
+ * dsmc_chi_mlp_table: the nE x nb table of Sec. 3.4.5 (row j: ln(E_r)* =
+ * j/(nE-1); column i: b/b_max = i/(nb-1)), chi = e^y - 1, FP32 device memory. */
+size_t dsmc_chi_mlp_packed_size(void);
+int dsmc_chi_mlp_pack(dsmc_ctx_t* ctx, const uint16_t* w_bits, void* packed, void* stream);
+int dsmc_chi_mlp_forward(dsmc_ctx_t* ctx, const void* packed, const float* bias, int64_t n, const float* x,
+                         float* y, float* chi, void* stream);
+int dsmc_chi_mlp_table(dsmc_ctx_t* ctx, const void* packed, const float* bias, int32_t nb, int32_t nE,
+                       float* table, void* stream);
+
 /* Sec. 3.4.5: fill a chi table with the exact deflection angle (the
  * computation of dsmc_jager_chi at every node; b_max from gas->b_max).
  * table: nE x nb FP32, device memory. */

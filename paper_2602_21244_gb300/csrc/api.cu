@@ -297,6 +297,32 @@ int dsmc_transport_viscosity(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_po
                                           omega22, mu, ws, ws_bytes, S(stream));
 }
 
+size_t dsmc_chi_mlp_packed_size(void) { return dsmc::chi_mlp_packed_size(); }
+
+int dsmc_chi_mlp_pack(dsmc_ctx_t* c, const uint16_t* w_bits, void* packed, void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, w_bits && packed, "chi_mlp_pack: null pointer");
+  REQUIRE(c, ((uintptr_t)packed & 15u) == 0, "chi_mlp_pack: packed buffer must be 16-byte aligned");
+  return dsmc::launch_chi_mlp_pack(c, w_bits, packed, S(stream));
+}
+
+int dsmc_chi_mlp_forward(dsmc_ctx_t* c, const void* packed, const float* bias, int64_t n, const float* x, float* y,
+                         float* chi, void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, packed && bias && n >= 0 && (n == 0 || (x && (y || chi))), "chi_mlp_forward: bad arguments");
+  REQUIRE(c, ((uintptr_t)packed & 15u) == 0, "chi_mlp_forward: packed buffer must be 16-byte aligned");
+  return dsmc::launch_chi_mlp_forward(c, packed, bias, n, x, y, chi, S(stream));
+}
+
+int dsmc_chi_mlp_table(dsmc_ctx_t* c, const void* packed, const float* bias, int32_t nb, int32_t nE, float* table,
+                       void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, packed && bias && table && nb >= 2 && nE >= 2 && (int64_t)nb * nE <= (1ll << 31),
+          "chi_mlp_table: bad arguments");
+  REQUIRE(c, ((uintptr_t)packed & 15u) == 0, "chi_mlp_table: packed buffer must be 16-byte aligned");
+  return dsmc::launch_chi_mlp_table(c, packed, bias, nb, nE, table, S(stream));
+}
+
 int dsmc_collide_jager(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_potential_t* pot,
                        int32_t n_nodes, uint64_t step, int32_t n, const int32_t* pairs, const uint32_t* deps,
                        const int32_t* round_offsets, const dsmc_select_info_t* info,

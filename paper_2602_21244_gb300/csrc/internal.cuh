@@ -267,6 +267,12 @@ int launch_collide_table(Ctx* c, const dsmc_gas_t& gas, const dsmc_chi_table_t& 
                          void* ws, size_t ws_bytes, cudaStream_t s);
 int occupancy_collide_table(int threads);
 size_t transport_ws(int32_t n_T, int32_t x_panels);
+size_t chi_mlp_packed_size();
+int launch_chi_mlp_pack(Ctx* c, const uint16_t* w_bits, void* packed, cudaStream_t s);
+int launch_chi_mlp_forward(Ctx* c, const void* packed, const float* bias, int64_t n, const float* x, float* y,
+                           float* chi, cudaStream_t s);
+int launch_chi_mlp_table(Ctx* c, const void* packed, const float* bias, int32_t nb, int32_t nE, float* table,
+                         cudaStream_t s);
 int launch_transport_q2(Ctx* c, const dsmc_potential_t& pot, int n_nodes, int32_t n_E, const double* E,
                         double bmax, int32_t b_panels, double* q2, cudaStream_t s);
 int launch_transport_viscosity(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& pot, int n_nodes,

@@ -199,6 +199,101 @@ __device__ __forceinline__ void st_shared_v4(uint32_t saddr, uint32_t a, uint32_
                : "memory");
 }
 
+// thread-block cluster: this CTA's rank, the cluster's index and the number
+// of clusters along x; a barrier over all threads of the cluster
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_id_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t nclusters_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// The bulk copy multicast to the same shared-memory offset, and its
+// transaction count to the same mbarrier offset, in every CTA of `mask`.
+__device__ __forceinline__ void bulk_g2s_mc(uint32_t dst, const void* src, uint32_t bytes, uint64_t* mbar,
+                                            uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], "
+      "%4;" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(smem_u32(mbar)), "h"(mask)
+      : "memory");
+}
+
+// commit: arrive on the mbarrier at this offset in every CTA of `mask` once
+// the MMAs issued so far have completed
+__device__ __forceinline__ void commit_mc(uint64_t* mbar, uint16_t mask) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::
+                   "r"(smem_u32(mbar)),
+               "h"(mask)
+               : "memory");
+}
+
+// mbarrier: arrive once and declare `bytes` of asynchronous transactions that
+// must also land before the phase completes
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+               : "memory");
+}
+
+// Untiled bulk copy global -> shared (asynchronous proxy), counted on mbar in
+// bytes.  Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+               : "memory");
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// SiLU of four values with one reciprocal: d_k = 1 + e^{-z_k} (z_k clamped
+// below at -20, where SiLU is below 5e-8 in magnitude, so that the product
+// of the four d_k stays finite), r = 1/(d0 d1 d2 d3), 1/d0 = d1 (d2 d3 r) and
+// so on.  The special-function unit, which bounds the activation epilogue,
+// does 1.25 operations per value instead of 2; the extra multiplications
+// cost a few FP32 roundings.
+__device__ __forceinline__ void silu4(float* z) {
+  float d[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) d[k] = 1.f + __expf(-fmaxf(z[k], -20.f));
+  const float d01 = d[0] * d[1], d23 = d[2] * d[3];
+  const float r = rcp_approx(d01 * d23);
+  const float r01 = r * d23, r23 = r * d01;   // 1/(d0 d1), 1/(d2 d3)
+  z[0] *= d[1] * r01;
+  z[1] *= d[0] * r01;
+  z[2] *= d[3] * r23;
+  z[3] *= d[2] * r23;
+}
+
+// silu4 on two packed pairs (z0, z1), (z2, z3): the same operations in the
+// same order, the additions and the final products as FP32x2 instructions
+// (Blackwell's paired FP32 pipe), so the results equal silu4's bit for bit.
+__device__ __forceinline__ void silu4x2(float2& za, float2& zb) {
+  const float2 one = make_float2(1.f, 1.f);
+  const float2 da = __fadd2_rn(make_float2(__expf(-fmaxf(za.x, -20.f)), __expf(-fmaxf(za.y, -20.f))), one);
+  const float2 db = __fadd2_rn(make_float2(__expf(-fmaxf(zb.x, -20.f)), __expf(-fmaxf(zb.y, -20.f))), one);
+  const float d01 = da.x * da.y, d23 = db.x * db.y;
+  const float r = rcp_approx(d01 * d23);
+  const float r01 = r * d23, r23 = r * d01;
+  za = __fmul2_rn(za, make_float2(da.y * r01, da.x * r01));
+  zb = __fmul2_rn(zb, make_float2(db.y * r23, db.x * r23));
+}
+
 __device__ __forceinline__ float tanh_approx(float x) {
   float y;
   asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));

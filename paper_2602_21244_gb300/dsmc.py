@@ -137,6 +137,10 @@ def load(build: bool = True):
                                              vp, vp, vp, vp, sz, vp]),
             "dsmc_chi_table_build": (C.c_int, [vp, P(Gas), P(Potential), i32, i32, i32, d, d, vp, vp]),
             "dsmc_transport_q2": (C.c_int, [vp, P(Potential), i32, i32, vp, d, i32, vp, vp]),
+            "dsmc_chi_mlp_packed_size": (C.c_size_t, []),
+            "dsmc_chi_mlp_pack": (C.c_int, [vp, vp, vp, vp]),
+            "dsmc_chi_mlp_forward": (C.c_int, [vp, vp, vp, i64, vp, vp, vp, vp]),
+            "dsmc_chi_mlp_table": (C.c_int, [vp, vp, vp, i32, i32, vp, vp]),
             "dsmc_transport_workspace_size": (C.c_size_t, [i32, i32]),
             "dsmc_transport_viscosity": (C.c_int, [vp, P(Gas), P(Potential), i32, i32, vp, d, i32, i32, vp, vp,
                                                    vp, C.c_size_t, vp]),
@@ -391,6 +395,35 @@ class Context:
                                                        _ptr(om, torch.float64), _ptr(mu, torch.float64), _ptr(ws),
                                                        nb, _stream(stream)), "transport_viscosity")
         return om, mu
+
+    def chi_mlp_pack(self, w_bits, stream=None):
+        """dsmc_chi_mlp_pack: the chi-MLP weights (bf16 bits, int16 tensor) in the
+        kernel's streamed operand layout."""
+        nb = self._lib.dsmc_chi_mlp_packed_size()
+        packed = torch.empty(nb, dtype=torch.uint8, device=w_bits.device)
+        self._check(self._lib.dsmc_chi_mlp_pack(self.h, _ptr(w_bits, torch.int16), _ptr(packed), _stream(stream)),
+                    "chi_mlp_pack")
+        return packed
+
+    def chi_mlp_forward(self, packed, bias, x, y=None, chi=None, stream=None):
+        """dsmc_chi_mlp_forward: x [n, 2] float32 -> (y, chi), float32 [n]."""
+        n = x.shape[0]
+        if y is None:
+            y = torch.empty(n, dtype=torch.float32, device=x.device)
+        if chi is None:
+            chi = torch.empty(n, dtype=torch.float32, device=x.device)
+        self._check(self._lib.dsmc_chi_mlp_forward(self.h, _ptr(packed), _ptr(bias, torch.float32), n,
+                                                   _ptr(x, torch.float32), _ptr(y, torch.float32),
+                                                   _ptr(chi, torch.float32), _stream(stream)), "chi_mlp_forward")
+        return y, chi
+
+    def chi_mlp_table(self, packed, bias, nb=512, nE=512, out=None, stream=None):
+        """dsmc_chi_mlp_table: the nE x nb chi table synthesised by the chi-MLP."""
+        if out is None:
+            out = torch.empty((nE, nb), dtype=torch.float32, device=packed.device)
+        self._check(self._lib.dsmc_chi_mlp_table(self.h, _ptr(packed), _ptr(bias, torch.float32), nb, nE,
+                                                 _ptr(out, torch.float32), _stream(stream)), "chi_mlp_table")
+        return out
 
     def collide_table(self, gas: Gas, table: "ChiTable", step, sel, vx, vy, vz, chi_out=None, ws=None,
                       stream=None):
