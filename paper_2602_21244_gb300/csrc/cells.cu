@@ -303,7 +303,16 @@ k_rs_scatter(const int32_t* __restrict__ cell_id, const uint32_t* __restrict__ k
   for (int j = 0; j < kRsPer; ++j) {
     const bool has = s0 + j * 32 + lane < n;
     const int d = has ? (int)((key[j] >> shift) & (kRadix - 1)) : -1;
-    const unsigned same = __match_any_sync(0xffffffffu, d);
+    // lanes holding the same digit: one ballot per digit bit (ALU pipe),
+    // the same set as a match on d (a lane without an element has d = -1:
+    // all ones, in no valid lane's set, and the ones without form their own)
+    unsigned same = __ballot_sync(0xffffffffu, has);
+    if (!has) same = ~same;
+#pragma unroll
+    for (int bit = 0; bit < kRadixBits; ++bit) {
+      const unsigned m = __ballot_sync(0xffffffffu, (d >> bit) & 1);
+      same &= ((d >> bit) & 1) ? m : ~m;
+    }
     if (has) {
       const int q = wh[w][d] + __popc(same & lt);
       if (keys_out) keys_out[q] = key[j];
