@@ -410,6 +410,18 @@ def oracle_sample(seconds_target=15.0, path="neural", steps=1):
                        f"{dt:.1f} s single-threaded")
 
 
+def aggregate(ms, pairs, dist, device="cpu"):
+    """Replicas: the job's time is the slowest rank's, its work the sum of the
+    ranks' pairs; value = summed pairs / slowest time (pairs per second)."""
+    if dist is None:
+        return ms, pairs / (ms * 1e-3)
+    import torch
+    t = torch.tensor([ms, pairs], dtype=torch.float64, device=device)
+    mx = t.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone(); dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1]) / (float(mx[0]) * 1e-3)
+
+
 def headline_config(name, n, nc, path, world):
     """The workload the headline is quoted on (both arms report the same)."""
     return {"workload": f"hypersonic argon gas {name}, {n} particles, {nc} cells", "path": path,
@@ -463,10 +475,7 @@ def main():
     ms = head["ms_per_step"]
     value = head["collisions_per_s"]
     if dist is not None:
-        t = torch.tensor([ms, head["pairs_per_step"]], dtype=torch.float64, device="cuda")
-        mx = t.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone(); dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms = float(mx[0]); value = float(sm[1]) / (ms * 1e-3)
+        ms, value = aggregate(ms, head["pairs_per_step"], dist, device="cuda")
     if rank == 0:
         pk = peaks()
         roof = None
