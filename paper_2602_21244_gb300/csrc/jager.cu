@@ -827,10 +827,13 @@ __global__ void __launch_bounds__(kTrThreads) k_transport_q2(PotDev P, Transport
     const double E = a.T ? tr_x(a, e % a.nx) * a.T[e / a.nx] : a.E[e];
     double acc = 0.0;
     if (E > 0.0 && E < 1e30) {   // chi takes E in FP32
+      // the node's b only ever enters chi in FP32: formed in FP32 (GB300's
+      // FP64 pipe bounds this kernel); the weights stay FP64
+      const float inv_panels = 1.f / (float)a.b_panels, bmaxf = (float)a.bmax;
       for (int32_t k = threadIdx.x; k < a.nb; k += kTrThreads) {
         const int q = k % kTrNodes;
-        const double u = (k / kTrNodes + a.gl_x[q]) / a.b_panels;
-        const float chi = chi_device(P, (float)(a.bmax * sqrt(u)), (float)E);
+        const float u = ((float)(k / kTrNodes) + (float)a.gl_x[q]) * inv_panels;
+        const float chi = chi_device(P, bmaxf * sqrtf(u), (float)E);
         const float sn = sinf(chi);
         acc += a.gl_w[q] * (double)(sn * sn);
       }
