@@ -188,9 +188,14 @@ int dsmc_sort_cells_static(int32_t n, int32_t n_cells, const int32_t* cell_id, c
                            const double* vy, const double* vz, int32_t* perm, int32_t* cell_start,
                            double* svx, double* svy, double* svz, int* status, void* stream);
 
-/* Per-cell moments of sorted velocities, two FP64 passes:
+/* Per-cell moments of sorted velocities:
  * mom[5k..5k+4] = {N, sum vx, sum vy, sum vz, Theta = sum |v - u|^2},
- * u = sum v / N.  Non-finite velocities record DSMC_ERR_NONFINITE. */
+ * u = sum v / N, as exact integer sums: each component is rounded to the
+ * cell's unit (the unit in the last place of its largest component, 2^c
+ * coarser for cells of 2^(9+c) particles or more so that the sums fit 64
+ * bits), the sums and the centred sum of squares are exact (128-bit), and
+ * only the results are converted to FP64 (independent of the order of the
+ * sums).  Non-finite velocities record DSMC_ERR_NONFINITE. */
 int dsmc_cell_moments(dsmc_ctx_t* ctx, int32_t n_cells, const int32_t* cell_start,
                       const double* vx, const double* vy, const double* vz, double* mom,
                       void* stream);
@@ -453,8 +458,8 @@ enum {
   DSMC_TUNE_GATHER = 0,        /* cell sort: gather of the velocities into sorted order */
   DSMC_TUNE_MOMENTS = 1,       /* cell moments */
   DSMC_TUNE_MOMENT_MATCH = 2,  /* moment matching */
-  DSMC_TUNE_COLLIDE_VHS = 3,   /* VHS collide (persistent, cooperative) */
-  DSMC_TUNE_COLLIDE_JAGER = 4, /* Jager collide (persistent, cooperative) */
+  DSMC_TUNE_COLLIDE_VHS = 3,   /* VHS collide (persistent) */
+  DSMC_TUNE_COLLIDE_JAGER = 4, /* Jager collide (persistent) */
   DSMC_TUNE_JAGER_CHI = 5,     /* chi batch */
   DSMC_TUNE_COLLIDE_TABLE = 6, /* look-up collide */
   DSMC_TUNE_KERNELS = 7
@@ -466,7 +471,7 @@ typedef struct {
   int32_t threads;       /* threads per block: a multiple of 32 up to the kernel's limit */
   int32_t blocks_per_sm; /* blocks per SM of the grid (1..64): the grid is this many
                             blocks per SM, or fewer when the work is smaller; for the
-                            cooperative collides at most what the occupancy allows
+                            persistent collides at most what the occupancy allows
                             (clamped there at launch) */
   float ms;              /* mean time of one launch, ms (0 when not measured) */
 } dsmc_tune_entry_t;

@@ -70,7 +70,7 @@ ShapeInfo shape_info(int k) {
 
 // Candidate shapes of one kernel: block sizes up to the kernel's limit with
 // at most 2048 threads and 32 blocks per SM (the chi batch grid-strides over up to
-// 64 blocks per SM); for the cooperative collides
+// 64 blocks per SM); for the persistent collides
 // the full occupancy at each block size and half of it.
 static int tune_candidates(int k, dsmc_tune_entry_t* out, int cap) {
   int n = 0;

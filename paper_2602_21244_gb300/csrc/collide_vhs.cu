@@ -61,13 +61,6 @@ __global__ void __launch_bounds__(256) k_collide_vhs(VhsArgs a) {
   }
 }
 
-int cooperative_blocks(Ctx* c, const void* kernel, int threads, size_t smem) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
-      per_sm < 1)
-    return 0;
-  return per_sm * sm_count(c);
-}
 
 // resident blocks per SM of the VHS collide at a block size (0 on failure)
 int occupancy_collide_vhs(int threads) {

@@ -292,7 +292,6 @@ int launch_mlp_forward(Ctx* c, const dsmc_mlp_t& mlp, const uint16_t* w, const f
                        int64_t n, const float* x, float* y, cudaStream_t s);
 int launch_tc_selftest(Ctx* c, int N, int K, int layout, const uint16_t* A, const uint16_t* B, float* D,
                        cudaStream_t s);
-int cooperative_blocks(Ctx* c, const void* kernel, int threads, size_t smem);
 
 // Launch shapes of the tunable kernels (DSMC_TUNE_*): threads per block and
 // blocks per SM, {0, 0} while the built-in shape is in force.
@@ -314,7 +313,7 @@ inline Shape shape_or_default(Ctx* c, int kernel) {
   }
   return s;
 }
-// resident blocks per SM of the cooperative collide kernels at a block size
+// resident blocks per SM of the persistent collide kernels at a block size
 int occupancy_collide_vhs(int threads);
 int occupancy_collide_jager(int threads);
 // the gather step of the cell sort alone (autotuning)

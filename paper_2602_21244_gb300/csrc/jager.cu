@@ -693,7 +693,6 @@ __global__ void __launch_bounds__(128) k_harvest(PotDev P, int64_t n, const doub
   }
 }
 
-int cooperative_blocks(Ctx* c, const void* kernel, int threads, size_t smem);
 
 static unsigned blocks_n(int64_t n, int threads, int cap) {
   int64_t b = (n + threads - 1) / threads;

@@ -18,9 +18,10 @@
 // projects y onto the energy shell and applies the centre-of-mass update of
 // its pair in FP64.
 //
-// The collide kernel is persistent and cooperative: it walks the rounds of
-// the step (pairs of one round are disjoint) with a bounded grid barrier in
-// between, as the other collide kernels do.
+// The collide kernel is persistent: each group claims 128-pair tiles of one
+// round at a time from a global cursor, in round-major order, and a row
+// waits (bounded) until the previous pairs of its two particles are done
+// (per-particle done stamps), so no grid-wide barrier separates the rounds.
 #include <cstdio>
 
 #include "internal.cuh"
@@ -633,7 +634,6 @@ int launch_selftest_mbar(Ctx* c, uint64_t limit_ns, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
 }
 
-int cooperative_blocks(Ctx* c, const void* kernel, int threads, size_t smem);
 
 static bool set_smem(const void* k, int bytes) {
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
