@@ -64,6 +64,17 @@ def parse():
     return ap.parse_args()
 
 
+def phase_bytes(n, nc, pairs):
+    """Algorithmic HBM bytes of each phase of one step (inputs read once,
+    outputs written once): sort 56 B/particle (cell id and velocities in, perm
+    and sorted velocities out) + cell_start; moments 24 B/particle + 40 B/cell;
+    selection 24 B/particle + 16 B/cell ((sigma g)_max in and out) + 20 B/pair
+    (pair and dependency word); collide 104 B/pair; moment matching 48
+    B/particle + 40 B/cell."""
+    return {"sort": 56 * n + 4 * (nc + 1), "moments": 24 * n + 40 * nc, "select": 24 * n + 16 * nc + 20 * pairs,
+            "collide": 104 * pairs, "moment_match": 48 * n + 40 * nc}
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -250,8 +261,13 @@ def run_gb300(args, rank, world, dist):
                 g_pairs += st.info_host()["n_pairs"]
         torch.cuda.synchronize()
         g_launches = C.launch_count() - lg0
+        pb = phase_bytes(n, nc, pairs / K)
+        pk = peaks()
+        hbm = pk.get("hbm_gbs") if pk else 6800.0
+        phase_gbs = {k: pb[k] / (phase_ms[k] / K * 1e-3) / 1e9 for k in pb}
         results[path] = dict(
             collisions_per_s=g_pairs / (g_ms * 1e-3), ms_per_step=g_ms / K,
+            phase_gbs=phase_gbs, phase_hbm_frac={k: v / hbm for k, v in phase_gbs.items()},
             phased=dict(collisions_per_s=pairs / (step_ms * 1e-3), ms_per_step=step_ms / K),
             pairs_per_step=pairs / K, rounds_per_step=float(np.mean(rounds)),
             phase_ms={k: v / K for k, v in phase_ms.items()}, gpu_launches=g_launches,
@@ -285,6 +301,30 @@ def run_gb300(args, rank, world, dist):
         ms = e0.elapsed_time(e1) / 3
         extra["chi_batch"] = dict(pairs=nb, ms=ms, chi_per_s=nb / (ms * 1e-3), n_nodes=args.n_nodes,
                                   shape=chi_tuned)
+        # the sort alone on the shuffled gas of the step and on a nearly sorted one
+        # (cell order with 10 % of the particles moved to a neighbouring cell, as
+        # after an advection step)
+        srt_out = dict(perm=st.perm, cell_start=st.cell_start, svx=st.svx, svy=st.svy, svz=st.svz)
+        order = np.argsort(wl["cell_id"], kind="stable")
+        cid_ns = wl["cell_id"][order].copy()
+        rng_ns = np.random.default_rng(11)
+        moved = rng_ns.random(n) < 0.1
+        cid_ns[moved] = np.clip(cid_ns[moved] + rng_ns.choice([-1, 1], int(moved.sum())), 0, nc - 1)
+        inputs_ns = [torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+                     for a in (cid_ns.astype(np.int32), wl["vx"][order], wl["vy"][order], wl["vz"][order])]
+        sort_ms = {}
+        for name, inp in (("shuffled", pristine), ("nearly_sorted", inputs_ns)):
+            for _ in range(2):
+                C.sort_cells(*inp, nc, out=srt_out, ws=st.ws)
+            e0.record(stream)
+            for _ in range(5):
+                C.sort_cells(*inp, nc, out=srt_out, ws=st.ws)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sort_ms[name] = e0.elapsed_time(e1) / 5
+        del inputs_ns
+        extra["sort"] = dict(particles=n, ms=sort_ms,
+                             gbs={k: phase_bytes(n, nc, 0)["sort"] / (v * 1e-3) / 1e9 for k, v in sort_ms.items()})
         # transport integrals: Omega(2,2)(T) and mu(T) at 64 temperatures (500 K to 20,000 K),
         # 32 b-panels x 8 x-panels of 16 nodes: 65,536 chi per temperature
         Tt = torch.from_numpy(np.geomspace(500.0, 2.0e4, 64)).to(dev)
