@@ -545,7 +545,7 @@ __device__ __forceinline__ double unit_bits(const FixScale& f) {
   return e > 0 ? __longlong_as_double((long long)e << 52) : __longlong_as_double(1ll << (f.E + f.c - 1));
 }
 
-__global__ void __launch_bounds__(kCellWarps * 32)
+__global__ void __launch_bounds__(kCellWarps * 32, 5)
 k_moments(int32_t n_cells, const int32_t* __restrict__ cs, const double* __restrict__ vx,
           const double* __restrict__ vy, const double* __restrict__ vz, double* __restrict__ mom,
           int* status) {
@@ -589,7 +589,7 @@ int launch_moments(Ctx* c, int32_t n_cells, const int32_t* cs, const double* vx,
 // formed by lanes 0..2 of the cell together (GB300's FP64 pipe costs a whole
 // warp instruction however few lanes are active) and passed to the cell's
 // eight lanes by shuffles.
-__global__ void __launch_bounds__(kCellWarps * 32)
+__global__ void __launch_bounds__(kCellWarps * 32, 5)
 k_moment_match(int32_t n_cells, const int32_t* __restrict__ cs, const double* __restrict__ mom,
                double* __restrict__ vx, double* __restrict__ vy, double* __restrict__ vz) {
   const int lane = threadIdx.x & 31, sl = lane & (kSeg - 1), seg = lane / kSeg;
