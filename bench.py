@@ -15,7 +15,8 @@ per-phase (per-kernel) times.
 
 Output: one JSON line on rank 0.  The headline ``value`` is accepted pair
 collisions per second of the whole step on the neural path; ``paths``
-holds all three update rules.  Multi-GPU runs are replicas (each rank its
+holds every update rule; for the VHS and look-up rules ``fused`` times the
+same step fused into one pass over cell groups (dsmc_step_fused).  Multi-GPU runs are replicas (each rank its
 own gas, no collective on the data path): ``value`` sums over ranks.
 """
 from __future__ import annotations
@@ -261,6 +262,29 @@ def run_gb300(args, rank, world, dist):
                 g_pairs += st.info_host()["n_pairs"]
         torch.cuda.synchronize()
         g_launches = C.launch_count() - lg0
+        fused = None
+        if path in ("vhs", "table"):
+            # the same step fused into one pass over cell groups (dsmc_step_fused)
+            C.sigma_g_max_init(gas, T_cell, 5.0, out=st.sigma_g_max)
+            f_ms, f_pairs, lf0 = 0.0, 0, None
+            for it in range(args.warmup + args.steps):
+                if it == args.warmup:
+                    torch.cuda.synchronize()
+                    lf0 = C.launch_count()
+                restore()
+                e0, e1 = ev(), ev()
+                e0.record(stream)
+                C.step_fused(gas, path_d, st, it)
+                e1.record(stream)
+                if it >= args.warmup:
+                    torch.cuda.synchronize()
+                    if C.sync_status() != 0:
+                        raise RuntimeError(f"device status on fused path {path}")
+                    f_ms += e0.elapsed_time(e1)
+                    f_pairs += st.info_host()["n_pairs"]
+            torch.cuda.synchronize()
+            fused = dict(collisions_per_s=f_pairs / (f_ms * 1e-3), ms_per_step=f_ms / K,
+                         gpu_launches=C.launch_count() - lf0)
         pb = phase_bytes(n, nc, pairs / K)
         pk = peaks()
         hbm = pk.get("hbm_gbs") if pk else 6800.0
@@ -272,7 +296,7 @@ def run_gb300(args, rank, world, dist):
             pairs_per_step=pairs / K, rounds_per_step=float(np.mean(rounds)),
             phase_ms={k: v / K for k, v in phase_ms.items()}, gpu_launches=g_launches,
             phased_gpu_launches=launches,
-            step_ms_total=step_ms, pairs_total=pairs, autotune=tuned)
+            step_ms_total=step_ms, pairs_total=pairs, autotune=tuned, fused=fused)
         if path == "neural":
             neural_kernel = dict(ms=phase_ms["collide"] / K, pairs=pairs / K)
     # ------------------------------------------------------------ standalone kernels

@@ -434,6 +434,24 @@ size_t dsmc_step_workspace_size(int32_t n, int32_t n_cells, int64_t capacity);
 int dsmc_step(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_path_t* path,
               const dsmc_step_buffers_t* buf, uint64_t step, void* stream);
 
+/* The same step fused into one pass (Sec. 2.2-2.5): after the cell sort's
+ * keys, one persistent kernel stages groups of consecutive cells in shared
+ * memory once and runs their gather, pre moments, NTC selection, rounds,
+ * pair updates and moment matching there, so each particle's velocity is
+ * read from and written to device memory once.  Paths: DSMC_PATH_VHS and
+ * DSMC_PATH_TABLE (others return DSMC_ERR_UNSUPPORTED).  Same buffers and
+ * results as dsmc_step -- bit for bit: perm, cell_start, s{x,y,z}, mom,
+ * sigma_g_max and *info (n_pairs, n_candidates, n_rounds) -- except that no
+ * pair list is produced: `pairs`, `deps` and `round_offsets` are left
+ * unspecified.  A cell whose particles or candidates exceed a shared-memory
+ * batch (1024 particles, 3072 candidates) takes 12 bytes of scratch per
+ * candidate from `pairs` (capacity entries); if that runs out,
+ * DSMC_ERR_CAPACITY is recorded and the cell is not collided; a cell of more
+ * than 65536 particles records DSMC_ERR_UNSUPPORTED the same way.  ws:
+ * dsmc_step_workspace_size bytes.  Not captured by dsmc_step_graph_capture. */
+int dsmc_step_fused(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_path_t* path,
+                    const dsmc_step_buffers_t* buf, uint64_t step, void* stream);
+
 /* Capture one whole step -- dsmc_step with these arguments -- as a CUDA
  * graph owned by the context (replacing any earlier one).  The buffers must
  * stay allocated while the graph is used.  `stream` must be a non-default

@@ -512,8 +512,9 @@ size_t dsmc_step_workspace_size(int32_t n, int32_t n_cells, int64_t capacity) {
   // the phases run one after another and share the workspace
   const size_t a = dsmc::sort_ws(n, n_cells), b = dsmc::select_ws(n, n_cells, capacity),
                d = dsmc::collide_ws(n);
-  const size_t ab = a > b ? a : b;
-  return ab > d ? ab : d;
+  const size_t ab = a > b ? a : b, f = dsmc::fused_ws(n) > a ? dsmc::fused_ws(n) : a;
+  const size_t abd = ab > d ? ab : d;
+  return abd > f ? abd : f;
 }
 
 // the pair update of one step's path (after selection)
@@ -573,6 +574,32 @@ static int step_after_sort(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path
   rc = collide_step(c, gas, path, B, step, stream);
   if (rc) return rc;
   return dsmc_moment_match(c, B->n_cells, B->cell_start, B->mom, B->svx, B->svy, B->svz, stream);
+}
+
+int dsmc_step_fused(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t* path,
+                    const dsmc_step_buffers_t* B, uint64_t step, void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, gas && path && B, "step_fused: null argument");
+  if (int rc = check_gas(c, gas)) return rc;
+  if (path->path != DSMC_PATH_VHS && path->path != DSMC_PATH_TABLE)
+    return dsmc::record(c, DSMC_ERR_UNSUPPORTED, "step_fused: VHS and look-up paths only");
+  if (path->path == DSMC_PATH_TABLE) {
+    REQUIRE(c, gas->mass > 0, "step_fused: gas with mass > 0 required");
+    if (int rc = check_table(c, path->table)) return rc;
+  }
+  REQUIRE(c, B->n >= 0 && B->n_cells >= 1 && B->capacity >= 0, "step_fused: bad sizes");
+  REQUIRE(c, B->cell_start && B->ws && B->mom && B->sigma_g_max && B->info, "step_fused: null buffer");
+  REQUIRE(c, B->n == 0 || (B->cell_id && B->vx && B->vy && B->vz && B->perm && B->svx && B->svy && B->svz),
+          "step_fused: null array");
+  REQUIRE(c, B->capacity == 0 || B->pairs, "step_fused: null pair buffer");
+  REQUIRE(c, B->ws_bytes >= dsmc_step_workspace_size(B->n, B->n_cells, B->capacity),
+          "step_fused: workspace too small");
+  cudaStream_t s = S(stream);
+  int rc = dsmc::launch_sort_keys(c, B->n, B->n_cells, B->cell_id, B->perm, B->cell_start, B->ws, B->ws_bytes, s);
+  if (rc) return rc;
+  return dsmc::launch_step_fused(c, *gas, path->path, path->table, step, B->n, B->n_cells, B->cell_start, B->perm,
+                                 B->vx, B->vy, B->vz, B->svx, B->svy, B->svz, B->mom, B->sigma_g_max, B->pairs,
+                                 B->capacity, B->info, B->ws, B->ws_bytes, s);
 }
 
 int dsmc_step_graph_capture(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t* path,

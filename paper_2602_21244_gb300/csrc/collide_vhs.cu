@@ -7,6 +7,7 @@
 // pairs of a round are disjoint, so no two lanes of a unit touch the same
 // particle.  Velocities are read and written through L2 (ld/st .cg).
 #include "internal.cuh"
+#include "pair.cuh"
 
 namespace dsmc {
 
@@ -41,19 +42,11 @@ __global__ void __launch_bounds__(256) k_collide_vhs(VhsArgs a) {
       const int4 q = a.pairs[p];
       ok = wait_deps(a.done, q.x, q.y, a.deps[p], a.bar + 2, a.status);
       if (ok) {
-        const double xi = __ldcg(a.vx + q.x), yi = __ldcg(a.vy + q.x), zi = __ldcg(a.vz + q.x);
-        const double xj = __ldcg(a.vx + q.y), yj = __ldcg(a.vy + q.y), zj = __ldcg(a.vz + q.y);
-        const double dx = xi - xj, dy = yi - yj, dz = zi - zj;
-        const double g = sqrt(dx * dx + dy * dy + dz * dz);
-        const u32x4 w = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_ISO);
-        const double c = 2.0 * u53(w.x, w.y) - 1.0;
-        const double s = sqrt(1.0 - c * c);
-        double se, ce;
-        sincos(2.0 * DSMC_PI * u53(w.z, w.w), &se, &ce);
-        const double rx = g * c, ry = g * s * ce, rz = g * s * se;
-        const double cx = 0.5 * (xi + xj), cy = 0.5 * (yi + yj), cz = 0.5 * (zi + zj);
-        __stcg(a.vx + q.x, cx + 0.5 * rx); __stcg(a.vy + q.x, cy + 0.5 * ry); __stcg(a.vz + q.x, cz + 0.5 * rz);
-        __stcg(a.vx + q.y, cx - 0.5 * rx); __stcg(a.vy + q.y, cy - 0.5 * ry); __stcg(a.vz + q.y, cz - 0.5 * rz);
+        double v[6] = {__ldcg(a.vx + q.x), __ldcg(a.vy + q.x), __ldcg(a.vz + q.x),
+                       __ldcg(a.vx + q.y), __ldcg(a.vy + q.y), __ldcg(a.vz + q.y)};
+        vhs_pair(a.seed, a.step, (uint32_t)q.w, (uint32_t)q.z, v);
+        __stcg(a.vx + q.x, v[0]); __stcg(a.vy + q.x, v[1]); __stcg(a.vz + q.x, v[2]);
+        __stcg(a.vx + q.y, v[3]); __stcg(a.vy + q.y, v[4]); __stcg(a.vz + q.y, v[5]);
         release_pair(a.done, q.x, q.y, (unsigned)(r + 1));
       }
     }

@@ -332,6 +332,14 @@ int launch_train(Ctx* c, const dsmc_mlp_t& mlp, int mode, uint64_t seed, uint64_
 int launch_adam(Ctx* c, int n_w, int n_b, const float* grad, float* master, float* m, float* v, uint16_t* w,
                 float* bias, float lr, double b1, double b2, double eps, int64_t step, cudaStream_t s);
 
+// the fused step (cell groups staged in shared memory), after the sort's keys
+size_t fused_ws(int32_t n);
+int launch_step_fused(Ctx* c, const dsmc_gas_t& gas, int path, const dsmc_chi_table_t* tab, uint64_t step,
+                      int32_t n, int32_t n_cells, const int32_t* cs, const int32_t* perm, const double* vx,
+                      const double* vy, const double* vz, double* svx, double* svy, double* svz, double* mom,
+                      double* sgmax, int32_t* pairs, int64_t capacity, dsmc_select_info_t* info, void* ws,
+                      size_t ws_bytes, cudaStream_t s);
+
 // exclusive scan of int32 counts -> offsets[n+1] (offsets[n] = total)
 size_t scan_ws(int64_t n);
 int launch_scan(Ctx* c, const int32_t* in, int32_t* out, int64_t n, void* ws, cudaStream_t s);

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "pair.cuh"
 
 namespace dsmc {
 
@@ -457,56 +458,6 @@ __device__ __forceinline__ void deflect(double u, double v, double w, double g, 
   o[2] = cc * w + g * sc * (ce * cz + se * az);
 }
 
-// The rotation of v_r = (ux, uy, uz) by chi with azimuth eps (Bird 1994,
-// Eq. 2.22) with the direction in FP32 -- chi itself carries FP32 accuracy
-// -- then scaled in FP64 to |v_r'| = |v_r| exactly: s = |v_r|/|y| from an
-// FP32 estimate and one FP64 Newton step on s^2 |y|^2 = |v_r|^2 (relative
-// error ~1e-14).  About a third of the FP64 work of deflect().
-__device__ __forceinline__ void deflect_shell_h(double ux, double uy, double uz, double g2, float chi, float eps,
-                                                double* h, double* Y);
-
-__device__ __forceinline__ void deflect_shell(double ux, double uy, double uz, double g2, float chi, float eps,
-                                              double* o) {
-  double h, Y[3];
-  deflect_shell_h(ux, uy, uz, g2, chi, eps, &h, Y);
-  o[0] = 2.0 * h * Y[0]; o[1] = 2.0 * h * Y[1]; o[2] = 2.0 * h * Y[2];
-}
-
-// The same rotation, returned as v_r' = 2 h Y (Y the FP32 rotated direction
-// widened to FP64, h half the FP64 shell scale), so that a caller can form
-// the post-collision velocities as c +- h Y with one FMA each.
-__device__ __forceinline__ void deflect_shell_h(double ux, double uy, double uz, double g2, float chi, float eps,
-                                                double* h, double* Yo) {
-  const float fx = f64_to_f32(ux), fy = f64_to_f32(uy), fz = f64_to_f32(uz);
-  float sc, cc, se, ce;
-  sincosf(chi, &sc, &cc);
-  sincosf(eps, &se, &ce);
-  const float q2 = fy * fy + fz * fz, gf2 = fx * fx + q2;
-  const float gf = sqrtf(gf2);
-  float cx, cy, cz, ax, ay, az;
-  if (q2 > 1e-24f * gf2 && q2 > 0.f) {
-    const float iq = rsqrtf(q2), q = q2 * iq, ig = 1.f / gf;
-    cx = 0.f; cy = fz * iq; cz = -fy * iq;
-    ax = q * ig; ay = -fx * fy * iq * ig; az = -fx * fz * iq * ig;
-  } else {
-    cx = 0.f; cy = 1.f; cz = 0.f;
-    ax = 0.f; ay = 0.f; az = fx >= 0.f ? -1.f : 1.f;
-  }
-  const float y0 = cc * fx + gf * sc * (ce * cx + se * ax);
-  const float y1 = cc * fy + gf * sc * (ce * cy + se * ay);
-  const float y2 = cc * fz + gf * sc * (ce * cz + se * az);
-  const double Y0 = y0, Y1 = y1, Y2 = y2;
-  Yo[0] = Y0; Yo[1] = Y1; Yo[2] = Y2;
-  const double ny2 = Y0 * Y0 + Y1 * Y1 + Y2 * Y2;
-  if (!(ny2 > 0.0)) { *h = 0.0; return; }
-  const float ny2f = (float)ny2, g2f = (float)g2;
-  const float sf = sqrtf(g2f / ny2f);
-  const double s0 = sf;
-  const double res = g2 - s0 * s0 * ny2;
-  // one Newton step on s^2 ny2 = g2 from s0, halved: h = s / 2
-  *h = 0.5 * s0 + res * (double)(0.25f * sf / g2f);
-}
-
 struct JagerArgs {
   uint64_t seed, step;
   const uint64_t* step_dev;
@@ -592,11 +543,7 @@ __global__ void __launch_bounds__(128) k_chi_table(PotDev P, int32_t nb, int32_t
 struct TableArgs {
   uint64_t seed, step;
   const uint64_t* step_dev;
-  const float* T;
-  int32_t nb, nE;
-  float nb1;                 // nb - 1: x = b~ (nb - 1)
-  float lnE_min, inv_dlnE;   // y = (ln E - lnE_min) inv_dlnE
-  float mass_over_4k;
+  TableLook look;
   const int4* pairs;
   const uint32_t* deps;
   const int32_t* ro;
@@ -607,18 +554,6 @@ struct TableArgs {
   unsigned* bar;   // [2] abort word, [3] unit cursor
   int* status;
 };
-
-// chi by bilinear interpolation at (x, y) in node units, y clamped to the table
-__device__ __forceinline__ float chi_lookup(const TableArgs& a, float x, float y) {
-  x = fminf(fmaxf(x, 0.f), (float)(a.nb - 1));
-  y = fminf(fmaxf(y, 0.f), (float)(a.nE - 1));
-  const int i0 = min((int)x, a.nb - 2), j0 = min((int)y, a.nE - 2);
-  const float fx = x - (float)i0, fy = y - (float)j0;
-  const float* r0 = a.T + (size_t)j0 * a.nb + i0;
-  const float* r1 = r0 + a.nb;
-  const float t00 = __ldg(r0), t01 = __ldg(r0 + 1), t10 = __ldg(r1), t11 = __ldg(r1 + 1);
-  return (1.f - fy) * ((1.f - fx) * t00 + fx * t01) + fy * ((1.f - fx) * t10 + fx * t11);
-}
 
 // The Jager pair update with chi from the table (b~ = sqrt(U1), eps = 2 pi U2
 // from tag 4, E~ = ln(m g^2 / (4 k_B))); work claimed and ordered as in
@@ -641,26 +576,12 @@ __global__ void __launch_bounds__(256) k_collide_table(TableArgs a) {
       const int4 q = a.pairs[p];
       ok = wait_deps(a.done, q.x, q.y, a.deps[p], a.bar + 2, a.status);
       if (ok) {
-        const double xi = __ldcg(a.vx + q.x), yi = __ldcg(a.vy + q.x), zi = __ldcg(a.vz + q.x);
-        const double xj = __ldcg(a.vx + q.y), yj = __ldcg(a.vy + q.y), zj = __ldcg(a.vz + q.y);
-        const double ux = xi - xj, uy = yi - yj, uz = zi - zj;
-        const double g2 = ux * ux + uy * uy + uz * uz;
-        const u32x4 w = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_JAGER);
-        float chi = 0.f;
-        double h = 0.0, Y[3] = {0.0, 0.0, 0.0};
-        if (g2 > 0.0) {
-          // the table coordinate and the azimuth only ever enter in FP32:
-          // their uniforms are formed in FP32 too (GB300's FP64 pipe bounds
-          // this kernel), to within one FP32 rounding of the FP64 values
-          const float x = sqrtf(u_f32(w.x, w.y)) * a.nb1;
-          const float y = (logf(a.mass_over_4k * (float)g2) - a.lnE_min) * a.inv_dlnE;
-          chi = chi_lookup(a, x, y);
-          deflect_shell_h(ux, uy, uz, g2, chi, u_f32(w.z, w.w) * 6.2831855f, &h, Y);
-        }
+        double v[6] = {__ldcg(a.vx + q.x), __ldcg(a.vy + q.x), __ldcg(a.vz + q.x),
+                       __ldcg(a.vx + q.y), __ldcg(a.vy + q.y), __ldcg(a.vz + q.y)};
+        const float chi = table_pair(a.look, a.seed, a.step, (uint32_t)q.w, (uint32_t)q.z, v);
         if (a.chi_out) a.chi_out[p] = chi;
-        const double sx = 0.5 * (xi + xj), sy = 0.5 * (yi + yj), sz = 0.5 * (zi + zj);
-        __stcg(a.vx + q.x, fma(h, Y[0], sx)); __stcg(a.vy + q.x, fma(h, Y[1], sy)); __stcg(a.vz + q.x, fma(h, Y[2], sz));
-        __stcg(a.vx + q.y, fma(-h, Y[0], sx)); __stcg(a.vy + q.y, fma(-h, Y[1], sy)); __stcg(a.vz + q.y, fma(-h, Y[2], sz));
+        __stcg(a.vx + q.x, v[0]); __stcg(a.vy + q.x, v[1]); __stcg(a.vz + q.x, v[2]);
+        __stcg(a.vx + q.y, v[3]); __stcg(a.vy + q.y, v[4]); __stcg(a.vz + q.y, v[5]);
         release_pair(a.done, q.x, q.y, (unsigned)(r + 1));
       }
     }
@@ -767,10 +688,7 @@ int launch_collide_table(Ctx* c, const dsmc_gas_t& gas, const dsmc_chi_table_t& 
   const int blocks = sm_count(c) * (sh.blocks_per_sm > 0 && sh.blocks_per_sm < occ ? sh.blocks_per_sm : occ);
   TableArgs a;
   a.seed = gas.seed; a.step = step; a.step_dev = graph_step_ptr(c);
-  a.T = tab.chi; a.nb = tab.nb; a.nE = tab.nE; a.nb1 = (float)(tab.nb - 1);
-  a.lnE_min = (float)tab.lnE_min;
-  a.inv_dlnE = (float)((tab.nE - 1) / (tab.lnE_max - tab.lnE_min));
-  a.mass_over_4k = (float)(gas.mass / (4.0 * DSMC_KB));
+  a.look = table_look(gas, tab);
   a.pairs = (const int4*)pairs; a.deps = deps; a.ro = ro; a.info = info;
   a.vx = vx; a.vy = vy; a.vz = vz; a.chi_out = chi_out;
   a.done = (unsigned*)ws; a.bar = barrier_ptr(c); a.status = status_ptr(c);

@@ -1,0 +1,135 @@
+// Per-pair post-collision velocities of the CUDA-core update rules, shared
+// by the collide kernels and the fused step: the VHS isotropic scatter
+// (Sec. 2.1) and the deflection by a chi looked up in the table of the
+// look-up path (Sec. 3.4.5), each with the centre-of-mass update (Sec. 2.3).
+// A pair's random numbers are keyed by its candidate index m and cell k, so
+// which thread runs a pair never changes its result.
+#pragma once
+#include "internal.cuh"
+
+namespace dsmc {
+
+// VHS (tag 3): v_r' = g (c, s cos e, s sin e), c = 2 U1 - 1, s = sqrt(1 - c^2),
+// e = 2 pi U2; v = (vi, vj) in, post-collision (vi', vj') out.
+__device__ __forceinline__ void vhs_pair(uint64_t seed, uint64_t step, uint32_t m, uint32_t k, double v[6]) {
+  const double xi = v[0], yi = v[1], zi = v[2], xj = v[3], yj = v[4], zj = v[5];
+  const double dx = xi - xj, dy = yi - yj, dz = zi - zj;
+  const double g = sqrt(dx * dx + dy * dy + dz * dz);
+  const u32x4 w = draw(seed, m, k, step, TAG_ISO);
+  const double c = 2.0 * u53(w.x, w.y) - 1.0;
+  const double s = sqrt(1.0 - c * c);
+  double se, ce;
+  sincos(2.0 * DSMC_PI * u53(w.z, w.w), &se, &ce);
+  const double rx = g * c, ry = g * s * ce, rz = g * s * se;
+  const double cx = 0.5 * (xi + xj), cy = 0.5 * (yi + yj), cz = 0.5 * (zi + zj);
+  v[0] = cx + 0.5 * rx; v[1] = cy + 0.5 * ry; v[2] = cz + 0.5 * rz;
+  v[3] = cx - 0.5 * rx; v[4] = cy - 0.5 * ry; v[5] = cz - 0.5 * rz;
+}
+
+// The rotation of v_r = (ux, uy, uz) by chi with azimuth eps (Bird 1994,
+// Eq. 2.22) with the direction in FP32 -- chi itself carries FP32 accuracy
+// -- then scaled in FP64 to |v_r'| = |v_r| exactly: s = |v_r|/|y| from an
+// FP32 estimate and one FP64 Newton step on s^2 |y|^2 = |v_r|^2 (relative
+// error ~1e-14).  About a third of the FP64 work of deflect().
+__device__ __forceinline__ void deflect_shell_h(double ux, double uy, double uz, double g2, float chi, float eps,
+                                                double* h, double* Y);
+
+__device__ __forceinline__ void deflect_shell(double ux, double uy, double uz, double g2, float chi, float eps,
+                                              double* o) {
+  double h, Y[3];
+  deflect_shell_h(ux, uy, uz, g2, chi, eps, &h, Y);
+  o[0] = 2.0 * h * Y[0]; o[1] = 2.0 * h * Y[1]; o[2] = 2.0 * h * Y[2];
+}
+
+// The same rotation, returned as v_r' = 2 h Y (Y the FP32 rotated direction
+// widened to FP64, h half the FP64 shell scale), so that a caller can form
+// the post-collision velocities as c +- h Y with one FMA each.
+__device__ __forceinline__ void deflect_shell_h(double ux, double uy, double uz, double g2, float chi, float eps,
+                                                double* h, double* Yo) {
+  const float fx = f64_to_f32(ux), fy = f64_to_f32(uy), fz = f64_to_f32(uz);
+  float sc, cc, se, ce;
+  sincosf(chi, &sc, &cc);
+  sincosf(eps, &se, &ce);
+  const float q2 = fy * fy + fz * fz, gf2 = fx * fx + q2;
+  const float gf = sqrtf(gf2);
+  float cx, cy, cz, ax, ay, az;
+  if (q2 > 1e-24f * gf2 && q2 > 0.f) {
+    const float iq = rsqrtf(q2), q = q2 * iq, ig = 1.f / gf;
+    cx = 0.f; cy = fz * iq; cz = -fy * iq;
+    ax = q * ig; ay = -fx * fy * iq * ig; az = -fx * fz * iq * ig;
+  } else {
+    cx = 0.f; cy = 1.f; cz = 0.f;
+    ax = 0.f; ay = 0.f; az = fx >= 0.f ? -1.f : 1.f;
+  }
+  const float y0 = cc * fx + gf * sc * (ce * cx + se * ax);
+  const float y1 = cc * fy + gf * sc * (ce * cy + se * ay);
+  const float y2 = cc * fz + gf * sc * (ce * cz + se * az);
+  const double Y0 = y0, Y1 = y1, Y2 = y2;
+  Yo[0] = Y0; Yo[1] = Y1; Yo[2] = Y2;
+  const double ny2 = Y0 * Y0 + Y1 * Y1 + Y2 * Y2;
+  if (!(ny2 > 0.0)) { *h = 0.0; return; }
+  const float ny2f = (float)ny2, g2f = (float)g2;
+  const float sf = sqrtf(g2f / ny2f);
+  const double s0 = sf;
+  const double res = g2 - s0 * s0 * ny2;
+  // one Newton step on s^2 ny2 = g2 from s0, halved: h = s / 2
+  *h = 0.5 * s0 + res * (double)(0.25f * sf / g2f);
+}
+
+// The chi table of the look-up path in the form the pair update reads it.
+struct TableLook {
+  const float* T;
+  int32_t nb, nE;
+  float nb1;                 // nb - 1: x = b~ (nb - 1)
+  float lnE_min, inv_dlnE;   // y = (ln E - lnE_min) inv_dlnE
+  float mass_over_4k;
+};
+
+inline TableLook table_look(const dsmc_gas_t& gas, const dsmc_chi_table_t& tab) {
+  TableLook L;
+  L.T = tab.chi; L.nb = tab.nb; L.nE = tab.nE; L.nb1 = (float)(tab.nb - 1);
+  L.lnE_min = (float)tab.lnE_min;
+  L.inv_dlnE = (float)((tab.nE - 1) / (tab.lnE_max - tab.lnE_min));
+  L.mass_over_4k = (float)(gas.mass / (4.0 * DSMC_KB));
+  return L;
+}
+
+// chi by bilinear interpolation at (x, y) in node units, y clamped to the table
+__device__ __forceinline__ float chi_lookup(const TableLook& a, float x, float y) {
+  x = fminf(fmaxf(x, 0.f), (float)(a.nb - 1));
+  y = fminf(fmaxf(y, 0.f), (float)(a.nE - 1));
+  const int i0 = min((int)x, a.nb - 2), j0 = min((int)y, a.nE - 2);
+  const float fx = x - (float)i0, fy = y - (float)j0;
+  const float* r0 = a.T + (size_t)j0 * a.nb + i0;
+  const float* r1 = r0 + a.nb;
+  const float t00 = __ldg(r0), t01 = __ldg(r0 + 1), t10 = __ldg(r1), t11 = __ldg(r1 + 1);
+  return (1.f - fy) * ((1.f - fx) * t00 + fx * t01) + fy * ((1.f - fx) * t10 + fx * t11);
+}
+
+// The Jager pair update with chi from the table (tag 4: b~ = sqrt(U1),
+// eps = 2 pi U2; E~ = ln(m g^2 / (4 k_B))); v in/out as in vhs_pair.
+// Returns chi.
+__device__ __forceinline__ float table_pair(const TableLook& L, uint64_t seed, uint64_t step, uint32_t m,
+                                            uint32_t k, double v[6]) {
+  const double xi = v[0], yi = v[1], zi = v[2], xj = v[3], yj = v[4], zj = v[5];
+  const double ux = xi - xj, uy = yi - yj, uz = zi - zj;
+  const double g2 = ux * ux + uy * uy + uz * uz;
+  const u32x4 w = draw(seed, m, k, step, TAG_JAGER);
+  float chi = 0.f;
+  double h = 0.0, Y[3] = {0.0, 0.0, 0.0};
+  if (g2 > 0.0) {
+    // the table coordinate and the azimuth only ever enter in FP32: their
+    // uniforms are formed in FP32 too (GB300's FP64 pipe bounds this
+    // update), to within one FP32 rounding of the FP64 values
+    const float x = sqrtf(u_f32(w.x, w.y)) * L.nb1;
+    const float y = (logf(L.mass_over_4k * (float)g2) - L.lnE_min) * L.inv_dlnE;
+    chi = chi_lookup(L, x, y);
+    deflect_shell_h(ux, uy, uz, g2, chi, u_f32(w.z, w.w) * 6.2831855f, &h, Y);
+  }
+  const double sx = 0.5 * (xi + xj), sy = 0.5 * (yi + yj), sz = 0.5 * (zi + zj);
+  v[0] = fma(h, Y[0], sx); v[1] = fma(h, Y[1], sy); v[2] = fma(h, Y[2], sz);
+  v[3] = fma(-h, Y[0], sx); v[4] = fma(-h, Y[1], sy); v[5] = fma(-h, Y[2], sz);
+  return chi;
+}
+
+}  // namespace dsmc

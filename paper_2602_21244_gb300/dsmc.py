@@ -154,6 +154,7 @@ def load(build: bool = True):
             "dsmc_moment_match": (C.c_int, [vp, i32, vp, vp, vp, vp, vp, vp]),
             "dsmc_step_workspace_size": (sz, [i32, i32, i64]),
             "dsmc_step": (C.c_int, [vp, P(Gas), P(Path), P(StepBuffers), u64, vp]),
+            "dsmc_step_fused": (C.c_int, [vp, P(Gas), P(Path), P(StepBuffers), u64, vp]),
             "dsmc_ctx_reserve": (C.c_int, [vp, i32, i32, i64]),
             "dsmc_step_graph_capture": (C.c_int, [vp, P(Gas), P(Path), P(StepBuffers), vp]),
             "dsmc_step_graph_launch": (C.c_int, [vp, u64, vp]),
@@ -540,6 +541,11 @@ class Context:
     def step(self, gas: Gas, path: Path, bufs: "StepState", step: int, stream=None):
         self._check(self._lib.dsmc_step(self.h, C.byref(gas), C.byref(path), C.byref(bufs.desc),
                                         step, _stream(stream)), "step")
+
+    def step_fused(self, gas: Gas, path: Path, bufs: "StepState", step: int, stream=None):
+        """The step fused into one pass over cell groups (VHS and look-up paths)."""
+        self._check(self._lib.dsmc_step_fused(self.h, C.byref(gas), C.byref(path), C.byref(bufs.desc),
+                                              step, _stream(stream)), "step_fused")
 
     def step_graph_capture(self, gas: Gas, path: Path, bufs: "StepState", stream):
         """Capture a whole step as a CUDA graph (stream: a non-default torch stream)."""
