@@ -155,8 +155,19 @@ def run_gb300(args, rank, world, dist):
     stream = torch.cuda.current_stream()
     sel = st.sel
 
-    def restore():
-        st.cell_id.copy_(pristine[0]); st.vx.copy_(pristine[1]); st.vy.copy_(pristine[2]); st.vz.copy_(pristine[3])
+    def restore(src=None):
+        src = pristine if src is None else src
+        st.cell_id.copy_(src[0]); st.vx.copy_(src[1]); st.vy.copy_(src[2]); st.vz.copy_(src[3])
+
+    # the same gas nearly sorted: cell order with 10 % of the particles moved
+    # to a neighbouring cell, as after an advection step
+    order = np.argsort(wl["cell_id"], kind="stable")
+    cid_ns = wl["cell_id"][order].copy()
+    rng_ns = np.random.default_rng(11)
+    moved = rng_ns.random(n) < 0.1
+    cid_ns[moved] = np.clip(cid_ns[moved] + rng_ns.choice([-1, 1], int(moved.sum())), 0, nc - 1)
+    nearly_sorted = [torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+                     for a in (cid_ns.astype(np.int32), wl["vx"][order], wl["vy"][order], wl["vz"][order])]
 
     results = {}
     neural_kernel = None
@@ -264,27 +275,36 @@ def run_gb300(args, rank, world, dist):
         g_launches = C.launch_count() - lg0
         fused = None
         if path in ("vhs", "table"):
-            # the same step fused into one pass over cell groups (dsmc_step_fused)
-            C.sigma_g_max_init(gas, T_cell, 5.0, out=st.sigma_g_max)
-            f_ms, f_pairs, lf0 = 0.0, 0, None
-            for it in range(args.warmup + args.steps):
-                if it == args.warmup:
-                    torch.cuda.synchronize()
-                    lf0 = C.launch_count()
-                restore()
-                e0, e1 = ev(), ev()
-                e0.record(stream)
-                C.step_fused(gas, path_d, st, it)
-                e1.record(stream)
-                if it >= args.warmup:
-                    torch.cuda.synchronize()
-                    if C.sync_status() != 0:
-                        raise RuntimeError(f"device status on fused path {path}")
-                    f_ms += e0.elapsed_time(e1)
-                    f_pairs += st.info_host()["n_pairs"]
-            torch.cuda.synchronize()
-            fused = dict(collisions_per_s=f_pairs / (f_ms * 1e-3), ms_per_step=f_ms / K,
-                         gpu_launches=C.launch_count() - lf0)
+            # the same step fused into one pass over cell groups (dsmc_step_fused),
+            # on the shuffled gas; then both forms on the nearly sorted one
+            def timed(run, src, s=stream):
+                C.sigma_g_max_init(gas, T_cell, 5.0, out=st.sigma_g_max)
+                torch.cuda.synchronize()
+                t_ms, t_pairs, l0 = 0.0, 0, None
+                for it in range(args.warmup + args.steps):
+                    if it == args.warmup:
+                        torch.cuda.synchronize()
+                        l0 = C.launch_count()
+                    with torch.cuda.stream(s):
+                        restore(src)
+                        e0, e1 = ev(), ev()
+                        e0.record(s)
+                        run(it)
+                        e1.record(s)
+                    if it >= args.warmup:
+                        torch.cuda.synchronize()
+                        if C.sync_status(s) != 0:
+                            raise RuntimeError(f"device status on {path}")
+                        t_ms += e0.elapsed_time(e1)
+                        t_pairs += st.info_host()["n_pairs"]
+                torch.cuda.synchronize()
+                return dict(collisions_per_s=t_pairs / (t_ms * 1e-3), ms_per_step=t_ms / K,
+                            gpu_launches=C.launch_count() - l0)
+            fused = timed(lambda it: C.step_fused(gas, path_d, st, it), None)
+            # the unfused step as the graph captured above
+            fused["nearly_sorted"] = dict(
+                unfused=timed(lambda it: C.step_graph_launch(it, gstream), nearly_sorted, gstream),
+                fused=timed(lambda it: C.step_fused(gas, path_d, st, it), nearly_sorted))
         pb = phase_bytes(n, nc, pairs / K)
         pk = peaks()
         hbm = pk.get("hbm_gbs") if pk else 6800.0
@@ -329,15 +349,8 @@ def run_gb300(args, rank, world, dist):
         # (cell order with 10 % of the particles moved to a neighbouring cell, as
         # after an advection step)
         srt_out = dict(perm=st.perm, cell_start=st.cell_start, svx=st.svx, svy=st.svy, svz=st.svz)
-        order = np.argsort(wl["cell_id"], kind="stable")
-        cid_ns = wl["cell_id"][order].copy()
-        rng_ns = np.random.default_rng(11)
-        moved = rng_ns.random(n) < 0.1
-        cid_ns[moved] = np.clip(cid_ns[moved] + rng_ns.choice([-1, 1], int(moved.sum())), 0, nc - 1)
-        inputs_ns = [torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-                     for a in (cid_ns.astype(np.int32), wl["vx"][order], wl["vy"][order], wl["vz"][order])]
         sort_ms = {}
-        for name, inp in (("shuffled", pristine), ("nearly_sorted", inputs_ns)):
+        for name, inp in (("shuffled", pristine), ("nearly_sorted", nearly_sorted)):
             for _ in range(2):
                 C.sort_cells(*inp, nc, out=srt_out, ws=st.ws)
             e0.record(stream)
@@ -346,7 +359,6 @@ def run_gb300(args, rank, world, dist):
             e1.record(stream)
             torch.cuda.synchronize()
             sort_ms[name] = e0.elapsed_time(e1) / 5
-        del inputs_ns
         extra["sort"] = dict(particles=n, ms=sort_ms,
                              gbs={k: phase_bytes(n, nc, 0)["sort"] / (v * 1e-3) / 1e9 for k, v in sort_ms.items()})
         # transport integrals: Omega(2,2)(T) and mu(T) at 64 temperatures (500 K to 20,000 K),

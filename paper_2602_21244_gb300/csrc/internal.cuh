@@ -142,6 +142,30 @@ __device__ __forceinline__ float f64_to_f32(double v) {
   return __uint_as_float(e < 897 ? sign : f);
 }
 
+// FP32 -> FP64 (exact) on the integer pipe, from the IEEE-754 layouts: the
+// exponent rebiased by 1023 - 127 = 896 and the 23-bit fraction placed at
+// the top of the 52-bit one; subnormal inputs normalised first, zeros,
+// infinities and NaNs kept.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t sign = u & 0x80000000u;
+  uint32_t e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  uint32_t hi;
+  if (e == 0xFFu) {
+    hi = sign | 0x7FF00000u | (m >> 3);
+  } else if (e == 0u && m == 0u) {
+    hi = sign;
+  } else {
+    if (e == 0u) {   // subnormal: value 2^-126 m 2^-23, leading one moved to bit 23
+      const uint32_t sh = (uint32_t)__clz(m) - 8u;
+      m = (m << sh) & 0x7FFFFFu;
+      e = 1u - sh;
+    }
+    hi = sign | ((e + 896u) << 20) | (m >> 3);
+  }
+  return __hiloint2double((int)hi, (int)(m << 29));
+}
+
 // ---------------------------------------------------------------- pair dependencies
 // The collide kernels walk the pairs of a step in round-major order without
 // grid-wide barriers.  Work units (a warp's 32 pairs, a 128-pair MLP tile)

@@ -527,14 +527,19 @@ __device__ __forceinline__ void update_row(const NeuralArgs& a, const float y[3]
   for (int c = 0; c < 6; ++c) v[c] = __hiloint2double((int)st[5 + 2 * c], (int)st[4 + 2 * c]);
   const double ux = v[0] - v[3], uy = v[1] - v[4], uz = v[2] - v[5];
   const double g2 = ux * ux + uy * uy + uz * uz;
-  double y0 = y[0], y1 = y[1], y2 = y[2];
+  // the FP32 <-> FP64 conversions on the integer pipe (GB300's FP64 pipe,
+  // which runs the conversion instructions, bounds this update)
+  double y0 = f32_to_f64(y[0]), y1 = f32_to_f64(y[1]), y2 = f32_to_f64(y[2]);
   const double ny2 = y0 * y0 + y1 * y1 + y2 * y2;
-  if (ny2 > a.eps * a.eps) {
-    const float g2f = (float)g2, ny2f = (float)ny2;
+  const float g2f = f64_to_f32(g2);
+  // (a pair with g = 0, or g^2 below the FP32 range, takes the other branch:
+  // v_r' = g e = 0 up to ~1e-19 m/s, where the shell scale would divide by 0)
+  if (ny2 > a.eps * a.eps && g2f > 0.f) {
+    const float ny2f = f64_to_f32(ny2);
     const float sf = sqrtf(g2f / ny2f);
-    const double s0 = sf;
+    const double s0 = f32_to_f64(sf);
     const double res = g2 - s0 * s0 * ny2;           // g2 - s0^2 ny2
-    const double sc = s0 + res * (double)(0.5f * sf / g2f);
+    const double sc = s0 + res * f32_to_f64(0.5f * sf / g2f);
     y0 *= sc; y1 *= sc; y2 *= sc;                    // v_r'
   } else {  // isotropic fallback direction (tag 3)
     const int4 q = a.pairs[p];
