@@ -368,7 +368,9 @@ int dsmc_mlp_forward(dsmc_ctx_t* ctx, const dsmc_mlp_t* mlp, const uint16_t* wei
  * N a multiple of 16 in [16, 256], K a multiple of 16 in [16, 128].
  * layout bit 0: A held MN-major in shared memory, bit 1: B MN-major (as the
  * backward pass reads them), bit 2: exchange the two descriptor offsets of
- * MN-major operands (a check of the descriptor convention). */
+ * MN-major operands (a check of the descriptor convention), bit 3: A in
+ * tensor memory instead of shared memory (row m in lane m, two bf16 per
+ * 32-bit column; not with bit 0). */
 int dsmc_tc_selftest(dsmc_ctx_t* ctx, int32_t N, int32_t K, int32_t layout, const uint16_t* A,
                      const uint16_t* B, float* D, void* stream);
 

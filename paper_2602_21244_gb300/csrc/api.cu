@@ -402,7 +402,8 @@ int dsmc_tc_selftest(dsmc_ctx_t* c, int32_t N, int32_t K, int32_t layout, const 
   CHECK_CTX(c);
   REQUIRE(c, N >= 16 && N <= 256 && N % 16 == 0 && K >= 16 && K <= 128 && K % 16 == 0,
           "tc_selftest: N in [16,256], K in [16,128], multiples of 16");
-  REQUIRE(c, layout >= 0 && layout <= 7, "tc_selftest: layout in [0, 7]");
+  REQUIRE(c, layout >= 0 && layout <= 15 && !((layout & 8) && (layout & 1)),
+          "tc_selftest: layout in [0, 15], A in tensor memory is K-major");
   REQUIRE(c, A && B && D, "tc_selftest: null pointer");
   return dsmc::launch_tc_selftest(c, N, K, layout, A, B, D, S(stream));
 }

@@ -1,19 +1,22 @@
 // Neural collision operator (Sec. 2.2-2.3) on the tcgen05 tensor cores.
 //
 // A CTA of 512 threads runs two warp groups of 8 warps, each owning a tile
-// of 128 pairs in its own shared-memory slot and its own 128 TMEM columns,
-// so that one group's feature build, activation epilogue and pair update run
-// while the tensor core works on the other group's layer (ping-pong; a
-// single 16-warp group when two slots do not fit in shared memory).  Within
-// a group: thread t < 128 builds row t of the bf16 input tile X, one elected
-// thread issues the layer's tcgen05.mma chain (K-major operands, FP32
+// of 128 pairs and 256 TMEM columns (the FP32 accumulator, then the next
+// layer's A operand), so that one group's feature build, activation epilogue
+// and pair update run while the tensor core works on the other group's layer
+// (ping-pong; a single 16-warp group when two slots do not fit).  Within a
+// group: thread t < 128 builds row t of the bf16 input tile X (shared
+// memory), one elected thread issues the layer's tcgen05.mma chain (FP32
 // accumulator in TMEM) and waits on the group's mbarrier, the group's warps
 // read their 32 TMEM lanes back (tcgen05.ld), add the bias, apply the
-// activation and write the next layer's A operand to shared memory as two
-// bf16 terms (hi = bf16(a), lo = bf16(a - hi)) multiplied by the same bf16
-// weights: bf16 operands, FP32 accumulation, about 16 significant bits kept
-// for the activations (single bf16 storage costs up to 6e-2 in the output
-// direction of badly conditioned pairs).  The weights of all layers stay in
+// activation and write the next layer's A operand into tensor memory
+// (tcgen05.st; row m in lane m, two bf16 per column) as two bf16 terms
+// (hi = bf16(a), lo = bf16(a - hi)) multiplied by the same bf16 weights:
+// bf16 operands, FP32 accumulation, about 16 significant bits kept for the
+// activations (single bf16 storage costs up to 6e-2 in the output direction
+// of badly conditioned pairs).  A hidden layer's MMA thus reads only its
+// weights from shared memory (with A there too its operand reads ran near
+// the SM's shared-memory bandwidth).  The weights of all layers stay in
 // shared memory for the life of the CTA.  After the last layer thread t
 // projects y onto the energy shell and applies the centre-of-mass update of
 // its pair in FP64.
@@ -36,17 +39,16 @@ constexpr int kWidth = 128;
 constexpr int kKin = 32;         // input as two bf16 terms: [hi (16) | lo (16)]
 constexpr int kNout = 16;        // padded output width
 constexpr int kMaxHidden = 4;
-constexpr int kStashCols = 16;   // per-row pair data handed from builder to updater threads
+constexpr int kStashWords = 16;  // per-row pair data handed from builder to updater threads
 
 // dynamic shared memory layout (bytes).  The weights are shared; each of the
 // `slots` tile slots (one per warp group) has its own X, activation tiles,
 // mbarrier and flag.
 struct MlpLayout {
-  uint32_t w_out, w_in, w_sq, slot0, slot_bytes, bias, ybuf, ybuf_bytes, mbar, tptr, flag, claim, fail, total;
+  uint32_t w_out, w_in, w_sq, slot0, slot_bytes, bias, ybuf, ybuf_bytes, mbar, tptr, flag, claim, fail, stash,
+      total;
   int slots;
   __host__ __device__ uint32_t x(int g) const { return slot0 + (uint32_t)g * slot_bytes; }
-  __host__ __device__ uint32_t h(int g) const { return x(g) + kTileM * kKin * 2; }
-  __host__ __device__ uint32_t hlo(int g) const { return h(g) + kTileM * kWidth * 2; }
 };
 
 constexpr uint32_t kMaxSmem = 232448 - 1024;  // 227 KB opt-in per CTA, less the static shared memory
@@ -58,7 +60,7 @@ __host__ __device__ inline MlpLayout mlp_layout(int n_hidden, int slots) {
   L.w_in = L.w_out + 3 * kWidth * 4;                  // [128 x 32] = [W1 | W1]
   L.w_sq = L.w_in + kWidth * kKin * 2;                // (n_hidden-1) x [128 x 128]
   L.slot0 = L.w_sq + (uint32_t)(n_hidden - 1) * kWidth * kWidth * 2;
-  L.slot_bytes = kTileM * kKin * 2 + 2 * kTileM * kWidth * 2;  // X [128 x 32], hi and lo [128 x 128]
+  L.slot_bytes = kTileM * kKin * 2;                  // X [128 x 32] (hi | lo)
   L.bias = L.slot0 + (uint32_t)slots * L.slot_bytes;  // floats: n_hidden*128 + 16
   // per slot: partial outputs of the column groups other than the first
   L.ybuf = L.bias + (uint32_t)(n_hidden * kWidth + kNout) * 4;
@@ -69,7 +71,10 @@ __host__ __device__ inline MlpLayout mlp_layout(int n_hidden, int slots) {
   L.flag = L.tptr + 4;                                // slots x 4 bytes: mbarrier wait result
   L.claim = L.flag + 8;                               // slots x 4 bytes: next claimed unit
   L.fail = L.claim + 8;                               // slots x 4 bytes: a dependency wait failed
-  L.total = L.fail + 8 + 2048;  // slack after the last operand tile
+  // slots x 2 buffers x kStashWords x 128 words (word-major: a warp's rows
+  // are consecutive words)
+  L.stash = (L.fail + 8 + 15u) & ~15u;
+  L.total = L.stash + (uint32_t)slots * 2 * kStashWords * kTileM * 4 + 256;
   return L;
 }
 
@@ -154,9 +159,12 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
   uint64_t* mbar = (uint64_t*)(smem + L.mbar) + q.g;
   volatile int* flag = (volatile int*)(smem + L.flag) + q.g;
   const uint32_t sbase = tc::smem_u32(smem);
-  const uint32_t xs = L.x(q.g), hs = L.h(q.g), hls = L.hlo(q.g);
-  const uint32_t acc = tmem + (uint32_t)(q.g * kWidth);
-  const uint32_t lane_tm = acc + ((uint32_t)((gw & 3) * 32) << 16);
+  const uint32_t xs = L.x(q.g);
+  const uint32_t acc = tmem + (uint32_t)(q.g * 2 * kWidth);
+  // the next layer's A operand: hi in columns [0, 64) of this region, lo in [64, 128)
+  const uint32_t a_hi = acc + kWidth, a_lo = a_hi + kWidth / 2;
+  const uint32_t lane_q = (uint32_t)((gw & 3) * 32) << 16;
+  const uint32_t lane_tm = acc + lane_q;
   const float* bs = (const float*)(smem + L.bias);
   const float* wo = (const float*)(smem + L.w_out);
   // output-layer partial sums, even and odd columns apart
@@ -176,12 +184,10 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
         // activations enter as hi + lo bf16 terms against the same weights
 #pragma unroll
         for (int s = 0; s < kWidth / 16; ++s)
-          tc::mma_bf16(acc, tc::sdesc(sbase + hs + 256u * s, 128, 2048),
-                       tc::sdesc(sbase + wb + 256u * s, 128, 2048), idesc, s > 0);
+          tc::mma_bf16_ta(acc, a_hi + 8u * s, tc::sdesc(sbase + wb + 256u * s, 128, 2048), idesc, s > 0);
 #pragma unroll
         for (int s = 0; s < kWidth / 16; ++s)
-          tc::mma_bf16(acc, tc::sdesc(sbase + hls + 256u * s, 128, 2048),
-                       tc::sdesc(sbase + wb + 256u * s, 128, 2048), idesc, 1);
+          tc::mma_bf16_ta(acc, a_lo + 8u * s, tc::sdesc(sbase + wb + 256u * s, 128, 2048), idesc, 1);
       }
       tc::commit(mbar);
       if (l == 0 && cursor) *claim = (int)atomicAdd(cursor, 1u);
@@ -244,19 +250,16 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
                                         m1, v[k]);
             lo[k] = tc::pack_bf16x2(r.x, r.y);
           }
-#pragma unroll
-          for (int j = 0; j < 2; ++j) {
-            const uint32_t off = tc::kmajor_offset(row, c0 + 8 * j, kWidth);
-            tc::st_shared_v4(sbase + hs + off, pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
-            tc::st_shared_v4(sbase + hls + off, lo[4 * j], lo[4 * j + 1], lo[4 * j + 2], lo[4 * j + 3]);
-          }
+          // columns c0 .. c0 + 15 of this row: 8 TMEM columns per term
+          tc::st8_async(a_hi + lane_q + (uint32_t)(c0 >> 1), pk);
+          tc::st8_async(a_lo + lane_q + (uint32_t)(c0 >> 1), lo);
         }
         if (more) tc::wait_ld16(nxt);
       }
     }
     if (!last) {
+      tc::wait_st();   // this thread's A operand stores complete before the MMA is issued
       tc::fence_before();
-      tc::fence_async_smem();
       group_sync(q);
     }
   }
@@ -301,9 +304,8 @@ __device__ __forceinline__ void write_x_row(char* smem, const MlpLayout& L, int 
   tc::st_shared_v4(sb + tc::kmajor_offset(t, 24, kKin), lo[4], lo[5], lo[6], lo[7]);
 }
 
-// CTA prologue/epilogue: TMEM allocation by warp 0 (128 columns per tile
-// slot), one mbarrier per slot.
-// accumulators (128 per slot) then two stashes of 16 columns per slot
+// CTA prologue/epilogue: TMEM allocation by warp 0 (per tile slot 128
+// accumulator columns and 128 columns of A operand), one mbarrier per slot.
 __device__ __forceinline__ uint32_t tmem_cols(int slots) { return slots > 1 ? 512u : 256u; }
 
 __device__ __forceinline__ uint32_t cta_setup(char* smem, const MlpLayout& L) {
@@ -366,7 +368,8 @@ __global__ void __launch_bounds__(kThreads) k_mlp_forward(MlpShape sh, const uin
 // D[128 x N] = A[128 x K] B[N x K]^T with the same operand layout and MMA
 // issue as the MLP (one CTA).  layout bit 0: A stored MN-major (the tile of
 // A^T, rows = k), bit 1: B stored MN-major, bit 2: exchange the roles of the
-// two descriptor offsets for MN-major operands (diagnostic).
+// two descriptor offsets for MN-major operands (diagnostic), bit 3: A in
+// tensor memory (row m in lane m, columns 256 + k/2, two bf16 per column).
 __device__ __forceinline__ uint64_t operand_desc(uint32_t base, int mn_major, int swap, int MN, int K, int s) {
   if (!mn_major) return tc::sdesc(base + 256u * s, 128, (uint32_t)(K / 8) * 128);
   // MN-major: core matrices along MN are 128 B apart, along K (8 rows) MN/8*128 B
@@ -382,8 +385,8 @@ __global__ void __launch_bounds__(128) k_tc_selftest(int N, int K, int layout, c
   const uint32_t a_off = 0, b_off = 128u * K * 2, mb = b_off + (uint32_t)N * K * 2;
   const uint32_t tp = mb + 8, fl = tp + 4;
   const int t = threadIdx.x;
-  const int a_mn = layout & 1, b_mn = (layout >> 1) & 1, swap = (layout >> 2) & 1;
-  for (int e = t; e < 128 * K; e += 128) {
+  const int a_mn = layout & 1, b_mn = (layout >> 1) & 1, swap = (layout >> 2) & 1, a_tm = (layout >> 3) & 1;
+  for (int e = t; e < 128 * K && !a_tm; e += 128) {
     const int m = e / K, k = e % K;
     *(uint16_t*)(smem + a_off + (a_mn ? tc::kmajor_offset(k, m, 128) : tc::kmajor_offset(m, k, K))) = A[e];
   }
@@ -393,6 +396,7 @@ __global__ void __launch_bounds__(128) k_tc_selftest(int N, int K, int layout, c
   }
   uint32_t ncols = 32;
   while ((int)ncols < N) ncols <<= 1;
+  if (a_tm) ncols = 512;   // D in columns [0, N), A in [256, 256 + K/2)
   if (t < 32) { tc::tmem_alloc((uint32_t*)(smem + tp), ncols); tc::tmem_relinquish(); }
   if (t == 0) { tc::mbar_init((uint64_t*)(smem + mb), 1); tc::mbar_fence_init(); }
   tc::fence_async_smem();
@@ -402,11 +406,29 @@ __global__ void __launch_bounds__(128) k_tc_selftest(int N, int K, int layout, c
   const uint32_t tmem = *(volatile uint32_t*)(smem + tp);
   const uint32_t sbase = tc::smem_u32(smem);
   volatile int* flag = (volatile int*)(smem + fl);
+  if (a_tm) {
+    // row t of A into lane t: columns 256 + k/2, k even in the low half
+    const uint32_t lane_a = tmem + ((uint32_t)((t >> 5) * 32) << 16) + 256u;
+    for (int c0 = 0; c0 < K / 2; c0 += 8) {
+      uint32_t r[8];
+      for (int q = 0; q < 8; ++q)
+        r[q] = (uint32_t)A[t * K + 2 * (c0 + q)] | ((uint32_t)A[t * K + 2 * (c0 + q) + 1] << 16);
+      tc::st8_async(lane_a + (uint32_t)c0, r);
+    }
+    tc::wait_st();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+  }
   if (t == 0) {
     const uint32_t idesc = tc::idesc_bf16(128, N) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16);
-    for (int s = 0; s < K / 16; ++s)
-      tc::mma_bf16(tmem, operand_desc(sbase + a_off, a_mn, swap, 128, K, s),
-                   operand_desc(sbase + b_off, b_mn, swap, N, K, s), idesc, s > 0);
+    for (int s = 0; s < K / 16; ++s) {
+      if (a_tm)
+        tc::mma_bf16_ta(tmem, tmem + 256u + 8u * s, operand_desc(sbase + b_off, b_mn, swap, N, K, s), idesc, s > 0);
+      else
+        tc::mma_bf16(tmem, operand_desc(sbase + a_off, a_mn, swap, 128, K, s),
+                     operand_desc(sbase + b_off, b_mn, swap, N, K, s), idesc, s > 0);
+    }
     tc::commit((uint64_t*)(smem + mb));
     *flag = tc::mbar_wait((uint64_t*)(smem + mb), 0, status, kBarrierLimitNs) ? 1 : 0;
   }
@@ -458,10 +480,10 @@ __device__ __forceinline__ void box_muller_f(uint32_t w1, uint32_t w2, float* z0
 
 // Build the MLP input row of pair p (features in FP32, Sec. 2.2 Eq. (mlp_input))
 // into the group's X tile and stash what the pair update needs -- p, the
-// particle slots and the six velocity components -- in this row's TMEM lane
-// (16 columns at `stash`).  p < 0 marks a padding row.
+// particle slots and the six velocity components -- in word w of the row at
+// stash[w * 128 + row] (shared memory).  p < 0 marks a padding row.
 __device__ __forceinline__ void build_row(char* smem, const MlpLayout& L, const MlpShape& sh,
-                                          const NeuralArgs& a, int g, int row, int32_t p, uint32_t stash) {
+                                          const NeuralArgs& a, int g, int row, int32_t p, uint32_t* stash) {
   float f[16];
 #pragma unroll
   for (int c = 0; c < 16; ++c) f[c] = 0.f;
@@ -508,17 +530,19 @@ __device__ __forceinline__ void build_row(char* smem, const MlpLayout& L, const 
   }
   write_x_row(smem, L, g, row, f);
   tc::fence_async_smem();
-  tc::st16(stash, st);
+#pragma unroll
+  for (int c = 0; c < kStashWords; ++c) stash[c * kTileM + row] = st[c];
 }
 
-// Pair update of one row from the MLP output y and the row's TMEM stash:
+// Pair update of one row from the MLP output y and the row's stash:
 // shell projection v_r' = |v_r| y/|y| and centre-of-mass update in FP64.
 // s = |v_r|/|y| from an FP32 estimate and one FP64 Newton step on
 // s^2 |y|^2 = |v_r|^2 (relative error ~1e-14), so |v_r'| = |v_r|.
-__device__ __forceinline__ void update_row(const NeuralArgs& a, const float y[3], uint32_t stash,
-                                           unsigned round1) {
+__device__ __forceinline__ void update_row(const NeuralArgs& a, const float y[3], const uint32_t* stash,
+                                           int row, unsigned round1) {
   uint32_t st[16];
-  tc::ld16u(stash, st);
+#pragma unroll
+  for (int c = 0; c < kStashWords; ++c) st[c] = stash[c * kTileM + row];
   const int32_t p = (int32_t)st[0];
   if (p < 0) return;
   const int32_t qi = (int32_t)st[1], qj = (int32_t)st[2];
@@ -567,8 +591,8 @@ __device__ __forceinline__ void update_row(const NeuralArgs& a, const float y[3]
 // done).  Within a group, threads 128..255 (the builders) prepare the next
 // tile's input rows while threads 0..127 (the updaters) apply this tile's
 // pair updates and stamp its particles done, the per-row data passing
-// through two alternating 16-column TMEM stashes; so the global loads of
-// the next tile overlap the FP64 update of this one.
+// through two alternating shared-memory stashes; so the global loads of the
+// next tile overlap the FP64 update of this one.
 __global__ void __launch_bounds__(kThreads) k_collide_neural(MlpShape sh, const uint16_t* __restrict__ w,
                                                            const float* __restrict__ bias, NeuralArgs a) {
   if (a.step_dev) a.step = *a.step_dev;
@@ -580,9 +604,8 @@ __global__ void __launch_bounds__(kThreads) k_collide_neural(MlpShape sh, const 
   uint32_t phase = 0;
   const int t = gq.t;
   const bool builder = t >= kTileM && t < 2 * kTileM, updater = t < kTileM;
-  // this thread's TMEM lane quadrant; stash columns after the accumulators
-  const uint32_t lane_off = (uint32_t)((((int)threadIdx.x >> 5) & 3) * 32) << 16;
-  const uint32_t stash0 = tmem + lane_off + (uint32_t)(L.slots * kWidth + gq.g * 2 * kStashCols);
+  // the group's two alternating stashes (builder -> updater)
+  uint32_t* stash0 = (uint32_t*)(smem + L.stash) + (size_t)gq.g * 2 * kStashWords * kTileM;
   volatile int* claim = (volatile int*)(smem + L.claim) + gq.g;
   volatile int* fail = (volatile int*)(smem + L.fail) + gq.g;
   const int R = a.info->n_rounds;
@@ -609,9 +632,9 @@ __global__ void __launch_bounds__(kThreads) k_collide_neural(MlpShape sh, const 
     const bool have_next = unit_range(a.ro, R, kTileM, r, base, (unsigned)*claim, &n0, &n1);
     if (builder && have_next) {
       const int32_t p = n0 + (t - kTileM);
-      build_row(smem, L, sh, a, gq.g, t - kTileM, p < n1 ? p : -1, stash0 + (buf ^ 1u) * kStashCols);
+      build_row(smem, L, sh, a, gq.g, t - kTileM, p < n1 ? p : -1, stash0 + (buf ^ 1u) * kStashWords * kTileM);
     }
-    if (updater) update_row(a, y, stash0 + buf * kStashCols, (unsigned)(r_cur + 1));
+    if (updater) update_row(a, y, stash0 + buf * kStashWords * kTileM, t, (unsigned)(r_cur + 1));
     tc::fence_before();
     group_sync(gq);
     tc::fence_after();

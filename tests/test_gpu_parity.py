@@ -42,7 +42,7 @@ def oracle_sorted(w):
 
 # ------------------------------------------------------------------ tensor-core layout
 
-@pytest.mark.parametrize("layout", [0, 1, 2, 3])
+@pytest.mark.parametrize("layout", [0, 1, 2, 3, 8, 10])
 @pytest.mark.parametrize("N,K", [(16, 16), (128, 16), (16, 128), (128, 128), (256, 64), (32, 128)])
 def test_tc_selftest_matches_matmul(N, K, layout):
     T = torch()
