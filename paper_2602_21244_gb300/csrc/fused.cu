@@ -73,7 +73,7 @@ struct FusedShared {
   float cdg[kFCells], csg32[kFCells];
   int32_t rcount[DSMC_MAX_ROUNDS + 1];  // per round: count, then start, then end
   int32_t scan_tmp[2 * kFWarps];
-  int32_t group, k0, k1, nb_cells, big, skip, rmax, npairs;
+  int32_t group, k0, k1, skip, rmax, npairs;
   long long gofs;
 };
 
@@ -418,7 +418,6 @@ __global__ void __launch_bounds__(kFThreads, 3) k_step_fused(FusedArgs a) {
       if (tid == 0) {
         S.cstart[c] = a.cs[kb + c] - a.cs[kb];
         if (big) S.cmofs[1] = S.cM[0];
-        S.big = big;
         S.skip = 0;
         if (big) {
           // a cell that alone exceeds the shared-memory batch: its candidates
