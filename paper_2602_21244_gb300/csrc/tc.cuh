@@ -283,37 +283,33 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
-// SiLU of four values with one reciprocal: d_k = 1 + e^{-z_k} (z_k clamped
-// below at -20, where SiLU is below 5e-8 in magnitude, so that the product
-// of the four d_k stays finite), r = 1/(d0 d1 d2 d3), 1/d0 = d1 (d2 d3 r) and
-// so on.  The special-function unit, which bounds the activation epilogue,
-// does 1.25 operations per value instead of 2; the extra multiplications
-// cost a few FP32 roundings.
-__device__ __forceinline__ void silu4(float* z) {
-  float d[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) d[k] = 1.f + __expf(-fmaxf(z[k], -20.f));
-  const float d01 = d[0] * d[1], d23 = d[2] * d[3];
-  const float r = rcp_approx(d01 * d23);
-  const float r01 = r * d23, r23 = r * d01;   // 1/(d0 d1), 1/(d2 d3)
-  z[0] *= d[1] * r01;
-  z[1] *= d[0] * r01;
-  z[2] *= d[3] * r23;
-  z[3] *= d[2] * r23;
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
-// silu4 on two packed pairs (z0, z1), (z2, z3): the same operations in the
-// same order, the additions and the final products as FP32x2 instructions
-// (Blackwell's paired FP32 pipe), so the results equal silu4's bit for bit.
+// SiLU z / (1 + e^{-z}) of two packed pairs (z0, z1), (z2, z3) with one
+// reciprocal: d_k = 1 + 2^{-z_k log2 e} (z_k clamped below at -20, where SiLU
+// is below 5e-8 in magnitude, so that the product of the four d_k stays
+// finite), r = 1/(d0 d1 d2 d3), z0/d0 = z0 d1 (d2 d3 r) and so on.  The
+// special-function unit, which bounds the activation epilogue, does 1.25
+// operations per value instead of 2; the scalings, the additions and the
+// final products run as FP32x2 instructions (Blackwell's paired FP32 pipe),
+// the denominators formed in swapped order so that z * (partner d) is one
+// paired product.
 __device__ __forceinline__ void silu4x2(float2& za, float2& zb) {
+  const float2 nl = make_float2(-1.44269504f, -1.44269504f);   // -log2(e)
+  const float2 ta = __fmul2_rn(make_float2(fmaxf(za.x, -20.f), fmaxf(za.y, -20.f)), nl);
+  const float2 tb = __fmul2_rn(make_float2(fmaxf(zb.x, -20.f), fmaxf(zb.y, -20.f)), nl);
   const float2 one = make_float2(1.f, 1.f);
-  const float2 da = __fadd2_rn(make_float2(__expf(-fmaxf(za.x, -20.f)), __expf(-fmaxf(za.y, -20.f))), one);
-  const float2 db = __fadd2_rn(make_float2(__expf(-fmaxf(zb.x, -20.f)), __expf(-fmaxf(zb.y, -20.f))), one);
+  const float2 da = __fadd2_rn(make_float2(ex2_approx(ta.y), ex2_approx(ta.x)), one);   // (d1, d0)
+  const float2 db = __fadd2_rn(make_float2(ex2_approx(tb.y), ex2_approx(tb.x)), one);   // (d3, d2)
   const float d01 = da.x * da.y, d23 = db.x * db.y;
   const float r = rcp_approx(d01 * d23);
-  const float r01 = r * d23, r23 = r * d01;
-  za = __fmul2_rn(za, make_float2(da.y * r01, da.x * r01));
-  zb = __fmul2_rn(zb, make_float2(db.y * r23, db.x * r23));
+  const float r01 = r * d23, r23 = r * d01;   // 1/(d0 d1), 1/(d2 d3)
+  za = __fmul2_rn(__fmul2_rn(za, da), make_float2(r01, r01));
+  zb = __fmul2_rn(__fmul2_rn(zb, db), make_float2(r23, r23));
 }
 
 __device__ __forceinline__ float tanh_approx(float x) {
