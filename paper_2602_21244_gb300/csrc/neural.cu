@@ -139,6 +139,19 @@ __device__ __forceinline__ void group_sync(const Group& q) {
   asm volatile("bar.sync %0, %1;" ::"r"(1 + q.g), "r"(q.nthr) : "memory");
 }
 
+// Layer 0's bias into this thread's TMEM lane of the group's accumulator,
+// in the columns its warp reads in the epilogues (before the first tile);
+// the caller synchronises the group before the first MMA.
+__device__ __forceinline__ void preload_bias(char* smem, const MlpLayout& L, const Group& q, uint32_t tmem) {
+  const int gw = q.t >> 5;
+  const int cgroups = q.nthr / kTileM, cols = kWidth / cgroups, cbeg = (gw >> 2) * cols;
+  const uint32_t lane_tm = tmem + (uint32_t)(q.g * 2 * kWidth) + ((uint32_t)((gw & 3) * 32) << 16);
+  const float* bs = (const float*)(smem + L.bias);
+  for (int c0 = cbeg; c0 < cbeg + cols; c0 += 16) tc::st16_async(lane_tm + (uint32_t)c0, (const uint32_t*)(bs + c0));
+  tc::wait_st();
+  tc::fence_before();
+}
+
 // Run all layers on the X tile already in the group's slot (fenced and
 // synchronised by the caller).  Returns false if a bounded wait ran out
 // (status recorded); y receives the output row (+ bias) of group thread q.t
@@ -152,6 +165,8 @@ __device__ __forceinline__ void group_sync(const Group& q) {
 __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, const Group& q,
                          uint32_t tmem, uint32_t& phase, float y[3], int* status,
                          unsigned* cursor = nullptr, volatile int* claim = nullptr) {
+  // every layer's accumulator starts from its bias, stored into it by the
+  // previous epilogue (by preload_bias before the first tile)
   const int gw = q.t >> 5;
   const int row = ((gw & 3) << 5) | (q.t & 31);
   const int cgroups = q.nthr / kTileM, cg = gw >> 2;
@@ -177,14 +192,14 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
         for (int s = 0; s < kKin / 16; ++s)
           tc::mma_bf16(acc, tc::sdesc(sbase + xs + 256u * s, 128, kKin * 16),
                        tc::sdesc(sbase + L.w_in + 256u * s, 128, kKin * 16),
-                       tc::idesc_bf16(kTileM, kWidth), s > 0);
+                       tc::idesc_bf16(kTileM, kWidth), 1);
       } else {
         const uint32_t wb = L.w_sq + (uint32_t)(l - 1) * kWidth * kWidth * 2;
         const uint32_t idesc = tc::idesc_bf16(kTileM, kWidth);
         // activations enter as hi + lo bf16 terms against the same weights
 #pragma unroll
         for (int s = 0; s < kWidth / 16; ++s)
-          tc::mma_bf16_ta(acc, a_hi + 8u * s, tc::sdesc(sbase + wb + 256u * s, 128, 2048), idesc, s > 0);
+          tc::mma_bf16_ta(acc, a_hi + 8u * s, tc::sdesc(sbase + wb + 256u * s, 128, 2048), idesc, 1);
 #pragma unroll
         for (int s = 0; s < kWidth / 16; ++s)
           tc::mma_bf16_ta(acc, a_lo + 8u * s, tc::sdesc(sbase + wb + 256u * s, 128, 2048), idesc, 1);
@@ -197,8 +212,10 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
     if (!*flag) return false;
     phase ^= 1u;
     tc::fence_after();
-    const float* bl = bs + l * kWidth;
     const bool last = l == sh.n_hidden - 1;
+    // the bias the accumulator must hold for its next use: layer l + 1's, or
+    // after the last layer the next tile's layer 0's
+    const float* bn = bs + (last ? 0 : l + 1) * kWidth;
     // this warp's columns in 16-wide pieces, the TMEM read of the next piece
     // in flight while the current one is processed
     const int cbeg = cg * cols, npieces = cols / 16;
@@ -214,14 +231,14 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
         const int c0 = cbeg + 16 * (pc + half);
         const bool more = pc + half + 1 < npieces;
         if (more) tc::ld16_async(lane_tm + (uint32_t)(c0 + 16), nxt);
-        // values in packed pairs (columns 2k, 2k + 1): bias additions,
-        // activation products, residuals and output-layer FMAs run two per
-        // instruction
+        // values in packed pairs (columns 2k, 2k + 1; the bias is already in
+        // them): activation products, residuals and output-layer FMAs run two
+        // per instruction
         float2 v[8];
-        const float2* b2 = (const float2*)(bl + c0);
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
-          v[k] = __fadd2_rn(make_float2(__uint_as_float(cur[2 * k]), __uint_as_float(cur[2 * k + 1])), b2[k]);
+        for (int k = 0; k < 8; ++k) v[k] = make_float2(__uint_as_float(cur[2 * k]), __uint_as_float(cur[2 * k + 1]));
+        // these 16 columns are read: they now receive the next use's bias
+        tc::st16_async(lane_tm + (uint32_t)c0, (const uint32_t*)(bn + c0));
         if (sh.act == 0) {
 #pragma unroll
           for (int k = 0; k < 8; k += 2) tc::silu4x2(v[k], v[k + 1]);
@@ -257,8 +274,9 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
         if (more) tc::wait_ld16(nxt);
       }
     }
+    // this thread's A operand and bias stores complete before the next MMA
+    tc::wait_st();
     if (!last) {
-      tc::wait_st();   // this thread's A operand stores complete before the MMA is issued
       tc::fence_before();
       group_sync(q);
     }
@@ -341,6 +359,7 @@ __global__ void __launch_bounds__(kThreads) k_mlp_forward(MlpShape sh, const uin
   load_weights(smem, L, sh, w, bias);
   const uint32_t tmem = cta_setup(smem, L);
   const Group q = my_group(L.slots);
+  preload_bias(smem, L, q, tmem);
   uint32_t phase = 0;
   const int64_t tiles = (n + kTileM - 1) / kTileM;
   bool alive = true;
@@ -601,6 +620,7 @@ __global__ void __launch_bounds__(kThreads) k_collide_neural(MlpShape sh, const 
   load_weights(smem, L, sh, w, bias);
   const uint32_t tmem = cta_setup(smem, L);
   const Group gq = my_group(L.slots);
+  preload_bias(smem, L, gq, tmem);
   uint32_t phase = 0;
   const int t = gq.t;
   const bool builder = t >= kTileM && t < 2 * kTileM, updater = t < kTileM;

@@ -167,6 +167,17 @@ __device__ __forceinline__ void st16(uint32_t taddr, const uint32_t* r) {
         "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
       : "memory");
 }
+// 16 consecutive 32-bit columns of this thread's TMEM lane, not waited for
+// (tcgen05.wait::st before an MMA or another thread uses them).
+__device__ __forceinline__ void st16_async(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+      "%13, %14, %15, %16};"
+      ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+
 // 8 consecutive 32-bit columns of this thread's TMEM lane, not waited for
 // (tcgen05.wait::st before the data is used by an MMA or another thread).
 __device__ __forceinline__ void st8_async(uint32_t taddr, const uint32_t* r) {
