@@ -55,17 +55,6 @@ __device__ __forceinline__ float u_f32(uint32_t a, uint32_t b) {
 // uniform integer in [0, n): high word of w*n
 __device__ __forceinline__ uint32_t mulhi_n(uint32_t w, uint32_t n) { return __umulhi(w, n); }
 
-// ---------------------------------------------------------------- warp helpers
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
 __device__ __forceinline__ int warp_sum_i(int v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -157,16 +157,6 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float* v) {
   for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-// 16 consecutive 32-bit columns of this thread's TMEM lane (same lane mapping
-// as ld16), waited for before returning.
-__device__ __forceinline__ void st16(uint32_t taddr, const uint32_t* r) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-      "%13, %14, %15, %16};\n\ttcgen05.wait::st.sync.aligned;"
-      ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
-        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
-      : "memory");
-}
 // 16 consecutive 32-bit columns of this thread's TMEM lane, not waited for
 // (tcgen05.wait::st before an MMA or another thread uses them).
 __device__ __forceinline__ void st16_async(uint32_t taddr, const uint32_t* r) {
@@ -188,16 +178,6 @@ __device__ __forceinline__ void st8_async(uint32_t taddr, const uint32_t* r) {
 }
 __device__ __forceinline__ void wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ void ld16u(uint32_t taddr, uint32_t* r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15}, [%16];\n\ttcgen05.wait::ld.sync.aligned;"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
-}
 
 // 16 columns issued without waiting; the registers are undefined until
 // wait_ld16 on the same array (which carries them as in/out operands, so no
@@ -323,11 +303,6 @@ __device__ __forceinline__ void silu4x2(float2& za, float2& zb) {
   zb = __fmul2_rn(__fmul2_rn(zb, db), make_float2(r23, r23));
 }
 
-__device__ __forceinline__ float tanh_approx(float x) {
-  float y;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
 
 }  // namespace tc
 }  // namespace dsmc
