@@ -239,12 +239,27 @@ __global__ void __launch_bounds__(kNT, 1) k_train(TrainArgs a) {
       float v[32];
       tc::ld32(lane_tm + (uint32_t)c0, v);
       uint32_t pk[16], lo[16];
+      // bias, activation (SiLU four values at a time on the paired FP32 pipe,
+      // as in the collide kernel's epilogue) and the hi + lo split, in pairs
+      const float2* b2 = (const float2*)(bias + l * kH + c0);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const float a0 = act_fn(a.act, v[2 * q] + bias[l * kH + c0 + 2 * q]);
-        const float a1 = act_fn(a.act, v[2 * q + 1] + bias[l * kH + c0 + 2 * q + 1]);
-        pk[q] = tc::pack_bf16x2(a0, a1);
-        lo[q] = tc::pack_bf16x2(a0 - __uint_as_float(pk[q] << 16), a1 - __uint_as_float(pk[q] & 0xFFFF0000u));
+      for (int q = 0; q < 16; q += 2) {
+        float2 va = __fadd2_rn(make_float2(v[2 * q], v[2 * q + 1]), b2[q]);
+        float2 vb = __fadd2_rn(make_float2(v[2 * q + 2], v[2 * q + 3]), b2[q + 1]);
+        if (a.act == 0) {
+          tc::silu4x2(va, vb);
+        } else {
+          va = make_float2(act_fn(a.act, va.x), act_fn(a.act, va.y));
+          vb = make_float2(act_fn(a.act, vb.x), act_fn(a.act, vb.y));
+        }
+        const float2 m1 = make_float2(-1.f, -1.f);
+        pk[q] = tc::pack_bf16x2(va.x, va.y);
+        pk[q + 1] = tc::pack_bf16x2(vb.x, vb.y);
+        const float2 ra = __ffma2_rn(make_float2(__uint_as_float(pk[q] << 16), __uint_as_float(pk[q] & 0xFFFF0000u)), m1, va);
+        const float2 rb = __ffma2_rn(make_float2(__uint_as_float(pk[q + 1] << 16), __uint_as_float(pk[q + 1] & 0xFFFF0000u)),
+                                     m1, vb);
+        lo[q] = tc::pack_bf16x2(ra.x, ra.y);
+        lo[q + 1] = tc::pack_bf16x2(rb.x, rb.y);
       }
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
