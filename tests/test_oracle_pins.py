@@ -404,6 +404,98 @@ def test_deflect_geometry():
     np.testing.assert_allclose(out, [300 * math.cos(0.5), 300 * math.sin(0.5), 0], atol=1e-12)
 
 
+def test_chi_batch_energy_is_the_reduced_mass_kinetic_energy():
+    """Sec. 3.4.2: the scattering integral depends on the relative kinetic
+    energy E_r = (1/2) mu g^2 with the reduced mass mu = m1 m2 / (m1 + m2)
+    (m/2 for like particles).  With a repulsive Coulomb potential V = kappa/r
+    the deflection angle has the closed form tan(chi/2) = kappa / (2 E_r b),
+    so the (b, g) batch pins the g -> E mapping of the oracle."""
+    kappa = 3.0e3
+    P = O.make_pot(dict(kind=2, kappa=kappa, p=1.0))
+    gas = O.make_gas(W.M_AR, 4.17e-10, 0.81, 273.0, 1.0, 1.0, 0, model=1, b_max=1.2e-9)
+    b = np.array([0.3, 1.0, 2.5, 4.0, 7.5, 11.0])
+    g = np.array([300.0, 1200.0, 4000.0, 800.0, 15000.0, 2500.0])
+    mu = W.M_AR * W.M_AR / (W.M_AR + W.M_AR)
+    E = 0.5 * mu * g * g / KB
+    want = 2.0 * np.arctan(kappa / (2.0 * E * b))
+    got = O.chi_batch(gas, P, b, g)
+    np.testing.assert_allclose(got, want, rtol=1e-10, atol=1e-13)
+
+
+def _hs_jager_run(n=100_000, g=1500.0, step=3):
+    """n pairs of distinct particles, all with the same relative velocity
+    g * d (d a fixed unit vector), through the oracle's Jager collide with
+    the hard-sphere potential."""
+    d = np.array([0.3, -0.5, 0.81])
+    d /= np.linalg.norm(d)
+    vi = 0.5 * g * d + np.array([120.0, -40.0, 15.0])
+    vj = -0.5 * g * d + np.array([120.0, -40.0, 15.0])
+    vx = np.empty(2 * n); vy = np.empty(2 * n); vz = np.empty(2 * n)
+    vx[0::2], vy[0::2], vz[0::2] = vi
+    vx[1::2], vy[1::2], vz[1::2] = vj
+    p = np.arange(n, dtype=np.int32)
+    pairs = dict(i=2 * p, j=2 * p + 1, cell=p // 1000, m=p % 1000, n_pairs=n)
+    gas = O.make_gas(W.M_AR, 4.17e-10, 0.81, 273.0, 1.0, 1.0, 77, model=1, b_max=1.2e-9)
+    ox, oy, oz, chi = O.collide_jager(gas, O.make_pot(W.HARD_SPHERE_AR), pairs, step, vx, vy, vz, want_chi=True)
+    vr1 = np.stack([ox[0::2] - ox[1::2], oy[0::2] - oy[1::2], oz[0::2] - oz[1::2]], 1)
+    return d, g, chi, vr1
+
+
+def test_jager_collide_impact_parameter_and_azimuth_draws():
+    """The collide draws b with b^2 uniform on [0, b_max^2] and eps uniform on
+    [0, 2 pi) (Sec. 3.4.2: b up to b_max; the azimuth of an isotropic
+    collision plane).  With hard spheres (d = 3.6 A) these fix: P(chi = 0) =
+    P(b > d) = 1 - (d/b_max)^2 = 0.91; given b < d, cos^2(chi/2) = (b/d)^2 is
+    uniform on [0, 1]; the azimuth of v_r' about the common v_r is uniform on
+    [0, 2 pi) and the angle between v_r and v_r' is |chi|."""
+    n = 100_000
+    d, g, chi, vr1 = _hs_jager_run(n)
+    zero = np.abs(chi) < 1e-9
+    p0 = 1.0 - (3.6 / 12.0) ** 2
+    assert abs(zero.mean() - p0) < 4.0 * math.sqrt(p0 * (1 - p0) / n), zero.mean()
+    c2 = np.cos(0.5 * chi[~zero]) ** 2
+    assert stats.kstest(c2, "uniform").pvalue > 1e-3
+    # |v_r'| = g and the angle between v_r and v_r' is chi
+    np.testing.assert_allclose(np.linalg.norm(vr1, axis=1), g, rtol=1e-12)
+    cosang = vr1 @ d / g
+    np.testing.assert_allclose(cosang, np.cos(chi), atol=1e-11)
+    # azimuth about d in a fixed frame (e1, e2) perpendicular to d
+    e1 = np.cross(d, [0.0, 0.0, 1.0]); e1 /= np.linalg.norm(e1)
+    e2 = np.cross(d, e1)
+    sel = np.abs(np.sin(chi)) > 1e-3
+    phi = np.mod(np.arctan2(vr1[sel] @ e2, vr1[sel] @ e1), 2 * math.pi)
+    assert stats.kstest(phi / (2 * math.pi), "uniform").pvalue > 1e-3
+
+
+def test_neural_collide_cell_temperature():
+    """Sec. 2.2: the MLP sees the cell's kinetic temperature, (3/2) k T =
+    (1/2) m <|v - u|^2>.  A cell of six particles at u + (+-a, 0, 0),
+    u + (0, +-a, 0), u + (0, 0, +-a) has <|v - u|^2> = a^2, so it is at
+    T = m a^2 / (3 k) by construction; the collide's direction must equal the
+    network's output for the features formed with that T (network and noise
+    are pinned by their own tests)."""
+    wts, mlp = _mlp()
+    bias = np.random.default_rng(3).standard_normal(len(wts["bias"])) * 0.05
+    T_known = 800.0
+    a = math.sqrt(3.0 * KB * T_known / W.M_AR)
+    u = np.array([150.0, -320.0, 40.0])
+    offs = np.array([[a, 0, 0], [-a, 0, 0], [0, a, 0], [0, -a, 0], [0, 0, a], [0, 0, -a]])
+    v = u + offs
+    vx, vy, vz = v[:, 0].copy(), v[:, 1].copy(), v[:, 2].copy()
+    cs = np.array([0, 6], np.int32)
+    mom = O.cell_moments(cs, vx, vy, vz)
+    gas = O.make_gas(W.M_AR, 4.17e-10, 0.81, 273.0, 1.0, 1.0, 21, model=1, b_max=1.2e-9)
+    for (i, j, m) in [(0, 3, 0), (4, 1, 5), (2, 5, 9)]:
+        pairs = dict(i=np.array([i], np.int32), j=np.array([j], np.int32), cell=np.array([0], np.int32),
+                     m=np.array([m], np.int32), n_pairs=1)
+        *_, ug = O.collide_neural(gas, mlp, wts["W"], bias, mom, pairs, 2, vx, vy, vz, want_u=True)
+        vr = v[i] - v[j]
+        xi = O.noise4(21, 0, m, 2)
+        x = np.concatenate([vr / W.sigma_v(), [T_known / 273.0], xi])[None, :]
+        y = O.mlp_forward(mlp, wts["W"], bias, x)[0]
+        np.testing.assert_allclose(ug[0], y / np.linalg.norm(y), rtol=0, atol=1e-12)
+
+
 # ------------------------------------------------------------------ neural operator (Sec. 2.2-2.3)
 
 def _mlp(d_in=8):
