@@ -34,7 +34,6 @@ namespace {
 constexpr int kRows = 128;
 constexpr int kEpiWarps = 16;                  // epilogue warps: 4 TMEM lane quadrants x 4 column groups
 constexpr int kThr = (kEpiWarps + 1) * 32;     // + one producer warp (copies and MMAs)
-constexpr int kCl = 1;      // CTAs per cluster sharing the weight stream (2 and 4 measured no faster)
 constexpr int kNbuf = 5;
 constexpr int kLag = 2;     // a buffer is recycled once the chunk kLag before the current one is done
 constexpr int kChunkK = 16;
@@ -155,38 +154,32 @@ __global__ void __launch_bounds__(kThr, 1) k_chi_mlp(ChiArgs a) {
     tc::tmem_relinquish();
   }
   if (t == 0) {
-    // full: this CTA's expect-tx plus the cluster's slices; empty: the MMA
-    // completions of every CTA of the cluster; acc: this CTA's commit
-    for (int b = 0; b < kNbuf; ++b) { tc::mbar_init(full + b, 1); tc::mbar_init(empty + b, kCl); }
+    // full: the producer's expect-tx and the copy's bytes; empty: the commit
+    // of the MMAs that read the buffer; acc: the commit of a layer's last MMAs
+    for (int b = 0; b < kNbuf; ++b) { tc::mbar_init(full + b, 1); tc::mbar_init(empty + b, 1); }
     tc::mbar_init(acc_bar, 1);
     tc::mbar_fence_init();
     *fail = 0;
   }
   tc::fence_before();
   __syncthreads();
-  tc::cluster_sync();   // every CTA's barriers exist before any multicast reaches them
   tc::fence_after();
   const uint32_t tmem = *(volatile uint32_t*)(smem + kTptrOff);
 
-  // Tiles in groups of kCl: the cluster's CTAs take the tiles of one group
-  // together (rank r: tile g kCl + r; past the last tile a CTA computes on
-  // zero input and stores nothing), so that all walk the same chunk sequence.
-  const uint32_t rank = tc::cluster_ctarank(), cid = tc::cluster_id_x(), ncl = tc::nclusters_x();
+  // Tiles blockIdx.x, blockIdx.x + gridDim.x, ...: every CTA streams the
+  // whole weight sequence once per tile into its own buffers.
   const int64_t n_tiles = (a.n + kRows - 1) / kRows;
-  const int64_t n_groups = (n_tiles + kCl - 1) / kCl;
-  const int my_its = cid < n_groups ? (int)((n_groups - 1 - cid) / ncl + 1) : 0;
-  const int total = my_its * kPerTile;     // chunks every CTA of the cluster consumes
-  const uint16_t cmask = (uint16_t)((1u << kCl) - 1u);
+  const int my_its = (int64_t)blockIdx.x < n_tiles ? (int)((n_tiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+  const int total = my_its * kPerTile;     // chunks this CTA consumes
   int issued = 0, consumed = 0;            // producer warp's counters
-  // producer lane 0: this CTA's slice of chunk m, multicast into buffer m % kNbuf of the cluster
+  // producer lane 0: chunk m into buffer m % kNbuf
   auto issue_copy = [&](int m) {
     int l, c;
     chunk_id(m, &l, &c);
     const int b = m % kNbuf;
-    const uint32_t slice = (uint32_t)chunk_bytes(l) / kCl;
     tc::mbar_arrive_expect_tx(full + b, (uint32_t)chunk_bytes(l));
-    tc::bulk_g2s_mc(sbase + kBufOff + (uint32_t)b * kBufBytes + rank * slice,
-                    a.packed + layer_off(l) + (uint32_t)c * chunk_bytes(l) + rank * slice, slice, full + b, cmask);
+    tc::bulk_g2s(sbase + kBufOff + (uint32_t)b * kBufBytes, a.packed + layer_off(l) + (uint32_t)c * chunk_bytes(l),
+                 (uint32_t)chunk_bytes(l), full + b);
   };
   if (w == kEpiWarps) {
     if (lane == 0)
@@ -197,7 +190,7 @@ __global__ void __launch_bounds__(kThr, 1) k_chi_mlp(ChiArgs a) {
   uint32_t acc_phase = 0;
   bool ok = true;
   for (int it = 0; it < my_its && ok; ++it) {
-    const int64_t tile = (int64_t)(cid + (uint32_t)it * ncl) * kCl + rank;
+    const int64_t tile = (int64_t)blockIdx.x + (int64_t)it * gridDim.x;
     // input row (threads 0..127): [x0 hi, x1 hi, x0 lo, x1 lo, 0 ...] as a K = 16 tile
     if (t < kRows) {
       const int64_t gr = tile * kRows + t;
@@ -239,7 +232,7 @@ __global__ void __launch_bounds__(kThr, 1) k_chi_mlp(ChiArgs a) {
             for (int h = 0; h < nh; ++h)
               tc::mma_bf16(tmem + (uint32_t)(256 * h), tc::sdesc(sbase + kActOff + 256u * (uint32_t)c, 128, sbo_a),
                            tc::sdesc(bb + (uint32_t)h * 8192u, 128, 256), idesc, c > 0);
-            tc::commit_mc(empty + b, cmask);
+            tc::commit(empty + b);
           }
           __syncwarp();
           ++consumed;
@@ -337,11 +330,7 @@ __global__ void __launch_bounds__(kThr, 1) k_chi_mlp(ChiArgs a) {
   }
   tc::fence_before();
   __syncthreads();
-  // no CTA leaves while a peer may still signal its barriers (on the normal
-  // path every CTA of the cluster gets here; after a timeout, all of them
-  // fail and skip this)
-  const bool all_ok = __syncthreads_and(ok);
-  if (all_ok) tc::cluster_sync();
+  tc::fence_after();
   if (w == 0) tc::tmem_dealloc(tmem, 512);
 }
 
@@ -359,27 +348,10 @@ static int launch_chi_mlp(Ctx* c, const ChiArgs& a, cudaStream_t s) {
   if (cudaFuncSetAttribute((const void*)k_chi_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) !=
       cudaSuccess)
     return record(c, DSMC_ERR_CUDA, "chi_mlp: shared memory attribute");
+  // one wave of persistent CTAs, one per SM (223 KB of shared memory each)
   const int64_t tiles = (a.n + kRows - 1) / kRows;
-  const int64_t groups = (tiles + kCl - 1) / kCl;
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kCl;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(kThr);
-  cfg.dynamicSmemBytes = kSmemBytes;
-  cfg.stream = s;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  // one wave of clusters (persistent CTAs, one per SM)
-  int max_clusters = 0;
-  cfg.gridDim = dim3((unsigned)(sm_count(c) / kCl * kCl));
-  if (cudaOccupancyMaxActiveClusters(&max_clusters, (const void*)k_chi_mlp, &cfg) != cudaSuccess || max_clusters < 1)
-    return record(c, DSMC_ERR_CUDA, "chi_mlp: no cluster of the kernel fits");
-  const int64_t clusters = groups < max_clusters ? groups : max_clusters;
-  cfg.gridDim = dim3((unsigned)(clusters * kCl));
-  if (cudaLaunchKernelEx(&cfg, k_chi_mlp, a) != cudaSuccess) return record(c, DSMC_ERR_CUDA, "chi_mlp: launch");
+  const int64_t grid = tiles < sm_count(c) ? tiles : sm_count(c);
+  k_chi_mlp<<<(unsigned)grid, kThr, kSmemBytes, s>>>(a);
   count_launches(c, 1);
   return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
 }

@@ -212,47 +212,6 @@ __device__ __forceinline__ void st_shared_v4(uint32_t saddr, uint32_t a, uint32_
                : "memory");
 }
 
-// thread-block cluster: this CTA's rank, the cluster's index and the number
-// of clusters along x; a barrier over all threads of the cluster
-__device__ __forceinline__ uint32_t cluster_ctarank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_id_x() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t nclusters_x() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-// The bulk copy multicast to the same shared-memory offset, and its
-// transaction count to the same mbarrier offset, in every CTA of `mask`.
-__device__ __forceinline__ void bulk_g2s_mc(uint32_t dst, const void* src, uint32_t bytes, uint64_t* mbar,
-                                            uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], "
-      "%4;" ::"r"(dst),
-      "l"(src), "r"(bytes), "r"(smem_u32(mbar)), "h"(mask)
-      : "memory");
-}
-
-// commit: arrive on the mbarrier at this offset in every CTA of `mask` once
-// the MMAs issued so far have completed
-__device__ __forceinline__ void commit_mc(uint64_t* mbar, uint16_t mask) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::
-                   "r"(smem_u32(mbar)),
-               "h"(mask)
-               : "memory");
-}
-
 // mbarrier: arrive once and declare `bytes` of asynchronous transactions that
 // must also land before the phase completes
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
@@ -260,10 +219,11 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t b
                : "memory");
 }
 
-// Untiled bulk copy global -> shared (asynchronous proxy), counted on mbar in
-// bytes.  Both addresses 16-byte aligned, bytes a multiple of 16.
+// Untiled bulk copy global -> this CTA's shared memory (asynchronous proxy),
+// counted on mbar in bytes.  Both addresses 16-byte aligned, bytes a
+// multiple of 16.
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* mbar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+  asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                "l"(src), "r"(bytes), "r"(smem_u32(mbar))
                : "memory");
 }
