@@ -127,16 +127,14 @@ __global__ void k_scatter(const int32_t* __restrict__ cell_id, int32_t n, int32_
 }
 
 constexpr int kFixWarps = 8;
-constexpr int kFixCap = 1024;  // cells up to this size sort in shared memory
+constexpr int kFixCap = 1024;  // cells up to this size sort in shared memory, one warp each
 
-// Warp per cell: order the cell's slot contents ascending (bitonic network in
-// shared memory; rank counting for larger cells).
+// Warp per cell of at most kFixCap particles: order the cell's slot contents
+// ascending (bitonic network in shared memory).  Larger cells are left to
+// k_fix_large.
 __global__ void __launch_bounds__(kFixWarps * 32)
 k_fix_gather(int32_t n_cells, const int32_t* __restrict__ cell_start,
-             const int32_t* __restrict__ slots, int32_t* __restrict__ perm,
-             const double* __restrict__ vx, const double* __restrict__ vy,
-             const double* __restrict__ vz, double* __restrict__ svx, double* __restrict__ svy,
-             double* __restrict__ svz) {
+             const int32_t* __restrict__ slots, int32_t* __restrict__ perm) {
   __shared__ int buf_all[kFixWarps][kFixCap];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int* buf = buf_all[wid];
@@ -162,13 +160,96 @@ k_fix_gather(int32_t n_cells, const int32_t* __restrict__ cell_start,
         }
       }
       for (int t = lane; t < N; t += 32) perm[a + t] = buf[t];
-    } else {
-      // rank of each slot value among the cell's values (all distinct)
-      for (int t = lane; t < N; t += 32) {
-        const int x = slots[a + t];
-        int r = 0;
-        for (int q = 0; q < N; ++q) r += slots[a + q] < x;
-        perm[a + r] = x;
+    }
+  }
+}
+
+// Block per cell of more than kFixCap particles: the cell's slot contents
+// (distinct input indices below 2^24) sorted ascending by a stable LSD radix
+// sort on 8-bit digits, three passes that alternate between the cell's slot
+// range (scratch) and its perm range: slots -> perm -> slots -> perm.  Each
+// pass counts the digits of the whole cell, then scatters it in order in
+// tiles of kLgTile values: warp w of the block owns the tile's w-th
+// segment (kLgPer values per lane, in order), the warps' digit counts become
+// per-warp starting positions, and equal digits within a warp are ranked by
+// lane from ballots.  O(N) work per cell; a cell of 2^20 particles takes
+// 3 x 256 tiles.
+constexpr int kLgWarps = 16;
+constexpr int kLgPer = 8;
+constexpr int kLgTile = kLgWarps * 32 * kLgPer;
+constexpr int kLgBits = 8;
+constexpr int kLgRadix = 1 << kLgBits;
+
+__global__ void __launch_bounds__(kLgWarps * 32)
+k_fix_large(int32_t n_cells, const int32_t* __restrict__ cell_start, int32_t* slots, int32_t* perm) {
+  __shared__ int run[kLgRadix];               // the cell's digit counts, then running positions
+  __shared__ int wh[kLgWarps][kLgRadix];      // per-warp positions inside the current tile
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int32_t k = blockIdx.x; k < n_cells; k += gridDim.x) {
+    const int32_t a = cell_start[k], N = cell_start[k + 1] - a;
+    if (N <= kFixCap) continue;
+    for (int pass = 0; pass < 3; ++pass) {
+      const int32_t* src = (pass & 1) ? perm + a : slots + a;
+      int32_t* dst = (pass & 1) ? slots + a : perm + a;
+      const int shift = pass * kLgBits;
+      for (int t = threadIdx.x; t < kLgRadix; t += blockDim.x) run[t] = 0;
+      __syncthreads();
+      for (int32_t t = threadIdx.x; t < N; t += blockDim.x) atomicAdd(&run[(src[t] >> shift) & (kLgRadix - 1)], 1);
+      __syncthreads();
+      if (w == 0) {   // exclusive scan of the 256 counts, 8 per lane
+        int c[kLgRadix / 32], sum = 0;
+#pragma unroll
+        for (int q = 0; q < kLgRadix / 32; ++q) { c[q] = run[lane * (kLgRadix / 32) + q]; sum += c[q]; }
+        int x = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x += y;
+        }
+        int acc = x - sum;
+#pragma unroll
+        for (int q = 0; q < kLgRadix / 32; ++q) { run[lane * (kLgRadix / 32) + q] = acc; acc += c[q]; }
+      }
+      __syncthreads();
+      for (int32_t t0 = 0; t0 < N; t0 += kLgTile) {
+        const int32_t s0 = t0 + w * (32 * kLgPer);
+        int32_t val[kLgPer];
+#pragma unroll
+        for (int j = 0; j < kLgPer; ++j) {
+          const int32_t i = s0 + j * 32 + lane;
+          val[j] = i < N ? src[i] : -1;
+        }
+        for (int t = threadIdx.x; t < kLgWarps * kLgRadix; t += blockDim.x) wh[t / kLgRadix][t % kLgRadix] = 0;
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kLgPer; ++j)
+          if (val[j] >= 0) atomicAdd(&wh[w][(val[j] >> shift) & (kLgRadix - 1)], 1);
+        __syncthreads();
+        for (int d = threadIdx.x; d < kLgRadix; d += blockDim.x) {
+          int acc = run[d];
+          for (int q = 0; q < kLgWarps; ++q) { const int c = wh[q][d]; wh[q][d] = acc; acc += c; }
+          run[d] = acc;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kLgPer; ++j) {
+          const bool has = val[j] >= 0;
+          const int d = has ? (val[j] >> shift) & (kLgRadix - 1) : -1;
+          // lanes with the same digit (lanes without a value form their own set)
+          unsigned same = __ballot_sync(0xffffffffu, has);
+          if (!has) same = ~same;
+#pragma unroll
+          for (int bit = 0; bit < kLgBits; ++bit) {
+            const unsigned m = __ballot_sync(0xffffffffu, (d >> bit) & 1);
+            same &= ((d >> bit) & 1) ? m : ~m;
+          }
+          if (has) dst[wh[w][d] + __popc(same & lt)] = val[j];
+          __syncwarp();
+          if (has && (same & lt) == 0) wh[w][d] += __popc(same);
+          __syncwarp();
+        }
+        __syncthreads();
       }
     }
   }
@@ -569,6 +650,7 @@ extern "C" int dsmc_sort_cells_static(int32_t n, int32_t n_cells, const int32_t*
   int32_t* scan = (int32_t*)(d->scratch + kStaticCountsBytes + kStaticSlotsBytes);
   int* st = status ? status : (int*)(d->scratch + kStaticCountsBytes + kStaticSlotsBytes + kStaticScanSlot);
   static_assert(kStaticScanBytes <= kStaticScanSlot, "scan block sums must fit their slot");
+  static_assert(DSMC_STATIC_SORT_MAX_N <= (1 << (3 * kLgBits)), "three 8-bit passes order every slot value");
   // the counters must start at zero on every call (the array keeps the last call's contents)
   if (cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)n_cells, s) != cudaSuccess) return DSMC_ERR_CUDA;
   if (n > 0) k_hist<<<grid_for(n, 256, d->sms * 16), 256, 0, s>>>(cell_id, n, n_cells, counts, st);
@@ -576,8 +658,9 @@ extern "C" int dsmc_sort_cells_static(int32_t n, int32_t n_cells, const int32_t*
   if (n > 0) {
     if (cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)n_cells, s) != cudaSuccess) return DSMC_ERR_CUDA;
     k_scatter<<<grid_for(n, 256, d->sms * 16), 256, 0, s>>>(cell_id, n, n_cells, cell_start, counts, slots);
-    k_fix_gather<<<grid_for(n_cells, kFixWarps, d->sms * 4), kFixWarps * 32, 0, s>>>(
-        n_cells, cell_start, slots, perm, vx, vy, vz, svx, svy, svz);
+    k_fix_gather<<<grid_for(n_cells, kFixWarps, d->sms * 4), kFixWarps * 32, 0, s>>>(n_cells, cell_start, slots,
+                                                                                      perm);
+    k_fix_large<<<grid_for(n_cells, 1, d->sms), kLgWarps * 32, 0, s>>>(n_cells, cell_start, slots, perm);
     k_gather<<<grid_for(n, 256, d->sms * 16), 256, 0, s>>>(n, cell_start, n_cells, perm, vx, vy, vz, svx,
                                                            svy, svz);
   }

@@ -670,7 +670,9 @@ def sort_cells_static(cell_id, vx, vy, vz, n_cells, out=None, status=None, strea
     """Allocation-free cell sort (dsmc_sort_cells_static): no context, no
     workspace; at most STATIC_SORT_MAX_N particles and STATIC_SORT_MAX_CELLS
     cells.  Output tensors may be passed in ``out`` so that nothing is
-    allocated around the call either."""
+    allocated around the call either.  Every tensor must live on the same
+    GPU; the call runs with that GPU current (the library looks up its
+    scratch array on the current device)."""
     L = load()
     n = cell_id.numel()
     dev = cell_id.device
@@ -680,11 +682,22 @@ def sort_cells_static(cell_id, vx, vy, vz, n_cells, out=None, status=None, strea
                    svx=torch.empty(n, dtype=torch.float64, device=dev),
                    svy=torch.empty(n, dtype=torch.float64, device=dev),
                    svz=torch.empty(n, dtype=torch.float64, device=dev))
+    need = dict(perm=n, cell_start=n_cells + 1, svx=n, svy=n, svz=n)
+    for k, m in need.items():
+        if out[k].numel() < m:
+            raise ValueError(f"sort_cells_static: out['{k}'] holds {out[k].numel()} entries, needs {m}")
+    for name, t in [("vx", vx), ("vy", vy), ("vz", vz), ("status", status)] + list(out.items()):
+        if t is not None and t.device != dev:
+            raise ValueError(f"sort_cells_static: {name} is on {t.device}, cell_id on {dev}")
+    if min(vx.numel(), vy.numel(), vz.numel()) < n:
+        raise ValueError("sort_cells_static: velocity arrays shorter than cell_id")
     f64 = torch.float64
-    rc = L.dsmc_sort_cells_static(n, n_cells, _ptr(cell_id, torch.int32), _ptr(vx, f64), _ptr(vy, f64),
-                                  _ptr(vz, f64), _ptr(out["perm"]), _ptr(out["cell_start"]),
-                                  _ptr(out["svx"]), _ptr(out["svy"]), _ptr(out["svz"]),
-                                  _ptr(status, torch.int32), _stream(stream))
+    with torch.cuda.device(dev):
+        rc = L.dsmc_sort_cells_static(n, n_cells, _ptr(cell_id, torch.int32), _ptr(vx, f64), _ptr(vy, f64),
+                                      _ptr(vz, f64), _ptr(out["perm"], torch.int32),
+                                      _ptr(out["cell_start"], torch.int32), _ptr(out["svx"], f64),
+                                      _ptr(out["svy"], f64), _ptr(out["svz"], f64),
+                                      _ptr(status, torch.int32), _stream(stream))
     if rc != 0:
         raise DsmcError(rc, "dsmc_sort_cells_static")
     return out
