@@ -31,13 +31,16 @@ KB = 1.380649e-23
 TAG_NTC, TAG_CAND, TAG_ISO, TAG_JAGER, TAG_NOISE, TAG_HARVEST = 1, 2, 3, 4, 5, 6
 
 
-def build(force: bool = False, openmp: bool = False) -> str:
-    """Compile the C oracle with gcc (no FMA contraction)."""
+def build(force: bool = False, openmp: bool = True) -> str:
+    """Compile the C oracle with gcc (no FMA contraction), with OpenMP where
+    the compiler has it (the results do not depend on the thread count)."""
     with _lock:
         if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-            cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-                   "-o", _LIB + ".tmp", _SRC, "-lm"]
-            subprocess.run(cmd, check=True)
+            base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                    "-o", _LIB + ".tmp", _SRC, "-lm"]
+            r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True) if openmp else None
+            if r is None or r.returncode != 0:
+                subprocess.run(base, check=True)
             os.replace(_LIB + ".tmp", _LIB)
     return _LIB
 
@@ -91,6 +94,10 @@ def lib():
             "or_chi_batch": (None, [P(Gas), P(Pot), i64, vp, vp, vp]),
             "or_deflect": (None, [vp, d, d, vp]),
             "or_collide_jager": (None, [P(Gas), P(Pot), i64, vp, vp, vp, vp, u64, vp, vp, vp, vp]),
+            "or_collide_given_chi": (None, [P(Gas), i64, vp, vp, vp, vp, u64, vp, vp, vp, vp, vp, vp]),
+            "or_chi_many": (None, [P(Pot), i64, vp, vp, vp]),
+            "or_num_threads": (C.c_int, []),
+            "or_set_num_threads": (None, [C.c_int]),
             "or_bf16_round": (d, [d]),
             "or_mlp_forward": (None, [P(Mlp), vp, vp, i64, vp, C.c_int, vp]),
             "or_noise4": (None, [u64, i32, i32, u64, vp]),
@@ -290,6 +297,42 @@ def collide_jager(gas: Gas, pot: Pot, pairs: dict, step, vx, vy, vz, want_chi=Fa
     if want_chi:
         return vx, vy, vz, chi_out[:pairs["n_pairs"]]
     return vx, vy, vz
+
+
+def collide_given_chi(gas: Gas, pairs: dict, step, chi, vx, vy, vz, want_vr=False):
+    """The rotation and centre-of-mass update of the Jager collide with each
+    pair's chi given (pair order, e.g. a GPU kernel's own chi) and the
+    azimuth from tag 4.  want_vr: also each pair's pre-collision v_r [n x 3]
+    and impact parameter b (Angstrom, tag 4)."""
+    vx, vy, vz = _f64(vx).copy(), _f64(vy).copy(), _f64(vz).copy()
+    n = pairs["n_pairs"]
+    chi = _f64(chi)
+    assert len(chi) >= n
+    vr = np.zeros((max(n, 1), 3))
+    b = np.zeros(max(n, 1))
+    lib().or_collide_given_chi(C.byref(gas), n, _p(_i32(pairs["i"])), _p(_i32(pairs["j"])),
+                               _p(_i32(pairs["cell"])), _p(_i32(pairs["m"])), step, _p(chi), _p(vx), _p(vy),
+                               _p(vz), _p(vr), _p(b))
+    if want_vr:
+        return vx, vy, vz, vr[:n], b[:n]
+    return vx, vy, vz
+
+
+def chi_many(pot: Pot, b, E) -> np.ndarray:
+    """chi at independent points (b in Angstrom, E = E_r/k_B in K)."""
+    b, E = _f64(b), _f64(E)
+    out = np.zeros_like(b)
+    lib().or_chi_many(C.byref(pot), len(b), _p(b), _p(E), _p(out))
+    return out
+
+
+def num_threads() -> int:
+    """Threads of the oracle's parallel loops (1 if built without OpenMP)."""
+    return int(lib().or_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    lib().or_set_num_threads(int(n))
 
 
 def chi_table(pot: Pot, bmax_A: float, nb: int, nE: int, lnE_min: float, lnE_max: float) -> np.ndarray:

@@ -8,10 +8,14 @@
  * product (the CUDA library under paper_2602_21244_gb300/) never calls it and
  * shares no code, header, table or constant generator with it.
  *
- * Everything is double precision, sequential in the order the method states,
- * with no blocking or fusion.  Compile with -ffp-contract=off so that no
- * a*b+c is fused into an FMA: the integer decisions of pair selection must be
- * the same on every host.
+ * Everything is double precision, in the order the method states, with no
+ * blocking or fusion.  Compile with -ffp-contract=off so that no a*b+c is
+ * fused into an FMA: the integer decisions of pair selection must be the
+ * same on every host.  Built with OpenMP when the compiler has it: loops
+ * over independent cells (Sec. 2.6: cells are processed in parallel),
+ * independent pairs of the chi batch and independent table nodes run on
+ * several threads; each cell's pairs still act one after another in
+ * candidate order, so every result is the sequential one bit for bit.
  *
  * Citations are to the paper's sections and equations:
  *   Sec. 2.1   DSMC collision step, NTC rate nu ~ n sigma v_r
@@ -61,9 +65,55 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_KB 1.380649e-23 /* Boltzmann constant, J/K (exact SI value) */
 #define OR_PI 3.14159265358979323846
+
+/* threads the parallel loops use (1 without OpenMP), and a way to set them */
+int or_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+void or_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
+/* Pairs of different cells share no particle.  A pair list in cell-major
+ * order (pcell non-decreasing) is therefore processed cell by cell in
+ * parallel, each cell's pairs one after another in their given order, which
+ * is the sequential result exactly; any other order runs sequentially. */
+typedef void (*or_pair_fn)(const void* ctx, int64_t p);
+static void for_each_pair(int64_t n_pairs, const int32_t* pcell, or_pair_fn f, const void* ctx) {
+  int cell_major = pcell != NULL;
+  for (int64_t p = 1; cell_major && p < n_pairs; ++p)
+    if (pcell[p] < pcell[p - 1]) cell_major = 0;
+  if (!cell_major || n_pairs < 2) {
+    for (int64_t p = 0; p < n_pairs; ++p) f(ctx, p);
+    return;
+  }
+  int64_t nseg = 1;
+  for (int64_t p = 1; p < n_pairs; ++p) nseg += pcell[p] != pcell[p - 1];
+  int64_t* st = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nseg + 1));
+  int64_t q = 0;
+  st[q++] = 0;
+  for (int64_t p = 1; p < n_pairs; ++p)
+    if (pcell[p] != pcell[p - 1]) st[q++] = p;
+  st[nseg] = n_pairs;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t g = 0; g < nseg; ++g)
+    for (int64_t p = st[g]; p < st[g + 1]; ++p) f(ctx, p);
+  free(st);
+}
 
 /* ------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, Sec. 3.3)         */
@@ -177,6 +227,7 @@ int or_sort_cells(int32_t n, int32_t n_cells, const int32_t* cell_id,
 /* ------------------------------------------------------------------ */
 void or_cell_moments(int32_t n_cells, const int32_t* cs, const double* vx,
                      const double* vy, const double* vz, double* mom) {
+#pragma omp parallel for schedule(dynamic, 256)
   for (int32_t k = 0; k < n_cells; ++k) {
     int32_t a = cs[k], b = cs[k + 1];
     double sx = 0, sy = 0, sz = 0;
@@ -198,56 +249,96 @@ void or_cell_moments(int32_t n_cells, const int32_t* cs, const double* vx,
 /* Sec. 2.2: NTC selection, readings R2-R4                             */
 /* Output pairs are cell-major in candidate order.                    */
 /* ------------------------------------------------------------------ */
+/* One cell k: its M candidates in order, the accepted ones with their
+ * rounds.  *acc_out receives {i, j, m, round} per accepted pair (candidate
+ * order, cell-local i and j), the return value their number; *best the
+ * cell's raised (sigma g)_max, *rounds its number of rounds, *n_cand = M.
+ * Returns -1 if M does not fit an int32. */
+static int64_t select_cell(const or_gas_t* gs, int32_t k, const int32_t* cs, const double* vx,
+                           const double* vy, const double* vz, const double* sgmax, uint64_t step,
+                           int32_t** acc_out, double* best, int32_t* rounds, int64_t* n_cand) {
+  int32_t a = cs[k], N = cs[k + 1] - cs[k];
+  *acc_out = NULL; *best = sgmax[k]; *rounds = 0; *n_cand = 0;
+  if (N < 2) return 0;
+  uint32_t w[4];
+  draw(gs->seed, 0, (uint32_t)k, step, OR_TAG_NTC, 0, w);
+  double mt = 0.5 * (double)N * (double)(N - 1);
+  mt = mt * gs->fn_over_vc;
+  mt = mt * sgmax[k];
+  mt = mt * gs->dt;
+  double mf = floor(mt + or_u53(w[0], w[1]));
+  if (!(mf < 2147483647.0)) return -1;
+  int32_t M = (int32_t)mf;
+  *n_cand = M;
+  if (M == 0) return 0;
+  int32_t* last = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+  int32_t* acc = (int32_t*)malloc(sizeof(int32_t) * 4 * (size_t)M);
+  for (int32_t q = 0; q < N; ++q) last[q] = -1;
+  int64_t na = 0;
+  int32_t rmax = 0;
+  for (int32_t m = 0; m < M; ++m) {
+    draw(gs->seed, (uint32_t)m, (uint32_t)k, step, OR_TAG_CAND, 0, w);
+    uint32_t i = mulhi_n(w[0], (uint32_t)N);
+    uint32_t j = mulhi_n(w[1], (uint32_t)(N - 1));
+    if (j >= i) j += 1;
+    double dx = vx[a + i] - vx[a + j], dy = vy[a + i] - vy[a + j], dz = vz[a + i] - vz[a + j];
+    double g = sqrt((dx * dx + dy * dy) + dz * dz);
+    double sg = or_sigma(gs, g) * g;
+    if (sg > *best) *best = sg;
+    double U = or_u53(w[2], w[3]);
+    if (U < sg / sgmax[k]) {
+      int32_t r = 1 + (last[i] > last[j] ? last[i] : last[j]);
+      last[i] = r; last[j] = r;
+      if (r + 1 > rmax) rmax = r + 1;
+      acc[4 * na + 0] = (int32_t)i; acc[4 * na + 1] = (int32_t)j;
+      acc[4 * na + 2] = m; acc[4 * na + 3] = r;
+      na++;
+    }
+  }
+  free(last);
+  *acc_out = acc;
+  *rounds = rmax;
+  return na;
+}
+
+/* The cells are independent (Sec. 2.6): each is selected on its own, then
+ * the accepted pairs are concatenated in cell order and (sigma g)_max is
+ * raised, so the output does not depend on the number of threads. */
 int or_select_pairs(const or_gas_t* gs, int32_t n_cells, const int32_t* cs,
                     const double* vx, const double* vy, const double* vz,
                     double* sgmax, uint64_t step, int64_t capacity,
                     int32_t* pi, int32_t* pj, int32_t* pcell, int32_t* pm,
                     int32_t* pround, int64_t* n_pairs, int64_t* n_cand,
                     int32_t* n_rounds) {
+  size_t nk = (size_t)(n_cells > 0 ? n_cells : 1);
+  int32_t** acc = (int32_t**)calloc(nk, sizeof(int32_t*));
+  int64_t* cnt = (int64_t*)calloc(nk, sizeof(int64_t));
+  int64_t* cand = (int64_t*)calloc(nk, sizeof(int64_t));
+  int32_t* rk = (int32_t*)calloc(nk, sizeof(int32_t));
+  double* best = (double*)malloc(sizeof(double) * nk);
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(| : bad)
+  for (int32_t k = 0; k < n_cells; ++k) {
+    cnt[k] = select_cell(gs, k, cs, vx, vy, vz, sgmax, step, &acc[k], &best[k], &rk[k], &cand[k]);
+    if (cnt[k] < 0) bad = 1;
+  }
   int64_t np = 0, nc = 0;
   int32_t rmax = 0;
-  int32_t* last = NULL;
-  int32_t last_cap = 0;
-  for (int32_t k = 0; k < n_cells; ++k) {
-    int32_t a = cs[k], N = cs[k + 1] - cs[k];
-    if (N < 2) continue;
-    uint32_t w[4];
-    draw(gs->seed, 0, (uint32_t)k, step, OR_TAG_NTC, 0, w);
-    double mt = 0.5 * (double)N * (double)(N - 1);
-    mt = mt * gs->fn_over_vc;
-    mt = mt * sgmax[k];
-    mt = mt * gs->dt;
-    double mf = floor(mt + or_u53(w[0], w[1]));
-    if (!(mf < 2147483647.0)) return -3; /* DSMC_ERR_CAPACITY */
-    int32_t M = (int32_t)mf;
-    nc += M;
-    if (N > last_cap) { free(last); last_cap = N; last = (int32_t*)malloc(sizeof(int32_t) * (size_t)N); }
-    for (int32_t q = 0; q < N; ++q) last[q] = -1;
-    double best = sgmax[k];
-    for (int32_t m = 0; m < M; ++m) {
-      draw(gs->seed, (uint32_t)m, (uint32_t)k, step, OR_TAG_CAND, 0, w);
-      uint32_t i = mulhi_n(w[0], (uint32_t)N);
-      uint32_t j = mulhi_n(w[1], (uint32_t)(N - 1));
-      if (j >= i) j += 1;
-      double dx = vx[a + i] - vx[a + j], dy = vy[a + i] - vy[a + j], dz = vz[a + i] - vz[a + j];
-      double g = sqrt((dx * dx + dy * dy) + dz * dz);
-      double sg = or_sigma(gs, g) * g;
-      if (sg > best) best = sg;
-      double U = or_u53(w[2], w[3]);
-      if (U < sg / sgmax[k]) {
-        int32_t r = 1 + (last[i] > last[j] ? last[i] : last[j]);
-        last[i] = r; last[j] = r;
-        if (r + 1 > rmax) rmax = r + 1;
-        if (np < capacity) {
-          pi[np] = a + (int32_t)i; pj[np] = a + (int32_t)j;
-          pcell[np] = k; pm[np] = m; pround[np] = r;
-        }
-        np++;
+  for (int32_t k = 0; k < n_cells && !bad; ++k) {
+    for (int64_t q = 0; q < cnt[k]; ++q) {
+      if (np < capacity) {
+        pi[np] = cs[k] + acc[k][4 * q]; pj[np] = cs[k] + acc[k][4 * q + 1];
+        pcell[np] = k; pm[np] = acc[k][4 * q + 2]; pround[np] = acc[k][4 * q + 3];
       }
+      np++;
     }
-    sgmax[k] = best;
+    nc += cand[k];
+    if (rk[k] > rmax) rmax = rk[k];
+    sgmax[k] = best[k];
   }
-  free(last);
+  for (int32_t k = 0; k < n_cells; ++k) free(acc[k]);
+  free(acc); free(cnt); free(cand); free(rk); free(best);
+  if (bad) return -3; /* DSMC_ERR_CAPACITY */
   *n_pairs = np; *n_cand = nc; *n_rounds = rmax;
   return np > capacity ? -3 : 0;
 }
@@ -275,18 +366,30 @@ static void iso_dir(uint64_t seed, int32_t cell, int32_t m, uint64_t step, doubl
 /* VHS isotropic scatter (the phenomenological kernel of Sec. 2.1),
  * pairs applied one after another in the given (cell-major, candidate)
  * order, reading the current velocities. */
+typedef struct {
+  const or_gas_t* gs;
+  const int32_t *pi, *pj, *pcell, *pm;
+  uint64_t step;
+  double *vx, *vy, *vz;
+} pairs_ctx;
+
+static void vhs_pair(const void* c_, int64_t p) {
+  const pairs_ctx* c = (const pairs_ctx*)c_;
+  double *vx = c->vx, *vy = c->vy, *vz = c->vz;
+  int32_t i = c->pi[p], j = c->pj[p];
+  double dx = vx[i] - vx[j], dy = vy[i] - vy[j], dz = vz[i] - vz[j];
+  double g = sqrt((dx * dx + dy * dy) + dz * dz);
+  double e[3];
+  iso_dir(c->gs->seed, c->pcell[p], c->pm[p], c->step, e);
+  double vrp[3] = {g * e[0], g * e[1], g * e[2]};
+  pair_update(vx, vy, vz, i, j, vrp);
+}
+
 void or_collide_vhs(const or_gas_t* gs, int64_t n_pairs, const int32_t* pi,
                     const int32_t* pj, const int32_t* pcell, const int32_t* pm,
                     uint64_t step, double* vx, double* vy, double* vz) {
-  for (int64_t p = 0; p < n_pairs; ++p) {
-    int32_t i = pi[p], j = pj[p];
-    double dx = vx[i] - vx[j], dy = vy[i] - vy[j], dz = vz[i] - vz[j];
-    double g = sqrt((dx * dx + dy * dy) + dz * dz);
-    double e[3];
-    iso_dir(gs->seed, pcell[p], pm[p], step, e);
-    double vrp[3] = {g * e[0], g * e[1], g * e[2]};
-    pair_update(vx, vy, vz, i, j, vrp);
-  }
+  pairs_ctx c = {gs, pi, pj, pcell, pm, step, vx, vy, vz};
+  for_each_pair(n_pairs, pcell, vhs_pair, &c);
 }
 
 /* ------------------------------------------------------------------ */
@@ -294,6 +397,7 @@ void or_collide_vhs(const or_gas_t* gs, int64_t n_pairs, const int32_t* pi,
 /* ------------------------------------------------------------------ */
 void or_moment_match(int32_t n_cells, const int32_t* cs, const double* mom_pre,
                      double* vx, double* vy, double* vz) {
+#pragma omp parallel for schedule(dynamic, 256)
   for (int32_t k = 0; k < n_cells; ++k) {
     int32_t a = cs[k], b = cs[k + 1];
     if (b <= a) continue;
@@ -402,8 +506,8 @@ static double pot_dV_between(const or_pot_t* P, double r0, double dr) {
   if (P->kind == 0 && r0 < rc && r0 + dr > rc) /* split at the core boundary */
     return pot_dV_between(P, r0, rc - r0) + pot_dV_between(P, rc, r0 + dr - rc);
   if (dr > 0.05 * r0) return or_pot_V(P, r0 + dr) - or_pot_V(P, r0);
-  static double gx[12], gw[12];
-  static int ready = 0;
+  static _Thread_local double gx[12], gw[12];
+  static _Thread_local int ready = 0;
   if (!ready) { gauss_legendre01(12, gx, gw); ready = 1; }
   double s = 0.0;
   for (int q = 0; q < 12; ++q) s += gw[q] * or_pot_dV(P, r0 + gx[q] * dr);
@@ -522,9 +626,16 @@ static double e_kelvin(const or_gas_t* gs, double g) {
   return 0.25 * gs->mass * g * g / OR_KB;
 }
 
+/* chi(b[q], E[q]) for n independent (b, E) points, b in Angstrom, E = E_r/k_B in K */
+void or_chi_many(const or_pot_t* P, int64_t n, const double* b, const double* E, double* chi) {
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t q = 0; q < n; ++q) chi[q] = or_chi(P, b[q], E[q]);
+}
+
 /* C1 batch: b in Angstrom, g in m/s; chi for each pair */
 void or_chi_batch(const or_gas_t* gs, const or_pot_t* P, int64_t n, const double* b,
                   const double* g, double* chi) {
+#pragma omp parallel for schedule(dynamic, 64)
   for (int64_t q = 0; q < n; ++q) chi[q] = or_chi(P, b[q], e_kelvin(gs, g[q]));
 }
 
@@ -553,25 +664,74 @@ void or_deflect(const double vr[3], double chi, double eps, double out[3]) {
 /* Jager-potential collision: b = b_max sqrt(U1) (b^2 uniform on
  * [0, b_max^2]), eps = 2 pi U2 from tag 4; chi from the scattering
  * integral; pairs in order.  chi_out (optional) receives each chi. */
+typedef struct {
+  pairs_ctx c;
+  const or_pot_t* P;
+  double* chi_out;
+} jager_ctx;
+
+static void jager_pair(const void* c_, int64_t p) {
+  const jager_ctx* J = (const jager_ctx*)c_;
+  const pairs_ctx* c = &J->c;
+  const or_gas_t* gs = c->gs;
+  double *vx = c->vx, *vy = c->vy, *vz = c->vz;
+  int32_t i = c->pi[p], j = c->pj[p];
+  double vr[3] = {vx[i] - vx[j], vy[i] - vy[j], vz[i] - vz[j]};
+  double g = sqrt((vr[0] * vr[0] + vr[1] * vr[1]) + vr[2] * vr[2]);
+  uint32_t w[4];
+  draw(gs->seed, (uint32_t)c->pm[p], (uint32_t)c->pcell[p], c->step, OR_TAG_JAGER, 0, w);
+  double b = gs->b_max * 1e10 * sqrt(or_u53(w[0], w[1]));
+  double eps = 2.0 * OR_PI * or_u53(w[2], w[3]);
+  double chi = g > 0.0 ? or_chi(J->P, b, e_kelvin(gs, g)) : 0.0;
+  if (J->chi_out) J->chi_out[p] = chi;
+  double vrp[3];
+  if (g > 0.0) or_deflect(vr, chi, eps, vrp); else { vrp[0] = vrp[1] = vrp[2] = 0.0; }
+  pair_update(vx, vy, vz, i, j, vrp);
+}
+
 void or_collide_jager(const or_gas_t* gs, const or_pot_t* P, int64_t n_pairs,
                       const int32_t* pi, const int32_t* pj, const int32_t* pcell,
                       const int32_t* pm, uint64_t step, double* vx, double* vy,
                       double* vz, double* chi_out) {
-  double bmax_A = gs->b_max * 1e10;
-  for (int64_t p = 0; p < n_pairs; ++p) {
-    int32_t i = pi[p], j = pj[p];
-    double vr[3] = {vx[i] - vx[j], vy[i] - vy[j], vz[i] - vz[j]};
-    double g = sqrt((vr[0] * vr[0] + vr[1] * vr[1]) + vr[2] * vr[2]);
-    uint32_t w[4];
-    draw(gs->seed, (uint32_t)pm[p], (uint32_t)pcell[p], step, OR_TAG_JAGER, 0, w);
-    double b = bmax_A * sqrt(or_u53(w[0], w[1]));
-    double eps = 2.0 * OR_PI * or_u53(w[2], w[3]);
-    double chi = g > 0.0 ? or_chi(P, b, e_kelvin(gs, g)) : 0.0;
-    if (chi_out) chi_out[p] = chi;
-    double vrp[3];
-    if (g > 0.0) or_deflect(vr, chi, eps, vrp); else { vrp[0] = vrp[1] = vrp[2] = 0.0; }
-    pair_update(vx, vy, vz, i, j, vrp);
-  }
+  jager_ctx J = {{gs, pi, pj, pcell, pm, step, vx, vy, vz}, P, chi_out};
+  for_each_pair(n_pairs, pcell, jager_pair, &J);
+}
+
+/* The rotation and centre-of-mass update of or_collide_jager with each
+ * pair's chi given (chi_in, pair order) instead of integrated, the azimuth
+ * eps = 2 pi U2 from tag 4 as there: the deflection a collide kernel must
+ * produce from its own chi.  vr_pre (optional, n_pairs x 3) receives each
+ * pair's relative velocity before its collision, b_out (optional) its
+ * impact parameter b = b_max sqrt(U1) (tag 4) in Angstrom. */
+typedef struct {
+  pairs_ctx c;
+  const double* chi_in;
+  double* vr_pre;
+  double* b_out;
+} given_ctx;
+
+static void given_chi_pair(const void* c_, int64_t p) {
+  const given_ctx* G = (const given_ctx*)c_;
+  const pairs_ctx* c = &G->c;
+  double *vx = c->vx, *vy = c->vy, *vz = c->vz;
+  int32_t i = c->pi[p], j = c->pj[p];
+  double vr[3] = {vx[i] - vx[j], vy[i] - vy[j], vz[i] - vz[j]};
+  if (G->vr_pre) { G->vr_pre[3 * p] = vr[0]; G->vr_pre[3 * p + 1] = vr[1]; G->vr_pre[3 * p + 2] = vr[2]; }
+  double g = sqrt((vr[0] * vr[0] + vr[1] * vr[1]) + vr[2] * vr[2]);
+  uint32_t w[4];
+  draw(c->gs->seed, (uint32_t)c->pm[p], (uint32_t)c->pcell[p], c->step, OR_TAG_JAGER, 0, w);
+  double eps = 2.0 * OR_PI * or_u53(w[2], w[3]);
+  if (G->b_out) G->b_out[p] = c->gs->b_max * 1e10 * sqrt(or_u53(w[0], w[1]));
+  double vrp[3];
+  if (g > 0.0) or_deflect(vr, G->chi_in[p], eps, vrp); else { vrp[0] = vrp[1] = vrp[2] = 0.0; }
+  pair_update(vx, vy, vz, i, j, vrp);
+}
+
+void or_collide_given_chi(const or_gas_t* gs, int64_t n_pairs, const int32_t* pi, const int32_t* pj,
+                          const int32_t* pcell, const int32_t* pm, uint64_t step, const double* chi_in,
+                          double* vx, double* vy, double* vz, double* vr_pre, double* b_out) {
+  given_ctx G = {{gs, pi, pj, pcell, pm, step, vx, vy, vz}, chi_in, vr_pre, b_out};
+  for_each_pair(n_pairs, pcell, given_chi_pair, &G);
 }
 
 /* ------------------------------------------------------------------ */
@@ -583,6 +743,7 @@ void or_collide_jager(const or_gas_t* gs, const or_pot_t* P, int64_t n_pairs,
  * exp(lnE_min + j (lnE_max - lnE_min)/(nE-1))) (reading R7). */
 void or_chi_table(const or_pot_t* P, double bmax_A, int32_t nb, int32_t nE, double lnE_min,
                   double lnE_max, double* T) {
+#pragma omp parallel for schedule(dynamic, 1)
   for (int32_t j = 0; j < nE; ++j) {
     const double E = exp(lnE_min + j * (lnE_max - lnE_min) / (nE - 1));
     for (int32_t i = 0; i < nb; ++i) T[(int64_t)j * nb + i] = or_chi(P, bmax_A * i / (nb - 1), E);
@@ -611,24 +772,39 @@ double or_chi_lookup(const float* T, int32_t nb, int32_t nE, double lnE_min, dou
 /* Pair update with chi from the table: b~ = sqrt(U1), eps = 2 pi U2 (tag 4,
  * as the Jager path), E~ = ln(m g^2/(4 k_B)); rotation and centre-of-mass
  * update as or_collide_jager; pairs in order. */
+typedef struct {
+  pairs_ctx c;
+  const float* T;
+  int32_t nb, nE;
+  double lnE_min, lnE_max;
+  double* chi_out;
+} table_ctx;
+
+static void table_pair(const void* c_, int64_t p) {
+  const table_ctx* L = (const table_ctx*)c_;
+  const pairs_ctx* c = &L->c;
+  double *vx = c->vx, *vy = c->vy, *vz = c->vz;
+  int32_t i = c->pi[p], j = c->pj[p];
+  double vr[3] = {vx[i] - vx[j], vy[i] - vy[j], vz[i] - vz[j]};
+  double g = sqrt((vr[0] * vr[0] + vr[1] * vr[1]) + vr[2] * vr[2]);
+  uint32_t w[4];
+  draw(c->gs->seed, (uint32_t)c->pm[p], (uint32_t)c->pcell[p], c->step, OR_TAG_JAGER, 0, w);
+  double bt = sqrt(or_u53(w[0], w[1]));
+  double eps = 2.0 * OR_PI * or_u53(w[2], w[3]);
+  double chi = g > 0.0 ? or_chi_lookup(L->T, L->nb, L->nE, L->lnE_min, L->lnE_max, bt, log(e_kelvin(c->gs, g)))
+                       : 0.0;
+  if (L->chi_out) L->chi_out[p] = chi;
+  double vrp[3];
+  if (g > 0.0) or_deflect(vr, chi, eps, vrp); else { vrp[0] = vrp[1] = vrp[2] = 0.0; }
+  pair_update(vx, vy, vz, i, j, vrp);
+}
+
 void or_collide_table(const or_gas_t* gs, const float* T, int32_t nb, int32_t nE, double lnE_min,
                       double lnE_max, int64_t n_pairs, const int32_t* pi, const int32_t* pj,
                       const int32_t* pcell, const int32_t* pm, uint64_t step, double* vx, double* vy,
                       double* vz, double* chi_out) {
-  for (int64_t p = 0; p < n_pairs; ++p) {
-    int32_t i = pi[p], j = pj[p];
-    double vr[3] = {vx[i] - vx[j], vy[i] - vy[j], vz[i] - vz[j]};
-    double g = sqrt((vr[0] * vr[0] + vr[1] * vr[1]) + vr[2] * vr[2]);
-    uint32_t w[4];
-    draw(gs->seed, (uint32_t)pm[p], (uint32_t)pcell[p], step, OR_TAG_JAGER, 0, w);
-    double bt = sqrt(or_u53(w[0], w[1]));
-    double eps = 2.0 * OR_PI * or_u53(w[2], w[3]);
-    double chi = g > 0.0 ? or_chi_lookup(T, nb, nE, lnE_min, lnE_max, bt, log(e_kelvin(gs, g))) : 0.0;
-    if (chi_out) chi_out[p] = chi;
-    double vrp[3];
-    if (g > 0.0) or_deflect(vr, chi, eps, vrp); else { vrp[0] = vrp[1] = vrp[2] = 0.0; }
-    pair_update(vx, vy, vz, i, j, vrp);
-  }
+  table_ctx L = {{gs, pi, pj, pcell, pm, step, vx, vy, vz}, T, nb, nE, lnE_min, lnE_max, chi_out};
+  for_each_pair(n_pairs, pcell, table_pair, &L);
 }
 
 /* ------------------------------------------------------------------ */
@@ -700,6 +876,7 @@ void or_mlp_forward1(const or_mlp_t* d, const double* W, const double* bias,
 
 void or_mlp_forward(const or_mlp_t* d, const double* W, const double* bias, int64_t n,
                     const double* x, int bf16, double* y) {
+#pragma omp parallel for schedule(static)
   for (int64_t s = 0; s < n; ++s) or_mlp_forward1(d, W, bias, x + s * d->d_in, bf16, y + s * d->d_out);
 }
 
@@ -730,28 +907,44 @@ void or_neural_features(const or_mlp_t* d, const double vr[3], double T_cell,
 /* Neural collision: features, MLP, projection (reading R6), CM update,
  * pairs in order.  T_cell of a cell = m Theta_pre / (3 k_B N).  u_out
  * (optional) receives each pair's unit direction. */
+typedef struct {
+  pairs_ctx c;
+  const or_mlp_t* d;
+  const double *W, *bias, *mom_pre;
+  int bf16;
+  double* u_out;
+} neural_ctx;
+
+static void neural_pair(const void* c_, int64_t p) {
+  const neural_ctx* Nc = (const neural_ctx*)c_;
+  const pairs_ctx* c = &Nc->c;
+  const or_gas_t* gs = c->gs;
+  const or_mlp_t* d = Nc->d;
+  double *vx = c->vx, *vy = c->vy, *vz = c->vz;
+  int32_t i = c->pi[p], j = c->pj[p], k = c->pcell[p];
+  double vr[3] = {vx[i] - vx[j], vy[i] - vy[j], vz[i] - vz[j]};
+  double g = sqrt((vr[0] * vr[0] + vr[1] * vr[1]) + vr[2] * vr[2]);
+  double T = gs->mass * Nc->mom_pre[5 * k + 4] / (3.0 * OR_KB * Nc->mom_pre[5 * k + 0]);
+  double z[4], x[8], y[3];
+  or_noise4(gs->seed, k, c->pm[p], c->step, z);
+  or_neural_features(d, vr, T, z, x);
+  or_mlp_forward1(d, Nc->W, Nc->bias, x, Nc->bf16, y);
+  double ny = sqrt((y[0] * y[0] + y[1] * y[1]) + y[2] * y[2]);
+  double e[3];
+  if (ny > d->eps) { e[0] = y[0] / ny; e[1] = y[1] / ny; e[2] = y[2] / ny; }
+  else iso_dir(gs->seed, k, c->pm[p], c->step, e);
+  if (Nc->u_out) { Nc->u_out[3 * p] = e[0]; Nc->u_out[3 * p + 1] = e[1]; Nc->u_out[3 * p + 2] = e[2]; }
+  double vrp[3] = {g * e[0], g * e[1], g * e[2]};
+  pair_update(vx, vy, vz, i, j, vrp);
+}
+
 void or_collide_neural(const or_gas_t* gs, const or_mlp_t* d, const double* W,
                        const double* bias, const double* mom_pre, int64_t n_pairs,
                        const int32_t* pi, const int32_t* pj, const int32_t* pcell,
                        const int32_t* pm, uint64_t step, int bf16, double* vx,
                        double* vy, double* vz, double* u_out) {
-  for (int64_t p = 0; p < n_pairs; ++p) {
-    int32_t i = pi[p], j = pj[p], k = pcell[p];
-    double vr[3] = {vx[i] - vx[j], vy[i] - vy[j], vz[i] - vz[j]};
-    double g = sqrt((vr[0] * vr[0] + vr[1] * vr[1]) + vr[2] * vr[2]);
-    double T = gs->mass * mom_pre[5 * k + 4] / (3.0 * OR_KB * mom_pre[5 * k + 0]);
-    double z[4], x[8], y[3];
-    or_noise4(gs->seed, k, pm[p], step, z);
-    or_neural_features(d, vr, T, z, x);
-    or_mlp_forward1(d, W, bias, x, bf16, y);
-    double ny = sqrt((y[0] * y[0] + y[1] * y[1]) + y[2] * y[2]);
-    double e[3];
-    if (ny > d->eps) { e[0] = y[0] / ny; e[1] = y[1] / ny; e[2] = y[2] / ny; }
-    else iso_dir(gs->seed, k, pm[p], step, e);
-    if (u_out) { u_out[3 * p] = e[0]; u_out[3 * p + 1] = e[1]; u_out[3 * p + 2] = e[2]; }
-    double vrp[3] = {g * e[0], g * e[1], g * e[2]};
-    pair_update(vx, vy, vz, i, j, vrp);
-  }
+  neural_ctx Nc = {{gs, pi, pj, pcell, pm, step, vx, vy, vz}, d, W, bias, mom_pre, bf16, u_out};
+  for_each_pair(n_pairs, pcell, neural_pair, &Nc);
 }
 
 /* Jager harvest of training targets (Sec. 3.4.5 "physics harvesting"):
@@ -760,6 +953,7 @@ void or_collide_neural(const or_gas_t* gs, const or_mlp_t* d, const double* W,
 void or_harvest_jager(const or_gas_t* gs, const or_pot_t* P, int64_t n,
                       const double* vi, const double* vj, const double* b,
                       const double* eps, double* vi_out, double* vj_out) {
+#pragma omp parallel for schedule(dynamic, 64)
   for (int64_t p = 0; p < n; ++p) {
     double vr[3] = {vi[3 * p] - vj[3 * p], vi[3 * p + 1] - vj[3 * p + 1], vi[3 * p + 2] - vj[3 * p + 2]};
     double g = sqrt((vr[0] * vr[0] + vr[1] * vr[1]) + vr[2] * vr[2]);
@@ -799,6 +993,7 @@ double or_transport_q2(const or_pot_t* P, double E, double bmax, int32_t nb, con
 void or_transport_viscosity(const or_pot_t* P, double mass, int32_t n_T, const double* T, double bmax,
                             int32_t nb, const double* u, const double* wu, int32_t nx, const double* x,
                             const double* wx, double* omega22, double* mu) {
+#pragma omp parallel for schedule(dynamic, 1)
   for (int32_t i = 0; i < n_T; ++i) {
     double om = 0.0;
     for (int32_t j = 0; j < nx; ++j) {
@@ -824,8 +1019,11 @@ static double or_softplus(double z) { return fmax(z, 0.0) + log1p(exp(-fabs(z)))
  * (hi + lo), the activations of hidden layers 1-4 rounded to bf16 once, the
  * fifth hidden layer's activations exact (an FP32 dot product follows). */
 void or_chi_mlp_forward(const double* W, const double* bias, int64_t n, const double* x, int emul, double* y) {
+#pragma omp parallel
+  {
   double* a = (double*)malloc(sizeof(double) * 512);
   double* b = (double*)malloc(sizeof(double) * 512);
+#pragma omp for schedule(dynamic, 16)
   for (int64_t s = 0; s < n; ++s) {
     for (int q = 0; q < 2; ++q) {
       double v = x[2 * s + q];
@@ -854,4 +1052,5 @@ void or_chi_mlp_forward(const double* W, const double* bias, int64_t n, const do
   }
   free(a);
   free(b);
+  }
 }

@@ -474,7 +474,10 @@ struct JagerArgs {
 };
 
 // One pair: chi(b, E) for its impact parameter and energy, rotation of v_r
-// (Bird 1994, Eq. 2.22), centre-of-mass update; velocities through L2.
+// (Bird 1994, Eq. 2.22) in FP64 -- cos and sin of the FP32 chi and of the
+// azimuth eps = 2 pi U2 in FP64, so that the post-collision velocities are
+// the exact deflection by that chi to FP64 rounding -- then the
+// centre-of-mass update; velocities through L2.
 __device__ __forceinline__ void collide_pair(const PotDev& P, const JagerArgs& a, int64_t p, int4 q) {
   const double xi = __ldcg(a.vx + q.x), yi = __ldcg(a.vy + q.x), zi = __ldcg(a.vz + q.x);
   const double xj = __ldcg(a.vx + q.y), yj = __ldcg(a.vy + q.y), zj = __ldcg(a.vz + q.y);
@@ -486,7 +489,13 @@ __device__ __forceinline__ void collide_pair(const PotDev& P, const JagerArgs& a
   const float chi = g2 > 0.0 ? chi_device(P, b, E) : 0.f;
   if (a.chi_out) a.chi_out[p] = chi;
   double o[3] = {0.0, 0.0, 0.0};
-  if (g2 > 0.0) deflect_shell(ux, uy, uz, g2, chi, (float)(2.0 * DSMC_PI * u53(w.z, w.w)), o);
+  if (g2 > 0.0) {
+    double sc, cc, se, ce;
+    sincos((double)chi, &sc, &cc);
+    sincospi(2.0 * u53(w.z, w.w), &se, &ce);
+    const double ig = rsqrt(g2);
+    deflect(ux, uy, uz, g2 * ig, ig, cc, sc, ce, se, o);
+  }
   const double cx = 0.5 * (xi + xj), cy = 0.5 * (yi + yj), cz = 0.5 * (zi + zj);
   __stcg(a.vx + q.x, cx + 0.5 * o[0]); __stcg(a.vy + q.x, cy + 0.5 * o[1]); __stcg(a.vz + q.x, cz + 0.5 * o[2]);
   __stcg(a.vx + q.y, cx - 0.5 * o[0]); __stcg(a.vy + q.y, cy - 0.5 * o[1]); __stcg(a.vz + q.y, cz - 0.5 * o[2]);

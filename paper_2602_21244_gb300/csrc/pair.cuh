@@ -30,20 +30,12 @@ __device__ __forceinline__ void vhs_pair(uint64_t seed, uint64_t step, uint32_t 
 // Eq. 2.22) with the direction in FP32 -- chi itself carries FP32 accuracy
 // -- then scaled in FP64 to |v_r'| = |v_r| exactly: s = |v_r|/|y| from an
 // FP32 estimate and one FP64 Newton step on s^2 |y|^2 = |v_r|^2 (relative
-// error ~1e-14).  About a third of the FP64 work of deflect().
-__device__ __forceinline__ void deflect_shell_h(double ux, double uy, double uz, double g2, float chi, float eps,
-                                                double* h, double* Y);
-
-__device__ __forceinline__ void deflect_shell(double ux, double uy, double uz, double g2, float chi, float eps,
-                                              double* o) {
-  double h, Y[3];
-  deflect_shell_h(ux, uy, uz, g2, chi, eps, &h, Y);
-  o[0] = 2.0 * h * Y[0]; o[1] = 2.0 * h * Y[1]; o[2] = 2.0 * h * Y[2];
-}
-
-// The same rotation, returned as v_r' = 2 h Y (Y the FP32 rotated direction
+// error ~1e-14).  Returned as v_r' = 2 h Y (Y the FP32 rotated direction
 // widened to FP64, h half the FP64 shell scale), so that a caller can form
-// the post-collision velocities as c +- h Y with one FMA each.
+// the post-collision velocities as c +- h Y with one FMA each.  The
+// direction is within about 2e-6 rad of the exact deflection by the same
+// chi and eps (the FP32 roundings of the inputs, the frame, sincosf and the
+// FP32 azimuth); about a third of the FP64 work of an FP64 rotation.
 __device__ __forceinline__ void deflect_shell_h(double ux, double uy, double uz, double g2, float chi, float eps,
                                                 double* h, double* Yo) {
   const float fx = f64_to_f32(ux), fy = f64_to_f32(uy), fz = f64_to_f32(uz);

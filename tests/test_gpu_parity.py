@@ -305,27 +305,52 @@ def _sensitivity(P, b, E, h=1e-4):
     return s1 + s2
 
 
+def _check_chi(P, b, E, chi_gpu, max_ill_frac=1e-3):
+    """J5: |chi_gpu - chi_ref| <= 1e-5 |chi_ref| + 1e-6 rad with the oracle
+    evaluated at the kernel's FP32 inputs; a pair whose chi the FP32
+    rounding of its inputs alone moves by more than 1e-6 rad
+    ((|b dchi/db| + |g dchi/dg|) 2^-24 > 1e-6, near orbiting) is
+    ill-conditioned: counted, not gated, at most max_ill_frac of the pairs."""
+    ref = O.chi_many(P, b, E)
+    err = np.abs(chi_gpu - ref)
+    out = np.flatnonzero(err > 1e-5 * np.abs(ref) + 1e-6)
+    bad, ill = [], 0
+    for q in out:
+        if _sensitivity(P, float(b[q]), float(E[q])) * 2.0 ** -24 > 1e-6:
+            ill += 1
+        else:
+            bad.append((float(b[q]), float(E[q]), float(ref[q]), float(chi_gpu[q])))
+    assert not bad, (len(bad), bad[:5])
+    assert ill <= max(3, max_ill_frac * len(b)), ill
+    return ill
+
+
+def _kernel_energy(g2):
+    """E_r/k_B as the kernels form it: FP32 (m/(4 k_B)) times FP32 g^2."""
+    return (np.float32(W.M_AR / (4.0 * KB)) * np.asarray(g2, np.float64).astype(np.float32)).astype(np.float64)
+
+
 @pytest.mark.parametrize("n_nodes", [32, 48])
 def test_chi_jager_parity_sampled(n_nodes):
+    """C1 batch, a stratified sample of 2 x 10^4 of its 2^22 pairs: half
+    below 1.5 well depths (E_r/k_B < 215 K, where orbiting, multiple roots and
+    the finer bracket and quadrature act), half above."""
     from paper_2602_21244_gb300 import dsmc as D
     b, g = W.chi_pairs(1 << 22, seed=0)
     chi = host(ctx().jager_chi(D.make_gas(_gas_ar()), D.make_potential(JP), cuda(b), cuda(g),
                                n_nodes=n_nodes))
     assert ctx().sync_status() == 0
-    idx = np.random.default_rng(1).choice(len(b), 3000, replace=False)
+    g32 = g.astype(np.float32)
+    E = (np.float32(W.M_AR / (4.0 * KB)) * g32 * g32).astype(np.float64)
     P = O.make_pot(JP)
-    bad, ill = [], 0
-    for q in idx:
-        bq, E = float(b[q]), float(O.e_kelvin(W.M_AR, float(g[q])))
-        ref = O.chi(P, bq, E)
-        err = abs(chi[q] - ref)
-        if err > 1e-5 * abs(ref) + 1e-6:
-            if _sensitivity(P, bq, E) * 2.0 ** -24 > 1e-6:
-                ill += 1
-            else:
-                bad.append((bq, float(g[q]), ref, float(chi[q])))
-    assert not bad, bad[:5]
-    assert ill <= 3
+    depth = -min(O.pot_V(P, r) for r in np.linspace(3.0, 6.0, 601))
+    rng = np.random.default_rng(1)
+    low = np.flatnonzero(E < 1.5 * depth)
+    high = np.flatnonzero(E >= 1.5 * depth)
+    idx = np.concatenate([rng.choice(low, 10000, replace=False), rng.choice(high, 10000, replace=False)])
+    ill = _check_chi(P, b[idx].astype(np.float64), E[idx], chi[idx].astype(np.float64))
+    print(f"n_nodes {n_nodes}: {len(idx)} pairs ({len(low)} of 2^22 below 1.5 well depths), "
+          f"{ill} ill-conditioned")
 
 
 # ------------------------------------------------------------------ neural operator
@@ -425,40 +450,46 @@ def test_step_host_matches_device_step():
 # ------------------------------------------------------------------ Jager collide
 
 def test_collide_jager_parity():
+    """J6: the collide's velocities, element by element, within 1e-12
+    (relative to max(|v|, c_ref)) of the oracle's rotation and
+    centre-of-mass update driven by the kernel's own chi (FP64 rotation on
+    both sides); J5: each pair's chi against the oracle at the kernel's FP32
+    inputs (b from tag 4, E from the pair's pre-collision velocities);
+    pairs bit-exact; pair energy and momentum exact."""
+    from paper_2602_21244_gb300 import dsmc as D
     w = W.hypersonic(scale=0.06)
     gas = O.make_gas(**w["gas"])
     P = O.make_pot(JP)
     sg0 = _sgmax0(w, gas)
     perm, cs, sx, sy, sz = oracle_sorted(w)
     pr = O.select_pairs(gas, cs, sx, sy, sz, sg0, 4, capacity=1 << 22)
-    rx, ry, rz, chi_ref = O.collide_jager(gas, P, pr, 4, sx, sy, sz, want_chi=True)
-    from paper_2602_21244_gb300 import dsmc as D
     Dg, srt, mom, sg, sel = gpu_step_pieces(w, sg0, step=4)
     C = ctx()
     sh = sel_host(sel)
+    assert sh["n_pairs"] == pr["n_pairs"]
     chi_gpu = torch().zeros(max(sh["n_pairs"], 1), dtype=torch().float32, device="cuda")
     C.collide_jager(Dg, D.make_potential(JP), 4, sel, srt["svx"], srt["svy"], srt["svz"],
                     n_nodes=32, chi_out=chi_gpu)
     assert C.sync_status() == 0
-    # chi of each pair (matched by cell, candidate) within the chi gate
     p = sh["pairs"]
     order = np.lexsort((p[:, 3], p[:, 2]))
-    cg = host(chi_gpu)[:sh["n_pairs"]][order]
-    err = np.abs(cg - chi_ref)
-    gate = 1e-5 * np.abs(chi_ref) + 1e-6
-    # later collisions see velocities already perturbed at the 1e-5 level, so
-    # the gate for a pair is widened by its chi sensitivity; count the rest
-    frac_out = np.mean(err > 10 * gate)
-    assert frac_out < 2e-3, (frac_out, err.max())
-    # velocities: per collision |dv| <= |g| |dchi|, compounded over the step
-    dv = np.sqrt((host(srt["svx"]) - rx) ** 2 + (host(srt["svy"]) - ry) ** 2 + (host(srt["svz"]) - rz) ** 2)
-    c8000 = math.sqrt(2 * KB * 8000.0 / W.M_AR)
-    assert np.mean(dv > 1e-3 * c8000) < 2e-3, (np.mean(dv > 1e-3 * c8000), dv.max())
-    # pair energy and momentum are exact whatever chi
+    for c, k in enumerate(("i", "j", "cell", "m")):
+        assert np.array_equal(p[order, c], pr[k])
+    cg = host(chi_gpu)[:sh["n_pairs"]][order].astype(np.float64)
+    rx, ry, rz, vr, bA = O.collide_given_chi(gas, pr, 4, cg, sx, sy, sz, want_vr=True)
+    got = [host(a) for a in (srt["svx"], srt["svy"], srt["svz"])]
+    cr = c_ref(W.M_AR)
+    worst = 0.0
+    for g_, r_ in zip(got, (rx, ry, rz)):
+        rel = np.abs(g_ - r_) / np.maximum(np.abs(r_), cr)
+        worst = max(worst, rel.max())
+    assert worst <= 1e-12, worst
+    _check_chi(P, bA.astype(np.float32).astype(np.float64), _kernel_energy((vr ** 2).sum(1)), cg)
     e0 = np.sum(sx ** 2 + sy ** 2 + sz ** 2)
-    e1 = np.sum(host(srt["svx"]) ** 2 + host(srt["svy"]) ** 2 + host(srt["svz"]) ** 2)
+    e1 = np.sum(got[0] ** 2 + got[1] ** 2 + got[2] ** 2)
     assert abs(e1 / e0 - 1) < 1e-12
-    assert abs(np.sum(host(srt["svx"])) - np.sum(sx)) < 1e-9 * np.abs(sx).sum()
+    assert abs(np.sum(got[0]) - np.sum(sx)) < 1e-9 * np.abs(sx).sum()
+    print(f"{sh['n_pairs']} pairs, worst velocity difference {worst:.2e} of max(|v|, c_ref)")
 
 
 # ------------------------------------------------------------------ failure detection

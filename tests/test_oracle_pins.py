@@ -811,3 +811,62 @@ def test_chi_mlp_table_is_forward_at_the_nodes():
     assert T.shape == (3, 5)
     np.testing.assert_allclose([T[2, 1], T[0, 4]], np.expm1(y), rtol=1e-15)
     assert np.all(T >= 0)
+
+
+# ------------------------------------------------------------------ threads and the given-chi mode
+
+def test_oracle_results_do_not_depend_on_threads():
+    """The oracle's parallel loops (cells, independent pairs, table nodes)
+    must reproduce its sequential results bit for bit."""
+    w = W.hypersonic(scale=0.05)
+    P = O.make_pot(W.JAGER_SYNTHETIC_AR)
+    wts = W.mlp_weights()
+    mlp = O.make_mlp(8, 128, 3, 3, 0, W.sigma_v(), 273.0, 1e-12)
+    table = O.chi_table(P, 12.0, 33, 17, math.log(5.0), math.log(6e4)).astype(np.float32)
+    runs = []
+    n0 = O.num_threads()
+    try:
+        for nt in (1, max(2, n0)):
+            O.set_num_threads(nt)
+            gas = O.make_gas(**dict(w["gas"], model=1))
+            sg = O.sigma_g_max_init(gas, w["T_cell"], 5.0)
+            perm, cs, sx, sy, sz = O.sort_cells(w["cell_id"], w["vx"], w["vy"], w["vz"], w["n_cells"])
+            mom = O.cell_moments(cs, sx, sy, sz)
+            pr = O.select_pairs(gas, cs, sx, sy, sz, sg, 2, capacity=1 << 20)
+            out = [mom, pr["sgmax"], pr["i"], pr["j"], pr["round"]]
+            out += list(O.collide_vhs(gas, pr, 2, sx, sy, sz))
+            out += list(O.collide_neural(gas, mlp, wts["W"], wts["bias"], mom, pr, 2, sx, sy, sz))
+            out += list(O.collide_table(gas, table, math.log(5.0), math.log(6e4), pr, 2, sx, sy, sz))
+            sub = {k: (v[:400] if isinstance(v, np.ndarray) else v) for k, v in pr.items()}
+            sub["n_pairs"] = min(400, pr["n_pairs"])
+            out += list(O.collide_jager(gas, P, sub, 2, sx, sy, sz))
+            out += list(O.moment_match(cs, mom, *O.collide_vhs(gas, pr, 2, sx, sy, sz)))
+            out.append(O.chi_batch(gas, P, *W.chi_pairs(300, seed=4)))
+            runs.append(out)
+    finally:
+        O.set_num_threads(n0)
+    for a, b in zip(*runs):
+        assert np.array_equal(a, b)
+
+
+def test_given_chi_mode_reproduces_the_jager_collide():
+    """Fed the Jager collide's own chi, the given-chi mode must give the same
+    velocities bit for bit (same rotation, azimuth and update), and record
+    each pair's pre-collision v_r."""
+    w = W.hypersonic(scale=0.03)
+    gas = O.make_gas(**dict(w["gas"], model=1))
+    P = O.make_pot(W.JAGER_SYNTHETIC_AR)
+    sg = O.sigma_g_max_init(gas, w["T_cell"], 5.0)
+    perm, cs, sx, sy, sz = O.sort_cells(w["cell_id"], w["vx"], w["vy"], w["vz"], w["n_cells"])
+    pr = O.select_pairs(gas, cs, sx, sy, sz, sg, 5, capacity=1 << 20)
+    *ref, chi = O.collide_jager(gas, P, pr, 5, sx, sy, sz, want_chi=True)
+    *got, vr, b_imp = O.collide_given_chi(gas, pr, 5, chi, sx, sy, sz, want_vr=True)
+    for x, y in zip(ref, got):
+        assert np.array_equal(x, y)
+    # the first pair of each cell sees the input velocities
+    first = np.r_[0, np.flatnonzero(np.diff(pr["cell"])) + 1]
+    i, j = pr["i"][first], pr["j"][first]
+    np.testing.assert_array_equal(vr[first], np.stack([sx[i] - sx[j], sy[i] - sy[j], sz[i] - sz[j]], 1))
+    # its impact parameters reproduce the collide's chi
+    E = O.e_kelvin(W.M_AR, np.linalg.norm(vr, axis=1))
+    np.testing.assert_allclose(O.chi_many(P, b_imp[:200], E[:200]), chi[:200], rtol=1e-9, atol=1e-12)
