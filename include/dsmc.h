@@ -383,6 +383,28 @@ int dsmc_tc_selftest(dsmc_ctx_t* ctx, int32_t N, int32_t K, int32_t layout, cons
  * traps or spins without bound; the context stays usable. */
 int dsmc_selftest_timeout(dsmc_ctx_t* ctx, int32_t which, uint64_t limit_ns, void* stream);
 
+/* Diagnostic with no counterpart in the paper (roofline denominators of
+ * the arithmetic pipes): a kernel of `blocks` x `threads` threads (threads a
+ * multiple of 32, at most 256), each repeating `iters` times 32 dependent
+ * operations of one kind spread over 8 independent chains -- which 0: FP32
+ * FMA, 1: paired FP32 FMA (fma.rn.f32x2), 2: FP64 FMA, 3: the
+ * special-function unit's ex2.approx.f32 -- and writing one float per
+ * thread to `sink` (device memory, blocks x threads floats) so that no work
+ * is optimised away.  dsmc_selftest_peak_ops gives the operations one thread
+ * performs (FLOPs for the FMA kinds, 2 per FMA and 4 per paired FMA;
+ * results for ex2; -1 for bad arguments); the caller times the launch. */
+/* Diagnostic with no counterpart in the paper: the FP64 helpers of the
+ * turning-point refinement against CUDA's own routines, y[i] = f(x[i]) for
+ * n values (device memory) -- which 0: the refinement's exponential (Cody-
+ * Waite reduction by ln 2, Taylor polynomial to degree 12; |x| < 700),
+ * 1: CUDA's exp, 2: the refinement's reciprocal (FP32 seed and two Newton
+ * steps; x positive, inside the FP32 normal range), 3: 1.0 / x. */
+int dsmc_selftest_math(dsmc_ctx_t* ctx, int32_t which, int64_t n, const double* x, double* y, void* stream);
+
+int64_t dsmc_selftest_peak_ops(int32_t which, int32_t iters);
+int dsmc_selftest_peak(dsmc_ctx_t* ctx, int32_t which, int32_t blocks, int32_t threads, int32_t iters,
+                       float* sink, void* stream);
+
 /* ---------------------------------------------------------------- moment matching */
 
 /* Sec. 2.5, centred: per cell v <- u_pre + alpha (v - u_post),

@@ -417,6 +417,26 @@ int dsmc_selftest_timeout(dsmc_ctx_t* c, int32_t which, uint64_t limit_ns, void*
                     : dsmc::launch_selftest_mbar(c, limit_ns, S(stream));
 }
 
+int dsmc_selftest_math(dsmc_ctx_t* c, int32_t which, int64_t n, const double* x, double* y, void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, which >= 0 && which <= 3 && n >= 0 && (n == 0 || (x && y)), "selftest_math: which 0..3, n >= 0, x, y");
+  return dsmc::launch_selftest_math(c, which, n, x, y, S(stream));
+}
+
+int64_t dsmc_selftest_peak_ops(int32_t which, int32_t iters) {
+  if (which < 0 || which > 3 || iters < 1) return -1;
+  return dsmc::peak_ops_per_thread(which, iters);
+}
+
+int dsmc_selftest_peak(dsmc_ctx_t* c, int32_t which, int32_t blocks, int32_t threads, int32_t iters, float* sink,
+                       void* stream) {
+  CHECK_CTX(c);
+  REQUIRE(c, which >= 0 && which <= 3 && blocks >= 1 && threads >= 32 && threads <= 256 && threads % 32 == 0 &&
+                 iters >= 1 && sink,
+          "selftest_peak: which 0..3, blocks >= 1, threads a multiple of 32 up to 256, iters >= 1, sink");
+  return dsmc::launch_peak(c, which, blocks, threads, iters, sink, S(stream));
+}
+
 int dsmc_moment_match(dsmc_ctx_t* c, int32_t n_cells, const int32_t* cell_start,
                       const double* mom_pre, double* vx, double* vy, double* vz, void* stream) {
   CHECK_CTX(c);

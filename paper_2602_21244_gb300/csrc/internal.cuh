@@ -334,6 +334,9 @@ int launch_gather(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_start,
                   const double* vx, const double* vy, const double* vz, double* svx, double* svy,
                   double* svz, cudaStream_t s);
 int launch_selftest_barrier(Ctx* c, uint64_t limit_ns, cudaStream_t s);
+int64_t peak_ops_per_thread(int which, int32_t iters);
+int launch_selftest_math(Ctx* c, int which, int64_t n, const double* x, double* y, cudaStream_t s);
+int launch_peak(Ctx* c, int which, int32_t blocks, int32_t threads, int32_t iters, float* sink, cudaStream_t s);
 int launch_selftest_deps(Ctx* c, uint64_t limit_ns, cudaStream_t s);
 int launch_selftest_mbar(Ctx* c, uint64_t limit_ns, cudaStream_t s);
 

@@ -29,6 +29,48 @@ namespace dsmc {
 
 constexpr int kMaxNodes = 128;
 
+__device__ __forceinline__ float tc_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// e^x in FP64 for |x| < 700, written from the mathematics (Cody and Waite's
+// additive argument reduction, then the Taylor series): x = n ln 2 + r with
+// n = rint(x / ln 2) and r = (x - n L_hi) - n L_lo, where L_hi is ln 2
+// truncated to 16 bits (n L_hi exact) and L_lo = ln 2 - L_hi to FP64; |r| <=
+// ln2/2, so the Taylor polynomial of e^r to r^12 truncates below 2e-16
+// relative; 2^n enters through the exponent field.  Seventeen FP64
+// operations, within a few ulp of a correctly rounded e^x.
+struct Exp64 {
+  double inv_ln2, ln2_hi, ln2_lo;
+  double c[13];   // 1/k!
+};
+
+__host__ inline Exp64 make_exp64() {
+  Exp64 e;
+  e.inv_ln2 = 1.0 / 0.6931471805599453;
+  e.ln2_hi = 0.693145751953125;   // ln 2 truncated to 16 significant bits (n L_hi exact)
+  // ln 2 - L_hi from the decimal expansion of ln 2 (0.69314718055994530941723212145817656807...)
+  e.ln2_lo = 1.4286068203094172321214581765680755e-06;
+  double f = 1.0;
+  for (int k = 0; k <= 12; ++k) { if (k) f *= k; e.c[k] = 1.0 / f; }
+  return e;
+}
+
+__device__ __forceinline__ double exp64(const Exp64& E, double x) {
+  const double magic = 6755399441055744.0;   // 1.5 2^52: adding it rounds to an integer
+  const double t = fma(x, E.inv_ln2, magic);
+  const double n = t - magic;
+  const int ni = __double2loint(t);          // n, from the low word
+  const double r = fma(-n, E.ln2_lo, fma(-n, E.ln2_hi, x));
+  double p = E.c[12];
+#pragma unroll
+  for (int k = 11; k >= 0; --k) p = fma(p, r, E.c[k]);
+  return __hiloint2double(__double2hiint(p) + (ni << 20), __double2loint(p));
+}
+
+
 struct PotDev {
   int kind;
   int n_nodes;
@@ -41,6 +83,7 @@ struct PotDev {
   double Cd[6];       // (6 + 2n) C_n
   double Cdd[6];      // (6 + 2n)(7 + 2n) C_n
   float D[17];        // P(r) = sum_p D_p r^-p,  e^{-beta r} P(r) = sum_n C_2n r^-2n e^{-x} S_2n(x)
+  Exp64 ex64;         // constants of the FP64 exponential of the refinement
   float sigma0;       // zero crossing of V (F > 0 above max(b, sigma0))
   float orbit_E;      // below this energy use the fine bracket scan
   double d_hs, kappa, p;
@@ -96,49 +139,59 @@ __host__ __device__ inline double V64(const PotDev& P, double r, double* dV, dou
   return rep - q + ex * Pr;
 }
 
-// V, V' and V'' in FP64 at r (ir = 1/r given), the same expansion as V64;
-// *rep, *ex receive A e^{poly} and e^{-beta r} (Jager form).
-__host__ __device__ inline double V64_d2(const PotDev& P, double r, double ir, double* dV, double* d2V,
-                                         double* rep_out, double* ex_out) {
+// V and V' in FP64 at r (ir = 1/r given), the same expansion as V64, for
+// the Newton refinement of the turning point; *rep, *ex receive A e^{poly}
+// and e^{-beta r}, *Pr, *dPr the damping polynomial P(r) and P'(r) (Jager
+// form), from which the quadrature's coefficients are carried to the root.
+__device__ __forceinline__ double V64n(const PotDev& P, double r, double ir, double* dV, double* rep_out,
+                                       double* ex_out, double* Pr_out, double* dPr_out) {
   const double ir2 = ir * ir;
   if (P.kind == 2) {
     const double v = P.kappa * pow(r, -P.p);
     *dV = -P.p * v * ir;
-    *d2V = P.p * (P.p + 1.0) * v * ir2;
     return v;
   }
   if (r < P.rc) {
-    const double e = P.At * exp(-P.at * r) * ir, k = P.at + ir;
-    *dV = -e * k;
-    *d2V = e * (k * k + ir2);
+    const double e = P.At * exp(-P.at * r) * ir;
+    *dV = -e * (P.at + ir);
     return e;
   }
-  const double rep = P.A * exp(P.a1 * r + P.a2 * r * r + P.am1 * ir + P.am2 * ir2);
+  const double rep = P.A * exp64(P.ex64, P.a1 * r + P.a2 * r * r + P.am1 * ir + P.am2 * ir2);
   const double pp = P.a1 + 2.0 * P.a2 * r - P.am1 * ir2 - 2.0 * P.am2 * ir2 * ir;   // poly'
-  const double ppp = 2.0 * P.a2 + 2.0 * P.am1 * ir2 * ir + 6.0 * P.am2 * ir2 * ir2;  // poly''
-  double q = 0.0, dq = 0.0, d2q = 0.0, pw = ir2 * ir2 * ir2;
+  double q = 0.0, dq = 0.0, pw = ir2 * ir2 * ir2;
 #pragma unroll
   for (int n = 0; n < 6; ++n) {
     q = fma(P.C[n], pw, q);
     dq = fma(P.Cd[n], pw, dq);
-    d2q = fma(P.Cdd[n], pw, d2q);
     pw *= ir2;
   }
   dq *= -ir;
-  d2q *= ir2;
-  double Pr = P.Dd[16], dPr = P.Dp[15], d2Pr = P.Dpp[15];
+  double Pr = P.Dd[16], dPr = P.Dp[15];
 #pragma unroll
   for (int k = 15; k >= 0; --k) Pr = fma(Pr, ir, P.Dd[k]);
 #pragma unroll
-  for (int k = 14; k >= 0; --k) { dPr = fma(dPr, ir, P.Dp[k]); d2Pr = fma(d2Pr, ir, P.Dpp[k]); }
+  for (int k = 14; k >= 0; --k) dPr = fma(dPr, ir, P.Dp[k]);
   dPr *= -ir2;
-  d2Pr *= ir2 * ir;
-  const double ex = exp(-P.beta * r);
+  const double ex = exp64(P.ex64, -P.beta * r);
   *rep_out = rep;
   *ex_out = ex;
+  *Pr_out = Pr;
+  *dPr_out = dPr;
   *dV = rep * pp - dq + ex * (dPr - P.beta * Pr);
-  *d2V = rep * (pp * pp + ppp) - d2q + ex * (d2Pr - P.beta * (2.0 * dPr - P.beta * Pr));
   return rep - q + ex * Pr;
+}
+
+// 1/x in FP64 without a division: the FP32 reciprocal (relative error
+// about 2^-23) refined by Newton's iteration r <- r (2 - x r), written
+// r + r (1 - x r): each step squares the relative error (2^-46, then below
+// FP64 rounding).  x positive and inside the FP32 normal range.
+__device__ __forceinline__ double rcp64_1(double x) {
+  const double r = f32_to_f64(tc_rcp(f64_to_f32(x)));
+  return fma(r, fma(-x, r, 1.0), r);
+}
+__device__ __forceinline__ double rcp64(double x) {
+  const double r = rcp64_1(x);
+  return fma(r, fma(-x, r, 1.0), r);
 }
 
 // ---------------------------------------------------------------- FP32 potential
@@ -187,13 +240,38 @@ __device__ __forceinline__ float F32(const PotDev& P, float b2, float E, float r
 }
 
 // ---------------------------------------------------------------- turning point
-// Returns r_min in FP64: FP32 bracket + safeguarded Newton, then FP64 Newton
-// until a step is below 1e-12 r.  The returned point is the last point where
-// V was evaluated in FP64 (F there is below 1e-12); *rep and *ex receive the
-// repulsion A e^{poly} and e^{-beta r} at that point (Jager form).
-__device__ double rmin_device(const PotDev& P, float b, float E, double* rep = nullptr,
-                              double* ex = nullptr) {
-  if (P.kind == 1) return (double)fmaxf(b, (float)P.d_hs);
+// The FP64 turning point and what the quadrature's coefficients reuse from
+// its last FP64 evaluation, carried to the returned point.
+struct Turn {
+  double r, ir;        // r_min and 1/r_min
+  double rep, ex;      // A e^{poly(r_min)}, e^{-beta r_min} (Jager form)
+  double Pr;           // damping polynomial P(r_min)
+};
+
+// r_min in FP64: FP32 bracket + safeguarded Newton, then FP64 Newton steps
+// (the turning-point refinement).  From the FP32 root (relative error about
+// 1e-7) one step leaves about 1e-14.  Newton converges quadratically, so
+// after a step eps the error is about (F''/2F') eps^2, below 1e-9 r for
+// eps <= 2e-5 r away from orbiting; only a larger step (the FP32 stage ended
+// away from the root) is followed by another (each extra iteration costs
+// the whole warp).  The repulsion,
+// e^{-beta r} and P(r) of the last evaluation are carried to the returned
+// point by their Taylor series in the last step (|dpoly|, |beta dr| <
+// 1e-5): their truncation is below 1e-10 relative, and the quadrature uses
+// them in FP32.
+// kWarp: every lane of the warp calls this together (a lane with nothing to
+// compute on harmless inputs); the lanes leave the FP32 stage at different
+// times, and the warp is reconverged before the FP64 steps, which then run
+// for all lanes as long as any lane still refines (GB300's FP64 pipe costs a
+// warp instruction however few lanes are active).
+template <bool kWarp>
+__device__ Turn rmin_device(const PotDev& P, float b, float E) {
+  Turn T = {};
+  if (P.kind == 1) {   // the same kind for every lane
+    T.r = (double)fmaxf(b, (float)P.d_hs);
+    T.ir = rcp64(T.r);
+    return T;
+  }
   const float b2 = b * b;
   float dF;
   float r_hi;
@@ -208,12 +286,17 @@ __device__ double rmin_device(const PotDev& P, float b, float E, double* rep = n
     r_hi = r_lo;
     if (r_hi < 1e-3f) break;
   }
-  if (!found) return (double)r_hi;
+  const float r_nf = r_hi;   // the result when no sign change was found
+  if (!kWarp && !found) {
+    T.r = (double)r_nf;
+    T.ir = rcp64(T.r);
+    return T;
+  }
   // safeguarded Newton in [r_lo, r_hi], F(r_lo) < 0 <= F(r_hi).  Convergence
   // is tested before the bisection fallback: a step below FP32 resolution
   // ends the iteration even when it lands on a bracket end.
   float r = r_hi;
-  for (int it = 0; it < 24; ++it) {
+  for (int it = 0; it < 24 && found; ++it) {
     const float f = F32(P, b2, E, r, &dF);
     if (f == 0.f) break;
     if (f < 0.f) r_lo = r; else r_hi = r;
@@ -222,53 +305,73 @@ __device__ double rmin_device(const PotDev& P, float b, float E, double* rep = n
     if (fabsf(rn - r) <= 4e-7f * r) { if (inside) r = rn; break; }
     r = inside ? rn : 0.5f * (r_lo + r_hi);
   }
-  // FP64 Halley refinement of the turning point (cubic convergence: from the
-  // FP32 root, relative error ~1e-7, one step leaves ~1e-20 times the
-  // curvature constant), kept inside the FP32 bracket widened by 1e-4 (FP32
-  // rounding can misplace its ends slightly).  A step above 1e-6 r (the FP32
-  // stage ended away from the root) is followed by more steps.  The
-  // exponentials of the last evaluation are carried to the returned point
-  // by their Taylor series in the step (|beta dr|, |dpoly| < 1e-5).
-  double rd = r;
-  const double lo = (double)r_lo * (1.0 - 1e-4), hi = (double)r_hi * (1.0 + 1e-4);
-  const double bd2 = (double)b * b, iEd = 1.0 / (double)E;
-  double rep0 = 0.0, ex0 = 0.0, dpoly = 0.0, dr = 0.0;
-  for (int it = 0; it < 4; ++it) {
-    double dV, d2V;
-    const double ir = 1.0 / rd, ir2 = ir * ir;
-    const double V = V64_d2(P, rd, ir, &dV, &d2V, &rep0, &ex0);
+  // FP64 Newton steps, kept inside the FP32 bracket widened by 1e-4 (FP32
+  // rounding can misplace its ends slightly)
+  double rd = f32_to_f64(r), ir = rcp64(rd);
+  const double lo = f32_to_f64(r_lo) * (1.0 - 1e-4), hi = f32_to_f64(r_hi) * (1.0 + 1e-4);
+  const double bd2 = f32_to_f64(b) * f32_to_f64(b), iEd = rcp64(f32_to_f64(E));
+  double rep0 = 0.0, ex0 = 0.0, Pr0 = 0.0, dPr0 = 0.0, dpoly = 0.0, dr = 0.0;
+  if (kWarp) __syncwarp();
+  bool act = found;
+  for (int it = 0; it < 6; ++it) {
+    if (kWarp ? !__any_sync(0xffffffffu, act) : !act) break;
+    double dV;
+    const double ir2 = ir * ir;
+    const double V = V64n(P, rd, ir, &dV, &rep0, &ex0, &Pr0, &dPr0);
     const double f = 1.0 - bd2 * ir2 - V * iEd;
     const double df = 2.0 * bd2 * ir2 * ir - dV * iEd;
-    const double d2f = -6.0 * bd2 * ir2 * ir2 - d2V * iEd;
-    const double step = -2.0 * f * df / (2.0 * df * df - f * d2f);
+    const double step = -f * rcp64_1(fabs(df)) * (df < 0.0 ? -1.0 : 1.0);
     const double rn = rd + step;
-    if (!(rn >= lo && rn <= hi)) { dr = 0.0; break; }
-    dr = step;
-    dpoly = step * (P.a1 + 2.0 * P.a2 * rd - P.am1 * ir2 - 2.0 * P.am2 * ir2 * ir);
-    rd = rn;
-    if (fabs(step) <= 1e-6 * rd) break;
-  }
-  if (rep) {
-    if (fabs(dr) <= 1e-4 * rd) {
-      const double eb = -P.beta * dr;
-      *rep = rep0 * (1.0 + dpoly * (1.0 + 0.5 * dpoly));
-      *ex = ex0 * (1.0 + eb * (1.0 + 0.5 * eb));
-    } else {  // a long last step (not converged): evaluate at rd
-      double dV;
-      V64(P, rd, &dV, rep, ex);
+    // 1/rn from 1/rd: with s = step/rd, 1/(rd + step) = (1/rd)(1 - s + s^2 - ...),
+    // truncated after s^2 (|s| < 1e-4: error below 1e-12 relative, then one
+    // Newton step on the result)
+    const double sr = step * ir;
+    double irn = fma(ir, fma(sr, sr, -sr), ir);
+    irn = fma(irn, fma(-rn, irn, 1.0), irn);
+    if (act) {
+      if (!(rn >= lo && rn <= hi) || !(df != 0.0)) {
+        dr = 0.0;
+        act = false;
+      } else {
+        dr = step;
+        dpoly = step * (P.a1 + 2.0 * P.a2 * rd - P.am1 * ir2 - 2.0 * P.am2 * ir2 * ir);
+        ir = irn;
+        rd = rn;
+        if (fabs(step) <= 2e-5 * rd) act = false;
+      }
     }
   }
-  return rd;
+  if (!found) {
+    T.r = (double)r_nf;
+    T.ir = rcp64(T.r);
+    return T;
+  }
+  T.r = rd;
+  T.ir = ir;
+  if (P.kind == 0 && rd >= P.rc) {
+    if (fabs(dr) <= 1e-4 * rd) {
+      const double eb = -P.beta * dr;
+      T.rep = rep0 * (1.0 + dpoly * (1.0 + 0.5 * dpoly));
+      T.ex = ex0 * (1.0 + eb * (1.0 + 0.5 * eb));
+      T.Pr = fma(dPr0, dr, Pr0);
+    } else {  // a long last step (not converged): evaluate at rd
+      double dV, dPr;
+      V64n(P, rd, ir, &dV, &T.rep, &T.ex, &T.Pr, &dPr);
+    }
+  }
+  return T;
 }
 
 // ---------------------------------------------------------------- chi
-__device__ float chi_device(const PotDev& P, float b, float E) {
-  if (!(b > 0.f)) return (float)DSMC_PI;
-  double rep_d = 0.0, ex_d = 0.0;
-  const double rd = rmin_device(P, b, E, &rep_d, &ex_d);
-  const float r0 = (float)rd;
-  const double ird = 1.0 / rd;
-  const float bt = (float)((double)b * ird);
+// kWarp: see rmin_device (every lane of the warp calls it together).
+template <bool kWarp = false>
+__device__ float chi_device(const PotDev& P, float b_in, float E) {
+  if (!kWarp && !(b_in > 0.f)) return (float)DSMC_PI;
+  const float b = b_in > 0.f ? b_in : 1.f;   // b = 0: head-on, chi = pi (set at the end)
+  const Turn Tp = rmin_device<kWarp>(P, b, E);
+  const double rd = Tp.r, ird = Tp.ir;
+  const float r0 = f64_to_f32(rd);
+  const float bt = f64_to_f32(f32_to_f64(b) * ird);
   const float bt2 = bt * bt;
   const float iE = 1.f / E;
   float F0 = 0.f;
@@ -278,16 +381,18 @@ __device__ float chi_device(const PotDev& P, float b, float E) {
   float d[17], qn[6], Rep0 = 0.f, e0 = 0.f, P0 = 0.f, Vc0 = 0.f, powk = 0.f;
   const bool core = P.kind == 0 && r0 < P.frc;
   if (P.kind == 0 && !core) {
-    const double ir = ird, ir2 = ir * ir;
-    double pw = 1.0, p0 = 0.0;
+    // d_p = D_p r0^-p and the dispersion coefficients C_2n r0^-2n from the
+    // FP64 powers of 1/r0, each rounded once to FP32 (integer pipe)
+    double pw = 1.0;
 #pragma unroll
-    for (int p = 0; p <= 16; ++p) { const double t = P.Dd[p] * pw; d[p] = (float)t; p0 += t; pw *= ir; }
-    P0 = (float)p0;
-    pw = ir2 * ir2 * ir2;
-#pragma unroll
-    for (int n = 0; n < 6; ++n) { qn[n] = (float)(P.C[n] * pw); pw *= ir2; }
-    Rep0 = (float)rep_d;   // from the last FP64 evaluation, at rd
-    e0 = (float)ex_d;
+    for (int p = 0; p <= 16; ++p) {
+      d[p] = f64_to_f32(P.Dd[p] * pw);
+      if (p >= 6 && (p & 1) == 0) qn[(p - 6) >> 1] = f64_to_f32(P.C[(p - 6) >> 1] * pw);
+      pw *= ird;
+    }
+    P0 = f64_to_f32(Tp.Pr);   // P(r0), carried from the last FP64 evaluation
+    Rep0 = f64_to_f32(Tp.rep);
+    e0 = f64_to_f32(Tp.ex);
   } else if (P.kind == 2) {
     Vc0 = (float)(P.kappa * pow(rd, -P.p));
     powk = P.fp;
@@ -338,7 +443,7 @@ __device__ float chi_device(const PotDev& P, float b, float E) {
     const float rG = rsqrtf(G), rG0 = rsqrtf(G0);
     I += P.w_node[q] * 2.f * s * (dG * rG * rG0 / (G * rG + G0 * rG0));
   }
-  return -2.f * bt * I;
+  return b_in > 0.f ? -2.f * bt * I : (float)DSMC_PI;
 }
 
 // ---------------------------------------------------------------- host set-up
@@ -374,6 +479,7 @@ static PotDev make_pot(const dsmc_gas_t& gas, const dsmc_potential_t& p, int n_n
   P.fat = (float)p.at;
   P.d_hs = p.d_hs; P.kappa = p.kappa; P.p = p.p; P.fkappa = (float)p.kappa; P.fp = (float)p.p;
   P.mass_over_4k = (float)(gas.mass / (4.0 * DSMC_KB));
+  P.ex64 = make_exp64();
   // D_p = sum_{n: 2n >= p} C_2n beta^(2n-p) / (2n-p)!
   for (int pp = 0; pp <= 16; ++pp) {
     double s = 0.0;
@@ -415,12 +521,19 @@ static PotDev make_pot(const dsmc_gas_t& gas, const dsmc_potential_t& p, int n_n
 }
 
 // ---------------------------------------------------------------- kernels
+// Warp-uniform loop: every lane of a warp computes chi together (a lane past
+// the end, or with g = 0, on harmless inputs whose result is not kept).
 __global__ void __launch_bounds__(128) k_jager_chi(PotDev P, int64_t n, const float* __restrict__ b,
                                                    const float* __restrict__ g, float* __restrict__ chi) {
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-    const float gg = g[q];
-    const float E = P.mass_over_4k * gg * gg;
-    chi[q] = gg > 0.f ? chi_device(P, b[q], E) : 0.f;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+    const int64_t q = base + lane;
+    const bool valid = q < n;
+    const float gg = valid ? g[q] : 0.f;
+    const bool use = valid && gg > 0.f;
+    const float c = chi_device<true>(P, use ? b[q] : 1.f, use ? P.mass_over_4k * gg * gg : 1.0e4f);
+    if (valid) chi[q] = use ? c : 0.f;
   }
 }
 
@@ -477,28 +590,39 @@ struct JagerArgs {
 // (Bird 1994, Eq. 2.22) in FP64 -- cos and sin of the FP32 chi and of the
 // azimuth eps = 2 pi U2 in FP64, so that the post-collision velocities are
 // the exact deflection by that chi to FP64 rounding -- then the
-// centre-of-mass update; velocities through L2.
-__device__ __forceinline__ void collide_pair(const PotDev& P, const JagerArgs& a, int64_t p, int4 q) {
-  const double xi = __ldcg(a.vx + q.x), yi = __ldcg(a.vy + q.x), zi = __ldcg(a.vz + q.x);
-  const double xj = __ldcg(a.vx + q.y), yj = __ldcg(a.vy + q.y), zj = __ldcg(a.vz + q.y);
+// centre-of-mass update; velocities through L2.  Every lane of the warp runs
+// it together (live false: a lane with no pair, or whose dependency wait
+// failed, computes on harmless inputs and stores nothing), so that chi's FP64
+// refinement and the FP64 rotation run with the warp converged.
+__device__ __forceinline__ void collide_pair(const PotDev& P, const JagerArgs& a, int64_t p, int4 q, bool live) {
+  double xi = 0.0, yi = 0.0, zi = 0.0, xj = 0.0, yj = 0.0, zj = 0.0;
+  if (live) {
+    xi = __ldcg(a.vx + q.x); yi = __ldcg(a.vy + q.x); zi = __ldcg(a.vz + q.x);
+    xj = __ldcg(a.vx + q.y); yj = __ldcg(a.vy + q.y); zj = __ldcg(a.vz + q.y);
+  }
   const double ux = xi - xj, uy = yi - yj, uz = zi - zj;
   const double g2 = ux * ux + uy * uy + uz * uz;
+  const bool use = live && g2 > 0.0;
   const u32x4 w = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_JAGER);
-  const float b = (float)(a.bmax_A * sqrt(u53(w.x, w.y)));
-  const float E = P.mass_over_4k * (float)g2;
-  const float chi = g2 > 0.0 ? chi_device(P, b, E) : 0.f;
-  if (a.chi_out) a.chi_out[p] = chi;
-  double o[3] = {0.0, 0.0, 0.0};
-  if (g2 > 0.0) {
-    double sc, cc, se, ce;
-    sincos((double)chi, &sc, &cc);
-    sincospi(2.0 * u53(w.z, w.w), &se, &ce);
-    const double ig = rsqrt(g2);
-    deflect(ux, uy, uz, g2 * ig, ig, cc, sc, ce, se, o);
+  const float b = use ? (float)(a.bmax_A * sqrt(u53(w.x, w.y))) : 1.f;
+  const float E = use ? P.mass_over_4k * (float)g2 : 1.0e4f;
+  const float chi_c = chi_device<true>(P, b, E);
+  const float chi = use ? chi_c : 0.f;
+  if (live && a.chi_out) a.chi_out[p] = chi;
+  __syncwarp();
+  double sc, cc, se, ce;
+  sincos(f32_to_f64(chi), &sc, &cc);
+  sincospi(2.0 * u53(w.z, w.w), &se, &ce);
+  const double g2s = use ? g2 : 1.0;
+  const double ig = rsqrt(g2s);
+  double o[3];
+  deflect(use ? ux : 1.0, use ? uy : 0.0, use ? uz : 0.0, g2s * ig, ig, cc, sc, ce, se, o);
+  if (!use) o[0] = o[1] = o[2] = 0.0;
+  if (live) {
+    const double cx = 0.5 * (xi + xj), cy = 0.5 * (yi + yj), cz = 0.5 * (zi + zj);
+    __stcg(a.vx + q.x, cx + 0.5 * o[0]); __stcg(a.vy + q.x, cy + 0.5 * o[1]); __stcg(a.vz + q.x, cz + 0.5 * o[2]);
+    __stcg(a.vx + q.y, cx - 0.5 * o[0]); __stcg(a.vy + q.y, cy - 0.5 * o[1]); __stcg(a.vz + q.y, cz - 0.5 * o[2]);
   }
-  const double cx = 0.5 * (xi + xj), cy = 0.5 * (yi + yj), cz = 0.5 * (zi + zj);
-  __stcg(a.vx + q.x, cx + 0.5 * o[0]); __stcg(a.vy + q.x, cy + 0.5 * o[1]); __stcg(a.vz + q.x, cz + 0.5 * o[2]);
-  __stcg(a.vx + q.y, cx - 0.5 * o[0]); __stcg(a.vy + q.y, cy - 0.5 * o[1]); __stcg(a.vz + q.y, cz - 0.5 * o[2]);
 }
 
 // Pairs are claimed 32 at a time per warp, in round-major order, from one
@@ -521,15 +645,16 @@ __global__ void __launch_bounds__(128, 4) k_collide_jager(PotDev P, JagerArgs a)
     int32_t p0, p1;
     if (!unit_range(a.ro, R, 32, r, base, unit, &p0, &p1)) break;
     const int32_t p = p0 + lane;
+    const bool valid = p < p1;
+    int4 q = make_int4(0, 0, 0, 0);
     bool ok = true;
-    if (p < p1) {
-      const int4 q = a.pairs[p];
+    if (valid) {
+      q = a.pairs[p];
       ok = wait_deps(a.done, q.x, q.y, a.deps[p], a.bar + 2, a.status);
-      if (ok) {
-        collide_pair(P, a, p, q);
-        release_pair(a.done, q.x, q.y, (unsigned)(r + 1));
-      }
     }
+    __syncwarp();
+    collide_pair(P, a, p, q, valid && ok);
+    if (valid && ok) release_pair(a.done, q.x, q.y, (unsigned)(r + 1));
     if (!__all_sync(0xffffffffu, ok)) break;
   }
 }
@@ -624,11 +749,27 @@ __global__ void __launch_bounds__(128) k_harvest(PotDev P, int64_t n, const doub
 }
 
 
+// Self test of the refinement's FP64 helpers against CUDA's own routines:
+// which 0: exp64, 1: exp, 2: rcp64, 3: 1.0 / x.
+__global__ void k_selftest_math(Exp64 E, int which, int64_t n, const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const double v = x[q];
+    y[q] = which == 0 ? exp64(E, v) : which == 1 ? exp(v) : which == 2 ? rcp64(v) : 1.0 / v;
+  }
+}
+
 static unsigned blocks_n(int64_t n, int threads, int cap) {
   int64_t b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
   if (b > cap) b = cap;
   return (unsigned)b;
+}
+
+int launch_selftest_math(Ctx* c, int which, int64_t n, const double* x, double* y, cudaStream_t s) {
+  if (n == 0) return 0;
+  k_selftest_math<<<blocks_n(n, 256, sm_count(c) * 8), 256, 0, s>>>(make_exp64(), which, n, x, y);
+  count_launches(c, 1);
+  return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
 }
 
 int launch_jager_chi(Ctx* c, const dsmc_gas_t& gas, const dsmc_potential_t& pot, int n_nodes,

@@ -151,6 +151,9 @@ def load(build: bool = True):
             "dsmc_mlp_forward": (C.c_int, [vp, P(Mlp), vp, vp, i64, vp, vp, vp]),
             "dsmc_tc_selftest": (C.c_int, [vp, i32, i32, i32, vp, vp, vp, vp]),
             "dsmc_selftest_timeout": (C.c_int, [vp, i32, u64, vp]),
+            "dsmc_selftest_peak_ops": (i64, [i32, i32]),
+            "dsmc_selftest_math": (C.c_int, [vp, i32, i64, vp, vp, vp]),
+            "dsmc_selftest_peak": (C.c_int, [vp, i32, i32, i32, i32, vp, vp]),
             "dsmc_moment_match": (C.c_int, [vp, i32, vp, vp, vp, vp, vp, vp]),
             "dsmc_step_workspace_size": (sz, [i32, i32, i64]),
             "dsmc_step": (C.c_int, [vp, P(Gas), P(Path), P(StepBuffers), u64, vp]),
@@ -460,6 +463,24 @@ class Context:
                                                _ptr(B_bits, torch.int16), _ptr(D), _stream(stream)),
                     "tc_selftest")
         return D
+
+    def selftest_math(self, which: int, x, stream=None):
+        """dsmc_selftest_math: f(x) elementwise (float64 device tensors)."""
+        y = torch.empty_like(x)
+        self._check(self._lib.dsmc_selftest_math(self.h, which, x.numel(), _ptr(x, torch.float64), _ptr(y),
+                                                 _stream(stream)), "selftest_math")
+        return y
+
+    PEAK_KINDS = ("fp32_fma", "fp32x2_fma", "fp64_fma", "mufu_ex2")
+
+    def selftest_peak(self, which: int, blocks: int, threads: int, iters: int, sink=None, stream=None):
+        """dsmc_selftest_peak: launch one pipe-rate kernel; returns (sink, total
+        operations of the launch).  Time it with CUDA events on `stream`."""
+        if sink is None or sink.numel() < blocks * threads:
+            sink = torch.empty(blocks * threads, dtype=torch.float32, device=torch.device("cuda", self.device))
+        self._check(self._lib.dsmc_selftest_peak(self.h, which, blocks, threads, iters, _ptr(sink, torch.float32),
+                                                 _stream(stream)), "selftest_peak")
+        return sink, int(self._lib.dsmc_selftest_peak_ops(which, iters)) * blocks * threads
 
     def selftest_timeout(self, which: int, limit_ns: int = 10_000_000, stream=None):
         self._check(self._lib.dsmc_selftest_timeout(self.h, which, limit_ns, _stream(stream)),
