@@ -598,8 +598,11 @@ int dsmc_neural_operator_forward(dsmc_ctx_t* ctx, const dsmc_mlp_t* mlp, const f
  * ([n x 3] FP64), writes dL/dtheta (FP32, theta layout) to grad.  The
  * moment-matching and projection backward are closed forms; the MLP
  * backward recomputes each layer's pre-activation from the saved input of
- * that layer (no activations stored in HBM); dW accumulates per SM in
- * TMEM and the per-SM partials are summed in a fixed order. */
+ * that layer from exactly the forward's operands (the low bf16 terms of
+ * the hidden activations regenerated by running the first layers again), so
+ * the recomputed pre-activations equal the forward's bit for bit, and no
+ * activations are stored in HBM; dW accumulates per SM in TMEM and the
+ * per-SM partials are summed in a fixed order. */
 int dsmc_neural_operator_backward(dsmc_ctx_t* ctx, const dsmc_mlp_t* mlp, const float* theta, uint64_t seed,
                                   uint64_t t, int64_t n, const double* vi, const double* vj, const double* T,
                                   const double* g_vi, const double* g_vj, float* grad, void* ws,
@@ -610,6 +613,18 @@ int dsmc_train_loss_grad(dsmc_ctx_t* ctx, const dsmc_mlp_t* mlp, const float* th
                          int64_t n, const double* vi, const double* vj, const double* T, const double* vi_target,
                          const double* vj_target, float* grad, double* loss, void* ws, size_t ws_bytes,
                          void* stream);
+/* The stored-activation variant of dsmc_train_loss_grad, with no
+ * counterpart in the paper (the check of the recomputation): the forward
+ * writes every hidden layer's pre-activation accumulator (FP32, [tiles of
+ * 128 pairs x 3 layers x 128 x 128]) to `act` (device memory of at least
+ * dsmc_train_act_size(n) bytes, caller-owned) and the backward reads it back
+ * instead of recomputing it; grad and loss equal dsmc_train_loss_grad's bit
+ * for bit. */
+size_t dsmc_train_act_size(int64_t n);
+int dsmc_train_loss_grad_stored(dsmc_ctx_t* ctx, const dsmc_mlp_t* mlp, const float* theta, uint64_t seed,
+                                uint64_t t, int64_t n, const double* vi, const double* vj, const double* T,
+                                const double* vi_target, const double* vj_target, float* grad, double* loss,
+                                void* ws, size_t ws_bytes, float* act, size_t act_bytes, void* stream);
 /* Adam (Kingma & Ba 2015, Algorithm 1) on theta with moments m, v (FP32,
  * n_params each); step counts from 1.  The first n_weights entries are
  * weights: if weights_bf16 / biases are given, the updated weights are also

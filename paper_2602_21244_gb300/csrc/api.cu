@@ -505,6 +505,21 @@ int dsmc_train_loss_grad(dsmc_ctx_t* c, const dsmc_mlp_t* mlp, const float* thet
                             nullptr, nullptr, grad, loss, ws, ws_bytes, S(stream));
 }
 
+size_t dsmc_train_act_size(int64_t n) { return n > 0 ? dsmc::train_act_bytes(n) : 0; }
+
+int dsmc_train_loss_grad_stored(dsmc_ctx_t* c, const dsmc_mlp_t* mlp, const float* theta, uint64_t seed, uint64_t t,
+                                int64_t n, const double* vi, const double* vj, const double* T,
+                                const double* vi_target, const double* vj_target, float* grad, double* loss,
+                                void* ws, size_t ws_bytes, float* act, size_t act_bytes, void* stream) {
+  CHECK_CTX(c);
+  if (int rc = check_train(c, mlp, n)) return rc;
+  REQUIRE(c, theta && grad && loss && ws && (n == 0 || (vi && vj && T && vi_target && vj_target && act)),
+          "train_loss_grad_stored: null pointer");
+  REQUIRE(c, act_bytes >= dsmc_train_act_size(n), "train_loss_grad_stored: activation buffer too small");
+  return dsmc::launch_train(c, *mlp, 2, seed, t, n, theta, vi, vj, T, vi_target, vj_target, nullptr, nullptr,
+                            nullptr, nullptr, grad, loss, ws, ws_bytes, S(stream), act);
+}
+
 int dsmc_adam_step(dsmc_ctx_t* c, int32_t n_params, int32_t n_weights, const float* grad, float* theta,
                    float* m, float* v, int64_t step, float lr, float beta1, float beta2, float eps,
                    uint16_t* weights_bf16, float* biases, void* stream) {

@@ -46,6 +46,18 @@ __device__ __forceinline__ double u53(uint32_t a, uint32_t b) {
   return (double)x * (1.0 / 9007199254740992.0);
 }
 
+// the same uniform built on the integer pipe (no FP64 conversion): the
+// 53-bit integer x = (a << 32 | b) >> 11 normalised into the fraction of a
+// double, x 2^-53 exactly
+__device__ __forceinline__ double u53_int(uint32_t a, uint32_t b) {
+  const uint64_t x = ((((uint64_t)a) << 32) | b) >> 11;
+  if (x == 0) return 0.0;
+  const int lz = __clzll((long long)x) - 11;         // leading 1 moved to bit 52
+  const uint64_t m = (x << lz) & 0xFFFFFFFFFFFFFull;
+  const uint64_t e = (uint64_t)(1023 - 1 - lz);       // x 2^-53 = 1.m 2^(-1 - lz)
+  return __longlong_as_double((long long)((e << 52) | m));
+}
+
 // the same uniform rounded to FP32 (within 2^-23 relative of u53(a, b);
 // the low word matters below 2^-8)
 __device__ __forceinline__ float u_f32(uint32_t a, uint32_t b) {
@@ -344,7 +356,8 @@ size_t train_ws(int sms);
 int launch_train(Ctx* c, const dsmc_mlp_t& mlp, int mode, uint64_t seed, uint64_t t, int64_t n,
                  const float* theta, const double* vi, const double* vj, const double* T,
                  const double* ti, const double* tj, const double* gi, const double* gj, double* oi, double* oj,
-                 float* grad, double* loss, void* ws, size_t ws_bytes, cudaStream_t s);
+                 float* grad, double* loss, void* ws, size_t ws_bytes, cudaStream_t s, float* act = nullptr);
+size_t train_act_bytes(int64_t n);
 int launch_adam(Ctx* c, int n_w, int n_b, const float* grad, float* master, float* m, float* v, uint16_t* w,
                 float* bias, float lr, double b1, double b2, double eps, int64_t step, cudaStream_t s);
 

@@ -83,6 +83,8 @@ struct PotDev {
   double Cd[6];       // (6 + 2n) C_n
   double Cdd[6];      // (6 + 2n)(7 + 2n) C_n
   float D[17];        // P(r) = sum_p D_p r^-p,  e^{-beta r} P(r) = sum_n C_2n r^-2n e^{-x} S_2n(x)
+  float Dlo[17];      // D_p - D[p] (D as an FP32 pair)
+  float Clo[6];       // C_2n - fC[n]
   Exp64 ex64;         // constants of the FP64 exponential of the refinement
   float sigma0;       // zero crossing of V (F > 0 above max(b, sigma0))
   float orbit_E;      // below this energy use the fine bracket scan
@@ -95,6 +97,32 @@ struct PotDev {
   int n_low;
   float s_node[2 * kMaxNodes], w_node[2 * kMaxNodes];
 };
+
+// ---------------------------------------------------------------- FP32 pairs
+// A value as an unevaluated sum hi + lo of two FP32 numbers (about 44
+// significant bits), for products that need more than FP32 but not the
+// FP64 pipe (about 1/64 of the FP32 rate on GB300): the exact product of two
+// FP32 numbers from one FMA (Dekker / Kahan's error-free transformation),
+// the cross terms added in FP32, the sum renormalised.
+struct F2 {
+  float hi, lo;
+};
+__device__ __forceinline__ F2 f2_mul(F2 a, F2 b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float s = p + e;
+  return F2{s, e - (s - p)};
+}
+// the FP32 rounding of (a_hi + a_lo)(b_hi + b_lo)
+__device__ __forceinline__ float f2_mul_round(float ah, float al, F2 b) {
+  const float p = ah * b.hi;
+  float e = fmaf(ah, b.hi, -p);
+  e = fmaf(ah, b.lo, e);
+  e = fmaf(al, b.hi, e);
+  return p + e;
+}
 
 // ---------------------------------------------------------------- FP64 potential
 // V and V' in FP64, with the damped dispersion expanded into
@@ -192,6 +220,16 @@ __device__ __forceinline__ double rcp64_1(double x) {
 __device__ __forceinline__ double rcp64(double x) {
   const double r = rcp64_1(x);
   return fma(r, fma(-x, r, 1.0), r);
+}
+
+// sqrt(x) for x in [0, 1]: y = x / sqrt(x) from the FP32 reciprocal square
+// root, then one FP64 Newton step on y^2 = x (relative error about 2^-46,
+// far below the FP32 rounding the impact parameter then takes).  x = 0 -> 0.
+__device__ __forceinline__ double sqrt64(double x) {
+  const float xf = f64_to_f32(x);
+  if (!(xf > 0.f)) return 0.0;
+  const double y = x * f32_to_f64(rsqrtf(xf));
+  return fma(0.5 * (x - y * y), f32_to_f64(rsqrtf(xf)), y);
 }
 
 // ---------------------------------------------------------------- FP32 potential
@@ -381,14 +419,18 @@ __device__ float chi_device(const PotDev& P, float b_in, float E) {
   float d[17], qn[6], Rep0 = 0.f, e0 = 0.f, P0 = 0.f, Vc0 = 0.f, powk = 0.f;
   const bool core = P.kind == 0 && r0 < P.frc;
   if (P.kind == 0 && !core) {
-    // d_p = D_p r0^-p and the dispersion coefficients C_2n r0^-2n from the
-    // FP64 powers of 1/r0, each rounded once to FP32 (integer pipe)
-    double pw = 1.0;
+    // d_p = D_p r0^-p and the dispersion coefficients C_2n r0^-2n, each the
+    // FP32 rounding of a product formed with about 44 bits: the powers of
+    // 1/r0 as FP32 pairs (1/r0 split from its FP64 value), the coefficients
+    // as FP32 pairs
+    const float ih = f64_to_f32(ird);
+    const F2 ir2 = F2{ih, f64_to_f32(ird - f32_to_f64(ih))};
+    F2 pw = F2{1.f, 0.f};
 #pragma unroll
     for (int p = 0; p <= 16; ++p) {
-      d[p] = f64_to_f32(P.Dd[p] * pw);
-      if (p >= 6 && (p & 1) == 0) qn[(p - 6) >> 1] = f64_to_f32(P.C[(p - 6) >> 1] * pw);
-      pw *= ird;
+      d[p] = p == 0 ? P.D[0] : f2_mul_round(P.D[p], P.Dlo[p], pw);
+      if (p >= 6 && (p & 1) == 0) qn[(p - 6) >> 1] = f2_mul_round(P.fC[(p - 6) >> 1], P.Clo[(p - 6) >> 1], pw);
+      pw = p == 0 ? ir2 : f2_mul(pw, ir2);
     }
     P0 = f64_to_f32(Tp.Pr);   // P(r0), carried from the last FP64 evaluation
     Rep0 = f64_to_f32(Tp.rep);
@@ -491,11 +533,13 @@ static PotDev make_pot(const dsmc_gas_t& gas, const dsmc_potential_t& p, int n_n
       s += p.C[n - 3] * t;
     }
     P.D[pp] = (float)s;
+    P.Dlo[pp] = (float)(s - (double)P.D[pp]);
     P.Dd[pp] = s;
   }
   for (int pp = 0; pp < 16; ++pp) P.Dp[pp] = (pp + 1) * P.Dd[pp + 1];
   for (int pp = 0; pp < 16; ++pp) P.Dpp[pp] = (double)(pp + 1) * (pp + 2) * P.Dd[pp + 1];
   for (int q = 0; q < 6; ++q) P.Cd[q] = (6 + 2 * q) * p.C[q];
+  for (int q = 0; q < 6; ++q) P.Clo[q] = (float)(p.C[q] - (double)P.fC[q]);
   for (int q = 0; q < 6; ++q) P.Cdd[q] = (double)(6 + 2 * q) * (7 + 2 * q) * p.C[q];
   if (p.kind == 0) {
     // sigma0: outermost zero of V (bisection on a sign change found inward from 4 R_eps)
@@ -604,7 +648,7 @@ __device__ __forceinline__ void collide_pair(const PotDev& P, const JagerArgs& a
   const double g2 = ux * ux + uy * uy + uz * uz;
   const bool use = live && g2 > 0.0;
   const u32x4 w = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_JAGER);
-  const float b = use ? (float)(a.bmax_A * sqrt(u53(w.x, w.y))) : 1.f;
+  const float b = use ? f64_to_f32(a.bmax_A * sqrt64(u53_int(w.x, w.y))) : 1.f;
   const float E = use ? P.mass_over_4k * (float)g2 : 1.0e4f;
   const float chi_c = chi_device<true>(P, b, E);
   const float chi = use ? chi_c : 0.f;
@@ -612,7 +656,7 @@ __device__ __forceinline__ void collide_pair(const PotDev& P, const JagerArgs& a
   __syncwarp();
   double sc, cc, se, ce;
   sincos(f32_to_f64(chi), &sc, &cc);
-  sincospi(2.0 * u53(w.z, w.w), &se, &ce);
+  sincospi(2.0 * u53_int(w.z, w.w), &se, &ce);
   const double g2s = use ? g2 : 1.0;
   const double ig = rsqrt(g2s);
   double o[3];

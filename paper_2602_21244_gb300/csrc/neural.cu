@@ -40,6 +40,21 @@ constexpr int kKin = 32;         // input as two bf16 terms: [hi (16) | lo (16)]
 constexpr int kNout = 16;        // padded output width
 constexpr int kMaxHidden = 4;
 constexpr int kStashWords = 16;  // per-row pair data handed from builder to updater threads
+// columns of a hidden layer's epilogue per TMEM read (16: four independent
+// SiLU chains of a thread per wait; 32 spilled at the 128-register cap of a
+// 512-thread CTA and measured slower, 2.57 against 2.51 ms per collide)
+constexpr int kEpiW = 16;
+
+template <int W>
+__device__ __forceinline__ void tmem_ld_async(uint32_t taddr, uint32_t* r) {
+  if (W == 32) tc::ld32_async(taddr, r);
+  else tc::ld16_async(taddr, r);
+}
+template <int W>
+__device__ __forceinline__ void tmem_wait_ld(uint32_t* r) {
+  if (W == 32) tc::wait_ld32(r);
+  else tc::wait_ld16(r);
+}
 
 // dynamic shared memory layout (bytes).  The weights are shared; each of the
 // `slots` tile slots (one per warp group) has its own X, activation tiles,
@@ -163,8 +178,7 @@ __device__ __forceinline__ void preload_bias(char* smem, const MlpLayout& L, con
 // bf16 weights, summed in FP32), its column-group partials combined through
 // shared memory -- no tensor-core pass, barrier and TMEM read for 3 outputs.
 __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, const Group& q,
-                         uint32_t tmem, uint32_t& phase, float y[3], int* status,
-                         unsigned* cursor = nullptr, volatile int* claim = nullptr) {
+                         uint32_t tmem, uint32_t& phase, float y[3], int* status, uint32_t xs) {
   // every layer's accumulator starts from its bias, stored into it by the
   // previous epilogue (by preload_bias before the first tile)
   const int gw = q.t >> 5;
@@ -174,7 +188,6 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
   uint64_t* mbar = (uint64_t*)(smem + L.mbar) + q.g;
   volatile int* flag = (volatile int*)(smem + L.flag) + q.g;
   const uint32_t sbase = tc::smem_u32(smem);
-  const uint32_t xs = L.x(q.g);
   const uint32_t acc = tmem + (uint32_t)(q.g * 2 * kWidth);
   // the next layer's A operand: hi in columns [0, 64) of this region, lo in [64, 128)
   const uint32_t a_hi = acc + kWidth, a_lo = a_hi + kWidth / 2;
@@ -205,7 +218,6 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
           tc::mma_bf16_ta(acc, a_lo + 8u * s, tc::sdesc(sbase + wb + 256u * s, 128, 2048), idesc, 1);
       }
       tc::commit(mbar);
-      if (l == 0 && cursor) *claim = (int)atomicAdd(cursor, 1u);
       *flag = tc::mbar_wait(mbar, phase, status, kBarrierLimitNs) ? 1 : 0;
     }
     group_sync(q);
@@ -218,60 +230,67 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
     const float* bn = bs + (last ? 0 : l + 1) * kWidth;
     // this warp's columns in 16-wide pieces, the TMEM read of the next piece
     // in flight while the current one is processed
-    const int cbeg = cg * cols, npieces = cols / 16;
-    uint32_t ra[16], rb[16];
-    tc::ld16_async(lane_tm + (uint32_t)cbeg, ra);
-    tc::wait_ld16(ra);
+    const int cbeg = cg * cols, npieces = cols / kEpiW;
+    uint32_t ra[kEpiW], rb[kEpiW];
+    tmem_ld_async<kEpiW>(lane_tm + (uint32_t)cbeg, ra);
+    tmem_wait_ld<kEpiW>(ra);
 #pragma unroll 1
     for (int pc = 0; pc < npieces; pc += 2) {
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
+        if (pc + half >= npieces) break;
         uint32_t* cur = half ? rb : ra;
         uint32_t* nxt = half ? ra : rb;
-        const int c0 = cbeg + 16 * (pc + half);
+        const int c0 = cbeg + kEpiW * (pc + half);
         const bool more = pc + half + 1 < npieces;
-        if (more) tc::ld16_async(lane_tm + (uint32_t)(c0 + 16), nxt);
+        if (more) tmem_ld_async<kEpiW>(lane_tm + (uint32_t)(c0 + kEpiW), nxt);
         // values in packed pairs (columns 2k, 2k + 1; the bias is already in
         // them): activation products, residuals and output-layer FMAs run two
         // per instruction
-        float2 v[8];
+        float2 v[kEpiW / 2];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = make_float2(__uint_as_float(cur[2 * k]), __uint_as_float(cur[2 * k + 1]));
-        // these 16 columns are read: they now receive the next use's bias
-        tc::st16_async(lane_tm + (uint32_t)c0, (const uint32_t*)(bn + c0));
+        for (int k = 0; k < kEpiW / 2; ++k)
+          v[k] = make_float2(__uint_as_float(cur[2 * k]), __uint_as_float(cur[2 * k + 1]));
+        // these columns are read: they now receive the next use's bias
+#pragma unroll
+        for (int h = 0; h < kEpiW / 16; ++h)
+          tc::st16_async(lane_tm + (uint32_t)(c0 + 16 * h), (const uint32_t*)(bn + c0 + 16 * h));
         if (sh.act == 0) {
 #pragma unroll
-          for (int k = 0; k < 8; k += 2) tc::silu4x2(v[k], v[k + 1]);
+          for (int k = 0; k < kEpiW / 2; k += 2) tc::silu4x2(v[k], v[k + 1]);
         } else {
 #pragma unroll
-          for (int k = 0; k < 8; ++k) v[k] = make_float2(act_f(sh.act, v[k].x), act_f(sh.act, v[k].y));
+          for (int k = 0; k < kEpiW / 2; ++k) v[k] = make_float2(act_f(sh.act, v[k].x), act_f(sh.act, v[k].y));
         }
         if (last) {
           const float2* w0 = (const float2*)(wo + c0);
           const float2* w1 = (const float2*)(wo + kWidth + c0);
           const float2* w2 = (const float2*)(wo + 2 * kWidth + c0);
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
+          for (int k = 0; k < kEpiW / 2; ++k) {
             yq0 = __ffma2_rn(v[k], w0[k], yq0);
             yq1 = __ffma2_rn(v[k], w1[k], yq1);
             yq2 = __ffma2_rn(v[k], w2[k], yq2);
           }
         } else {
-          uint32_t pk[8], lo[8];
+          uint32_t pk[kEpiW / 2], lo[kEpiW / 2];
           const float2 m1 = make_float2(-1.f, -1.f);
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
+          for (int k = 0; k < kEpiW / 2; ++k) {
             pk[k] = tc::pack_bf16x2(v[k].x, v[k].y);
             // a - hi is exact (hi is a rounding of a); as an FMA with -1
             const float2 r = __ffma2_rn(make_float2(__uint_as_float(pk[k] << 16), __uint_as_float(pk[k] & 0xFFFF0000u)),
                                         m1, v[k]);
             lo[k] = tc::pack_bf16x2(r.x, r.y);
           }
-          // columns c0 .. c0 + 15 of this row: 8 TMEM columns per term
-          tc::st8_async(a_hi + lane_q + (uint32_t)(c0 >> 1), pk);
-          tc::st8_async(a_lo + lane_q + (uint32_t)(c0 >> 1), lo);
+          // columns c0 .. c0 + kEpiW - 1 of this row: kEpiW / 2 TMEM columns per term
+#pragma unroll
+          for (int h = 0; h < kEpiW / 16; ++h) {
+            tc::st8_async(a_hi + lane_q + (uint32_t)((c0 >> 1) + 8 * h), pk + 8 * h);
+            tc::st8_async(a_lo + lane_q + (uint32_t)((c0 >> 1) + 8 * h), lo + 8 * h);
+          }
         }
-        if (more) tc::wait_ld16(nxt);
+        if (more) tmem_wait_ld<kEpiW>(nxt);
       }
     }
     // this thread's A operand and bias stores complete before the next MMA
@@ -307,8 +326,8 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
 // Write row t of the X tile from 16 FP32 features (padding zeros included):
 // columns 0..15 hold hi = bf16(x), columns 16..31 lo = bf16(x - hi), so the
 // first layer sees x to about 16 significant bits through bf16 operands.
-__device__ __forceinline__ void write_x_row(char* smem, const MlpLayout& L, int g, int t, const float* f) {
-  const uint32_t sb = tc::smem_u32(smem) + L.x(g);
+__device__ __forceinline__ void write_x_row(char* smem, uint32_t xoff, int t, const float* f) {
+  const uint32_t sb = tc::smem_u32(smem) + xoff;
   uint32_t hi[8], lo[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
@@ -371,12 +390,12 @@ __global__ void __launch_bounds__(kThreads) k_mlp_forward(MlpShape sh, const uin
       for (int k = 0; k < 16; ++k) f[k] = 0.f;
       if (row < n)
         for (int k = 0; k < sh.d_in; ++k) f[k] = x[row * sh.d_in + k];
-      write_x_row(smem, L, q.g, q.t, f);
+      write_x_row(smem, L.x(q.g), q.t, f);
       tc::fence_async_smem();
     }
     group_sync(q);
     float o[3];
-    if (!mlp_tile(smem, L, sh, q, tmem, phase, o, status)) { alive = false; break; }
+    if (!mlp_tile(smem, L, sh, q, tmem, phase, o, status, L.x(q.g))) { alive = false; break; }
     if (q.t < kTileM && row < n) { y[3 * row] = o[0]; y[3 * row + 1] = o[1]; y[3 * row + 2] = o[2]; }
   }
   (void)alive;
@@ -501,8 +520,8 @@ __device__ __forceinline__ void box_muller_f(uint32_t w1, uint32_t w2, float* z0
 // into the group's X tile and stash what the pair update needs -- p, the
 // particle slots and the six velocity components -- in word w of the row at
 // stash[w * 128 + row] (shared memory).  p < 0 marks a padding row.
-__device__ __forceinline__ void build_row(char* smem, const MlpLayout& L, const MlpShape& sh,
-                                          const NeuralArgs& a, int g, int row, int32_t p, uint32_t* stash) {
+__device__ __forceinline__ void build_row(char* smem, uint32_t xoff, volatile int* fail, const MlpShape& sh,
+                                          const NeuralArgs& a, int row, int32_t p, uint32_t* stash) {
   float f[16];
 #pragma unroll
   for (int c = 0; c < 16; ++c) f[c] = 0.f;
@@ -515,7 +534,7 @@ __device__ __forceinline__ void build_row(char* smem, const MlpLayout& L, const 
     q = a.pairs[p];
     // the previous pairs of both particles must be done (bounded wait)
     if (!wait_deps(a.done, q.x, q.y, a.deps[p], a.bar + 2, a.status)) {
-      *((volatile int*)(smem + L.fail) + g) = 1;
+      *fail = 1;
       p = -1;
     }
   }
@@ -547,7 +566,7 @@ __device__ __forceinline__ void build_row(char* smem, const MlpLayout& L, const 
       st[5 + 2 * c] = __double2hiint(v[c]);
     }
   }
-  write_x_row(smem, L, g, row, f);
+  write_x_row(smem, xoff, row, f);
   tc::fence_async_smem();
 #pragma unroll
   for (int c = 0; c < kStashWords; ++c) stash[c * kTileM + row] = st[c];
@@ -604,63 +623,214 @@ __device__ __forceinline__ void update_row(const NeuralArgs& a, const float y[3]
   release_pair(a.done, qi, qj, round1);
 }
 
-// Tiles of 128 pairs of one round are claimed in round-major order from a
-// global cursor, one group at a time (no grid-wide barrier between rounds:
-// a row waits, bounded, until the previous pairs of its two particles are
-// done).  Within a group, threads 128..255 (the builders) prepare the next
-// tile's input rows while threads 0..127 (the updaters) apply this tile's
-// pair updates and stamp its particles done, the per-row data passing
-// through two alternating shared-memory stashes; so the global loads of the
-// next tile overlap the FP64 update of this one.
-__global__ void __launch_bounds__(kThreads) k_collide_neural(MlpShape sh, const uint16_t* __restrict__ w,
-                                                           const float* __restrict__ bias, NeuralArgs a) {
+// ---------------------------------------------------------------- pipelined collide
+// A CTA of 768 threads: two MLP warp groups of 8 warps (threads 0..511, TMEM
+// columns and tile work as in mlp_tile), four builder warps (512..639) and
+// four updater warps (640..767).  Tiles of 128 pairs of one round are
+// claimed by the builders from a global cursor in round-major order and
+// handed to the two MLP groups alternately through three buffers per group
+// (the input tile X, the per-row pair data the update needs, the MLP output
+// y, the tile's pair range and round): builders build tile k + 2 (waiting,
+// bounded, until the previous pairs of its particles are done) while an MLP
+// group runs the layers of tile k + 1 and the updaters apply the pair updates
+// of tile k and stamp its particles done.  So the MLP groups never wait for
+// the latency-bound build or the FP64 update.  Hand-offs are mbarriers:
+// built (128 builder arrivals), ydone (the 128 threads that hold y), freed
+// (128 updater arrivals); each buffer is reused every third tile of its
+// group.  No wait can be circular: a build only waits on tiles claimed
+// earlier, whose MLP and update stages never wait on a later build.  Every
+// wait is bounded and ends early once any role of the CTA (or a dependency
+// wait of any CTA) has failed.
+constexpr int kPipeThreads = 768;
+constexpr int kPipeBufs = 3;
+constexpr int kBuildBase = 512, kUpdateBase = 640, kRoleThreads = 128;
+
+struct PipeLayout {
+  MlpLayout m;        // weights, biases, per-group MMA barriers, TMEM pointer, column-group partials
+  uint32_t x0, st0, y0, info0, bars, abort, bcast, total;
+  __host__ __device__ uint32_t buf(int g, int b) const { return (uint32_t)(g * kPipeBufs + b); }
+  __host__ __device__ uint32_t x(int g, int b) const { return x0 + buf(g, b) * (uint32_t)(kTileM * kKin * 2); }
+  __host__ __device__ uint32_t st(int g, int b) const { return st0 + buf(g, b) * (uint32_t)(kStashWords * kTileM * 4); }
+  __host__ __device__ uint32_t y(int g, int b) const { return y0 + buf(g, b) * (uint32_t)(kTileM * 3 * 4); }
+  __host__ __device__ uint32_t info(int g, int b) const { return info0 + buf(g, b) * 16u; }
+  // mbarriers: built[6], ydone[6], freed[6]
+  __host__ __device__ uint32_t built(int g, int b) const { return bars + buf(g, b) * 8u; }
+  __host__ __device__ uint32_t ydone(int g, int b) const { return bars + (6u + buf(g, b)) * 8u; }
+  __host__ __device__ uint32_t freed(int g, int b) const { return bars + (12u + buf(g, b)) * 8u; }
+};
+
+__host__ __device__ inline PipeLayout pipe_layout(int n_hidden) {
+  PipeLayout P;
+  MlpLayout& L = P.m;
+  L.slots = 2;
+  L.w_out = 0;
+  L.w_in = L.w_out + 3 * kWidth * 4;
+  L.w_sq = L.w_in + kWidth * kKin * 2;
+  L.slot0 = 0;                                   // (the X tiles are per buffer below)
+  L.slot_bytes = 0;
+  L.bias = L.w_sq + (uint32_t)(n_hidden - 1) * kWidth * kWidth * 2;
+  L.ybuf = L.bias + (uint32_t)(n_hidden * kWidth + kNout) * 4;
+  L.ybuf_bytes = (uint32_t)(256 / kTileM - 1) * kTileM * 3 * 4;   // 8-warp groups: 2 column groups
+  L.mbar = (L.ybuf + 2 * L.ybuf_bytes + 15u) & ~15u;
+  L.tptr = L.mbar + 16;
+  L.flag = L.tptr + 4;
+  L.claim = L.flag + 8;
+  L.fail = L.claim + 8;
+  L.stash = 0;
+  P.x0 = (L.fail + 8 + 127u) & ~127u;            // X tiles: K-major core matrices
+  P.st0 = P.x0 + 2 * kPipeBufs * kTileM * kKin * 2;
+  P.y0 = P.st0 + 2 * kPipeBufs * kStashWords * kTileM * 4;
+  P.info0 = P.y0 + 2 * kPipeBufs * kTileM * 3 * 4;
+  P.bars = (P.info0 + 2 * kPipeBufs * 16 + 7u) & ~7u;
+  P.abort = P.bars + 18 * 8;
+  P.bcast = P.abort + 16;
+  P.total = P.bcast + 16 + 256;
+  L.total = P.total;
+  return P;
+}
+
+__device__ __forceinline__ bool pipe_aborted(char* smem, const PipeLayout& P, const NeuralArgs& a) {
+  return *(volatile int*)(smem + P.abort) != 0 || ld_relaxed(a.bar + 2) != 0;
+}
+__device__ __forceinline__ void pipe_abort(char* smem, const PipeLayout& P, const NeuralArgs& a) {
+  *(volatile int*)(smem + P.abort) = 1;
+  atomicExch(a.bar + 2, 1u);
+}
+
+// Bounded wait for phase `parity` of an mbarrier, ending early once the CTA
+// or the grid has aborted; false on timeout or abort (a timeout records
+// DSMC_ERR_TIMEOUT and aborts).
+__device__ __forceinline__ bool pipe_wait(char* smem, const PipeLayout& P, const NeuralArgs& a, uint32_t bar_off,
+                                          uint32_t parity) {
+  uint64_t* mb = (uint64_t*)(smem + bar_off);
+  if (tc::mbar_try_wait(mb, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (;;) {
+    if (tc::mbar_try_wait_hint(mb, parity, 2000u)) return true;
+    if (pipe_aborted(smem, P, a)) return false;
+    if (globaltimer_ns() - t0 > kBarrierLimitNs) {
+      set_status(a.status, DSMC_ERR_TIMEOUT);
+      pipe_abort(smem, P, a);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(char* smem, uint32_t bar_off) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(smem + bar_off)) : "memory");
+}
+
+// AND of a predicate over the `n` threads of named barrier `id`
+__device__ __forceinline__ bool role_all(int id, int n, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+      "barrier.red.and.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void role_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
+__global__ void __launch_bounds__(kPipeThreads, 1) k_collide_neural(MlpShape sh, const uint16_t* __restrict__ w,
+                                                                 const float* __restrict__ bias, NeuralArgs a) {
   if (a.step_dev) a.step = *a.step_dev;
   extern __shared__ __align__(1024) char smem[];
-  const MlpLayout L = mlp_layout(sh.n_hidden, sh.slots);
+  const PipeLayout P = pipe_layout(sh.n_hidden);
+  const MlpLayout& L = P.m;
   load_weights(smem, L, sh, w, bias);
-  const uint32_t tmem = cta_setup(smem, L);
-  const Group gq = my_group(L.slots);
-  preload_bias(smem, L, gq, tmem);
-  uint32_t phase = 0;
-  const int t = gq.t;
-  const bool builder = t >= kTileM && t < 2 * kTileM, updater = t < kTileM;
-  // the group's two alternating stashes (builder -> updater)
-  uint32_t* stash0 = (uint32_t*)(smem + L.stash) + (size_t)gq.g * 2 * kStashWords * kTileM;
-  volatile int* claim = (volatile int*)(smem + L.claim) + gq.g;
-  volatile int* fail = (volatile int*)(smem + L.fail) + gq.g;
-  const int R = a.info->n_rounds;
-  int r = 0;            // round of the last unit mapped (group-uniform)
-  int64_t base = 0;     // first unit of round r
-  if (t == 0) { *claim = (int)atomicAdd(a.bar + 3, 1u); *fail = 0; }
-  group_sync(gq);
-  int32_t p0 = 0, p1 = 0;
-  bool have = unit_range(a.ro, R, kTileM, r, base, (unsigned)*claim, &p0, &p1);
-  int r_cur = r;
-  if (have) {
-    if (builder) build_row(smem, L, sh, a, gq.g, t - kTileM, p0 + (t - kTileM) < p1 ? p0 + (t - kTileM) : -1, stash0);
-    tc::fence_before();
-    group_sync(gq);
-    if (*fail) have = false;
-  }
-  uint32_t buf = 0;
-  while (have) {
-    float y[3];
-    // the leader claims the next unit while the first layer's MMA runs (read
-    // after the tile's barriers)
-    if (!mlp_tile(smem, L, sh, gq, tmem, phase, y, a.status, a.bar + 3, claim)) break;
-    int32_t n0 = 0, n1 = 0;
-    const bool have_next = unit_range(a.ro, R, kTileM, r, base, (unsigned)*claim, &n0, &n1);
-    if (builder && have_next) {
-      const int32_t p = n0 + (t - kTileM);
-      build_row(smem, L, sh, a, gq.g, t - kTileM, p < n1 ? p : -1, stash0 + (buf ^ 1u) * kStashWords * kTileM);
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 6; ++q) {
+      tc::mbar_init((uint64_t*)(smem + P.bars) + q, kRoleThreads);        // built
+      tc::mbar_init((uint64_t*)(smem + P.bars) + 6 + q, kRoleThreads);    // ydone
+      tc::mbar_init((uint64_t*)(smem + P.bars) + 12 + q, kRoleThreads);   // freed
     }
-    if (updater) update_row(a, y, stash0 + buf * kStashWords * kTileM, t, (unsigned)(r_cur + 1));
+    *(volatile int*)(smem + P.abort) = 0;
+  }
+  const uint32_t tmem = cta_setup(smem, L);   // TMEM (512 columns), per-group MMA barriers; CTA-wide barrier
+  const int R = a.info->n_rounds;
+  const int t = threadIdx.x;
+  if (t < kBuildBase) {
+    // ------------------------------------------------ MLP groups
+    const Group q{t / 256, 2, t % 256, 256};
+    preload_bias(smem, L, q, tmem);
     tc::fence_before();
-    group_sync(gq);
+    group_sync(q);
     tc::fence_after();
-    if (*fail) break;
-    buf ^= 1u;
-    p0 = n0; p1 = n1; r_cur = r; have = have_next;
+    uint32_t phase = 0;
+    const int row = (((q.t >> 5) & 3) << 5) | (q.t & 31);
+    const bool yrow = q.t < kTileM;   // column group 0: holds the row's output
+    for (int kk = 0;; ++kk) {
+      const int b = kk % kPipeBufs;
+      const bool ok = role_all(1 + q.g, 256, pipe_wait(smem, P, a, P.built(q.g, b), (uint32_t)(kk / kPipeBufs) & 1u));
+      if (!ok) break;
+      tc::fence_after();
+      const int end = ((volatile int*)(smem + P.info(q.g, b)))[3];
+      if (end) {
+        if (yrow) mbar_arrive(smem, P.ydone(q.g, b));
+        break;
+      }
+      float y[3];
+      if (!mlp_tile(smem, L, sh, q, tmem, phase, y, a.status, P.x(q.g, b))) {
+        pipe_abort(smem, P, a);
+        break;
+      }
+      if (yrow) {
+        float* yb = (float*)(smem + P.y(q.g, b)) + 3 * row;
+        yb[0] = y[0]; yb[1] = y[1]; yb[2] = y[2];
+        mbar_arrive(smem, P.ydone(q.g, b));
+      }
+    }
+  } else if (t < kUpdateBase) {
+    // ------------------------------------------------ builders
+    const int tb = t - kBuildBase;
+    int r = 0;
+    int64_t base = 0;
+    volatile int* fail = (volatile int*)(smem + P.abort);
+    for (int k = 0;; ++k) {
+      const int g = k & 1, kk = k >> 1, b = kk % kPipeBufs;
+      bool ok = true;
+      if (kk >= kPipeBufs) ok = pipe_wait(smem, P, a, P.freed(g, b), (uint32_t)(kk / kPipeBufs - 1) & 1u);
+      if (!role_all(3, kRoleThreads, ok)) break;
+      volatile unsigned* bc = (volatile unsigned*)(smem + P.bcast) + (k & 1);
+      if (tb == 0) *bc = atomicAdd(a.bar + 3, 1u);
+      role_sync(3, kRoleThreads);
+      int32_t p0 = 0, p1 = 0;
+      const bool have = unit_range(a.ro, R, kTileM, r, base, *bc, &p0, &p1);
+      int* info = (int*)(smem + P.info(g, b));
+      if (tb == 0) { info[0] = p0; info[1] = p1; info[2] = r; info[3] = have ? 0 : 1; }
+      if (have) {
+        const int32_t p = p0 + tb;
+        build_row(smem, P.x(g, b), fail, sh, a, tb, p < p1 ? p : -1, (uint32_t*)(smem + P.st(g, b)));
+      }
+      mbar_arrive(smem, P.built(g, b));
+      if (!have) {
+        // the other group's next buffer carries the end too
+        const int k2 = k + 1, g2 = k2 & 1, kk2 = k2 >> 1, b2 = kk2 % kPipeBufs;
+        bool ok2 = true;
+        if (kk2 >= kPipeBufs) ok2 = pipe_wait(smem, P, a, P.freed(g2, b2), (uint32_t)(kk2 / kPipeBufs - 1) & 1u);
+        if (role_all(3, kRoleThreads, ok2)) {
+          if (tb == 0) ((volatile int*)(smem + P.info(g2, b2)))[3] = 1;
+          mbar_arrive(smem, P.built(g2, b2));
+        }
+        break;
+      }
+      if (*fail) pipe_abort(smem, P, a);
+    }
+  } else {
+    // ------------------------------------------------ updaters
+    const int tu = t - kUpdateBase;
+    for (int k = 0;; ++k) {
+      const int g = k & 1, kk = k >> 1, b = kk % kPipeBufs;
+      if (!role_all(4, kRoleThreads, pipe_wait(smem, P, a, P.ydone(g, b), (uint32_t)(kk / kPipeBufs) & 1u))) break;
+      const int* info = (const int*)(smem + P.info(g, b));
+      if (((volatile const int*)info)[3]) break;
+      const float* yb = (const float*)(smem + P.y(g, b)) + 3 * tu;
+      const float y[3] = {yb[0], yb[1], yb[2]};
+      update_row(a, y, (const uint32_t*)(smem + P.st(g, b)), tu, (unsigned)(info[2] + 1));
+      mbar_arrive(smem, P.freed(g, b));
+    }
   }
   cta_teardown(tmem, L);
 }
@@ -694,12 +864,13 @@ int launch_collide_neural(Ctx* c, const dsmc_gas_t& gas, const dsmc_mlp_t& mlp,
                           double* vz, float* u_out, void* ws, size_t ws_bytes, cudaStream_t s) {
   if (mlp.n_hidden > kMaxHidden) return record(c, DSMC_ERR_UNSUPPORTED, "collide_neural: n_hidden > 4");
   if (ws_bytes < collide_ws(n)) return record(c, DSMC_ERR_ARG, "collide_neural: workspace too small");
-  const MlpShape sh{mlp.d_in, mlp.n_hidden, mlp.act, mlp_slots(mlp.n_hidden)};
-  const MlpLayout L = mlp_layout(sh.n_hidden, sh.slots);
-  if (!set_smem((const void*)k_collide_neural, (int)L.total))
+  const MlpShape sh{mlp.d_in, mlp.n_hidden, mlp.act, 2};
+  const PipeLayout P = pipe_layout(sh.n_hidden);
+  if (P.total > kMaxSmem) return record(c, DSMC_ERR_UNSUPPORTED, "collide_neural: layout exceeds shared memory");
+  if (!set_smem((const void*)k_collide_neural, (int)P.total))
     return record(c, DSMC_ERR_CUDA, "collide_neural: shared-memory attribute");
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_collide_neural, kThreads, L.total) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_collide_neural, kPipeThreads, P.total) !=
           cudaSuccess || per_sm < 1)
     return record(c, DSMC_ERR_CUDA, "collide_neural: occupancy query failed");
   NeuralArgs a;
@@ -713,7 +884,7 @@ int launch_collide_neural(Ctx* c, const dsmc_gas_t& gas, const dsmc_mlp_t& mlp,
   if (cudaMemsetAsync(a.bar, 0, 4 * sizeof(unsigned), s) != cudaSuccess ||
       cudaMemsetAsync(a.done, 0, sizeof(unsigned) * (size_t)(n > 0 ? n : 1), s) != cudaSuccess)
     return DSMC_ERR_CUDA;
-  k_collide_neural<<<sm_count(c) * per_sm, kThreads, L.total, s>>>(sh, w, bias, a);
+  k_collide_neural<<<sm_count(c) * per_sm, kPipeThreads, P.total, s>>>(sh, w, bias, a);
   count_launches(c, 1);
   return cudaGetLastError() == cudaSuccess ? 0 : record(c, DSMC_ERR_CUDA, "collide_neural: launch failed");
 }

@@ -8,8 +8,13 @@
 //             y, u = y/|y|, v_r' = |v_r| u, centre-of-mass update, moment
 //             matching over pseudo-cells of 16 pairs (32 particles), loss
 //   backward  dL/dv_new -> closed-form moment-matching and projection
-//             backward -> dz4 = dL/dy; then for l = 3, 2, 1: z_l recomputed
-//             by an MMA from the saved input of layer l (single bf16 copy),
+//             backward -> dz4 = dL/dy; the activations recomputed: the low
+//             bf16 terms of h1 and h2 regenerated by running layers 1 and 2
+//             again from the saved input and high terms, then for l = 3, 2,
+//             1: z_l by an MMA from exactly the forward's operands, so every
+//             recomputed z_l equals the forward's bit for bit (the stored
+//             variant reads back the copy the forward wrote to global
+//             memory instead),
 //             dz_l = dh_l * act'(z_l), dW_l += dz_l^T h_{l-1} (MN-major
 //             operands, accumulated in TMEM across the CTA's tiles),
 //             dh_{l-1} = dz_l W_l (W_l read MN-major from the forward tile)
@@ -66,6 +71,7 @@ struct TrainArgs {
   const double *vi, *vj, *T, *ti, *tj;   // [n x 3], [n], targets [n x 3]
   const double *gi, *gj;     // mode 1: dL/dv_new [n x 3]
   double *oi, *oj;           // mode 0: v_new [n x 3]
+  float* zst;                // stored variant: z_l (accumulator, without bias) per tile, else null
   float* partial;            // [gridDim x kPartial]
   int* status;
 };
@@ -185,6 +191,53 @@ __global__ void __launch_bounds__(kNT, 1) k_train(TrainArgs a) {
     __syncthreads();
   };
 
+  // The MMA of hidden layer l + 1 (l = 1, 2) on its input as hi + lo terms:
+  // h1 = S_H1 + S_WKLO, h2 = S_H2 + S_WK (thread 0)
+  auto hidden_mma = [&](int l) {
+    const uint32_t id = tc::idesc_bf16(kT, kH);
+    const uint32_t wl = l == 1 ? S_W2 : S_W3, hhi = l == 1 ? S_H1 : S_H2, hlo = l == 1 ? S_WKLO : S_WK;
+    for (int s = 0; s < 8; ++s)
+      tc::mma_bf16(tm, kdesc(sb + hhi + 256u * s, kH), kdesc(sb + wl + 256u * s, kH), id, s > 0);
+    for (int s = 0; s < 8; ++s)
+      tc::mma_bf16(tm, kdesc(sb + hlo + 256u * s, kH), kdesc(sb + wl + 256u * s, kH), id, 1);
+  };
+  // Epilogue of hidden layer l from this thread's 32 accumulator values v:
+  // bias, activation (SiLU four values at a time on the paired FP32 pipe, as
+  // in the collide kernel's epilogue), the hi + lo split; hi and lo stored as
+  // the next layer's input (l = 0: S_H1, S_WKLO; l = 1: S_H2, S_WK; l = 2,
+  // the output layer's: S_WK, S_WKLO).  with_hi false: only the lo term
+  // (the backward's regeneration; the hi terms are still in S_H1, S_H2).
+  auto hidden_epilogue = [&](int l, const float* v, bool with_hi) {
+    uint32_t pk[16], lo[16];
+    const float2* b2 = (const float2*)(bias + l * kH + c0);
+#pragma unroll
+    for (int q = 0; q < 16; q += 2) {
+      float2 va = __fadd2_rn(make_float2(v[2 * q], v[2 * q + 1]), b2[q]);
+      float2 vb = __fadd2_rn(make_float2(v[2 * q + 2], v[2 * q + 3]), b2[q + 1]);
+      if (a.act == 0) {
+        tc::silu4x2(va, vb);
+      } else {
+        va = make_float2(act_fn(a.act, va.x), act_fn(a.act, va.y));
+        vb = make_float2(act_fn(a.act, vb.x), act_fn(a.act, vb.y));
+      }
+      const float2 m1 = make_float2(-1.f, -1.f);
+      pk[q] = tc::pack_bf16x2(va.x, va.y);
+      pk[q + 1] = tc::pack_bf16x2(vb.x, vb.y);
+      const float2 ra = __ffma2_rn(make_float2(__uint_as_float(pk[q] << 16), __uint_as_float(pk[q] & 0xFFFF0000u)), m1, va);
+      const float2 rb = __ffma2_rn(make_float2(__uint_as_float(pk[q + 1] << 16), __uint_as_float(pk[q + 1] & 0xFFFF0000u)),
+                                   m1, vb);
+      lo[q] = tc::pack_bf16x2(ra.x, ra.y);
+      lo[q + 1] = tc::pack_bf16x2(rb.x, rb.y);
+    }
+    const uint32_t dhi = l == 0 ? S_H1 : l == 1 ? S_H2 : S_WK, dlo = l == 1 ? S_WK : S_WKLO;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t off = tc::kmajor_offset(row, c0 + 8 * j, kH);
+      if (with_hi) tc::st_shared_v4(sb + dhi + off, pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+      tc::st_shared_v4(sb + dlo + off, lo[4 * j], lo[4 * j + 1], lo[4 * j + 2], lo[4 * j + 3]);
+    }
+  };
+
   const int64_t ntiles = (a.n + kT - 1) / kT;
   for (int64_t tile = blockIdx.x; tile < ntiles && alive; tile += gridDim.x) {
     const int64_t p = tile * kT + row;
@@ -228,47 +281,18 @@ __global__ void __launch_bounds__(kNT, 1) k_train(TrainArgs a) {
           for (int s = 0; s < 2; ++s)
             tc::mma_bf16(tm, kdesc(sb + S_X + 256u * s, kXin), kdesc(sb + S_WIN + 256u * s, kXin), id, s > 0);
         } else {
-          const uint32_t wl = l == 1 ? S_W2 : S_W3;
-          for (int s = 0; s < 8; ++s)
-            tc::mma_bf16(tm, kdesc(sb + S_WK + 256u * s, kH), kdesc(sb + wl + 256u * s, kH), id, s > 0);
-          for (int s = 0; s < 8; ++s)
-            tc::mma_bf16(tm, kdesc(sb + S_WKLO + 256u * s, kH), kdesc(sb + wl + 256u * s, kH), id, 1);
+          hidden_mma(l);
         }
       }
       if (!sync_mma()) { alive = false; break; }
       float v[32];
       tc::ld32(lane_tm + (uint32_t)c0, v);
-      uint32_t pk[16], lo[16];
-      // bias, activation (SiLU four values at a time on the paired FP32 pipe,
-      // as in the collide kernel's epilogue) and the hi + lo split, in pairs
-      const float2* b2 = (const float2*)(bias + l * kH + c0);
+      if (a.zst && a.mode != 0) {   // stored variant: this tile's z_l, row-major [128 x 128]
+        float4* dst = (float4*)(a.zst + (((size_t)tile * 3 + l) * kT + row) * kH + c0);
 #pragma unroll
-      for (int q = 0; q < 16; q += 2) {
-        float2 va = __fadd2_rn(make_float2(v[2 * q], v[2 * q + 1]), b2[q]);
-        float2 vb = __fadd2_rn(make_float2(v[2 * q + 2], v[2 * q + 3]), b2[q + 1]);
-        if (a.act == 0) {
-          tc::silu4x2(va, vb);
-        } else {
-          va = make_float2(act_fn(a.act, va.x), act_fn(a.act, va.y));
-          vb = make_float2(act_fn(a.act, vb.x), act_fn(a.act, vb.y));
-        }
-        const float2 m1 = make_float2(-1.f, -1.f);
-        pk[q] = tc::pack_bf16x2(va.x, va.y);
-        pk[q + 1] = tc::pack_bf16x2(vb.x, vb.y);
-        const float2 ra = __ffma2_rn(make_float2(__uint_as_float(pk[q] << 16), __uint_as_float(pk[q] & 0xFFFF0000u)), m1, va);
-        const float2 rb = __ffma2_rn(make_float2(__uint_as_float(pk[q + 1] << 16), __uint_as_float(pk[q + 1] & 0xFFFF0000u)),
-                                     m1, vb);
-        lo[q] = tc::pack_bf16x2(ra.x, ra.y);
-        lo[q + 1] = tc::pack_bf16x2(rb.x, rb.y);
+        for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
       }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const uint32_t off = tc::kmajor_offset(row, c0 + 8 * j, kH);
-        tc::st_shared_v4(sb + S_WK + off, pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
-        tc::st_shared_v4(sb + S_WKLO + off, lo[4 * j], lo[4 * j + 1], lo[4 * j + 2], lo[4 * j + 3]);
-        if (l < 2)
-          tc::st_shared_v4(sb + (l == 0 ? S_H1 : S_H2) + off, pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
-      }
+      hidden_epilogue(l, v, true);
       to_mma();
     }
     if (!alive) break;
@@ -390,11 +414,29 @@ __global__ void __launch_bounds__(kNT, 1) k_train(TrainArgs a) {
                      (acc0 | (s > 0)) ? 1u : 0u);
       for (int s = 0; s < 8; ++s)
         tc::mma_bf16(tm + TM_DW4, mdesc(sb + S_WKLO + 2u * 2048u * s, kH), mdesc(sb + S_DZ4 + 2u * 256u * s, 16), id4, 1);
-      const uint32_t id = tc::idesc_bf16(kT, kH);
-      for (int s = 0; s < 8; ++s)
-        tc::mma_bf16(tm, kdesc(sb + S_H2 + 256u * s, kH), kdesc(sb + S_W3 + 256u * s, kH), id, s > 0);
+      if (!a.zst) {   // regeneration starts with z1 from x (hi + lo)
+        const uint32_t id = tc::idesc_bf16(kT, kH);
+        for (int s = 0; s < 2; ++s)
+          tc::mma_bf16(tm, kdesc(sb + S_X + 256u * s, kXin), kdesc(sb + S_WIN + 256u * s, kXin), id, s > 0);
+      }
     }
     if (!sync_mma()) { alive = false; break; }
+    if (!a.zst) {
+      // h1 and h2 low terms regenerated (the forward's arithmetic on the same
+      // accumulators), then z3 = W3 (h2 hi + lo): all equal to the forward's
+      for (int l = 0; l < 2 && alive; ++l) {
+        float v[32];
+        tc::ld32(lane_tm + (uint32_t)c0, v);
+        hidden_epilogue(l, v, false);
+        to_mma();
+        if (t == 0) {
+          tc::fence_after();
+          hidden_mma(l + 1);
+        }
+        if (!sync_mma()) alive = false;
+      }
+      if (!alive) break;
+    }
     // dh3 = dz4 W4 on CUDA cores (K = 3), dz3 = dh3 * act'(z3)
     float dh[32];
     {
@@ -412,7 +454,16 @@ __global__ void __launch_bounds__(kNT, 1) k_train(TrainArgs a) {
     // layers 3, 2, 1
     for (int l = 2; l >= 0 && alive; --l) {
       float z[32];
-      tc::ld32(lane_tm + (uint32_t)c0, z);
+      if (a.zst) {
+        const float4* src = (const float4*)(a.zst + (((size_t)tile * 3 + l) * kT + row) * kH + c0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float4 f = src[q];
+          z[4 * q] = f.x; z[4 * q + 1] = f.y; z[4 * q + 2] = f.z; z[4 * q + 3] = f.w;
+        }
+      } else {
+        tc::ld32(lane_tm + (uint32_t)c0, z);
+      }
       float dz[32];
 #pragma unroll
       for (int q = 0; q < 32; ++q) dz[q] = dh[q] * act_grad(a.act, z[q] + bias[l * kH + c0 + q]);
@@ -451,13 +502,15 @@ __global__ void __launch_bounds__(kNT, 1) k_train(TrainArgs a) {
       tc::ld32(lane_tm + (uint32_t)c0, dh);
       tc::fence_before();
       __syncthreads();
-      // z_{l-1} recomputed: from h1 (single copy) for layer 2, from x (hi + lo) for layer 1
+      if (a.zst) continue;   // the stored variant reads z_{l-1} back
+      // z_{l-1} recomputed from the forward's own operands: h1 (hi + lo, the
+      // low terms regenerated above and still in S_WKLO) for layer 2, x (hi
+      // + lo) for layer 1
       if (t == 0) {
         tc::fence_after();
         const uint32_t id = tc::idesc_bf16(kT, kH);
         if (l == 2) {
-          for (int s = 0; s < 8; ++s)
-            tc::mma_bf16(tm, kdesc(sb + S_H1 + 256u * s, kH), kdesc(sb + S_W2 + 256u * s, kH), id, s > 0);
+          hidden_mma(1);
         } else {
           for (int s = 0; s < 2; ++s)
             tc::mma_bf16(tm, kdesc(sb + S_X + 256u * s, kXin), kdesc(sb + S_WIN + 256u * s, kXin), id, s > 0);
@@ -557,12 +610,14 @@ __global__ void k_adam(int n_w, int n_b, const float* __restrict__ grad, float* 
   }
 }
 
+size_t train_act_bytes(int64_t n) { return sizeof(float) * 3 * (size_t)kT * kH * (size_t)((n + kT - 1) / kT); }
+
 size_t train_ws(int sms) { return align256(sizeof(float) * (size_t)kPartial * (size_t)(sms > 0 ? sms : 1)); }
 
 int launch_train(Ctx* c, const dsmc_mlp_t& mlp, int mode, uint64_t seed, uint64_t t, int64_t n,
                  const float* theta, const double* vi, const double* vj, const double* T,
                  const double* ti, const double* tj, const double* gi, const double* gj, double* oi, double* oj,
-                 float* grad, double* loss, void* ws, size_t ws_bytes, cudaStream_t s) {
+                 float* grad, double* loss, void* ws, size_t ws_bytes, cudaStream_t s, float* act) {
   const int sms = sm_count(c);
   if (mode != 0 && ws_bytes < train_ws(sms)) return record(c, DSMC_ERR_ARG, "train: workspace too small");
   if (cudaFuncSetAttribute((const void*)k_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S_TOTAL) !=
@@ -572,7 +627,7 @@ int launch_train(Ctx* c, const dsmc_mlp_t& mlp, int mode, uint64_t seed, uint64_
   a.mode = mode; a.act = mlp.act; a.n = n; a.seed = seed; a.t = t;
   a.sigma_v_inv = 1.0 / mlp.sigma_v; a.T_ref_inv = 1.0 / mlp.T_ref; a.eps = mlp.eps;
   a.theta = theta; a.vi = vi; a.vj = vj; a.T = T; a.ti = ti; a.tj = tj; a.gi = gi; a.gj = gj;
-  a.oi = oi; a.oj = oj; a.partial = (float*)ws; a.status = status_ptr(c);
+  a.oi = oi; a.oj = oj; a.zst = act; a.partial = (float*)ws; a.status = status_ptr(c);
   const int64_t tiles = (n + kT - 1) / kT;
   const int blocks = (int)(tiles < sms ? (tiles > 0 ? tiles : 1) : sms);
   k_train<<<blocks, kNT, S_TOTAL, s>>>(a);

@@ -172,6 +172,9 @@ def load(build: bool = True):
                                                         vp, sz, vp]),
             "dsmc_train_loss_grad": (C.c_int, [vp, P(Mlp), vp, u64, u64, i64, vp, vp, vp, vp, vp, vp, vp, vp,
                                                sz, vp]),
+            "dsmc_train_act_size": (sz, [i64]),
+            "dsmc_train_loss_grad_stored": (C.c_int, [vp, P(Mlp), vp, u64, u64, i64, vp, vp, vp, vp, vp, vp, vp, vp,
+                                                      sz, vp, sz, vp]),
             "dsmc_adam_step": (C.c_int, [vp, i32, i32, vp, vp, vp, vp, i64, C.c_float, C.c_float, C.c_float,
                                          C.c_float, vp, vp, vp]),
             "dsmc_tune_set": (C.c_int, [vp, i32, i32, i32]),
@@ -537,6 +540,25 @@ class Context:
             self.h, C.byref(mlp), _ptr(theta, torch.float32), seed, t, vi.shape[0], _ptr(vi, f64),
             _ptr(vj, f64), _ptr(T, f64), _ptr(vi_t, f64), _ptr(vj_t, f64), _ptr(grad), _ptr(loss),
             _ptr(ws), ws.numel(), _stream(stream)), "train_loss_grad")
+        return grad, loss
+
+    def train_loss_grad_stored(self, mlp: Mlp, theta, seed, t, vi, vj, T, vi_t, vj_t, ws=None, act=None,
+                               stream=None):
+        """dsmc_train_loss_grad_stored: the same loss and gradient with the
+        hidden layers' pre-activations stored by the forward and read back by
+        the backward (the check of the recomputation)."""
+        grad = torch.empty_like(theta)
+        loss = torch.zeros(1, dtype=torch.float64, device=theta.device)
+        ws = ws if ws is not None else self.train_workspace(theta.device)
+        nb = self._lib.dsmc_train_act_size(vi.shape[0])
+        if act is None or act.numel() * 4 < nb:
+            act = torch.empty(max(nb // 4, 1), dtype=torch.float32, device=theta.device)
+        f64 = torch.float64
+        self._check(self._lib.dsmc_train_loss_grad_stored(
+            self.h, C.byref(mlp), _ptr(theta, torch.float32), seed, t, vi.shape[0], _ptr(vi, f64),
+            _ptr(vj, f64), _ptr(T, f64), _ptr(vi_t, f64), _ptr(vj_t, f64), _ptr(grad), _ptr(loss),
+            _ptr(ws), ws.numel(), _ptr(act, torch.float32), act.numel() * 4, _stream(stream)),
+            "train_loss_grad_stored")
         return grad, loss
 
     def adam_step(self, n_weights, grad, theta, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,

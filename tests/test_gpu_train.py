@@ -187,3 +187,19 @@ def test_adam_step_matches_oracle_and_training_reduces_loss():
         losses.append(float(loss.item()))
     assert C.sync_status() == 0
     assert losses[-1] < 0.9 * losses[0], losses[::7]
+
+
+@pytest.mark.parametrize("n", [1040, 1 << 16])
+def test_recomputation_equals_stored_activations(n):
+    """The backward recomputes every hidden layer's pre-activation from the
+    forward's own MMA operands; the stored-activation variant writes them in
+    the forward and reads them back.  Both must give the same loss and the
+    same gradient bit for bit (several tiles per CTA at 2^16 pairs)."""
+    dims, theta, hv, vit, vjt = _setup(n, seed=4)
+    C = ctx()
+    args = (_mlp(), cuda(theta), SEED, T_STEP, *_gpu_inputs(hv, vit, vjt))
+    g1, l1 = C.train_loss_grad(*args)
+    g2, l2 = C.train_loss_grad_stored(*args)
+    assert C.sync_status() == 0
+    assert torch().equal(g1, g2)
+    assert float(l1.item()) == float(l2.item())
