@@ -521,7 +521,8 @@ typedef struct {
 /* Set (threads, blocks_per_sm) of one kernel for later launches of this
  * context; (0, 0) restores the built-in shape.  DSMC_ERR_ARG for an unknown
  * kernel, a block size that is not a multiple of 32 or above the kernel's
- * limit, or more than 64 blocks per SM.  A captured step graph keeps the
+ * limit (the cell-moment and moment-matching kernels take 256 only), or
+ * more than 64 blocks per SM.  A captured step graph keeps the
  * shapes it was captured with. */
 int dsmc_tune_set(dsmc_ctx_t* ctx, int32_t kernel, int32_t threads, int32_t blocks_per_sm);
 /* Current shape of one kernel (the built-in one if none was set). */

@@ -45,6 +45,8 @@ int* status_ptr(Ctx* c) { return c->d_status; }
 // grid-barrier words: one slot for direct calls, another for graph replays,
 // so that a replay and a direct call on another stream do not share counters
 unsigned* barrier_ptr(Ctx* c) { return c->capturing ? c->d_bar + 32 : c->d_bar; }
+// work counters: words 40-41 for direct calls, 48-49 for graph replays
+unsigned* work_ptr(Ctx* c) { return c->capturing ? c->d_bar + 48 : c->d_bar + 40; }
 int sm_count(Ctx* c) { return c->sms; }
 Shape tune_shape(Ctx* c, int k) { return Shape{c->tune_threads[k], c->tune_bps[k]}; }
 void count_launches(Ctx* c, int k) { c->launches += k; }
@@ -58,8 +60,8 @@ __global__ void k_set_step(uint64_t* slot, uint64_t step) { *slot = step; }
 ShapeInfo shape_info(int k) {
   switch (k) {
     case DSMC_TUNE_GATHER: return ShapeInfo{256, 16, 1024};
-    case DSMC_TUNE_MOMENTS: return ShapeInfo{256, 8, 256};
-    case DSMC_TUNE_MOMENT_MATCH: return ShapeInfo{256, 8, 256};
+    case DSMC_TUNE_MOMENTS: return ShapeInfo{256, 4, 256};
+    case DSMC_TUNE_MOMENT_MATCH: return ShapeInfo{256, 3, 256};
     case DSMC_TUNE_COLLIDE_VHS: return ShapeInfo{256, 0, 256};
     case DSMC_TUNE_COLLIDE_JAGER: return ShapeInfo{128, 0, 128};
     case DSMC_TUNE_JAGER_CHI: return ShapeInfo{128, 64, 128};
@@ -86,9 +88,8 @@ static int tune_candidates(int k, dsmc_tune_entry_t* out, int cap) {
       break;
     case DSMC_TUNE_MOMENTS:
     case DSMC_TUNE_MOMENT_MATCH:
-      for (int t : {64, 128, 256})
-        for (int b : {4, 8, 16, 32})
-          if (t * b <= 2048) push(t, b);
+      // block size fixed (256 threads); up to four blocks resident per SM
+      for (int b : {1, 2, 3, 4}) push(256, b);
       break;
     case DSMC_TUNE_COLLIDE_VHS:
     case DSMC_TUNE_COLLIDE_JAGER:
@@ -783,6 +784,8 @@ int dsmc_tune_set(dsmc_ctx_t* c, int32_t kernel, int32_t threads, int32_t blocks
   REQUIRE(c, threads >= 32 && threads % 32 == 0 && threads <= dsmc::shape_info(kernel).max_threads,
           "tune_set: block size must be a multiple of 32 within the kernel's limit");
   REQUIRE(c, blocks_per_sm >= 1 && blocks_per_sm <= 64, "tune_set: blocks per SM must be 1..64");
+  REQUIRE(c, (kernel != DSMC_TUNE_MOMENTS && kernel != DSMC_TUNE_MOMENT_MATCH) || threads == 256,
+          "tune_set: the cell kernels run 256-thread blocks");
   c->tune_threads[kernel] = threads;
   c->tune_bps[kernel] = blocks_per_sm;
   return DSMC_OK;

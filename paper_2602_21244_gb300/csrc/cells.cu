@@ -290,7 +290,9 @@ __global__ void k_gather(int32_t n, const int32_t* __restrict__ cell_start, int3
 
 // One velocity component at a time: the 73 MB source array of a 9M-particle
 // gas stays in L2 (129 MB) while its random reads land, so each sector comes
-// from DRAM once instead of once per particle that reads it.
+// from DRAM once instead of once per particle that reads it.  perm and the
+// output stream through with evict-first hints so that they do not push
+// the source array out.
 __global__ void k_gather1(int32_t n, const int32_t* __restrict__ cell_start, int32_t n_cells,
                           const int32_t* __restrict__ perm, const double* __restrict__ v,
                           double* __restrict__ sv) {
@@ -302,7 +304,7 @@ __global__ void k_gather1(int32_t n, const int32_t* __restrict__ cell_start, int
 #pragma unroll
     for (int u = 0; u < kIlp; ++u) {
       const int64_t s = s0 + u * stride;
-      src[u] = s < filled ? perm[s] : -1;
+      src[u] = s < filled ? __ldcs(perm + s) : -1;
     }
     double x[kIlp];
 #pragma unroll
@@ -310,7 +312,7 @@ __global__ void k_gather1(int32_t n, const int32_t* __restrict__ cell_start, int
       if (src[u] >= 0) x[u] = __ldg(v + src[u]);
 #pragma unroll
     for (int u = 0; u < kIlp; ++u)
-      if (src[u] >= 0) sv[s0 + u * stride] = x[u];
+      if (src[u] >= 0) __stcs(sv + s0 + u * stride, x[u]);
   }
 }
 
@@ -318,7 +320,7 @@ __global__ void k_gather1(int32_t n, const int32_t* __restrict__ cell_start, int
 constexpr int kRadixBits = 9;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kRsChunk = 4096;   // elements per block
-constexpr int kRsWarps = 8;
+constexpr int kRsWarps = 16;
 
 // key of input element i: its cell id, or n_cells for an id out of range
 // (recorded as DSMC_ERR_ARG; such particles sort after every cell)
@@ -345,15 +347,22 @@ k_rs_count(const int32_t* __restrict__ cell_id, const uint32_t* __restrict__ key
   for (int t = threadIdx.x; t < kRadix; t += blockDim.x) cnt[(size_t)t * chunks + blockIdx.x] = hist[t];
 }
 
-// Ordered scatter of one chunk: warp w owns the chunk's w-th eighth, its 16
-// elements per lane loaded into registers first; each warp counts its
-// digits, the counts become per-warp starting positions (warps in order
-// after the chunk's base from the scan), then each warp writes its elements
-// in order, ranks among equal digits within 32 lanes from __match_any_sync.
+// Ordered scatter of one chunk: warp w owns the chunk's w-th sixteenth, its
+// kRsPer elements per lane loaded into registers first.  Stable ranks in
+// two steps: (1) per element batch j (32 consecutive elements), the lanes
+// holding the same digit find each other from one ballot per digit bit; the lowest
+// of them adds the group's size to the warp's counter of that digit in
+// shared memory and keeps the old value (the count of that digit in the
+// warp's earlier batches; the batches' atomics are ordered by __syncwarp),
+// the others their rank inside the group.  (2) After the counts are
+// complete, each counter becomes the warp's starting position for its digit
+// (the chunk's base from the scan, then the warps in order) and every
+// element goes to start + old value of its group's leader + rank.  No
+// element waits on the shared-memory result of the batch before it.
 // Values: the input index (first pass) or vals.
 constexpr int kRsPer = kRsChunk / kRsWarps / 32;
 
-__global__ void __launch_bounds__(kRsWarps * 32)
+__global__ void __launch_bounds__(kRsWarps * 32, 2)
 k_rs_scatter(const int32_t* __restrict__ cell_id, const uint32_t* __restrict__ keys,
              const int32_t* __restrict__ vals, int32_t n, int32_t n_cells, int shift, int32_t chunks,
              const int32_t* __restrict__ base, uint32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out) {
@@ -371,49 +380,71 @@ k_rs_scatter(const int32_t* __restrict__ cell_id, const uint32_t* __restrict__ k
     val[j] = has ? (vals ? vals[i] : (int32_t)i) : 0;
   }
   __syncthreads();
-#pragma unroll
-  for (int j = 0; j < kRsPer; ++j)
-    if (s0 + j * 32 + lane < n) atomicAdd(&wh[w][(key[j] >> shift) & (kRadix - 1)], 1);
-  __syncthreads();
-  for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
-    int acc = base[(size_t)d * chunks + blockIdx.x];
-    for (int q = 0; q < kRsWarps; ++q) { const int c = wh[q][d]; wh[q][d] = acc; acc += c; }
-  }
-  __syncthreads();
   const unsigned lt = (1u << lane) - 1u;
+  int old[kRsPer];
+  uint32_t pk[kRsPer];   // leader lane | rank in the group << 5
 #pragma unroll
   for (int j = 0; j < kRsPer; ++j) {
     const bool has = s0 + j * 32 + lane < n;
-    const int d = has ? (int)((key[j] >> shift) & (kRadix - 1)) : -1;
-    // lanes holding the same digit: one ballot per digit bit (ALU pipe),
-    // the same set as a match on d (a lane without an element has d = -1:
-    // all ones, in no valid lane's set, and the ones without form their own)
-    unsigned same = __ballot_sync(0xffffffffu, has);
-    if (!has) same = ~same;
+    // lanes without an element share the digit kRadix (no counter)
+    const int d = has ? (int)((key[j] >> shift) & (kRadix - 1)) : kRadix;
+    // lanes holding the same digit: one ballot per digit bit (ALU pipe); the
+    // lanes without an element form their own set
+    unsigned peers = __ballot_sync(0xffffffffu, has);
+    if (!has) peers = ~peers;
 #pragma unroll
     for (int bit = 0; bit < kRadixBits; ++bit) {
       const unsigned m = __ballot_sync(0xffffffffu, (d >> bit) & 1);
-      same &= ((d >> bit) & 1) ? m : ~m;
+      peers &= ((d >> bit) & 1) ? m : ~m;
     }
+    const int rank = __popc(peers & lt);
+    old[j] = 0;
+    if (has && rank == 0) old[j] = atomicAdd(&wh[w][d], __popc(peers));
+    pk[j] = (uint32_t)(__ffs(peers) - 1) | ((uint32_t)rank << 5);
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
+    int acc = base[(size_t)d * chunks + blockIdx.x];
+#pragma unroll
+    for (int q = 0; q < kRsWarps; ++q) { const int c = wh[q][d]; wh[q][d] = acc; acc += c; }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kRsPer; ++j) {
+    const bool has = s0 + j * 32 + lane < n;
+    const int o = __shfl_sync(0xffffffffu, old[j], (int)(pk[j] & 31u));
     if (has) {
-      const int q = wh[w][d] + __popc(same & lt);
+      const int d = (int)((key[j] >> shift) & (kRadix - 1));
+      const int q = wh[w][d] + o + (int)(pk[j] >> 5);
       if (keys_out) keys_out[q] = key[j];
       vals_out[q] = val[j];
     }
-    __syncwarp();
-    if (has && (same & lt) == 0) wh[w][d] += __popc(same);
-    __syncwarp();
   }
 }
 
 // cell_start from the sorted keys: slot s starts every cell in (key[s-1], key[s]]
-// (slot n closes the list with key n_cells).
+// (slot n closes the list with key n_cells).  Four slots per thread.
 __global__ void k_cell_start(const uint32_t* __restrict__ skeys, int32_t n, int32_t n_cells,
                              int32_t* __restrict__ cell_start) {
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s <= n; s += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t hi = s < n ? (int64_t)skeys[s] : (int64_t)n_cells;
-    const int64_t lo = s > 0 ? (int64_t)skeys[s - 1] : -1;
-    for (int64_t c = lo + 1; c <= hi && c <= n_cells; ++c) cell_start[c] = (int32_t)s;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
+  for (int64_t s0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; s0 <= n; s0 += stride) {
+    int64_t key[5];   // key[q] = skeys[s0 - 1 + q] (-1 before the first slot, n_cells from slot n on)
+    key[0] = s0 > 0 ? (int64_t)skeys[s0 - 1] : -1;
+    if (s0 + 4 <= n && ((uintptr_t)(skeys + s0) & 15) == 0) {
+      const uint4 k4 = __ldcs(reinterpret_cast<const uint4*>(skeys + s0));
+      key[1] = k4.x; key[2] = k4.y; key[3] = k4.z; key[4] = k4.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) key[q + 1] = s0 + q < n ? (int64_t)skeys[s0 + q] : (int64_t)n_cells;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t s = s0 + q;
+      if (s > n) break;
+      const int64_t lo = key[q], hi = key[q + 1];
+      for (int64_t c = lo + 1; c <= hi && c <= n_cells; ++c) cell_start[c] = (int32_t)s;
+    }
   }
 }
 
@@ -487,7 +518,7 @@ int launch_sort_keys(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_id,
     kin = kout;
     vin = vout;
   }
-  k_cell_start<<<grid_for((int64_t)n + 1, 256, sm_count(c) * 8), 256, 0, s>>>(kin, n, n_cells, cell_start);
+  k_cell_start<<<grid_for(((int64_t)n + 4) / 4, 256, sm_count(c) * 8), 256, 0, s>>>(kin, n, n_cells, cell_start);
   count_launches(c, 1);
   return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
 }
@@ -506,78 +537,184 @@ int launch_gather(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_start,
 }
 
 // ---------------------------------------------------------------- moments
-// (integer moment helpers: moments.cuh)
-constexpr int kCellWarps = 8;
+// Cell moments and moment matching without block-wide synchronisation: each
+// warp claims runs of kCwRun consecutive cells from a counter (so that the
+// warps given cheap runs, such as empty cells or the free stream, take more
+// of them) and collects kCwClaims runs before finishing their cells.
+// Segments of 8 lanes take four cells at a time through the two passes of
+// the exact integer moments (the largest exponent, then the split sums of
+// moments.cuh); the per-cell remainder (means, centred sum of squares,
+// FP64 results) then runs one lane per cell, so that its FP64 instructions
+// serve 16 cells at once; moment matching finally updates each run's
+// particles one lane per particle, four at a time (three FP64 FMAs each,
+// every lane busy, coalesced reads and writes).
+constexpr int kCwWarps = 8;
+constexpr int kCwRun = 8;                    // cells per claim
+constexpr int kCwClaims = 2;                 // claims per batch
+constexpr int kCwCells = kCwRun * kCwClaims; // cells per batch (one lane each in the remainder)
 
-__global__ void __launch_bounds__(kCellWarps * 32, 5)
-k_moments(int32_t n_cells, const int32_t* __restrict__ cs, const double* __restrict__ vx,
-          const double* __restrict__ vy, const double* __restrict__ vz, double* __restrict__ mom,
-          int* status) {
-  const int lane = threadIdx.x & 31, sl = lane & (kSeg - 1), seg = lane / kSeg;
-  const int32_t per_warp = 32 / kSeg, wpb = blockDim.x >> 5;
-  const int32_t warps = gridDim.x * wpb;
-  for (int32_t k0 = (blockIdx.x * wpb + (threadIdx.x >> 5)) * per_warp; k0 < n_cells;
-       k0 += warps * per_warp) {
-    const int32_t k = k0 + seg;
-    const bool has = k < n_cells;
-    const int32_t a = has ? cs[k] : 0, b = has ? cs[k + 1] : 0;
-    const CellFix C = cell_fix(vx, vy, vz, a, b, sl);
-    // lane c < 3 of the cell writes component c, lane 3 Theta, lane 4 N
-    if (has && sl < 5) moment_store(C, b - a, sl, mom + 5 * (size_t)k, status);
+struct CwWarp {
+  FixAcc acc[kCwCells];
+  int E[kCwCells];
+  int32_t cs[kCwClaims][kCwRun + 1];
+  int32_t k0[kCwClaims];
+  double coef[kCwCells][4];   // alpha and the three offsets (moment matching)
+};
+
+template <int SEG>
+__device__ __forceinline__ FixAcc seg_sum_acc(FixAcc q) {
+  q.sx = seg_sum_ll<SEG>(q.sx); q.sy = seg_sum_ll<SEG>(q.sy); q.sz = seg_sum_ll<SEG>(q.sz);
+  q.A = (unsigned long long)seg_sum_ll<SEG>((long long)q.A);
+  q.B = (unsigned long long)seg_sum_ll<SEG>((long long)q.B);
+  q.L = (unsigned long long)seg_sum_ll<SEG>((long long)q.L);
+  return q;
+}
+
+// Sums of one cell [a, b) by the SEG lanes of a segment (lane sl); returns
+// the segment-reduced sums and *E.  Called by whole warps (lanes of a
+// segment without a cell pass an empty range).
+template <int SEG>
+__device__ __forceinline__ FixAcc cell_sums(const double* __restrict__ X, const double* __restrict__ Y,
+                                            const double* __restrict__ Z, int32_t a, int32_t b, int sl, int* E_out) {
+  int E = 0;
+#pragma unroll 4
+  for (int32_t i = a + sl; i < b; i += SEG) E = max(E, max(dexp(X[i]), max(dexp(Y[i]), dexp(Z[i]))));
+  E = seg_max_i<SEG>(E);
+  const int32_t n = b - a;
+  const int Ec = E + cell_scale(E, n).c, sp = fix_split(n);
+  FixAcc q{0, 0, 0, 0ull, 0ull, 0ull};
+#pragma unroll 4
+  for (int32_t i = a + sl; i < b; i += SEG) {
+    fix_add(q, q.sx, X[i], Ec, sp);
+    fix_add(q, q.sy, Y[i], Ec, sp);
+    fix_add(q, q.sz, Z[i], Ec, sp);
+  }
+  *E_out = E;
+  return seg_sum_acc<SEG>(q);
+}
+
+// v <- alpha v + o over the particles [p0, p1) of one run of cells (cell
+// starts cs[0..nc]), coefficients coef[0..nc); four particles per lane at
+// a time, their loads issued together.
+__device__ __forceinline__ void apply_run(const int32_t* cs, int nc, const double (*coef)[4], double* vx, double* vy,
+                                          double* vz) {
+  const int lane = threadIdx.x & 31;
+  const int32_t p0 = cs[0], p1 = cs[nc];
+  int c = 0;
+  for (int32_t pb = p0; pb < p1; pb += 128) {
+    double x[4], y[4], z[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int32_t p = pb + 32 * u + lane;
+      if (p < p1) { x[u] = vx[p]; y[u] = vy[p]; z[u] = vz[p]; }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int32_t p = pb + 32 * u + lane;
+      if (p < p1) {
+        while (c < nc - 1 && p >= cs[c + 1]) ++c;
+        const double* cf = coef[c];
+        vx[p] = fma(cf[0], x[u], cf[1]);
+        vy[p] = fma(cf[0], y[u], cf[2]);
+        vz[p] = fma(cf[0], z[u], cf[3]);
+      }
+    }
   }
 }
 
-int launch_moments(Ctx* c, int32_t n_cells, const int32_t* cs, const double* vx,
-                   const double* vy, const double* vz, double* mom, cudaStream_t s) {
+// Moments into mom (MATCH = false), or matching of the velocities to the
+// pre-collision moments in mom (MATCH = true).
+template <bool MATCH>
+__global__ void __launch_bounds__(kCwWarps * 32, MATCH ? 3 : 4)
+k_cells(int32_t n_cells, const int32_t* __restrict__ cs, double* vx, double* vy, double* vz, double* mom,
+        int* status, unsigned* work) {
+  __shared__ CwWarp sw[kCwWarps];
+  CwWarp& W = sw[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31, sl = lane & (kSeg - 1), seg = lane / kSeg;
+  for (;;) {
+    int nclaim = 0;
+    for (int q = 0; q < kCwClaims; ++q) {
+      unsigned k0u = 0u;
+      if (lane == 0) k0u = atomicAdd(work, (unsigned)kCwRun);
+      k0u = __shfl_sync(0xffffffffu, k0u, 0);
+      if (k0u >= (unsigned)n_cells) break;
+      const int32_t k0 = (int32_t)k0u;
+      const int nc = min(kCwRun, n_cells - k0);
+      if (lane <= kCwRun) W.cs[q][lane] = cs[k0 + min(lane, nc)];
+      if (lane == 0) W.k0[q] = k0;
+      __syncwarp();
+      for (int g = 0; g * 4 < nc; ++g) {
+        const int ci = 4 * g + seg;
+        const bool act = ci < nc;
+        const int32_t a = act ? W.cs[q][ci] : 0, b = act ? W.cs[q][ci + 1] : 0;
+        int E;
+        const FixAcc f = cell_sums<kSeg>(vx, vy, vz, a, b, sl, &E);
+        if (act && sl == 0) { W.acc[q * kCwRun + ci] = f; W.E[q * kCwRun + ci] = E; }
+      }
+      ++nclaim;
+    }
+    if (nclaim == 0) break;
+    __syncwarp();
+    {
+      const int q = lane / kCwRun, ci = lane % kCwRun;
+      const int32_t k = q < nclaim ? W.k0[q] + ci : n_cells;
+      if (k < n_cells) {
+        const int32_t n = W.cs[q][ci + 1] - W.cs[q][ci];
+        const CellFix C = cellfix_from(W.E[lane], n, W.acc[lane]);
+        double* mk = mom + 5 * (size_t)k;
+        if (!MATCH) {
+          for (int r = 0; r < 5; ++r) moment_store(C, n, r, mk, status);
+        } else {
+          double alpha, o[3];
+          match_coeffs3(C, n, mk, &alpha, o);
+          W.coef[lane][0] = alpha; W.coef[lane][1] = o[0]; W.coef[lane][2] = o[1]; W.coef[lane][3] = o[2];
+        }
+      }
+    }
+    __syncwarp();
+    if (MATCH) {
+      for (int q = 0; q < nclaim; ++q)
+        apply_run(W.cs[q], min(kCwRun, n_cells - W.k0[q]), W.coef + q * kCwRun, vx, vy, vz);
+    }
+    __syncwarp();
+    if (nclaim < kCwClaims) break;
+  }
+  // the last warp of the grid to finish resets the counters for the next
+  // launch (the fences order every warp's last claim before the reset)
+  if (lane == 0) {
+    __threadfence();
+    if (atomicAdd(work + 1, 1u) == gridDim.x * kCwWarps - 1) {
+      __threadfence();
+      work[0] = 0u;
+      work[1] = 0u;
+    }
+  }
+}
+
+static int launch_cells(Ctx* c, bool match, int32_t n_cells, const int32_t* cs, double* vx, double* vy,
+                        double* vz, double* mom, cudaStream_t s) {
   if (n_cells <= 0) return 0;
-  const Shape sh = shape_or_default(c, DSMC_TUNE_MOMENTS);
-  k_moments<<<grid_for((n_cells + 3) / 4, sh.threads / 32, sm_count(c) * sh.blocks_per_sm), sh.threads, 0, s>>>(
-      n_cells, cs, vx, vy, vz, mom, status_ptr(c));
+  const Shape sh = shape_or_default(c, match ? DSMC_TUNE_MOMENT_MATCH : DSMC_TUNE_MOMENTS);
+  const int64_t runs = ((int64_t)n_cells + kCwRun - 1) / kCwRun;
+  const unsigned g = grid_for(runs, kCwWarps * kCwClaims, sm_count(c) * sh.blocks_per_sm);
+  if (match) k_cells<true><<<g, kCwWarps * 32, 0, s>>>(n_cells, cs, vx, vy, vz, mom, nullptr, work_ptr(c));
+  else k_cells<false><<<g, kCwWarps * 32, 0, s>>>(n_cells, cs, vx, vy, vz, mom, status_ptr(c), work_ptr(c));
   count_launches(c, 1);
   return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
+}
+
+int launch_moments(Ctx* c, int32_t n_cells, const int32_t* cs, const double* vx, const double* vy,
+                   const double* vz, double* mom, cudaStream_t s) {
+  return launch_cells(c, false, n_cells, cs, (double*)vx, (double*)vy, (double*)vz, mom, s);
 }
 
 // ---------------------------------------------------------------- moment matching
 // Sec. 2.5 (centred): v <- u_pre + alpha (v - u_post), alpha = sqrt(Th_pre/Th_post),
 // applied as v <- alpha v + (u_pre - alpha u_post) (FP64); u_post and Th_post
-// from the exact integer moments above.  The three components' offsets are
-// formed by lanes 0..2 of the cell together (GB300's FP64 pipe costs a whole
-// warp instruction however few lanes are active) and passed to the cell's
-// eight lanes by shuffles.
-__global__ void __launch_bounds__(kCellWarps * 32, 5)
-k_moment_match(int32_t n_cells, const int32_t* __restrict__ cs, const double* __restrict__ mom,
-               double* __restrict__ vx, double* __restrict__ vy, double* __restrict__ vz) {
-  const int lane = threadIdx.x & 31, sl = lane & (kSeg - 1), seg = lane / kSeg;
-  const int32_t per_warp = 32 / kSeg, wpb = blockDim.x >> 5;
-  const int32_t warps = gridDim.x * wpb;
-  for (int32_t k0 = (blockIdx.x * wpb + (threadIdx.x >> 5)) * per_warp; k0 < n_cells;
-       k0 += warps * per_warp) {
-    const int32_t k = k0 + seg;
-    const bool has = k < n_cells;
-    const int32_t a = has ? cs[k] : 0, b = has ? cs[k + 1] : 0;
-    const CellFix C = cell_fix(vx, vy, vz, a, b, sl);
-    double alpha, o;
-    match_coeffs(C, b - a, sl, mom + 5 * (size_t)k, &alpha, &o);
-    const int l0 = seg * kSeg;
-    const double ox = __shfl_sync(0xffffffffu, o, l0), oy = __shfl_sync(0xffffffffu, o, l0 + 1),
-                 oz = __shfl_sync(0xffffffffu, o, l0 + 2);
-#pragma unroll 4
-    for (int32_t i = a + sl; i < b; i += kSeg) {
-      vx[i] = fma(alpha, vx[i], ox);
-      vy[i] = fma(alpha, vy[i], oy);
-      vz[i] = fma(alpha, vz[i], oz);
-    }
-  }
-}
-
+// from the exact integer moments above (k_cells<true>).
 int launch_moment_match(Ctx* c, int32_t n_cells, const int32_t* cs, const double* mom,
                         double* vx, double* vy, double* vz, cudaStream_t s) {
-  if (n_cells <= 0) return 0;
-  const Shape sh = shape_or_default(c, DSMC_TUNE_MOMENT_MATCH);
-  k_moment_match<<<grid_for((n_cells + 3) / 4, sh.threads / 32, sm_count(c) * sh.blocks_per_sm), sh.threads, 0,
-                   s>>>(n_cells, cs, mom, vx, vy, vz);
-  count_launches(c, 1);
-  return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
+  return launch_cells(c, true, n_cells, cs, vx, vy, vz, (double*)mom, s);
 }
 
 }  // namespace dsmc

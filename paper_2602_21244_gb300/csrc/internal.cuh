@@ -248,6 +248,9 @@ struct Ctx;
 int record(Ctx* c, int code, const char* msg);  // sets last error text, returns code
 int* status_ptr(Ctx* c);
 unsigned* barrier_ptr(Ctx* c);  // 4 words of device memory per barrier slot
+// Two words of device memory for a work counter (next item, finished warps),
+// zero between launches: the kernel that uses them leaves them zero.
+unsigned* work_ptr(Ctx* c);
 int sm_count(Ctx* c);
 void count_launches(Ctx* c, int k);  // kernels launched by this context
 // Device address the kernels read the step index from while a step graph is

@@ -121,6 +121,61 @@ __device__ __forceinline__ CellFix cell_fix(const double* __restrict__ vx, const
   return C;
 }
 
+// ---- split integer accumulation (the block-staged cell kernels)
+// The same exact moments with cheaper sums of squares: x = round(v/unit)
+// is split as x = h 2^s + l (l < 2^s) and the cell accumulates the 64-bit
+// sums A = sum h^2, B = sum h l and L = sum l^2 (one 32 x 32 -> 64 bit
+// multiply-add each), so that sum x^2 = A 2^(2s) + B 2^(s+1) + L exactly.
+// With N < 2^bits particles and |x| <= 2^(53-c) (c = max(0, bits - 10)):
+// A < 2^(126-bits-2s) and L < 2^(bits+2s) both fit in 64 bits for
+// s = 26 (bits <= 10) and s = (63 - bits) / 2 (bits >= 11); B < 2^63 and
+// the signed sums of x stay below 2^63 as before.
+__device__ __forceinline__ int fix_split(int32_t n) {
+  const int bits = 32 - __clz(n > 0 ? n : 1);
+  return bits <= 10 ? 26 : (63 - bits) >> 1;
+}
+
+struct FixAcc {
+  long long sx, sy, sz;
+  unsigned long long A, B, L;
+};
+
+// v added to the sums with integer unit 2^(Ec - 1075) (Ec = E + c)
+__device__ __forceinline__ void fix_add(FixAcc& q, long long& sc, double v, int Ec, int s) {
+  const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  const int sh = Ec - e;
+  const unsigned long long m = ((unsigned long long)((hi & 0xFFFFFu) | 0x100000u) << 32) | lo;
+  unsigned long long x;
+  if (e == 0 || sh >= 64) x = 0;
+  else if (sh <= 0) x = m;
+  else x = ((m >> (sh - 1)) + 1) >> 1;   // = (m + 2^(sh-1)) >> sh
+  sc += (hi & 0x80000000u) ? -(long long)x : (long long)x;
+  const uint32_t h = (uint32_t)(x >> s), l = (uint32_t)x & ((1u << s) - 1u);
+  q.A += (unsigned long long)h * h;
+  q.B += (unsigned long long)h * l;
+  q.L += (unsigned long long)l * l;
+}
+
+// The cell's moments from its reduced sums (the tail of cell_fix).
+__device__ __forceinline__ CellFix cellfix_from(int E, int32_t n, const FixAcc& q) {
+  CellFix C;
+  C.f = cell_scale(E, n);
+  const int s = fix_split(n);
+  C.sx = q.sx; C.sy = q.sy; C.sz = q.sz;
+  const unsigned __int128 s2 = ((unsigned __int128)q.A << (2 * s)) + ((unsigned __int128)q.B << (s + 1)) +
+                               (unsigned __int128)q.L;
+  const long long nn = n;
+  C.mx = nn > 0 ? div_round(C.sx, nn) : 0;
+  C.my = nn > 0 ? div_round(C.sy, nn) : 0;
+  C.mz = nn > 0 ? div_round(C.sz, nn) : 0;
+  const __int128 corr = (__int128)C.mx * (2 * (__int128)C.sx - (__int128)nn * C.mx) +
+                        (__int128)C.my * (2 * (__int128)C.sy - (__int128)nn * C.my) +
+                        (__int128)C.mz * (2 * (__int128)C.sz - (__int128)nn * C.mz);
+  C.th = s2 - (unsigned __int128)corr;
+  return C;
+}
+
 __device__ __forceinline__ double th_double(unsigned __int128 v) {
   return fma((double)(unsigned long long)(v >> 64), 18446744073709551616.0, (double)(unsigned long long)v);
 }

@@ -43,13 +43,14 @@ __global__ void k_sel_nwords(SelArgs a) {
   if ((threadIdx.x & 31) == 0 && total) atomicAdd(a.n_cand, total);
 }
 
-// Stage the cell's velocities (FP32) in this warp's shared-memory slice and
-// derive the screening constants.
+// Stage the cell's velocities (FP32) in this warp's shared-memory slice
+// (none when sm is null: the candidates then read FP64 from global memory)
+// and derive the screening constants.
 __device__ __forceinline__ CellView stage_cell(const SelArgs& a, float* sm, int32_t base, int32_t N,
                                                double sgk, int lane) {
   CellView cv;
   float vmax = 0.f;
-  if (N <= kStage) {
+  if (sm && N <= kStage) {
     float* x = sm; float* y = sm + kStage; float* z = sm + 2 * kStage;
     for (int32_t t = lane; t < N; t += 32) {
       const float fx = f64_to_f32(a.vx[base + t]), fy = f64_to_f32(a.vy[base + t]), fz = f64_to_f32(a.vz[base + t]);
@@ -73,7 +74,7 @@ __device__ __forceinline__ CellView stage_cell(const SelArgs& a, float* sm, int3
   return cv;
 }
 
-__global__ void __launch_bounds__(kSelWarps * 32) k_sel_count(SelArgs a) {
+__global__ void __launch_bounds__(kSelWarps * 32, 4) k_sel_count(SelArgs a) {
   if (a.step_dev) a.step = *a.step_dev;
   __shared__ float stage[kSelWarps][3 * kStage];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -115,15 +116,22 @@ __global__ void __launch_bounds__(kSelWarps * 32) k_sel_count(SelArgs a) {
   }
 }
 
-constexpr int kEmitWarps = 4;
-constexpr int kEmitPairs = 1024;  // accepted pairs of a cell kept in shared memory
+constexpr int kEmitWarps = 8;
+constexpr int kEmitWords = 16;    // accept-bit words expanded per step (512 candidates)
 
-// five blocks per SM (shared memory allows five): registers capped to match
-__global__ void __launch_bounds__(kEmitWarps * 32, 5) k_sel_emit(SelArgs a) {
+// Warp per cell.  The accepted candidates come from the count pass's accept
+// bits (kEmitWords words at a time, compacted in candidate order into the
+// warp's list); their particles are drawn 32 at a time (the generator runs
+// once per accepted candidate with every lane busy) and each batch of 32
+// pairs gets its rounds at once (batch_rounds), so no per-cell pair buffer
+// is kept.  A cell whose bits were not kept re-evaluates its candidates
+// from the FP64 velocities; a cell of more than kStage particles takes its
+// rounds on one lane from global memory.
+__global__ void __launch_bounds__(kEmitWarps * 32, 4) k_sel_emit(SelArgs a) {
   if (a.step_dev) a.step = *a.step_dev;
-  __shared__ float stage[kEmitWarps][3 * kStage];
-  __shared__ uint32_t spairs[kEmitWarps][kEmitPairs];   // local i | local j << 16, candidate order
-  __shared__ uint16_t slast[kEmitWarps][kStage];         // last round of each particle (+1; 0 = none)
+  __shared__ uint32_t slist[kEmitWarps][kEmitWords * 32];  // accepted candidate indices
+  __shared__ uint32_t smsk[kEmitWarps][kStage];            // per-particle lane masks (batch_rounds)
+  __shared__ uint16_t slast[kEmitWarps][kStage];           // last round of each particle (+1; 0 = none)
   __shared__ int hist[DSMC_MAX_ROUNDS];
   __shared__ int rmax_blk;
   for (int t = threadIdx.x; t < DSMC_MAX_ROUNDS; t += blockDim.x) hist[t] = 0;
@@ -133,145 +141,128 @@ __global__ void __launch_bounds__(kEmitWarps * 32, 5) k_sel_emit(SelArgs a) {
   const bool over = total > a.capacity;
   if (over && blockIdx.x == 0 && threadIdx.x == 0) set_status(a.status, DSMC_ERR_CAPACITY);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  uint32_t* list = slist[wid];
+  uint32_t* msk = smsk[wid];
+  uint16_t* last = slast[wid];
   const int32_t warps = gridDim.x * kEmitWarps;
+  int rm = -1;
   for (int32_t k = blockIdx.x * kEmitWarps + wid; k < a.n_cells && !over; k += warps) {
     const int32_t base = a.cs[k], N = a.cs[k + 1] - base;
     if (N < 2) continue;
     const double sgk = a.sgmax[k];
     const int32_t M = a.ncand[k];
-    // accept bits from the count pass when they were kept, else re-evaluate
     const bool from_bits = bits_kept(a, k, M);
     const int64_t w0 = a.wofs[k];
-    CellView cv{};
-    if (!from_bits) cv = stage_cell(a, stage[wid], base, N, sgk, lane);
     const int32_t p0 = a.offs[k], p1 = a.offs[k + 1];
-    const bool local = N <= kStage && p1 - p0 <= kEmitPairs;
-    int32_t pos = p0;
-    if (from_bits) {
-      // Accepted candidates first compacted in candidate order (32 words at a
-      // time, lane L expanding word L into the staging slice, unused on this
-      // path), then drawn 32 at a time: the generator runs once per accepted
-      // candidate with every lane busy.
-      uint32_t* list = (uint32_t*)stage[wid];
-      const int32_t nwords = (M + 31) / 32;
-      for (int32_t wb = 0; wb < nwords; wb += 32) {
-        const int32_t wi = wb + lane;
-        uint32_t bw = wi < nwords ? a.bits[w0 + wi] : 0u;
-        const int cnt = __popc(bw);
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int v = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += v;
-        }
-        const int tot = __shfl_sync(0xffffffffu, incl, 31);
-        int r = incl - cnt;
-        while (bw) {
-          list[r++] = (uint32_t)(wi * 32 + __ffs(bw) - 1);
-          bw &= bw - 1u;
-        }
-        __syncwarp();
-        for (int t0 = 0; t0 < tot; t0 += 32) {
-          const int t = t0 + lane;
-          if (t < tot) {
-            const int32_t m = (int32_t)list[t];
-            int32_t i, j;
-            cand_ij(a, k, N, m, &i, &j);
-            const int32_t q = pos + t;
-            a.tmp[q] = make_int4(base + i, base + j, k, m);
-            if (local) spairs[wid][q - p0] = (uint32_t)i | ((uint32_t)j << 16);
-          }
-        }
-        pos += tot;
-        __syncwarp();
-      }
-    }
-    for (int32_t c0 = 0; c0 < M && !from_bits; c0 += 32) {
-      const int32_t m = c0 + lane;
-      int32_t i = 0, j = 0;
-      double sg;
-      const bool ok = m < M && candidate(a, cv, CellRef{a.vx, a.vy, a.vz, base}, k, N, m, sgk, &i, &j, &sg);
-      const unsigned mask = __ballot_sync(0xffffffffu, ok);
-      if (ok) {
-        const int32_t q = pos + __popc(mask & ((1u << lane) - 1u));
-        a.tmp[q] = make_int4(base + i, base + j, k, m);
-        if (local) spairs[wid][q - p0] = (uint32_t)i | ((uint32_t)j << 16);
-      }
-      pos += __popc(mask);
-    }
+    const bool local = N <= kStage;
     if (local) {
-      for (int32_t t = lane; t < N; t += 32) slast[wid][t] = 0;
+      for (int32_t t = lane; t < N; t += 32) { last[t] = 0; msk[t] = 0u; }
     } else {
       for (int32_t t = lane; t < N; t += 32) a.last[base + t] = -1;
     }
     __syncwarp();
-    // rounds in candidate order: round = 1 + max(last round of i, of j)
-    if (local) {
-      // Warp-parallel, batch of 32 pairs (candidate order) at a time
-      // (batch_rounds).
-      uint16_t* last = slast[wid];
-      uint32_t* msk = (uint32_t*)stage[wid];   // the velocity staging is no longer needed
-      for (int32_t t = lane; t < N; t += 32) msk[t] = 0u;
-      __syncwarp();
-      int rm = -1;
-      const unsigned below = (1u << lane) - 1u;
-      for (int32_t b0 = p0; b0 < p1; b0 += 32) {
-        const int32_t p = b0 + lane;
-        const bool act = p < p1;
-        const uint32_t ij = act ? spairs[wid][p - p0] : 0u;
+    int32_t pos = p0;
+    // one batch of up to 32 accepted pairs in candidate order: lane t holds
+    // pair pos + t (act), candidate m, particles i, j
+    auto batch = [&](bool act, int32_t m, int32_t i, int32_t j, int cnt) {
+      const int32_t q = pos + lane;
+      if (act) a.tmp[q] = make_int4(base + i, base + j, k, m);
+      if (local) {
         int Li, Lj;
-        const int r = batch_rounds(act, ij & 0xFFFFu, ij >> 16, msk, last, a.status, &Li, &Lj);
+        const int r = batch_rounds(act, (uint32_t)i, (uint32_t)j, msk, last, a.status, &Li, &Lj);
         if (act) {
-          a.tmp_round[p] = r;
-          a.tmp_dep[p] = (uint32_t)Li | ((uint32_t)Lj << 16);
+          a.tmp_round[q] = r;
+          a.tmp_dep[q] = (uint32_t)Li | ((uint32_t)Lj << 16);
           rm = r > rm ? r : rm;
         }
         const unsigned am = __ballot_sync(0xffffffffu, act);
         if (act) {
           const unsigned same = __match_any_sync(am, r);
-          if ((same & below) == 0) atomicAdd(&hist[r], __popc(same));
+          if ((same & lt) == 0) atomicAdd(&hist[r], __popc(same));
         }
         __syncwarp();
       }
-      rm = __reduce_max_sync(0xffffffffu, rm);
-      if (lane == 0) {
-        atomicMax(&rmax_blk, rm + 1);
-        a.sgmax[k] = a.sgnew[k];
-      }
-    } else if (lane == 0) {
-      int rm = -1;
-      {
-        for (int32_t p = p0; p < p1; ++p) {
-          const int4 q = a.tmp[p];
-          const int li = a.last[q.x], lj = a.last[q.y];
-          int r = 1 + (li > lj ? li : lj);
-          if (r >= DSMC_MAX_ROUNDS) { set_status(a.status, DSMC_ERR_UNSUPPORTED); r = DSMC_MAX_ROUNDS - 1; }
-          a.last[q.x] = r;
-          a.last[q.y] = r;
-          a.tmp_round[p] = r;
-          a.tmp_dep[p] = (uint32_t)(li + 1) | ((uint32_t)(lj + 1) << 16);
-          atomicAdd(&hist[r], 1);
-          rm = r > rm ? r : rm;
+      pos += cnt;
+    };
+    if (from_bits) {
+      const int32_t nwords = (M + 31) / 32;
+      for (int32_t wb = 0; wb < nwords; wb += kEmitWords) {
+        const int nq = min(kEmitWords, nwords - wb);
+        const uint32_t bw = lane < nq ? a.bits[w0 + wb + lane] : 0u;
+        const int cnt = __popc(bw);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < kEmitWords; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += v;
         }
+        const int tot = __shfl_sync(0xffffffffu, incl, kEmitWords - 1);
+        const int before = incl - cnt;
+        for (int q = 0; q < nq; ++q) {
+          const uint32_t wq = __shfl_sync(0xffffffffu, bw, q);
+          const int bq = __shfl_sync(0xffffffffu, before, q);
+          if ((wq >> lane) & 1u) list[bq + __popc(wq & lt)] = (uint32_t)((wb + q) * 32 + lane);
+        }
+        __syncwarp();
+        for (int t0 = 0; t0 < tot; t0 += 32) {
+          const int t = t0 + lane;
+          const bool act = t < tot;
+          int32_t m = 0, i = 0, j = 1;
+          if (act) {
+            m = (int32_t)list[t];
+            cand_ij(a, k, N, m, &i, &j);
+          }
+          batch(act, m, i, j, min(32, tot - t0));
+        }
+        __syncwarp();
       }
-      atomicMax(&rmax_blk, rm + 1);
-      a.sgmax[k] = a.sgnew[k];
+    } else {
+      // bits not kept: re-evaluate every candidate (FP64 velocities from global memory)
+      CellView cv = stage_cell(a, nullptr, base, N, sgk, lane);
+      for (int32_t c0 = 0; c0 < M; c0 += 32) {
+        const int32_t m = c0 + lane;
+        int32_t i = 0, j = 1;
+        double sg;
+        const bool ok = m < M && candidate(a, cv, CellRef{a.vx, a.vy, a.vz, base}, k, N, m, sgk, &i, &j, &sg);
+        const unsigned mask = __ballot_sync(0xffffffffu, ok);
+        // compact the accepted lanes into lanes 0.. in candidate order
+        int32_t cm = 0, ci = 0, cj = 1;
+        for (int q = 0; q < 32; ++q) {
+          if (!((mask >> q) & 1u)) continue;
+          const int r = __popc(mask & ((1u << q) - 1u));
+          const int32_t vm = __shfl_sync(0xffffffffu, m, q), vi = __shfl_sync(0xffffffffu, i, q),
+                        vj = __shfl_sync(0xffffffffu, j, q);
+          if (lane == r) { cm = vm; ci = vi; cj = vj; }
+        }
+        const int cnt = __popc(mask);
+        batch(lane < cnt, cm, ci, cj, cnt);
+      }
     }
+    __syncwarp();   // the cell's pairs (written by all lanes) before lane 0 reads them
+    if (!local && lane == 0) {
+      for (int32_t p = p0; p < p1; ++p) {
+        const int4 q = a.tmp[p];
+        const int li = a.last[q.x], lj = a.last[q.y];
+        int r = 1 + (li > lj ? li : lj);
+        if (r >= DSMC_MAX_ROUNDS) { set_status(a.status, DSMC_ERR_UNSUPPORTED); r = DSMC_MAX_ROUNDS - 1; }
+        a.last[q.x] = r;
+        a.last[q.y] = r;
+        a.tmp_round[p] = r;
+        a.tmp_dep[p] = (uint32_t)(li + 1) | ((uint32_t)(lj + 1) << 16);
+        atomicAdd(&hist[r], 1);
+        rm = r > rm ? r : rm;
+      }
+    }
+    if (lane == 0) a.sgmax[k] = a.sgnew[k];
     __syncwarp();
   }
+  rm = __reduce_max_sync(0xffffffffu, rm);
+  if (lane == 0 && rm >= 0) atomicMax(&rmax_blk, rm + 1);
   __syncthreads();
   for (int t = threadIdx.x; t < DSMC_MAX_ROUNDS; t += blockDim.x)
     if (hist[t]) atomicAdd(a.round_count + t, hist[t]);
   if (threadIdx.x == 0 && rmax_blk > 0) atomicMax(a.n_rounds, rmax_blk);
-}
-
-// Cells with fewer than two particles keep their (sigma g)_max; cells whose
-// emit was skipped (capacity overflow) get the new value here.
-__global__ void k_sel_sg_commit(SelArgs a) {
-  const int64_t total = a.offs[a.n_cells];
-  if (total <= a.capacity) return;
-  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n_cells; k += gridDim.x * blockDim.x)
-    a.sgmax[k] = a.sgnew[k];
 }
 
 constexpr int kScatterChunk = 4096;
@@ -282,12 +273,21 @@ constexpr int kScatterChunk = 4096;
 // the round's offset, then each chunk writes its pairs in order.  Inside a
 // round the pairs keep the cell-major candidate order, so the list is
 // deterministic and the pairs of a round's first cells come first.
+//
+// On a capacity overflow the emit pass skipped every cell; k_sel_rcount
+// then commits the new (sigma g)_max of every cell instead (cells with
+// fewer than two particles keep theirs).
 __global__ void __launch_bounds__(256)
 k_sel_rcount(const int32_t* __restrict__ tmp_round, const int32_t* __restrict__ offs, int32_t n_cells,
-             int64_t capacity, const int32_t* __restrict__ n_rounds, int32_t n_chunks, int32_t* __restrict__ cnt) {
+             int64_t capacity, const int32_t* __restrict__ n_rounds, int32_t n_chunks, int32_t* __restrict__ cnt,
+             const double* __restrict__ sgnew, double* __restrict__ sgmax) {
   __shared__ int hist[DSMC_MAX_ROUNDS];
   const int64_t total = offs[n_cells];
-  if (total > capacity) return;
+  if (total > capacity) {
+    for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n_cells; k += gridDim.x * blockDim.x)
+      sgmax[k] = sgnew[k];
+    return;
+  }
   const int64_t p0 = (int64_t)blockIdx.x * kScatterChunk;
   if (p0 >= total) return;
   const int64_t p1 = p0 + kScatterChunk < total ? p0 + kScatterChunk : total;
@@ -299,19 +299,67 @@ k_sel_rcount(const int32_t* __restrict__ tmp_round, const int32_t* __restrict__ 
   for (int t = threadIdx.x; t < R; t += blockDim.x) cnt[(size_t)t * n_chunks + blockIdx.x] = hist[t];
 }
 
-// Block r: exclusive scan of cnt[r][0..chunks) + round_off[r] (in place).
+// Block r: exclusive scan of cnt[r][0..chunks) + the offset of round r (in
+// place).  The round offsets (exclusive scan of the per-round counts) are
+// formed here too: block r sums the counts of rounds < r, and block 0
+// writes the whole list.
+__device__ __forceinline__ int block_sum_256(int v, int* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  int t = 0;
+  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+  return t;
+}
+
 __global__ void __launch_bounds__(256)
 k_sel_rscan(const int32_t* __restrict__ offs, int32_t n_cells, int64_t capacity,
-            const int32_t* __restrict__ n_rounds, const int32_t* __restrict__ round_off, int32_t n_chunks,
-            int32_t* __restrict__ cnt) {
+            const int32_t* __restrict__ n_rounds, const int32_t* __restrict__ round_count,
+            int32_t* __restrict__ round_off, int32_t n_chunks, int32_t* __restrict__ cnt) {
   __shared__ int warp_tot[8];
+  __shared__ int red[8];
   __shared__ int carry;
   const int64_t total = offs[n_cells];
   if (total > capacity || (int)blockIdx.x >= *n_rounds) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (blockIdx.x == 0) {
+    // round_off[0..DSMC_MAX_ROUNDS]: kPer consecutive counts per thread
+    constexpr int kPer = (DSMC_MAX_ROUNDS + 255) / 256;
+    int v[kPer], sum = 0;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int r = threadIdx.x * kPer + q;
+      v[q] = r < DSMC_MAX_ROUNDS ? round_count[r] : 0;
+      sum += v[q];
+    }
+    int x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    int run = x - sum;
+    for (int q = 0; q < w; ++q) run += warp_tot[q];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int r = threadIdx.x * kPer + q;
+      if (r < DSMC_MAX_ROUNDS) round_off[r] = run;
+      run += v[q];
+    }
+    if (threadIdx.x == blockDim.x - 1) round_off[DSMC_MAX_ROUNDS] = run;   // the total
+    __syncthreads();
+  }
+  int part = 0;
+  for (int q = threadIdx.x; q < (int)blockIdx.x; q += blockDim.x) part += round_count[q];
+  part = block_sum_256(part, red);
   const int chunks = (int)((total + kScatterChunk - 1) / kScatterChunk);
   int32_t* row = cnt + (size_t)blockIdx.x * n_chunks;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (threadIdx.x == 0) carry = round_off[blockIdx.x];
+  if (threadIdx.x == 0) carry = part;
   __syncthreads();
   for (int c0 = 0; c0 < chunks; c0 += blockDim.x) {
     const int c = c0 + threadIdx.x;
@@ -481,15 +529,14 @@ int launch_select(Ctx* c, const dsmc_gas_t& gas, int32_t n, int32_t n_cells, con
     int rc = launch_scan(c, w.counts, w.offs, n_cells, w.scan, s);
     if (rc) return rc;
     k_sel_emit<<<blocks_for(n_cells, kEmitWarps, sms * 16), kEmitWarps * 32, 0, s>>>(a);
-    k_sel_sg_commit<<<blocks_for(n_cells, 256, sms * 4), 256, 0, s>>>(a);
-    count_launches(c, 2);
-    rc = launch_scan(c, w.round_count, round_offsets, DSMC_MAX_ROUNDS, w.scan, s);
-    if (rc) return rc;
-    const unsigned sb = (unsigned)((capacity + kScatterChunk - 1) / kScatterChunk);
-    if (sb > 0) {
-      k_sel_rcount<<<sb, 256, 0, s>>>(w.tmp_round, w.offs, n_cells, capacity, w.n_rounds, w.n_chunks, w.chunk_cnt);
-      k_sel_rscan<<<DSMC_MAX_ROUNDS, 256, 0, s>>>(w.offs, n_cells, capacity, w.n_rounds, round_offsets,
-                                                 w.n_chunks, w.chunk_cnt);
+    count_launches(c, 1);
+    // at least one block: the capacity-overflow commit of (sigma g)_max runs in k_sel_rcount
+    const unsigned sb = (unsigned)((capacity + kScatterChunk - 1) / kScatterChunk) + (capacity <= 0);
+    {
+      k_sel_rcount<<<sb, 256, 0, s>>>(w.tmp_round, w.offs, n_cells, capacity, w.n_rounds, w.n_chunks, w.chunk_cnt,
+                                      w.sgnew, sgmax);
+      k_sel_rscan<<<DSMC_MAX_ROUNDS, 256, 0, s>>>(w.offs, n_cells, capacity, w.n_rounds, w.round_count,
+                                                 round_offsets, w.n_chunks, w.chunk_cnt);
       k_sel_scatter<<<sb, kScatterWarps * 32, 0, s>>>(w.tmp, w.tmp_round, w.tmp_dep, w.offs, n_cells, capacity,
                                                        w.n_rounds, w.n_chunks, w.chunk_cnt, (int4*)pairs, deps);
       count_launches(c, 3);

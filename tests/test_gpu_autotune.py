@@ -81,8 +81,8 @@ def _reset(C, D):
 
 # non-default shapes: small blocks, few blocks per SM, large blocks
 SHAPES = [
-    {0: (128, 2), 1: (64, 4), 2: (64, 32), 3: (64, 1), 4: (32, 1), 6: (64, 1)},
-    {0: (512, 4), 1: (128, 16), 2: (256, 4), 3: (128, 2), 4: (64, 2), 6: (128, 2)},
+    {0: (128, 2), 1: (256, 1), 2: (256, 2), 3: (64, 1), 4: (32, 1), 6: (64, 1)},
+    {0: (512, 4), 1: (256, 3), 2: (256, 5), 3: (128, 2), 4: (64, 2), 6: (128, 2)},
 ]
 
 
@@ -112,7 +112,7 @@ def test_tune_set_rejects_bad_shapes_and_resets():
     default = C.tune_get(D.TUNE_KERNELS.index("collide_jager"))
     assert default == (128, 0)  # full occupancy
     for args in [(7, 128, 1), (-1, 128, 1), (0, 48, 4), (0, 2048, 1), (1, 512, 4), (0, 128, 0),
-                 (0, 128, 65), (4, 256, 1)]:
+                 (0, 128, 65), (4, 256, 1), (1, 128, 2), (2, 64, 1)]:
         with pytest.raises(D.DsmcError) as e:
             C.tune_set(*args)
         assert e.value.code == D.DSMC_ERR_ARG
