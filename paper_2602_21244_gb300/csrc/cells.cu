@@ -356,20 +356,31 @@ k_rs_count(const int32_t* __restrict__ cell_id, const uint32_t* __restrict__ key
 // warp's earlier batches; the batches' atomics are ordered by __syncwarp),
 // the others their rank inside the group.  (2) After the counts are
 // complete, each counter becomes the warp's starting position for its digit
-// (the chunk's base from the scan, then the warps in order) and every
-// element goes to start + old value of its group's leader + rank.  No
-// element waits on the shared-memory result of the batch before it.
+// in the chunk's own digit order (the digit's start in the chunk, then the
+// warps in order), and every element's place is that warp start + old
+// value of its group's leader + rank.  No element waits on the
+// shared-memory result of the batch before it.  (3) The chunk is reordered
+// by digit in shared memory and written out from there: consecutive threads
+// write consecutive addresses of each digit's run (its global start from
+// the scan), so the stores coalesce.
 // Values: the input index (first pass) or vals.
 constexpr int kRsPer = kRsChunk / kRsWarps / 32;
+static_assert(kRsWarps * 32 == kRadix, "one thread per digit in the offset step");
 
 __global__ void __launch_bounds__(kRsWarps * 32, 2)
 k_rs_scatter(const int32_t* __restrict__ cell_id, const uint32_t* __restrict__ keys,
              const int32_t* __restrict__ vals, int32_t n, int32_t n_cells, int shift, int32_t chunks,
              const int32_t* __restrict__ base, uint32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out) {
-  __shared__ int wh[kRsWarps][kRadix];
+  __shared__ union {
+    int wh[kRsWarps][kRadix];                              // per-warp digit counters, then positions
+    struct { uint32_t key[kRsChunk]; int32_t val[kRsChunk]; } st;  // the chunk in digit order
+  } sm;
+  __shared__ int gdelta[kRadix];   // global start - chunk-local start of each digit
+  __shared__ int wt[kRsWarps];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int t = threadIdx.x; t < kRsWarps * kRadix; t += blockDim.x) wh[t / kRadix][t % kRadix] = 0;
-  const int64_t s0 = (int64_t)blockIdx.x * kRsChunk + (int64_t)w * (kRsPer * 32);
+  for (int t = threadIdx.x; t < kRsWarps * kRadix; t += blockDim.x) sm.wh[t / kRadix][t % kRadix] = 0;
+  const int64_t c0 = (int64_t)blockIdx.x * kRsChunk;
+  const int64_t s0 = c0 + (int64_t)w * (kRsPer * 32);
   uint32_t key[kRsPer];
   int32_t val[kRsPer];
 #pragma unroll
@@ -399,27 +410,62 @@ k_rs_scatter(const int32_t* __restrict__ cell_id, const uint32_t* __restrict__ k
     }
     const int rank = __popc(peers & lt);
     old[j] = 0;
-    if (has && rank == 0) old[j] = atomicAdd(&wh[w][d], __popc(peers));
+    if (has && rank == 0) old[j] = atomicAdd(&sm.wh[w][d], __popc(peers));
     pk[j] = (uint32_t)(__ffs(peers) - 1) | ((uint32_t)rank << 5);
     __syncwarp();
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
-    int acc = base[(size_t)d * chunks + blockIdx.x];
+  {
+    // thread d: the warps' positions for digit d inside the chunk's digit
+    // order (exclusive scan of the digit totals, then the warps in order)
+    const int d = threadIdx.x;
+    int tot = 0;
 #pragma unroll
-    for (int q = 0; q < kRsWarps; ++q) { const int c = wh[q][d]; wh[q][d] = acc; acc += c; }
+    for (int q = 0; q < kRsWarps; ++q) tot += sm.wh[q][d];
+    int x = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wt[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      int v = lane < kRsWarps ? wt[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < kRsWarps; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+      }
+      if (lane < kRsWarps) wt[lane] = v;
+    }
+    __syncthreads();
+    const int ls = (w ? wt[w - 1] : 0) + x - tot;   // chunk-local start of digit d
+    gdelta[d] = base[(size_t)d * chunks + blockIdx.x] - ls;
+    int acc = ls;
+#pragma unroll
+    for (int q = 0; q < kRsWarps; ++q) { const int c = sm.wh[q][d]; sm.wh[q][d] = acc; acc += c; }
   }
   __syncthreads();
+  int lp[kRsPer];
 #pragma unroll
   for (int j = 0; j < kRsPer; ++j) {
-    const bool has = s0 + j * 32 + lane < n;
     const int o = __shfl_sync(0xffffffffu, old[j], (int)(pk[j] & 31u));
-    if (has) {
-      const int d = (int)((key[j] >> shift) & (kRadix - 1));
-      const int q = wh[w][d] + o + (int)(pk[j] >> 5);
-      if (keys_out) keys_out[q] = key[j];
-      vals_out[q] = val[j];
-    }
+    const int d = (int)((key[j] >> shift) & (kRadix - 1));
+    lp[j] = sm.wh[w][d] + o + (int)(pk[j] >> 5);
+  }
+  __syncthreads();   // every position read before the counters' storage is reused
+#pragma unroll
+  for (int j = 0; j < kRsPer; ++j) {
+    if (s0 + j * 32 + lane < n) { sm.st.key[lp[j]] = key[j]; sm.st.val[lp[j]] = val[j]; }
+  }
+  __syncthreads();
+  const int cnt = (int)min((int64_t)kRsChunk, (int64_t)n - c0);
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+    const uint32_t k = sm.st.key[t];
+    const int q = t + gdelta[(k >> shift) & (kRadix - 1)];
+    if (keys_out) keys_out[q] = k;
+    vals_out[q] = sm.st.val[t];
   }
 }
 

@@ -482,7 +482,7 @@ int launch_step_fused(Ctx* c, const dsmc_gas_t& gas, int path, const dsmc_chi_ta
   FusedArgs a;
   a.sel = SelArgs{};
   a.sel.sgmax = sgmax; a.sel.status = status_ptr(c); a.sel.n_cells = n_cells;
-  a.sel.seed = gas.seed; a.sel.step = step; a.sel.step_dev = nullptr;   // not captured in the step graph
+  a.sel.seed = gas.seed; a.sel.key = philox_key(gas.seed); a.sel.step = step; a.sel.step_dev = nullptr;   // not captured in the step graph
   a.sel.fn = gas.fn_over_vc; a.sel.dt = gas.dt;
   sel_model(a.sel, gas);
   a.look = path == DSMC_PATH_TABLE ? table_look(gas, *tab) : TableLook{};

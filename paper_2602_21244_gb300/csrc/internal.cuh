@@ -40,6 +40,37 @@ __device__ __forceinline__ u32x4 draw(uint64_t seed, uint32_t idx, uint32_t cell
                 (uint32_t)seed, (uint32_t)(seed >> 32));
 }
 
+// The same generator with its ten round keys formed once on the host (the
+// Weyl sequence of the seed), so that inside a kernel they are launch
+// constants: each round is then two multiplies and two three-way XORs with
+// a constant operand, with no key arithmetic per draw.
+struct PhiloxKey {
+  uint32_t k0[10], k1[10];
+};
+
+inline PhiloxKey philox_key(uint64_t seed) {
+  PhiloxKey K;
+  uint32_t a = (uint32_t)seed, b = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    K.k0[r] = a; K.k1[r] = b;
+    a += 0x9E3779B9u; b += 0xBB67AE85u;
+  }
+  return K;
+}
+
+__device__ __forceinline__ u32x4 draw_k(const PhiloxKey& K, uint32_t idx, uint32_t cell, uint64_t step,
+                                        uint32_t tag, uint32_t sub = 0) {
+  uint32_t c0 = idx, c1 = cell, c2 = (uint32_t)step, c3 = tag | (sub << 8) | ((uint32_t)(step >> 32) << 16);
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ K.k0[r], n2 = hi0 ^ c3 ^ K.k1[r];
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+  }
+  return {c0, c1, c2, c3};
+}
+
 // 53-bit uniform in [0,1): exact in double
 __device__ __forceinline__ double u53(uint32_t a, uint32_t b) {
   const uint64_t x = ((((uint64_t)a) << 32) | b) >> 11;

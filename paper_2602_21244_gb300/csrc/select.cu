@@ -511,7 +511,7 @@ int launch_select(Ctx* c, const dsmc_gas_t& gas, int32_t n, int32_t n_cells, con
   a.wcnt = w.wcnt; a.wofs = w.wofs; a.bits = w.bits; a.words_cap = w.words_cap; a.ncand = w.ncand;
   a.last = w.last; a.round_count = w.round_count; a.n_rounds = w.n_rounds; a.n_cand = w.n_cand;
   a.status = status_ptr(c); a.n_cells = n_cells; a.capacity = capacity;
-  a.seed = gas.seed; a.step = step; a.step_dev = graph_step_ptr(c); a.fn = gas.fn_over_vc; a.dt = gas.dt;
+  a.seed = gas.seed; a.key = philox_key(gas.seed); a.step = step; a.step_dev = graph_step_ptr(c); a.fn = gas.fn_over_vc; a.dt = gas.dt;
   sel_model(a, gas);
   const int sms = sm_count(c);
   if (cudaMemsetAsync(w.round_count, 0, sizeof(int32_t) * DSMC_MAX_ROUNDS * 2 + 256, s) != cudaSuccess)

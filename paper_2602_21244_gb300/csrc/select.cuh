@@ -32,6 +32,7 @@ struct SelArgs {
   int32_t model;
   int64_t capacity;
   uint64_t seed, step;
+  PhiloxKey key;             // round keys of seed
   const uint64_t* step_dev;  // if set, the step index is read here (graph replay)
   double fn, dt;
   // model 0: sigma(g) = pid2 * pow(x, om_half) / gam, x = two_kt / ((mr g) g)
@@ -50,7 +51,7 @@ __device__ __forceinline__ double sigma_g(const SelArgs& a, double g) {
 }
 
 __device__ __forceinline__ int32_t ntc_count(const SelArgs& a, int32_t k, int32_t N, int* bad) {
-  const u32x4 w = draw(a.seed, 0, (uint32_t)k, a.step, TAG_NTC);
+  const u32x4 w = draw_k(a.key, 0, (uint32_t)k, a.step, TAG_NTC);
   double mt = __dmul_rn(0.5, (double)N);
   mt = __dmul_rn(mt, (double)(N - 1));
   mt = __dmul_rn(mt, a.fn);
@@ -104,7 +105,7 @@ __device__ __forceinline__ bool bits_kept(const SelArgs& a, int32_t k, int32_t M
 // Particles (local indices) of candidate m of cell k (tag 2).
 __device__ __forceinline__ void cand_ij(const SelArgs& a, int32_t k, int32_t N, int32_t m, int32_t* pi,
                                         int32_t* pj) {
-  const u32x4 w = draw(a.seed, (uint32_t)m, (uint32_t)k, a.step, TAG_CAND);
+  const u32x4 w = draw_k(a.key, (uint32_t)m, (uint32_t)k, a.step, TAG_CAND);
   const uint32_t i = mulhi_n(w.x, (uint32_t)N);
   uint32_t j = mulhi_n(w.y, (uint32_t)(N - 1));
   j += (j >= i);
@@ -119,7 +120,7 @@ __device__ __forceinline__ void cand_ij(const SelArgs& a, int32_t k, int32_t N, 
 __device__ __forceinline__ bool candidate(const SelArgs& a, const CellView& cv, const CellRef& v, int32_t k,
                                           int32_t N, int32_t m, double sgmax_k, int32_t* pi, int32_t* pj,
                                           double* raise_sg) {
-  const u32x4 w = draw(a.seed, (uint32_t)m, (uint32_t)k, a.step, TAG_CAND);
+  const u32x4 w = draw_k(a.key, (uint32_t)m, (uint32_t)k, a.step, TAG_CAND);
   const uint32_t i = mulhi_n(w.x, (uint32_t)N);
   uint32_t j = mulhi_n(w.y, (uint32_t)(N - 1));
   j += (j >= i);
