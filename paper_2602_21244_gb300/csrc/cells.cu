@@ -347,6 +347,38 @@ k_rs_count(const int32_t* __restrict__ cell_id, const uint32_t* __restrict__ key
   for (int t = threadIdx.x; t < kRadix; t += blockDim.x) cnt[(size_t)t * chunks + blockIdx.x] = hist[t];
 }
 
+// Block d: exclusive scan of digit d's counts over the chunks (row d of
+// the digit-major table, in place into off) and the digit's total.
+__global__ void __launch_bounds__(256)
+k_rs_rowscan(const int32_t* __restrict__ cnt, int32_t chunks, int32_t* __restrict__ off, int32_t* __restrict__ tot) {
+  __shared__ int wt[8];
+  __shared__ int carry;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int32_t* row = cnt + (size_t)blockIdx.x * chunks;
+  int32_t* orow = off + (size_t)blockIdx.x * chunks;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int32_t c0 = 0; c0 < chunks; c0 += 256) {
+    const int32_t c = c0 + threadIdx.x;
+    const int v = c < chunks ? row[c] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wt[w] = x;
+    __syncthreads();
+    int before = carry;
+    for (int q = 0; q < w; ++q) before += wt[q];
+    if (c < chunks) orow[c] = before + x - v;
+    __syncthreads();
+    if (threadIdx.x == 255) carry = before + x;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) tot[blockIdx.x] = carry;
+}
+
 // Ordered scatter of one chunk: warp w owns the chunk's w-th sixteenth, its
 // kRsPer elements per lane loaded into registers first.  Stable ranks in
 // two steps: (1) per element batch j (32 consecutive elements), the lanes
@@ -370,13 +402,14 @@ static_assert(kRsWarps * 32 == kRadix, "one thread per digit in the offset step"
 __global__ void __launch_bounds__(kRsWarps * 32, 2)
 k_rs_scatter(const int32_t* __restrict__ cell_id, const uint32_t* __restrict__ keys,
              const int32_t* __restrict__ vals, int32_t n, int32_t n_cells, int shift, int32_t chunks,
-             const int32_t* __restrict__ base, uint32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out) {
+             const int32_t* __restrict__ base, const int32_t* __restrict__ tot, uint32_t* __restrict__ keys_out,
+             int32_t* __restrict__ vals_out) {
   __shared__ union {
     int wh[kRsWarps][kRadix];                              // per-warp digit counters, then positions
     struct { uint32_t key[kRsChunk]; int32_t val[kRsChunk]; } st;  // the chunk in digit order
   } sm;
   __shared__ int gdelta[kRadix];   // global start - chunk-local start of each digit
-  __shared__ int wt[kRsWarps];
+  __shared__ int wt[kRsWarps], wg[kRsWarps];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int t = threadIdx.x; t < kRsWarps * kRadix; t += blockDim.x) sm.wh[t / kRadix][t % kRadix] = 0;
   const int64_t c0 = (int64_t)blockIdx.x * kRsChunk;
@@ -418,30 +451,34 @@ k_rs_scatter(const int32_t* __restrict__ cell_id, const uint32_t* __restrict__ k
   {
     // thread d: the warps' positions for digit d inside the chunk's digit
     // order (exclusive scan of the digit totals, then the warps in order)
+    // (and the digit's global start: the totals of the smaller digits plus
+    // the digit's count in earlier chunks)
     const int d = threadIdx.x;
-    int tot = 0;
+    int ct = 0;
 #pragma unroll
-    for (int q = 0; q < kRsWarps; ++q) tot += sm.wh[q][d];
-    int x = tot;
+    for (int q = 0; q < kRsWarps; ++q) ct += sm.wh[q][d];
+    const int gt = tot[d];
+    int x = ct, xg = gt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+      const int y = __shfl_up_sync(0xffffffffu, x, o), yg = __shfl_up_sync(0xffffffffu, xg, o);
+      if (lane >= o) { x += y; xg += yg; }
     }
-    if (lane == 31) wt[w] = x;
+    if (lane == 31) { wt[w] = x; wg[w] = xg; }
     __syncthreads();
     if (w == 0) {
-      int v = lane < kRsWarps ? wt[lane] : 0;
+      int v = lane < kRsWarps ? wt[lane] : 0, vg = lane < kRsWarps ? wg[lane] : 0;
 #pragma unroll
       for (int o = 1; o < kRsWarps; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += y;
+        const int y = __shfl_up_sync(0xffffffffu, v, o), yg = __shfl_up_sync(0xffffffffu, vg, o);
+        if (lane >= o) { v += y; vg += yg; }
       }
-      if (lane < kRsWarps) wt[lane] = v;
+      if (lane < kRsWarps) { wt[lane] = v; wg[lane] = vg; }
     }
     __syncthreads();
-    const int ls = (w ? wt[w - 1] : 0) + x - tot;   // chunk-local start of digit d
-    gdelta[d] = base[(size_t)d * chunks + blockIdx.x] - ls;
+    const int ls = (w ? wt[w - 1] : 0) + x - ct;    // chunk-local start of digit d
+    const int gs = (w ? wg[w - 1] : 0) + xg - gt;   // global start of digit d
+    gdelta[d] = gs + base[(size_t)d * chunks + blockIdx.x] - ls;
     int acc = ls;
 #pragma unroll
     for (int q = 0; q < kRsWarps; ++q) { const int c = sm.wh[q][d]; sm.wh[q][d] = acc; acc += c; }
@@ -505,8 +542,8 @@ size_t sort_ws(int32_t n, int32_t n_cells) {
   const size_t chunks = (nn + kRsChunk - 1) / kRsChunk;
   const size_t tab = (size_t)kRadix * chunks;
   return 4 * align256(sizeof(uint32_t) * nn)        // keys and values, two buffers each
-         + 2 * align256(sizeof(int32_t) * (tab + 1)) // digit counts and their scan
-         + scan_ws((int64_t)tab);
+         + 2 * align256(sizeof(int32_t) * (tab + 1)) // digit counts and their scan along the chunks
+         + align256(sizeof(int32_t) * kRadix);       // digit totals
 }
 
 static unsigned grid_for(int64_t work, int per_block, int max_blocks) {
@@ -540,7 +577,7 @@ int launch_sort_keys(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_id,
   int32_t* vb = (int32_t*)take(4 * nn);
   int32_t* cnt = (int32_t*)take(4 * (tab + 1));
   int32_t* off = (int32_t*)take(4 * (tab + 1));
-  void* sws = p;
+  int32_t* dtot = (int32_t*)take(sizeof(int32_t) * kRadix);   // digit totals
   if (n == 0) {
     k_cell_start<<<1, 256, 0, s>>>(kb, 0, n_cells, cell_start);
     count_launches(c, 1);
@@ -556,11 +593,10 @@ int launch_sort_keys(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_id,
     k_rs_count<<<chunks, 256, 0, s>>>(cell_id, kin, n, n_cells, q * kRadixBits, chunks, cnt,
                                       q == 0 ? status_ptr(c) : nullptr);
     count_launches(c, 1);
-    int rc = launch_scan(c, cnt, off, (int64_t)tab, sws, s);
-    if (rc) return rc;
+    k_rs_rowscan<<<kRadix, 256, 0, s>>>(cnt, chunks, off, dtot);
     k_rs_scatter<<<chunks, kRsWarps * 32, 0, s>>>(cell_id, kin, vin, n, n_cells, q * kRadixBits, chunks, off,
-                                                  kout, vout);
-    count_launches(c, 1);
+                                                  dtot, kout, vout);
+    count_launches(c, 2);
     kin = kout;
     vin = vout;
   }
