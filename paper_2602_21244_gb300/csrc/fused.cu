@@ -251,6 +251,7 @@ __device__ __forceinline__ void run_batch(const FusedArgs& a, FusedShared& S, co
     const int32_t ls = S.cstart[ci];
     CellView cv;
     cv.x = mem.fx + ls; cv.y = mem.fy + ls; cv.z = mem.fz + ls;
+    cv.v4 = nullptr;
     cv.dg = S.cdg[ci];
     cv.sgmax32 = S.csg32[ci];
     cv.inv_sgmax32 = 1.f / cv.sgmax32;

@@ -46,22 +46,22 @@ __global__ void k_sel_nwords(SelArgs a) {
 // Stage the cell's velocities (FP32) in this warp's shared-memory slice
 // (none when sm is null: the candidates then read FP64 from global memory)
 // and derive the screening constants.
-__device__ __forceinline__ CellView stage_cell(const SelArgs& a, float* sm, int32_t base, int32_t N,
+__device__ __forceinline__ CellView stage_cell(const SelArgs& a, float4* sm, int32_t base, int32_t N,
                                                double sgk, int lane) {
   CellView cv;
+  cv.x = cv.y = cv.z = nullptr;
+  cv.v4 = nullptr;
   float vmax = 0.f;
   if (sm && N <= kStage) {
-    float* x = sm; float* y = sm + kStage; float* z = sm + 2 * kStage;
     for (int32_t t = lane; t < N; t += 32) {
       const float fx = f64_to_f32(a.vx[base + t]), fy = f64_to_f32(a.vy[base + t]), fz = f64_to_f32(a.vz[base + t]);
-      x[t] = fx; y[t] = fy; z[t] = fz;
+      sm[t] = make_float4(fx, fy, fz, 0.f);
       vmax = fmaxf(vmax, fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))));
     }
-    cv.x = x; cv.y = y; cv.z = z;
+    cv.v4 = sm;
   } else {
     for (int32_t t = lane; t < N; t += 32)
       vmax = fmaxf(vmax, (float)fmax(fabs(a.vx[base + t]), fmax(fabs(a.vy[base + t]), fabs(a.vz[base + t]))));
-    cv.x = cv.y = cv.z = nullptr;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
@@ -76,7 +76,7 @@ __device__ __forceinline__ CellView stage_cell(const SelArgs& a, float* sm, int3
 
 __global__ void __launch_bounds__(kSelWarps * 32, 4) k_sel_count(SelArgs a) {
   if (a.step_dev) a.step = *a.step_dev;
-  __shared__ float stage[kSelWarps][3 * kStage];
+  __shared__ float4 stage[kSelWarps][kStage];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int32_t warps = gridDim.x * kSelWarps;
   for (int32_t k = blockIdx.x * kSelWarps + wid; k < a.n_cells; k += warps) {
@@ -381,19 +381,24 @@ k_sel_rscan(const int32_t* __restrict__ offs, int32_t n_cells, int64_t capacity,
   }
 }
 
-// Block (8 warps) per chunk; warp w owns the chunk's w-th eighth.  Each
-// warp counts its rounds, the counts are turned into per-warp starting
-// positions (warps in order after the chunk's base), then each warp writes
-// its pairs in order, the rank among equal rounds within 32 lanes coming
-// from __match_any_sync.
-constexpr int kScatterWarps = 8;
+// Block (16 warps) per chunk; warp w owns the chunk's w-th sixteenth, its
+// rounds loaded first.  Stable ranks without a shared-memory round trip per
+// batch: in each batch of 32 pairs the lanes of equal round find each other
+// with __match_any_sync, the lowest adds the group's size to the warp's
+// counter of that round (atomic, ordered across batches by __syncwarp) and
+// keeps the old value; once the counts are complete they become per-warp
+// starting positions (warps in order after the chunk's base), and each
+// pair goes to start + its leader's old value + its rank in the group.
+// The counters live in dynamic shared memory, kScatterWarps x n_rounds.
+constexpr int kScatterWarps = 16;
+constexpr int kScatterPer = kScatterChunk / kScatterWarps / 32;
 
-__global__ void __launch_bounds__(kScatterWarps * 32)
+__global__ void __launch_bounds__(kScatterWarps * 32, 2)
 k_sel_scatter(const int4* __restrict__ tmp, const int32_t* __restrict__ tmp_round,
               const uint32_t* __restrict__ tmp_dep, const int32_t* __restrict__ offs, int32_t n_cells,
               int64_t capacity, const int32_t* __restrict__ n_rounds, int32_t n_chunks,
               const int32_t* __restrict__ base, int4* __restrict__ out, uint32_t* __restrict__ deps) {
-  __shared__ int wh[kScatterWarps][DSMC_MAX_ROUNDS];
+  extern __shared__ int swh[];   // [kScatterWarps][R]
   const int64_t total = offs[n_cells];
   if (total > capacity) return;
   const int64_t p0 = (int64_t)blockIdx.x * kScatterChunk;
@@ -401,31 +406,42 @@ k_sel_scatter(const int4* __restrict__ tmp, const int32_t* __restrict__ tmp_roun
   const int64_t p1 = p0 + kScatterChunk < total ? p0 + kScatterChunk : total;
   const int R = *n_rounds;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  constexpr int kSub = kScatterChunk / kScatterWarps;
-  const int64_t s0 = p0 + (int64_t)w * kSub, s1 = s0 + kSub < p1 ? s0 + kSub : p1;
-  for (int t = threadIdx.x; t < kScatterWarps * R; t += blockDim.x) wh[t / R][t % R] = 0;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int t = threadIdx.x; t < kScatterWarps * R; t += blockDim.x) swh[t] = 0;
+  const int64_t s0 = p0 + (int64_t)w * (kScatterPer * 32);
+  int rr[kScatterPer];
+#pragma unroll
+  for (int j = 0; j < kScatterPer; ++j) {
+    const int64_t p = s0 + j * 32 + lane;
+    rr[j] = p < p1 ? tmp_round[p] : -1;
+  }
   __syncthreads();
-  for (int64_t p = s0 + lane; p < s1; p += 32) atomicAdd(&wh[w][tmp_round[p]], 1);
+  int old[kScatterPer];
+  uint32_t pk[kScatterPer];   // leader lane | rank in the group << 5
+#pragma unroll
+  for (int j = 0; j < kScatterPer; ++j) {
+    const unsigned peers = __match_any_sync(0xffffffffu, rr[j]);
+    const int rank = __popc(peers & lt);
+    old[j] = 0;
+    if (rr[j] >= 0 && rank == 0) old[j] = atomicAdd(&swh[w * R + rr[j]], __popc(peers));
+    pk[j] = (uint32_t)(__ffs(peers) - 1) | ((uint32_t)rank << 5);
+    __syncwarp();
+  }
   __syncthreads();
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
     int acc = base[(size_t)r * n_chunks + blockIdx.x];
-    for (int q = 0; q < kScatterWarps; ++q) { const int c = wh[q][r]; wh[q][r] = acc; acc += c; }
+    for (int q = 0; q < kScatterWarps; ++q) { const int c = swh[q * R + r]; swh[q * R + r] = acc; acc += c; }
   }
   __syncthreads();
-  const unsigned lt = (1u << lane) - 1u;
-  for (int64_t q0 = s0; q0 < s1; q0 += 32) {
-    const int64_t p = q0 + lane;
-    const bool has = p < s1;
-    const int r = has ? tmp_round[p] : -1;
-    const unsigned same = __match_any_sync(0xffffffffu, r);
-    if (has) {
-      const int q = wh[w][r] + __popc(same & lt);
+#pragma unroll
+  for (int j = 0; j < kScatterPer; ++j) {
+    const int o = __shfl_sync(0xffffffffu, old[j], (int)(pk[j] & 31u));
+    if (rr[j] >= 0) {
+      const int64_t p = s0 + j * 32 + lane;
+      const int q = swh[w * R + rr[j]] + o + (int)(pk[j] >> 5);
       out[q] = tmp[p];
       deps[q] = tmp_dep[p];
     }
-    __syncwarp();
-    if (has && (same & lt) == 0) wh[w][r] += __popc(same);
-    __syncwarp();
   }
 }
 
@@ -537,7 +553,10 @@ int launch_select(Ctx* c, const dsmc_gas_t& gas, int32_t n, int32_t n_cells, con
                                       w.sgnew, sgmax);
       k_sel_rscan<<<DSMC_MAX_ROUNDS, 256, 0, s>>>(w.offs, n_cells, capacity, w.n_rounds, w.round_count,
                                                  round_offsets, w.n_chunks, w.chunk_cnt);
-      k_sel_scatter<<<sb, kScatterWarps * 32, 0, s>>>(w.tmp, w.tmp_round, w.tmp_dep, w.offs, n_cells, capacity,
+      const int ssm = (int)(sizeof(int) * kScatterWarps * DSMC_MAX_ROUNDS);
+      if (cudaFuncSetAttribute(k_sel_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, ssm) != cudaSuccess)
+        return DSMC_ERR_CUDA;
+      k_sel_scatter<<<sb, kScatterWarps * 32, ssm, s>>>(w.tmp, w.tmp_round, w.tmp_dep, w.offs, n_cells, capacity,
                                                        w.n_rounds, w.n_chunks, w.chunk_cnt, (int4*)pairs, deps);
       count_launches(c, 3);
     }

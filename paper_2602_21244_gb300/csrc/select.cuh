@@ -90,6 +90,7 @@ constexpr int kStage = 384;
 
 struct CellView {
   const float *x, *y, *z;  // staged FP32 velocities, or null
+  const float4* v4;        // or staged as (x, y, z, 0) per particle (one 16-byte load each)
   float dg;                // bound on the FP32 error of g for this cell
   float sgmax32, inv_sgmax32, thr_raise;
 };
@@ -126,7 +127,10 @@ __device__ __forceinline__ bool candidate(const SelArgs& a, const CellView& cv, 
   j += (j >= i);
   *pi = (int32_t)i; *pj = (int32_t)j;
   float dx, dy, dz;
-  if (cv.x) {
+  if (cv.v4) {
+    const float4 pi4 = cv.v4[i], pj4 = cv.v4[j];
+    dx = pi4.x - pj4.x; dy = pi4.y - pj4.y; dz = pi4.z - pj4.z;
+  } else if (cv.x) {
     dx = cv.x[i] - cv.x[j]; dy = cv.y[i] - cv.y[j]; dz = cv.z[i] - cv.z[j];
   } else {
     dx = (float)(v.x(i) - v.x(j));
