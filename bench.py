@@ -66,11 +66,11 @@ KERNEL_OPS = {
 
 # the kernels of each phase of the step (for the per-phase rooflines)
 PHASE_KERNELS = {
-    "sort": ["k_rs_count", "k_scan_*", "k_rs_scatter", "k_cell_start", "k_gather1"],
-    "moments": ["k_moments"],
-    "select": ["k_sel_nwords", "k_sel_count", "k_sel_emit", "k_sel_rcount", "k_sel_rscan", "k_sel_scatter",
-               "k_scan_*"],
-    "moment_match": ["k_moment_match"],
+    "sort": ["k_rs_count", "k_rs_rowscan", "k_rs_scatter", "k_cell_start", "k_gather1"],
+    "moments": ["k_cells<false>"],
+    "select": ["k_sel_nwords", "k_scan_*", "k_sel_count", "k_sel_emit", "k_sel_rcount", "k_sel_rscan",
+               "k_sel_scatter", "k_sel_finalize"],
+    "moment_match": ["k_cells<true>"],
 }
 COLLIDE_KERNEL = {"vhs": "k_collide_vhs", "table": "k_collide_table", "jager": "k_collide_jager",
                   "neural": "k_collide_neural"}
