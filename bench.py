@@ -40,10 +40,10 @@ MLP_FLOP_PER_PAIR = 2 * (8 * 128 + 128 * 128 * 2 + 128 * 3)   # 68,352 (unpadded
 CHI_MLP_FLOP_PER_QUERY = 2 * (2 * 512 + 512 * 512 * 2 + 512 * 256 + 256 * 128 + 128)
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per pair of
 # k_collide_neural, from one ncu capture of a full-size launch on the
-# hypersonic gas: 985.9 + 949.1 MB for about 6.882 million pairs
-# (profiles/step_kernels_hypersonic.md); the roofline's traffic is this times
-# the pairs of the timed launch.
-NEURAL_DRAM_BYTES_PER_PAIR = (985.86e6 + 949.13e6) / 6.882e6
+# hypersonic gas: 1070.7 + 932.6 MB for about 6.882 million pairs
+# (the committed ncu summary of this kernel); the roofline's traffic is this
+# times the pairs of the timed launch.
+NEURAL_DRAM_BYTES_PER_PAIR = (1070.69e6 + 932.64e6) / 6.882e6
 CANDIDATE_BYTES = 48                                             # two FP64 3-vectors read
 PAIR_BYTES = 104                                                 # 2x24 read + 2x24 write + 8 index
 # special-function operations per pair of the neural collide: 3 hidden layers
@@ -52,7 +52,7 @@ PAIR_BYTES = 104                                                 # 2x24 read + 2
 MLP_MUFU_PER_PAIR = 3 * 128 * 1.25
 
 # Per-pair instruction counts of the ALU-bound collide kernels, from one ncu
-# capture each (profiles/collide_kernels_ops.md: sm__sass_thread_inst_executed_
+# capture each (the committed ncu summary of the collide kernels: sm__sass_thread_inst_executed_
 # op_{dfma,dadd,dmul,ffma,ffma2,fadd,fmul,...}_pred_on.sum and
 # sm__inst_executed_pipe_xu.sum x 32, divided by the launch's pairs); None
 # until captured for the current kernels.  FP64 and FP32 in FLOPs (an FMA is

@@ -176,11 +176,7 @@ __global__ void __launch_bounds__(kEmitWarps * 32, 4) k_sel_emit(SelArgs a) {
           a.tmp_dep[q] = (uint32_t)Li | ((uint32_t)Lj << 16);
           rm = r > rm ? r : rm;
         }
-        const unsigned am = __ballot_sync(0xffffffffu, act);
-        if (act) {
-          const unsigned same = __match_any_sync(am, r);
-          if ((same & lt) == 0) atomicAdd(&hist[r], __popc(same));
-        }
+        if (act) atomicAdd(&hist[r], 1);
         __syncwarp();
       }
       pos += cnt;
@@ -384,7 +380,7 @@ k_sel_rscan(const int32_t* __restrict__ offs, int32_t n_cells, int64_t capacity,
 // Block (16 warps) per chunk; warp w owns the chunk's w-th sixteenth, its
 // rounds loaded first.  Stable ranks without a shared-memory round trip per
 // batch: in each batch of 32 pairs the lanes of equal round find each other
-// with __match_any_sync, the lowest adds the group's size to the warp's
+// from ballots over the round's bits, the lowest adds the group's size to the warp's
 // counter of that round (atomic, ordered across batches by __syncwarp) and
 // keeps the old value; once the counts are complete they become per-warp
 // starting positions (warps in order after the chunk's base), and each
@@ -420,7 +416,14 @@ k_sel_scatter(const int4* __restrict__ tmp, const int32_t* __restrict__ tmp_roun
   uint32_t pk[kScatterPer];   // leader lane | rank in the group << 5
 #pragma unroll
   for (int j = 0; j < kScatterPer; ++j) {
-    const unsigned peers = __match_any_sync(0xffffffffu, rr[j]);
+    // lanes of equal round (or without a pair): one ballot per bit of the
+    // round numbers in use (the match instruction measured slower)
+    unsigned peers = __ballot_sync(0xffffffffu, rr[j] >= 0);
+    if (rr[j] < 0) peers = ~peers;
+    for (int bit = 0; (1 << bit) < R; ++bit) {
+      const unsigned m = __ballot_sync(0xffffffffu, (rr[j] >> bit) & 1);
+      peers &= ((rr[j] >> bit) & 1) ? m : ~m;
+    }
     const int rank = __popc(peers & lt);
     old[j] = 0;
     if (rr[j] >= 0 && rank == 0) old[j] = atomicAdd(&swh[w * R + rr[j]], __popc(peers));

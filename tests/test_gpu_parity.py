@@ -208,6 +208,50 @@ def test_select_bit_exact(name, model):
     assert rel.max() <= (0.0 if model == 1 else 4e-16)
 
 
+def _dense_cells(seed=5):
+    """Cells of 2, 40, 120, 383, 384, 385 and 600 particles (the FP32 staging
+    holds 384) at a number density that gives a few hundred candidates per
+    particle in the large cells, hence long chains of pairs sharing
+    particles: 73 rounds (VHS) and 622 (hard spheres), seven and ten bits of
+    round number."""
+    rng = np.random.default_rng(seed)
+    sizes = [2, 40, 120, 383, 384, 385, 600]
+    cs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    n = int(cs[-1])
+    s = math.sqrt(KB * 300.0 / W.M_AR)
+    v = rng.standard_normal((n, 3)) * s + np.array([300.0, 0.0, 0.0])
+    return cs, v[:, 0].copy(), v[:, 1].copy(), v[:, 2].copy()
+
+
+@pytest.mark.parametrize("model", [1, 0])
+def test_select_bit_exact_dense_cells(model):
+    cs, vx, vy, vz = _dense_cells()
+    nc = len(cs) - 1
+    gas_d = dict(mass=W.M_AR, d_ref=4.17e-10, omega=0.81, T_ref=273.0, fn_over_vc=1e21, dt=1e-7,
+                 seed=7, model=model, b_max=1.2e-9)
+    gas = O.make_gas(**gas_d)
+    sg0 = O.sigma_g_max_init(gas, np.full(nc, 300.0), 3.0)
+    ref = O.select_pairs(gas, cs, vx, vy, vz, sg0, 2, capacity=1 << 22)
+    assert ref["n_rounds"] > 64, ref["n_rounds"]
+    from paper_2602_21244_gb300 import dsmc as D
+    C = ctx()
+    sg = cuda(sg0).clone()
+    sel = C.select_pairs(D.make_gas(gas_d), cuda(cs), cuda(vx), cuda(vy), cuda(vz), sg, 2, 1 << 22)
+    assert C.sync_status() == 0
+    sh = sel_host(sel)
+    assert sh["n_pairs"] == ref["n_pairs"] and sh["n_cand"] == ref["n_cand"]
+    assert sh["n_rounds"] == ref["n_rounds"]
+    p = sh["pairs"]
+    rr = pairs_round_of(sh)
+    order = np.lexsort((p[:, 3], p[:, 2]))
+    assert np.array_equal(p[order, 0], ref["i"]) and np.array_equal(p[order, 1], ref["j"])
+    assert np.array_equal(p[order, 3], ref["m"]) and np.array_equal(rr[order], ref["round"])
+    ro_ = np.lexsort((ref["m"], ref["cell"], ref["round"]))
+    assert np.array_equal(p[:, 2], ref["cell"][ro_]) and np.array_equal(p[:, 3], ref["m"][ro_])
+    rel = np.abs(host(sg) - ref["sgmax"]) / ref["sgmax"]
+    assert rel.max() <= (0.0 if model == 1 else 4e-16)
+
+
 def test_select_capacity_overflow_reported():
     w = wl("hyper01")
     gas = O.make_gas(**w["gas"])
