@@ -26,6 +26,10 @@ struct Ctx {
   void* r_host_info = nullptr;
   // dsmc_step_host: a side stream for the copies that overlap the step
   cudaStream_t r_side = nullptr;
+  // dsmc_step: a side stream for the cell moments, which run beside the
+  // selection (both only read the sorted velocities)
+  cudaStream_t f_side = nullptr;
+  cudaEvent_t f_ev[2] = {nullptr, nullptr};
   cudaEvent_t r_ev[4] = {nullptr, nullptr, nullptr, nullptr};
   int64_t launches = 0;
   int64_t graph_launches = 0;
@@ -143,7 +147,10 @@ int dsmc_ctx_create(dsmc_ctx_t** out, int device) {
             cudaMalloc(&c->d_bar, 256) == cudaSuccess &&
             cudaMallocHost(&c->h_status, 256) == cudaSuccess &&
             cudaMemset(c->d_status, 0, 256) == cudaSuccess &&
-            cudaMemset(c->d_bar, 0, 256) == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
+            cudaMemset(c->d_bar, 0, 256) == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess &&
+            cudaStreamCreateWithFlags(&c->f_side, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&c->f_ev[0], cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&c->f_ev[1], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     dsmc_ctx_destroy(c);
     return DSMC_ERR_CUDA;
@@ -164,6 +171,9 @@ void dsmc_ctx_destroy(dsmc_ctx_t* c) {
   for (cudaEvent_t e : c->r_ev)
     if (e) cudaEventDestroy(e);
   if (c->r_side) cudaStreamDestroy(c->r_side);
+  for (cudaEvent_t e : c->f_ev)
+    if (e) cudaEventDestroy(e);
+  if (c->f_side) cudaStreamDestroy(c->f_side);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   delete c;
 }
@@ -598,18 +608,25 @@ int dsmc_step(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t* path,
   return step_after_sort(c, gas, path, B, step, stream);
 }
 
-// the step from the sorted velocities on: moments, selection, pair update,
-// moment matching
+// the step from the sorted velocities on: moments (on the context's side
+// stream, beside the selection: both only read the sorted velocities),
+// selection, pair update, moment matching (after the moments have joined)
 static int step_after_sort(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t* path,
                            const dsmc_step_buffers_t* B, uint64_t step, void* stream) {
-  int rc = dsmc_cell_moments(c, B->n_cells, B->cell_start, B->svx, B->svy, B->svz, B->mom, stream);
+  cudaStream_t s = S(stream);
+  if (cudaEventRecord(c->f_ev[0], s) != cudaSuccess || cudaStreamWaitEvent(c->f_side, c->f_ev[0], 0) != cudaSuccess)
+    return dsmc::record(c, DSMC_ERR_CUDA, "step: fork of the moments stream failed");
+  int rc = dsmc_cell_moments(c, B->n_cells, B->cell_start, B->svx, B->svy, B->svz, B->mom, c->f_side);
+  // the side stream joins the caller's stream whatever happens next
+  const bool joined_ev = cudaEventRecord(c->f_ev[1], c->f_side) == cudaSuccess;
+  if (!rc)
+    rc = dsmc_select_pairs(c, gas, B->n, B->n_cells, B->cell_start, B->svx, B->svy, B->svz,
+                           B->sigma_g_max, step, B->capacity, B->pairs, B->deps, B->round_offsets, B->info,
+                           B->ws, B->ws_bytes, stream);
+  if (!rc) rc = collide_step(c, gas, path, B, step, stream);
+  const bool joined = joined_ev && cudaStreamWaitEvent(s, c->f_ev[1], 0) == cudaSuccess;
   if (rc) return rc;
-  rc = dsmc_select_pairs(c, gas, B->n, B->n_cells, B->cell_start, B->svx, B->svy, B->svz,
-                         B->sigma_g_max, step, B->capacity, B->pairs, B->deps, B->round_offsets, B->info,
-                         B->ws, B->ws_bytes, stream);
-  if (rc) return rc;
-  rc = collide_step(c, gas, path, B, step, stream);
-  if (rc) return rc;
+  if (!joined) return dsmc::record(c, DSMC_ERR_CUDA, "step: join of the moments stream failed");
   return dsmc_moment_match(c, B->n_cells, B->cell_start, B->mom, B->svx, B->svy, B->svz, stream);
 }
 
