@@ -65,6 +65,17 @@ KERNEL_OPS = {
 }
 
 # the kernels of each phase of the step (for the per-phase rooflines)
+# Warp instructions issued per step by the shared phases on the full
+# hypersonic gas (9,144,283 particles, 150,000 cells), from one ncu capture
+# of smsp__inst_executed.sum over a bench run (median launch of each kernel
+# times its launches per step); the selection's depend on the collision
+# model (21.6M candidates for hard spheres, 3.2M for VHS).  They give the
+# phases' instruction-issue roof (only at that size).
+ISSUE_REF_PARTICLES = 9144283
+PHASE_WARP_INSTR = {
+    1: {"sort": 155.78e6, "moments": 60.94e6, "select": 289.08e6, "moment_match": 77.84e6},
+    0: {"sort": 155.78e6, "moments": 60.96e6, "select": 92.44e6, "moment_match": 77.84e6},
+}
 PHASE_KERNELS = {
     "sort": ["k_rs_count", "k_rs_rowscan", "k_rs_scatter", "k_cell_start", "k_gather1"],
     "moments": ["k_cells<false>"],
@@ -151,14 +162,17 @@ def roof_entry(achieved, peak, unit, peak_source):
             "peak_source": peak_source}
 
 
-def phase_rooflines(path, n, nc, pairs, phase_ms, pipe, pk):
+def phase_rooflines(path, n, nc, pairs, phase_ms, pipe, pk, issue_peak=None):
     """Per-phase (per-kernel for the collide) achieved rates against their
     roofs: HBM for sort, moments, selection and moment matching (algorithmic
     bytes of phase_bytes); for the collide HBM (104 B/pair) and, per path,
     the tensor pipe (neural: 68,352 FLOP/pair, bf16 burst peak: the kernel
     runs inside a 4 ms step), the MUFU (neural: 480 operations/pair), and the
     FP64 / FP32 / MUFU pipes from the kernel's per-pair instruction counts
-    (KERNEL_OPS).  "bound" is the roof with the largest fraction."""
+    (KERNEL_OPS); for the shared phases on the full gas also instruction
+    issue (PHASE_WARP_INSTR against issue_peak warp instructions/s: 4 per
+    cycle per SM at the maximum SM clock).  "bound" is the roof with the
+    largest fraction."""
     hbm = pk.get("hbm_gbs") if pk else 6800.0
     hbm_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if pk else "fallback 6800 GB/s"
     bf16 = pk.get("bf16_tflops") if pk else 1900.0
@@ -168,6 +182,11 @@ def phase_rooflines(path, n, nc, pairs, phase_ms, pipe, pk):
     for ph, ms in phase_ms.items():
         t = ms * 1e-3
         roofs = {"hbm": roof_entry(pb[ph] / t / 1e9, hbm, "GB/s", hbm_src)}
+        instr = PHASE_WARP_INSTR[0 if path == "vhs" else 1].get(ph)
+        if issue_peak and instr and n == ISSUE_REF_PARTICLES:
+            roofs["issue"] = roof_entry(instr / t / 1e9, issue_peak / 1e9, "Ginst/s",
+                                        "nominal issue rate: 4 warp instructions per cycle per SM at the "
+                                        "maximum SM clock (ncu instruction counts)")
         kern = PHASE_KERNELS.get(ph)
         if ph == "collide":
             kname = COLLIDE_KERNEL[path]
@@ -419,7 +438,10 @@ def run_gb300(args, rank, world, dist):
         pk = peaks()
         hbm = pk.get("hbm_gbs") if pk else 6800.0
         phase_gbs = {k: pb[k] / (phase_ms[k] / K * 1e-3) / 1e9 for k in pb}
-        roofs = phase_rooflines(path, n, nc, pairs / K, {k: v / K for k, v in phase_ms.items()}, pipe, pk)
+        sm_clk = (pk.get("sm_max_mhz") if pk else None) or 2070.0
+        issue_peak = torch.cuda.get_device_properties(dev).multi_processor_count * 4 * sm_clk * 1e6
+        roofs = phase_rooflines(path, n, nc, pairs / K, {k: v / K for k, v in phase_ms.items()}, pipe, pk,
+                                issue_peak)
         results[path] = dict(
             rooflines=roofs,
             collisions_per_s=g_pairs / (g_ms * 1e-3), ms_per_step=g_ms / K,
