@@ -412,14 +412,16 @@ k_rs_scatter(const int32_t* __restrict__ cell_id, const uint32_t* __restrict__ k
   __shared__ int wt[kRsWarps], wg[kRsWarps];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int t = threadIdx.x; t < kRsWarps * kRadix; t += blockDim.x) sm.wh[t / kRadix][t % kRadix] = 0;
-  const int64_t c0 = (int64_t)blockIdx.x * kRsChunk;
-  const int64_t s0 = c0 + (int64_t)w * (kRsPer * 32);
+  // 32-bit unsigned indices (below n + 4096 < 2^32)
+  const uint32_t un = (uint32_t)n;
+  const uint32_t c0 = blockIdx.x * (uint32_t)kRsChunk;
+  const uint32_t s0 = c0 + (uint32_t)w * (kRsPer * 32);
   uint32_t key[kRsPer];
   int32_t val[kRsPer];
 #pragma unroll
   for (int j = 0; j < kRsPer; ++j) {
-    const int64_t i = s0 + j * 32 + lane;
-    const bool has = i < n;
+    const uint32_t i = s0 + j * 32 + lane;
+    const bool has = i < un;
     key[j] = has ? rs_key(cell_id, keys, i, n_cells, nullptr) : 0u;
     val[j] = has ? (vals ? vals[i] : (int32_t)i) : 0;
   }
@@ -429,7 +431,7 @@ k_rs_scatter(const int32_t* __restrict__ cell_id, const uint32_t* __restrict__ k
   uint32_t pk[kRsPer];   // leader lane | rank in the group << 5
 #pragma unroll
   for (int j = 0; j < kRsPer; ++j) {
-    const bool has = s0 + j * 32 + lane < n;
+    const bool has = s0 + j * 32 + lane < un;
     // lanes without an element share the digit kRadix (no counter)
     const int d = has ? (int)((key[j] >> shift) & (kRadix - 1)) : kRadix;
     // lanes holding the same digit: one ballot per digit bit (ALU pipe); the
@@ -494,10 +496,10 @@ k_rs_scatter(const int32_t* __restrict__ cell_id, const uint32_t* __restrict__ k
   __syncthreads();   // every position read before the counters' storage is reused
 #pragma unroll
   for (int j = 0; j < kRsPer; ++j) {
-    if (s0 + j * 32 + lane < n) { sm.st.key[lp[j]] = key[j]; sm.st.val[lp[j]] = val[j]; }
+    if (s0 + j * 32 + lane < un) { sm.st.key[lp[j]] = key[j]; sm.st.val[lp[j]] = val[j]; }
   }
   __syncthreads();
-  const int cnt = (int)min((int64_t)kRsChunk, (int64_t)n - c0);
+  const int cnt = (int)min((uint32_t)kRsChunk, un - c0);
   for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
     const uint32_t k = sm.st.key[t];
     const int q = t + gdelta[(k >> shift) & (kRadix - 1)];
@@ -510,23 +512,23 @@ k_rs_scatter(const int32_t* __restrict__ cell_id, const uint32_t* __restrict__ k
 // (slot n closes the list with key n_cells).  Four slots per thread.
 __global__ void k_cell_start(const uint32_t* __restrict__ skeys, int32_t n, int32_t n_cells,
                              int32_t* __restrict__ cell_start) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
-  for (int64_t s0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; s0 <= n; s0 += stride) {
-    int64_t key[5];   // key[q] = skeys[s0 - 1 + q] (-1 before the first slot, n_cells from slot n on)
-    key[0] = s0 > 0 ? (int64_t)skeys[s0 - 1] : -1;
-    if (s0 + 4 <= n && ((uintptr_t)(skeys + s0) & 15) == 0) {
+  // 32-bit indices: slots 0..n (n < 2^31), keys 0..n_cells
+  const uint32_t un = (uint32_t)n, stride = gridDim.x * blockDim.x * 4u;
+  for (uint32_t s0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4u; s0 <= un; s0 += stride) {
+    int32_t key[5];   // key[q] = skeys[s0 - 1 + q] (-1 before the first slot, n_cells from slot n on)
+    key[0] = s0 > 0 ? (int32_t)skeys[s0 - 1] : -1;
+    if (s0 + 4 <= un && ((uintptr_t)(skeys + s0) & 15) == 0) {
       const uint4 k4 = __ldcs(reinterpret_cast<const uint4*>(skeys + s0));
-      key[1] = k4.x; key[2] = k4.y; key[3] = k4.z; key[4] = k4.w;
+      key[1] = (int32_t)k4.x; key[2] = (int32_t)k4.y; key[3] = (int32_t)k4.z; key[4] = (int32_t)k4.w;
     } else {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) key[q + 1] = s0 + q < n ? (int64_t)skeys[s0 + q] : (int64_t)n_cells;
+      for (int q = 0; q < 4; ++q) key[q + 1] = s0 + q < un ? (int32_t)skeys[s0 + q] : n_cells;
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int64_t s = s0 + q;
-      if (s > n) break;
-      const int64_t lo = key[q], hi = key[q + 1];
-      for (int64_t c = lo + 1; c <= hi && c <= n_cells; ++c) cell_start[c] = (int32_t)s;
+      const uint32_t s = s0 + q;
+      if (s > un) break;
+      for (int32_t c = key[q] + 1; c <= key[q + 1] && c <= n_cells; ++c) cell_start[c] = (int32_t)s;
     }
   }
 }
