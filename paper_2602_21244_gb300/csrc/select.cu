@@ -74,45 +74,113 @@ __device__ __forceinline__ CellView stage_cell(const SelArgs& a, float4* sm, int
   return cv;
 }
 
+// One cell by the whole warp (candidates 32 at a time).
+__device__ __forceinline__ void count_cell(const SelArgs& a, float4* stage, int32_t k, int lane) {
+  const int32_t base = a.cs[k], N = a.cs[k + 1] - base;
+  const double sgk = a.sgmax[k];
+  if (N < 2) {
+    if (lane == 0) { a.counts[k] = 0; a.sgnew[k] = sgk; }
+    return;
+  }
+  const int32_t M = a.ncand[k];   // from k_sel_nwords (which reports an overflow)
+  const CellView cv = stage_cell(a, stage, base, N, sgk, lane);
+  int acc = 0;
+  // The maximum is taken on the bit patterns: for non-negative doubles the
+  // int64 order is the numeric order, and it keeps the FP64 pipe free
+  // (candidates that cannot raise the maximum carry -1.0, a negative int64).
+  long long best = __double_as_longlong(sgk);
+  const int64_t w0 = a.wofs[k];
+  const bool keep = bits_kept(a, k, M);
+  for (int32_t c0 = 0; c0 < M; c0 += 32) {
+    const int32_t m = c0 + lane;
+    int32_t i, j;
+    double sg = -1.0;
+    const bool ok = m < M && candidate(a, cv, CellRef{a.vx, a.vy, a.vz, base}, k, N, m, sgk, &i, &j, &sg);
+    acc += ok;
+    best = max(best, __double_as_longlong(sg));
+    const unsigned mask = __ballot_sync(0xffffffffu, ok);
+    if (keep && lane == 0) a.bits[w0 + c0 / 32] = mask;
+  }
+  acc = warp_sum_i(acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if (lane == 0) {
+    a.counts[k] = acc;
+    a.sgnew[k] = __longlong_as_double(best);
+  }
+  __syncwarp();
+}
+
+// Two cells of at most 16 candidates each, one per half-warp (lanes 16h ..
+// 16h + 15): most cells of a dilute gas draw so few candidates that a whole
+// warp per cell would leave half its lanes idle and pay the per-cell work
+// twice.  Called by the whole warp; kk[h] = the half's cell (n_cells: none).
+__device__ __forceinline__ void count_pair(const SelArgs& a, float4* stage, const int32_t kk[2], int lane) {
+  const int h = lane >> 4, hl = lane & 15;
+  const int32_t k = kk[h];
+  const bool valid = k < a.n_cells;
+  const int32_t base = valid ? a.cs[k] : 0, N = valid ? a.cs[k + 1] - base : 0;
+  const double sgk = valid ? a.sgmax[k] : 0.0;
+  const int32_t M = N >= 2 ? a.ncand[k] : 0;
+  // the half's FP32 copy and screening constants (as stage_cell, 16 lanes)
+  float4* sm = stage + h * (kStage / 2);
+  float vmax = 0.f;
+  for (int32_t t = hl; t < N; t += 16) {
+    const float fx = f64_to_f32(a.vx[base + t]), fy = f64_to_f32(a.vy[base + t]), fz = f64_to_f32(a.vz[base + t]);
+    sm[t] = make_float4(fx, fy, fz, 0.f);
+    vmax = fmaxf(vmax, fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))));
+  }
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+  __syncwarp();
+  CellView cv;
+  cv.x = cv.y = cv.z = nullptr;
+  cv.v4 = sm;
+  cv.dg = 4.0f * vmax * 5.9604645e-8f;
+  cv.sgmax32 = f64_to_f32(sgk);
+  cv.inv_sgmax32 = 1.f / cv.sgmax32;
+  cv.thr_raise = cv.sgmax32 * (1.f - 3e-4f);
+  int32_t i, j;
+  double sg = -1.0;
+  const bool ok = hl < M && candidate(a, cv, CellRef{a.vx, a.vy, a.vz, base}, k, N, hl, sgk, &i, &j, &sg);
+  const unsigned mask = __ballot_sync(0xffffffffu, ok);
+  const unsigned word = h ? mask >> 16 : mask & 0xFFFFu;
+  long long best = valid ? __double_as_longlong(sgk) : 0ll;
+  best = max(best, __double_as_longlong(sg));
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if (hl == 0 && valid) {
+    a.counts[k] = N >= 2 ? __popc(word) : 0;
+    a.sgnew[k] = __longlong_as_double(best);
+    if (N >= 2 && M > 0 && bits_kept(a, k, M)) a.bits[a.wofs[k]] = word;
+  }
+  __syncwarp();
+}
+
+// Warp per pair of consecutive cells: both by half-warps when each draws at
+// most 16 candidates (and fits half the staging slice), else one after the
+// other by the whole warp.
 __global__ void __launch_bounds__(kSelWarps * 32, 4) k_sel_count(SelArgs a) {
   if (a.step_dev) a.step = *a.step_dev;
   __shared__ float4 stage[kSelWarps][kStage];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int32_t warps = gridDim.x * kSelWarps;
-  for (int32_t k = blockIdx.x * kSelWarps + wid; k < a.n_cells; k += warps) {
-    const int32_t base = a.cs[k], N = a.cs[k + 1] - base;
-    const double sgk = a.sgmax[k];
-    if (N < 2) {
-      if (lane == 0) { a.counts[k] = 0; a.sgnew[k] = sgk; }
-      continue;
-    }
-    const int32_t M = a.ncand[k];   // from k_sel_nwords (which reports an overflow)
-    const CellView cv = stage_cell(a, stage[wid], base, N, sgk, lane);
-    int acc = 0;
-    // The maximum is taken on the bit patterns: for non-negative doubles the
-    // int64 order is the numeric order, and it keeps the FP64 pipe free
-    // (candidates that cannot raise the maximum carry -1.0, a negative int64).
-    long long best = __double_as_longlong(sgk);
-    const int64_t w0 = a.wofs[k];
-    const bool keep = bits_kept(a, k, M);
-    for (int32_t c0 = 0; c0 < M; c0 += 32) {
-      const int32_t m = c0 + lane;
-      int32_t i, j;
-      double sg = -1.0;
-      const bool ok = m < M && candidate(a, cv, CellRef{a.vx, a.vy, a.vz, base}, k, N, m, sgk, &i, &j, &sg);
-      acc += ok;
-      best = max(best, __double_as_longlong(sg));
-      const unsigned mask = __ballot_sync(0xffffffffu, ok);
-      if (keep && lane == 0) a.bits[w0 + c0 / 32] = mask;
-    }
-    acc = warp_sum_i(acc);
+  const int32_t npairs = (a.n_cells + 1) / 2;
+  for (int32_t kp = blockIdx.x * kSelWarps + wid; kp < npairs; kp += warps) {
+    const int32_t kk[2] = {2 * kp, 2 * kp + 1 < a.n_cells ? 2 * kp + 1 : a.n_cells};
+    bool small = true;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
-    if (lane == 0) {
-      a.counts[k] = acc;
-      a.sgnew[k] = __longlong_as_double(best);
+    for (int h = 0; h < 2; ++h) {
+      if (kk[h] >= a.n_cells) continue;
+      const int32_t N = a.cs[kk[h] + 1] - a.cs[kk[h]];
+      if (N >= 2 && (N > kStage / 2 || a.ncand[kk[h]] > 16)) small = false;
     }
-    __syncwarp();
+    if (small) {
+      count_pair(a, stage[wid], kk, lane);
+    } else {
+      count_cell(a, stage[wid], kk[0], lane);
+      if (kk[1] < a.n_cells) count_cell(a, stage[wid], kk[1], lane);
+    }
   }
 }
 
@@ -542,7 +610,7 @@ int launch_select(Ctx* c, const dsmc_gas_t& gas, int32_t n, int32_t n_cells, con
     count_launches(c, 1);
     int rcw = launch_scan(c, w.wcnt, w.wofs, n_cells, w.scan, s);
     if (rcw) return rcw;
-    const unsigned gb = blocks_for(n_cells, kSelWarps, sms * 8);
+    const unsigned gb = blocks_for((n_cells + 1) / 2, kSelWarps, sms * 8);
     k_sel_count<<<gb, kSelWarps * 32, 0, s>>>(a);
     count_launches(c, 1);
     int rc = launch_scan(c, w.counts, w.offs, n_cells, w.scan, s);
