@@ -215,9 +215,10 @@ __global__ void __launch_bounds__(kEmitWarps * 32, 4) k_sel_emit(SelArgs a) {
   uint16_t* last = slast[wid];
   const int32_t warps = gridDim.x * kEmitWarps;
   int rm = -1;
-  for (int32_t k = blockIdx.x * kEmitWarps + wid; k < a.n_cells && !over; k += warps) {
+  // one cell by the whole warp
+  auto emit_cell = [&](const int32_t k) {
     const int32_t base = a.cs[k], N = a.cs[k + 1] - base;
-    if (N < 2) continue;
+    if (N < 2) return;
     const double sgk = a.sgmax[k];
     const int32_t M = a.ncand[k];
     const bool from_bits = bits_kept(a, k, M);
@@ -320,6 +321,63 @@ __global__ void __launch_bounds__(kEmitWarps * 32, 4) k_sel_emit(SelArgs a) {
     }
     if (lane == 0) a.sgmax[k] = a.sgnew[k];
     __syncwarp();
+  };
+  // two cells of at most 16 candidates each (their accept bits kept, at most
+  // kStage/2 particles), one per half-warp: the accepted candidates of a
+  // cell fit one batch of its 16 lanes, and the lane masks of the round
+  // assignment stay within a half since each half has its own particles
+  auto emit_pair = [&](const int32_t kk[2]) {
+    const int h = lane >> 4, hl = lane & 15;
+    const int32_t k = kk[h];
+    const bool valid = k < a.n_cells;
+    const int32_t base = valid ? a.cs[k] : 0, N = valid ? a.cs[k + 1] - base : 0;
+    uint32_t* mh = msk + h * (kStage / 2);
+    uint16_t* lh = last + h * (kStage / 2);
+    for (int32_t t = hl; t < N; t += 16) { lh[t] = 0; mh[t] = 0u; }
+    __syncwarp();
+    const bool live = N >= 2;
+    const int32_t M = live ? a.ncand[k] : 0;
+    const uint32_t word = M > 0 ? a.bits[a.wofs[k]] : 0u;
+    const bool act = hl < __popc(word);
+    int32_t m = 0, i = 0, j = 1;
+    if (act) {
+      uint32_t w = word;   // the hl-th accepted candidate, in candidate order
+      for (int c = 0; c < hl; ++c) w &= w - 1u;
+      m = __ffs(w) - 1;
+      cand_ij(a, k, N, m, &i, &j);
+    }
+    const int32_t q = (live ? a.offs[k] : 0) + hl;
+    if (act) a.tmp[q] = make_int4(base + i, base + j, k, m);
+    int Li, Lj;
+    const int r = batch_rounds(act, (uint32_t)i, (uint32_t)j, mh, lh, a.status, &Li, &Lj);
+    if (act) {
+      a.tmp_round[q] = r;
+      a.tmp_dep[q] = (uint32_t)Li | ((uint32_t)Lj << 16);
+      rm = r > rm ? r : rm;
+      atomicAdd(&hist[r], 1);
+    }
+    __syncwarp();
+    if (hl == 0 && live) a.sgmax[k] = a.sgnew[k];
+    __syncwarp();
+  };
+  const int32_t npairs = (a.n_cells + 1) / 2;
+  for (int32_t kp = blockIdx.x * kEmitWarps + wid; kp < npairs && !over; kp += warps) {
+    const int32_t kk[2] = {2 * kp, 2 * kp + 1 < a.n_cells ? 2 * kp + 1 : a.n_cells};
+    bool small = true;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (kk[h] >= a.n_cells) continue;
+      const int32_t N = a.cs[kk[h] + 1] - a.cs[kk[h]];
+      if (N < 2) continue;
+      const int32_t M = a.ncand[kk[h]];
+      if (N > kStage / 2 || M > 16 || !bits_kept(a, kk[h], M)) small = false;
+    }
+    if (small) {
+      emit_pair(kk);
+    } else {
+      emit_cell(kk[0]);
+      if (kk[1] < a.n_cells) emit_cell(kk[1]);
+    }
   }
   rm = __reduce_max_sync(0xffffffffu, rm);
   if (lane == 0 && rm >= 0) atomicMax(&rmax_blk, rm + 1);
@@ -615,7 +673,7 @@ int launch_select(Ctx* c, const dsmc_gas_t& gas, int32_t n, int32_t n_cells, con
     count_launches(c, 1);
     int rc = launch_scan(c, w.counts, w.offs, n_cells, w.scan, s);
     if (rc) return rc;
-    k_sel_emit<<<blocks_for(n_cells, kEmitWarps, sms * 16), kEmitWarps * 32, 0, s>>>(a);
+    k_sel_emit<<<blocks_for((n_cells + 1) / 2, kEmitWarps, sms * 16), kEmitWarps * 32, 0, s>>>(a);
     count_launches(c, 1);
     // at least one block: the capacity-overflow commit of (sigma g)_max runs in k_sel_rcount
     const unsigned sb = (unsigned)((capacity + kScatterChunk - 1) / kScatterChunk) + (capacity <= 0);
