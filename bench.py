@@ -73,8 +73,8 @@ KERNEL_OPS = {
 # phases' instruction-issue roof (only at that size).
 ISSUE_REF_PARTICLES = 9144283
 PHASE_WARP_INSTR = {
-    1: {"sort": 155.78e6, "moments": 60.94e6, "select": 289.08e6, "moment_match": 77.84e6},
-    0: {"sort": 155.78e6, "moments": 60.96e6, "select": 92.44e6, "moment_match": 77.84e6},
+    1: {"sort": 151.11e6, "moments": 60.94e6, "select": 249.49e6, "moment_match": 77.84e6},
+    0: {"sort": 151.12e6, "moments": 60.95e6, "select": 77.67e6, "moment_match": 77.84e6},
 }
 PHASE_KERNELS = {
     "sort": ["k_rs_count", "k_rs_rowscan", "k_rs_scatter", "k_cell_start", "k_gather1"],
