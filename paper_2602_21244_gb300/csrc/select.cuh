@@ -146,15 +146,25 @@ __device__ __forceinline__ bool candidate(const SelArgs& a, const CellView& cv, 
   // U32 <= U < U32 + 2^-24 (top 24 bits of the 53-bit uniform)
   const float U32 = (float)(w.z >> 8) * 5.9604645e-8f;
   // error bound of the FP32 ratio: 1e-4 relative (arithmetic, __powf) plus
-  // the effect of the FP32 rounding of the velocities on g
-  const float relg = __fdividef(cv.dg, fmaxf(g, 1e-30f));
-  const float margin = 2e-7f + ratio * (1e-4f + a.e32 * relg);
+  // the effect of the FP32 rounding of the velocities on g, ratio e32 dg/g;
+  // for hard spheres (sigma g = k32 g, e32 = 1) that term is the cell's
+  // constant k32 dg / (sigma g)_max, and dg/g > 1e-3 is g < 1e3 dg
+  float margin;
+  bool tiny_g;
+  if (a.model == 1) {
+    margin = 2e-7f + ratio * 1e-4f + a.k32 * cv.inv_sgmax32 * cv.dg;
+    tiny_g = g < 1e3f * cv.dg;
+  } else {
+    const float relg = __fdividef(cv.dg, fmaxf(g, 1e-30f));
+    margin = 2e-7f + ratio * (1e-4f + a.e32 * relg);
+    tiny_g = relg > 1e-3f;
+  }
   bool acc;
   double sg64 = -1.0;
   if (ratio > U32 + 5.9604645e-8f + margin) acc = true;
   else if (ratio < U32 - margin) acc = false;
   else acc = decide64(a, v, i, j, u53(w.z, w.w), sgmax_k, &sg64);
-  if (sg > cv.thr_raise || relg > 1e-3f) {
+  if (sg > cv.thr_raise || tiny_g) {
     if (sg64 < 0.0) decide64(a, v, i, j, 0.0, sgmax_k, &sg64);
   } else {
     sg64 = -1.0;
