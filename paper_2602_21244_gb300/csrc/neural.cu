@@ -39,6 +39,8 @@ constexpr int kWidth = 128;
 constexpr int kKin = 32;         // input as two bf16 terms: [hi (16) | lo (16)]
 constexpr int kNout = 16;        // padded output width
 constexpr int kMaxHidden = 4;
+constexpr int kBiasCol = 13;     // X columns 13..15 (hi term) hold 1.0, against the bias terms
+constexpr uint32_t kBiasTile = kWidth * 8 * 2;   // [128 x 8] bf16: columns 8..15 of a bias step's B
 constexpr int kStashWords = 16;  // per-row pair data handed from builder to updater threads
 // columns of a hidden layer's epilogue per TMEM read (16: four independent
 // SiLU chains of a thread per wait; 32 spilled at the 128-register cap of a
@@ -60,8 +62,8 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t* r) {
 // `slots` tile slots (one per warp group) has its own X, activation tiles,
 // mbarrier and flag.
 struct MlpLayout {
-  uint32_t w_out, w_in, w_sq, slot0, slot_bytes, bias, ybuf, ybuf_bytes, mbar, tptr, flag, claim, fail, stash,
-      total;
+  uint32_t w_out, w_in, w_sq, w_zero, w_bias, slot0, slot_bytes, bias, ybuf, ybuf_bytes, mbar, tptr, flag, claim,
+      fail, stash, total;
   int slots;
   __host__ __device__ uint32_t x(int g) const { return slot0 + (uint32_t)g * slot_bytes; }
 };
@@ -74,7 +76,9 @@ __host__ __device__ inline MlpLayout mlp_layout(int n_hidden, int slots) {
   L.w_out = 0;                                        // FP32 [3 x 128] output layer
   L.w_in = L.w_out + 3 * kWidth * 4;                  // [128 x 32] = [W1 | W1]
   L.w_sq = L.w_in + kWidth * kKin * 2;                // (n_hidden-1) x [128 x 128]
-  L.slot0 = L.w_sq + (uint32_t)(n_hidden - 1) * kWidth * kWidth * 2;
+  L.w_zero = L.w_sq + (uint32_t)(n_hidden - 1) * kWidth * kWidth * 2;   // [128 x 8] zeros
+  L.w_bias = L.w_zero + kBiasTile;                   // (n_hidden-1) x [128 x 8] bias terms
+  L.slot0 = L.w_bias + (uint32_t)(n_hidden - 1) * kBiasTile;
   L.slot_bytes = kTileM * kKin * 2;                  // X [128 x 32] (hi | lo)
   L.bias = L.slot0 + (uint32_t)slots * L.slot_bytes;  // floats: n_hidden*128 + 16
   // per slot: partial outputs of the column groups other than the first
@@ -102,14 +106,50 @@ struct MlpShape {
   int d_in, n_hidden, act, slots;
 };
 
+// bf16 bits of x, rounded to nearest even
+__device__ __forceinline__ uint16_t bf16_bits(float x) { return (uint16_t)(tc::pack_bf16x2(x, 0.f) & 0xFFFFu); }
+
+// A bias b as three bf16 terms b0 + b1 + b2 (b0 = bf16(b), b1 = bf16(b - b0),
+// b2 = bf16(b - b0 - b1); the differences are exact in FP32): 24 significant
+// bits, FP32's, so the MMA that multiplies them by 1.0 adds b to the
+// accumulator up to its FP32 rounding.
+__device__ __forceinline__ void bias_terms(float b, uint16_t r[3]) {
+  r[0] = bf16_bits(b);
+  const float d1 = b - __uint_as_float((uint32_t)r[0] << 16);
+  r[1] = bf16_bits(d1);
+  r[2] = bf16_bits(d1 - __uint_as_float((uint32_t)r[1] << 16));
+}
+
 // Copy the caller's row-major [out x in] bf16 layers into K-major core-matrix
-// tiles (zero padded) and the biases into shared memory.
+// tiles (zero padded) and the biases into shared memory.  The biases enter
+// through the MMAs, against the input tile's constant columns 13..15 (1.0):
+// layer 0's as its weight columns 13..15, a hidden layer's in one more K
+// step over the input tile's first 16 columns, issued first with the
+// accumulator overwritten, whose B is zero in columns 0..12 and holds the
+// bias terms in 13..15.  That B is two K-adjacent core-matrix columns: the
+// first (columns 0..7) a zero tile shared by the layers, the second
+// (columns 8..15) the layer's [128 x 8] bias tile, which the descriptor's
+// K-direction offset reaches.
 __device__ void load_weights(char* smem, const MlpLayout& L, const MlpShape& sh,
                              const uint16_t* __restrict__ w, const float* __restrict__ bias) {
   const int t = threadIdx.x, nt = blockDim.x;
   uint32_t* z = (uint32_t*)(smem + L.w_in);
   for (int q = t; q < (kWidth * kKin * 2) / 4; q += nt) z[q] = 0u;
+  uint32_t* zb = (uint32_t*)(smem + L.w_zero);
+  for (int q = t; q < (int)(sh.n_hidden * kBiasTile / 4); q += nt) zb[q] = 0u;
   __syncthreads();
+  for (int n = t; n < sh.n_hidden * kWidth; n += nt) {
+    uint16_t r[3];
+    bias_terms(bias[n], r);
+    const int l = n / kWidth, nn = n % kWidth;
+    for (int k = 0; k < 3; ++k) {
+      if (l == 0)
+        *(uint16_t*)(smem + L.w_in + tc::kmajor_offset(nn, kBiasCol + k, kKin)) = r[k];
+      else
+        *(uint16_t*)(smem + L.w_bias + (uint32_t)(l - 1) * kBiasTile + tc::kmajor_offset(nn, kBiasCol - 8 + k, 8)) =
+            r[k];
+    }
+  }
   // layer 0: [128 x d_in], stored twice (columns k and 16 + k) so that the
   // two bf16 terms of the input share the weights
   for (int e = t; e < kWidth * sh.d_in; e += nt) {
@@ -132,6 +172,7 @@ __device__ void load_weights(char* smem, const MlpLayout& L, const MlpShape& sh,
   float* bs = (float*)(smem + L.bias);
   for (int e = t; e < sh.n_hidden * kWidth; e += nt) bs[e] = bias[e];
   for (int e = t; e < kNout; e += nt) bs[sh.n_hidden * kWidth + e] = e < 3 ? bias[sh.n_hidden * kWidth + e] : 0.f;
+  tc::fence_async_smem();   // the operand tiles are read by the tensor core (async proxy)
 }
 
 __device__ __forceinline__ float act_f(int act, float z) {
@@ -154,19 +195,6 @@ __device__ __forceinline__ void group_sync(const Group& q) {
   asm volatile("bar.sync %0, %1;" ::"r"(1 + q.g), "r"(q.nthr) : "memory");
 }
 
-// Layer 0's bias into this thread's TMEM lane of the group's accumulator,
-// in the columns its warp reads in the epilogues (before the first tile);
-// the caller synchronises the group before the first MMA.
-__device__ __forceinline__ void preload_bias(char* smem, const MlpLayout& L, const Group& q, uint32_t tmem) {
-  const int gw = q.t >> 5;
-  const int cgroups = q.nthr / kTileM, cols = kWidth / cgroups, cbeg = (gw >> 2) * cols;
-  const uint32_t lane_tm = tmem + (uint32_t)(q.g * 2 * kWidth) + ((uint32_t)((gw & 3) * 32) << 16);
-  const float* bs = (const float*)(smem + L.bias);
-  for (int c0 = cbeg; c0 < cbeg + cols; c0 += 16) tc::st16_async(lane_tm + (uint32_t)c0, (const uint32_t*)(bs + c0));
-  tc::wait_st();
-  tc::fence_before();
-}
-
 // Run all layers on the X tile already in the group's slot (fenced and
 // synchronised by the caller).  Returns false if a bounded wait ran out
 // (status recorded); y receives the output row (+ bias) of group thread q.t
@@ -179,8 +207,8 @@ __device__ __forceinline__ void preload_bias(char* smem, const MlpLayout& L, con
 // shared memory -- no tensor-core pass, barrier and TMEM read for 3 outputs.
 __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, const Group& q,
                          uint32_t tmem, uint32_t& phase, float y[3], int* status, uint32_t xs) {
-  // every layer's accumulator starts from its bias, stored into it by the
-  // previous epilogue (by preload_bias before the first tile)
+  // every layer's bias enters through its MMAs (the first one overwrites the
+  // accumulator)
   const int gw = q.t >> 5;
   const int row = ((gw & 3) << 5) | (q.t & 31);
   const int cgroups = q.nthr / kTileM, cg = gw >> 2;
@@ -205,10 +233,14 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
         for (int s = 0; s < kKin / 16; ++s)
           tc::mma_bf16(acc, tc::sdesc(sbase + xs + 256u * s, 128, kKin * 16),
                        tc::sdesc(sbase + L.w_in + 256u * s, 128, kKin * 16),
-                       tc::idesc_bf16(kTileM, kWidth), 1);
+                       tc::idesc_bf16(kTileM, kWidth), s > 0);
       } else {
         const uint32_t wb = L.w_sq + (uint32_t)(l - 1) * kWidth * kWidth * 2;
         const uint32_t idesc = tc::idesc_bf16(kTileM, kWidth);
+        // the bias: the input tile's first 16 columns (1.0 in 13..15) against
+        // [zeros | the layer's bias tile] (core-matrix rows 128 bytes apart)
+        tc::mma_bf16(acc, tc::sdesc(sbase + xs, 128, kKin * 16),
+                     tc::sdesc(sbase + L.w_zero, L.w_bias + (uint32_t)(l - 1) * kBiasTile - L.w_zero, 128), idesc, 0);
         // activations enter as hi + lo bf16 terms against the same weights
 #pragma unroll
         for (int s = 0; s < kWidth / 16; ++s)
@@ -225,9 +257,6 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
     phase ^= 1u;
     tc::fence_after();
     const bool last = l == sh.n_hidden - 1;
-    // the bias the accumulator must hold for its next use: layer l + 1's, or
-    // after the last layer the next tile's layer 0's
-    const float* bn = bs + (last ? 0 : l + 1) * kWidth;
     // this warp's columns in 16-wide pieces, the TMEM read of the next piece
     // in flight while the current one is processed
     const int cbeg = cg * cols, npieces = cols / kEpiW;
@@ -251,10 +280,6 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
 #pragma unroll
         for (int k = 0; k < kEpiW / 2; ++k)
           v[k] = make_float2(__uint_as_float(cur[2 * k]), __uint_as_float(cur[2 * k + 1]));
-        // these columns are read: they now receive the next use's bias
-#pragma unroll
-        for (int h = 0; h < kEpiW / 16; ++h)
-          tc::st16_async(lane_tm + (uint32_t)(c0 + 16 * h), (const uint32_t*)(bn + c0 + 16 * h));
         if (sh.act == 0) {
 #pragma unroll
           for (int k = 0; k < kEpiW / 2; k += 2) tc::silu4x2(v[k], v[k + 1]);
@@ -293,9 +318,9 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
         if (more) tmem_wait_ld<kEpiW>(nxt);
       }
     }
-    // this thread's A operand and bias stores complete before the next MMA
-    tc::wait_st();
+    // this thread's A operand stores complete before the next MMA
     if (!last) {
+      tc::wait_st();
       tc::fence_before();
       group_sync(q);
     }
@@ -326,15 +351,21 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
 // Write row t of the X tile from 16 FP32 features (padding zeros included):
 // columns 0..15 hold hi = bf16(x), columns 16..31 lo = bf16(x - hi), so the
 // first layer sees x to about 16 significant bits through bf16 operands.
+// Columns 13..15 of hi hold 1.0 (and those of lo 0): against the weight
+// columns that carry layer 0's bias terms.  Features occupy at most columns
+// 0..7.
 __device__ __forceinline__ void write_x_row(char* smem, uint32_t xoff, int t, const float* f) {
   const uint32_t sb = tc::smem_u32(smem) + xoff;
   uint32_t hi[8], lo[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
+  for (int q = 0; q < 6; ++q) {
     hi[q] = tc::pack_bf16x2(f[2 * q], f[2 * q + 1]);
     const float h0 = __uint_as_float(hi[q] << 16), h1 = __uint_as_float(hi[q] & 0xFFFF0000u);
     lo[q] = tc::pack_bf16x2(f[2 * q] - h0, f[2 * q + 1] - h1);
   }
+  static_assert(kBiasCol == 13, "the constant columns are 13, 14, 15");
+  hi[6] = 0x3F800000u; hi[7] = 0x3F803F80u;   // columns 12 = 0, 13..15 = 1.0
+  lo[6] = 0u; lo[7] = 0u;
   tc::st_shared_v4(sb + tc::kmajor_offset(t, 0, kKin), hi[0], hi[1], hi[2], hi[3]);
   tc::st_shared_v4(sb + tc::kmajor_offset(t, 8, kKin), hi[4], hi[5], hi[6], hi[7]);
   tc::st_shared_v4(sb + tc::kmajor_offset(t, 16, kKin), lo[0], lo[1], lo[2], lo[3]);
@@ -378,7 +409,6 @@ __global__ void __launch_bounds__(kThreads) k_mlp_forward(MlpShape sh, const uin
   load_weights(smem, L, sh, w, bias);
   const uint32_t tmem = cta_setup(smem, L);
   const Group q = my_group(L.slots);
-  preload_bias(smem, L, q, tmem);
   uint32_t phase = 0;
   const int64_t tiles = (n + kTileM - 1) / kTileM;
   bool alive = true;
@@ -666,9 +696,11 @@ __host__ __device__ inline PipeLayout pipe_layout(int n_hidden) {
   L.w_out = 0;
   L.w_in = L.w_out + 3 * kWidth * 4;
   L.w_sq = L.w_in + kWidth * kKin * 2;
+  L.w_zero = L.w_sq + (uint32_t)(n_hidden - 1) * kWidth * kWidth * 2;
+  L.w_bias = L.w_zero + kBiasTile;
   L.slot0 = 0;                                   // (the X tiles are per buffer below)
   L.slot_bytes = 0;
-  L.bias = L.w_sq + (uint32_t)(n_hidden - 1) * kWidth * kWidth * 2;
+  L.bias = L.w_bias + (uint32_t)(n_hidden - 1) * kBiasTile;
   L.ybuf = L.bias + (uint32_t)(n_hidden * kWidth + kNout) * 4;
   L.ybuf_bytes = (uint32_t)(256 / kTileM - 1) * kTileM * 3 * 4;   // 8-warp groups: 2 column groups
   L.mbar = (L.ybuf + 2 * L.ybuf_bytes + 15u) & ~15u;
@@ -754,10 +786,6 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_collide_neural(MlpShape sh,
   if (t < kBuildBase) {
     // ------------------------------------------------ MLP groups
     const Group q{t / 256, 2, t % 256, 256};
-    preload_bias(smem, L, q, tmem);
-    tc::fence_before();
-    group_sync(q);
-    tc::fence_after();
     uint32_t phase = 0;
     const int row = (((q.t >> 5) & 3) << 5) | (q.t & 31);
     const bool yrow = q.t < kTileM;   // column group 0: holds the row's output
