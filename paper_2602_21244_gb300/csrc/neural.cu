@@ -7,9 +7,9 @@
 // (ping-pong; a single 16-warp group when two slots do not fit).  Within a
 // group: thread t < 128 builds row t of the bf16 input tile X (shared
 // memory), one elected thread issues the layer's tcgen05.mma chain (FP32
-// accumulator in TMEM) and waits on the group's mbarrier, the group's warps
-// read their 32 TMEM lanes back (tcgen05.ld), add the bias, apply the
-// activation and write the next layer's A operand into tensor memory
+// accumulator in TMEM, the bias added by the MMAs) and waits on the group's
+// mbarrier, the group's warps read their 32 TMEM lanes back (tcgen05.ld),
+// apply the activation and write the next layer's A operand into tensor memory
 // (tcgen05.st; row m in lane m, two bf16 per column) as two bf16 terms
 // (hi = bf16(a), lo = bf16(a - hi)) multiplied by the same bf16 weights:
 // bf16 operands, FP32 accumulation, about 16 significant bits kept for the
@@ -39,6 +39,12 @@ constexpr int kWidth = 128;
 constexpr int kKin = 32;         // input as two bf16 terms: [hi (16) | lo (16)]
 constexpr int kNout = 16;        // padded output width
 constexpr int kMaxHidden = 4;
+// SiLU layers run in base-2 units: their pre-activations u = -z log2(e)
+// (input and biases scaled by -log2 e), their stored activations a/(-ln 2),
+// absorbed by the next layer's weights (log2(e) ln 2 = 1) and the output
+// layer's (scaled by -ln 2)
+constexpr float kNegLog2e = -1.4426950408889634f, kNegLn2 = -0.6931471805599453f;
+__host__ __device__ __forceinline__ float input_scale(int act) { return act == 0 ? kNegLog2e : 1.f; }
 constexpr int kBiasCol = 13;     // X columns 13..15 (hi term) hold 1.0, against the bias terms
 constexpr uint32_t kBiasTile = kWidth * 8 * 2;   // [128 x 8] bf16: columns 8..15 of a bias step's B
 constexpr int kStashWords = 16;  // per-row pair data handed from builder to updater threads
@@ -138,9 +144,10 @@ __device__ void load_weights(char* smem, const MlpLayout& L, const MlpShape& sh,
   uint32_t* zb = (uint32_t*)(smem + L.w_zero);
   for (int q = t; q < (int)(sh.n_hidden * kBiasTile / 4); q += nt) zb[q] = 0u;
   __syncthreads();
+  const float zs = input_scale(sh.act);
   for (int n = t; n < sh.n_hidden * kWidth; n += nt) {
     uint16_t r[3];
-    bias_terms(bias[n], r);
+    bias_terms(bias[n] * zs, r);
     const int l = n / kWidth, nn = n % kWidth;
     for (int k = 0; k < 3; ++k) {
       if (l == 0)
@@ -168,7 +175,8 @@ __device__ void load_weights(char* smem, const MlpLayout& L, const MlpShape& sh,
   }
   // output layer in FP32 [3 x 128] for the CUDA-core dot products
   float* wo = (float*)(smem + L.w_out);
-  for (int e = t; e < 3 * kWidth; e += nt) wo[e] = __uint_as_float((uint32_t)wl[e] << 16);
+  const float os = sh.act == 0 ? kNegLn2 : 1.f;
+  for (int e = t; e < 3 * kWidth; e += nt) wo[e] = __uint_as_float((uint32_t)wl[e] << 16) * os;
   float* bs = (float*)(smem + L.bias);
   for (int e = t; e < sh.n_hidden * kWidth; e += nt) bs[e] = bias[e];
   for (int e = t; e < kNout; e += nt) bs[sh.n_hidden * kWidth + e] = e < 3 ? bias[sh.n_hidden * kWidth + e] : 0.f;
@@ -282,7 +290,7 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
           v[k] = make_float2(__uint_as_float(cur[2 * k]), __uint_as_float(cur[2 * k + 1]));
         if (sh.act == 0) {
 #pragma unroll
-          for (int k = 0; k < kEpiW / 2; k += 2) tc::silu4x2(v[k], v[k + 1]);
+          for (int k = 0; k < kEpiW / 2; k += 2) tc::silu2_4x2(v[k], v[k + 1]);
         } else {
 #pragma unroll
           for (int k = 0; k < kEpiW / 2; ++k) v[k] = make_float2(act_f(sh.act, v[k].x), act_f(sh.act, v[k].y));
@@ -348,20 +356,22 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
   return true;
 }
 
-// Write row t of the X tile from 16 FP32 features (padding zeros included):
-// columns 0..15 hold hi = bf16(x), columns 16..31 lo = bf16(x - hi), so the
-// first layer sees x to about 16 significant bits through bf16 operands.
+// Write row t of the X tile from 16 FP32 features (padding zeros included),
+// x = scale * feature (the first layer's input scale): columns 0..15 hold
+// hi = bf16(x), columns 16..31 lo = bf16(x - hi), so the first layer sees x
+// to about 16 significant bits through bf16 operands.
 // Columns 13..15 of hi hold 1.0 (and those of lo 0): against the weight
 // columns that carry layer 0's bias terms.  Features occupy at most columns
 // 0..7.
-__device__ __forceinline__ void write_x_row(char* smem, uint32_t xoff, int t, const float* f) {
+__device__ __forceinline__ void write_x_row(char* smem, uint32_t xoff, int t, const float* f, float scale) {
   const uint32_t sb = tc::smem_u32(smem) + xoff;
   uint32_t hi[8], lo[8];
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
-    hi[q] = tc::pack_bf16x2(f[2 * q], f[2 * q + 1]);
+    const float x0 = f[2 * q] * scale, x1 = f[2 * q + 1] * scale;
+    hi[q] = tc::pack_bf16x2(x0, x1);
     const float h0 = __uint_as_float(hi[q] << 16), h1 = __uint_as_float(hi[q] & 0xFFFF0000u);
-    lo[q] = tc::pack_bf16x2(f[2 * q] - h0, f[2 * q + 1] - h1);
+    lo[q] = tc::pack_bf16x2(x0 - h0, x1 - h1);
   }
   static_assert(kBiasCol == 13, "the constant columns are 13, 14, 15");
   hi[6] = 0x3F800000u; hi[7] = 0x3F803F80u;   // columns 12 = 0, 13..15 = 1.0
@@ -420,7 +430,7 @@ __global__ void __launch_bounds__(kThreads) k_mlp_forward(MlpShape sh, const uin
       for (int k = 0; k < 16; ++k) f[k] = 0.f;
       if (row < n)
         for (int k = 0; k < sh.d_in; ++k) f[k] = x[row * sh.d_in + k];
-      write_x_row(smem, L.x(q.g), q.t, f);
+      write_x_row(smem, L.x(q.g), q.t, f, input_scale(sh.act));
       tc::fence_async_smem();
     }
     group_sync(q);
@@ -596,7 +606,7 @@ __device__ __forceinline__ void build_row(char* smem, uint32_t xoff, volatile in
       st[5 + 2 * c] = __double2hiint(v[c]);
     }
   }
-  write_x_row(smem, xoff, row, f);
+  write_x_row(smem, xoff, row, f, input_scale(sh.act));
   tc::fence_async_smem();
 #pragma unroll
   for (int c = 0; c < kStashWords; ++c) stash[c * kTileM + row] = st[c];

@@ -290,5 +290,22 @@ __device__ __forceinline__ void silu4x2(float2& za, float2& zb) {
 }
 
 
+// The same activation in base-2 units: for u = -z log2(e) (the accumulator
+// of a layer whose weights and bias carry that factor), a/(-ln 2) =
+// u / (1 + 2^u) with a = SiLU(z); the next layer's weights absorb the -ln 2,
+// so the scalings of silu4x2 drop out.  u is clamped above at 28 inside the
+// exponential (z below -19.4, where SiLU is below 8e-8 in magnitude), so
+// that the product of the four denominators stays finite.
+__device__ __forceinline__ void silu2_4x2(float2& ua, float2& ub) {
+  const float2 one = make_float2(1.f, 1.f);
+  const float2 da = __fadd2_rn(make_float2(ex2_approx(fminf(ua.y, 28.f)), ex2_approx(fminf(ua.x, 28.f))), one);
+  const float2 db = __fadd2_rn(make_float2(ex2_approx(fminf(ub.y, 28.f)), ex2_approx(fminf(ub.x, 28.f))), one);
+  const float d01 = da.x * da.y, d23 = db.x * db.y;   // da = (d1, d0), db = (d3, d2)
+  const float r = rcp_approx(d01 * d23);
+  const float2 rr = __fmul2_rn(make_float2(r, r), make_float2(d23, d01));   // 1/(d0 d1), 1/(d2 d3)
+  ua = __fmul2_rn(__fmul2_rn(ua, da), make_float2(rr.x, rr.x));
+  ub = __fmul2_rn(__fmul2_rn(ub, db), make_float2(rr.y, rr.y));
+}
+
 }  // namespace tc
 }  // namespace dsmc
