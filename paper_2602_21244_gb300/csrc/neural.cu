@@ -93,7 +93,7 @@ __host__ __device__ inline MlpLayout mlp_layout(int n_hidden, int slots) {
   L.mbar = L.ybuf + (uint32_t)slots * L.ybuf_bytes;
   L.mbar = (L.mbar + 15u) & ~15u;                     // slots x 8 bytes
   L.tptr = L.mbar + 16;
-  L.flag = L.tptr + 4;                                // slots x 4 bytes: mbarrier wait result
+  L.flag = L.tptr + 4;                                // slots x 4 bytes: 1 until an MMA wait of the group times out
   L.claim = L.flag + 8;                               // slots x 4 bytes: next claimed unit
   L.fail = L.claim + 8;                               // slots x 4 bytes: a dependency wait failed
   // slots x 2 buffers x kStashWords x 128 words (word-major: a warp's rows
@@ -258,10 +258,11 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
           tc::mma_bf16_ta(acc, a_lo + 8u * s, tc::sdesc(sbase + wb + 256u * s, 128, 2048), idesc, 1);
       }
       tc::commit(mbar);
-      *flag = tc::mbar_wait(mbar, phase, status, kBarrierLimitNs) ? 1 : 0;
     }
-    group_sync(q);
-    if (!*flag) return false;
+    // every thread waits for the layer's MMAs itself (no barrier after the
+    // issue); a timeout clears the group's flag, read after the group's next
+    // barrier so that all its threads leave together
+    if (!tc::mbar_wait(mbar, phase, status, kBarrierLimitNs)) *flag = 0;
     phase ^= 1u;
     tc::fence_after();
     const bool last = l == sh.n_hidden - 1;
@@ -331,6 +332,7 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
       tc::wait_st();
       tc::fence_before();
       group_sync(q);
+      if (!*flag) return false;
     }
   }
   const float yp0 = yq0.x + yq0.y, yp1 = yq1.x + yq1.y, yp2 = yq2.x + yq2.y;
@@ -342,6 +344,7 @@ __device__ bool mlp_tile(char* smem, const MlpLayout& L, const MlpShape& sh, con
   }
   tc::fence_before();
   group_sync(q);
+  if (!*flag) return false;
   if (cg == 0) {
     const float* bo = bs + sh.n_hidden * kWidth;
     float s0 = yp0, s1 = yp1, s2 = yp2;
@@ -392,7 +395,10 @@ __device__ __forceinline__ uint32_t cta_setup(char* smem, const MlpLayout& L) {
     tc::tmem_relinquish();
   }
   if (threadIdx.x == 0) {
-    for (int g = 0; g < L.slots; ++g) tc::mbar_init((uint64_t*)(smem + L.mbar) + g, 1);
+    for (int g = 0; g < L.slots; ++g) {
+      tc::mbar_init((uint64_t*)(smem + L.mbar) + g, 1);
+      ((volatile int*)(smem + L.flag))[g] = 1;   // the group's MMA waits have not failed
+    }
     tc::mbar_fence_init();
   }
   tc::fence_before();
