@@ -399,13 +399,13 @@ def test_chi_jager_parity_sampled(n_nodes):
 
 # ------------------------------------------------------------------ neural operator
 
-def _mlp_setup(d_in=8):
+def _mlp_setup(d_in=8, n_hidden=3, act=0):
     from paper_2602_21244_gb300 import dsmc as D
-    wts = W.mlp_weights(d_in=d_in)
+    wts = W.mlp_weights(d_in=d_in, n_hidden=n_hidden)
     bias = np.random.default_rng(7).standard_normal(len(wts["bias"])) * 0.05
     bias = bias.astype(np.float32).astype(np.float64)
-    mlp_o = O.make_mlp(d_in, 128, 3, 3, 0, W.sigma_v(), 273.0, 1e-12)
-    mlp_d = D.make_mlp(d_in, 128, 3, 3, 0, W.sigma_v(), 273.0, 1e-12)
+    mlp_o = O.make_mlp(d_in, 128, n_hidden, 3, act, W.sigma_v(), 273.0, 1e-12)
+    mlp_d = D.make_mlp(d_in, 128, n_hidden, 3, act, W.sigma_v(), 273.0, 1e-12)
     return wts, bias, mlp_o, mlp_d
 
 
@@ -424,14 +424,39 @@ def test_mlp_forward_parity(n):
     assert np.abs(y - y64).max() <= 3e-2 * sc
 
 
-@pytest.mark.parametrize("name", ["cavity40", "hyper01"])
-def test_collide_neural_parity(name):
+# every shape the tensor-core MLP accepts: input width, hidden layers, activation
+MLP_SHAPES = [(6, 1, 0), (8, 2, 1), (6, 4, 0), (8, 4, 1), (8, 3, 1), (6, 3, 0)]
+
+
+@pytest.mark.parametrize("d_in,n_hidden,act", MLP_SHAPES)
+def test_mlp_forward_shapes(d_in, n_hidden, act):
+    """The standalone MLP for each accepted shape: within 1e-2 of the output
+    scale of the oracle's bf16-storage emulation and 3e-2 of its FP64 forward
+    (2 tiles and a ragged tail)."""
+    wts, bias, mlp_o, mlp_d = _mlp_setup(d_in, n_hidden, act)
+    x = np.random.default_rng(17 + n_hidden).standard_normal((300, d_in)) * 1.5
+    y = host(ctx().mlp_forward(mlp_d, w_bits_tensor(wts["W_bits"]), cuda(bias, torch().float32),
+                               cuda(x, torch().float32)))
+    assert ctx().sync_status() == 0
+    xr = x.astype(np.float32).astype(np.float64)
+    yb = O.mlp_forward(mlp_o, wts["W"], bias, xr, bf16=True)
+    y64 = O.mlp_forward(mlp_o, wts["W"], bias, xr, bf16=False)
+    sc = np.abs(y64).max()
+    assert np.abs(y - yb).max() <= 1e-2 * sc
+    assert np.abs(y - y64).max() <= 3e-2 * sc
+
+
+@pytest.mark.parametrize("name,shape", [("cavity40", (8, 3, 0)), ("hyper01", (8, 3, 0)),
+                                        ("hyper01", (6, 2, 1)), ("cavity40", (8, 4, 0)),
+                                        ("hyper01", (6, 1, 0))])
+def test_collide_neural_parity(name, shape):
     """Gate (2e-2) on the normalised post-collision relative velocity v_r'/|v_r| of
     every pair against the FP64 oracle; a tighter gate against the oracle's
-    bf16-storage emulation catches layout and indexing errors."""
+    bf16-storage emulation catches layout and indexing errors.  shape = (input
+    width, hidden layers, activation)."""
     w = wl(name)
     gas = O.make_gas(**w["gas"])
-    wts, bias, mlp_o, mlp_d = _mlp_setup()
+    wts, bias, mlp_o, mlp_d = _mlp_setup(*shape)
     sg0 = _sgmax0(w, gas)
     perm, cs, sx, sy, sz = oracle_sorted(w)
     mom = O.cell_moments(cs, sx, sy, sz)
