@@ -40,10 +40,10 @@ MLP_FLOP_PER_PAIR = 2 * (8 * 128 + 128 * 128 * 2 + 128 * 3)   # 68,352 (unpadded
 CHI_MLP_FLOP_PER_QUERY = 2 * (2 * 512 + 512 * 512 * 2 + 512 * 256 + 256 * 128 + 128)
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per pair of
 # k_collide_neural, from one ncu capture of a full-size launch on the
-# hypersonic gas: 1070.7 + 932.6 MB for about 6.882 million pairs
+# hypersonic gas: 1000.1 + 941.5 MB for about 6.885 million pairs
 # (the committed ncu summary of this kernel); the roofline's traffic is this
 # times the pairs of the timed launch.
-NEURAL_DRAM_BYTES_PER_PAIR = (1070.69e6 + 932.64e6) / 6.882e6
+NEURAL_DRAM_BYTES_PER_PAIR = (1000.14e6 + 941.49e6) / 6.885e6
 CANDIDATE_BYTES = 48                                             # two FP64 3-vectors read
 PAIR_BYTES = 104                                                 # 2x24 read + 2x24 write + 8 index
 # special-function operations per pair of the neural collide: 3 hidden layers
