@@ -649,7 +649,7 @@ __device__ __forceinline__ void collide_pair(const PotDev& P, const JagerArgs& a
   const bool use = live && g2 > 0.0;
   const u32x4 w = draw(a.seed, (uint32_t)q.w, (uint32_t)q.z, a.step, TAG_JAGER);
   const float b = use ? f64_to_f32(a.bmax_A * sqrt64(u53_int(w.x, w.y))) : 1.f;
-  const float E = use ? P.mass_over_4k * (float)g2 : 1.0e4f;
+  const float E = use ? P.mass_over_4k * f64_to_f32(g2) : 1.0e4f;
   const float chi_c = chi_device<true>(P, b, E);
   const float chi = use ? chi_c : 0.f;
   if (live && a.chi_out) a.chi_out[p] = chi;

@@ -56,16 +56,21 @@ __device__ __forceinline__ void deflect_shell_h(double ux, double uy, double uz,
   const float y0 = cc * fx + gf * sc * (ce * cx + se * ax);
   const float y1 = cc * fy + gf * sc * (ce * cy + se * ay);
   const float y2 = cc * fz + gf * sc * (ce * cz + se * az);
-  const double Y0 = y0, Y1 = y1, Y2 = y2;
+  // the FP32 <-> FP64 conversions on the integer pipe (exact, and
+  // correctly rounded to FP32): GB300's FP64 pipe, which runs the conversion
+  // instructions, bounds this update
+  const double Y0 = f32_to_f64(y0), Y1 = f32_to_f64(y1), Y2 = f32_to_f64(y2);
   Yo[0] = Y0; Yo[1] = Y1; Yo[2] = Y2;
   const double ny2 = Y0 * Y0 + Y1 * Y1 + Y2 * Y2;
   if (!(ny2 > 0.0)) { *h = 0.0; return; }
-  const float ny2f = (float)ny2, g2f = (float)g2;
+  const float ny2f = f64_to_f32(ny2), g2f = f64_to_f32(g2);
+  // (|v_r|^2 below the FP32 normal range: v_r' = 0 up to ~1e-19 m/s)
+  if (!(g2f > 0.f) || !(ny2f > 0.f)) { *h = 0.0; return; }
   const float sf = sqrtf(g2f / ny2f);
-  const double s0 = sf;
+  const double s0 = f32_to_f64(sf);
   const double res = g2 - s0 * s0 * ny2;
   // one Newton step on s^2 ny2 = g2 from s0, halved: h = s / 2
-  *h = 0.5 * s0 + res * (double)(0.25f * sf / g2f);
+  *h = 0.5 * s0 + res * f32_to_f64(0.25f * sf / g2f);
 }
 
 // The chi table of the look-up path in the form the pair update reads it.
@@ -114,7 +119,7 @@ __device__ __forceinline__ float table_pair(const TableLook& L, uint64_t seed, u
     // uniforms are formed in FP32 too (GB300's FP64 pipe bounds this
     // update), to within one FP32 rounding of the FP64 values
     const float x = sqrtf(u_f32(w.x, w.y)) * L.nb1;
-    const float y = (logf(L.mass_over_4k * (float)g2) - L.lnE_min) * L.inv_dlnE;
+    const float y = (logf(L.mass_over_4k * f64_to_f32(g2)) - L.lnE_min) * L.inv_dlnE;
     chi = chi_lookup(L, x, y);
     deflect_shell_h(ux, uy, uz, g2, chi, u_f32(w.z, w.w) * 6.2831855f, &h, Y);
   }
