@@ -749,19 +749,29 @@ __global__ void __launch_bounds__(256) k_collide_table(TableArgs a) {
     int32_t p0, p1;
     if (!unit_range(a.ro, R, 32, r, base, unit, &p0, &p1)) break;
     const int32_t p = p0 + lane;
+    const bool valid = p < p1;
+    int4 q = make_int4(0, 0, 0, 0);
     bool ok = true;
-    if (p < p1) {
-      const int4 q = a.pairs[p];
+    if (valid) {
+      q = a.pairs[p];
       ok = wait_deps(a.done, q.x, q.y, a.deps[p], a.bar + 2, a.status);
-      if (ok) {
-        double v[6] = {__ldcg(a.vx + q.x), __ldcg(a.vy + q.x), __ldcg(a.vz + q.x),
-                       __ldcg(a.vx + q.y), __ldcg(a.vy + q.y), __ldcg(a.vz + q.y)};
-        const float chi = table_pair(a.look, a.seed, a.step, (uint32_t)q.w, (uint32_t)q.z, v);
-        if (a.chi_out) a.chi_out[p] = chi;
-        __stcg(a.vx + q.x, v[0]); __stcg(a.vy + q.x, v[1]); __stcg(a.vz + q.x, v[2]);
-        __stcg(a.vx + q.y, v[3]); __stcg(a.vy + q.y, v[4]); __stcg(a.vz + q.y, v[5]);
-        release_pair(a.done, q.x, q.y, (unsigned)(r + 1));
-      }
+    }
+    const bool live = valid && ok;
+    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (live) {
+      v[0] = __ldcg(a.vx + q.x); v[1] = __ldcg(a.vy + q.x); v[2] = __ldcg(a.vz + q.x);
+      v[3] = __ldcg(a.vx + q.y); v[4] = __ldcg(a.vy + q.y); v[5] = __ldcg(a.vz + q.y);
+    }
+    // every lane runs the pair update together after the warp reconverges
+    // (as in k_collide_jager; a lane without a pair on zero velocities, its
+    // result not stored)
+    __syncwarp();
+    const float chi = table_pair(a.look, a.seed, a.step, (uint32_t)q.w, (uint32_t)q.z, v);
+    if (live) {
+      if (a.chi_out) a.chi_out[p] = chi;
+      __stcg(a.vx + q.x, v[0]); __stcg(a.vy + q.x, v[1]); __stcg(a.vz + q.x, v[2]);
+      __stcg(a.vx + q.y, v[3]); __stcg(a.vy + q.y, v[4]); __stcg(a.vz + q.y, v[5]);
+      release_pair(a.done, q.x, q.y, (unsigned)(r + 1));
     }
     if (!__all_sync(0xffffffffu, ok)) break;
   }

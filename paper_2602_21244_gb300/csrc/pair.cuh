@@ -3,7 +3,10 @@
 // (Sec. 2.1) and the deflection by a chi looked up in the table of the
 // look-up path (Sec. 3.4.5), each with the centre-of-mass update (Sec. 2.3).
 // A pair's random numbers are keyed by its candidate index m and cell k, so
-// which thread runs a pair never changes its result.
+// which thread runs a pair never changes its result.  Every rounding is
+// explicit (the _rn intrinsics, fma): no multiply-add contraction is left to
+// the compiler, so every kernel that inlines these functions computes the
+// same bits.
 #pragma once
 #include "internal.cuh"
 
@@ -13,17 +16,18 @@ namespace dsmc {
 // e = 2 pi U2; v = (vi, vj) in, post-collision (vi', vj') out.
 __device__ __forceinline__ void vhs_pair(uint64_t seed, uint64_t step, uint32_t m, uint32_t k, double v[6]) {
   const double xi = v[0], yi = v[1], zi = v[2], xj = v[3], yj = v[4], zj = v[5];
-  const double dx = xi - xj, dy = yi - yj, dz = zi - zj;
-  const double g = sqrt(dx * dx + dy * dy + dz * dz);
+  const double dx = __dsub_rn(xi, xj), dy = __dsub_rn(yi, yj), dz = __dsub_rn(zi, zj);
+  const double g = sqrt(__fma_rn(dx, dx, __fma_rn(dy, dy, __dmul_rn(dz, dz))));
   const u32x4 w = draw(seed, m, k, step, TAG_ISO);
-  const double c = 2.0 * u53(w.x, w.y) - 1.0;
-  const double s = sqrt(1.0 - c * c);
+  const double c = __fma_rn(2.0, u53(w.x, w.y), -1.0);   // exact
+  const double s = sqrt(__fma_rn(-c, c, 1.0));
   double se, ce;
-  sincos(2.0 * DSMC_PI * u53(w.z, w.w), &se, &ce);
-  const double rx = g * c, ry = g * s * ce, rz = g * s * se;
-  const double cx = 0.5 * (xi + xj), cy = 0.5 * (yi + yj), cz = 0.5 * (zi + zj);
-  v[0] = cx + 0.5 * rx; v[1] = cy + 0.5 * ry; v[2] = cz + 0.5 * rz;
-  v[3] = cx - 0.5 * rx; v[4] = cy - 0.5 * ry; v[5] = cz - 0.5 * rz;
+  sincos(__dmul_rn(2.0 * DSMC_PI, u53(w.z, w.w)), &se, &ce);
+  const double gs = __dmul_rn(g, s);
+  const double rx = __dmul_rn(g, c), ry = __dmul_rn(gs, ce), rz = __dmul_rn(gs, se);
+  const double cx = 0.5 * __dadd_rn(xi, xj), cy = 0.5 * __dadd_rn(yi, yj), cz = 0.5 * __dadd_rn(zi, zj);
+  v[0] = __fma_rn(0.5, rx, cx); v[1] = __fma_rn(0.5, ry, cy); v[2] = __fma_rn(0.5, rz, cz);
+  v[3] = __fma_rn(-0.5, rx, cx); v[4] = __fma_rn(-0.5, ry, cy); v[5] = __fma_rn(-0.5, rz, cz);
 }
 
 // The rotation of v_r = (ux, uy, uz) by chi with azimuth eps (Bird 1994,
@@ -42,35 +46,37 @@ __device__ __forceinline__ void deflect_shell_h(double ux, double uy, double uz,
   float sc, cc, se, ce;
   sincosf(chi, &sc, &cc);
   sincosf(eps, &se, &ce);
-  const float q2 = fy * fy + fz * fz, gf2 = fx * fx + q2;
+  const float q2 = __fmaf_rn(fy, fy, __fmul_rn(fz, fz)), gf2 = __fmaf_rn(fx, fx, q2);
   const float gf = sqrtf(gf2);
   float cx, cy, cz, ax, ay, az;
-  if (q2 > 1e-24f * gf2 && q2 > 0.f) {
-    const float iq = rsqrtf(q2), q = q2 * iq, ig = 1.f / gf;
-    cx = 0.f; cy = fz * iq; cz = -fy * iq;
-    ax = q * ig; ay = -fx * fy * iq * ig; az = -fx * fz * iq * ig;
+  if (q2 > __fmul_rn(1e-24f, gf2) && q2 > 0.f) {
+    const float iq = rsqrtf(q2), q = __fmul_rn(q2, iq), ig = __fdiv_rn(1.f, gf);
+    const float iqg = __fmul_rn(iq, ig);
+    cx = 0.f; cy = __fmul_rn(fz, iq); cz = __fmul_rn(-fy, iq);
+    ax = __fmul_rn(q, ig); ay = __fmul_rn(__fmul_rn(-fx, fy), iqg); az = __fmul_rn(__fmul_rn(-fx, fz), iqg);
   } else {
     cx = 0.f; cy = 1.f; cz = 0.f;
     ax = 0.f; ay = 0.f; az = fx >= 0.f ? -1.f : 1.f;
   }
-  const float y0 = cc * fx + gf * sc * (ce * cx + se * ax);
-  const float y1 = cc * fy + gf * sc * (ce * cy + se * ay);
-  const float y2 = cc * fz + gf * sc * (ce * cz + se * az);
+  const float gs = __fmul_rn(gf, sc);
+  const float y0 = __fmaf_rn(cc, fx, __fmul_rn(gs, __fmaf_rn(ce, cx, __fmul_rn(se, ax))));
+  const float y1 = __fmaf_rn(cc, fy, __fmul_rn(gs, __fmaf_rn(ce, cy, __fmul_rn(se, ay))));
+  const float y2 = __fmaf_rn(cc, fz, __fmul_rn(gs, __fmaf_rn(ce, cz, __fmul_rn(se, az))));
   // the FP32 <-> FP64 conversions on the integer pipe (exact, and
   // correctly rounded to FP32): GB300's FP64 pipe, which runs the conversion
   // instructions, bounds this update
   const double Y0 = f32_to_f64(y0), Y1 = f32_to_f64(y1), Y2 = f32_to_f64(y2);
   Yo[0] = Y0; Yo[1] = Y1; Yo[2] = Y2;
-  const double ny2 = Y0 * Y0 + Y1 * Y1 + Y2 * Y2;
+  const double ny2 = __fma_rn(Y0, Y0, __fma_rn(Y1, Y1, __dmul_rn(Y2, Y2)));
   if (!(ny2 > 0.0)) { *h = 0.0; return; }
   const float ny2f = f64_to_f32(ny2), g2f = f64_to_f32(g2);
   // (|v_r|^2 below the FP32 normal range: v_r' = 0 up to ~1e-19 m/s)
   if (!(g2f > 0.f) || !(ny2f > 0.f)) { *h = 0.0; return; }
-  const float sf = sqrtf(g2f / ny2f);
+  const float sf = sqrtf(__fdiv_rn(g2f, ny2f));
   const double s0 = f32_to_f64(sf);
-  const double res = g2 - s0 * s0 * ny2;
+  const double res = __fma_rn(-__dmul_rn(s0, s0), ny2, g2);   // g2 - s0^2 ny2
   // one Newton step on s^2 ny2 = g2 from s0, halved: h = s / 2
-  *h = 0.5 * s0 + res * f32_to_f64(0.25f * sf / g2f);
+  *h = __fma_rn(res, f32_to_f64(__fdiv_rn(__fmul_rn(0.25f, sf), g2f)), 0.5 * s0);
 }
 
 // The chi table of the look-up path in the form the pair update reads it.
@@ -96,11 +102,13 @@ __device__ __forceinline__ float chi_lookup(const TableLook& a, float x, float y
   x = fminf(fmaxf(x, 0.f), (float)(a.nb - 1));
   y = fminf(fmaxf(y, 0.f), (float)(a.nE - 1));
   const int i0 = min((int)x, a.nb - 2), j0 = min((int)y, a.nE - 2);
-  const float fx = x - (float)i0, fy = y - (float)j0;
+  const float fx = __fsub_rn(x, (float)i0), fy = __fsub_rn(y, (float)j0);
   const float* r0 = a.T + (size_t)j0 * a.nb + i0;
   const float* r1 = r0 + a.nb;
   const float t00 = __ldg(r0), t01 = __ldg(r0 + 1), t10 = __ldg(r1), t11 = __ldg(r1 + 1);
-  return (1.f - fy) * ((1.f - fx) * t00 + fx * t01) + fy * ((1.f - fx) * t10 + fx * t11);
+  const float gx = __fsub_rn(1.f, fx);
+  const float c0 = __fmaf_rn(fx, t01, __fmul_rn(gx, t00)), c1 = __fmaf_rn(fx, t11, __fmul_rn(gx, t10));
+  return __fmaf_rn(fy, c1, __fmul_rn(__fsub_rn(1.f, fy), c0));
 }
 
 // The Jager pair update with chi from the table (tag 4: b~ = sqrt(U1),
@@ -109,8 +117,8 @@ __device__ __forceinline__ float chi_lookup(const TableLook& a, float x, float y
 __device__ __forceinline__ float table_pair(const TableLook& L, uint64_t seed, uint64_t step, uint32_t m,
                                             uint32_t k, double v[6]) {
   const double xi = v[0], yi = v[1], zi = v[2], xj = v[3], yj = v[4], zj = v[5];
-  const double ux = xi - xj, uy = yi - yj, uz = zi - zj;
-  const double g2 = ux * ux + uy * uy + uz * uz;
+  const double ux = __dsub_rn(xi, xj), uy = __dsub_rn(yi, yj), uz = __dsub_rn(zi, zj);
+  const double g2 = __fma_rn(ux, ux, __fma_rn(uy, uy, __dmul_rn(uz, uz)));
   const u32x4 w = draw(seed, m, k, step, TAG_JAGER);
   float chi = 0.f;
   double h = 0.0, Y[3] = {0.0, 0.0, 0.0};
@@ -118,12 +126,12 @@ __device__ __forceinline__ float table_pair(const TableLook& L, uint64_t seed, u
     // the table coordinate and the azimuth only ever enter in FP32: their
     // uniforms are formed in FP32 too (GB300's FP64 pipe bounds this
     // update), to within one FP32 rounding of the FP64 values
-    const float x = sqrtf(u_f32(w.x, w.y)) * L.nb1;
-    const float y = (logf(L.mass_over_4k * f64_to_f32(g2)) - L.lnE_min) * L.inv_dlnE;
+    const float x = __fmul_rn(sqrtf(u_f32(w.x, w.y)), L.nb1);
+    const float y = __fmul_rn(__fsub_rn(logf(__fmul_rn(L.mass_over_4k, f64_to_f32(g2))), L.lnE_min), L.inv_dlnE);
     chi = chi_lookup(L, x, y);
-    deflect_shell_h(ux, uy, uz, g2, chi, u_f32(w.z, w.w) * 6.2831855f, &h, Y);
+    deflect_shell_h(ux, uy, uz, g2, chi, __fmul_rn(u_f32(w.z, w.w), 6.2831855f), &h, Y);
   }
-  const double sx = 0.5 * (xi + xj), sy = 0.5 * (yi + yj), sz = 0.5 * (zi + zj);
+  const double sx = 0.5 * __dadd_rn(xi, xj), sy = 0.5 * __dadd_rn(yi, yj), sz = 0.5 * __dadd_rn(zi, zj);
   v[0] = fma(h, Y[0], sx); v[1] = fma(h, Y[1], sy); v[2] = fma(h, Y[2], sz);
   v[3] = fma(-h, Y[0], sx); v[4] = fma(-h, Y[1], sy); v[5] = fma(-h, Y[2], sz);
   return chi;
