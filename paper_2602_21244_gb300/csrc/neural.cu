@@ -584,6 +584,9 @@ __device__ __forceinline__ void build_row(char* smem, uint32_t xoff, volatile in
       p = -1;
     }
   }
+  // the lanes leave their waits at different times: the gather, the draws
+  // and the input row run with the warp reconverged
+  __syncwarp();
   if (p >= 0) {
     const double xi = __ldcg(a.vx + q.x), yi = __ldcg(a.vy + q.x), zi = __ldcg(a.vz + q.x);
     const double xj = __ldcg(a.vx + q.y), yj = __ldcg(a.vy + q.y), zj = __ldcg(a.vz + q.y);
