@@ -82,6 +82,7 @@ struct PotDev {
   double Dpp[16];     // (p + 1)(p + 2) D_{p+1}: P''(r) = r^-3 sum_p Dpp_p r^-p
   double Cd[6];       // (6 + 2n) C_n
   double Cdd[6];      // (6 + 2n)(7 + 2n) C_n
+  float fDp[16], fCd[6];   // FP32 copies of Dp and Cd (the refinement's derivative)
   float D[17];        // P(r) = sum_p D_p r^-p,  e^{-beta r} P(r) = sum_n C_2n r^-2n e^{-x} S_2n(x)
   float Dlo[17];      // D_p - D[p] (D as an FP32 pair)
   float Clo[6];       // C_2n - fC[n]
@@ -167,45 +168,61 @@ __host__ __device__ inline double V64(const PotDev& P, double r, double* dV, dou
   return rep - q + ex * Pr;
 }
 
-// V and V' in FP64 at r (ir = 1/r given), the same expansion as V64, for
-// the Newton refinement of the turning point; *rep, *ex receive A e^{poly}
-// and e^{-beta r}, *Pr, *dPr the damping polynomial P(r) and P'(r) (Jager
-// form), from which the quadrature's coefficients are carried to the root.
-__device__ __forceinline__ double V64n(const PotDev& P, double r, double ir, double* dV, double* rep_out,
-                                       double* ex_out, double* Pr_out, double* dPr_out) {
+// V in FP64 at r (ir = 1/r given), the same expansion as V64, for the
+// Newton refinement of the turning point, and V' in FP32: the derivative
+// only sets the Newton step, and a relative error d in it leaves d times
+// the step (about 1e-7 of a step that is itself about 1e-7 r: below 1e-13 r,
+// or a linear rather than quadratic rate if the derivative cancels).  *rep,
+// *ex receive A e^{poly} and e^{-beta r}, *Pr the damping polynomial P(r)
+// (Jager form), from which the quadrature's coefficients are carried to the
+// root, *dPr P'(r) and *dpoly poly'(r) in FP32 for that carry.
+__device__ __forceinline__ double V64n(const PotDev& P, double r, double ir, float* dV, double* rep_out,
+                                       double* ex_out, double* Pr_out, float* dPr_out, float* dpoly_out) {
   const double ir2 = ir * ir;
+  *dPr_out = 0.f;
+  *dpoly_out = 0.f;
   if (P.kind == 2) {
     const double v = P.kappa * pow(r, -P.p);
-    *dV = -P.p * v * ir;
+    *dV = f64_to_f32(-P.p * v * ir);
     return v;
   }
   if (r < P.rc) {
     const double e = P.At * exp(-P.at * r) * ir;
-    *dV = -e * (P.at + ir);
+    *dV = f64_to_f32(-e * (P.at + ir));
     return e;
   }
   const double rep = P.A * exp64(P.ex64, P.a1 * r + P.a2 * r * r + P.am1 * ir + P.am2 * ir2);
-  const double pp = P.a1 + 2.0 * P.a2 * r - P.am1 * ir2 - 2.0 * P.am2 * ir2 * ir;   // poly'
-  double q = 0.0, dq = 0.0, pw = ir2 * ir2 * ir2;
+  double q = 0.0, pw = ir2 * ir2 * ir2;
 #pragma unroll
   for (int n = 0; n < 6; ++n) {
     q = fma(P.C[n], pw, q);
-    dq = fma(P.Cd[n], pw, dq);
     pw *= ir2;
   }
-  dq *= -ir;
-  double Pr = P.Dd[16], dPr = P.Dp[15];
+  double Pr = P.Dd[16];
 #pragma unroll
   for (int k = 15; k >= 0; --k) Pr = fma(Pr, ir, P.Dd[k]);
-#pragma unroll
-  for (int k = 14; k >= 0; --k) dPr = fma(dPr, ir, P.Dp[k]);
-  dPr *= -ir2;
   const double ex = exp64(P.ex64, -P.beta * r);
+  // the derivative in FP32
+  const float rf = f64_to_f32(r), irf = f64_to_f32(ir), ir2f = irf * irf;
+  const float ppf = P.fa1 + 2.f * P.fa2 * rf - P.fam1 * ir2f - 2.f * P.fam2 * ir2f * irf;   // poly'
+  float dqf = 0.f, pwf = ir2f * ir2f * ir2f;
+#pragma unroll
+  for (int n = 0; n < 6; ++n) {
+    dqf = fmaf(P.fCd[n], pwf, dqf);
+    pwf *= ir2f;
+  }
+  dqf *= -irf;
+  float dPrf = P.fDp[15];
+#pragma unroll
+  for (int k = 14; k >= 0; --k) dPrf = fmaf(dPrf, irf, P.fDp[k]);
+  dPrf *= -ir2f;                                   // P'(r) = -sum p D_p r^-(p+1)
+  const float repf = f64_to_f32(rep), exf = f64_to_f32(ex), Prf = f64_to_f32(Pr);
   *rep_out = rep;
   *ex_out = ex;
   *Pr_out = Pr;
-  *dPr_out = dPr;
-  *dV = rep * pp - dq + ex * (dPr - P.beta * Pr);
+  *dPr_out = dPrf;
+  *dpoly_out = ppf;
+  *dV = repf * ppf - dqf + exf * (dPrf - P.fbeta * Prf);
   return rep - q + ex * Pr;
 }
 
@@ -348,17 +365,21 @@ __device__ Turn rmin_device(const PotDev& P, float b, float E) {
   double rd = f32_to_f64(r), ir = rcp64(rd);
   const double lo = f32_to_f64(r_lo) * (1.0 - 1e-4), hi = f32_to_f64(r_hi) * (1.0 + 1e-4);
   const double bd2 = f32_to_f64(b) * f32_to_f64(b), iEd = rcp64(f32_to_f64(E));
-  double rep0 = 0.0, ex0 = 0.0, Pr0 = 0.0, dPr0 = 0.0, dpoly = 0.0, dr = 0.0;
+  const float iEf = 1.f / E;
+  double rep0 = 0.0, ex0 = 0.0, Pr0 = 0.0, dpoly = 0.0, dr = 0.0;
+  float dPr0 = 0.f;
   if (kWarp) __syncwarp();
   bool act = found;
   for (int it = 0; it < 6; ++it) {
     if (kWarp ? !__any_sync(0xffffffffu, act) : !act) break;
-    double dV;
+    float dV, ppf;
     const double ir2 = ir * ir;
-    const double V = V64n(P, rd, ir, &dV, &rep0, &ex0, &Pr0, &dPr0);
+    const double V = V64n(P, rd, ir, &dV, &rep0, &ex0, &Pr0, &dPr0, &ppf);
     const double f = 1.0 - bd2 * ir2 - V * iEd;
-    const double df = 2.0 * bd2 * ir2 * ir - dV * iEd;
-    const double step = -f * rcp64_1(fabs(df)) * (df < 0.0 ? -1.0 : 1.0);
+    // F'(r) in FP32 (see V64n)
+    const float irf = f64_to_f32(ir);
+    const float df = 2.f * b2 * irf * irf * irf - dV * iEf;
+    const double step = -f * f32_to_f64(1.f / df);
     const double rn = rd + step;
     // 1/rn from 1/rd: with s = step/rd, 1/(rd + step) = (1/rd)(1 - s + s^2 - ...),
     // truncated after s^2 (|s| < 1e-4: error below 1e-12 relative, then one
@@ -372,7 +393,7 @@ __device__ Turn rmin_device(const PotDev& P, float b, float E) {
         act = false;
       } else {
         dr = step;
-        dpoly = step * (P.a1 + 2.0 * P.a2 * rd - P.am1 * ir2 - 2.0 * P.am2 * ir2 * ir);
+        dpoly = step * f32_to_f64(ppf);
         ir = irn;
         rd = rn;
         if (fabs(step) <= 2e-5 * rd) act = false;
@@ -391,10 +412,10 @@ __device__ Turn rmin_device(const PotDev& P, float b, float E) {
       const double eb = -P.beta * dr;
       T.rep = rep0 * (1.0 + dpoly * (1.0 + 0.5 * dpoly));
       T.ex = ex0 * (1.0 + eb * (1.0 + 0.5 * eb));
-      T.Pr = fma(dPr0, dr, Pr0);
+      T.Pr = fma(f32_to_f64(dPr0), dr, Pr0);
     } else {  // a long last step (not converged): evaluate at rd
-      double dV, dPr;
-      V64n(P, rd, ir, &dV, &T.rep, &T.ex, &T.Pr, &dPr);
+      float dV, dPr, ppf;
+      V64n(P, rd, ir, &dV, &T.rep, &T.ex, &T.Pr, &dPr, &ppf);
     }
   }
   return T;
@@ -539,6 +560,8 @@ static PotDev make_pot(const dsmc_gas_t& gas, const dsmc_potential_t& p, int n_n
   for (int pp = 0; pp < 16; ++pp) P.Dp[pp] = (pp + 1) * P.Dd[pp + 1];
   for (int pp = 0; pp < 16; ++pp) P.Dpp[pp] = (double)(pp + 1) * (pp + 2) * P.Dd[pp + 1];
   for (int q = 0; q < 6; ++q) P.Cd[q] = (6 + 2 * q) * p.C[q];
+  for (int pp = 0; pp < 16; ++pp) P.fDp[pp] = (float)P.Dp[pp];
+  for (int q = 0; q < 6; ++q) P.fCd[q] = (float)P.Cd[q];
   for (int q = 0; q < 6; ++q) P.Clo[q] = (float)(p.C[q] - (double)P.fC[q]);
   for (int q = 0; q < 6; ++q) P.Cdd[q] = (double)(6 + 2 * q) * (7 + 2 * q) * p.C[q];
   if (p.kind == 0) {
