@@ -58,10 +58,10 @@ MLP_MUFU_PER_PAIR = 3 * 128 * 1.25
 # until captured for the current kernels.  FP64 and FP32 in FLOPs (an FMA is
 # two), MUFU in thread operations.
 KERNEL_OPS = {
-    "k_collide_vhs": {"fp64_flop": 104.4, "fp32_flop": 0.0, "mufu": 21.9},
-    "k_collide_table": {"fp64_flop": 46.0, "fp32_flop": 176.0, "mufu": 56.1},
-    "k_collide_jager": {"fp64_flop": 418.4, "fp32_flop": 7476.5, "mufu": 660.6},
-    "k_jager_chi": {"fp64_flop": 258.9, "fp32_flop": 8927.3, "mufu": 1914.1},
+    "k_collide_vhs": {"fp64_flop": 99.2, "fp32_flop": 0.0, "mufu": 25.4},
+    "k_collide_table": {"fp64_flop": 37.0, "fp32_flop": 180.0, "mufu": 18.0},
+    "k_collide_jager": {"fp64_flop": 340.3, "fp32_flop": 7560.6, "mufu": 661.7},
+    "k_jager_chi": {"fp64_flop": 179.3, "fp32_flop": 9008.9, "mufu": 1915.1},
 }
 
 # the kernels of each phase of the step (for the per-phase rooflines)
