@@ -551,9 +551,11 @@ int dsmc_autotune_chi(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_potenti
 /* Same step from and to HOST memory: copies cell_id_host / v*_host into
  * device buffers reserved by dsmc_ctx_reserve, runs dsmc_step, copies the
  * sorted post-collision velocities and perm back, and synchronises the
- * stream.  The velocity upload runs on a side stream of the context while
- * the cell ids are sorted, and perm downloads while the pairs are selected
- * and updated; all of it has completed when the call returns.  sigma_g_max
+ * stream.  The cell ids upload first; the velocity upload runs on a side
+ * stream of the context while the cell ids are sorted, each component
+ * gathered into cell order as soon as it has landed, and perm downloads
+ * while the pairs are selected and updated; all of it has completed when
+ * the call returns.  sigma_g_max
  * stays on the device between calls (initialised from T_cell_host on the
  * first call after a reserve).  Returns the first error, device-side ones
  * included.  Host arrays should be page-locked for the copies to overlap. */

@@ -30,7 +30,7 @@ struct Ctx {
   // selection (both only read the sorted velocities)
   cudaStream_t f_side = nullptr;
   cudaEvent_t f_ev[2] = {nullptr, nullptr};
-  cudaEvent_t r_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t r_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int64_t launches = 0;
   int64_t graph_launches = 0;
   // step graph
@@ -747,15 +747,18 @@ int dsmc_step_host(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t* path
         return dsmc::record(c, DSMC_ERR_CUDA, "step_host: event");
   }
   cudaStream_t s2 = c->r_side;
-  // Copies overlap the step: the velocities upload on the side stream while
-  // the radix passes sort the cell ids, and perm downloads while the pairs
-  // are selected and updated.
-  bool ok = cudaEventRecord(c->r_ev[0], s) == cudaSuccess && cudaStreamWaitEvent(s2, c->r_ev[0], 0) == cudaSuccess &&
+  // Copies overlap the step: the cell ids upload first (alone on the host
+  // link), then the velocities on the side stream while the radix passes sort
+  // the cell ids, each component gathered as soon as it has landed; perm
+  // downloads while the pairs are selected and updated.
+  bool ok = cudaMemcpyAsync((void*)b.cell_id, cell_id_h, n4, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+            cudaEventRecord(c->r_ev[0], s) == cudaSuccess && cudaStreamWaitEvent(s2, c->r_ev[0], 0) == cudaSuccess &&
             cudaMemcpyAsync((void*)b.vx, vx_h, n8, cudaMemcpyHostToDevice, s2) == cudaSuccess &&
+            cudaEventRecord(c->r_ev[4], s2) == cudaSuccess &&
             cudaMemcpyAsync((void*)b.vy, vy_h, n8, cudaMemcpyHostToDevice, s2) == cudaSuccess &&
+            cudaEventRecord(c->r_ev[5], s2) == cudaSuccess &&
             cudaMemcpyAsync((void*)b.vz, vz_h, n8, cudaMemcpyHostToDevice, s2) == cudaSuccess &&
-            cudaEventRecord(c->r_ev[1], s2) == cudaSuccess &&
-            cudaMemcpyAsync((void*)b.cell_id, cell_id_h, n4, cudaMemcpyHostToDevice, s) == cudaSuccess;
+            cudaEventRecord(c->r_ev[1], s2) == cudaSuccess;
   if (!ok) return dsmc::record(c, DSMC_ERR_CUDA, "step_host: host-to-device copy failed");
   if (!c->r_sg_ready) {
     REQUIRE(c, T_cell_h, "step_host: T_cell_host needed on the first call");
@@ -769,9 +772,15 @@ int dsmc_step_host(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t* path
   if (rc) return rc;
   ok = cudaEventRecord(c->r_ev[2], s) == cudaSuccess && cudaStreamWaitEvent(s2, c->r_ev[2], 0) == cudaSuccess &&
        (!perm_h || cudaMemcpyAsync(perm_h, b.perm, n4, cudaMemcpyDeviceToHost, s2) == cudaSuccess) &&
-       cudaEventRecord(c->r_ev[3], s2) == cudaSuccess && cudaStreamWaitEvent(s, c->r_ev[1], 0) == cudaSuccess;
+       cudaEventRecord(c->r_ev[3], s2) == cudaSuccess;
   if (!ok) return dsmc::record(c, DSMC_ERR_CUDA, "step_host: stream ordering failed");
-  rc = dsmc::launch_gather(c, n, b.n_cells, b.cell_start, b.perm, b.vx, b.vy, b.vz, b.svx, b.svy, b.svz, s);
+  const double* vin[3] = {b.vx, b.vy, b.vz};
+  double* vout[3] = {b.svx, b.svy, b.svz};
+  const int landed[3] = {4, 5, 1};   // the event after each component's upload
+  for (int q = 0; q < 3 && !rc; ++q)
+    rc = cudaStreamWaitEvent(s, c->r_ev[landed[q]], 0) != cudaSuccess
+             ? dsmc::record(c, DSMC_ERR_CUDA, "step_host: stream ordering failed")
+             : dsmc::launch_gather_one(c, n, b.n_cells, b.cell_start, b.perm, vin[q], vout[q], s);
   if (!rc) rc = step_after_sort(c, gas, path, &b, step, stream);
   // the side stream's copies join the caller's stream whatever happened
   const bool joined = cudaStreamWaitEvent(s, c->r_ev[3], 0) == cudaSuccess;

@@ -607,6 +607,17 @@ int launch_sort_keys(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_id,
   return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
 }
 
+// one component: sv[s] = v[perm[s]]
+int launch_gather_one(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_start, const int32_t* perm,
+                      const double* v, double* sv, cudaStream_t s) {
+  if (n <= 0) return 0;
+  const Shape sh = shape_or_default(c, DSMC_TUNE_GATHER);
+  const unsigned g = grid_for(n, sh.threads, sm_count(c) * sh.blocks_per_sm);
+  k_gather1<<<g, sh.threads, 0, s>>>(n, cell_start, n_cells, perm, v, sv);
+  count_launches(c, 1);
+  return cudaGetLastError() == cudaSuccess ? 0 : DSMC_ERR_CUDA;
+}
+
 int launch_gather(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_start, const int32_t* perm,
                   const double* vx, const double* vy, const double* vz, double* svx, double* svy,
                   double* svz, cudaStream_t s) {

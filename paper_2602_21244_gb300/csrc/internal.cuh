@@ -376,6 +376,8 @@ inline Shape shape_or_default(Ctx* c, int kernel) {
 int occupancy_collide_vhs(int threads);
 int occupancy_collide_jager(int threads);
 // the gather step of the cell sort alone (autotuning)
+int launch_gather_one(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_start, const int32_t* perm,
+                      const double* v, double* sv, cudaStream_t s);
 int launch_gather(Ctx* c, int32_t n, int32_t n_cells, const int32_t* cell_start, const int32_t* perm,
                   const double* vx, const double* vy, const double* vz, double* svx, double* svy,
                   double* svz, cudaStream_t s);
