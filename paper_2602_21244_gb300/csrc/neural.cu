@@ -34,7 +34,6 @@ namespace dsmc {
 
 constexpr int kTileM = 128;
 constexpr int kThreads = 512;    // 16 warps: 4 per TMEM lane group, splitting the columns
-constexpr int kColGroups = kThreads / kTileM;
 constexpr int kWidth = 128;
 constexpr int kKin = 32;         // input as two bf16 terms: [hi (16) | lo (16)]
 constexpr int kNout = 16;        // padded output width
@@ -427,7 +426,6 @@ __global__ void __launch_bounds__(kThreads) k_mlp_forward(MlpShape sh, const uin
   const Group q = my_group(L.slots);
   uint32_t phase = 0;
   const int64_t tiles = (n + kTileM - 1) / kTileM;
-  bool alive = true;
   for (int64_t tile = blockIdx.x + (int64_t)gridDim.x * q.g; tile < tiles; tile += (int64_t)gridDim.x * q.G) {
     const int64_t row = tile * kTileM + q.t;
     if (q.t < kTileM) {
@@ -441,10 +439,9 @@ __global__ void __launch_bounds__(kThreads) k_mlp_forward(MlpShape sh, const uin
     }
     group_sync(q);
     float o[3];
-    if (!mlp_tile(smem, L, sh, q, tmem, phase, o, status, L.x(q.g))) { alive = false; break; }
+    if (!mlp_tile(smem, L, sh, q, tmem, phase, o, status, L.x(q.g))) break;   // status recorded
     if (q.t < kTileM && row < n) { y[3 * row] = o[0]; y[3 * row + 1] = o[1]; y[3 * row + 2] = o[2]; }
   }
-  (void)alive;
   cta_teardown(tmem, L);
 }
 
