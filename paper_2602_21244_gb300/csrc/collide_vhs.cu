@@ -30,20 +30,32 @@ __global__ void __launch_bounds__(256) k_collide_vhs(VhsArgs a) {
   const int lane = threadIdx.x & 31;
   int r = 0;
   int64_t base = 0;
-  for (;;) {
+  // the next unit claimed and its pair records loading while the current
+  // one updates (as in k_collide_table)
+  auto claim = [&](int32_t* u0, int32_t* u1, int* ur) {
     unsigned unit = 0;
     if (lane == 0) unit = atomicAdd(a.bar + 3, 1u);
     unit = __shfl_sync(0xffffffffu, unit, 0);
-    int32_t p0, p1;
-    if (!unit_range(a.ro, R, 32, r, base, unit, &p0, &p1)) break;
-    const int32_t p = p0 + lane;
-    const bool valid = p < p1;
-    int4 q = make_int4(0, 0, 0, 0);
+    const bool got = unit_range(a.ro, R, 32, r, base, unit, u0, u1);
+    *ur = r;
+    return got;
+  };
+  int32_t p0 = 0, p1 = 0;
+  int rc = 0;
+  bool have = claim(&p0, &p1, &rc);
+  int4 q = make_int4(0, 0, 0, 0);
+  uint32_t dep = 0u;
+  if (have && p0 + lane < p1) { q = a.pairs[p0 + lane]; dep = a.deps[p0 + lane]; }
+  while (have) {
+    int32_t n0 = 0, n1 = 0;
+    int rn = 0;
+    const bool next = claim(&n0, &n1, &rn);
+    int4 qn = make_int4(0, 0, 0, 0);
+    uint32_t depn = 0u;
+    if (next && n0 + lane < n1) { qn = a.pairs[n0 + lane]; depn = a.deps[n0 + lane]; }
+    const bool valid = p0 + lane < p1;
     bool ok = true;
-    if (valid) {
-      q = a.pairs[p];
-      ok = wait_deps(a.done, q.x, q.y, a.deps[p], a.bar + 2, a.status);
-    }
+    if (valid) ok = wait_deps(a.done, q.x, q.y, dep, a.bar + 2, a.status);
     const bool live = valid && ok;
     double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (live) {
@@ -59,9 +71,10 @@ __global__ void __launch_bounds__(256) k_collide_vhs(VhsArgs a) {
     if (live) {
       __stcg(a.vx + q.x, v[0]); __stcg(a.vy + q.x, v[1]); __stcg(a.vz + q.x, v[2]);
       __stcg(a.vx + q.y, v[3]); __stcg(a.vy + q.y, v[4]); __stcg(a.vz + q.y, v[5]);
-      release_pair(a.done, q.x, q.y, (unsigned)(r + 1));
+      release_pair(a.done, q.x, q.y, (unsigned)(rc + 1));
     }
     if (!__all_sync(0xffffffffu, ok)) break;
+    have = next; p0 = n0; p1 = n1; rc = rn; q = qn; dep = depn;
   }
 }
 
