@@ -490,6 +490,69 @@ def test_collide_neural_parity(name, shape):
     assert np.all(np.abs(e1 - e0) <= 1e-12 * np.maximum(e0, 1e-300))
 
 
+# ------------------------------------------------------------------ C4 at full size
+
+def test_c4_full_size_neural_step():
+    """The hypersonic gas at its full size (9,144,283 particles, 150,000
+    cells) through dsmc_step on the neural path, as the bench times it.
+    Bit-exact: perm, cell_start, the step's pair, candidate and round counts,
+    every pair (cell, candidate, particles, round).  Sampled: 20,000 pairs
+    whose particles collide exactly once in the step -- their inputs are the
+    sorted pre-collision state and their final relative velocity is the
+    pair's post-collision one scaled by moment matching's alpha > 0, so its
+    direction is the collide's u -- within 2e-3 of the oracle's bf16-storage
+    emulation and 2e-2 of its FP64 forward.  At every cell: momentum and
+    energy after moment matching within 1e-12 of the pre-collision moments."""
+    from paper_2602_21244_gb300 import dsmc as D
+    T = torch()
+    w = W.hypersonic()
+    n, nc = len(w["cell_id"]), w["n_cells"]
+    gas_o = O.make_gas(**w["gas"])
+    sg0 = _sgmax0(w, gas_o)
+    step = 3
+    perm, cs, sx, sy, sz = oracle_sorted(w)
+    mom = O.cell_moments(cs, sx, sy, sz)
+    pr = O.select_pairs(gas_o, cs, sx, sy, sz, sg0, step, capacity=1 << 24)
+    wts, bias, mlp_o, mlp_d = _mlp_setup()
+    C = ctx()
+    st = D.StepState(C, n, nc, 1 << 24)
+    st.sigma_g_max.copy_(cuda(sg0))
+    st.cell_id.copy_(cuda(w["cell_id"])); st.vx.copy_(cuda(w["vx"]))
+    st.vy.copy_(cuda(w["vy"])); st.vz.copy_(cuda(w["vz"]))
+    path = D.make_path(D.PATH_NEURAL, mlp=mlp_d, w_bits=w_bits_tensor(wts["W_bits"]), bias=cuda(bias, T.float32))
+    C.step(D.make_gas(w["gas"]), path, st, step)
+    assert C.sync_status() == 0
+    assert np.array_equal(host(st.perm), perm) and np.array_equal(host(st.cell_start), cs)
+    inf = st.info_host()
+    assert inf["n_pairs"] == pr["n_pairs"] and inf["n_candidates"] == pr["n_cand"]
+    assert inf["n_rounds"] == pr["n_rounds"]
+    sh = sel_host(st.sel)
+    p = sh["pairs"]
+    order = np.lexsort((p[:, 3], p[:, 2]))
+    assert np.array_equal(p[order, 0], pr["i"]) and np.array_equal(p[order, 1], pr["j"])
+    assert np.array_equal(p[order, 3], pr["m"]) and np.array_equal(pairs_round_of(sh)[order], pr["round"])
+    # pairs whose two particles collide only once in the step
+    cnt = np.bincount(np.concatenate([pr["i"], pr["j"]]), minlength=n)
+    once = np.flatnonzero((cnt[pr["i"]] == 1) & (cnt[pr["j"]] == 1))
+    pick = np.sort(np.random.default_rng(41).choice(once, size=min(20000, len(once)), replace=False))
+    sub = dict(i=pr["i"][pick], j=pr["j"][pick], cell=pr["cell"][pick], m=pr["m"][pick], n_pairs=len(pick))
+    *_, ub = O.collide_neural(gas_o, mlp_o, wts["W"], bias, mom, sub, step, sx, sy, sz, bf16=True, want_u=True)
+    *_, u64 = O.collide_neural(gas_o, mlp_o, wts["W"], bias, mom, sub, step, sx, sy, sz, want_u=True)
+    got = [host(a) for a in (st.svx, st.svy, st.svz)]
+    d = np.stack([g_[sub["i"]] - g_[sub["j"]] for g_ in got], 1)
+    u = d / np.linalg.norm(d, axis=1, keepdims=True)
+    assert np.linalg.norm(u - ub, axis=1).max() <= 2e-3
+    assert np.linalg.norm(u - u64, axis=1).max() <= 2e-2
+    # conservation at every cell after moment matching
+    m1 = O.cell_moments(cs, *got)
+    nn = np.maximum(mom[:, 0], 1)
+    vmax = max(np.abs(sx).max(), np.abs(sy).max(), np.abs(sz).max())
+    assert np.all(np.abs(m1[:, 1:4] - mom[:, 1:4]) <= 1e-12 * nn[:, None] * vmax)
+    e0 = mom[:, 4] + (mom[:, 1] ** 2 + mom[:, 2] ** 2 + mom[:, 3] ** 2) / nn
+    e1 = m1[:, 4] + (m1[:, 1] ** 2 + m1[:, 2] ** 2 + m1[:, 3] ** 2) / nn
+    assert np.all(np.abs(e1 - e0) <= 1e-12 * np.maximum(e0, 1e-300))
+
+
 # ------------------------------------------------------------------ host-buffer step
 
 def test_step_host_matches_device_step():
