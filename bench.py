@@ -300,7 +300,7 @@ def run_gb300(args, rank, world, dist):
 
     results = {}
     neural_kernel = None
-    # the look-up path's table (Sec. 3.4.5): 512 x 512 nodes over b/b_max and
+    # the look-up path's table (Sec. 3.4.4): 512 x 512 nodes over b/b_max and
     # ln(E_r/k_B) in [ln 5, ln 6e4], filled with the exact chi (128 nodes)
     table, table_info = None, None
     if "table" in args.paths.split(","):

@@ -112,7 +112,7 @@ typedef struct {
   double eps;     /* projection safeguard on ||y|| (normalised units) */
 } dsmc_mlp_t;
 
-/* Deflection-angle table of the look-up path (Sec. 3.4.5): chi[j nb + i] =
+/* Deflection-angle table of the look-up path (Sec. 3.4.4): chi[j nb + i] =
  * chi(b_max i/(nb-1), exp(lnE_min + j (lnE_max - lnE_min)/(nE-1))), i.e. a
  * uniform grid in b/b_max over [0, 1] and in ln(E_r/k_B) over [lnE_min,
  * lnE_max], both ends included.  chi: device memory, FP32. */
@@ -315,7 +315,7 @@ int dsmc_transport_viscosity(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_
  * dsmc_chi_mlp_packed_size() bytes, 16-byte aligned) in the operand layout
  * the kernel streams.  dsmc_chi_mlp_forward: n rows x [2] (FP32, device) ->
  * y (Softplus output) and/or chi (e^y - 1), either may be NULL.
- * dsmc_chi_mlp_table: the nE x nb table of Sec. 3.4.5 (row j: ln(E_r)* =
+ * dsmc_chi_mlp_table: the nE x nb table of Sec. 3.4.4 (row j: ln(E_r)* =
  * j/(nE-1); column i: b/b_max = i/(nb-1)), chi = e^y - 1, FP32 device memory. */
 size_t dsmc_chi_mlp_packed_size(void);
 int dsmc_chi_mlp_pack(dsmc_ctx_t* ctx, const uint16_t* w_bits, void* packed, void* stream);
@@ -324,12 +324,12 @@ int dsmc_chi_mlp_forward(dsmc_ctx_t* ctx, const void* packed, const float* bias,
 int dsmc_chi_mlp_table(dsmc_ctx_t* ctx, const void* packed, const float* bias, int32_t nb, int32_t nE,
                        float* table, void* stream);
 
-/* Sec. 3.4.5: fill a chi table with the exact deflection angle (the
+/* Sec. 3.4.4: fill a chi table with the exact deflection angle (the
  * computation of dsmc_jager_chi at every node; b_max from gas->b_max).
  * table: nE x nb FP32, device memory. */
 int dsmc_chi_table_build(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_potential_t* pot, int32_t n_nodes,
                          int32_t nb, int32_t nE, double lnE_min, double lnE_max, float* table, void* stream);
-/* Sec. 3.4.5 look-up path: the pair update of dsmc_collide_jager with chi by
+/* Sec. 3.4.4 look-up path: the pair update of dsmc_collide_jager with chi by
  * bilinear interpolation in `table` at (b/b_max, ln(E_r/k_B)); ln E outside
  * the table is clamped to its range.  b/b_max = sqrt(U1) and eps = 2 pi U2
  * from tag 4, as the Jager path.  chi_out (optional) as dsmc_collide_jager. */
@@ -568,7 +568,7 @@ int dsmc_step_host(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_path_t* pa
 
 /* ---------------------------------------------------------------- training */
 
-/* Sec. 3.4.5 physics harvesting: target post-collision velocities of pairs
+/* Sec. 3.4.4 physics harvesting: target post-collision velocities of pairs
  * (vi, vj: [n x 3] FP64 row-major) deflected by chi(b, E) with azimuth eps
  * (b in Angstrom, eps in rad), as in dsmc_collide_jager. */
 int dsmc_harvest_jager(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_potential_t* pot,

@@ -474,7 +474,7 @@ def chi_mlp_forward(W, bias, x, bf16=False) -> np.ndarray:
 
 
 def chi_mlp_table(W, bias, nb: int, nE: int, bf16=False) -> np.ndarray:
-    """The look-up table of Sec. 3.4.5 synthesised by the chi-MLP: node (j, i)
+    """The look-up table of Sec. 3.4.4 synthesised by the chi-MLP: node (j, i)
     at ln(E_r)* = j/(nE-1), b/b_max = i/(nb-1), chi = e^y - 1; [nE x nb]."""
     xe = np.repeat(np.arange(nE) / (nE - 1), nb)
     xb = np.tile(np.arange(nb) / (nb - 1), nE)

@@ -28,7 +28,7 @@
  *   Sec. 3.4.1 Eq. (jager_potential), Eq. (damping), screened Coulomb core
  *   Sec. 3.4.2 classical scattering integral chi(b, E_r)
  *   Sec. 3.4.4 r_min = largest root, Brent-Dekker to 1e-14, u = r_min/r
- *   Sec. 3.4.5 look-up table over (b/b_max, ln E_r/k_B), bilinear interpolation
+ *   Sec. 3.4.4 look-up table over (b/b_max, ln E_r/k_B), bilinear interpolation
  *
  * Readings where the paper is silent (all listed in the design notes):
  *   R1  Philox4x32-10 (Salmon et al., SC'11) keyed by seed, counter
@@ -44,7 +44,7 @@
  *       when the cell mean velocity is zero.
  *   R6  energy-shell projection divides by ||y|| (not ||y||+eps) so the pair
  *       energy is exact; ||y|| <= eps falls back to an isotropic direction.
- *   R7  the chi table of the look-up path (Sec. 3.4.5: b~ = b/b_max,
+ *   R7  the chi table of the look-up path (Sec. 3.4.4: b~ = b/b_max,
  *       E~ = ln(E_r/k_B), bilinear interpolation) has uniform nodes including
  *       both ends of each axis; E~ outside the table is clamped to it.
  *   R8  transport integrals (Eq. chapman_enskog and the two integrals after
@@ -735,7 +735,7 @@ void or_collide_given_chi(const or_gas_t* gs, int64_t n_pairs, const int32_t* pi
 }
 
 /* ------------------------------------------------------------------ */
-/* Sec. 3.4.5 (look-up strategy): chi table and collision by look-up    */
+/* Sec. 3.4.4 (look-up strategy): chi table and collision by look-up    */
 /* ------------------------------------------------------------------ */
 /* The table of the paper's look-up path, filled here by the exact chi: a
  * uniform grid in b~ = b/b_max over [0, 1] (nb nodes) and in E~ = ln(E_r/k_B)
@@ -947,7 +947,7 @@ void or_collide_neural(const or_gas_t* gs, const or_mlp_t* d, const double* W,
   for_each_pair(n_pairs, pcell, neural_pair, &Nc);
 }
 
-/* Jager harvest of training targets (Sec. 3.4.5 "physics harvesting"):
+/* Jager harvest of training targets (Sec. 3.4.4 "physics harvesting"):
  * per pair, deflect v_r = v_i - v_j by chi(b, E) with azimuth eps and
  * apply the CM update.  b in Angstrom. */
 void or_harvest_jager(const or_gas_t* gs, const or_pot_t* P, int64_t n,

@@ -1,7 +1,7 @@
 // chi-MLP surrogate (Sec. 3.4, Fig. nn_architecture; reading R9) on the
 // tcgen05 tensor cores: inputs [ln(E_r)*, b/b_max] -> 512, 512, 512, 256, 128
 // (SiLU) -> 1 (Softplus); the Softplus output y approximates ln(1 + chi),
-// so chi = e^y - 1.  It synthesises the look-up table of Sec. 3.4.5.
+// so chi = e^y - 1.  It synthesises the look-up table of Sec. 3.4.4.
 //
 // One persistent CTA of 17 warps per SM works on 128-row tiles.  The
 // tile's activations stay in shared memory (bf16, K-major core matrices,

@@ -727,7 +727,7 @@ __global__ void __launch_bounds__(128, 4) k_collide_jager(PotDev P, JagerArgs a)
 }
 
 // ---------------------------------------------------------------- look-up table
-// Sec. 3.4.5: the table of the look-up path over b~ = b/b_max (nb uniform
+// Sec. 3.4.4: the table of the look-up path over b~ = b/b_max (nb uniform
 // nodes on [0, 1]) and E~ = ln(E_r/k_B) (nE uniform nodes on [lnE_min,
 // lnE_max]), both ends included; filled here with the exact chi.
 __global__ void __launch_bounds__(128) k_chi_table(PotDev P, int32_t nb, int32_t nE, double bmax_A, double lnE_min,

@@ -1,7 +1,7 @@
 // Per-pair post-collision velocities of the CUDA-core update rules, shared
 // by the collide kernels and the fused step: the VHS isotropic scatter
 // (Sec. 2.1) and the deflection by a chi looked up in the table of the
-// look-up path (Sec. 3.4.5), each with the centre-of-mass update (Sec. 2.3).
+// look-up path (Sec. 3.4.4), each with the centre-of-mass update (Sec. 2.3).
 // A pair's random numbers are keyed by its candidate index m and cell k, so
 // which thread runs a pair never changes its result.  Every rounding is
 // explicit (the _rn intrinsics, fma): no multiply-add contraction is left to

@@ -63,7 +63,7 @@ def test_chi_mlp_table_matches_oracle_and_is_deterministic():
     T = host(T1)
     assert T.shape == (17, 33)
     assert np.abs(T - Te).max() <= 1e-3 * np.abs(Te).max()
-    # the full-size table of Sec. 3.4.5 against forward at sampled nodes
+    # the full-size table of Sec. 3.4.4 against forward at sampled nodes
     big = host(C.chi_mlp_table(packed, bias, 512, 512))
     rng = np.random.default_rng(9)
     j, i = rng.integers(0, 512, 64), rng.integers(0, 512, 64)

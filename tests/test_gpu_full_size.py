@@ -7,7 +7,7 @@ and every pair (cell, candidate, particles, round) bit-exact against the
 oracle; every cell's momentum and energy after moment matching within 1e-12
 of its pre-collision moments.
 
-VHS (Sec. 2.5, FP64 throughout): every particle's velocity within 1e-12 of
+VHS (Sec. 2.1; FP64 throughout): every particle's velocity within 1e-12 of
 the oracle's collide and moment matching.
 
 Look-up and Jager: the oracle cannot redo millions of exact chi in seconds,

@@ -1,4 +1,4 @@
-"""The look-up path (Sec. 3.4.5): chi table built on the GPU with the exact
+"""The look-up path (Sec. 3.4.4): chi table built on the GPU with the exact
 chi, and the pair update with chi by bilinear interpolation in a table,
 through the C ABI against the FP64 oracle (oracle/dsmc_oracle.c:
 or_chi_table, or_chi_lookup, or_collide_given_chi, pinned in

@@ -659,7 +659,7 @@ def test_adam_matches_torch():
     np.testing.assert_allclose(th, p.detach().numpy(), rtol=1e-12, atol=1e-14)
 
 
-# ------------------------------------------------------------------ look-up table (Sec. 3.4.5)
+# ------------------------------------------------------------------ look-up table (Sec. 3.4.4)
 
 def test_chi_table_nodes_hard_sphere_closed_form():
     """Table nodes: b = b_max i/(nb-1) and E = exp(lnE_min + j dE); the hard
