@@ -351,7 +351,7 @@ def run_gb300(args, rank, world, dist):
             C.cell_moments(st.cell_start, st.svx, st.svy, st.svz, mom=st.mom)
             e[2].record(stream)
             C.select_pairs(gas, st.cell_start, st.svx, st.svy, st.svz, st.sigma_g_max, it, capacity,
-                           out=sel, ws=st.ws)
+                           out=sel, ws=st.ws, order=D.ORDER_LEVELS if path == "neural" else D.ORDER_ROUNDS)
             e[3].record(stream)
             if path == "vhs":
                 C.collide_vhs(gas, it, sel, st.svx, st.svy, st.svz)

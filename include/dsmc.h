@@ -57,6 +57,9 @@ enum { DSMC_PATH_VHS = 0, DSMC_PATH_JAGER = 1, DSMC_PATH_NEURAL = 2, DSMC_PATH_T
 /* Largest number of conflict-free rounds one step may need (see dsmc_select_pairs). */
 #define DSMC_MAX_ROUNDS 1024
 
+/* Bucket order of the selection's pair list (dsmc_select_pairs_ordered). */
+enum { DSMC_ORDER_ROUNDS = 0, DSMC_ORDER_LEVELS = 1 };
+
 typedef struct dsmc_ctx dsmc_ctx_t;
 
 /* Gas and selection parameters (Sec. 2.2).
@@ -231,6 +234,24 @@ int dsmc_select_pairs(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, int32_t n, int32_t
                       const double* vz, double* sigma_g_max, uint64_t step, int64_t capacity,
                       int32_t* pairs, uint32_t* deps, int32_t* round_offsets, dsmc_select_info_t* info,
                       void* ws, size_t ws_bytes, void* stream);
+/* dsmc_select_pairs with the pair list's buckets chosen by `order`:
+ * DSMC_ORDER_ROUNDS is dsmc_select_pairs.  DSMC_ORDER_LEVELS buckets the
+ * same pairs by claim level = round + (n_rounds - 1 - the last round of the
+ * pair's cell): every pair of a cell moves by the same amount, so each
+ * particle's pairs keep their order and the levels are again conflict-free
+ * buckets that reproduce the sequential result in level order, but a cell
+ * with few rounds is deferred to the end of the list while the cells with
+ * the longest dependency chains start at once.  round_offsets[l] = first
+ * pair of level l (l = 0..n_rounds), inside a level in cell order and
+ * candidate order within a cell; deps[p] holds the 1-based levels of the
+ * previous pairs of i and j (0 = none); *info (n_rounds included) is as for
+ * rounds.  The collide calls take either list.  Another order returns
+ * DSMC_ERR_ARG. */
+int dsmc_select_pairs_ordered(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, int32_t n, int32_t n_cells,
+                              const int32_t* cell_start, const double* vx, const double* vy,
+                              const double* vz, double* sigma_g_max, uint64_t step, int64_t capacity,
+                              int32_t* pairs, uint32_t* deps, int32_t* round_offsets, dsmc_select_info_t* info,
+                              int32_t order, void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------- pair updates */
 
@@ -454,7 +475,9 @@ typedef struct {
 
 size_t dsmc_step_workspace_size(int32_t n, int32_t n_cells, int64_t capacity);
 /* One collision step: sort, pre moments, selection, pair updates of the
- * chosen path, moment matching (Sec. 2.1-2.6). */
+ * chosen path, moment matching (Sec. 2.1-2.6).  The pair list in `buf` is
+ * bucketed by claim level (DSMC_ORDER_LEVELS) on DSMC_PATH_NEURAL and by
+ * round on the other paths. */
 int dsmc_step(dsmc_ctx_t* ctx, const dsmc_gas_t* gas, const dsmc_path_t* path,
               const dsmc_step_buffers_t* buf, uint64_t step, void* stream);
 

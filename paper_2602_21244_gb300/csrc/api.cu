@@ -235,18 +235,28 @@ static int check_gas(Ctx* c, const dsmc_gas_t* gas) {
   return 0;
 }
 
-int dsmc_select_pairs(dsmc_ctx_t* c, const dsmc_gas_t* gas, int32_t n, int32_t n_cells,
-                      const int32_t* cell_start, const double* vx, const double* vy,
-                      const double* vz, double* sgmax, uint64_t step, int64_t capacity,
-                      int32_t* pairs, uint32_t* deps, int32_t* round_offsets, dsmc_select_info_t* info,
-                      void* ws, size_t ws_bytes, void* stream) {
+int dsmc_select_pairs_ordered(dsmc_ctx_t* c, const dsmc_gas_t* gas, int32_t n, int32_t n_cells,
+                              const int32_t* cell_start, const double* vx, const double* vy,
+                              const double* vz, double* sgmax, uint64_t step, int64_t capacity,
+                              int32_t* pairs, uint32_t* deps, int32_t* round_offsets, dsmc_select_info_t* info,
+                              int32_t order, void* ws, size_t ws_bytes, void* stream) {
   CHECK_CTX(c);
   if (int rc = check_gas(c, gas)) return rc;
   REQUIRE(c, n >= 0 && n_cells >= 1 && capacity >= 0, "select: bad sizes");
   REQUIRE(c, cell_start && sgmax && round_offsets && info && ws, "select: null pointer");
   REQUIRE(c, capacity == 0 || (pairs && deps), "select: null pairs or deps");
+  REQUIRE(c, order == DSMC_ORDER_ROUNDS || order == DSMC_ORDER_LEVELS, "select: bad order");
   return dsmc::launch_select(c, *gas, n, n_cells, cell_start, vx, vy, vz, sgmax, step, capacity,
-                             pairs, deps, round_offsets, info, ws, ws_bytes, S(stream));
+                             pairs, deps, round_offsets, info, ws, ws_bytes, order, S(stream));
+}
+
+int dsmc_select_pairs(dsmc_ctx_t* c, const dsmc_gas_t* gas, int32_t n, int32_t n_cells,
+                      const int32_t* cell_start, const double* vx, const double* vy,
+                      const double* vz, double* sgmax, uint64_t step, int64_t capacity,
+                      int32_t* pairs, uint32_t* deps, int32_t* round_offsets, dsmc_select_info_t* info,
+                      void* ws, size_t ws_bytes, void* stream) {
+  return dsmc_select_pairs_ordered(c, gas, n, n_cells, cell_start, vx, vy, vz, sgmax, step, capacity, pairs,
+                                   deps, round_offsets, info, DSMC_ORDER_ROUNDS, ws, ws_bytes, stream);
 }
 
 size_t dsmc_collide_workspace_size(int32_t n) { return dsmc::collide_ws(n); }
@@ -592,6 +602,15 @@ static int collide_step(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t*
   return rc;
 }
 
+// The pair list's bucket order in a step: claim levels for the neural path,
+// whose pair updates are long enough that the round structure's tail (the
+// deep cells' last rounds, one dependency link each) sets its end; rounds
+// for the others, whose short updates wait on fresher dependencies when the
+// levels interleave the rounds.
+static int32_t step_order(const dsmc_path_t* path) {
+  return path->path == DSMC_PATH_NEURAL ? DSMC_ORDER_LEVELS : DSMC_ORDER_ROUNDS;
+}
+
 static int step_after_sort(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path_t* path,
                            const dsmc_step_buffers_t* B, uint64_t step, void* stream);
 
@@ -620,9 +639,9 @@ static int step_after_sort(dsmc_ctx_t* c, const dsmc_gas_t* gas, const dsmc_path
   // the side stream joins the caller's stream whatever happens next
   const bool joined_ev = cudaEventRecord(c->f_ev[1], c->f_side) == cudaSuccess;
   if (!rc)
-    rc = dsmc_select_pairs(c, gas, B->n, B->n_cells, B->cell_start, B->svx, B->svy, B->svz,
-                           B->sigma_g_max, step, B->capacity, B->pairs, B->deps, B->round_offsets, B->info,
-                           B->ws, B->ws_bytes, stream);
+    rc = dsmc_select_pairs_ordered(c, gas, B->n, B->n_cells, B->cell_start, B->svx, B->svy, B->svz,
+                                   B->sigma_g_max, step, B->capacity, B->pairs, B->deps, B->round_offsets,
+                                   B->info, step_order(path), B->ws, B->ws_bytes, stream);
   if (!rc) rc = collide_step(c, gas, path, B, step, stream);
   const bool joined = joined_ev && cudaStreamWaitEvent(s, c->f_ev[1], 0) == cudaSuccess;
   if (rc) return rc;

@@ -304,7 +304,7 @@ size_t select_ws(int32_t n, int32_t n_cells, int64_t capacity);
 int launch_select(Ctx* c, const dsmc_gas_t& gas, int32_t n, int32_t n_cells, const int32_t* cs,
                   const double* vx, const double* vy, const double* vz, double* sgmax,
                   uint64_t step, int64_t capacity, int32_t* pairs, uint32_t* deps, int32_t* round_offsets,
-                  dsmc_select_info_t* info, void* ws, size_t ws_bytes, cudaStream_t s);
+                  dsmc_select_info_t* info, void* ws, size_t ws_bytes, int32_t order, cudaStream_t s);
 int launch_sgmax_init(Ctx* c, const dsmc_gas_t& gas, int32_t n_cells, const double* T,
                       double factor, double* sgmax, cudaStream_t s);
 // per-particle done stamps of the collide kernels

@@ -232,6 +232,7 @@ __global__ void __launch_bounds__(kEmitWarps * 32, 4) k_sel_emit(SelArgs a) {
     }
     __syncwarp();
     int32_t pos = p0;
+    int cm = -1;   // this lane's largest round of the cell
     // one batch of up to 32 accepted pairs in candidate order: lane t holds
     // pair pos + t (act), candidate m, particles i, j
     auto batch = [&](bool act, int32_t m, int32_t i, int32_t j, int cnt) {
@@ -244,6 +245,7 @@ __global__ void __launch_bounds__(kEmitWarps * 32, 4) k_sel_emit(SelArgs a) {
           a.tmp_round[q] = r;
           a.tmp_dep[q] = (uint32_t)Li | ((uint32_t)Lj << 16);
           rm = r > rm ? r : rm;
+          cm = r > cm ? r : cm;
         }
         if (act) atomicAdd(&hist[r], 1);
         __syncwarp();
@@ -317,7 +319,14 @@ __global__ void __launch_bounds__(kEmitWarps * 32, 4) k_sel_emit(SelArgs a) {
         a.tmp_dep[p] = (uint32_t)(li + 1) | ((uint32_t)(lj + 1) << 16);
         atomicAdd(&hist[r], 1);
         rm = r > rm ? r : rm;
+        cm = r > cm ? r : cm;
       }
+    }
+    if (a.order) {
+      // the cell's last round beside each of its pairs' rounds
+      __syncwarp();
+      const int last_round = __reduce_max_sync(0xffffffffu, cm);
+      for (int32_t p = p0 + lane; p < p1; p += 32) a.tmp_round[p] |= last_round << 16;
     }
     if (lane == 0) a.sgmax[k] = a.sgnew[k];
     __syncwarp();
@@ -350,8 +359,11 @@ __global__ void __launch_bounds__(kEmitWarps * 32, 4) k_sel_emit(SelArgs a) {
     if (act) a.tmp[q] = make_int4(base + i, base + j, k, m);
     int Li, Lj;
     const int r = batch_rounds(act, (uint32_t)i, (uint32_t)j, mh, lh, a.status, &Li, &Lj);
+    int cm = act ? r : -1;   // the half's cell's last round (shuffles within the half)
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) cm = max(cm, __shfl_xor_sync(0xffffffffu, cm, o));
     if (act) {
-      a.tmp_round[q] = r;
+      a.tmp_round[q] = a.order ? (r | (cm << 16)) : r;
       a.tmp_dep[q] = (uint32_t)Li | ((uint32_t)Lj << 16);
       rm = r > rm ? r : rm;
       atomicAdd(&hist[r], 1);
@@ -382,8 +394,11 @@ __global__ void __launch_bounds__(kEmitWarps * 32, 4) k_sel_emit(SelArgs a) {
   rm = __reduce_max_sync(0xffffffffu, rm);
   if (lane == 0 && rm >= 0) atomicMax(&rmax_blk, rm + 1);
   __syncthreads();
-  for (int t = threadIdx.x; t < DSMC_MAX_ROUNDS; t += blockDim.x)
-    if (hist[t]) atomicAdd(a.round_count + t, hist[t]);
+  // per-round counts (the level counts, which need the step's round count,
+  // come from k_sel_rcount)
+  if (!a.order)
+    for (int t = threadIdx.x; t < DSMC_MAX_ROUNDS; t += blockDim.x)
+      if (hist[t]) atomicAdd(a.round_count + t, hist[t]);
   if (threadIdx.x == 0 && rmax_blk > 0) atomicMax(a.n_rounds, rmax_blk);
 }
 
@@ -402,7 +417,8 @@ constexpr int kScatterChunk = 4096;
 __global__ void __launch_bounds__(256)
 k_sel_rcount(const int32_t* __restrict__ tmp_round, const int32_t* __restrict__ offs, int32_t n_cells,
              int64_t capacity, const int32_t* __restrict__ n_rounds, int32_t n_chunks, int32_t* __restrict__ cnt,
-             const double* __restrict__ sgnew, double* __restrict__ sgmax) {
+             const double* __restrict__ sgnew, double* __restrict__ sgmax, int order,
+             int32_t* __restrict__ level_count) {
   __shared__ int hist[DSMC_MAX_ROUNDS];
   const int64_t total = offs[n_cells];
   if (total > capacity) {
@@ -416,9 +432,15 @@ k_sel_rcount(const int32_t* __restrict__ tmp_round, const int32_t* __restrict__ 
   const int R = *n_rounds;
   for (int t = threadIdx.x; t < R; t += blockDim.x) hist[t] = 0;
   __syncthreads();
-  for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) atomicAdd(&hist[tmp_round[p]], 1);
+  for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    const int t = tmp_round[p];
+    atomicAdd(&hist[order ? (t & 0xFFFF) + R - 1 - (t >> 16) : t], 1);
+  }
   __syncthreads();
-  for (int t = threadIdx.x; t < R; t += blockDim.x) cnt[(size_t)t * n_chunks + blockIdx.x] = hist[t];
+  for (int t = threadIdx.x; t < R; t += blockDim.x) {
+    cnt[(size_t)t * n_chunks + blockIdx.x] = hist[t];
+    if (order && hist[t]) atomicAdd(level_count + t, hist[t]);
+  }
 }
 
 // Block r: exclusive scan of cnt[r][0..chunks) + the offset of round r (in
@@ -519,7 +541,7 @@ __global__ void __launch_bounds__(kScatterWarps * 32, 2)
 k_sel_scatter(const int4* __restrict__ tmp, const int32_t* __restrict__ tmp_round,
               const uint32_t* __restrict__ tmp_dep, const int32_t* __restrict__ offs, int32_t n_cells,
               int64_t capacity, const int32_t* __restrict__ n_rounds, int32_t n_chunks,
-              const int32_t* __restrict__ base, int4* __restrict__ out, uint32_t* __restrict__ deps) {
+              const int32_t* __restrict__ base, int4* __restrict__ out, uint32_t* __restrict__ deps, int order) {
   extern __shared__ int swh[];   // [kScatterWarps][R]
   const int64_t total = offs[n_cells];
   if (total > capacity) return;
@@ -535,7 +557,8 @@ k_sel_scatter(const int4* __restrict__ tmp, const int32_t* __restrict__ tmp_roun
 #pragma unroll
   for (int j = 0; j < kScatterPer; ++j) {
     const int64_t p = s0 + j * 32 + lane;
-    rr[j] = p < p1 ? tmp_round[p] : -1;
+    const int t = p < p1 ? tmp_round[p] : -1;
+    rr[j] = order && t >= 0 ? (t & 0xFFFF) + R - 1 - (t >> 16) : t;
   }
   __syncthreads();
   int old[kScatterPer];
@@ -569,7 +592,16 @@ k_sel_scatter(const int4* __restrict__ tmp, const int32_t* __restrict__ tmp_roun
       const int64_t p = s0 + j * 32 + lane;
       const int q = swh[w * R + rr[j]] + o + (int)(pk[j] >> 5);
       out[q] = tmp[p];
-      deps[q] = tmp_dep[p];
+      uint32_t d = tmp_dep[p];
+      if (order) {
+        // the previous pairs of i and j lie in the same cell: the same shift
+        const uint32_t sh = (uint32_t)(rr[j] - (tmp_round[p] & 0xFFFF));
+        uint32_t di = d & 0xFFFFu, dj = d >> 16;
+        if (di) di += sh;
+        if (dj) dj += sh;
+        d = di | (dj << 16);
+      }
+      deps[q] = d;
     }
   }
 }
@@ -644,7 +676,7 @@ static unsigned blocks_for(int64_t work, int per_block, int max_blocks) {
 int launch_select(Ctx* c, const dsmc_gas_t& gas, int32_t n, int32_t n_cells, const int32_t* cs,
                   const double* vx, const double* vy, const double* vz, double* sgmax,
                   uint64_t step, int64_t capacity, int32_t* pairs, uint32_t* deps, int32_t* round_offsets,
-                  dsmc_select_info_t* info, void* ws, size_t ws_bytes, cudaStream_t s) {
+                  dsmc_select_info_t* info, void* ws, size_t ws_bytes, int32_t order, cudaStream_t s) {
   if (ws_bytes < select_ws(n, n_cells, capacity))
     return record(c, DSMC_ERR_ARG, "select: workspace too small");
   if (capacity > INT32_MAX) return record(c, DSMC_ERR_ARG, "select: capacity >= 2^31");
@@ -658,6 +690,7 @@ int launch_select(Ctx* c, const dsmc_gas_t& gas, int32_t n, int32_t n_cells, con
   a.status = status_ptr(c); a.n_cells = n_cells; a.capacity = capacity;
   a.seed = gas.seed; a.key = philox_key(gas.seed); a.step = step; a.step_dev = graph_step_ptr(c); a.fn = gas.fn_over_vc; a.dt = gas.dt;
   sel_model(a, gas);
+  a.order = order;
   const int sms = sm_count(c);
   if (cudaMemsetAsync(w.round_count, 0, sizeof(int32_t) * DSMC_MAX_ROUNDS * 2 + 256, s) != cudaSuccess)
     return DSMC_ERR_CUDA;
@@ -679,14 +712,15 @@ int launch_select(Ctx* c, const dsmc_gas_t& gas, int32_t n, int32_t n_cells, con
     const unsigned sb = (unsigned)((capacity + kScatterChunk - 1) / kScatterChunk) + (capacity <= 0);
     {
       k_sel_rcount<<<sb, 256, 0, s>>>(w.tmp_round, w.offs, n_cells, capacity, w.n_rounds, w.n_chunks, w.chunk_cnt,
-                                      w.sgnew, sgmax);
+                                      w.sgnew, sgmax, order, w.round_count);
       k_sel_rscan<<<DSMC_MAX_ROUNDS, 256, 0, s>>>(w.offs, n_cells, capacity, w.n_rounds, w.round_count,
                                                  round_offsets, w.n_chunks, w.chunk_cnt);
       const int ssm = (int)(sizeof(int) * kScatterWarps * DSMC_MAX_ROUNDS);
       if (cudaFuncSetAttribute(k_sel_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, ssm) != cudaSuccess)
         return DSMC_ERR_CUDA;
       k_sel_scatter<<<sb, kScatterWarps * 32, ssm, s>>>(w.tmp, w.tmp_round, w.tmp_dep, w.offs, n_cells, capacity,
-                                                       w.n_rounds, w.n_chunks, w.chunk_cnt, (int4*)pairs, deps);
+                                                       w.n_rounds, w.n_chunks, w.chunk_cnt, (int4*)pairs, deps,
+                                                       order);
       count_launches(c, 3);
     }
   } else {

@@ -41,6 +41,11 @@ struct SelArgs {
   double sig_const;
   // FP32 screen: sigma(g) g = k32 * g^e32 (e32 = 1 for model 1)
   float k32, e32;
+  // bucket order of the pair list: 0 = rounds; 1 = claim levels, level =
+  // round + (R - 1 - the last round of the pair's cell), R = the step's
+  // round count (the emit pass then keeps each cell's last round in bits
+  // 16.. of tmp_round)
+  int32_t order;
 };
 
 __device__ __forceinline__ double sigma_g(const SelArgs& a, double g) {

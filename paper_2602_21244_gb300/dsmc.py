@@ -20,6 +20,7 @@ DSMC_OK, DSMC_ERR_ARG, DSMC_ERR_CUDA, DSMC_ERR_CAPACITY = 0, -1, -2, -3
 DSMC_ERR_TIMEOUT, DSMC_ERR_NONFINITE, DSMC_ERR_UNSUPPORTED = -4, -5, -6
 PATH_VHS, PATH_JAGER, PATH_NEURAL, PATH_TABLE = 0, 1, 2, 3
 MAX_ROUNDS = 1024
+ORDER_ROUNDS, ORDER_LEVELS = 0, 1   # bucket order of the pair list (DSMC_ORDER_*)
 _ERRS = {-1: "DSMC_ERR_ARG", -2: "DSMC_ERR_CUDA", -3: "DSMC_ERR_CAPACITY", -4: "DSMC_ERR_TIMEOUT",
          -5: "DSMC_ERR_NONFINITE", -6: "DSMC_ERR_UNSUPPORTED"}
 
@@ -130,6 +131,8 @@ def load(build: bool = True):
             "dsmc_select_workspace_size": (sz, [i32, i32, i64]),
             "dsmc_select_pairs": (C.c_int, [vp, P(Gas), i32, i32, vp, vp, vp, vp, vp, u64, i64, vp, vp, vp,
                                             vp, vp, sz, vp]),
+            "dsmc_select_pairs_ordered": (C.c_int, [vp, P(Gas), i32, i32, vp, vp, vp, vp, vp, u64, i64, vp, vp,
+                                                    vp, vp, i32, vp, sz, vp]),
             "dsmc_collide_workspace_size": (sz, [i32]),
             "dsmc_collide_vhs": (C.c_int, [vp, P(Gas), u64, i32, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]),
             "dsmc_jager_chi": (C.c_int, [vp, P(Gas), P(Potential), i32, i64, vp, vp, vp, vp]),
@@ -312,7 +315,7 @@ class Context:
         return out
 
     def select_pairs(self, gas: Gas, cell_start, vx, vy, vz, sgmax, step, capacity, out=None,
-                     ws=None, stream=None):
+                     ws=None, stream=None, order=ORDER_ROUNDS):
         nc = cell_start.numel() - 1
         n = vx.numel()
         dev = vx.device
@@ -324,11 +327,11 @@ class Context:
         nbytes = self._lib.dsmc_select_workspace_size(n, nc, capacity)
         if ws is None or ws.numel() < nbytes:
             ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
-        self._check(self._lib.dsmc_select_pairs(
+        self._check(self._lib.dsmc_select_pairs_ordered(
             self.h, C.byref(gas), n, nc, _ptr(cell_start, torch.int32), _ptr(vx, torch.float64),
             _ptr(vy, torch.float64), _ptr(vz, torch.float64), _ptr(sgmax, torch.float64), step,
             capacity, _ptr(out["pairs"]), _ptr(out["deps"]), _ptr(out["round_offsets"]), _ptr(out["info"]),
-            _ptr(ws), nbytes, _stream(stream)), "select_pairs")
+            order, _ptr(ws), nbytes, _stream(stream)), "select_pairs")
         return out
 
     def _collide_ws(self, n, device, ws=None):

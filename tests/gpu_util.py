@@ -36,8 +36,9 @@ def w_bits_tensor(bits):
     return cuda(bits.view(np.int16))
 
 
-def gpu_step_pieces(wl, sgmax0, step=0, capacity=1 << 22):
-    """Sort, moments and selection on the GPU for a workload dict."""
+def gpu_step_pieces(wl, sgmax0, step=0, capacity=1 << 22, order=0):
+    """Sort, moments and selection on the GPU for a workload dict (order:
+    the pair list's buckets, rounds or claim levels)."""
     T = torch()
     from paper_2602_21244_gb300 import dsmc as D
     C = ctx()
@@ -48,7 +49,7 @@ def gpu_step_pieces(wl, sgmax0, step=0, capacity=1 << 22):
     mom = C.cell_moments(srt["cell_start"], srt["svx"], srt["svy"], srt["svz"])
     sg = cuda(sgmax0).clone()
     sel = C.select_pairs(gas, srt["cell_start"], srt["svx"], srt["svy"], srt["svz"], sg, step,
-                         capacity)
+                         capacity, order=order)
     T.cuda.synchronize()
     return gas, srt, mom, sg, sel
 
@@ -62,8 +63,31 @@ def sel_host(sel):
     return dict(n_pairs=n, n_cand=int(info[1]), n_rounds=R, ro=ro, pairs=pairs)
 
 
+def expected_buckets(ref, n_cells, order):
+    """Bucket of each of the oracle's pairs (candidate order) in the GPU's
+    list: its round, or its claim level = round + (n_rounds - 1 - the last
+    round of its cell), derived here from the oracle's rounds."""
+    r = np.asarray(ref["round"], np.int64)
+    if order == 0 or len(r) == 0:
+        return r
+    last = np.full(n_cells, -1, np.int64)
+    np.maximum.at(last, np.asarray(ref["cell"], np.int64), r)
+    return r + (ref["n_rounds"] - 1) - last[np.asarray(ref["cell"], np.int64)]
+
+
+def expected_deps(ref, bucket):
+    """deps of the oracle's pairs: the 1-based buckets of the previous pairs of
+    i and j in candidate order (0 = none), i | j << 16."""
+    want = np.zeros(len(ref["i"]), np.uint32)
+    last = {}
+    for k, (i, j, b) in enumerate(zip(ref["i"].tolist(), ref["j"].tolist(), np.asarray(bucket).tolist())):
+        want[k] = last.get(i, 0) | (last.get(j, 0) << 16)
+        last[i] = last[j] = b + 1
+    return want
+
+
 def pairs_round_of(sh):
-    """Round index of each pair of a round-major GPU pair list."""
+    """Bucket (round or level) of each pair of a bucket-major GPU pair list."""
     r = np.zeros(sh["n_pairs"], np.int32)
     for q in range(sh["n_rounds"]):
         r[sh["ro"][q]:sh["ro"][q + 1]] = q

@@ -13,8 +13,8 @@ import pytest
 import oracle as O
 from paper_2602_21244_gb300 import workloads as W
 
-from gpu_util import (KB, c_ref, ctx, cuda, gpu_step_pieces, host, pairs_round_of, sel_host,
-                      torch, w_bits_tensor)
+from gpu_util import (KB, c_ref, ctx, cuda, expected_buckets, expected_deps, gpu_step_pieces, host,
+                      pairs_round_of, sel_host, torch, w_bits_tensor)
 
 pytestmark = pytest.mark.gpu
 
@@ -172,37 +172,38 @@ def _sgmax0(w, gas):
     return O.sigma_g_max_init(gas, w["T_cell"], 5.0)
 
 
+@pytest.mark.parametrize("order", [0, 1])
 @pytest.mark.parametrize("name,model", [("couette", 0), ("cavity40", 0), ("hyper01", 1), ("hyper01", 0)])
-def test_select_bit_exact(name, model):
+def test_select_bit_exact(name, model, order):
+    """order 0: buckets are rounds; 1: claim levels (round + the cell's
+    slack to the last round)."""
     w = dict(wl(name))
     w["gas"] = dict(w["gas"], model=model)
     gas = O.make_gas(**w["gas"])
     perm, cs, sx, sy, sz = oracle_sorted(w)
     sg0 = _sgmax0(w, gas)
     ref = O.select_pairs(gas, cs, sx, sy, sz, sg0, 3, capacity=1 << 22)
-    _, srt, mom, sg, sel = gpu_step_pieces(w, sg0, step=3)
+    _, srt, mom, sg, sel = gpu_step_pieces(w, sg0, step=3, order=order)
     assert ctx().sync_status() == 0
     sh = sel_host(sel)
     assert sh["n_pairs"] == ref["n_pairs"] and sh["n_cand"] == ref["n_cand"]
     assert sh["n_rounds"] == ref["n_rounds"]
     p = sh["pairs"]
     rr = pairs_round_of(sh)
-    order = np.lexsort((p[:, 3], p[:, 2]))
-    assert np.array_equal(p[order, 0], ref["i"]) and np.array_equal(p[order, 1], ref["j"])
-    assert np.array_equal(p[order, 2], ref["cell"]) and np.array_equal(p[order, 3], ref["m"])
-    assert np.array_equal(rr[order], ref["round"])
-    # inside a round the list is in cell order, candidate order within a cell
-    ro_ = np.lexsort((ref["m"], ref["cell"], ref["round"]))
+    bucket = expected_buckets(ref, w["n_cells"], order)
+    if order == 1 and name == "hyper01":
+        assert not np.array_equal(bucket, ref["round"])   # there the levels do move pairs
+    order_ = np.lexsort((p[:, 3], p[:, 2]))
+    assert np.array_equal(p[order_, 0], ref["i"]) and np.array_equal(p[order_, 1], ref["j"])
+    assert np.array_equal(p[order_, 2], ref["cell"]) and np.array_equal(p[order_, 3], ref["m"])
+    assert np.array_equal(rr[order_], bucket)
+    # inside a bucket the list is in cell order, candidate order within a cell
+    ro_ = np.lexsort((ref["m"], ref["cell"], bucket))
     assert np.array_equal(p[:, 2], ref["cell"][ro_]) and np.array_equal(p[:, 3], ref["m"][ro_])
-    # deps: 1-based rounds of the previous pair of each particle, derived here
-    # from the oracle's pairs in candidate order and its rounds
+    # deps: 1-based buckets of the previous pair of each particle, derived
+    # here from the oracle's pairs in candidate order and its rounds
     deps = host(sel["deps"])[:sh["n_pairs"]].view(np.uint32)
-    want = np.zeros(len(ref["i"]), np.uint32)
-    last = {}
-    for k, (i, j, r) in enumerate(zip(ref["i"].tolist(), ref["j"].tolist(), ref["round"].tolist())):
-        want[k] = last.get(i, 0) | (last.get(j, 0) << 16)
-        last[i] = last[j] = r + 1
-    assert np.array_equal(deps[order], want)
+    assert np.array_equal(deps[order_], expected_deps(ref, bucket))
     rel = np.abs(host(sg) - ref["sgmax"]) / ref["sgmax"]
     assert rel.max() <= (0.0 if model == 1 else 4e-16)
 
@@ -222,8 +223,9 @@ def _dense_cells(seed=5):
     return cs, v[:, 0].copy(), v[:, 1].copy(), v[:, 2].copy()
 
 
+@pytest.mark.parametrize("order", [0, 1])
 @pytest.mark.parametrize("model", [1, 0])
-def test_select_bit_exact_dense_cells(model):
+def test_select_bit_exact_dense_cells(model, order):
     cs, vx, vy, vz = _dense_cells()
     nc = len(cs) - 1
     gas_d = dict(mass=W.M_AR, d_ref=4.17e-10, omega=0.81, T_ref=273.0, fn_over_vc=1e21, dt=1e-7,
@@ -235,18 +237,22 @@ def test_select_bit_exact_dense_cells(model):
     from paper_2602_21244_gb300 import dsmc as D
     C = ctx()
     sg = cuda(sg0).clone()
-    sel = C.select_pairs(D.make_gas(gas_d), cuda(cs), cuda(vx), cuda(vy), cuda(vz), sg, 2, 1 << 22)
+    sel = C.select_pairs(D.make_gas(gas_d), cuda(cs), cuda(vx), cuda(vy), cuda(vz), sg, 2, 1 << 22,
+                         order=order)
     assert C.sync_status() == 0
     sh = sel_host(sel)
     assert sh["n_pairs"] == ref["n_pairs"] and sh["n_cand"] == ref["n_cand"]
     assert sh["n_rounds"] == ref["n_rounds"]
     p = sh["pairs"]
     rr = pairs_round_of(sh)
-    order = np.lexsort((p[:, 3], p[:, 2]))
-    assert np.array_equal(p[order, 0], ref["i"]) and np.array_equal(p[order, 1], ref["j"])
-    assert np.array_equal(p[order, 3], ref["m"]) and np.array_equal(rr[order], ref["round"])
-    ro_ = np.lexsort((ref["m"], ref["cell"], ref["round"]))
+    bucket = expected_buckets(ref, nc, order)
+    order_ = np.lexsort((p[:, 3], p[:, 2]))
+    assert np.array_equal(p[order_, 0], ref["i"]) and np.array_equal(p[order_, 1], ref["j"])
+    assert np.array_equal(p[order_, 3], ref["m"]) and np.array_equal(rr[order_], bucket)
+    ro_ = np.lexsort((ref["m"], ref["cell"], bucket))
     assert np.array_equal(p[:, 2], ref["cell"][ro_]) and np.array_equal(p[:, 3], ref["m"][ro_])
+    deps = host(sel["deps"])[:sh["n_pairs"]].view(np.uint32)
+    assert np.array_equal(deps[order_], expected_deps(ref, bucket))
     rel = np.abs(host(sg) - ref["sgmax"]) / ref["sgmax"]
     assert rel.max() <= (0.0 if model == 1 else 4e-16)
 
@@ -496,7 +502,7 @@ def test_c4_full_size_neural_step():
     """The hypersonic gas at its full size (9,144,283 particles, 150,000
     cells) through dsmc_step on the neural path, as the bench times it.
     Bit-exact: perm, cell_start, the step's pair, candidate and round counts,
-    every pair (cell, candidate, particles, round).  Sampled: 20,000 pairs
+    every pair (cell, candidate, particles, claim level).  Sampled: 20,000 pairs
     whose particles collide exactly once in the step -- their inputs are the
     sorted pre-collision state and their final relative velocity is the
     pair's post-collision one scaled by moment matching's alpha > 0, so its
@@ -530,7 +536,9 @@ def test_c4_full_size_neural_step():
     p = sh["pairs"]
     order = np.lexsort((p[:, 3], p[:, 2]))
     assert np.array_equal(p[order, 0], pr["i"]) and np.array_equal(p[order, 1], pr["j"])
-    assert np.array_equal(p[order, 3], pr["m"]) and np.array_equal(pairs_round_of(sh)[order], pr["round"])
+    # the neural step buckets its pairs by claim level
+    assert np.array_equal(p[order, 3], pr["m"])
+    assert np.array_equal(pairs_round_of(sh)[order], expected_buckets(pr, nc, 1))
     # pairs whose two particles collide only once in the step
     cnt = np.bincount(np.concatenate([pr["i"], pr["j"]]), minlength=n)
     once = np.flatnonzero((cnt[pr["i"]] == 1) & (cnt[pr["j"]] == 1))
