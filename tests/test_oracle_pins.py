@@ -164,6 +164,38 @@ def test_rounds_reproduce_sequential_order():
         assert pr["i"][q] in pts or pr["j"][q] in pts
 
 
+def test_claim_levels_reproduce_sequential_order():
+    # Reading R4 with the neural step's bucketing: level = round + (R - 1 -
+    # the last round of the pair's cell).  Each level's pairs share no
+    # particle, each particle's pairs keep their order, and applying the
+    # pairs level-major gives bit-for-bit the candidate-order result; the
+    # reversed level order (a plausible sign slip) does not.
+    wl = W.hypersonic(scale=0.06)
+    gas = O.make_gas(**wl["gas"])
+    perm, cs, sx, sy, sz = O.sort_cells(wl["cell_id"], wl["vx"], wl["vy"], wl["vz"], wl["n_cells"])
+    sg = O.sigma_g_max_init(gas, wl["T_cell"], 5.0)
+    pr = O.select_pairs(gas, cs, sx, sy, sz, sg, 0, capacity=1 << 22)
+    R = pr["n_rounds"]
+    last = np.full(wl["n_cells"], -1)
+    np.maximum.at(last, pr["cell"], pr["round"])
+    lvl = pr["round"] + (R - 1) - last[pr["cell"]]
+    assert lvl.min() >= 0 and lvl.max() == R - 1 and not np.array_equal(lvl, pr["round"])
+    for v in range(R):
+        sel = lvl == v
+        parts = np.concatenate([pr["i"][sel], pr["j"][sel]])
+        assert len(np.unique(parts)) == len(parts)
+    a = O.collide_vhs(gas, pr, 0, sx, sy, sz)
+
+    def apply(key):
+        order = np.lexsort((pr["m"], pr["cell"], key))
+        pr2 = {k: (v[order] if isinstance(v, np.ndarray) and len(v) == pr["n_pairs"] else v)
+               for k, v in pr.items()}
+        return O.collide_vhs(gas, pr2, 0, sx, sy, sz)
+    for x, y in zip(a, apply(lvl)):
+        assert np.array_equal(x, y)
+    assert not all(np.array_equal(x, y) for x, y in zip(a, apply((R - 1) - lvl)))
+
+
 def test_sigma_g_max_only_grows_and_capacity():
     wl = W.couette()
     gas = O.make_gas(**wl["gas"])
